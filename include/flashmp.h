@@ -1,0 +1,208 @@
+/*
+ * flashmp.h - C ABI of the B300 (sm_103a) FlashMP subdomain-transform solver.
+ *
+ * Problem (Sec. II-A, Eqs. 2-5; Sec. III-A, Eq. 7): the Crank-Nicolson FDTD
+ * system (eps + beta K) E = R on a Yee grid with perfectly conducting walls,
+ * K = C^T C the discrete double curl, beta = (dt/2)^2 in grid units (h = c = 1).
+ * It is solved by restarted flexible GMRES (Sec. IV-A) preconditioned by
+ * restricted additive Schwarz (Sec. II-B) whose subdomain problems are solved
+ * exactly by discrete transforms (Sec. III-A Steps 1-3, Algorithm 1
+ * exact_solve): DCT-II / DST-I along x, y, z per component, a closed-form 3x3
+ * inverse per transform mode (Eq. 12), inverse transforms.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Grid: nx*ny*nz unit cells. Field arrays are caller-owned DEVICE memory,
+ * contiguous float64, 8-byte aligned (16-byte for best speed), laid out
+ * [3][nz][ny][nx] with x fastest:
+ *   edge fields (E, b, x, r, z, J): slot (c,k,j,i) is Ex(i+1/2,j,k),
+ *     Ey(i,j+1/2,k), Ez(i,j,k+1/2). Wall slots (Ex: j==0||k==0;
+ *     Ey: i==0||k==0; Ez: i==0||j==0) must hold 0 on input and are written 0.
+ *   face fields (H): slot (c,k,j,i) is Hx(i,j+1/2,k+1/2), Hy(i+1/2,j,k+1/2),
+ *     Hz(i+1/2,j+1/2,k); wall faces (Hx: i==0, Hy: j==0, Hz: k==0) hold 0.
+ *   cell arrays (eps_cell): [nz][ny][nx].
+ * Box-local arrays (fmp_box_solve) use the same layout on an mx*my*mz box.
+ *
+ * Streams: every call is enqueued on the context's stream (a cudaStream_t
+ * passed as void*; NULL = legacy default stream). Calls that fill an
+ * fmp_solve_info, and fmp_setup / fmp_get_* calls, synchronise that stream;
+ * the others are asynchronous.
+ *
+ * Ownership: the library owns its context, tables, work lists, Krylov basis
+ * and scratch (device memory allocated in fmp_setup / on first solve, freed in
+ * fmp_destroy). Callers own every pointer they pass.
+ *
+ * Errors: calls return an fmp_status; nothing throws or exits. A CUDA error is
+ * latched in the context; that call and every later call on the context
+ * return FMP_ERR_CUDA. Argument errors return FMP_ERR_ARG and change nothing.
+ */
+#ifndef FLASHMP_H
+#define FLASHMP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FMP_ABI_VERSION 1
+
+typedef struct fmp_ctx fmp_ctx; /* opaque, library-owned */
+
+typedef enum fmp_status {
+    FMP_OK = 0,
+    FMP_ERR_ARG = -1,             /* invalid argument, shape or null pointer   */
+    FMP_ERR_CUDA = -2,            /* a CUDA call failed (latched)              */
+    FMP_ERR_NOMEM = -3,           /* device allocation failed                  */
+    FMP_ERR_NOT_CONVERGED = -4,   /* max_iters reached; best x written         */
+    FMP_ERR_BREAKDOWN = -5,       /* Krylov breakdown before convergence       */
+    FMP_ERR_NONFINITE = -6,       /* NaN/Inf met in a residual or coefficient  */
+    FMP_ERR_UNSUPPORTED = -7      /* option not available in this build        */
+} fmp_status;
+
+/* Arithmetic of the transforms inside the preconditioner. The Krylov side
+ * (dots, norms, Givens, SpMV, true residual) is float64 in every mode. */
+typedef enum fmp_precision {
+    FMP_PREC_FP64 = 0,   /* plain float64 transforms                          */
+    FMP_PREC_TF32 = 1,   /* tf32 tensor-core inputs, fp32 accumulation        */
+    FMP_PREC_FP16 = 2,   /* fp16 tensor-core inputs (scaled), fp32 accumulate */
+    FMP_PREC_BF16 = 3    /* bf16 tensor-core inputs, fp32 accumulation        */
+} fmp_precision;
+
+typedef enum fmp_krylov_kind {
+    FMP_KRYLOV_FGMRES = 0,    /* right-preconditioned flexible GMRES(restart) */
+    FMP_KRYLOV_BICGSTAB = 1   /* right-preconditioned BiCGSTAB                */
+} fmp_krylov_kind;
+
+typedef struct fmp_grid { int nx, ny, nz; } fmp_grid; /* cells, h = 1 */
+
+/* Tensor-product partition into subdomains (Sec. II-B): cuts[a] is a HOST
+ * array of n_cuts[a] owned sizes along axis a (x, y, z) summing to the grid
+ * extent. Box (bx,by,bz) owns cells [a0, a0+n) per axis; its extended box is
+ * [a0-overlap, a0+n+overlap) clipped to the grid. overlap >= 1 is required
+ * when there is more than one box (the owned low-face edges must lie inside
+ * the extended box). Boxes are numbered z-major, then y, then x. */
+typedef struct fmp_subdomains {
+    int n_cuts[3];
+    const int* cuts[3];
+    int overlap;
+} fmp_subdomains;
+
+typedef struct fmp_options {
+    int precision;    /* fmp_precision (default FMP_PREC_FP64)                 */
+    int krylov;       /* fmp_krylov_kind (default FMP_KRYLOV_FGMRES)           */
+    int restart;      /* FGMRES restart length, 1..32 (default 30)             */
+    double rtol;      /* stop when ||b - A x||_2 / ||b||_2 <= rtol (1e-8)      */
+    int max_iters;    /* cap on preconditioner applications (default 1000)     */
+    int use_graph;    /* 1: replay the Arnoldi step as a CUDA graph            */
+    int use_learned;  /* reserved, must be 0                                   */
+    int timing;       /* 1: fill the ms_* phase times (adds synchronisation)   */
+} fmp_options;
+
+typedef struct fmp_solve_info {
+    int iters;             /* preconditioner applications (Arnoldi steps)      */
+    int restarts;          /* completed restart cycles                         */
+    double true_rel_res;   /* ||b - A x||_2 / ||b||_2 recomputed in float64    */
+    double est_rel_res;    /* last Krylov residual estimate                    */
+    float ms_precond, ms_spmv, ms_orth, ms_total; /* phase times if timing=1 */
+    int used_fallback;     /* reserved                                         */
+    int status;            /* fmp_status of the solve                          */
+} fmp_solve_info;
+
+/* Library version of this header (FMP_ABI_VERSION). */
+int fmp_abi_version(void);
+
+/* Static, human-readable name of a status code. */
+const char* fmp_status_string(int status);
+
+/* Fill *opt with the defaults listed in fmp_options. opt must not be NULL. */
+void fmp_default_options(fmp_options* opt);
+
+/* Create a context for one grid, material, beta and partition.
+ *   eps_cell: DEVICE [nz][ny][nx] relative permittivity per cell (> 0), or
+ *             NULL for eps = 1. The edge permittivity is the mean of the four
+ *             cells around each edge (Sec. II-A with eps kept per cell).
+ *   beta:     (dt/2)^2 > 0 (Eq. 5 / Eq. 7: alpha = dt^2/4).
+ *   sd:       partition (see fmp_subdomains); NULL = one box = whole grid.
+ *   opt:      options; NULL = defaults.
+ *   stream:   cudaStream_t used by every later call on this context.
+ * Builds, per distinct box extent m, the DCT-II/DST-I tables and singular
+ * values sigma_k = 2 sin(pi k / 2m) of the difference operator (Eq. 8), and per
+ * box its mean edge permittivity eps_bar (the subdomain's constant
+ * coefficient). On success *out owns device memory; release it with
+ * fmp_destroy. Errors: FMP_ERR_ARG (bad sizes or overlap, a box extent < 2),
+ * FMP_ERR_UNSUPPORTED (an extended box extent above 80 cells),
+ * FMP_ERR_NOMEM, FMP_ERR_CUDA. */
+int fmp_setup(fmp_ctx** out, fmp_grid g, const double* eps_cell, double beta,
+              const fmp_subdomains* sd, const fmp_options* opt, void* stream);
+
+/* Free every resource of ctx (NULL is a no-op). Synchronises its stream. */
+void fmp_destroy(fmp_ctx* ctx);
+
+/* Replace the options (precision, Krylov kind, tolerances...). */
+int fmp_set_options(fmp_ctx* ctx, const fmp_options* opt);
+
+/* Replace the stream used by later calls. */
+int fmp_set_stream(fmp_ctx* ctx, void* stream);
+
+/* Copy the edge permittivity [3][nz][ny][nx] (wall slots 0) to DEVICE out. */
+int fmp_get_eps_edge(fmp_ctx* ctx, double* out);
+
+/* Number of subdomain boxes. */
+int fmp_get_num_boxes(fmp_ctx* ctx, int* n);
+
+/* Geometry of box i (HOST outputs, each int[3] in x,y,z order, any may be
+ * NULL): extended low corner, extents m, owned low corner (global), owned
+ * extents, and its eps_bar. */
+int fmp_get_box(fmp_ctx* ctx, int i, int* ext_lo, int* m, int* own_lo,
+                int* own_n, double* eps_bar);
+
+/* y = c_eps * eps_edge o x + c_k * K x  (the operator of Eq. 7 when
+ * c_eps = 1, c_k = beta; the CN right-hand-side operator with c_k = -beta).
+ * K is the 13-point Yee double curl with PEC walls. x, y: DEVICE edge fields,
+ * must not alias. */
+int fmp_curlcurl_apply(fmp_ctx* ctx, const double* x, double* y, double c_eps,
+                       double c_k);
+
+/* z = M_RAS^{-1} r = sum_i S_i^{0T} (eps_bar_i I + beta K_i)^{-1} S_i^gamma r
+ * (Sec. II-B), each box solved by the transform route of Algorithm 1
+ * (exact_solve) in the context's precision. r, z: DEVICE edge fields, must not
+ * alias. Every slot of z is written (each is owned by exactly one box). */
+int fmp_precond_apply(fmp_ctx* ctx, const double* r, double* z);
+
+/* Exact solve on box i alone (Algorithm 1 exact_solve, no gather/scatter):
+ * x = (eps_bar_i I + beta K_i)^{-1} r with r, x DEVICE box-local arrays
+ * [3][mz][my][mx] of box i (box-wall slots of r must be 0; all of x written).
+ * With one box covering the grid this is the exact inverse of Eq. 7. */
+int fmp_box_solve(fmp_ctx* ctx, int i, const double* r, double* x);
+
+/* Solve (eps + beta K) x = b with the context's Krylov method, preconditioned
+ * by fmp_precond_apply, to ||b - A x|| / ||b|| <= rtol (true residual,
+ * recomputed in float64). b: DEVICE edge field; x: DEVICE edge field holding
+ * the initial guess on input and the solution on output (may not alias b).
+ * info (HOST, may be NULL) receives counts, residuals and times. Returns
+ * FMP_OK, or FMP_ERR_NOT_CONVERGED / _BREAKDOWN / _NONFINITE with the best x
+ * written. Synchronises the stream. */
+int fmp_krylov_solve(fmp_ctx* ctx, const double* b, double* x,
+                     fmp_solve_info* info);
+
+/* R = (eps - beta K) E + dt C^T H - dt J   (right side of Eq. 4 with eps and a
+ * current J). E, J, R: DEVICE edge fields (J may be NULL = 0); H: DEVICE face
+ * field. dt must satisfy dt^2/4 == beta (relative 1e-12). */
+int fmp_cn_rhs(fmp_ctx* ctx, const double* E, const double* H,
+               const double* J, double dt, double* R);
+
+/* H <- H - (dt/2) C (E_new + E_old)   (Eq. 3). DEVICE arrays. */
+int fmp_h_update(fmp_ctx* ctx, double* H, const double* E_new,
+                 const double* E_old, double dt);
+
+/* One Crank-Nicolson step (Sec. II-A): build R (fmp_cn_rhs), solve
+ * (eps + beta K) E^{n+1} = R with E^n as the initial guess (fmp_krylov_solve),
+ * then update H (fmp_h_update). E, H: DEVICE, updated in place. J: DEVICE edge
+ * current at t^{n+1/2} or NULL. info as in fmp_krylov_solve. */
+int fmp_cn_step(fmp_ctx* ctx, double* E, double* H, const double* J, double dt,
+                fmp_solve_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLASHMP_H */

@@ -1,0 +1,402 @@
+// C ABI entry points: context set-up (tables, partition, work lists, edge
+// permittivity, subdomain means), operator applies, preconditioner, Krylov
+// solve and the Crank-Nicolson step. Declarations and contracts are in
+// include/flashmp.h.
+#include "fmp_internal.h"
+
+#include <cmath>
+#include <cstring>
+#include <algorithm>
+#include <new>
+#include <vector>
+
+int fmp_column_tile(const int* max_m);
+
+int fmp_latch(fmp_ctx* c, cudaError_t e) {
+    if (c && c->latched == cudaSuccess) c->latched = e;
+    (void)cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? FMP_ERR_NOMEM : FMP_ERR_CUDA;
+}
+
+namespace {
+
+// ---- 1-D transform tables (Sec. III-A, Eq. 8) -------------------------------
+// For an extent m: DCT-II C[k][i] = sqrt((2 - [k==0]) / m) cos(pi k (2i+1) / 2m),
+// zero-padded DST-I S[k][j] = sqrt(2/m) sin(pi k j / m), and the singular
+// values sigma_k = 2 sin(pi k / 2m). Arguments are reduced exactly in integers
+// before the call to cos/sin.
+void build_tables(int m, double* C, double* S, double* sig) {
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k < m; ++k) {
+        const double a = std::sqrt((k == 0 ? 1.0 : 2.0) / m);
+        for (int i = 0; i < m; ++i) {
+            const long long p = ((long long)k * (2 * i + 1)) % (4LL * m);  // angle pi p / 2m
+            C[k * m + i] = a * std::cos(pi * (double)p / (2.0 * m));
+            const long long q = ((long long)k * i) % (2LL * m);             // angle pi q / m
+            S[k * m + i] = std::sqrt(2.0 / m) * std::sin(pi * (double)q / (double)m);
+        }
+        sig[k] = 2.0 * std::sin(pi * (double)k / (2.0 * m));
+    }
+}
+
+bool valid_ctx(fmp_ctx* c) { return c != nullptr; }
+
+int latched(fmp_ctx* c) { return c->latched != cudaSuccess ? FMP_ERR_CUDA : FMP_OK; }
+
+template <class T>
+cudaError_t upload(T** dptr, const std::vector<T>& h, cudaStream_t s) {
+    cudaError_t e = cudaMalloc(dptr, sizeof(T) * (h.empty() ? 1 : h.size()));
+    if (e) return e;
+    if (h.empty()) return cudaSuccess;
+    e = cudaMemcpyAsync(*dptr, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, s);
+    if (e) return e;
+    return cudaStreamSynchronize(s);   // h may go out of scope after return
+}
+
+// Work lists of the three transform passes for a set of boxes.
+void build_items(const std::vector<FmpBox>& boxes, int ct, std::vector<int4>& A, std::vector<int2>& Bv,
+                 std::vector<int4>& Cv) {
+    for (int b = 0; b < (int)boxes.size(); ++b) {
+        const FmpBox& x = boxes[b];
+        for (int c = 0; c < 3; ++c)
+            for (int z = 0; z < x.m[2]; ++z) A.push_back(make_int4(b, c, z, 0));
+        const int nxy = x.m[0] * x.m[1];
+        for (int q = 0; q < nxy; q += ct) Bv.push_back(make_int2(b, q));
+        for (int c = 0; c < 3; ++c)
+            for (int z = x.own_lo[2]; z < x.own_lo[2] + x.own_n[2]; ++z) Cv.push_back(make_int4(b, c, z, 0));
+    }
+}
+
+cudaError_t make_plan(FmpPlan& p, const std::vector<FmpBox>& boxes, cudaStream_t s) {
+    p.n_boxes = (int)boxes.size();
+    p.max_m[0] = p.max_m[1] = p.max_m[2] = 0;
+    long long scr = 0;
+    for (const FmpBox& b : boxes) {
+        for (int a = 0; a < 3; ++a) p.max_m[a] = b.m[a] > p.max_m[a] ? b.m[a] : p.max_m[a];
+        scr = b.scr_off + 3LL * b.m[0] * b.m[1] * b.m[2] > scr ? b.scr_off + 3LL * b.m[0] * b.m[1] * b.m[2] : scr;
+    }
+    p.scratch_doubles = scr;
+    std::vector<int4> A, C;
+    std::vector<int2> B;
+    build_items(boxes, fmp_column_tile(p.max_m), A, B, C);
+    p.n_items_a = (int)A.size(); p.n_items_b = (int)B.size(); p.n_items_c = (int)C.size();
+    cudaError_t e;
+    if ((e = upload(&p.d_boxes, boxes, s))) return e;
+    if ((e = upload(&p.d_items_a, A, s))) return e;
+    if ((e = upload(&p.d_items_b, B, s))) return e;
+    if ((e = upload(&p.d_items_c, C, s))) return e;
+    return cudaSuccess;
+}
+
+void free_plan(FmpPlan& p) {
+    cudaFree(p.d_boxes); cudaFree(p.d_items_a); cudaFree(p.d_items_b); cudaFree(p.d_items_c);
+    p = FmpPlan{};
+}
+
+bool dt_matches(double beta, double dt) {
+    const double b2 = dt * dt / 4.0;
+    return std::fabs(b2 - beta) <= 1e-12 * std::fabs(beta);
+}
+
+}  // namespace
+
+int fmp_precond(fmp_ctx* c, const double* r, double* z) {
+    switch (c->opt.precision) {
+        case FMP_PREC_FP64:
+            FMP_CK(fmp_launch_transform_solve_fp64(c->ras, c->d_tabs, r, z, c->d_scratch, c->nx, c->ny, c->nz,
+                                                   c->beta, c->stream));
+            return FMP_OK;
+        default:
+            return FMP_ERR_UNSUPPORTED;
+    }
+}
+
+extern "C" {
+
+int fmp_abi_version(void) { return FMP_ABI_VERSION; }
+
+const char* fmp_status_string(int s) {
+    switch (s) {
+        case FMP_OK: return "FMP_OK";
+        case FMP_ERR_ARG: return "FMP_ERR_ARG: invalid argument";
+        case FMP_ERR_CUDA: return "FMP_ERR_CUDA: a CUDA call failed (latched in the context)";
+        case FMP_ERR_NOMEM: return "FMP_ERR_NOMEM: device allocation failed";
+        case FMP_ERR_NOT_CONVERGED: return "FMP_ERR_NOT_CONVERGED: max_iters reached";
+        case FMP_ERR_BREAKDOWN: return "FMP_ERR_BREAKDOWN: Krylov breakdown";
+        case FMP_ERR_NONFINITE: return "FMP_ERR_NONFINITE: non-finite value met";
+        case FMP_ERR_UNSUPPORTED: return "FMP_ERR_UNSUPPORTED: option not available";
+        default: return "unknown fmp_status";
+    }
+}
+
+void fmp_default_options(fmp_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = FMP_PREC_FP64;
+    o->krylov = FMP_KRYLOV_FGMRES;
+    o->restart = 30;
+    o->rtol = 1e-8;
+    o->max_iters = 1000;
+}
+
+static int check_options(const fmp_options* o) {
+    if (o->precision < FMP_PREC_FP64 || o->precision > FMP_PREC_BF16) return FMP_ERR_ARG;
+    if (o->krylov != FMP_KRYLOV_FGMRES && o->krylov != FMP_KRYLOV_BICGSTAB) return FMP_ERR_ARG;
+    if (o->restart < 1 || o->restart > FMP_MAX_RESTART) return FMP_ERR_ARG;
+    if (!(o->rtol > 0.0) || o->max_iters < 1) return FMP_ERR_ARG;
+    if (o->use_learned != 0) return FMP_ERR_UNSUPPORTED;
+    return FMP_OK;
+}
+
+int fmp_setup(fmp_ctx** out, fmp_grid g, const double* eps_cell, double beta, const fmp_subdomains* sd,
+              const fmp_options* opt, void* stream) {
+    if (!out) return FMP_ERR_ARG;
+    *out = nullptr;
+    if (g.nx < 2 || g.ny < 2 || g.nz < 2 || !(beta > 0.0) || !std::isfinite(beta)) return FMP_ERR_ARG;
+    if ((long long)g.nx * g.ny * g.nz * 3 > (1LL << 40)) return FMP_ERR_ARG;
+    fmp_options o;
+    fmp_default_options(&o);
+    if (opt) o = *opt;
+    int rc = check_options(&o);
+    if (rc != FMP_OK) return rc;
+
+    // per-axis owned intervals
+    const int n_axis[3] = {g.nx, g.ny, g.nz};
+    std::vector<int> cuts[3];
+    int overlap = 0;
+    for (int a = 0; a < 3; ++a) {
+        if (sd && sd->n_cuts[a] > 0) {
+            if (!sd->cuts[a]) return FMP_ERR_ARG;
+            long long sum = 0;
+            for (int t = 0; t < sd->n_cuts[a]; ++t) {
+                if (sd->cuts[a][t] < 1) return FMP_ERR_ARG;
+                cuts[a].push_back(sd->cuts[a][t]);
+                sum += sd->cuts[a][t];
+            }
+            if (sum != n_axis[a]) return FMP_ERR_ARG;
+        } else {
+            cuts[a].push_back(n_axis[a]);
+        }
+    }
+    if (sd) overlap = sd->overlap;
+    if (overlap < 0) return FMP_ERR_ARG;
+    const long long nbox = (long long)cuts[0].size() * cuts[1].size() * cuts[2].size();
+    if (nbox > 1 && overlap < 1) return FMP_ERR_ARG;
+    if (nbox > (1 << 24)) return FMP_ERR_ARG;
+
+    fmp_ctx* c = new (std::nothrow) fmp_ctx();
+    if (!c) return FMP_ERR_NOMEM;
+    c->nx = g.nx; c->ny = g.ny; c->nz = g.nz;
+    c->n_slots = 3ull * g.nx * g.ny * g.nz;
+    c->beta = beta;
+    c->opt = o;
+    c->stream = (cudaStream_t)stream;
+    auto fail = [&](int code) { fmp_destroy(c); return code; };
+
+    // boxes, z-major then y then x
+    std::vector<int> lo[3];
+    for (int a = 0; a < 3; ++a) {
+        int acc = 0;
+        for (int v : cuts[a]) { lo[a].push_back(acc); acc += v; }
+    }
+    std::map<int, int> ext_index;  // extent -> table slot
+    std::vector<FmpBox> boxes;
+    for (size_t bz = 0; bz < cuts[2].size(); ++bz)
+        for (size_t by = 0; by < cuts[1].size(); ++by)
+            for (size_t bx = 0; bx < cuts[0].size(); ++bx) {
+                FmpBox b{};
+                const size_t idx[3] = {bx, by, bz};
+                for (int a = 0; a < 3; ++a) {
+                    const int o0 = lo[a][idx[a]], n0 = cuts[a][idx[a]];
+                    const int e0 = o0 - overlap < 0 ? 0 : o0 - overlap;
+                    const int e1 = o0 + n0 + overlap > n_axis[a] ? n_axis[a] : o0 + n0 + overlap;
+                    b.ext_lo[a] = e0;
+                    b.m[a] = e1 - e0;
+                    b.own_lo[a] = o0 - e0;
+                    b.own_n[a] = n0;
+                    if (b.m[a] < 2 || b.m[a] > FMP_MAX_EXTENT) { return fail(b.m[a] > FMP_MAX_EXTENT ? FMP_ERR_UNSUPPORTED : FMP_ERR_ARG); }
+                    ext_index[b.m[a]] = 0;
+                    c->h_own_lo_global.push_back(o0);
+                }
+                boxes.push_back(b);
+            }
+    // tables
+    std::vector<double> tabs;
+    std::map<int, int> off_c, off_s, off_sig;
+    for (auto& kv : ext_index) {
+        const int m = kv.first;
+        off_c[m] = (int)tabs.size(); tabs.resize(tabs.size() + (size_t)m * m);
+        off_s[m] = (int)tabs.size(); tabs.resize(tabs.size() + (size_t)m * m);
+        off_sig[m] = (int)tabs.size(); tabs.resize(tabs.size() + m);
+        build_tables(m, &tabs[off_c[m]], &tabs[off_s[m]], &tabs[off_sig[m]]);
+    }
+    long long scr = 0;
+    for (FmpBox& b : boxes) {
+        for (int a = 0; a < 3; ++a) {
+            b.dct_off[a] = off_c[b.m[a]];
+            b.dst_off[a] = off_s[b.m[a]];
+            b.sig_off[a] = off_sig[b.m[a]];
+        }
+        b.scr_off = scr;
+        scr += 3LL * b.m[0] * b.m[1] * b.m[2];
+    }
+    cudaError_t e;
+#define SETUP_CK(x) do { if ((e = (x)) != cudaSuccess) { (void)cudaGetLastError(); \
+        return fail(e == cudaErrorMemoryAllocation ? FMP_ERR_NOMEM : FMP_ERR_CUDA); } } while (0)
+    for (int t = 0; t < 8; ++t) SETUP_CK(cudaEventCreate(&c->ev[t]));
+    SETUP_CK(cudaMallocHost(&c->h_pinned, 64 * sizeof(double)));
+    SETUP_CK(upload(&c->d_tabs, tabs, c->stream));
+    c->tab_len = tabs.size();
+    SETUP_CK(cudaMalloc(&c->d_eps_edge, sizeof(double) * c->n_slots));
+    SETUP_CK(fmp_launch_eps_edge(eps_cell, c->d_eps_edge, g.nx, g.ny, g.nz, c->stream));
+    SETUP_CK(make_plan(c->ras, boxes, c->stream));
+    SETUP_CK(fmp_launch_eps_bar(c->d_eps_edge, c->ras.d_boxes, c->ras.n_boxes, g.nx, g.ny, g.nz, c->stream));
+    SETUP_CK(cudaMemcpyAsync(boxes.data(), c->ras.d_boxes, sizeof(FmpBox) * boxes.size(), cudaMemcpyDeviceToHost,
+                             c->stream));
+    SETUP_CK(cudaStreamSynchronize(c->stream));
+    c->h_boxes = boxes;
+    SETUP_CK(cudaMalloc(&c->d_scratch, sizeof(double) * (size_t)c->ras.scratch_doubles));
+    long long big = 0;
+    for (const FmpBox& b : boxes) big = std::max(big, 3LL * b.m[0] * b.m[1] * b.m[2]);
+    SETUP_CK(cudaMalloc(&c->d_scratch1, sizeof(double) * (size_t)big));
+    SETUP_CK(cudaMalloc(&c->d_partials, sizeof(double) * 148 * 4 * 32));
+    SETUP_CK(cudaMalloc(&c->d_ticket, sizeof(unsigned int) * 4));
+    SETUP_CK(cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned int) * 4, c->stream));
+    SETUP_CK(cudaMalloc(&c->d_tmp, sizeof(double) * c->n_slots));
+    SETUP_CK(cudaMalloc(&c->d_tmp2, sizeof(double) * c->n_slots));
+    SETUP_CK(cudaStreamSynchronize(c->stream));
+#undef SETUP_CK
+    *out = c;
+    return FMP_OK;
+}
+
+void fmp_destroy(fmp_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_plan(c->ras);
+    free_plan(c->single);
+    cudaFree(c->d_eps_edge); cudaFree(c->d_tabs); cudaFree(c->d_scratch); cudaFree(c->d_scratch1);
+    cudaFree(c->d_V); cudaFree(c->d_Z); cudaFree(c->d_w); cudaFree(c->d_tmp); cudaFree(c->d_tmp2);
+    cudaFree(c->d_partials); cudaFree(c->d_state); cudaFree(c->d_ticket);
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    for (int t = 0; t < 8; ++t)
+        if (c->ev[t]) cudaEventDestroy(c->ev[t]);
+    (void)cudaGetLastError();
+    delete c;
+}
+
+int fmp_set_options(fmp_ctx* c, const fmp_options* o) {
+    if (!valid_ctx(c) || !o) return FMP_ERR_ARG;
+    int rc = check_options(o);
+    if (rc != FMP_OK) return rc;
+    c->opt = *o;
+    return FMP_OK;
+}
+
+int fmp_set_stream(fmp_ctx* c, void* stream) {
+    if (!valid_ctx(c)) return FMP_ERR_ARG;
+    c->stream = (cudaStream_t)stream;
+    return FMP_OK;
+}
+
+int fmp_get_eps_edge(fmp_ctx* c, double* out) {
+    if (!valid_ctx(c) || !out) return FMP_ERR_ARG;
+    if (int rc = latched(c)) return rc;
+    FMP_CK(cudaMemcpyAsync(out, c->d_eps_edge, sizeof(double) * c->n_slots, cudaMemcpyDeviceToDevice, c->stream));
+    FMP_CK(cudaStreamSynchronize(c->stream));
+    return FMP_OK;
+}
+
+int fmp_get_num_boxes(fmp_ctx* c, int* n) {
+    if (!valid_ctx(c) || !n) return FMP_ERR_ARG;
+    *n = (int)c->h_boxes.size();
+    return FMP_OK;
+}
+
+int fmp_get_box(fmp_ctx* c, int i, int* ext_lo, int* m, int* own_lo, int* own_n, double* eps_bar) {
+    if (!valid_ctx(c) || i < 0 || i >= (int)c->h_boxes.size()) return FMP_ERR_ARG;
+    const FmpBox& b = c->h_boxes[i];
+    for (int a = 0; a < 3; ++a) {
+        if (ext_lo) ext_lo[a] = b.ext_lo[a];
+        if (m) m[a] = b.m[a];
+        if (own_lo) own_lo[a] = b.ext_lo[a] + b.own_lo[a];
+        if (own_n) own_n[a] = b.own_n[a];
+    }
+    if (eps_bar) *eps_bar = b.eps_bar;
+    return FMP_OK;
+}
+
+int fmp_curlcurl_apply(fmp_ctx* c, const double* x, double* y, double c_eps, double c_k) {
+    if (!valid_ctx(c) || !x || !y || x == y) return FMP_ERR_ARG;
+    if (int rc = latched(c)) return rc;
+    FMP_CK(fmp_launch_curlcurl(x, c->d_eps_edge, y, c_eps, c_k, c->nx, c->ny, c->nz, c->stream));
+    return FMP_OK;
+}
+
+int fmp_precond_apply(fmp_ctx* c, const double* r, double* z) {
+    if (!valid_ctx(c) || !r || !z || r == z) return FMP_ERR_ARG;
+    if (int rc = latched(c)) return rc;
+    return fmp_precond(c, r, z);
+}
+
+int fmp_box_solve(fmp_ctx* c, int i, const double* r, double* x) {
+    if (!valid_ctx(c) || !r || !x || r == x || i < 0 || i >= (int)c->h_boxes.size()) return FMP_ERR_ARG;
+    if (int rc = latched(c)) return rc;
+    if (c->opt.precision != FMP_PREC_FP64) return FMP_ERR_UNSUPPORTED;
+    // a one-box plan on the box-local array: the box is its own grid, owned = all
+    FmpBox b = c->h_boxes[i];
+    b.ext_lo[0] = b.ext_lo[1] = b.ext_lo[2] = 0;
+    for (int a = 0; a < 3; ++a) { b.own_lo[a] = 0; b.own_n[a] = b.m[a]; }
+    b.scr_off = 0;
+    if (c->single_box != i) {
+        FMP_CK(cudaStreamSynchronize(c->stream));
+        free_plan(c->single);
+        c->single_box = -1;
+        FMP_CK(make_plan(c->single, std::vector<FmpBox>{b}, c->stream));
+        c->single_box = i;
+    }
+    FMP_CK(fmp_launch_transform_solve_fp64(c->single, c->d_tabs, r, x, c->d_scratch1, b.m[0], b.m[1], b.m[2],
+                                           c->beta, c->stream));
+    return FMP_OK;
+}
+
+int fmp_krylov_solve(fmp_ctx* c, const double* b, double* x, fmp_solve_info* info) {
+    if (!valid_ctx(c) || !b || !x || b == x) return FMP_ERR_ARG;
+    if (int rc = latched(c)) return rc;
+    if (c->opt.krylov == FMP_KRYLOV_BICGSTAB) return fmp_bicgstab(c, b, x, info);
+    return fmp_fgmres(c, b, x, info);
+}
+
+int fmp_cn_rhs(fmp_ctx* c, const double* E, const double* H, const double* J, double dt, double* R) {
+    if (!valid_ctx(c) || !E || !H || !R || R == E || R == H || !dt_matches(c->beta, dt)) return FMP_ERR_ARG;
+    if (int rc = latched(c)) return rc;
+    FMP_CK(fmp_launch_cn_rhs(E, H, J, c->d_eps_edge, c->beta, dt, R, c->nx, c->ny, c->nz, c->stream));
+    return FMP_OK;
+}
+
+int fmp_h_update(fmp_ctx* c, double* H, const double* En, const double* Eo, double dt) {
+    if (!valid_ctx(c) || !H || !En || !Eo || !std::isfinite(dt)) return FMP_ERR_ARG;
+    if (int rc = latched(c)) return rc;
+    FMP_CK(fmp_launch_h_update(H, En, Eo, dt, c->nx, c->ny, c->nz, c->stream));
+    return FMP_OK;
+}
+
+int fmp_cn_step(fmp_ctx* c, double* E, double* H, const double* J, double dt, fmp_solve_info* info) {
+    if (!valid_ctx(c) || !E || !H || E == H || !dt_matches(c->beta, dt)) return FMP_ERR_ARG;
+    if (int rc = latched(c)) return rc;
+    double* R = c->d_tmp;
+    double* Eold = c->d_tmp2;
+    FMP_CK(fmp_launch_cn_rhs(E, H, J, c->d_eps_edge, c->beta, dt, R, c->nx, c->ny, c->nz, c->stream));
+    FMP_CK(cudaMemcpyAsync(Eold, E, sizeof(double) * c->n_slots, cudaMemcpyDeviceToDevice, c->stream));
+    int rc = fmp_krylov_solve(c, R, E, info);
+    if (rc != FMP_OK && rc != FMP_ERR_NOT_CONVERGED) return rc;
+    FMP_CK(fmp_launch_h_update(H, E, Eold, dt, c->nx, c->ny, c->nz, c->stream));
+    return rc;
+}
+
+}  // extern "C"
+
+int fmp_bicgstab(fmp_ctx*, const double*, double*, fmp_solve_info* info) {
+    if (info) { std::memset(info, 0, sizeof(*info)); info->status = FMP_ERR_UNSUPPORTED; }
+    return FMP_ERR_UNSUPPORTED;
+}
