@@ -42,6 +42,9 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="fp64")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--case", default="step", choices=["step", "precond", "spmv"],
+                   help="precond/spmv: only W + K applies of that operator (for profiler captures)")
+    p.add_argument("--workload", default="grid128", choices=["grid128", "grid256", "uneven"])
     return p.parse_args()
 
 
@@ -136,7 +139,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = wl.grid128()
+    w = {"grid128": wl.grid128, "grid256": wl.grid256, "uneven": wl.grid_uneven}[args.workload]()
     nx, ny, nz = w.grid
     dof = 3 * nx * ny * nz
     stream = torch.cuda.current_stream(dev)
@@ -251,6 +254,12 @@ def run_ours(args):
         "gpu_launches": None,
         "clocks": clocks,
     }
+    # phase breakdown from one extra (untimed) step with CUDA-event phase timers
+    ctx.set_options(timing=True)
+    E.zero_(); H.zero_()
+    ph = ctx.cn_step(E, H, J, dt)
+    ctx.set_options(timing=False)
+    out["phase_ms"] = {k: ph[k] for k in ("ms_precond", "ms_spmv", "ms_orth", "ms_total")}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, iters[0] if iters else 1)
     if rank == 0:
@@ -287,8 +296,30 @@ def cpu_baseline(w, iters, n_boxes_sample=4):
                       f"t_box={t_box:.3f}s t_spmv={t_spmv:.3f}s"}
 
 
+def run_case(args):
+    """W + K applies of one operator on a workload, for profiler captures."""
+    import torch
+
+    from paper_2508_07193_b300 import flashmp as F
+    from paper_2508_07193_b300 import workloads as wl
+
+    w = {"grid128": wl.grid128, "grid256": wl.grid256, "uneven": wl.grid_uneven}[args.workload]()
+    ctx = F.Context(w.grid, w.eps_cell, w.beta, w.cuts, w.overlap, precision=args.precision)
+    r = torch.as_tensor(w.rhs, device="cuda")
+    z = ctx.empty_field()
+    op = ctx.precond_apply if args.case == "precond" else ctx.curlcurl_apply
+    for _ in range(args.warmup + args.steps):
+        op(r, z)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": args.case, "workload": w.name, "applies": args.warmup + args.steps}))
+    ctx.close()
+
+
 def main():
     args = parse()
+    if args.case != "step":
+        run_case(args)
+        return
     if args.impl == "reference":
         rank, world, _ = dist_env()
         if rank != 0:
