@@ -201,6 +201,32 @@ int fmp_h_update(fmp_ctx* ctx, double* H, const double* E_new,
 int fmp_cn_step(fmp_ctx* ctx, double* E, double* H, const double* J, double dt,
                 fmp_solve_info* info);
 
+/* Allocation-free exact solve of one PEC box. The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc, such as
+ * applications that hand all device memory to their own allocator at
+ * start-up (a library allocation then fails or competes with it) and
+ * real-time or embedded loops that forbid any allocation after
+ * initialisation. It computes the same float64
+ * x = (eps_bar I + beta K_box)^{-1} r as fmp_box_solve, on a box-local array
+ * [3][mz][my][mx] (wall slots of r must be 0; every slot of x is written),
+ * with no context and no allocation: the transform scratch and the 1-D tables
+ * live in one fixed device array inside the library (about 6.5 MB on every
+ * GPU that loads the library, held until the process exits).
+ *   r, x:       DEVICE, caller-owned, must not alias.
+ *   mx, my, mz: box extents, each in [2, 64]; anything larger (or smaller)
+ *               returns FMP_ERR_ARG and launches nothing.
+ *   eps_bar, beta: > 0. stream: cudaStream_t (NULL = legacy default stream).
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture. Every call on a device uses the same array, which keeps the last
+ * call's contents, so calls that may overlap on the GPU (other streams, or
+ * other host threads without ordering) race and corrupt each other's
+ * results: order them. Nothing in the array needs clearing: each call writes
+ * every value it reads before reading it. Asynchronous on `stream`.
+ * Errors: FMP_ERR_ARG, FMP_ERR_CUDA. */
+int fmp_box_solve_static(const double* r, double* x, int mx, int my, int mz,
+                         double eps_bar, double beta, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
