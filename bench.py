@@ -41,6 +41,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="fp64")
+    p.add_argument("--krylov", default="fgmres", choices=["fgmres", "bicgstab"])
+    p.add_argument("--graph", action="store_true", help="replay each FGMRES restart cycle as one CUDA graph")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--case", default="step", choices=["step", "precond", "spmv"],
                    help="precond/spmv: only W + K applies of that operator (for profiler captures)")
@@ -144,7 +146,7 @@ def run_ours(args):
     dof = 3 * nx * ny * nz
     stream = torch.cuda.current_stream(dev)
     ctx = F.Context(w.grid, w.eps_cell, w.beta, w.cuts, w.overlap, precision=args.precision, restart=30,
-                    rtol=1e-8, stream=stream, device=dev)
+                    rtol=1e-8, stream=stream, device=dev, krylov=args.krylov, use_graph=args.graph)
     dt = 2.0 * math.sqrt(w.beta)
     b = torch.as_tensor(w.rhs, device=dev)
     J = (-b / dt).contiguous()
@@ -163,6 +165,7 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_launch0 = ctx.launch_count()
     with Clocks(local) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
@@ -172,6 +175,7 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
+    launches = ctx.launch_count() - n_launch0
     clocks = clk.summary()
     if world > 1:
         t = torch.tensor([ms], device=dev)
@@ -238,7 +242,8 @@ def run_ours(args):
         "dtype": "f64",
         "data": "synthetic (seeded eps boxes and uniform rhs)",
         "config": {"workload": w.name, "grid": list(w.grid), "subdomains": [len(c) for c in w.cuts],
-                   "overlap": w.overlap, "beta": w.beta, "krylov": "FGMRES(30)", "rtol": 1e-8,
+                   "overlap": w.overlap, "beta": w.beta, "krylov": "FGMRES(30)" if args.krylov == "fgmres" else "BiCGSTAB",
+                   "cuda_graph": bool(args.graph), "rtol": 1e-8,
                    "precision": args.precision, "l2": "inputs (50 MB per field, 3.1 GB Krylov basis) exceed L2 across a step"},
         "iters_per_step": iters,
         "true_rel_res_max": true_res,
@@ -251,7 +256,7 @@ def run_ours(args):
                      "peak_source": "B300 nominal float64 rate"},
         "e2e": {"value": world * dof / (ms_e2e * 1e-3), "unit": "DoF/s", "h2d_bytes_per_step": b.numel() * 8,
                 "d2h_bytes_per_step": E.numel() * 8},
-        "gpu_launches": None,
+        "gpu_launches": launches,
         "clocks": clocks,
     }
     # phase breakdown from one extra (untimed) step with CUDA-event phase timers

@@ -146,6 +146,10 @@ int fmp_set_stream(fmp_ctx* ctx, void* stream);
 /* Copy the edge permittivity [3][nz][ny][nx] (wall slots 0) to DEVICE out. */
 int fmp_get_eps_edge(fmp_ctx* ctx, double* out);
 
+/* Number of CUDA kernels this context has launched so far (kernel nodes of
+ * replayed graphs included), for launch accounting; *n is HOST. */
+int fmp_get_launch_count(fmp_ctx* ctx, long long* n);
+
 /* Number of subdomain boxes. */
 int fmp_get_num_boxes(fmp_ctx* ctx, int* n);
 

@@ -39,6 +39,22 @@ void build_tables(int m, double* C, double* S, double* sig) {
     }
 }
 
+// Folded copy of a table (layout in FoldDims).
+void fold_table(int m, bool dst, const double* T, double* F) {
+    const FoldDims f = fold_dims(m, dst);
+    double* FS = F;
+    double* FA = F + f.nks * f.la;
+    for (int ks = 0; ks < f.nks; ++ks) {
+        const int k = 2 * ks + f.s0;
+        for (int q = 0; q < f.npair; ++q) FS[ks * f.la + q] = T[k * m + f.off + q];
+        if (f.has_mid) FS[ks * f.la + f.npair] = T[k * m + f.mid];
+    }
+    for (int ka = 0; ka < f.nka; ++ka) {
+        const int k = 2 * ka + 1 - f.s0;
+        for (int q = 0; q < f.npair; ++q) FA[ka * f.lb + q] = T[k * m + f.off + q];
+    }
+}
+
 bool valid_ctx(fmp_ctx* c) { return c != nullptr; }
 
 int latched(fmp_ctx* c) { return c->latched != cudaSuccess ? FMP_ERR_CUDA : FMP_OK; }
@@ -100,16 +116,19 @@ bool dt_matches(double beta, double dt) {
 
 }  // namespace
 
-int fmp_precond(fmp_ctx* c, const double* r, double* z) {
+int fmp_precond_gated(fmp_ctx* c, const double* r, double* z, const double* gate) {
     switch (c->opt.precision) {
         case FMP_PREC_FP64:
+            c->launches += 3;
             FMP_CK(fmp_launch_transform_solve_fp64(c->ras, c->d_tabs, r, z, c->d_scratch, c->nx, c->ny, c->nz,
-                                                   c->beta, c->stream));
+                                                   c->beta, c->stream, gate));
             return FMP_OK;
         default:
             return FMP_ERR_UNSUPPORTED;
     }
 }
+
+int fmp_precond(fmp_ctx* c, const double* r, double* z) { return fmp_precond_gated(c, r, z, nullptr); }
 
 extern "C" {
 
@@ -222,13 +241,17 @@ int fmp_setup(fmp_ctx** out, fmp_grid g, const double* eps_cell, double beta, co
             }
     // tables
     std::vector<double> tabs;
-    std::map<int, int> off_c, off_s, off_sig;
+    std::map<int, int> off_c, off_s, off_sig, off_cf, off_sf;
     for (auto& kv : ext_index) {
         const int m = kv.first;
         off_c[m] = (int)tabs.size(); tabs.resize(tabs.size() + (size_t)m * m);
         off_s[m] = (int)tabs.size(); tabs.resize(tabs.size() + (size_t)m * m);
+        off_cf[m] = (int)tabs.size(); tabs.resize(tabs.size() + (size_t)m * m);
+        off_sf[m] = (int)tabs.size(); tabs.resize(tabs.size() + (size_t)m * m);
         off_sig[m] = (int)tabs.size(); tabs.resize(tabs.size() + m);
         build_tables(m, &tabs[off_c[m]], &tabs[off_s[m]], &tabs[off_sig[m]]);
+        fold_table(m, false, &tabs[off_c[m]], &tabs[off_cf[m]]);
+        fold_table(m, true, &tabs[off_s[m]], &tabs[off_sf[m]]);
     }
     long long scr = 0;
     for (FmpBox& b : boxes) {
@@ -236,6 +259,8 @@ int fmp_setup(fmp_ctx** out, fmp_grid g, const double* eps_cell, double beta, co
             b.dct_off[a] = off_c[b.m[a]];
             b.dst_off[a] = off_s[b.m[a]];
             b.sig_off[a] = off_sig[b.m[a]];
+            b.dctf_off[a] = off_cf[b.m[a]];
+            b.dstf_off[a] = off_sf[b.m[a]];
         }
         b.scr_off = scr;
         scr += 3LL * b.m[0] * b.m[1] * b.m[2];
@@ -250,6 +275,8 @@ int fmp_setup(fmp_ctx** out, fmp_grid g, const double* eps_cell, double beta, co
     SETUP_CK(cudaMalloc(&c->d_eps_edge, sizeof(double) * c->n_slots));
     SETUP_CK(fmp_launch_eps_edge(eps_cell, c->d_eps_edge, g.nx, g.ny, g.nz, c->stream));
     SETUP_CK(make_plan(c->ras, boxes, c->stream));
+    SETUP_CK(fmp_transform_init_fp64(c->ras));
+    SETUP_CK(fmp_krylov_init());
     SETUP_CK(fmp_launch_eps_bar(c->d_eps_edge, c->ras.d_boxes, c->ras.n_boxes, g.nx, g.ny, g.nz, c->stream));
     SETUP_CK(cudaMemcpyAsync(boxes.data(), c->ras.d_boxes, sizeof(FmpBox) * boxes.size(), cudaMemcpyDeviceToHost,
                              c->stream));
@@ -259,7 +286,7 @@ int fmp_setup(fmp_ctx** out, fmp_grid g, const double* eps_cell, double beta, co
     long long big = 0;
     for (const FmpBox& b : boxes) big = std::max(big, 3LL * b.m[0] * b.m[1] * b.m[2]);
     SETUP_CK(cudaMalloc(&c->d_scratch1, sizeof(double) * (size_t)big));
-    SETUP_CK(cudaMalloc(&c->d_partials, sizeof(double) * 148 * 4 * 32));
+    SETUP_CK(cudaMalloc(&c->d_partials, sizeof(double) * 148 * 8 * 40));
     SETUP_CK(cudaMalloc(&c->d_ticket, sizeof(unsigned int) * 4));
     SETUP_CK(cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned int) * 4, c->stream));
     SETUP_CK(cudaMalloc(&c->d_tmp, sizeof(double) * c->n_slots));
@@ -279,6 +306,8 @@ void fmp_destroy(fmp_ctx* c) {
     cudaFree(c->d_V); cudaFree(c->d_Z); cudaFree(c->d_w); cudaFree(c->d_tmp); cudaFree(c->d_tmp2);
     cudaFree(c->d_partials); cudaFree(c->d_state); cudaFree(c->d_ticket);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     for (int t = 0; t < 8; ++t)
         if (c->ev[t]) cudaEventDestroy(c->ev[t]);
     (void)cudaGetLastError();
@@ -289,6 +318,7 @@ int fmp_set_options(fmp_ctx* c, const fmp_options* o) {
     if (!valid_ctx(c) || !o) return FMP_ERR_ARG;
     int rc = check_options(o);
     if (rc != FMP_OK) return rc;
+    if (o->precision != c->opt.precision || o->restart != c->opt.restart) c->graph_valid = false;
     c->opt = *o;
     return FMP_OK;
 }
@@ -304,6 +334,12 @@ int fmp_get_eps_edge(fmp_ctx* c, double* out) {
     if (int rc = latched(c)) return rc;
     FMP_CK(cudaMemcpyAsync(out, c->d_eps_edge, sizeof(double) * c->n_slots, cudaMemcpyDeviceToDevice, c->stream));
     FMP_CK(cudaStreamSynchronize(c->stream));
+    return FMP_OK;
+}
+
+int fmp_get_launch_count(fmp_ctx* c, long long* n) {
+    if (!valid_ctx(c) || !n) return FMP_ERR_ARG;
+    *n = c->launches;
     return FMP_OK;
 }
 
@@ -329,7 +365,8 @@ int fmp_get_box(fmp_ctx* c, int i, int* ext_lo, int* m, int* own_lo, int* own_n,
 int fmp_curlcurl_apply(fmp_ctx* c, const double* x, double* y, double c_eps, double c_k) {
     if (!valid_ctx(c) || !x || !y || x == y) return FMP_ERR_ARG;
     if (int rc = latched(c)) return rc;
-    FMP_CK(fmp_launch_curlcurl(x, c->d_eps_edge, y, c_eps, c_k, c->nx, c->ny, c->nz, c->stream));
+    ++c->launches;
+    FMP_CK(fmp_launch_curlcurl(x, c->d_eps_edge, y, c_eps, c_k, c->nx, c->ny, c->nz, c->stream, nullptr));
     return FMP_OK;
 }
 
@@ -353,10 +390,12 @@ int fmp_box_solve(fmp_ctx* c, int i, const double* r, double* x) {
         free_plan(c->single);
         c->single_box = -1;
         FMP_CK(make_plan(c->single, std::vector<FmpBox>{b}, c->stream));
+        FMP_CK(fmp_transform_init_fp64(c->single));
         c->single_box = i;
     }
+    c->launches += 3;
     FMP_CK(fmp_launch_transform_solve_fp64(c->single, c->d_tabs, r, x, c->d_scratch1, b.m[0], b.m[1], b.m[2],
-                                           c->beta, c->stream));
+                                           c->beta, c->stream, nullptr));
     return FMP_OK;
 }
 
@@ -370,6 +409,7 @@ int fmp_krylov_solve(fmp_ctx* c, const double* b, double* x, fmp_solve_info* inf
 int fmp_cn_rhs(fmp_ctx* c, const double* E, const double* H, const double* J, double dt, double* R) {
     if (!valid_ctx(c) || !E || !H || !R || R == E || R == H || !dt_matches(c->beta, dt)) return FMP_ERR_ARG;
     if (int rc = latched(c)) return rc;
+    ++c->launches;
     FMP_CK(fmp_launch_cn_rhs(E, H, J, c->d_eps_edge, c->beta, dt, R, c->nx, c->ny, c->nz, c->stream));
     return FMP_OK;
 }
@@ -377,6 +417,7 @@ int fmp_cn_rhs(fmp_ctx* c, const double* E, const double* H, const double* J, do
 int fmp_h_update(fmp_ctx* c, double* H, const double* En, const double* Eo, double dt) {
     if (!valid_ctx(c) || !H || !En || !Eo || !std::isfinite(dt)) return FMP_ERR_ARG;
     if (int rc = latched(c)) return rc;
+    ++c->launches;
     FMP_CK(fmp_launch_h_update(H, En, Eo, dt, c->nx, c->ny, c->nz, c->stream));
     return FMP_OK;
 }
@@ -386,6 +427,7 @@ int fmp_cn_step(fmp_ctx* c, double* E, double* H, const double* J, double dt, fm
     if (int rc = latched(c)) return rc;
     double* R = c->d_tmp;
     double* Eold = c->d_tmp2;
+    c->launches += 2;   // rhs + H update
     FMP_CK(fmp_launch_cn_rhs(E, H, J, c->d_eps_edge, c->beta, dt, R, c->nx, c->ny, c->nz, c->stream));
     FMP_CK(cudaMemcpyAsync(Eold, E, sizeof(double) * c->n_slots, cudaMemcpyDeviceToDevice, c->stream));
     int rc = fmp_krylov_solve(c, R, E, info);
@@ -395,8 +437,3 @@ int fmp_cn_step(fmp_ctx* c, double* E, double* H, const double* J, double dt, fm
 }
 
 }  // extern "C"
-
-int fmp_bicgstab(fmp_ctx*, const double*, double*, fmp_solve_info* info) {
-    if (info) { std::memset(info, 0, sizeof(*info)); info->status = FMP_ERR_UNSUPPORTED; }
-    return FMP_ERR_UNSUPPORTED;
-}

@@ -22,9 +22,37 @@ struct FmpBox {
     int dct_off[3];    // offset of the m x m DCT-II table of axis a in tabs
     int dst_off[3];    // offset of the m x m DST-I table of axis a in tabs
     int sig_off[3];    // offset of the m singular values of axis a in tabs
+    int dctf_off[3];   // folded DCT-II table of axis a (see FoldDims)
+    int dstf_off[3];   // folded DST-I table of axis a
     long long scr_off; // offset (doubles) of the box's [3][mz][my][mx] scratch
     double eps_bar;    // subdomain-mean edge permittivity
 };
+
+// Even/odd folding of a 1-D table T (m x m) with the mirror symmetry
+// T[k][m-1-q'] = +-T[k][p_q] that DCT-II and (zero-padded) DST-I both have:
+// input pairs (p_q, p'_q) = (off + q, m - 1 - q), q < npair, plus a middle
+// index when m - off is odd; output rows split by the parity of k into a
+// 'sym' class (k = 2 ks + s0, combines x_p + x_p') and an 'anti' class
+// (k = 2 ka + 1 - s0, combines x_p - x_p'). The folded table is
+// FS[ks][q] = T[2ks+s0][p_q] (q < npair; column npair = T[k][mid] when
+// there is a middle) followed by FA[ka][q] = T[2ka+1-s0][p_q]. DCT-II: off = 0,
+// s0 = 0; DST-I: off = 1 (slot 0 is the wall), s0 = 1.
+struct FoldDims {
+    int off, npair, has_mid, mid, s0, nks, nka, la, lb;
+};
+__host__ __device__ inline FoldDims fold_dims(int m, bool dst) {
+    FoldDims f;
+    f.off = dst ? 1 : 0;
+    f.npair = (m - f.off) / 2;
+    f.has_mid = (m - f.off) & 1;
+    f.mid = f.off + f.npair;
+    f.s0 = dst ? 1 : 0;
+    f.nks = (m - f.s0 + 1) / 2;
+    f.nka = (m - (1 - f.s0) + 1) / 2;
+    f.la = f.npair + f.has_mid;
+    f.lb = f.npair;
+    return f;
+}
 
 // Launch-shape description of one batched transform solve (the three passes).
 struct FmpPlan {
@@ -61,6 +89,12 @@ struct fmp_ctx {
 
     // Krylov workspace (allocated on first solve)
     int kry_restart = 0;
+    int kry_nv = 0, kry_nz = 0;   // vectors allocated in d_V, d_Z
+    bool graph_valid = false;     // restart-cycle graph matches the buffers
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    long long graph_kernels = 0;  // kernel nodes in the cycle graph
+    long long launches = 0;       // kernels launched by this context (graph nodes included)
     size_t ld = 0;                // padded vector length
     double* d_V = nullptr;        // (restart+1) x ld
     double* d_Z = nullptr;        // restart x ld
@@ -79,11 +113,15 @@ cudaError_t fmp_launch_eps_edge(const double* eps_cell, double* eps_edge, int nx
                                 int nz, cudaStream_t s);
 cudaError_t fmp_launch_eps_bar(const double* eps_edge, FmpBox* d_boxes, int n_boxes, int nx,
                                int ny, int nz, cudaStream_t s);
+// gate: optional device flag; when *gate != 0 the kernels return at once.
+cudaError_t fmp_transform_init_fp64(const FmpPlan& p);
 cudaError_t fmp_launch_transform_solve_fp64(const FmpPlan& p, const double* tabs, const double* r,
                                             double* z, double* scratch, int nx, int ny, int nz,
-                                            double beta, cudaStream_t s);
+                                            double beta, cudaStream_t s, const double* gate);
+// y = s_b * b + c_eps * eps o x + c_k * K x  (b may be null)
 cudaError_t fmp_launch_curlcurl(const double* x, const double* eps, double* y, double c_eps,
-                                double c_k, int nx, int ny, int nz, cudaStream_t s);
+                                double c_k, int nx, int ny, int nz, cudaStream_t s,
+                                const double* gate, const double* b = nullptr, double s_b = 0.0);
 cudaError_t fmp_launch_cn_rhs(const double* E, const double* H, const double* J,
                               const double* eps, double beta, double dt, double* R, int nx,
                               int ny, int nz, cudaStream_t s);
@@ -94,7 +132,9 @@ cudaError_t fmp_launch_h_update(double* H, const double* En, const double* Eo, d
 int fmp_fgmres(fmp_ctx* c, const double* b, double* x, fmp_solve_info* info);
 int fmp_bicgstab(fmp_ctx* c, const double* b, double* x, fmp_solve_info* info);
 int fmp_precond(fmp_ctx* c, const double* r, double* z);
+int fmp_precond_gated(fmp_ctx* c, const double* r, double* z, const double* gate);
 cudaError_t fmp_ensure_krylov(fmp_ctx* c);
+cudaError_t fmp_krylov_init();
 
 #define FMP_CK(expr)                                                   \
     do {                                                               \

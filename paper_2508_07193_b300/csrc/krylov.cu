@@ -1,76 +1,92 @@
-// Outer Krylov solver: restarted right-preconditioned flexible GMRES
-// (Sec. IV-A: GMRES with restart k = 30; Table 3: per iteration one
-// preconditioner apply, one SpMV, k_avg + 1 dot products, k_avg AXPYs).
+// Outer Krylov solvers: restarted right-preconditioned flexible GMRES and
+// right-preconditioned BiCGSTAB (Sec. IV-A: GMRES with restart k = 30,
+// BiCGSTAB with standard parameters; Table 3: GMRES does 1 preconditioner
+// apply, 1 SpMV, k_avg + 1 dots and k_avg AXPYs per iteration, BiCGSTAB 2, 2,
+// 4 and 6).
 //
-// Everything on the Krylov side is float64. Orthogonalisation is classical
-// Gram-Schmidt applied twice (CGS2): three streaming passes over the basis per
-// Arnoldi step (dots; update + second dots; update + norm) instead of the
-// 2(j+1) dependent reductions of modified Gram-Schmidt. Reductions are
-// deterministic: per-block partial sums, reduced in block order by the last
-// block to finish (atomic ticket, no spinning). The Hessenberg column, Givens
-// rotations and residual estimate are updated on the device by that last
-// block; the host reads one scalar per step to decide convergence.
+// Everything here is float64. FGMRES orthogonalises by classical Gram-Schmidt
+// with selective re-orthogonalisation: one dot pass and one update pass over
+// the basis per Arnoldi step, and a second pair only when the projection
+// cancels more than kReorthRatio of ||w||. (The Daniel-Gragg-Kaufman-Stewart
+// threshold 1/sqrt(2) fires at every step here: with a good preconditioner
+// A M^{-1} v_j is close to v_j, so most of w lies in the basis. The loss of
+// orthogonality of one classical pass grows like eps (||w|| / ||w - V h||)^2,
+// which stays below 1e-13 at the ratio used.) The vector
+// kernels stream contiguous 1024-element chunks of every basis vector per
+// block (16-byte loads), so DRAM pages and TLB entries are reused.
+//
+// Reductions are deterministic: per-block partial sums reduced in block order
+// by the last block to finish (atomic ticket, no spinning). That last block
+// also updates the Hessenberg column, the Givens rotations and the residual
+// estimate, and raises a device-side 'done' flag; every kernel of an Arnoldi
+// step returns at once when the flag is set, so a whole restart cycle can be
+// enqueued (or replayed as one CUDA graph) and read back once.
 #include "fmp_internal.h"
+#include "bulk.cuh"
 
 #include <cmath>
 #include <cstring>
 
 namespace {
 
-constexpr int kRedThreads = 256;
-constexpr int kRedBlocks = 148 * 4;
-constexpr int kMaxV = 32;   // basis vectors per fused pass (restart <= 32)
+constexpr int kT = 256;                 // threads per block
+constexpr int kMaxV = FMP_MAX_RESTART;  // basis vectors per pass (restart <= 32)
+constexpr int kPartStride = kMaxV + 2;
+constexpr double kReorthRatio = 0.05;
 
-// layout of d_state (doubles)
+// ---- device state (doubles) ---------------------------------------------
 struct St {
-    int R;
-    int H, cs, sn, g, h1, h2, y, sc;
-    int total;
+    int R, H, cs, sn, g, h1, h2, y, sc, total;
 };
 __host__ __device__ inline St st_layout(int R) {
     St s;
     s.R = R;
-    s.H = 0;                       // (R+1) x R, column-major
+    s.H = 0;                      // (R+1) x R, column-major
     s.cs = s.H + (R + 1) * R;
     s.sn = s.cs + R;
-    s.g = s.sn + R;                // R+1
-    s.h1 = s.g + R + 1;            // R+1
-    s.h2 = s.h1 + R + 1;           // R+1
-    s.y = s.h2 + R + 1;            // R
-    s.sc = s.y + R;                // scalars
-    s.total = s.sc + 16;
+    s.g = s.sn + R;               // R+1
+    s.h1 = s.g + R + 1;           // R+2 (last slot: ||w||^2)
+    s.h2 = s.h1 + R + 2;          // R+2
+    s.y = s.h2 + R + 2;           // R
+    s.sc = s.y + R;
+    s.total = s.sc + 32;
     return s;
 }
-// scalar slots
-enum { SC_BNORM = 0, SC_EST = 1, SC_INV = 2, SC_HN = 3, SC_NRM = 4, SC_FLAG = 5, SC_TMP = 6 };
+enum {
+    SC_BNORM = 0, SC_EST, SC_INV, SC_HN, SC_NRM, SC_DONE, SC_REORTH, SC_JDONE, SC_STATUS, SC_RTOL,
+    SC_BUDGET, SC_NREORTH, SC_KERR,
+    // BiCGSTAB scalars
+    SC_RHO, SC_RHO_OLD, SC_ALPHA, SC_OMEGA, SC_BETA, SC_D0, SC_D1, SC_D2, SC_D3, SC_D4
+};
+// SC_STATUS codes written by the device
+enum { DS_RUN = 0, DS_CONV = 1, DS_BUDGET = 2, DS_LUCKY = 3, DS_BREAK = 4, DS_NONFINITE = 5 };
 
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return v;
 }
 
-// Block-reduce nv values per thread into partials[blockIdx.x * kMaxV + i];
-// returns true in the last block to finish, after its own partials are
-// visible. shm must hold (blockDim/32) * kMaxV doubles.
+// Reduce acc[0..nv) over the block into partials[blockIdx.x][.]; returns true
+// in the last block to finish (its partial sums of all blocks are visible).
 template <int NV>
-__device__ bool block_partials(const double (&acc)[NV], int nv, double* partials, unsigned int* ticket,
-                               double* shm) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+__device__ __forceinline__ bool block_partials(const double (&acc)[NV], int nv, double* partials, unsigned int* ticket) {
+    __shared__ double shm[(kT / 32) * kPartStride];
+    __shared__ unsigned int last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
         if (i < nv) {
             const double v = warp_sum(acc[i]);
-            if (lane == 0) shm[warp * kMaxV + i] = v;
+            if (lane == 0) shm[warp * kPartStride + i] = v;
         }
     }
     __syncthreads();
     if (threadIdx.x < nv) {
         double s = 0.0;
-        for (int w = 0; w < nw; ++w) s += shm[w * kMaxV + threadIdx.x];
-        partials[blockIdx.x * kMaxV + threadIdx.x] = s;
+        for (int w = 0; w < kT / 32; ++w) s += shm[w * kPartStride + threadIdx.x];
+        partials[blockIdx.x * kPartStride + threadIdx.x] = s;
     }
     __threadfence();
-    __shared__ unsigned int last;
     __syncthreads();
     if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
     __syncthreads();
@@ -78,204 +94,405 @@ __device__ bool block_partials(const double (&acc)[NV], int nv, double* partials
     return last;
 }
 
-// In the last block: sum partials over blocks in block order -> out[0..nv).
-__device__ void finish_sums(int nv, const double* partials, double* out) {
-    if (threadIdx.x < nv) {
-        double s = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(partials + b * kMaxV + threadIdx.x);
-        out[threadIdx.x] = s;
-    }
+__device__ double block_total(const double* partials, int i) {
+    double s = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(partials + b * kPartStride + i);
+    return s;
 }
 
-// out[i] = <V_i, w>, i < nv (V_i = V + (v0 + i) * ld)
-__global__ void __launch_bounds__(kRedThreads)
-k_mdot(const double* __restrict__ V, size_t ld, int nv, const double* __restrict__ w, size_t n,
-       double* partials, unsigned int* ticket, double* out) {
-    __shared__ double shm[(kRedThreads / 32) * kMaxV];
-    double acc[kMaxV];
-#pragma unroll
-    for (int i = 0; i < kMaxV; ++i) acc[i] = 0.0;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        const double we = w[e];
-#pragma unroll
-        for (int i = 0; i < kMaxV; ++i)
-            if (i < nv) acc[i] = fma(V[i * ld + e], we, acc[i]);
-    }
-    if (block_partials(acc, nv, partials, ticket, shm)) {
-        finish_sums(nv, partials, out);
-        if (threadIdx.x == 0) *ticket = 0;
-    }
+__device__ __forceinline__ bool gated(const double* st, int sc) { return st[sc + SC_DONE] != 0.0; }
+
+// ---- FGMRES kernels ---------------------------------------------------------
+
+// ---- streamed basis passes ----------------------------------------------
+// A block owns chunks blockIdx.x, blockIdx.x + gridDim.x, ... of kCH doubles.
+// For each chunk it streams w and then V_0..V_{nv-1} as 16 KB tiles through a
+// kNST-deep ring of shared-memory stages, each filled by one bulk copy whose
+// completion is signalled on that stage's mbarrier. The loads need no
+// registers while in flight, so each SM keeps 128-192 KB of reads pending.
+constexpr int kCH = 2048;
+constexpr int kNST = 4;
+constexpr int kPer = kCH / kT;
+constexpr size_t kStreamSmem = sizeof(double) * kNST * kCH;
+
+struct Ring {
+    uint64_t* bar;
+    double* stage;
+};
+
+// Issue tile t (thread 0): tile t of chunk-list position t / nt, vector t % nt
+// (0 = w, v >= 1 = V_{v-1}). Odd-length tails copy the even prefix; the last
+// element is read directly by its consumer.
+__device__ __forceinline__ void issue_tile(const Ring& rg, size_t t, int nt, const double* V, size_t ld,
+                                           const double* w, size_t n) {
+    const size_t cl = t / nt;
+    const int v = (int)(t - cl * nt);
+    const size_t e0 = ((size_t)blockIdx.x + cl * gridDim.x) * kCH;
+    const size_t len = n - e0 < (size_t)kCH ? n - e0 : (size_t)kCH;
+    const unsigned bytes = (unsigned)((len & ~(size_t)1) * sizeof(double));
+    const double* src = (v == 0 ? w : V + (size_t)(v - 1) * ld) + e0;
+    uint64_t* b = rg.bar + t % kNST;
+    fmp::fence_async_shared();
+    fmp::mbar_expect_tx(b, bytes);
+    if (bytes) fmp::bulk_g2s(rg.stage + (t % kNST) * kCH, src, bytes, b);
 }
 
-// w -= sum_i h[i] V_i ; then out2[i] = <V_i, w_new>  (second CGS pass dots)
-__global__ void __launch_bounds__(kRedThreads)
-k_update_dot(const double* __restrict__ V, size_t ld, int nv, double* __restrict__ w, size_t n,
-             const double* __restrict__ h, double* partials, unsigned int* ticket, double* out) {
-    __shared__ double shm[(kRedThreads / 32) * kMaxV];
-    __shared__ double hs[kMaxV];
-    if (threadIdx.x < nv) hs[threadIdx.x] = h[threadIdx.x];
+// Block-uniform bounded wait for tile t; false if any thread gave up.
+__device__ __forceinline__ bool wait_tile(const Ring& rg, size_t t) {
+    const bool ok = fmp::mbar_wait(rg.bar + t % kNST, (unsigned)((t / kNST) & 1));
+    return __syncthreads_and(ok) != 0;
+}
+
+__device__ __forceinline__ double tile_val(const double* sp, const double* g, size_t e0, size_t len, int idx) {
+    if ((size_t)idx >= len) return 0.0;
+    if ((len & 1) && (size_t)idx == len - 1) return g[e0 + idx];
+    return sp[idx];
+}
+
+// Give up: record the failure and drain the copies still in flight.
+__device__ void ring_abort(const Ring& rg, size_t t, size_t ntiles, double* st, int sc) {
+    if (threadIdx.x == 0) st[sc + SC_KERR] = 1.0;
+    for (size_t u = t + 1; u < ntiles && u < t + kNST; ++u) (void)fmp::mbar_wait(rg.bar + u % kNST, (unsigned)((u / kNST) & 1));
     __syncthreads();
-    double acc[kMaxV];
-#pragma unroll
-    for (int i = 0; i < kMaxV; ++i) acc[i] = 0.0;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        double we = w[e];
-        for (int i = 0; i < nv; ++i) we = fma(-hs[i], V[i * ld + e], we);
-        w[e] = we;
-#pragma unroll
-        for (int i = 0; i < kMaxV; ++i)
-            if (i < nv) acc[i] = fma(V[i * ld + e], we, acc[i]);   // re-read hits L1
-    }
-    if (block_partials(acc, nv, partials, ticket, shm)) {
-        finish_sums(nv, partials, out);
-        if (threadIdx.x == 0) *ticket = 0;
-    }
 }
 
-// Arnoldi step j, second CGS update + norm, then (last block) the Hessenberg
-// column, Givens rotation and residual estimate.
-__global__ void __launch_bounds__(kRedThreads)
-k_update_norm_givens(const double* __restrict__ V, size_t ld, int nv, double* __restrict__ w, size_t n,
-                     double* st, int R, int j, double* partials, unsigned int* ticket) {
-    __shared__ double shm[(kRedThreads / 32) * kMaxV];
-    __shared__ double hs[kMaxV];
+__device__ size_t my_tiles(size_t n, int nt) {
+    const size_t nchunks = (n + kCH - 1) / kCH;
+    const size_t mine = blockIdx.x < nchunks ? (nchunks - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    return mine * nt;
+}
+
+// Publish block totals tot[0..nv) as this block's partials; returns true in
+// the last block to finish.
+__device__ bool block_publish(const double* tot, int nv, double* partials, unsigned int* ticket) {
+    __shared__ unsigned int last;
+    if (threadIdx.x < nv) partials[blockIdx.x * kPartStride + threadIdx.x] = tot[threadIdx.x];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// out[i] = <V_i, w> for i < nv and out[nv] = <w, w>. mode 0: always (first
+// pass); mode 1: only when the re-orthogonalisation flag is up.
+__global__ void __launch_bounds__(kT)
+k_dots(const double* __restrict__ V, size_t ld, int nv, const double* __restrict__ w, size_t n, double* st,
+       int R, int out_off, int mode, double* partials, unsigned int* ticket) {
     const St L = st_layout(R);
-    if (threadIdx.x < nv) hs[threadIdx.x] = st[L.h2 + threadIdx.x];
-    __syncthreads();
-    double acc[1] = {0.0};
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        double we = w[e];
-        for (int i = 0; i < nv; ++i) we = fma(-hs[i], V[i * ld + e], we);
-        w[e] = we;
-        acc[0] = fma(we, we, acc[0]);
+    if (gated(st, L.sc) || (mode == 1 && st[L.sc + SC_REORTH] == 0.0)) return;
+    extern __shared__ __align__(128) double sm_stage[];
+    __shared__ __align__(8) uint64_t bars[kNST];
+    Ring rg{bars, sm_stage};
+    const int nt = nv + 1;
+    const size_t ntiles = my_tiles(n, nt);
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < kNST; ++q) fmp::mbar_init(bars + q, 1);
+        fmp::mbar_init_fence();
     }
-    if (block_partials(acc, 1, partials, ticket, shm)) {
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(partials + b * kMaxV);
-            *ticket = 0;
-            double* H = st + L.H + (size_t)j * (R + 1);
-            for (int i = 0; i <= j; ++i) H[i] = st[L.h1 + i] + st[L.h2 + i];
-            const double hn = sqrt(s);
-            H[j + 1] = hn;
-            double* cs = st + L.cs;
-            double* sn = st + L.sn;
-            double* g = st + L.g;
-            for (int i = 0; i < j; ++i) {
-                const double t = cs[i] * H[i] + sn[i] * H[i + 1];
-                H[i + 1] = -sn[i] * H[i] + cs[i] * H[i + 1];
-                H[i] = t;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (size_t t = 0; t < ntiles && t < (size_t)kNST; ++t) issue_tile(rg, t, nt, V, ld, w, n);
+    // per-warp running sums: slot v-1 for <V_{v-1}, w>, slot kMaxV for <w, w>
+    __shared__ double wsum[kT / 32][kMaxV + 1];
+    for (int q = threadIdx.x; q < (kT / 32) * (kMaxV + 1); q += kT) (&wsum[0][0])[q] = 0.0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double wr[kPer];
+    for (size_t t = 0; t < ntiles; ++t) {
+        if (!wait_tile(rg, t)) { ring_abort(rg, t, ntiles, st, L.sc); return; }
+        const size_t cl = t / nt;
+        const int v = (int)(t - cl * nt);
+        const size_t e0 = ((size_t)blockIdx.x + cl * gridDim.x) * kCH;
+        const size_t len = n - e0 < (size_t)kCH ? n - e0 : (size_t)kCH;
+        const double* sp = rg.stage + (t % kNST) * kCH;
+        double p = 0.0;
+        if (v == 0) {
+#pragma unroll
+            for (int k = 0; k < kPer; ++k) {
+                wr[k] = tile_val(sp, w, e0, len, threadIdx.x + k * kT);
+                p = fma(wr[k], wr[k], p);
             }
-            const double den = hypot(H[j], H[j + 1]);
-            double c = 1.0, sv = 0.0;
-            if (den > 0.0) { c = H[j] / den; sv = H[j + 1] / den; }
-            cs[j] = c; sn[j] = sv;
-            H[j] = den;
-            H[j + 1] = 0.0;
-            g[j + 1] = -sv * g[j];
-            g[j] = c * g[j];
-            st[L.sc + SC_HN] = hn;
-            st[L.sc + SC_INV] = hn > 0.0 ? 1.0 / hn : 0.0;
-            st[L.sc + SC_EST] = fabs(g[j + 1]) / st[L.sc + SC_BNORM];
-            st[L.sc + SC_FLAG] = (den == 0.0) ? 1.0 : 0.0;
+        } else {
+            const double* g = V + (size_t)(v - 1) * ld;
+#pragma unroll
+            for (int k = 0; k < kPer; ++k) p = fma(tile_val(sp, g, e0, len, threadIdx.x + k * kT), wr[k], p);
+        }
+        p = warp_sum(p);
+        if (lane == 0) wsum[warp][v == 0 ? kMaxV : v - 1] += p;
+        __syncthreads();
+        if (threadIdx.x == 0 && t + kNST < ntiles) issue_tile(rg, t + kNST, nt, V, ld, w, n);
+    }
+    __shared__ double tot[kMaxV + 2];
+    if (threadIdx.x <= nv) {
+        const int slot = threadIdx.x < nv ? threadIdx.x : kMaxV;   // <w,w> right after the nv dots
+        double sum = 0.0;
+        for (int q = 0; q < kT / 32; ++q) sum += wsum[q][slot];
+        tot[threadIdx.x] = sum;
+    }
+    __syncthreads();
+    if (block_publish(tot, nv + 1, partials, ticket)) {
+        if (threadIdx.x <= nv) st[out_off + threadIdx.x] = block_total(partials, threadIdx.x);
+        __syncthreads();
+        if (threadIdx.x == 0) *ticket = 0;
+    }
+}
+
+// Finish Arnoldi column j with coefficients h (length j+1) and ||w||:
+// rotate the new Hessenberg column by the previous Givens rotations, form the
+// new rotation, update g and the residual estimate |g_{j+1}| / ||b||, and
+// raise the done flag on convergence, breakdown or the end of the cycle.
+__device__ void arnoldi_finish(double* st, const St& L, int j, const double* h, double hn) {
+    double* H = st + L.H + (size_t)j * (L.R + 1);
+    for (int i = 0; i <= j; ++i) H[i] = h[i];
+    H[j + 1] = hn;
+    double* cs = st + L.cs;
+    double* sn = st + L.sn;
+    double* g = st + L.g;
+    for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * H[i] + sn[i] * H[i + 1];
+        H[i + 1] = -sn[i] * H[i] + cs[i] * H[i + 1];
+        H[i] = t;
+    }
+    const double den = hypot(H[j], H[j + 1]);
+    double c = 1.0, s = 0.0;
+    if (den > 0.0) { c = H[j] / den; s = H[j + 1] / den; }
+    cs[j] = c; sn[j] = s;
+    H[j] = den;
+    H[j + 1] = 0.0;
+    g[j + 1] = -s * g[j];
+    g[j] = c * g[j];
+    const double est = fabs(g[j + 1]) / st[L.sc + SC_BNORM];
+    st[L.sc + SC_HN] = hn;
+    st[L.sc + SC_INV] = hn > 0.0 ? 1.0 / hn : 0.0;
+    st[L.sc + SC_EST] = est;
+    st[L.sc + SC_JDONE] = j + 1;
+    int status = DS_RUN;
+    if (!isfinite(est) || !isfinite(hn)) status = DS_NONFINITE;
+    else if (est <= st[L.sc + SC_RTOL]) status = DS_CONV;
+    else if (den == 0.0) status = DS_BREAK;
+    else if (hn == 0.0) status = DS_LUCKY;
+    else if (j + 1 >= (int)st[L.sc + SC_BUDGET] || j + 1 >= L.R) status = DS_BUDGET;
+    if (status != DS_RUN) {
+        st[L.sc + SC_DONE] = 1.0;
+        st[L.sc + SC_STATUS] = status;
+    }
+}
+
+// w -= V h. mode 0: h = h1, then the DGKS test decides between finishing the
+// column and raising the re-orthogonalisation flag. mode 1 (flag up only):
+// h = h2, then finish the column with h1 + h2. Streams tiles like k_dots; the
+// updated chunk of w is written back after its last basis tile.
+__global__ void __launch_bounds__(kT)
+k_update(const double* __restrict__ V, size_t ld, int nv, double* __restrict__ w, size_t n, double* st, int R,
+         int j, int mode, double* partials, unsigned int* ticket) {
+    const St L = st_layout(R);
+    if (gated(st, L.sc) || (mode == 1 && st[L.sc + SC_REORTH] == 0.0)) return;
+    extern __shared__ __align__(128) double sm_stage[];
+    __shared__ __align__(8) uint64_t bars[kNST];
+    __shared__ double hs[kMaxV];
+    Ring rg{bars, sm_stage};
+    const double* h = st + (mode == 0 ? L.h1 : L.h2);
+    if (threadIdx.x < nv) hs[threadIdx.x] = h[threadIdx.x];
+    const int nt = nv + 1;
+    const size_t ntiles = my_tiles(n, nt);
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < kNST; ++q) fmp::mbar_init(bars + q, 1);
+        fmp::mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (size_t t = 0; t < ntiles && t < (size_t)kNST; ++t) issue_tile(rg, t, nt, V, ld, w, n);
+    double acc[1] = {0.0};
+    double wr[kPer];
+    for (size_t t = 0; t < ntiles; ++t) {
+        if (!wait_tile(rg, t)) { ring_abort(rg, t, ntiles, st, L.sc); return; }
+        const size_t cl = t / nt;
+        const int v = (int)(t - cl * nt);
+        const size_t e0 = ((size_t)blockIdx.x + cl * gridDim.x) * kCH;
+        const size_t len = n - e0 < (size_t)kCH ? n - e0 : (size_t)kCH;
+        const double* sp = rg.stage + (t % kNST) * kCH;
+        if (v == 0) {
+#pragma unroll
+            for (int k = 0; k < kPer; ++k) wr[k] = tile_val(sp, w, e0, len, threadIdx.x + k * kT);
+        } else {
+            const double* g = V + (size_t)(v - 1) * ld;
+            const double hv = hs[v - 1];
+#pragma unroll
+            for (int k = 0; k < kPer; ++k) wr[k] = fma(-hv, tile_val(sp, g, e0, len, threadIdx.x + k * kT), wr[k]);
+        }
+        if (v == nv) {
+#pragma unroll
+            for (int k = 0; k < kPer; ++k) {
+                const size_t idx = threadIdx.x + k * kT;
+                if (idx < len) {
+                    w[e0 + idx] = wr[k];
+                    acc[0] = fma(wr[k], wr[k], acc[0]);
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && t + kNST < ntiles) issue_tile(rg, t + kNST, nt, V, ld, w, n);
+    }
+    if (block_partials(acc, 1, partials, ticket)) {
+        if (threadIdx.x == 0) {
+            const double nrm = sqrt(block_total(partials, 0));
+            *ticket = 0;
+            if (mode == 0) {
+                const double wn = sqrt(st[L.h1 + nv]);   // ||w|| before projection
+                if (nrm >= kReorthRatio * wn || !isfinite(nrm)) {
+                    st[L.sc + SC_REORTH] = 0.0;
+                    arnoldi_finish(st, L, j, st + L.h1, nrm);
+                } else {
+                    st[L.sc + SC_REORTH] = 1.0;
+                    st[L.sc + SC_NREORTH] += 1.0;
+                }
+            } else {
+                double hsum[kMaxV];
+                for (int i = 0; i <= j; ++i) hsum[i] = st[L.h1 + i] + st[L.h2 + i];
+                st[L.sc + SC_REORTH] = 0.0;
+                arnoldi_finish(st, L, j, hsum, nrm);
+            }
         }
     }
 }
 
-// w *= st[slot]
-__global__ void k_scale(double* __restrict__ w, size_t n, const double* __restrict__ sp) {
-    const double a = *sp;
+// v_{j+1} = w / h_{j+1,j}; skipped for a step that did not run.
+__global__ void k_scale_next(double* __restrict__ w, size_t n, const double* st, int R, int j) {
+    const St L = st_layout(R);
+    if ((int)st[L.sc + SC_JDONE] != j + 1) return;
+    const double a = st[L.sc + SC_INV];
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
         w[e] *= a;
 }
 
-// ||w||^2 -> st[SC_NRM]; also sets g = [||w||, 0...] and SC_INV = 1/||w|| when init_g.
-__global__ void __launch_bounds__(kRedThreads)
-k_norm(const double* __restrict__ w, size_t n, double* st, int R, int init_g, double* partials,
-       unsigned int* ticket) {
-    __shared__ double shm[(kRedThreads / 32) * kMaxV];
-    const St L = st_layout(R);
-    double acc[1] = {0.0};
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
-        acc[0] = fma(w[e], w[e], acc[0]);
-    if (block_partials(acc, 1, partials, ticket, shm)) {
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(partials + b * kMaxV);
-            *ticket = 0;
-            const double nr = sqrt(s);
-            st[L.sc + SC_NRM] = nr;
-            if (init_g) {
-                for (int i = 0; i <= R; ++i) st[L.g + i] = 0.0;
-                st[L.g] = nr;
-                st[L.sc + SC_INV] = nr > 0.0 ? 1.0 / nr : 0.0;
-            }
-        }
+// Dots of up to four vector pairs: out[k] = <a_k, b_k>.
+struct Pairs {
+    const double* a[4];
+    const double* b[4];
+    int n;
+};
+__global__ void __launch_bounds__(kT)
+k_pairdots(Pairs p, size_t len, double* out, double* partials, unsigned int* ticket) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < len; e += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (k < p.n) acc[k] = fma(p.a[k][e], p.b[k][e], acc[k]);
+    }
+    if (block_partials(acc, p.n, partials, ticket)) {
+        if (threadIdx.x < p.n) out[threadIdx.x] = block_total(partials, threadIdx.x);
+        __syncthreads();
+        if (threadIdx.x == 0) *ticket = 0;
     }
 }
 
-// y = H(0:j,0:j)^{-1} g(0:j): back substitution on the rotated Hessenberg.
-__global__ void k_trisolve(double* st, int R, int j) {
+// Cycle start: g = [||r||, 0, ...], clear flags, store rtol and budget.
+__global__ void k_cycle_init(double* st, int R, double rtol, int budget) {
+    const St L = st_layout(R);
+    const double nr = sqrt(st[L.sc + SC_NRM]);
+    for (int i = 0; i <= R; ++i) st[L.g + i] = 0.0;
+    st[L.g] = nr;
+    st[L.sc + SC_INV] = nr > 0.0 ? 1.0 / nr : 0.0;
+    st[L.sc + SC_DONE] = 0.0;
+    st[L.sc + SC_REORTH] = 0.0;
+    st[L.sc + SC_STATUS] = DS_RUN;
+    st[L.sc + SC_JDONE] = 0.0;
+    st[L.sc + SC_RTOL] = rtol;
+    st[L.sc + SC_BUDGET] = budget;
+}
+
+// v_0 = r / ||r|| in place
+__global__ void k_scale_first(double* __restrict__ w, size_t n, const double* st, int R) {
+    const St L = st_layout(R);
+    const double a = st[L.sc + SC_INV];
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        w[e] *= a;
+}
+
+// y = H(0:J,0:J)^{-1} g(0:J), J = jdone, by back substitution.
+__global__ void k_trisolve(double* st, int R) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const St L = st_layout(R);
+    const int J = (int)st[L.sc + SC_JDONE];
     const double* H = st + L.H;
     double* y = st + L.y;
-    for (int i = j - 1; i >= 0; --i) {
+    for (int i = J - 1; i >= 0; --i) {
         double s = st[L.g + i];
-        for (int k = i + 1; k < j; ++k) s -= H[(size_t)k * (R + 1) + i] * y[k];
+        for (int k = i + 1; k < J; ++k) s -= H[(size_t)k * (R + 1) + i] * y[k];
         y[i] = s / H[(size_t)i * (R + 1) + i];
     }
 }
 
-// x += sum_{i<nv} y[i] Z_i
-__global__ void k_maxpy(double* __restrict__ x, const double* __restrict__ Z, size_t ld, int nv, size_t n,
-                        const double* __restrict__ y) {
-    __shared__ double ys[FMP_MAX_RESTART];
-    if (threadIdx.x < nv) ys[threadIdx.x] = y[threadIdx.x];
+// x += sum_{i < jdone} y_i Z_i
+__global__ void k_maxpy(double* __restrict__ x, const double* __restrict__ Z, size_t ld, size_t n, const double* st,
+                        int R) {
+    const St L = st_layout(R);
+    __shared__ double ys[kMaxV];
+    const int J = (int)st[L.sc + SC_JDONE];
+    if (threadIdx.x < J) ys[threadIdx.x] = st[L.y + threadIdx.x];
     __syncthreads();
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
         double a = x[e];
-        for (int i = 0; i < nv; ++i) a = fma(ys[i], Z[i * ld + e], a);
+        for (int i = 0; i < J; ++i) a = fma(ys[i], Z[i * ld + e], a);
         x[e] = a;
     }
 }
 
-// r = b - A x  (A = eps + beta K), into r; walls 0 (b, x obey the contract).
-__global__ void k_axpby(double* __restrict__ y, const double* __restrict__ b, size_t n, double alpha, double beta_) {
+// ---- BiCGSTAB kernels (van der Vorst's right-preconditioned form) -------
+// p = r + beta (p - omega v); first iteration p = r.
+__global__ void k_bicg_p(double* __restrict__ p, const double* __restrict__ r, const double* __restrict__ v,
+                         size_t n, const double* sc, int first) {
+    const double beta = first ? 0.0 : sc[SC_BETA];
+    const double omega = sc[SC_OMEGA];
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
-        y[e] = alpha * b[e] + beta_ * y[e];
+        p[e] = first ? r[e] : fma(beta, fma(-omega, v[e], p[e]), r[e]);
+}
+// s = r - alpha v
+__global__ void k_bicg_s(double* __restrict__ s, const double* __restrict__ r, const double* __restrict__ v,
+                         size_t n, const double* sc) {
+    const double alpha = sc[SC_ALPHA];
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        s[e] = fma(-alpha, v[e], r[e]);
+}
+// x += alpha phat + omega shat ; r = s - omega t
+__global__ void k_bicg_xr(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ ph,
+                          const double* __restrict__ sh, const double* __restrict__ s, const double* __restrict__ t,
+                          size_t n, const double* sc) {
+    const double alpha = sc[SC_ALPHA], omega = sc[SC_OMEGA];
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        x[e] = fma(omega, sh[e], fma(alpha, ph[e], x[e]));
+        r[e] = fma(-omega, t[e], s[e]);
+    }
+}
+// scalar updates from the dot slots D0, D1
+__global__ void k_bicg_scalars(double* sc, int which) {
+    if (threadIdx.x || blockIdx.x) return;
+    if (which == 0) {            // rho = <rhat, r> in D0: beta
+        const double rho = sc[SC_D0];
+        sc[SC_BETA] = (rho / sc[SC_RHO_OLD]) * (sc[SC_ALPHA] / sc[SC_OMEGA]);
+        sc[SC_RHO] = rho;
+    } else if (which == 1) {     // <rhat, v> in D0: alpha
+        sc[SC_ALPHA] = sc[SC_RHO] / sc[SC_D0];
+    } else {                     // <t, s> in D0, <t, t> in D1: omega
+        sc[SC_OMEGA] = sc[SC_D1] != 0.0 ? sc[SC_D0] / sc[SC_D1] : 0.0;
+        sc[SC_RHO_OLD] = sc[SC_RHO];
+    }
+}
+__global__ void k_bicg_reset(double* sc) {
+    if (threadIdx.x || blockIdx.x) return;
+    sc[SC_RHO_OLD] = sc[SC_ALPHA] = sc[SC_OMEGA] = 1.0;
 }
 
+
+int grid_stream(size_t n) {
+    size_t b = (n + kCH - 1) / kCH;
+    return (int)(b < 148 * 3 ? (b ? b : 1) : 148 * 3);
+}
 int grid_n(size_t n) {
-    size_t b = (n + kRedThreads - 1) / kRedThreads;
-    return (int)(b < (size_t)kRedBlocks ? (b ? b : 1) : kRedBlocks);
+    size_t b = (n + kT - 1) / kT;
+    return (int)(b < 148 * 8 ? (b ? b : 1) : 148 * 8);
 }
-
-// Dots of w against V_0..V_{nv-1} (nv <= kMaxV) into out[0..nv).
-cudaError_t mdot(fmp_ctx* c, const double* V, int nv, const double* w, double* out) {
-    k_mdot<<<grid_n(c->n_slots), kRedThreads, 0, c->stream>>>(V, c->ld, nv, w, c->n_slots, c->d_partials,
-                                                             c->d_ticket, out);
-    return cudaGetLastError();
-}
-
-}  // namespace
-
-cudaError_t fmp_ensure_krylov(fmp_ctx* c) {
-    const int R = c->opt.restart;
-    if (c->d_V && c->kry_restart >= R) return cudaSuccess;
-    cudaFree(c->d_V); cudaFree(c->d_Z); cudaFree(c->d_state);
-    c->d_V = c->d_Z = c->d_state = nullptr;
-    c->ld = (c->n_slots + 31) / 32 * 32;
-    cudaError_t e;
-    if ((e = cudaMalloc(&c->d_V, sizeof(double) * c->ld * (R + 1)))) return e;
-    if ((e = cudaMalloc(&c->d_Z, sizeof(double) * c->ld * R))) return e;
-    if ((e = cudaMalloc(&c->d_state, sizeof(double) * st_layout(R).total))) return e;
-    if ((e = cudaMemsetAsync(c->d_state, 0, sizeof(double) * st_layout(R).total, c->stream))) return e;
-    c->kry_restart = R;
-    return cudaSuccess;
-}
-
-namespace {
 
 struct Timer {
     fmp_ctx* c;
@@ -294,112 +511,311 @@ struct Timer {
     }
 };
 
-double read_scalar(fmp_ctx* c, const double* dptr, cudaError_t* err) {
-    *err = cudaMemcpyAsync(c->h_pinned, dptr, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-    if (*err == cudaSuccess) *err = cudaStreamSynchronize(c->stream);
-    return c->h_pinned[0];
+// <v, v> -> slot (v may be a caller buffer: scalar loads)
+cudaError_t norm2(fmp_ctx* c, const double* v, double* slot) {
+    Pairs p{};
+    p.a[0] = v; p.b[0] = v; p.n = 1;
+    ++c->launches;
+    k_pairdots<<<grid_n(c->n_slots), kT, 0, c->stream>>>(p, c->n_slots, slot, c->d_partials, c->d_ticket);
+    return cudaGetLastError();
+}
+
+// r = b - A x (one fused stencil pass)
+cudaError_t residual(fmp_ctx* c, const double* b, const double* x, double* r) {
+    ++c->launches;
+    return fmp_launch_curlcurl(x, c->d_eps_edge, r, -1.0, -c->beta, c->nx, c->ny, c->nz, c->stream, nullptr, b, 1.0);
+}
+
+// Enqueue Arnoldi step j; every kernel is gated on the device 'done' flag.
+int arnoldi_step(fmp_ctx* c, int j, fmp_solve_info* inf) {
+    const int R = c->kry_restart;
+    const St L = st_layout(R);
+    const size_t n = c->n_slots, ld = c->ld;
+    double* st = c->d_state;
+    const double* gate = st + L.sc + SC_DONE;
+    double* V = c->d_V;
+    double* vj = V + (size_t)j * ld;
+    double* zj = c->d_Z + (size_t)j * ld;
+    double* w = V + (size_t)(j + 1) * ld;
+    cudaStream_t s = c->stream;
+    {
+        Timer tm(c, &inf->ms_precond);
+        int rc = fmp_precond_gated(c, vj, zj, gate);
+        if (rc != FMP_OK) return rc;
+    }
+    {
+        Timer tm(c, &inf->ms_spmv);
+        ++c->launches;
+        FMP_CK(fmp_launch_curlcurl(zj, c->d_eps_edge, w, 1.0, c->beta, c->nx, c->ny, c->nz, s, gate));
+    }
+    {
+        Timer tm(c, &inf->ms_orth);
+        const int nv = j + 1;
+        ++c->launches;
+        k_dots<<<grid_stream(n), kT, kStreamSmem, s>>>(V, ld, nv, w, n, st, R, L.h1, 0, c->d_partials, c->d_ticket);
+        ++c->launches;
+        k_update<<<grid_stream(n), kT, kStreamSmem, s>>>(V, ld, nv, w, n, st, R, j, 0, c->d_partials, c->d_ticket);
+        ++c->launches;
+        k_dots<<<grid_stream(n), kT, kStreamSmem, s>>>(V, ld, nv, w, n, st, R, L.h2, 1, c->d_partials, c->d_ticket);
+        ++c->launches;
+        k_update<<<grid_stream(n), kT, kStreamSmem, s>>>(V, ld, nv, w, n, st, R, j, 1, c->d_partials, c->d_ticket);
+        ++c->launches;
+        k_scale_next<<<grid_n(n), kT, 0, s>>>(w, n, st, R, j);
+        FMP_CK(cudaGetLastError());
+    }
+    return FMP_OK;
+}
+
+// Capture one restart cycle (R gated Arnoldi steps) into a CUDA graph on
+// first use, then replay it.
+int run_cycle_graph(fmp_ctx* c) {
+    if (!c->graph_valid) {
+        if (c->graph_exec) { cudaGraphExecDestroy(c->graph_exec); c->graph_exec = nullptr; }
+        cudaStream_t orig = c->stream;
+        if (!c->capture_stream) FMP_CK(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+        c->stream = c->capture_stream;
+        cudaError_t e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal);
+        if (e) { c->stream = orig; return fmp_latch(c, e); }
+        fmp_solve_info dummy{};
+        int rc = FMP_OK;
+        const long long before = c->launches;
+        for (int j = 0; j < c->kry_restart && rc == FMP_OK; ++j) rc = arnoldi_step(c, j, &dummy);
+        c->graph_kernels = c->launches - before;
+        c->launches = before;
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(c->capture_stream, &g);
+        c->stream = orig;
+        if (rc != FMP_OK) { if (g) cudaGraphDestroy(g); return rc; }
+        FMP_CK(e);
+        e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        FMP_CK(e);
+        c->graph_valid = true;
+    }
+    FMP_CK(cudaGraphLaunch(c->graph_exec, c->stream));
+    c->launches += c->graph_kernels;
+    return FMP_OK;
 }
 
 }  // namespace
+
+// Opt the streamed kernels into their dynamic shared memory (at set-up).
+cudaError_t fmp_krylov_init() {
+    cudaError_t e = cudaFuncSetAttribute(k_dots, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStreamSmem);
+    if (e) return e;
+    return cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStreamSmem);
+}
+
+cudaError_t fmp_ensure_krylov(fmp_ctx* c) {
+    const int R = c->opt.restart;
+    const int need_v = R + 1 > 8 ? R + 1 : 8;   // BiCGSTAB uses 8: r, rhat, p, v, s, t, phat, shat
+    const int need_z = c->opt.krylov == FMP_KRYLOV_BICGSTAB ? 0 : R;
+    if (c->d_V && c->kry_restart == R && c->kry_nv >= need_v && c->kry_nz >= need_z) return cudaSuccess;
+    cudaFree(c->d_V); cudaFree(c->d_Z); cudaFree(c->d_state);
+    c->d_V = c->d_Z = c->d_state = nullptr;
+    c->kry_nv = c->kry_nz = c->kry_restart = 0;
+    c->graph_valid = false;
+    c->ld = (c->n_slots + 31) / 32 * 32;
+    cudaError_t e;
+    if ((e = cudaMalloc(&c->d_V, sizeof(double) * c->ld * need_v))) return e;
+    if (need_z && (e = cudaMalloc(&c->d_Z, sizeof(double) * c->ld * need_z))) return e;
+    if ((e = cudaMalloc(&c->d_state, sizeof(double) * st_layout(R).total))) return e;
+    if ((e = cudaMemsetAsync(c->d_state, 0, sizeof(double) * st_layout(R).total, c->stream))) return e;
+    c->kry_nv = need_v; c->kry_nz = need_z; c->kry_restart = R;
+    return cudaSuccess;
+}
 
 int fmp_fgmres(fmp_ctx* c, const double* b, double* x, fmp_solve_info* info) {
     fmp_solve_info inf;
     std::memset(&inf, 0, sizeof(inf));
     FMP_CK(fmp_ensure_krylov(c));
-    const int R = c->opt.restart;
+    const int R = c->kry_restart;
     const St L = st_layout(R);
     const size_t n = c->n_slots, ld = c->ld;
     double* st = c->d_state;
+    double* sc = st + L.sc;
     cudaStream_t s = c->stream;
-    cudaError_t err;
     cudaEvent_t t0 = c->ev[2], t1 = c->ev[3];
     FMP_CK(cudaEventRecord(t0, s));
+    double* V = c->d_V;
+    double* hp = c->h_pinned;
+    auto read_sc = [&]() -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(hp, sc, 16 * sizeof(double), cudaMemcpyDeviceToHost, s);
+        return e ? e : cudaStreamSynchronize(s);
+    };
 
-    // ||b||
-    k_norm<<<grid_n(n), kRedThreads, 0, s>>>(b, n, st, R, 0, c->d_partials, c->d_ticket);
-    FMP_CK(cudaGetLastError());
-    const double bnorm = read_scalar(c, st + L.sc + SC_NRM, &err);
-    FMP_CK(err);
+    FMP_CK(norm2(c, b, sc + SC_NRM));
+    FMP_CK(read_sc());
+    const double bnorm = std::sqrt(hp[SC_NRM]);
     int status = FMP_OK;
     if (!std::isfinite(bnorm)) status = FMP_ERR_NONFINITE;
     if (bnorm == 0.0) {
         FMP_CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
         inf.true_rel_res = 0.0;
     }
-    {
-        c->h_pinned[1] = bnorm;
-        FMP_CK(cudaMemcpyAsync(st + L.sc + SC_BNORM, &c->h_pinned[1], sizeof(double), cudaMemcpyHostToDevice, s));
-    }
-    double* V = c->d_V;
-    double* Z = c->d_Z;
+    hp[32] = bnorm;
+    FMP_CK(cudaMemcpyAsync(sc + SC_BNORM, hp + 32, sizeof(double), cudaMemcpyHostToDevice, s));
     while (status == FMP_OK && bnorm > 0.0) {
-        // r = b - A x -> V_0, true residual
-        FMP_CK(fmp_launch_curlcurl(x, c->d_eps_edge, V, 1.0, c->beta, c->nx, c->ny, c->nz, s));
-        k_axpby<<<grid_n(n), kRedThreads, 0, s>>>(V, b, n, 1.0, -1.0);
-        k_norm<<<grid_n(n), kRedThreads, 0, s>>>(V, n, st, R, 1, c->d_partials, c->d_ticket);
-        FMP_CK(cudaGetLastError());
-        const double rn = read_scalar(c, st + L.sc + SC_NRM, &err);
-        FMP_CK(err);
+        FMP_CK(residual(c, b, x, V));
+        FMP_CK(norm2(c, V, sc + SC_NRM));
+        FMP_CK(read_sc());
+        const double rn = std::sqrt(hp[SC_NRM]);
         inf.true_rel_res = rn / bnorm;
         if (!std::isfinite(rn)) { status = FMP_ERR_NONFINITE; break; }
         if (inf.true_rel_res <= c->opt.rtol) break;
         if (inf.iters >= c->opt.max_iters) { status = FMP_ERR_NOT_CONVERGED; break; }
-        k_scale<<<grid_n(n), kRedThreads, 0, s>>>(V, n, st + L.sc + SC_INV);
-        int jdone = 0;
-        bool stop = false;
-        for (int j = 0; j < R; ++j) {
-            double* vj = V + (size_t)j * ld;
-            double* zj = Z + (size_t)j * ld;
-            double* w = V + (size_t)(j + 1) * ld;
+        const int budget = c->opt.max_iters - inf.iters;
+        ++c->launches;
+        k_cycle_init<<<1, 1, 0, s>>>(st, R, c->opt.rtol, budget);
+        ++c->launches;
+        k_scale_first<<<grid_n(n), kT, 0, s>>>(V, n, st, R);
+        FMP_CK(cudaGetLastError());
+        if (c->opt.use_graph && !c->opt.timing) {
+            int rc = run_cycle_graph(c);
+            if (rc != FMP_OK) return rc;
+        } else {
+            for (int j = 0; j < R; ++j) {
+                int rc = arnoldi_step(c, j, &inf);
+                if (rc != FMP_OK) return rc;
+                FMP_CK(read_sc());   // stop enqueueing once the device says done
+                if (hp[SC_DONE] != 0.0) break;
+            }
+        }
+        ++c->launches;
+        k_trisolve<<<1, 32, 0, s>>>(st, R);
+        ++c->launches;
+        k_maxpy<<<grid_n(n), kT, 0, s>>>(x, c->d_Z, ld, n, st, R);
+        FMP_CK(cudaGetLastError());
+        FMP_CK(read_sc());
+        const int jdone = (int)hp[SC_JDONE];
+        inf.iters += jdone;
+        inf.restarts++;
+        inf.est_rel_res = hp[SC_EST];
+        const int ds = (int)hp[SC_STATUS];
+        if (hp[SC_KERR] != 0.0) return fmp_latch(c, cudaErrorLaunchTimeout);
+        if (ds == DS_NONFINITE) { status = FMP_ERR_NONFINITE; break; }
+        if (ds == DS_BREAK) {
+            FMP_CK(residual(c, b, x, V));
+            FMP_CK(norm2(c, V, sc + SC_NRM));
+            FMP_CK(read_sc());
+            inf.true_rel_res = std::sqrt(hp[SC_NRM]) / bnorm;
+            if (inf.true_rel_res > c->opt.rtol) status = FMP_ERR_BREAKDOWN;
+            break;
+        }
+    }
+    FMP_CK(cudaEventRecord(t1, s));
+    FMP_CK(cudaEventSynchronize(t1));
+    cudaEventElapsedTime(&inf.ms_total, t0, t1);
+    inf.status = status;
+    if (info) *info = inf;
+    return status;
+}
+
+int fmp_bicgstab(fmp_ctx* c, const double* b, double* x, fmp_solve_info* info) {
+    fmp_solve_info inf;
+    std::memset(&inf, 0, sizeof(inf));
+    FMP_CK(fmp_ensure_krylov(c));
+    const size_t n = c->n_slots, ld = c->ld;
+    cudaStream_t s = c->stream;
+    const St L = st_layout(c->kry_restart);
+    double* sc = c->d_state + L.sc;
+    double* hp = c->h_pinned;
+    double *r = c->d_V, *rh = r + ld, *p = rh + ld, *v = p + ld, *sv = v + ld, *t = sv + ld, *ph = t + ld,
+           *sh = ph + ld;
+    cudaEvent_t t0 = c->ev[2], t1 = c->ev[3];
+    FMP_CK(cudaEventRecord(t0, s));
+    auto read_sc = [&]() -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(hp, sc, 24 * sizeof(double), cudaMemcpyDeviceToHost, s);
+        return e ? e : cudaStreamSynchronize(s);
+    };
+    auto dots = [&](int k, const double* a0, const double* b0, const double* a1 = nullptr,
+                    const double* b1 = nullptr) -> cudaError_t {
+        Pairs pr{};
+        pr.a[0] = a0; pr.b[0] = b0; pr.n = 1;
+        if (a1) { pr.a[1] = a1; pr.b[1] = b1; pr.n = 2; }
+        ++c->launches;
+        k_pairdots<<<grid_n(n), kT, 0, s>>>(pr, n, sc + k, c->d_partials, c->d_ticket);
+        return cudaGetLastError();
+    };
+    FMP_CK(norm2(c, b, sc + SC_NRM));
+    FMP_CK(read_sc());
+    const double bnorm = std::sqrt(hp[SC_NRM]);
+    int status = FMP_OK;
+    if (!std::isfinite(bnorm)) status = FMP_ERR_NONFINITE;
+    if (bnorm == 0.0) {
+        FMP_CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    } else if (status == FMP_OK) {
+        FMP_CK(residual(c, b, x, r));
+        FMP_CK(cudaMemcpyAsync(rh, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        ++c->launches;
+        k_bicg_reset<<<1, 1, 0, s>>>(sc);
+        FMP_CK(dots(SC_D0, rh, r, r, r));   // rho, ||r||^2
+        FMP_CK(read_sc());
+        inf.true_rel_res = std::sqrt(hp[SC_D1]) / bnorm;
+        bool first = true;
+        while (inf.true_rel_res > c->opt.rtol) {
+            if (inf.iters >= c->opt.max_iters) { status = FMP_ERR_NOT_CONVERGED; break; }
+            ++c->launches;
+            k_bicg_scalars<<<1, 1, 0, s>>>(sc, 0);
+            ++c->launches;
+            k_bicg_p<<<grid_n(n), kT, 0, s>>>(p, r, v, n, sc, first ? 1 : 0);
+            first = false;
             {
                 Timer tm(c, &inf.ms_precond);
-                int rc = fmp_precond(c, vj, zj);
+                int rc = fmp_precond_gated(c, p, ph, nullptr);
                 if (rc != FMP_OK) return rc;
             }
             {
                 Timer tm(c, &inf.ms_spmv);
-                FMP_CK(fmp_launch_curlcurl(zj, c->d_eps_edge, w, 1.0, c->beta, c->nx, c->ny, c->nz, s));
+                ++c->launches;
+                FMP_CK(fmp_launch_curlcurl(ph, c->d_eps_edge, v, 1.0, c->beta, c->nx, c->ny, c->nz, s, nullptr));
+            }
+            FMP_CK(dots(SC_D0, rh, v));
+            ++c->launches;
+            k_bicg_scalars<<<1, 1, 0, s>>>(sc, 1);
+            ++c->launches;
+            k_bicg_s<<<grid_n(n), kT, 0, s>>>(sv, r, v, n, sc);
+            {
+                Timer tm(c, &inf.ms_precond);
+                int rc = fmp_precond_gated(c, sv, sh, nullptr);
+                if (rc != FMP_OK) return rc;
             }
             {
-                Timer tm(c, &inf.ms_orth);
-                const int nv = j + 1;
-                FMP_CK(mdot(c, V, nv, w, st + L.h1));
-                k_update_dot<<<grid_n(n), kRedThreads, 0, s>>>(V, ld, nv, w, n, st + L.h1, c->d_partials,
-                                                              c->d_ticket, st + L.h2);
-                k_update_norm_givens<<<grid_n(n), kRedThreads, 0, s>>>(V, ld, nv, w, n, st, R, j, c->d_partials,
-                                                                      c->d_ticket);
-                k_scale<<<grid_n(n), kRedThreads, 0, s>>>(w, n, st + L.sc + SC_INV);
-                FMP_CK(cudaGetLastError());
+                Timer tm(c, &inf.ms_spmv);
+                ++c->launches;
+                FMP_CK(fmp_launch_curlcurl(sh, c->d_eps_edge, t, 1.0, c->beta, c->nx, c->ny, c->nz, s, nullptr));
             }
-            FMP_CK(cudaMemcpyAsync(c->h_pinned, st + L.sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
-            FMP_CK(cudaStreamSynchronize(s));
-            const double est = c->h_pinned[SC_EST], flag = c->h_pinned[SC_FLAG], hn = c->h_pinned[SC_HN];
+            FMP_CK(dots(SC_D0, t, sv, t, t));
+            ++c->launches;
+            k_bicg_scalars<<<1, 1, 0, s>>>(sc, 2);
+            ++c->launches;
+            k_bicg_xr<<<grid_n(n), kT, 0, s>>>(x, r, ph, sh, sv, t, n, sc);
+            FMP_CK(dots(SC_D0, rh, r, r, r));
+            FMP_CK(read_sc());
             inf.iters++;
-            jdone = j + 1;
-            inf.est_rel_res = est;
-            if (!std::isfinite(est)) { status = FMP_ERR_NONFINITE; stop = true; break; }
-            if (est <= c->opt.rtol || inf.iters >= c->opt.max_iters) break;
-            if (flag != 0.0) { stop = true; status = FMP_ERR_BREAKDOWN; break; }
-            if (hn == 0.0) break;  // lucky breakdown: exact in this subspace
+            inf.est_rel_res = std::sqrt(hp[SC_D1]) / bnorm;
+            if (!std::isfinite(inf.est_rel_res) || !std::isfinite(hp[SC_OMEGA])) {
+                status = FMP_ERR_NONFINITE;
+                break;
+            }
+            if (inf.est_rel_res <= c->opt.rtol) {
+                FMP_CK(residual(c, b, x, t));
+                FMP_CK(norm2(c, t, sc + SC_NRM));
+                FMP_CK(read_sc());
+                inf.true_rel_res = std::sqrt(hp[SC_NRM]) / bnorm;
+                if (inf.true_rel_res <= c->opt.rtol) break;
+                // the recursive residual drifted from the true one: restart from it
+                FMP_CK(cudaMemcpyAsync(r, t, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+                FMP_CK(cudaMemcpyAsync(rh, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+                ++c->launches;
+                k_bicg_reset<<<1, 1, 0, s>>>(sc);
+                FMP_CK(dots(SC_D0, rh, r, r, r));
+                first = true;
+                continue;
+            }
+            if (hp[SC_OMEGA] == 0.0 || hp[SC_D0] == 0.0) { status = FMP_ERR_BREAKDOWN; break; }
+            inf.true_rel_res = inf.est_rel_res;
         }
-        if (jdone > 0 && status != FMP_ERR_NONFINITE) {
-            k_trisolve<<<1, 32, 0, s>>>(st, R, jdone);
-            k_maxpy<<<grid_n(n), kRedThreads, 0, s>>>(x, Z, ld, jdone, n, st + L.y);
-            FMP_CK(cudaGetLastError());
-            inf.restarts++;
-        }
-        if (stop && status == FMP_ERR_BREAKDOWN) {
-            // true residual decides whether the breakdown still met rtol
-            FMP_CK(fmp_launch_curlcurl(x, c->d_eps_edge, V, 1.0, c->beta, c->nx, c->ny, c->nz, s));
-            k_axpby<<<grid_n(n), kRedThreads, 0, s>>>(V, b, n, 1.0, -1.0);
-            k_norm<<<grid_n(n), kRedThreads, 0, s>>>(V, n, st, R, 0, c->d_partials, c->d_ticket);
-            const double rn = read_scalar(c, st + L.sc + SC_NRM, &err);
-            FMP_CK(err);
-            inf.true_rel_res = rn / bnorm;
-            if (inf.true_rel_res <= c->opt.rtol) status = FMP_OK;
-            break;
-        }
-        if (stop) break;
     }
     FMP_CK(cudaEventRecord(t1, s));
     FMP_CK(cudaEventSynchronize(t1));

@@ -14,6 +14,7 @@
 // The kernels are memory bound: one thread per cell computes the three
 // components, x-fastest so warps read 256-byte rows; neighbour reads hit L1/L2.
 #include "fmp_internal.h"
+#include "bulk.cuh"
 
 namespace {
 
@@ -117,21 +118,86 @@ __global__ void k_eps_bar(const double* __restrict__ ee, FmpBox* boxes, Dims d) 
     }
 }
 
-__global__ void __launch_bounds__(256)
+// Tiled, k-marching double-curl apply. A block owns a 32 x 8 (i, j) tile and
+// KC consecutive k-planes; the three components of planes k-1, k, k+1 (with
+// a one-cell halo in i and j, zero outside the grid) rotate through shared
+// memory, filled by cp.async two planes ahead, so each input value is read
+// from memory about once per tile. Short k-runs (KC = 4) give enough blocks
+// per SM to keep the loads of several planes in flight.
+// y = s_b * b + c_eps * eps o x + c_k * K x  (b may be null), walls -> 0.
+constexpr int TX = 32, TY = 8, KC = 4;
+constexpr int PX = TX + 2, PY = TY + 2, PLANE = 3 * PX * PY;
+
+__global__ void __launch_bounds__(TX * TY)
 k_curlcurl(const double* __restrict__ x, const double* __restrict__ eps, double* __restrict__ y,
-           double c_eps, double c_k, Dims d) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i >= d.nx || j >= d.ny) return;
-    const long long o = k * d.plane + (long long)j * d.nx + i;
-    double vx = 0.0, vy = 0.0, vz = 0.0;
-    if (j >= 1 && k >= 1) vx = c_eps * eps[o] * x[o] + c_k * kx_at(x, d, k, j, i);
-    if (i >= 1 && k >= 1) vy = c_eps * eps[d.comp + o] * x[d.comp + o] + c_k * ky_at(x, d, k, j, i);
-    if (i >= 1 && j >= 1) vz = c_eps * eps[2 * d.comp + o] * x[2 * d.comp + o] + c_k * kz_at(x, d, k, j, i);
-    y[o] = vx;
-    y[d.comp + o] = vy;
-    y[2 * d.comp + o] = vz;
+           const double* __restrict__ b, double s_b, double c_eps, double c_k, Dims d,
+           const double* __restrict__ gate) {
+    if (gate && *gate != 0.0) return;
+    __shared__ __align__(16) double P[4 * PLANE];   // planes k-1, k, k+1 and the one in flight
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * KC;
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    // asynchronous copy of plane k into slot (zero outside the grid), one commit group
+    auto issue = [&](int slot, int k) {
+        double* dst = P + slot * PLANE;
+        for (int t = threadIdx.x; t < PLANE; t += TX * TY) {
+            const int c = t / (PX * PY), r = t - c * PX * PY;
+            const int jj = r / PX, ii = r - jj * PX;
+            const int gi = i0 + ii - 1, gj = j0 + jj - 1;
+            const bool ok = k >= 0 && k < d.nz && gi >= 0 && gi < d.nx && gj >= 0 && gj < d.ny;
+            const double* src = ok ? x + c * d.comp + k * d.plane + (long long)gj * d.nx + gi : x;
+            fmp::cp_async8(dst + t, src, ok);
+        }
+        fmp::cp_async_commit();
+    };
+    issue(0, k0 - 1);
+    issue(1, k0);
+    issue(2, k0 + 1);
+    const int gi = i0 + tx, gj = j0 + ty;
+    const bool live = gi < d.nx && gj < d.ny;
+    const int ii = tx + 1, jj = ty + 1;
+    for (int kk = 0; kk < KC && k0 + kk < d.nz; ++kk) {
+        const int k = k0 + kk;
+        issue((kk + 3) & 3, k + 2);     // prefetch two planes ahead
+        fmp::cp_async_wait<1>();        // planes up to k+1 have landed
+        __syncthreads();
+        const double* Pm = P + (kk & 3) * PLANE;         // plane k-1
+        const double* Pc = P + ((kk + 1) & 3) * PLANE;   // plane k
+        const double* Pp = P + ((kk + 2) & 3) * PLANE;   // plane k+1
+        auto X = [&](const double* Q, int c, int dj, int di) { return Q[c * PX * PY + (jj + dj) * PX + ii + di]; };
+        if (live) {
+            const long long o = k * d.plane + (long long)gj * d.nx + gi;
+            double vx = 0.0, vy = 0.0, vz = 0.0;
+            if (gj >= 1 && k >= 1) {
+                const double kx = 4.0 * X(Pc, 0, 0, 0) - X(Pc, 0, 1, 0) - X(Pc, 0, -1, 0) - X(Pp, 0, 0, 0) -
+                                  X(Pm, 0, 0, 0) +
+                                  (X(Pc, 1, 0, 1) - X(Pc, 1, 0, 0) - X(Pc, 1, -1, 1) + X(Pc, 1, -1, 0)) +
+                                  (X(Pc, 2, 0, 1) - X(Pc, 2, 0, 0) - X(Pm, 2, 0, 1) + X(Pm, 2, 0, 0));
+                vx = c_eps * eps[o] * X(Pc, 0, 0, 0) + c_k * kx;
+                if (b) vx = fma(s_b, b[o], vx);
+            }
+            if (gi >= 1 && k >= 1) {
+                const double ky = 4.0 * X(Pc, 1, 0, 0) - X(Pp, 1, 0, 0) - X(Pm, 1, 0, 0) - X(Pc, 1, 0, 1) -
+                                  X(Pc, 1, 0, -1) +
+                                  (X(Pc, 2, 1, 0) - X(Pc, 2, 0, 0) - X(Pm, 2, 1, 0) + X(Pm, 2, 0, 0)) +
+                                  (X(Pc, 0, 1, 0) - X(Pc, 0, 0, 0) - X(Pc, 0, 1, -1) + X(Pc, 0, 0, -1));
+                vy = c_eps * eps[d.comp + o] * X(Pc, 1, 0, 0) + c_k * ky;
+                if (b) vy = fma(s_b, b[d.comp + o], vy);
+            }
+            if (gi >= 1 && gj >= 1) {
+                const double kz = 4.0 * X(Pc, 2, 0, 0) - X(Pc, 2, 0, 1) - X(Pc, 2, 0, -1) - X(Pc, 2, 1, 0) -
+                                  X(Pc, 2, -1, 0) +
+                                  (X(Pp, 0, 0, 0) - X(Pc, 0, 0, 0) - X(Pp, 0, 0, -1) + X(Pc, 0, 0, -1)) +
+                                  (X(Pp, 1, 0, 0) - X(Pc, 1, 0, 0) - X(Pp, 1, -1, 0) + X(Pc, 1, -1, 0));
+                vz = c_eps * eps[2 * d.comp + o] * X(Pc, 2, 0, 0) + c_k * kz;
+                if (b) vz = fma(s_b, b[2 * d.comp + o], vz);
+            }
+            y[o] = vx;
+            y[d.comp + o] = vy;
+            y[2 * d.comp + o] = vz;
+        }
+        __syncthreads();
+    }
+    fmp::cp_async_wait<0>();   // no copy may outlive the block
 }
 
 __global__ void __launch_bounds__(256)
@@ -201,10 +267,10 @@ cudaError_t fmp_launch_eps_bar(const double* eps_edge, FmpBox* d_boxes, int n_bo
     return cudaGetLastError();
 }
 
-cudaError_t fmp_launch_curlcurl(const double* x, const double* eps, double* y, double c_eps, double c_k,
-                                int nx, int ny, int nz, cudaStream_t s) {
-    dim3 b(64, 4, 1);
-    k_curlcurl<<<grid_of(nx, ny, nz, b), b, 0, s>>>(x, eps, y, c_eps, c_k, dims(nx, ny, nz));
+cudaError_t fmp_launch_curlcurl(const double* x, const double* eps, double* y, double c_eps, double c_k, int nx,
+                                int ny, int nz, cudaStream_t s, const double* gate, const double* b, double s_b) {
+    dim3 g((nx + TX - 1) / TX, (ny + TY - 1) / TY, (nz + KC - 1) / KC);
+    k_curlcurl<<<g, TX * TY, 0, s>>>(x, eps, y, b, s_b, c_eps, c_k, dims(nx, ny, nz), gate);
     return cudaGetLastError();
 }
 

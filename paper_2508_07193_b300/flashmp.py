@@ -81,6 +81,7 @@ def lib():
         "fmp_set_stream": (_I, [_P, _P]),
         "fmp_get_eps_edge": (_I, [_P, _P]),
         "fmp_get_num_boxes": (_I, [_P, C.POINTER(_I)]),
+        "fmp_get_launch_count": (_I, [_P, C.POINTER(C.c_longlong)]),
         "fmp_get_box": (_I, [_P, _I, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I),
                              C.POINTER(_D)]),
         "fmp_curlcurl_apply": (_I, [_P, _P, _P, _D, _D]),
@@ -219,6 +220,11 @@ class Context:
         out = self.empty_field()
         _check(lib().fmp_get_eps_edge(self._h, _ptr(out)), "fmp_get_eps_edge")
         return out
+
+    def launch_count(self):
+        n = C.c_longlong()
+        _check(lib().fmp_get_launch_count(self._h, C.byref(n)), "fmp_get_launch_count")
+        return n.value
 
     def num_boxes(self):
         n = C.c_int()

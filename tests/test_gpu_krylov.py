@@ -96,3 +96,29 @@ def test_cn_steps_match_oracle_and_conserve_energy():
     e1 = cn.energy(ee, host(Ed), host(Hd))
     e0 = cn.energy(ee, E, H)
     assert abs(e1 - e0) <= 1e-9 * e0
+
+
+@pytest.mark.parametrize("w", [
+    wl.small(),
+    wl.small(grid=(12, 10, 8), cuts=((3, 3, 3, 3), (2, 8), (8,)), overlap=2, seed=23, n_eps_boxes=3, beta=25.0),
+], ids=["small", "beta25"])
+def test_bicgstab_matches_oracle(w):
+    ctx = context(w, krylov="bicgstab", rtol=1e-10)
+    x, info = ctx.krylov_solve(dev(w.rhs))
+    ee, A, M = _oracle_ops(w)
+    b = w.rhs.reshape(-1)
+    true = np.linalg.norm(b - A @ host(x).reshape(-1)) / np.linalg.norm(b)
+    assert true <= 1e-10
+    _, io = krylov.bicgstab(lambda v: A @ v, M, b, rtol=1e-10)
+    assert abs(info["iters"] - io["iters"]) <= max(3, 0.3 * io["iters"])
+
+
+def test_graph_replay_matches_host_loop():
+    w = wl.small(grid=(24, 24, 24), cuts=((8, 8, 8),) * 3, overlap=2, seed=22, n_eps_boxes=6)
+    ctx = context(w, rtol=1e-10, restart=8)
+    x1, i1 = ctx.krylov_solve(dev(w.rhs))
+    ctx.set_options(use_graph=True)
+    x2, i2 = ctx.krylov_solve(dev(w.rhs))
+    x3, i3 = ctx.krylov_solve(dev(w.rhs))        # replay of the captured cycle
+    assert i1["iters"] == i2["iters"] == i3["iters"] and i1["restarts"] == i2["restarts"]
+    assert np.array_equal(host(x1), host(x2)) and np.array_equal(host(x2), host(x3))
