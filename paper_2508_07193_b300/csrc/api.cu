@@ -4,6 +4,10 @@
 // include/flashmp.h.
 #include "fmp_internal.h"
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cstdint>
+
 #include <cmath>
 #include <cstring>
 #include <algorithm>
@@ -52,6 +56,30 @@ void fold_table(int m, bool dst, const double* T, double* F) {
     for (int ka = 0; ka < f.nka; ++ka) {
         const int k = 2 * ka + 1 - f.s0;
         for (int q = 0; q < f.npair; ++q) FA[ka * f.lb + q] = T[k * m + f.off + q];
+    }
+}
+
+// Round a float to tf32 (10 explicit mantissa bits, to nearest, ties away).
+float round_tf32(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
+    float y;
+    std::memcpy(&y, &u, 4);
+    return y;
+}
+
+// Reduced-precision tables of one extent: T and T^T of DCT-II and DST-I, each
+// zero padded to [Mp][Mp] with Mp = round_up(m, 16), in the order
+// [C][C^T][S][S^T], as doubles (converted per element type on upload).
+void mp_tables(int m, const double* C, const double* S, std::vector<double>& out) {
+    const int M = (m + 15) / 16 * 16;
+    const double* T[2] = {C, S};
+    for (int w = 0; w < 2; ++w) {
+        for (int k = 0; k < M; ++k)
+            for (int i = 0; i < M; ++i) out.push_back(k < m && i < m ? T[w][k * m + i] : 0.0);
+        for (int i = 0; i < M; ++i)
+            for (int k = 0; k < M; ++k) out.push_back(k < m && i < m ? T[w][k * m + i] : 0.0);
     }
 }
 
@@ -123,6 +151,16 @@ int fmp_precond_gated(fmp_ctx* c, const double* r, double* z, const double* gate
             FMP_CK(fmp_launch_transform_solve_fp64(c->ras, c->d_tabs, r, z, c->d_scratch, c->nx, c->ny, c->nz,
                                                    c->beta, c->stream, gate));
             return FMP_OK;
+        case FMP_PREC_BF16:
+        case FMP_PREC_FP16:
+        case FMP_PREC_TF32: {
+            const int w = c->opt.precision == FMP_PREC_BF16 ? 0 : c->opt.precision == FMP_PREC_FP16 ? 1 : 2;
+            c->launches += c->opt.precision == FMP_PREC_FP16 ? 4 : 3;
+            FMP_CK(fmp_launch_transform_solve_mixed(c->opt.precision, c->ras, c->d_tab_mp[w], c->d_tabs, r, z,
+                                                    c->d_scratch, c->d_bscale, c->nx, c->ny, c->nz, c->beta,
+                                                    c->stream, gate));
+            return FMP_OK;
+        }
         default:
             return FMP_ERR_UNSUPPORTED;
     }
@@ -253,6 +291,14 @@ int fmp_setup(fmp_ctx** out, fmp_grid g, const double* eps_cell, double beta, co
         fold_table(m, false, &tabs[off_c[m]], &tabs[off_cf[m]]);
         fold_table(m, true, &tabs[off_s[m]], &tabs[off_sf[m]]);
     }
+    std::vector<double> mp;
+    std::map<int, int> off_mpc, off_mps;
+    for (auto& kv : ext_index) {
+        const int m = kv.first, M = (m + 15) / 16 * 16;
+        off_mpc[m] = (int)mp.size();
+        off_mps[m] = (int)mp.size() + 2 * M * M;
+        mp_tables(m, &tabs[off_c[m]], &tabs[off_s[m]], mp);
+    }
     long long scr = 0;
     for (FmpBox& b : boxes) {
         for (int a = 0; a < 3; ++a) {
@@ -261,6 +307,8 @@ int fmp_setup(fmp_ctx** out, fmp_grid g, const double* eps_cell, double beta, co
             b.sig_off[a] = off_sig[b.m[a]];
             b.dctf_off[a] = off_cf[b.m[a]];
             b.dstf_off[a] = off_sf[b.m[a]];
+            b.mpc_off[a] = off_mpc[b.m[a]];
+            b.mps_off[a] = off_mps[b.m[a]];
         }
         b.scr_off = scr;
         scr += 3LL * b.m[0] * b.m[1] * b.m[2];
@@ -271,11 +319,32 @@ int fmp_setup(fmp_ctx** out, fmp_grid g, const double* eps_cell, double beta, co
     for (int t = 0; t < 8; ++t) SETUP_CK(cudaEventCreate(&c->ev[t]));
     SETUP_CK(cudaMallocHost(&c->h_pinned, 64 * sizeof(double)));
     SETUP_CK(upload(&c->d_tabs, tabs, c->stream));
+    {
+        std::vector<__nv_bfloat16> tb(mp.size());
+        std::vector<__half> th(mp.size());
+        std::vector<float> tf(mp.size());
+        for (size_t q = 0; q < mp.size(); ++q) {
+            tb[q] = __float2bfloat16((float)mp[q]);
+            th[q] = __float2half((float)mp[q]);
+            tf[q] = round_tf32((float)mp[q]);
+        }
+        __nv_bfloat16* db = nullptr;
+        __half* dh = nullptr;
+        float* df = nullptr;
+        SETUP_CK(upload(&db, tb, c->stream));
+        c->d_tab_mp[0] = db;
+        SETUP_CK(upload(&dh, th, c->stream));
+        c->d_tab_mp[1] = dh;
+        SETUP_CK(upload(&df, tf, c->stream));
+        c->d_tab_mp[2] = df;
+    }
     c->tab_len = tabs.size();
     SETUP_CK(cudaMalloc(&c->d_eps_edge, sizeof(double) * c->n_slots));
     SETUP_CK(fmp_launch_eps_edge(eps_cell, c->d_eps_edge, g.nx, g.ny, g.nz, c->stream));
     SETUP_CK(make_plan(c->ras, boxes, c->stream));
     SETUP_CK(fmp_transform_init_fp64(c->ras));
+    SETUP_CK(fmp_transform_init_mixed(c->ras));
+    SETUP_CK(cudaMalloc(&c->d_bscale, sizeof(double) * boxes.size()));
     SETUP_CK(fmp_krylov_init());
     SETUP_CK(fmp_launch_eps_bar(c->d_eps_edge, c->ras.d_boxes, c->ras.n_boxes, g.nx, g.ny, g.nz, c->stream));
     SETUP_CK(cudaMemcpyAsync(boxes.data(), c->ras.d_boxes, sizeof(FmpBox) * boxes.size(), cudaMemcpyDeviceToHost,
@@ -305,6 +374,8 @@ void fmp_destroy(fmp_ctx* c) {
     cudaFree(c->d_eps_edge); cudaFree(c->d_tabs); cudaFree(c->d_scratch); cudaFree(c->d_scratch1);
     cudaFree(c->d_V); cudaFree(c->d_Z); cudaFree(c->d_w); cudaFree(c->d_tmp); cudaFree(c->d_tmp2);
     cudaFree(c->d_partials); cudaFree(c->d_state); cudaFree(c->d_ticket);
+    for (int t = 0; t < 3; ++t) cudaFree(c->d_tab_mp[t]);
+    cudaFree(c->d_bscale);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);

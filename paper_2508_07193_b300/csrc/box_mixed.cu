@@ -1,0 +1,418 @@
+// Reduced-precision batched subdomain exact solve: the transforms of
+// Algorithm 1 (exact_solve) as tensor-core GEMMs with bf16 / fp16 / tf32
+// inputs and fp32 accumulation; the per-mode 3x3 inverse (Eq. 12) in fp32;
+// float64 input r and float64 output z. The Krylov iteration around it stays
+// float64 (flexible GMRES absorbs the preconditioner's rounding).
+//
+// Same three passes as the float64 path (gather + x/y transforms per z-slab;
+// z transform + 3x3 + inverse z per column tile; inverse y/x + owned scatter
+// per owned z-slab), with the intermediate field kept in the input type
+// (2 bytes per slot for bf16/fp16), so the batch is bound by HBM traffic of
+// the float64 input and output. Every axis contraction is a small GEMM
+// (M, N, K <= 80, padded to the MMA shape) on mma.sync fragments loaded from
+// shared memory; tables are zero padded so padding never leaks into results.
+//
+// fp16 has a narrow exponent range: each box is scaled by the largest |r| on
+// its extended box (all three components share one factor, since the 3x3
+// couples them) before the cast and rescaled on output. bf16 and tf32 carry
+// the fp32 exponent range and are not scaled.
+#include "fmp_internal.h"
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+namespace {
+
+constexpr int kT = 256;   // 8 warps
+constexpr int kPad = 8;   // row padding (elements) against bank conflicts
+
+__host__ __device__ __forceinline__ int rup(int v, int a) { return (v + a - 1) / a * a; }
+
+// ---- MMA traits ---------------------------------------------------------
+struct BF16T {
+    using E = __nv_bfloat16;
+    static constexpr int KS = 16;
+    static __device__ __forceinline__ E cvt(float x) { return __float2bfloat16_rn(x); }
+    static __device__ __forceinline__ float back(E x) { return __bfloat162float(x); }
+    static __device__ __forceinline__ void mma(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+            "{%0,%1,%2,%3};"
+            : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+    }
+};
+struct FP16T {
+    using E = __half;
+    static constexpr int KS = 16;
+    static __device__ __forceinline__ E cvt(float x) { return __float2half_rn(x); }
+    static __device__ __forceinline__ float back(E x) { return __half2float(x); }
+    static __device__ __forceinline__ void mma(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+            "{%0,%1,%2,%3};"
+            : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+    }
+};
+struct TF32T {
+    using E = float;   // stored already rounded to tf32
+    static constexpr int KS = 8;
+    static __device__ __forceinline__ E cvt(float x) {
+        uint32_t r;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+        return __uint_as_float(r);
+    }
+    static __device__ __forceinline__ float back(E x) { return x; }
+    static __device__ __forceinline__ void mma(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+        asm volatile(
+            "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+            "{%0,%1,%2,%3};"
+            : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+    }
+};
+
+// Fragment loads from shared memory. A is row-major [M][lda] (K contiguous);
+// B is given transposed, Bt[N][ldb] (K contiguous), i.e. the "col" operand.
+template <class Tr>
+__device__ __forceinline__ void load_a(const typename Tr::E* A, int lda, int m0, int k0, uint32_t (&a)[4]) {
+    const int lane = threadIdx.x & 31, r = lane >> 2, c = lane & 3;
+    if constexpr (Tr::KS == 16) {
+        const typename Tr::E* p = A + (m0 + r) * lda + k0 + 2 * c;
+        a[0] = *reinterpret_cast<const uint32_t*>(p);
+        a[1] = *reinterpret_cast<const uint32_t*>(p + 8 * lda);
+        a[2] = *reinterpret_cast<const uint32_t*>(p + 8);
+        a[3] = *reinterpret_cast<const uint32_t*>(p + 8 * lda + 8);
+    } else {
+        const typename Tr::E* p = A + (m0 + r) * lda + k0 + c;
+        a[0] = __float_as_uint(p[0]);
+        a[1] = __float_as_uint(p[8 * lda]);
+        a[2] = __float_as_uint(p[4]);
+        a[3] = __float_as_uint(p[8 * lda + 4]);
+    }
+}
+template <class Tr>
+__device__ __forceinline__ void load_b(const typename Tr::E* Bt, int ldb, int n0, int k0, uint32_t (&b)[2]) {
+    const int lane = threadIdx.x & 31, r = lane >> 2, c = lane & 3;
+    if constexpr (Tr::KS == 16) {
+        const typename Tr::E* p = Bt + (n0 + r) * ldb + k0 + 2 * c;
+        b[0] = *reinterpret_cast<const uint32_t*>(p);
+        b[1] = *reinterpret_cast<const uint32_t*>(p + 8);
+    } else {
+        const typename Tr::E* p = Bt + (n0 + r) * ldb + k0 + c;
+        b[0] = __float_as_uint(p[0]);
+        b[1] = __float_as_uint(p[4]);
+    }
+}
+
+// C[m][n] = sum_k A[m][k] Bt[n][k] over 16 x 8 tiles whose rows start in
+// [mlo, mhi) (16-aligned) and columns in [0, N); the 8 warps share the tiles.
+// epi(m, n, value) receives every element of every computed tile.
+template <class Tr, class Epi>
+__device__ __forceinline__ void warp_gemm(const typename Tr::E* A, int lda, const typename Tr::E* Bt, int ldb,
+                                          int mlo, int mhi, int N, int K, Epi epi) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mt = (mhi - mlo) / 16, nt = N / 8;
+    for (int t = warp; t < mt * nt; t += kT / 32) {
+        const int m0 = mlo + (t / nt) * 16, n0 = (t % nt) * 8;
+        float c[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int k0 = 0; k0 < K; k0 += Tr::KS) {
+            uint32_t a[4], b[2];
+            load_a<Tr>(A, lda, m0, k0, a);
+            load_b<Tr>(Bt, ldb, n0, k0, b);
+            Tr::mma(c, a, b);
+        }
+        const int r = lane >> 2, cc = 2 * (lane & 3);
+        epi(m0 + r, n0 + cc, c[0]);
+        epi(m0 + r, n0 + cc + 1, c[1]);
+        epi(m0 + r + 8, n0 + cc, c[2]);
+        epi(m0 + r + 8, n0 + cc + 1, c[3]);
+    }
+}
+
+// Copy a padded table [rows][Kp] (global, element type) into shared rows of
+// stride ld.
+template <class E>
+__device__ __forceinline__ void stage_table(E* dst, int ld, const E* src, int rows, int Kp) {
+    for (int t = threadIdx.x; t < rows * Kp; t += blockDim.x) {
+        const int r = t / Kp, k = t - r * Kp;
+        dst[r * ld + k] = src[t];
+    }
+}
+
+__device__ __forceinline__ bool edge_wall(int c, int i, int j, int k) {
+    return c == 0 ? (j == 0 || k == 0) : c == 1 ? (i == 0 || k == 0) : (i == 0 || j == 0);
+}
+
+// Per extent m: Tp = T[k][i] and TTp = T^T[i][k], both zero padded to
+// [Mp][Mp], Mp = round_up(m, 16), for T in {DCT-II, DST-I}.
+struct MpTab {
+    const void* base;
+};
+template <class E>
+__device__ __forceinline__ const E* mp_table(const void* tabs, int off) {
+    return reinterpret_cast<const E*>(tabs) + off;
+}
+
+// ---- pass A: gather, cast, x and y transforms of one z-slab ------------
+template <class Tr>
+__global__ void __launch_bounds__(kT)
+k_mp_fwd_xy(const double* __restrict__ r, void* __restrict__ scr_v, const FmpBox* __restrict__ boxes,
+            const int4* __restrict__ items, const void* __restrict__ tabs, const double* __restrict__ bscale,
+            int nx, int ny, int nz, const double* __restrict__ gate) {
+    using E = typename Tr::E;
+    if (gate && *gate != 0.0) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int4 it = items[blockIdx.x];
+    const FmpBox B = boxes[it.x];
+    const int c = it.y, kz = it.z;
+    const int mx = B.m[0], my = B.m[1], mz = B.m[2];
+    const int MX = rup(mx, 16), MY = rup(my, 16);
+    const int LX = MX + kPad, LY = MY + kPad;
+    E* scr = reinterpret_cast<E*>(scr_v) + B.scr_off + ((long long)c * mz + kz) * mx * my;
+    E* Xs = reinterpret_cast<E*>(smraw);   // [MY][LX]   slab, rows y
+    E* TX = Xs + MY * LX;                  // [MX][LX]   T_x[kx][x]
+    E* Pt = TX + MX * LX;                  // [MX][LY]   P^T[kx][y]
+    E* TY = Pt + MX * LY;                  // [MY][LY]   T_y[ky][y]
+    const bool sx = c != 0, sy = c != 1;
+    stage_table(TX, LX, mp_table<E>(tabs, sx ? B.mps_off[0] : B.mpc_off[0]), MX, MX);
+    stage_table(TY, LY, mp_table<E>(tabs, sy ? B.mps_off[1] : B.mpc_off[1]), MY, MY);
+    const float inv_s = bscale ? (float)(1.0 / bscale[it.x]) : 1.f;
+    const int gk = B.ext_lo[2] + kz;
+    const double* src = r + (((long long)c * nz + gk) * ny + B.ext_lo[1]) * (long long)nx + B.ext_lo[0];
+    for (int t = threadIdx.x; t < MY * LX; t += blockDim.x) {
+        const int j = t / LX, i = t - j * LX;
+        float v = 0.f;
+        if (i < mx && j < my && !edge_wall(c, i, j, kz)) v = (float)src[(long long)j * nx + i] * inv_s;
+        Xs[t] = Tr::cvt(v);
+    }
+    for (int t = threadIdx.x; t < MX * LY; t += blockDim.x) Pt[t] = Tr::cvt(0.f);
+    __syncthreads();
+    // P[y][kx] = sum_x X[y][x] T_x[kx][x]  -> stored transposed
+    warp_gemm<Tr>(Xs, LX, TX, LX, 0, MY, rup(mx, 8), MX,
+                  [&](int y, int kx, float v) { Pt[kx * LY + y] = Tr::cvt(v); });
+    __syncthreads();
+    // out[ky][kx] = sum_y T_y[ky][y] P[y][kx]
+    warp_gemm<Tr>(TY, LY, Pt, LY, 0, MY, rup(mx, 8), MY, [&](int ky, int kx, float v) {
+        if (ky < my && kx < mx) scr[ky * mx + kx] = Tr::cvt(v);
+    });
+}
+
+// ---- pass B: z transform, 3x3 solve in fp32, inverse z (owned slabs) --
+template <class Tr>
+__global__ void __launch_bounds__(kT)
+k_mp_z_solve(void* __restrict__ scr_v, const FmpBox* __restrict__ boxes, const int2* __restrict__ items,
+             const void* __restrict__ tabs, const double* __restrict__ tabs64, double beta, int ct,
+             const double* __restrict__ gate) {
+    using E = typename Tr::E;
+    if (gate && *gate != 0.0) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int2 itb = items[blockIdx.x];
+    const FmpBox B = boxes[itb.x];
+    const int col0 = itb.y;
+    const int mx = B.m[0], my = B.m[1], mz = B.m[2];
+    const int nxy = mx * my;
+    const int ncol = min(ct, nxy - col0);
+    const int MZ = rup(mz, 16), LZ = MZ + kPad;
+    E* In = reinterpret_cast<E*>(smraw);   // [3][ct][LZ]  (col-major per component)
+    E* Es = In + 3 * ct * LZ;              // [3][ct][LZ]  solved modes, col-major
+    E* TC = Es + 3 * ct * LZ;              // [MZ][LZ] DCT_z[kz][z]
+    E* TS = TC + MZ * LZ;                  // DST_z[kz][z]
+    E* TCt = TS + MZ * LZ;                 // DCT_z^T[z][kz]
+    E* TSt = TCt + MZ * LZ;                // DST_z^T[z][kz]
+    float* Of = reinterpret_cast<float*>(TSt + MZ * LZ);   // [3][MZ][ct] fp32 modes
+    stage_table(TC, LZ, mp_table<E>(tabs, B.mpc_off[2]), MZ, MZ);
+    stage_table(TS, LZ, mp_table<E>(tabs, B.mps_off[2]), MZ, MZ);
+    stage_table(TCt, LZ, mp_table<E>(tabs, B.mpc_off[2] + MZ * MZ), MZ, MZ);
+    stage_table(TSt, LZ, mp_table<E>(tabs, B.mps_off[2] + MZ * MZ), MZ, MZ);
+    const E* scr = reinterpret_cast<const E*>(scr_v) + B.scr_off;
+    for (int t = threadIdx.x; t < 3 * ct * LZ; t += blockDim.x) {
+        const int cc = t / (ct * LZ), rem = t - cc * ct * LZ;
+        const int col = rem / LZ, z = rem - col * LZ;
+        In[t] = (col < ncol && z < mz) ? scr[((long long)cc * mz + z) * nxy + col0 + col] : Tr::cvt(0.f);
+        Es[t] = Tr::cvt(0.f);
+    }
+    __syncthreads();
+    for (int cc = 0; cc < 3; ++cc) {
+        const E* T = cc == 2 ? TC : TS;
+        float* O = Of + cc * MZ * ct;
+        warp_gemm<Tr>(T, LZ, In + cc * ct * LZ, LZ, 0, MZ, ct, MZ, [&](int kz, int col, float v) { O[kz * ct + col] = v; });
+    }
+    __syncthreads();
+    const double* sgx = tabs64 + B.sig_off[0];
+    const double* sgy = tabs64 + B.sig_off[1];
+    const double* sgz = tabs64 + B.sig_off[2];
+    const float eb = (float)B.eps_bar, bt = (float)beta, beb = (float)(beta / B.eps_bar);
+    for (int t = threadIdx.x; t < mz * ct; t += blockDim.x) {
+        const int kz = t / ct, col = t - kz * ct;
+        if (col >= ncol) continue;
+        const int q = col0 + col;
+        const int ky = q / mx, kx = q - ky * mx;
+        const float sx = (float)sgx[kx], sy = (float)sgy[ky], sz = (float)sgz[kz];
+        const float r0 = Of[kz * ct + col], r1 = Of[MZ * ct + kz * ct + col], r2 = Of[2 * MZ * ct + kz * ct + col];
+        const float sr = fmaf(sx, r0, fmaf(sy, r1, sz * r2));
+        const float inv = 1.f / fmaf(bt, fmaf(sx, sx, fmaf(sy, sy, sz * sz)), eb);
+        const float f = beb * sr;
+        Es[(0 * ct + col) * LZ + kz] = Tr::cvt(fmaf(f, sx, r0) * inv);
+        Es[(1 * ct + col) * LZ + kz] = Tr::cvt(fmaf(f, sy, r1) * inv);
+        Es[(2 * ct + col) * LZ + kz] = Tr::cvt(fmaf(f, sz, r2) * inv);
+    }
+    __syncthreads();
+    E* out = reinterpret_cast<E*>(scr_v) + B.scr_off;
+    const int oz0 = B.own_lo[2], oz1 = B.own_lo[2] + B.own_n[2];
+    const int mlo = oz0 / 16 * 16, mhi = rup(oz1, 16);
+    for (int cc = 0; cc < 3; ++cc) {
+        const E* Tt = cc == 2 ? TCt : TSt;
+        warp_gemm<Tr>(Tt, LZ, Es + cc * ct * LZ, LZ, mlo, mhi, ct, MZ, [&](int z, int col, float v) {
+            if (z >= oz0 && z < oz1 && col < ncol) out[((long long)cc * mz + z) * nxy + col0 + col] = Tr::cvt(v);
+        });
+    }
+}
+
+// ---- pass C: inverse y and x of one owned z-slab, scatter owned cells -
+template <class Tr>
+__global__ void __launch_bounds__(kT)
+k_mp_inv_xy(const void* __restrict__ scr_v, double* __restrict__ zout, const FmpBox* __restrict__ boxes,
+            const int4* __restrict__ items, const void* __restrict__ tabs, const double* __restrict__ bscale, int nx,
+            int ny, int nz, const double* __restrict__ gate) {
+    using E = typename Tr::E;
+    if (gate && *gate != 0.0) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int4 it = items[blockIdx.x];
+    const FmpBox B = boxes[it.x];
+    const int c = it.y, zl = it.z;
+    const int mx = B.m[0], my = B.m[1], mz = B.m[2];
+    const int MX = rup(mx, 16), MY = rup(my, 16);
+    const int LX = MX + kPad, LY = MY + kPad;
+    const int oy0 = B.own_lo[1], ony = B.own_n[1], ox0 = B.own_lo[0], onx = B.own_n[0];
+    E* St = reinterpret_cast<E*>(smraw);   // [MX][LY]  S^T[kx][ky]
+    E* TYt = St + MX * LY;                 // [MY][LY]  T_y^T[y][ky]
+    E* Qs = TYt + MY * LY;                 // [MY][LX]  Q[y][kx]
+    E* TXt = Qs + MY * LX;                 // [MX][LX]  T_x^T[x][kx]
+    const bool sx = c != 0, sy = c != 1;
+    stage_table(TYt, LY, mp_table<E>(tabs, (sy ? B.mps_off[1] : B.mpc_off[1]) + MY * MY), MY, MY);
+    stage_table(TXt, LX, mp_table<E>(tabs, (sx ? B.mps_off[0] : B.mpc_off[0]) + MX * MX), MX, MX);
+    const E* src = reinterpret_cast<const E*>(scr_v) + B.scr_off + ((long long)c * mz + zl) * mx * my;
+    for (int t = threadIdx.x; t < MX * LY; t += blockDim.x) {
+        const int kx = t / LY, ky = t - kx * LY;
+        St[t] = (kx < mx && ky < my) ? src[ky * mx + kx] : Tr::cvt(0.f);
+    }
+    for (int t = threadIdx.x; t < MY * LX; t += blockDim.x) Qs[t] = Tr::cvt(0.f);
+    __syncthreads();
+    // Q[y][kx] = sum_ky T_y^T[y][ky] S[ky][kx], owned rows only
+    const int ylo = oy0 / 16 * 16, yhi = rup(oy0 + ony, 16);
+    warp_gemm<Tr>(TYt, LY, St, LY, ylo, yhi, rup(mx, 8), MY,
+                  [&](int y, int kx, float v) { if (kx < mx) Qs[y * LX + kx] = Tr::cvt(v); });
+    __syncthreads();
+    // out[y][x] = sum_kx Q[y][kx] T_x^T[x][kx]
+    const double s = bscale ? bscale[it.x] : 1.0;
+    const int gk = B.ext_lo[2] + zl;
+    double* dst = zout + (((long long)c * nz + gk) * ny + B.ext_lo[1]) * (long long)nx + B.ext_lo[0];
+    warp_gemm<Tr>(Qs, LX, TXt, LX, ylo, yhi, rup(mx, 8), MX, [&](int y, int x, float v) {
+        if (y >= oy0 && y < oy0 + ony && x >= ox0 && x < ox0 + onx) dst[(long long)y * nx + x] = (double)v * s;
+    });
+}
+
+// ---- fp16 scale: largest |r| over each extended box ---------------------
+__global__ void k_mp_boxmax(const double* __restrict__ r, const FmpBox* __restrict__ boxes, double* __restrict__ out,
+                            int nx, int ny, int nz, const double* __restrict__ gate) {
+    if (gate && *gate != 0.0) return;
+    const FmpBox B = boxes[blockIdx.x];
+    const int mx = B.m[0], my = B.m[1], mz = B.m[2];
+    const long long nb = (long long)mx * my * mz;
+    double m = 0.0;
+    for (long long t = threadIdx.x; t < 3 * nb; t += blockDim.x) {
+        const int c = (int)(t / nb);
+        long long q = t - c * nb;
+        const int k = (int)(q / (mx * my));
+        q -= (long long)k * mx * my;
+        const int j = (int)(q / mx), i = (int)(q - (long long)j * mx);
+        m = fmax(m, fabs(r[(((long long)c * nz + B.ext_lo[2] + k) * ny + B.ext_lo[1] + j) * (long long)nx +
+                           B.ext_lo[0] + i]));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmax(v, red[w]);
+        out[blockIdx.x] = (v > 0.0 && isfinite(v)) ? v : 1.0;
+    }
+}
+
+template <class E>
+size_t smem_mp_a(const int* m) {
+    const int MX = rup(m[0], 16), MY = rup(m[1], 16), LX = MX + kPad, LY = MY + kPad;
+    return sizeof(E) * (MY * LX + MX * LX + MX * LY + MY * LY);
+}
+template <class E>
+size_t smem_mp_c(const int* m) { return smem_mp_a<E>(m); }
+template <class E>
+size_t smem_mp_b(const int* m, int ct) {
+    const int MZ = rup(m[2], 16), LZ = MZ + kPad;
+    return sizeof(E) * (6 * ct * LZ + 4 * MZ * LZ) + sizeof(float) * 3 * MZ * ct;
+}
+
+template <class Tr>
+cudaError_t init_mp(const FmpPlan& p, int ct) {
+    using E = typename Tr::E;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_mp_fwd_xy<Tr>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_mp_a<E>(p.max_m))))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_mp_z_solve<Tr>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_mp_b<E>(p.max_m, ct))))
+        return e;
+    return cudaFuncSetAttribute(k_mp_inv_xy<Tr>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_mp_c<E>(p.max_m));
+}
+
+template <class Tr>
+cudaError_t launch_mp(const FmpPlan& p, const void* tabs, const double* tabs64, const double* r, double* z,
+                      void* scratch, double* bscale, int nx, int ny, int nz, double beta, int ct, cudaStream_t s,
+                      const double* gate) {
+    using E = typename Tr::E;
+    if (bscale) k_mp_boxmax<<<p.n_boxes, 256, 0, s>>>(r, p.d_boxes, bscale, nx, ny, nz, gate);
+    k_mp_fwd_xy<Tr><<<p.n_items_a, kT, smem_mp_a<E>(p.max_m), s>>>(r, scratch, p.d_boxes, p.d_items_a, tabs, bscale,
+                                                                   nx, ny, nz, gate);
+    k_mp_z_solve<Tr><<<p.n_items_b, kT, smem_mp_b<E>(p.max_m, ct), s>>>(scratch, p.d_boxes, p.d_items_b, tabs,
+                                                                         tabs64, beta, ct, gate);
+    k_mp_inv_xy<Tr><<<p.n_items_c, kT, smem_mp_c<E>(p.max_m), s>>>(scratch, z, p.d_boxes, p.d_items_c, tabs, bscale,
+                                                                   nx, ny, nz, gate);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int fmp_column_tile(const int* max_m);
+
+cudaError_t fmp_transform_init_mixed(const FmpPlan& p) {
+    const int ct = fmp_column_tile(p.max_m);
+    cudaError_t e;
+    if ((e = init_mp<BF16T>(p, ct))) return e;
+    if ((e = init_mp<FP16T>(p, ct))) return e;
+    return init_mp<TF32T>(p, ct);
+}
+
+cudaError_t fmp_launch_transform_solve_mixed(int precision, const FmpPlan& p, const void* tabs, const double* tabs64,
+                                             const double* r, double* z, void* scratch, double* bscale, int nx,
+                                             int ny, int nz, double beta, cudaStream_t s, const double* gate) {
+    const int ct = fmp_column_tile(p.max_m);
+    switch (precision) {
+        case FMP_PREC_BF16:
+            return launch_mp<BF16T>(p, tabs, tabs64, r, z, scratch, nullptr, nx, ny, nz, beta, ct, s, gate);
+        case FMP_PREC_FP16:
+            return launch_mp<FP16T>(p, tabs, tabs64, r, z, scratch, bscale, nx, ny, nz, beta, ct, s, gate);
+        case FMP_PREC_TF32:
+            return launch_mp<TF32T>(p, tabs, tabs64, r, z, scratch, nullptr, nx, ny, nz, beta, ct, s, gate);
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+// Host-side tables for the reduced-precision kernels: for each extent m and
+// each of DCT-II / DST-I, T and T^T zero padded to [Mp][Mp] (Mp = round up to
+// 16), converted to the element type; offsets in elements of that type.
+int fmp_mp_table_len(int m) { const int M = rup(m, 16); return 2 * 2 * M * M; }

@@ -24,6 +24,8 @@ struct FmpBox {
     int sig_off[3];    // offset of the m singular values of axis a in tabs
     int dctf_off[3];   // folded DCT-II table of axis a (see FoldDims)
     int dstf_off[3];   // folded DST-I table of axis a
+    int mpc_off[3];    // reduced-precision DCT-II T and T^T (padded to 16) of axis a
+    int mps_off[3];    // reduced-precision DST-I T and T^T of axis a
     long long scr_off; // offset (doubles) of the box's [3][mz][my][mx] scratch
     double eps_bar;    // subdomain-mean edge permittivity
 };
@@ -86,6 +88,8 @@ struct fmp_ctx {
     int single_box = -1;          // box index the single plan was built for
     double* d_scratch = nullptr;  // transform scratch for the RAS plan
     double* d_scratch1 = nullptr; // scratch for one box (fmp_box_solve)
+    void* d_tab_mp[3] = {};       // reduced-precision tables: bf16, fp16, tf32 (same layout)
+    double* d_bscale = nullptr;   // per-box scale factors (fp16 transforms)
 
     // Krylov workspace (allocated on first solve)
     int kry_restart = 0;
@@ -127,6 +131,11 @@ cudaError_t fmp_launch_cn_rhs(const double* E, const double* H, const double* J,
                               int ny, int nz, cudaStream_t s);
 cudaError_t fmp_launch_h_update(double* H, const double* En, const double* Eo, double dt,
                                 int nx, int ny, int nz, cudaStream_t s);
+
+cudaError_t fmp_transform_init_mixed(const FmpPlan& p);
+cudaError_t fmp_launch_transform_solve_mixed(int precision, const FmpPlan& p, const void* tabs, const double* tabs64,
+                                             const double* r, double* z, void* scratch, double* bscale, int nx,
+                                             int ny, int nz, double beta, cudaStream_t s, const double* gate);
 
 // Krylov building blocks (krylov.cu)
 int fmp_fgmres(fmp_ctx* c, const double* b, double* x, fmp_solve_info* info);

@@ -1,0 +1,71 @@
+"""Reduced-precision transforms inside the preconditioner (bf16 / fp16 / tf32
+tensor-core GEMMs, fp32 accumulation and 3x3) against the float64 oracle, and
+float64 FGMRES with them converging to the same true residual."""
+import numpy as np
+import pytest
+
+from oracle import ras, yee
+from paper_2508_07193_b300 import workloads as wl
+from tests._gpu import context, dev, host, rel
+
+pytestmark = pytest.mark.gpu
+
+# relative 2-norm error of M^{-1} r against the float64 oracle; each bound
+# is a few times the unit roundoff of the input type (bf16 2^-9, fp16 and
+# tf32 2^-12) accumulated over six rounded GEMM stages
+BOUND = {"bf16": 3e-2, "fp16": 5e-3, "tf32": 5e-3}
+
+CASES = [
+    wl.small(),
+    wl.small(grid=(33, 17, 9), cuts=((11, 11, 11), (17,), (4, 5)), overlap=1, seed=21, n_eps_boxes=5),
+    wl.small(grid=(24, 24, 24), cuts=((8, 8, 8),) * 3, overlap=3, seed=22, n_eps_boxes=6),
+]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "tf32"])
+@pytest.mark.parametrize("w", CASES, ids=lambda w: "x".join(map(str, w.grid)))
+def test_mixed_precond_error(prec, w):
+    ctx = context(w, precision=prec)
+    ee = yee.edge_eps(w.grid, w.eps_cell)
+    ref = ras.precond_apply(w.rhs, ras.partition(w.grid, w.cuts, w.overlap), ee, w.beta)
+    z = host(ctx.precond_apply(dev(w.rhs)))
+    err = rel(z, ref)
+    assert err <= BOUND[prec], err
+    assert np.all(z[wl.edge_wall_mask(w.grid)] == 0.0)
+    # linear in r: scaling the input by 1e-6 scales the output (fp16 uses a per-box scale)
+    z2 = host(ctx.precond_apply(dev(w.rhs * 1e-6)))
+    assert rel(z2 * 1e6, ref) <= BOUND[prec]
+
+
+def test_mixed_precond_128_sampled_boxes():
+    from oracle import box
+    w = wl.grid128()
+    ee = yee.edge_eps(w.grid, w.eps_cell)
+    boxes = ras.partition(w.grid, w.cuts, w.overlap)
+    for prec in ("bf16", "fp16", "tf32"):
+        ctx = context(w, precision=prec)
+        z = host(ctx.precond_apply(dev(w.rhs)))
+        for i in (0, 42, 63):
+            b = boxes[i]
+            eb = box.exact_solve(ras.restrict(w.rhs, b), ras.eps_bar(ee, b), w.beta)
+            part = np.zeros_like(w.rhs)
+            ras.prolong_owned(part, eb, b)
+            (x0, y0, z0), (x1, y1, z1) = b.own_lo, b.own_hi
+            sl = (slice(None), slice(z0, z1), slice(y0, y1), slice(x0, x1))
+            assert rel(z[sl], part[sl]) <= BOUND[prec]
+        ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "tf32"])
+def test_fgmres_with_mixed_precond_reaches_fp64_residual(prec):
+    w = wl.small(grid=(24, 24, 24), cuts=((8, 8, 8),) * 3, overlap=2, seed=22, n_eps_boxes=6)
+    ctx = context(w, precision=prec, rtol=1e-10)
+    x, info = ctx.krylov_solve(dev(w.rhs))
+    ee = yee.edge_eps(w.grid, w.eps_cell)
+    A = yee.system_matrix(w.grid, ee, w.beta)
+    b = w.rhs.reshape(-1)
+    true = np.linalg.norm(b - A @ host(x).reshape(-1)) / np.linalg.norm(b)
+    assert true <= 1e-10
+    ctx64 = context(w, rtol=1e-10)
+    _, i64 = ctx64.krylov_solve(dev(w.rhs))
+    assert info["iters"] <= i64["iters"] + 3
