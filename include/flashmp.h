@@ -93,7 +93,8 @@ typedef struct fmp_options {
     double rtol;      /* stop when ||b - A x||_2 / ||b||_2 <= rtol (1e-8)      */
     int max_iters;    /* cap on preconditioner applications (default 1000)     */
     int use_graph;    /* 1: replay the Arnoldi step as a CUDA graph            */
-    int use_learned;  /* reserved, must be 0                                   */
+    int use_learned;  /* 0 off; 1 learned initial guess in fmp_cn_step; 2 also a
+                         learned correction inside FGMRES (see fmp_cnn_*)       */
     int timing;       /* 1: fill the ms_* phase times (adds synchronisation)   */
 } fmp_options;
 
@@ -103,7 +104,7 @@ typedef struct fmp_solve_info {
     double true_rel_res;   /* ||b - A x||_2 / ||b||_2 recomputed in float64    */
     double est_rel_res;    /* last Krylov residual estimate                    */
     float ms_precond, ms_spmv, ms_orth, ms_total; /* phase times if timing=1 */
-    int used_fallback;     /* reserved                                         */
+    int used_fallback;     /* 1: the learned initial guess was rejected        */
     int status;            /* fmp_status of the solve                          */
 } fmp_solve_info;
 
@@ -204,6 +205,49 @@ int fmp_h_update(fmp_ctx* ctx, double* H, const double* E_new,
  * current at t^{n+1/2} or NULL. info as in fmp_krylov_solve. */
 int fmp_cn_step(fmp_ctx* ctx, double* E, double* H, const double* J, double dt,
                 fmp_solve_info* info);
+
+/* ---- Learned initial guess / coarse correction (not in the paper) -------
+ * A 3-D CNN N (4 conv layers, 3x3x3 kernels, channels 4 -> 16 -> 16 -> 16 -> 3,
+ * ReLU between layers, bf16 tensor-core convolutions with fp32 accumulation)
+ * maps a residual r to an approximate correction A^{-1} r. The input at voxel
+ * (k,j,i) is (r_x, r_y, r_z)(k,j,i) / s and eps_cell(k,j,i) / 10, with
+ * s = sqrt(mean r^2); the output is multiplied by s. Parameters are float32,
+ * per layer W[co][ci][3][3][3] then b[co], layers in order. With
+ * fmp_options.use_learned = 1 fmp_cn_step starts the solve from
+ * E^n + N(R - A E^n) when that lowers the residual (else from E^n, reported
+ * as used_fallback = 1); with use_learned = 2 FGMRES also adds
+ * N(v - A M^{-1} v) to every preconditioner output. The network is created
+ * (Kaiming-uniform, fixed seed) on first use. */
+
+/* Number of float32 parameters of the network. */
+int fmp_cnn_num_params(void);
+
+/* Copy parameters from / to HOST memory (fmp_cnn_num_params() floats). Setting
+ * them resets the Adam state. */
+int fmp_cnn_set_params(fmp_ctx* ctx, const float* params);
+int fmp_cnn_get_params(fmp_ctx* ctx, float* params);
+
+/* out = N(r) over the full grid (DEVICE edge fields, no aliasing; wall slots
+ * of out are 0). */
+int fmp_cnn_apply(fmp_ctx* ctx, const double* r, double* out);
+
+/* Append one training pair to the device pool: input r (a residual) and
+ * target correction e (DEVICE edge fields), stored normalised by s = rms(r). */
+int fmp_cnn_add_sample(fmp_ctx* ctx, const double* r, const double* e);
+int fmp_cnn_num_samples(fmp_ctx* ctx, int* n);
+int fmp_cnn_clear_samples(fmp_ctx* ctx);
+
+/* Loss ||N(x) - t||^2 / ||t||^2 on the crop [lo, lo + crop)^3 (lo: HOST int[3],
+ * x, y, z) of pool sample `sample`, and its gradient with respect to every
+ * parameter into HOST grads (may be NULL); no update. */
+int fmp_cnn_grad(fmp_ctx* ctx, int sample, const int* lo, int crop, float* grads,
+                 double* loss);
+
+/* `steps` Adam steps (lr, beta1 0.9, beta2 0.999) on random crop^3 crops of
+ * random pool samples, drawn around each sample's significant residual;
+ * *last_loss (may be NULL) receives the mean loss of the last 8 steps. */
+int fmp_cnn_train(fmp_ctx* ctx, int steps, int crop, float lr,
+                  unsigned long long seed, double* last_loss);
 
 /* Allocation-free exact solve of one PEC box. The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc, such as

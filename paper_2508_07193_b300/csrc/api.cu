@@ -201,7 +201,7 @@ static int check_options(const fmp_options* o) {
     if (o->krylov != FMP_KRYLOV_FGMRES && o->krylov != FMP_KRYLOV_BICGSTAB) return FMP_ERR_ARG;
     if (o->restart < 1 || o->restart > FMP_MAX_RESTART) return FMP_ERR_ARG;
     if (!(o->rtol > 0.0) || o->max_iters < 1) return FMP_ERR_ARG;
-    if (o->use_learned != 0) return FMP_ERR_UNSUPPORTED;
+    if (o->use_learned < 0 || o->use_learned > 2) return FMP_ERR_ARG;
     return FMP_OK;
 }
 
@@ -340,6 +340,11 @@ int fmp_setup(fmp_ctx** out, fmp_grid g, const double* eps_cell, double beta, co
     }
     c->tab_len = tabs.size();
     SETUP_CK(cudaMalloc(&c->d_eps_edge, sizeof(double) * c->n_slots));
+    if (eps_cell) {
+        SETUP_CK(cudaMalloc(&c->d_eps_cell, sizeof(double) * (c->n_slots / 3)));
+        SETUP_CK(cudaMemcpyAsync(c->d_eps_cell, eps_cell, sizeof(double) * (c->n_slots / 3), cudaMemcpyDeviceToDevice,
+                                 c->stream));
+    }
     SETUP_CK(fmp_launch_eps_edge(eps_cell, c->d_eps_edge, g.nx, g.ny, g.nz, c->stream));
     SETUP_CK(make_plan(c->ras, boxes, c->stream));
     SETUP_CK(fmp_transform_init_fp64(c->ras));
@@ -376,6 +381,9 @@ void fmp_destroy(fmp_ctx* c) {
     cudaFree(c->d_partials); cudaFree(c->d_state); cudaFree(c->d_ticket);
     for (int t = 0; t < 3; ++t) cudaFree(c->d_tab_mp[t]);
     cudaFree(c->d_bscale);
+    cudaFree(c->d_eps_cell);
+    cudaFree(c->d_tmp3);
+    fmp_cnn_free(c);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
@@ -501,7 +509,30 @@ int fmp_cn_step(fmp_ctx* c, double* E, double* H, const double* J, double dt, fm
     c->launches += 2;   // rhs + H update
     FMP_CK(fmp_launch_cn_rhs(E, H, J, c->d_eps_edge, c->beta, dt, R, c->nx, c->ny, c->nz, c->stream));
     FMP_CK(cudaMemcpyAsync(Eold, E, sizeof(double) * c->n_slots, cudaMemcpyDeviceToDevice, c->stream));
+    int fallback = 0;
+    if (c->opt.use_learned >= 1) {
+        // learned initial guess x0 = E^n + N(R - A E^n), kept only if it lowers the residual
+        FMP_CK(fmp_ensure_krylov(c));
+        if (!c->d_tmp3) FMP_CK(cudaMalloc(&c->d_tmp3, sizeof(double) * c->n_slots));
+        FMP_CK(fmp_cnn_create(c));
+        cudaError_t err;
+        c->launches += 2;
+        FMP_CK(fmp_launch_curlcurl(E, c->d_eps_edge, c->d_tmp3, -1.0, -c->beta, c->nx, c->ny, c->nz, c->stream,
+                                   nullptr, R, 1.0));
+        const double n0 = fmp_norm(c, c->d_tmp3, &err);
+        FMP_CK(err);
+        FMP_CK(fmp_cnn_apply_dev(c, c->d_tmp3, E, 1.0, 1));
+        FMP_CK(fmp_launch_curlcurl(E, c->d_eps_edge, c->d_tmp3, -1.0, -c->beta, c->nx, c->ny, c->nz, c->stream,
+                                   nullptr, R, 1.0));
+        const double n1 = fmp_norm(c, c->d_tmp3, &err);
+        FMP_CK(err);
+        if (!(n1 < n0)) {   // includes NaN: revert to the plain guess
+            FMP_CK(cudaMemcpyAsync(E, Eold, sizeof(double) * c->n_slots, cudaMemcpyDeviceToDevice, c->stream));
+            fallback = 1;
+        }
+    }
     int rc = fmp_krylov_solve(c, R, E, info);
+    if (info) info->used_fallback = fallback;
     if (rc != FMP_OK && rc != FMP_ERR_NOT_CONVERGED) return rc;
     FMP_CK(fmp_launch_h_update(H, E, Eold, dt, c->nx, c->ny, c->nz, c->stream));
     return rc;

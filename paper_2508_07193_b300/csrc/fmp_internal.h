@@ -70,6 +70,8 @@ struct FmpPlan {
     long long scratch_doubles = 0;
 };
 
+struct FmpCnn;
+
 struct fmp_ctx {
     int nx = 0, ny = 0, nz = 0;
     size_t n_slots = 0;           // 3 * nx * ny * nz
@@ -90,6 +92,9 @@ struct fmp_ctx {
     double* d_scratch1 = nullptr; // scratch for one box (fmp_box_solve)
     void* d_tab_mp[3] = {};       // reduced-precision tables: bf16, fp16, tf32 (same layout)
     double* d_bscale = nullptr;   // per-box scale factors (fp16 transforms)
+    double* d_eps_cell = nullptr; // cell permittivity [nz][ny][nx] (null: eps = 1)
+    FmpCnn* cnn = nullptr;        // learned initial guess / correction (created on first use)
+    double* d_tmp3 = nullptr;     // third field-sized scratch (learned paths)
 
     // Krylov workspace (allocated on first solve)
     int kry_restart = 0;
@@ -144,6 +149,13 @@ int fmp_precond(fmp_ctx* c, const double* r, double* z);
 int fmp_precond_gated(fmp_ctx* c, const double* r, double* z, const double* gate);
 cudaError_t fmp_ensure_krylov(fmp_ctx* c);
 cudaError_t fmp_krylov_init();
+double fmp_norm(fmp_ctx* c, const double* v, cudaError_t* err);   // ||v||_2, synchronises
+
+// learned component (cnn.cu)
+cudaError_t fmp_cnn_create(fmp_ctx* c);
+void fmp_cnn_free(fmp_ctx* c);
+// out = (accumulate ? out : 0) + alpha * N(r) on the full grid
+cudaError_t fmp_cnn_apply_dev(fmp_ctx* c, const double* r, double* out, double alpha, int accumulate);
 
 #define FMP_CK(expr)                                                   \
     do {                                                               \

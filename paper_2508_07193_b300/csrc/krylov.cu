@@ -526,6 +526,22 @@ cudaError_t residual(fmp_ctx* c, const double* b, const double* x, double* r) {
     return fmp_launch_curlcurl(x, c->d_eps_edge, r, -1.0, -c->beta, c->nx, c->ny, c->nz, c->stream, nullptr, b, 1.0);
 }
 
+}  // namespace
+
+double fmp_norm(fmp_ctx* c, const double* v, cudaError_t* err) {
+    const St L = st_layout(c->kry_restart > 0 ? c->kry_restart : 1);
+    double* slot = c->d_state ? c->d_state + L.sc + SC_D4 : nullptr;
+    if (!slot) { *err = cudaErrorInvalidValue; return 0.0; }
+    ++c->launches;
+    *err = norm2(c, v, slot);
+    if (*err) return 0.0;
+    *err = cudaMemcpyAsync(c->h_pinned + 40, slot, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (!*err) *err = cudaStreamSynchronize(c->stream);
+    return std::sqrt(c->h_pinned[40]);
+}
+
+namespace {
+
 // Enqueue Arnoldi step j; every kernel is gated on the device 'done' flag.
 int arnoldi_step(fmp_ctx* c, int j, fmp_solve_info* inf) {
     const int R = c->kry_restart;
@@ -670,7 +686,7 @@ int fmp_fgmres(fmp_ctx* c, const double* b, double* x, fmp_solve_info* info) {
         ++c->launches;
         k_scale_first<<<grid_n(n), kT, 0, s>>>(V, n, st, R);
         FMP_CK(cudaGetLastError());
-        if (c->opt.use_graph && !c->opt.timing) {
+        if (c->opt.use_graph && !c->opt.timing && c->opt.use_learned < 2) {
             int rc = run_cycle_graph(c);
             if (rc != FMP_OK) return rc;
         } else {

@@ -91,6 +91,15 @@ def lib():
         "fmp_cn_rhs": (_I, [_P, _P, _P, _P, _D, _P]),
         "fmp_h_update": (_I, [_P, _P, _P, _P, _D]),
         "fmp_cn_step": (_I, [_P, _P, _P, _P, _D, C.POINTER(SolveInfo)]),
+        "fmp_cnn_num_params": (_I, []),
+        "fmp_cnn_set_params": (_I, [_P, _P]),
+        "fmp_cnn_get_params": (_I, [_P, _P]),
+        "fmp_cnn_apply": (_I, [_P, _P, _P]),
+        "fmp_cnn_add_sample": (_I, [_P, _P, _P]),
+        "fmp_cnn_num_samples": (_I, [_P, C.POINTER(_I)]),
+        "fmp_cnn_clear_samples": (_I, [_P]),
+        "fmp_cnn_grad": (_I, [_P, _I, C.POINTER(_I), _I, _P, C.POINTER(_D)]),
+        "fmp_cnn_train": (_I, [_P, _I, _I, C.c_float, C.c_ulonglong, C.POINTER(_D)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -134,7 +143,7 @@ class Context:
 
     def __init__(self, grid, eps_cell=None, beta=0.25, cuts=None, overlap=0, *, precision="fp64",
                  krylov="fgmres", restart=30, rtol=1e-8, max_iters=1000, timing=False, use_graph=False,
-                 stream=None, device=None):
+                 use_learned=0, stream=None, device=None):
         L = lib()
         if not torch.cuda.is_available():
             raise RuntimeError("flashmp needs a CUDA device")
@@ -144,7 +153,7 @@ class Context:
         self.shape = (3, nz, ny, nx)
         self.beta = float(beta)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        o = self._options(precision, krylov, restart, rtol, max_iters, timing, use_graph)
+        o = self._options(precision, krylov, restart, rtol, max_iters, timing, use_graph, use_learned)
         sd = None
         self._cut_arrays = None
         if cuts is not None:
@@ -170,8 +179,9 @@ class Context:
         self._opts = o
 
     @staticmethod
-    def _options(precision, krylov, restart, rtol, max_iters, timing, use_graph):
+    def _options(precision, krylov, restart, rtol, max_iters, timing, use_graph, use_learned=0):
         o = default_options()
+        o.use_learned = int(use_learned)
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         o.krylov = KRYLOV[krylov] if isinstance(krylov, str) else int(krylov)
         o.restart = int(restart)
@@ -202,7 +212,7 @@ class Context:
     def set_options(self, **kw):
         cur = dict(precision=self._opts.precision, krylov=self._opts.krylov, restart=self._opts.restart,
                    rtol=self._opts.rtol, max_iters=self._opts.max_iters, timing=self._opts.timing,
-                   use_graph=self._opts.use_graph)
+                   use_graph=self._opts.use_graph, use_learned=self._opts.use_learned)
         cur.update(kw)
         o = self._options(**cur)
         _check(lib().fmp_set_options(self._h, C.byref(o)), "fmp_set_options")
@@ -291,3 +301,53 @@ class Context:
         if check:
             _check(rc, "fmp_cn_step")
         return info.as_dict()
+
+    # -- learned component --------------------------------------------------
+    def cnn_num_params(self):
+        return lib().fmp_cnn_num_params()
+
+    def cnn_set_params(self, params):
+        import numpy as np
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != self.cnn_num_params():
+            raise ValueError(f"expected {self.cnn_num_params()} parameters, got {p.size}")
+        _check(lib().fmp_cnn_set_params(self._h, p.ctypes.data_as(C.c_void_p)), "fmp_cnn_set_params")
+
+    def cnn_get_params(self):
+        import numpy as np
+        p = np.empty(self.cnn_num_params(), dtype=np.float32)
+        _check(lib().fmp_cnn_get_params(self._h, p.ctypes.data_as(C.c_void_p)), "fmp_cnn_get_params")
+        return p
+
+    def cnn_apply(self, r, out=None):
+        _field(r, self.shape, "r")
+        out = self.empty_field() if out is None else _field(out, self.shape, "out")
+        _check(lib().fmp_cnn_apply(self._h, _ptr(r), _ptr(out)), "fmp_cnn_apply")
+        return out
+
+    def cnn_add_sample(self, r, e):
+        _field(r, self.shape, "r"); _field(e, self.shape, "e")
+        _check(lib().fmp_cnn_add_sample(self._h, _ptr(r), _ptr(e)), "fmp_cnn_add_sample")
+
+    def cnn_num_samples(self):
+        n = C.c_int()
+        _check(lib().fmp_cnn_num_samples(self._h, C.byref(n)), "fmp_cnn_num_samples")
+        return n.value
+
+    def cnn_clear_samples(self):
+        _check(lib().fmp_cnn_clear_samples(self._h), "fmp_cnn_clear_samples")
+
+    def cnn_grad(self, sample, lo, crop):
+        import numpy as np
+        g = np.empty(self.cnn_num_params(), dtype=np.float32)
+        loss = C.c_double()
+        lo_a = (C.c_int * 3)(*[int(v) for v in lo])
+        _check(lib().fmp_cnn_grad(self._h, int(sample), lo_a, int(crop), g.ctypes.data_as(C.c_void_p),
+                                  C.byref(loss)), "fmp_cnn_grad")
+        return loss.value, g
+
+    def cnn_train(self, steps, crop, lr=1e-3, seed=0):
+        loss = C.c_double()
+        _check(lib().fmp_cnn_train(self._h, int(steps), int(crop), float(lr), int(seed), C.byref(loss)),
+               "fmp_cnn_train")
+        return loss.value

@@ -65,8 +65,10 @@ def test_setup_rejects_bad_arguments_before_touching_the_device(so):
     assert L.fmp_setup(C.byref(h), g, None, 0.25, C.byref(sd), None, None) == F.FMP_ERR_ARG
     o = F.default_options(); o.restart = 33
     assert L.fmp_setup(C.byref(h), g, None, 0.25, None, C.byref(o), None) == F.FMP_ERR_ARG
-    o = F.default_options(); o.use_learned = 1
-    assert L.fmp_setup(C.byref(h), g, None, 0.25, None, C.byref(o), None) == F.FMP_ERR_UNSUPPORTED
+    o = F.default_options(); o.use_learned = 3
+    assert L.fmp_setup(C.byref(h), g, None, 0.25, None, C.byref(o), None) == F.FMP_ERR_ARG
+    o = F.default_options(); o.precision = 9
+    assert L.fmp_setup(C.byref(h), g, None, 0.25, None, C.byref(o), None) == F.FMP_ERR_ARG
     assert h.value is None
     # null context
     assert L.fmp_precond_apply(None, None, None) == F.FMP_ERR_ARG
