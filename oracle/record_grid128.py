@@ -1,0 +1,40 @@
+"""Record the oracle's FGMRES(30) iteration count on the 128^3 workload.
+
+Test infrastructure: runs only the float64 CPU oracle (about two minutes on 8
+cores) and writes oracle/recorded/grid128_fgmres.json, which the CPU reference
+arm of the benchmark reads to scale its per-iteration timing to a full step.
+
+    python -m oracle.record_grid128
+"""
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+from oracle import krylov, ras, yee  # noqa: E402
+from paper_2508_07193_b300 import workloads as wl  # noqa: E402
+
+
+def main():
+    w = wl.grid128()
+    ee = yee.edge_eps(w.grid, w.eps_cell)
+    A = yee.system_matrix(w.grid, ee, w.beta)
+    boxes = ras.partition(w.grid, w.cuts, w.overlap)
+    shp = w.rhs.shape
+    M = lambda r: ras.precond_apply(r.reshape(shp), boxes, ee, w.beta).reshape(-1)
+    t0 = time.time()
+    x, info = krylov.fgmres(lambda v: A @ v, M, w.rhs.reshape(-1), restart=30, rtol=1e-8)
+    out = {"workload": w.name, "krylov": "FGMRES(30), modified Gram-Schmidt", "rtol": 1e-8,
+           "iters": info["iters"], "restarts": info["restarts"], "true_rel_res": info["true_rel_res"],
+           "seconds": time.time() - t0, "cores": os.cpu_count()}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "recorded", "grid128_fgmres.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -245,10 +245,13 @@ __global__ void k_cnn_output(const float* __restrict__ Y, const double* rms, dou
     }
 }
 
-// rms of an edge field into *out (one block).
-__global__ void k_rms(const double* __restrict__ r, long long n, double* out) {
+// rms of a vector into *out: per-block partial sums, then one block adds
+// them in block order (deterministic).
+constexpr int kRmsBlocks = 296;
+__global__ void k_rms_part(const double* __restrict__ r, long long n, double* __restrict__ part) {
     double s = 0.0;
-    for (long long e = threadIdx.x; e < n; e += blockDim.x) s = fma(r[e], r[e], s);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        s = fma(r[e], r[e], s);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     __shared__ double red[32];
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -256,6 +259,13 @@ __global__ void k_rms(const double* __restrict__ r, long long n, double* out) {
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        part[blockIdx.x] = t;
+    }
+}
+__global__ void k_rms_final(const double* __restrict__ part, int nb, long long n, double* out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double t = 0.0;
+        for (int b = 0; b < nb; ++b) t += part[b];
         *out = sqrt(t / (double)n);
     }
 }
@@ -352,7 +362,7 @@ struct FmpCnn {
     float* part = nullptr;     // weight-gradient partials
     size_t part_cap = 0;
     float* wtmp = nullptr;     // one layer's gradient in [co][tap][ci] order
-    double* scal = nullptr;    // [0] rms, [1..2] loss sums, [3] second rms
+    double* scal = nullptr;    // [0] rms, [1..2] loss sums, [8..] rms partials
     int* bbox = nullptr;       // device scratch for bounding boxes
     std::vector<bf16*> pool_x; // training inputs  [4][N] bf16
     std::vector<float*> pool_t;// training targets [3][N] fp32
@@ -516,7 +526,7 @@ cudaError_t fmp_cnn_create(fmp_ctx* c) {
         if ((e = cudaMalloc(&n->wt[l], sizeof(bf16) * b))) return e;
     }
     if ((e = cudaMalloc(&n->wtmp, sizeof(float) * (16 * 27 * 16 + 16)))) return e;
-    if ((e = cudaMalloc(&n->scal, sizeof(double) * 8))) return e;
+    if ((e = cudaMalloc(&n->scal, sizeof(double) * (8 + kRmsBlocks)))) return e;
     if ((e = cudaMalloc(&n->bbox, sizeof(int) * 8))) return e;
     // default initialisation: Kaiming-uniform weights, zero biases
     std::vector<float> h(np, 0.f);
@@ -553,11 +563,12 @@ cudaError_t fmp_cnn_apply_dev(fmp_ctx* c, const double* r, double* out, double a
     const Vol v{c->nz, c->ny, c->nx};
     cudaError_t e;
     if ((e = ensure_vol(n, v.n()))) return e;
-    k_rms<<<1, 1024, 0, c->stream>>>(r, (long long)c->n_slots, n->scal);
+    k_rms_part<<<kRmsBlocks, 256, 0, c->stream>>>(r, (long long)c->n_slots, n->scal + 8);
+    k_rms_final<<<1, 32, 0, c->stream>>>(n->scal + 8, kRmsBlocks, (long long)c->n_slots, n->scal);
     k_cnn_input<<<grid1(v.n()), 256, 0, c->stream>>>(r, c->d_eps_cell, n->scal, n->x0, c->nx, c->ny, c->nz, 0, 0, 0, v);
     if ((e = net_forward(n, v, c->stream))) return e;
     k_cnn_output<<<grid1(3 * v.n()), 256, 0, c->stream>>>(n->out, n->scal, out, c->nx, c->ny, c->nz, alpha, accumulate);
-    c->launches += 7;
+    c->launches += 8;
     return cudaGetLastError();
 }
 
@@ -609,7 +620,8 @@ int fmp_cnn_add_sample(fmp_ctx* c, const double* r, const double* e_corr) {
     if (cudaError_t e = cudaMalloc(&t, sizeof(float) * 3 * v.n())) { cudaFree(x); return fmp_latch(c, e); }
     n->pool_x.push_back(x);
     n->pool_t.push_back(t);
-    k_rms<<<1, 1024, 0, c->stream>>>(r, (long long)c->n_slots, n->scal);
+    k_rms_part<<<kRmsBlocks, 256, 0, c->stream>>>(r, (long long)c->n_slots, n->scal + 8);
+    k_rms_final<<<1, 32, 0, c->stream>>>(n->scal + 8, kRmsBlocks, (long long)c->n_slots, n->scal);
     k_cnn_input<<<grid1(v.n()), 256, 0, c->stream>>>(r, c->d_eps_cell, n->scal, x, c->nx, c->ny, c->nz, 0, 0, 0, v);
     k_cnn_target<<<grid1(3 * v.n()), 256, 0, c->stream>>>(e_corr, n->scal, t, 3 * v.n());
     const int init[8] = {c->nx, c->ny, c->nz, -1, -1, -1, 0, 0};

@@ -1,0 +1,53 @@
+"""Time stepping with the learned component (small dipole run) and
+checkpoint / resume continuing bit for bit."""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2508_07193_b300 import cn_driver as D
+from paper_2508_07193_b300 import flashmp as F
+
+pytestmark = pytest.mark.gpu
+
+
+def test_dipole_run_plain_and_learned_converge(tmp_path):
+    class A:
+        grid, steps, train_until, train_iters, crop, lr, seed = 32, 10, 5, 40, 12, 2e-3, 0
+        precision, rtol, learned_mode = "bf16", 1e-8, 1
+        checkpoint = str(tmp_path / "ck.pt")
+        resume = None
+        out = None
+    log = D.run(A)
+    assert len(log["phase1"]) == 5 and len(log["plain"]) == 5 and len(log["learned"]) == 5
+    assert log["plain_max_res"] <= 1e-8 and log["learned_max_res"] <= 1e-8
+    assert os.path.exists(A.checkpoint)
+
+
+def test_checkpoint_resume_is_bitwise():
+    w = D.dipole_workload(32)
+    dt = 2.0 * math.sqrt(w.beta)
+    dev = torch.device("cuda", 0)
+
+    def make():
+        return F.Context(w.grid, w.eps_cell, w.beta, w.cuts, w.overlap, precision="fp64", rtol=1e-10)
+
+    ctx = make()
+    E, H = ctx.empty_field(), ctx.empty_field()
+    for n in range(6):
+        ctx.cn_step(E, H, D.current(w, n + 40, dt, dev), dt)
+    ref = (E.cpu().numpy().copy(), H.cpu().numpy().copy())
+    ctx.close()
+    ctx = make()
+    E, H = ctx.empty_field(), ctx.empty_field()
+    for n in range(3):
+        ctx.cn_step(E, H, D.current(w, n + 40, dt, dev), dt)
+    state = {"E": E.cpu(), "H": H.cpu(), "step": 3}
+    ctx.close()
+    ctx = make()
+    E, H = state["E"].to(dev), state["H"].to(dev)
+    for n in range(state["step"], 6):
+        ctx.cn_step(E, H, D.current(w, n + 40, dt, dev), dt)
+    assert np.array_equal(E.cpu().numpy(), ref[0]) and np.array_equal(H.cpu().numpy(), ref[1])

@@ -71,9 +71,12 @@ def test_grid128_solve_true_residual():
     A = yee.system_matrix(w.grid, ee, w.beta)
     b = w.rhs.reshape(-1)
     true = np.linalg.norm(b - A @ host(x).reshape(-1)) / np.linalg.norm(b)
-    # 63 Arnoldi steps were measured for this workload: eps varies 1..10 inside
-    # boxes while the subdomain solves use one mean coefficient per box
-    assert true <= 1e-8 and info["iters"] <= 80
+    # the oracle's own FGMRES(30) on this workload, recorded by
+    # oracle/record_grid128.py: same iteration count within 2, same residual
+    import json, os
+    rec = json.load(open(os.path.join(os.path.dirname(__file__), "..", "oracle", "recorded", "grid128_fgmres.json")))
+    assert true <= 1e-8 and abs(info["iters"] - rec["iters"]) <= 2
+    assert true == pytest.approx(rec["true_rel_res"], rel=1e-3)
 
 
 def test_cn_steps_match_oracle_and_conserve_energy():
