@@ -122,18 +122,37 @@ cudaError_t make_plan(FmpPlan& p, const std::vector<FmpBox>& boxes, cudaStream_t
     p.scratch_doubles = scr;
     std::vector<int4> A, C;
     std::vector<int2> B;
-    build_items(boxes, fmp_column_tile(p.max_m), A, B, C);
+    const int ct = fmp_column_tile(p.max_m);
+    build_items(boxes, ct, A, B, C);
     p.n_items_a = (int)A.size(); p.n_items_b = (int)B.size(); p.n_items_c = (int)C.size();
+    std::vector<int4> GA, GB, GC;
+    for (int b = 0; b < (int)boxes.size(); ++b) {
+        const FmpBox& x = boxes[b];
+        for (int c = 0; c < 3; ++c) {
+            for (int z = 0; z < x.m[2]; z += FMP_MP_SLAB_GROUP)
+                GA.push_back(make_int4(b, c, z, std::min(FMP_MP_SLAB_GROUP, x.m[2] - z)));
+            const int o0 = x.own_lo[2], o1 = x.own_lo[2] + x.own_n[2];
+            for (int z = o0; z < o1; z += FMP_MP_SLAB_GROUP)
+                GC.push_back(make_int4(b, c, z, std::min(FMP_MP_SLAB_GROUP, o1 - z)));
+        }
+        const int nxy = x.m[0] * x.m[1], span = ct * FMP_MP_TILE_GROUP;
+        for (int q = 0; q < nxy; q += span) GB.push_back(make_int4(b, q, std::min(span, nxy - q), 0));
+    }
+    p.n_items_ga = (int)GA.size(); p.n_items_gb = (int)GB.size(); p.n_items_gc = (int)GC.size();
     cudaError_t e;
     if ((e = upload(&p.d_boxes, boxes, s))) return e;
     if ((e = upload(&p.d_items_a, A, s))) return e;
     if ((e = upload(&p.d_items_b, B, s))) return e;
     if ((e = upload(&p.d_items_c, C, s))) return e;
+    if ((e = upload(&p.d_items_ga, GA, s))) return e;
+    if ((e = upload(&p.d_items_gb, GB, s))) return e;
+    if ((e = upload(&p.d_items_gc, GC, s))) return e;
     return cudaSuccess;
 }
 
 void free_plan(FmpPlan& p) {
     cudaFree(p.d_boxes); cudaFree(p.d_items_a); cudaFree(p.d_items_b); cudaFree(p.d_items_c);
+    cudaFree(p.d_items_ga); cudaFree(p.d_items_gb); cudaFree(p.d_items_gc);
     p = FmpPlan{};
 }
 

@@ -132,13 +132,21 @@ __device__ __forceinline__ void warp_gemm(const typename Tr::E* A, int lda, cons
 }
 
 // Copy a padded table [rows][Kp] (global, element type) into shared rows of
-// stride ld.
+// stride ld, in 16-byte chunks (row lengths and strides are multiples of 16 B).
 template <class E>
 __device__ __forceinline__ void stage_table(E* dst, int ld, const E* src, int rows, int Kp) {
-    for (int t = threadIdx.x; t < rows * Kp; t += blockDim.x) {
-        const int r = t / Kp, k = t - r * Kp;
-        dst[r * ld + k] = src[t];
+    const int cpr = Kp * (int)sizeof(E) / 16;   // chunks per row
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int r = warp; r < rows; r += kT / 32) {
+        const uint4* s4 = reinterpret_cast<const uint4*>(src + (size_t)r * Kp);
+        uint4* d4 = reinterpret_cast<uint4*>(dst + (size_t)r * ld);
+        for (int q = lane; q < cpr; q += 32) d4[q] = s4[q];
     }
+}
+
+template <class E>
+__device__ __forceinline__ void fill_zero(E* p, int n) {
+    for (int t = threadIdx.x; t < n; t += blockDim.x) p[t] = E(0.f);
 }
 
 __device__ __forceinline__ bool edge_wall(int c, int i, int j, int k) {
@@ -155,7 +163,7 @@ __device__ __forceinline__ const E* mp_table(const void* tabs, int off) {
     return reinterpret_cast<const E*>(tabs) + off;
 }
 
-// ---- pass A: gather, cast, x and y transforms of one z-slab ------------
+// ---- pass A: gather, cast, x and y transforms of a group of z-slabs -----
 template <class Tr>
 __global__ void __launch_bounds__(kT)
 k_mp_fwd_xy(const double* __restrict__ r, void* __restrict__ scr_v, const FmpBox* __restrict__ boxes,
@@ -166,11 +174,10 @@ k_mp_fwd_xy(const double* __restrict__ r, void* __restrict__ scr_v, const FmpBox
     extern __shared__ __align__(16) unsigned char smraw[];
     const int4 it = items[blockIdx.x];
     const FmpBox B = boxes[it.x];
-    const int c = it.y, kz = it.z;
+    const int c = it.y, z0 = it.z, zn = it.w;
     const int mx = B.m[0], my = B.m[1], mz = B.m[2];
     const int MX = rup(mx, 16), MY = rup(my, 16);
     const int LX = MX + kPad, LY = MY + kPad;
-    E* scr = reinterpret_cast<E*>(scr_v) + B.scr_off + ((long long)c * mz + kz) * mx * my;
     E* Xs = reinterpret_cast<E*>(smraw);   // [MY][LX]   slab, rows y
     E* TX = Xs + MY * LX;                  // [MX][LX]   T_x[kx][x]
     E* Pt = TX + MX * LX;                  // [MX][LY]   P^T[kx][y]
@@ -178,42 +185,54 @@ k_mp_fwd_xy(const double* __restrict__ r, void* __restrict__ scr_v, const FmpBox
     const bool sx = c != 0, sy = c != 1;
     stage_table(TX, LX, mp_table<E>(tabs, sx ? B.mps_off[0] : B.mpc_off[0]), MX, MX);
     stage_table(TY, LY, mp_table<E>(tabs, sy ? B.mps_off[1] : B.mpc_off[1]), MY, MY);
+    fill_zero(Pt, MX * LY);
     const float inv_s = bscale ? (float)(1.0 / bscale[it.x]) : 1.f;
-    const int gk = B.ext_lo[2] + kz;
-    const double* src = r + (((long long)c * nz + gk) * ny + B.ext_lo[1]) * (long long)nx + B.ext_lo[0];
-    for (int t = threadIdx.x; t < MY * LX; t += blockDim.x) {
-        const int j = t / LX, i = t - j * LX;
-        float v = 0.f;
-        if (i < mx && j < my && !edge_wall(c, i, j, kz)) v = (float)src[(long long)j * nx + i] * inv_s;
-        Xs[t] = Tr::cvt(v);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int NX8 = rup(mx, 8);
+    for (int kz = z0; kz < z0 + zn; ++kz) {
+        const int gk = B.ext_lo[2] + kz;
+        const double* src = r + (((long long)c * nz + gk) * ny + B.ext_lo[1]) * (long long)nx + B.ext_lo[0];
+        const bool zwall = (c != 2) && kz == 0;
+        for (int j = warp; j < MY; j += kT / 32) {
+            const bool rowok = j < my && !zwall && !(c == 0 && j == 0) && !(c == 2 && j == 0);
+            const double* srow = src + (long long)j * nx;
+            E* xrow = Xs + j * LX;
+            for (int i = lane; i < LX; i += 32) {
+                float v = 0.f;
+                if (rowok && i < mx && !(c != 0 && i == 0)) v = (float)srow[i] * inv_s;
+                xrow[i] = Tr::cvt(v);
+            }
+        }
+        __syncthreads();
+        // P[y][kx] = sum_x X[y][x] T_x[kx][x]  -> stored transposed
+        warp_gemm<Tr>(Xs, LX, TX, LX, 0, MY, NX8, MX,
+                      [&](int y, int kx, float v) { Pt[kx * LY + y] = Tr::cvt(v); });
+        __syncthreads();
+        // out[ky][kx] = sum_y T_y[ky][y] P[y][kx]
+        E* scr = reinterpret_cast<E*>(scr_v) + B.scr_off + ((long long)c * mz + kz) * mx * my;
+        warp_gemm<Tr>(TY, LY, Pt, LY, 0, MY, NX8, MY, [&](int ky, int kx, float v) {
+            if (ky < my && kx < mx) scr[ky * mx + kx] = Tr::cvt(v);
+        });
+        __syncthreads();
     }
-    for (int t = threadIdx.x; t < MX * LY; t += blockDim.x) Pt[t] = Tr::cvt(0.f);
-    __syncthreads();
-    // P[y][kx] = sum_x X[y][x] T_x[kx][x]  -> stored transposed
-    warp_gemm<Tr>(Xs, LX, TX, LX, 0, MY, rup(mx, 8), MX,
-                  [&](int y, int kx, float v) { Pt[kx * LY + y] = Tr::cvt(v); });
-    __syncthreads();
-    // out[ky][kx] = sum_y T_y[ky][y] P[y][kx]
-    warp_gemm<Tr>(TY, LY, Pt, LY, 0, MY, rup(mx, 8), MY, [&](int ky, int kx, float v) {
-        if (ky < my && kx < mx) scr[ky * mx + kx] = Tr::cvt(v);
-    });
 }
 
 // ---- pass B: z transform, 3x3 solve in fp32, inverse z (owned slabs) --
+// One CTA per group of column tiles of one box; the four z tables are staged
+// once and reused for every tile.
 template <class Tr>
 __global__ void __launch_bounds__(kT)
-k_mp_z_solve(void* __restrict__ scr_v, const FmpBox* __restrict__ boxes, const int2* __restrict__ items,
+k_mp_z_solve(void* __restrict__ scr_v, const FmpBox* __restrict__ boxes, const int4* __restrict__ items,
              const void* __restrict__ tabs, const double* __restrict__ tabs64, double beta, int ct,
              const double* __restrict__ gate) {
     using E = typename Tr::E;
     if (gate && *gate != 0.0) return;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int2 itb = items[blockIdx.x];
+    const int4 itb = items[blockIdx.x];
     const FmpBox B = boxes[itb.x];
-    const int col0 = itb.y;
+    const int gcol0 = itb.y, gcols = itb.z;
     const int mx = B.m[0], my = B.m[1], mz = B.m[2];
     const int nxy = mx * my;
-    const int ncol = min(ct, nxy - col0);
     const int MZ = rup(mz, 16), LZ = MZ + kPad;
     E* In = reinterpret_cast<E*>(smraw);   // [3][ct][LZ]  (col-major per component)
     E* Es = In + 3 * ct * LZ;              // [3][ct][LZ]  solved modes, col-major
@@ -226,51 +245,65 @@ k_mp_z_solve(void* __restrict__ scr_v, const FmpBox* __restrict__ boxes, const i
     stage_table(TS, LZ, mp_table<E>(tabs, B.mps_off[2]), MZ, MZ);
     stage_table(TCt, LZ, mp_table<E>(tabs, B.mpc_off[2] + MZ * MZ), MZ, MZ);
     stage_table(TSt, LZ, mp_table<E>(tabs, B.mps_off[2] + MZ * MZ), MZ, MZ);
-    const E* scr = reinterpret_cast<const E*>(scr_v) + B.scr_off;
-    for (int t = threadIdx.x; t < 3 * ct * LZ; t += blockDim.x) {
-        const int cc = t / (ct * LZ), rem = t - cc * ct * LZ;
-        const int col = rem / LZ, z = rem - col * LZ;
-        In[t] = (col < ncol && z < mz) ? scr[((long long)cc * mz + z) * nxy + col0 + col] : Tr::cvt(0.f);
-        Es[t] = Tr::cvt(0.f);
-    }
-    __syncthreads();
-    for (int cc = 0; cc < 3; ++cc) {
-        const E* T = cc == 2 ? TC : TS;
-        float* O = Of + cc * MZ * ct;
-        warp_gemm<Tr>(T, LZ, In + cc * ct * LZ, LZ, 0, MZ, ct, MZ, [&](int kz, int col, float v) { O[kz * ct + col] = v; });
-    }
-    __syncthreads();
+    fill_zero(In, 6 * ct * LZ);   // z padding of In and Es stays zero
     const double* sgx = tabs64 + B.sig_off[0];
     const double* sgy = tabs64 + B.sig_off[1];
     const double* sgz = tabs64 + B.sig_off[2];
     const float eb = (float)B.eps_bar, bt = (float)beta, beb = (float)(beta / B.eps_bar);
-    for (int t = threadIdx.x; t < mz * ct; t += blockDim.x) {
-        const int kz = t / ct, col = t - kz * ct;
-        if (col >= ncol) continue;
-        const int q = col0 + col;
-        const int ky = q / mx, kx = q - ky * mx;
-        const float sx = (float)sgx[kx], sy = (float)sgy[ky], sz = (float)sgz[kz];
-        const float r0 = Of[kz * ct + col], r1 = Of[MZ * ct + kz * ct + col], r2 = Of[2 * MZ * ct + kz * ct + col];
-        const float sr = fmaf(sx, r0, fmaf(sy, r1, sz * r2));
-        const float inv = 1.f / fmaf(bt, fmaf(sx, sx, fmaf(sy, sy, sz * sz)), eb);
-        const float f = beb * sr;
-        Es[(0 * ct + col) * LZ + kz] = Tr::cvt(fmaf(f, sx, r0) * inv);
-        Es[(1 * ct + col) * LZ + kz] = Tr::cvt(fmaf(f, sy, r1) * inv);
-        Es[(2 * ct + col) * LZ + kz] = Tr::cvt(fmaf(f, sz, r2) * inv);
-    }
-    __syncthreads();
-    E* out = reinterpret_cast<E*>(scr_v) + B.scr_off;
+    E* scr = reinterpret_cast<E*>(scr_v) + B.scr_off;
     const int oz0 = B.own_lo[2], oz1 = B.own_lo[2] + B.own_n[2];
     const int mlo = oz0 / 16 * 16, mhi = rup(oz1, 16);
-    for (int cc = 0; cc < 3; ++cc) {
-        const E* Tt = cc == 2 ? TCt : TSt;
-        warp_gemm<Tr>(Tt, LZ, Es + cc * ct * LZ, LZ, mlo, mhi, ct, MZ, [&](int z, int col, float v) {
-            if (z >= oz0 && z < oz1 && col < ncol) out[((long long)cc * mz + z) * nxy + col0 + col] = Tr::cvt(v);
-        });
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    for (int col0 = gcol0; col0 < gcol0 + gcols; col0 += ct) {
+        const int ncol = min(ct, gcol0 + gcols - col0);
+        // In[c][col][z] = scr[c][z][col0 + col]: rows (c, z) by warp, columns by lane
+        for (int cz = warp; cz < 3 * mz; cz += kT / 32) {
+            const int cc = cz / mz, z = cz - cc * mz;
+            const E* srow = scr + (long long)cz * nxy + col0;
+            E* dcol = In + cc * ct * LZ + z;
+            for (int col = lane; col < ct; col += 32) dcol[col * LZ] = col < ncol ? srow[col] : Tr::cvt(0.f);
+        }
+        __syncthreads();
+        for (int cc = 0; cc < 3; ++cc) {
+            const E* T = cc == 2 ? TC : TS;
+            float* O = Of + cc * MZ * ct;
+            warp_gemm<Tr>(T, LZ, In + cc * ct * LZ, LZ, 0, MZ, ct, MZ,
+                          [&](int kz, int col, float v) { O[kz * ct + col] = v; });
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < mz * ct; t += blockDim.x) {
+            const int kz = t / ct, col = t - kz * ct;
+            const int q = col0 + col;
+            float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+            if (col < ncol) {
+                const int ky = q / mx, kx = q - ky * mx;
+                const float sx = (float)sgx[kx], sy = (float)sgy[ky], sz = (float)sgz[kz];
+                const float r0 = Of[kz * ct + col], r1 = Of[MZ * ct + kz * ct + col];
+                const float r2 = Of[2 * MZ * ct + kz * ct + col];
+                const float sr = fmaf(sx, r0, fmaf(sy, r1, sz * r2));
+                const float inv = 1.f / fmaf(bt, fmaf(sx, sx, fmaf(sy, sy, sz * sz)), eb);
+                const float f = beb * sr;
+                e0 = fmaf(f, sx, r0) * inv;
+                e1 = fmaf(f, sy, r1) * inv;
+                e2 = fmaf(f, sz, r2) * inv;
+            }
+            Es[(0 * ct + col) * LZ + kz] = Tr::cvt(e0);
+            Es[(1 * ct + col) * LZ + kz] = Tr::cvt(e1);
+            Es[(2 * ct + col) * LZ + kz] = Tr::cvt(e2);
+        }
+        __syncthreads();
+        for (int cc = 0; cc < 3; ++cc) {
+            const E* Tt = cc == 2 ? TCt : TSt;
+            warp_gemm<Tr>(Tt, LZ, Es + cc * ct * LZ, LZ, mlo, mhi, ct, MZ, [&](int z, int col, float v) {
+                if (z >= oz0 && z < oz1 && col < ncol) scr[((long long)cc * mz + z) * nxy + col0 + col] = Tr::cvt(v);
+            });
+        }
+        __syncthreads();
     }
 }
 
-// ---- pass C: inverse y and x of one owned z-slab, scatter owned cells -
+// ---- pass C: inverse y and x of a group of owned z-slabs, owned scatter -
 template <class Tr>
 __global__ void __launch_bounds__(kT)
 k_mp_inv_xy(const void* __restrict__ scr_v, double* __restrict__ zout, const FmpBox* __restrict__ boxes,
@@ -281,7 +314,7 @@ k_mp_inv_xy(const void* __restrict__ scr_v, double* __restrict__ zout, const Fmp
     extern __shared__ __align__(16) unsigned char smraw[];
     const int4 it = items[blockIdx.x];
     const FmpBox B = boxes[it.x];
-    const int c = it.y, zl = it.z;
+    const int c = it.y, z0 = it.z, zn = it.w;
     const int mx = B.m[0], my = B.m[1], mz = B.m[2];
     const int MX = rup(mx, 16), MY = rup(my, 16);
     const int LX = MX + kPad, LY = MY + kPad;
@@ -293,25 +326,30 @@ k_mp_inv_xy(const void* __restrict__ scr_v, double* __restrict__ zout, const Fmp
     const bool sx = c != 0, sy = c != 1;
     stage_table(TYt, LY, mp_table<E>(tabs, (sy ? B.mps_off[1] : B.mpc_off[1]) + MY * MY), MY, MY);
     stage_table(TXt, LX, mp_table<E>(tabs, (sx ? B.mps_off[0] : B.mpc_off[0]) + MX * MX), MX, MX);
-    const E* src = reinterpret_cast<const E*>(scr_v) + B.scr_off + ((long long)c * mz + zl) * mx * my;
-    for (int t = threadIdx.x; t < MX * LY; t += blockDim.x) {
-        const int kx = t / LY, ky = t - kx * LY;
-        St[t] = (kx < mx && ky < my) ? src[ky * mx + kx] : Tr::cvt(0.f);
-    }
-    for (int t = threadIdx.x; t < MY * LX; t += blockDim.x) Qs[t] = Tr::cvt(0.f);
-    __syncthreads();
-    // Q[y][kx] = sum_ky T_y^T[y][ky] S[ky][kx], owned rows only
-    const int ylo = oy0 / 16 * 16, yhi = rup(oy0 + ony, 16);
-    warp_gemm<Tr>(TYt, LY, St, LY, ylo, yhi, rup(mx, 8), MY,
-                  [&](int y, int kx, float v) { if (kx < mx) Qs[y * LX + kx] = Tr::cvt(v); });
-    __syncthreads();
-    // out[y][x] = sum_kx Q[y][kx] T_x^T[x][kx]
+    fill_zero(St, MX * LY);   // padding rows kx >= mx and columns ky >= my stay zero
+    fill_zero(Qs, MY * LX);   // padding columns kx >= mx stay zero
     const double s = bscale ? bscale[it.x] : 1.0;
-    const int gk = B.ext_lo[2] + zl;
-    double* dst = zout + (((long long)c * nz + gk) * ny + B.ext_lo[1]) * (long long)nx + B.ext_lo[0];
-    warp_gemm<Tr>(Qs, LX, TXt, LX, ylo, yhi, rup(mx, 8), MX, [&](int y, int x, float v) {
-        if (y >= oy0 && y < oy0 + ony && x >= ox0 && x < ox0 + onx) dst[(long long)y * nx + x] = (double)v * s;
-    });
+    const int ylo = oy0 / 16 * 16, yhi = rup(oy0 + ony, 16);
+    const int NX8 = rup(mx, 8);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    for (int zl = z0; zl < z0 + zn; ++zl) {
+        const E* src = reinterpret_cast<const E*>(scr_v) + B.scr_off + ((long long)c * mz + zl) * mx * my;
+        for (int ky = warp; ky < my; ky += kT / 32)
+            for (int kx = lane; kx < mx; kx += 32) St[kx * LY + ky] = src[ky * mx + kx];
+        __syncthreads();
+        // Q[y][kx] = sum_ky T_y^T[y][ky] S[ky][kx], owned rows only
+        warp_gemm<Tr>(TYt, LY, St, LY, ylo, yhi, NX8, MY,
+                      [&](int y, int kx, float v) { if (kx < mx) Qs[y * LX + kx] = Tr::cvt(v); });
+        __syncthreads();
+        // out[y][x] = sum_kx Q[y][kx] T_x^T[x][kx]
+        const int gk = B.ext_lo[2] + zl;
+        double* dst = zout + (((long long)c * nz + gk) * ny + B.ext_lo[1]) * (long long)nx + B.ext_lo[0];
+        warp_gemm<Tr>(Qs, LX, TXt, LX, ylo, yhi, NX8, MX, [&](int y, int x, float v) {
+            if (y >= oy0 && y < oy0 + ony && x >= ox0 && x < ox0 + onx) dst[(long long)y * nx + x] = (double)v * s;
+        });
+        __syncthreads();
+    }
 }
 
 // ---- fp16 scale: largest |r| over each extended box ---------------------
@@ -375,12 +413,12 @@ cudaError_t launch_mp(const FmpPlan& p, const void* tabs, const double* tabs64, 
                       const double* gate) {
     using E = typename Tr::E;
     if (bscale) k_mp_boxmax<<<p.n_boxes, 256, 0, s>>>(r, p.d_boxes, bscale, nx, ny, nz, gate);
-    k_mp_fwd_xy<Tr><<<p.n_items_a, kT, smem_mp_a<E>(p.max_m), s>>>(r, scratch, p.d_boxes, p.d_items_a, tabs, bscale,
-                                                                   nx, ny, nz, gate);
-    k_mp_z_solve<Tr><<<p.n_items_b, kT, smem_mp_b<E>(p.max_m, ct), s>>>(scratch, p.d_boxes, p.d_items_b, tabs,
-                                                                         tabs64, beta, ct, gate);
-    k_mp_inv_xy<Tr><<<p.n_items_c, kT, smem_mp_c<E>(p.max_m), s>>>(scratch, z, p.d_boxes, p.d_items_c, tabs, bscale,
-                                                                   nx, ny, nz, gate);
+    k_mp_fwd_xy<Tr><<<p.n_items_ga, kT, smem_mp_a<E>(p.max_m), s>>>(r, scratch, p.d_boxes, p.d_items_ga, tabs,
+                                                                    bscale, nx, ny, nz, gate);
+    k_mp_z_solve<Tr><<<p.n_items_gb, kT, smem_mp_b<E>(p.max_m, ct), s>>>(scratch, p.d_boxes, p.d_items_gb, tabs,
+                                                                          tabs64, beta, ct, gate);
+    k_mp_inv_xy<Tr><<<p.n_items_gc, kT, smem_mp_c<E>(p.max_m), s>>>(scratch, z, p.d_boxes, p.d_items_gc, tabs,
+                                                                    bscale, nx, ny, nz, gate);
     return cudaGetLastError();
 }
 

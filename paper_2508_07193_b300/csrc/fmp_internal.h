@@ -11,6 +11,8 @@
 
 #define FMP_MAX_EXTENT 80   // float64 pass A/C slabs and tables fit shared memory
 #define FMP_MAX_RESTART 32
+#define FMP_MP_SLAB_GROUP 4   // z-slabs per CTA in the reduced-precision passes A and C
+#define FMP_MP_TILE_GROUP 4   // column tiles per CTA in the reduced-precision pass B
 
 // Device-side descriptor of one subdomain box (Sec. II-B). Coordinates are
 // in cells, ordered (x, y, z).
@@ -66,6 +68,15 @@ struct FmpPlan {
     int n_items_b = 0;
     int4* d_items_c = nullptr;  // (box, comp, owned slab, 0): inverse y/x
     int n_items_c = 0;
+    // grouped work lists of the reduced-precision passes (tables staged once
+    // per CTA): (box, comp, first slab, slabs) for A and C, (box, first
+    // column, columns, 0) for B
+    int4* d_items_ga = nullptr;
+    int n_items_ga = 0;
+    int4* d_items_gb = nullptr;
+    int n_items_gb = 0;
+    int4* d_items_gc = nullptr;
+    int n_items_gc = 0;
     int max_m[3] = {0, 0, 0};
     long long scratch_doubles = 0;
 };

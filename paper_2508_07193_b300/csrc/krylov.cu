@@ -487,7 +487,7 @@ __global__ void k_bicg_reset(double* sc) {
 
 int grid_stream(size_t n) {
     size_t b = (n + kCH - 1) / kCH;
-    return (int)(b < 148 * 3 ? (b ? b : 1) : 148 * 3);
+    return (int)(b < 148 * 3 ? (b ? b : 1) : 148 * 3);   // 3 blocks per SM (64 KB ring each)
 }
 int grid_n(size_t n) {
     size_t b = (n + kT - 1) / kT;
