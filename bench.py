@@ -43,6 +43,7 @@ def parse():
     p.add_argument("--precision", default="fp64")
     p.add_argument("--krylov", default="fgmres", choices=["fgmres", "bicgstab"])
     p.add_argument("--graph", action="store_true", help="replay each FGMRES restart cycle as one CUDA graph")
+    p.add_argument("--autotune", action="store_true", help="autotune the reduced-precision work lists first")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--case", default="step", choices=["step", "precond", "spmv"],
                    help="precond/spmv: only W + K applies of that operator (for profiler captures)")
@@ -227,6 +228,9 @@ def run_ours(args):
     ctx = F.Context(w.grid, w.eps_cell, w.beta, w.cuts, w.overlap, precision=args.precision, restart=30,
                     rtol=1e-8, stream=stream, device=dev, krylov=args.krylov, use_graph=args.graph)
     dt = 2.0 * math.sqrt(w.beta)
+    tuning = None
+    if args.autotune and args.precision != "fp64":
+        tuning = ctx.autotune(args.precision, reps=3)
     b = torch.as_tensor(w.rhs, device=dev)
     J = (-b / dt).contiguous()
     E = ctx.empty_field()
@@ -348,6 +352,7 @@ def run_ours(args):
         "e2e": {"value": world * dof / (ms_e2e * 1e-3), "unit": "DoF/s", "h2d_bytes_per_step": b.numel() * 8,
                 "d2h_bytes_per_step": E.numel() * 8},
         "gpu_launches": launches,
+        "tuning": list(tuning) if tuning else list(ctx.get_tuning()),
         "clocks": clocks,
     }
     # phase breakdown from one extra (untimed) step with CUDA-event phase timers

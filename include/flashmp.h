@@ -151,6 +151,20 @@ int fmp_get_eps_edge(fmp_ctx* ctx, double* out);
  * replayed graphs included), for launch accounting; *n is HOST. */
 int fmp_get_launch_count(fmp_ctx* ctx, long long* n);
 
+/* Work-list grouping of the reduced-precision preconditioner (not in the
+ * paper): slab_group z-slabs per CTA in the gather/x/y and inverse y/x passes,
+ * tile_group column tiles per CTA in the z/3x3 pass; each in [1, 64]
+ * (default 4, 4). Results do not depend on it, only speed. */
+int fmp_set_tuning(fmp_ctx* ctx, int slab_group, int tile_group);
+int fmp_get_tuning(fmp_ctx* ctx, int* slab_group, int* tile_group);
+
+/* Autotuner: time `reps` reduced-precision preconditioner applies (precision
+ * FMP_PREC_TF32, _FP16 or _BF16) for every grouping in {1,2,4,8} x {1,2,4,8}
+ * with CUDA events on the context's stream, keep the fastest, and return
+ * result[0] = slab group, result[1] = tile group, result[2] = microseconds per
+ * apply (HOST int[3]). Uses the context's own buffers; synchronises. */
+int fmp_autotune(fmp_ctx* ctx, int precision, int reps, int* result);
+
 /* Number of subdomain boxes. */
 int fmp_get_num_boxes(fmp_ctx* ctx, int* n);
 

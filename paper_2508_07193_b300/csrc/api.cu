@@ -111,6 +111,37 @@ void build_items(const std::vector<FmpBox>& boxes, int ct, std::vector<int4>& A,
     }
 }
 
+// Grouped work lists of the reduced-precision passes: sg z-slabs per CTA in
+// passes A and C, tg column tiles of ct columns per CTA in pass B.
+void group_items(const std::vector<FmpBox>& boxes, int ct, int sg, int tg, std::vector<int4>& GA,
+                 std::vector<int4>& GB, std::vector<int4>& GC) {
+    for (int b = 0; b < (int)boxes.size(); ++b) {
+        const FmpBox& x = boxes[b];
+        for (int c = 0; c < 3; ++c) {
+            for (int z = 0; z < x.m[2]; z += sg) GA.push_back(make_int4(b, c, z, std::min(sg, x.m[2] - z)));
+            const int o0 = x.own_lo[2], o1 = x.own_lo[2] + x.own_n[2];
+            for (int z = o0; z < o1; z += sg) GC.push_back(make_int4(b, c, z, std::min(sg, o1 - z)));
+        }
+        const int nxy = x.m[0] * x.m[1], span = ct * tg;
+        for (int q = 0; q < nxy; q += span) GB.push_back(make_int4(b, q, std::min(span, nxy - q), 0));
+    }
+}
+
+// Rebuild only the grouped lists for a new (sg, tg).
+cudaError_t regroup(FmpPlan& p, const std::vector<FmpBox>& boxes, int sg, int tg, cudaStream_t s) {
+    std::vector<int4> GA, GB, GC;
+    group_items(boxes, fmp_column_tile(p.max_m), sg, tg, GA, GB, GC);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e) return e;
+    cudaFree(p.d_items_ga); cudaFree(p.d_items_gb); cudaFree(p.d_items_gc);
+    p.d_items_ga = p.d_items_gb = p.d_items_gc = nullptr;
+    p.slab_group = sg; p.tile_group = tg;
+    p.n_items_ga = (int)GA.size(); p.n_items_gb = (int)GB.size(); p.n_items_gc = (int)GC.size();
+    if ((e = upload(&p.d_items_ga, GA, s))) return e;
+    if ((e = upload(&p.d_items_gb, GB, s))) return e;
+    return upload(&p.d_items_gc, GC, s);
+}
+
 cudaError_t make_plan(FmpPlan& p, const std::vector<FmpBox>& boxes, cudaStream_t s) {
     p.n_boxes = (int)boxes.size();
     p.max_m[0] = p.max_m[1] = p.max_m[2] = 0;
@@ -126,18 +157,7 @@ cudaError_t make_plan(FmpPlan& p, const std::vector<FmpBox>& boxes, cudaStream_t
     build_items(boxes, ct, A, B, C);
     p.n_items_a = (int)A.size(); p.n_items_b = (int)B.size(); p.n_items_c = (int)C.size();
     std::vector<int4> GA, GB, GC;
-    for (int b = 0; b < (int)boxes.size(); ++b) {
-        const FmpBox& x = boxes[b];
-        for (int c = 0; c < 3; ++c) {
-            for (int z = 0; z < x.m[2]; z += FMP_MP_SLAB_GROUP)
-                GA.push_back(make_int4(b, c, z, std::min(FMP_MP_SLAB_GROUP, x.m[2] - z)));
-            const int o0 = x.own_lo[2], o1 = x.own_lo[2] + x.own_n[2];
-            for (int z = o0; z < o1; z += FMP_MP_SLAB_GROUP)
-                GC.push_back(make_int4(b, c, z, std::min(FMP_MP_SLAB_GROUP, o1 - z)));
-        }
-        const int nxy = x.m[0] * x.m[1], span = ct * FMP_MP_TILE_GROUP;
-        for (int q = 0; q < nxy; q += span) GB.push_back(make_int4(b, q, std::min(span, nxy - q), 0));
-    }
+    group_items(boxes, ct, p.slab_group, p.tile_group, GA, GB, GC);
     p.n_items_ga = (int)GA.size(); p.n_items_gb = (int)GB.size(); p.n_items_gc = (int)GC.size();
     cudaError_t e;
     if ((e = upload(&p.d_boxes, boxes, s))) return e;
@@ -401,7 +421,7 @@ void fmp_destroy(fmp_ctx* c) {
     for (int t = 0; t < 3; ++t) cudaFree(c->d_tab_mp[t]);
     cudaFree(c->d_bscale);
     cudaFree(c->d_eps_cell);
-    cudaFree(c->d_tmp3);
+    cudaFree(c->d_tmp3); cudaFree(c->d_tmp4); cudaFree(c->d_tmp5);
     fmp_cnn_free(c);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
@@ -432,6 +452,57 @@ int fmp_get_eps_edge(fmp_ctx* c, double* out) {
     if (int rc = latched(c)) return rc;
     FMP_CK(cudaMemcpyAsync(out, c->d_eps_edge, sizeof(double) * c->n_slots, cudaMemcpyDeviceToDevice, c->stream));
     FMP_CK(cudaStreamSynchronize(c->stream));
+    return FMP_OK;
+}
+
+int fmp_set_tuning(fmp_ctx* c, int slab_group, int tile_group) {
+    if (!valid_ctx(c) || slab_group < 1 || slab_group > 64 || tile_group < 1 || tile_group > 64) return FMP_ERR_ARG;
+    if (int rc = latched(c)) return rc;
+    if (slab_group == c->ras.slab_group && tile_group == c->ras.tile_group) return FMP_OK;
+    FMP_CK(regroup(c->ras, c->h_boxes, slab_group, tile_group, c->stream));
+    c->graph_valid = false;
+    return FMP_OK;
+}
+
+int fmp_get_tuning(fmp_ctx* c, int* slab_group, int* tile_group) {
+    if (!valid_ctx(c) || !slab_group || !tile_group) return FMP_ERR_ARG;
+    *slab_group = c->ras.slab_group;
+    *tile_group = c->ras.tile_group;
+    return FMP_OK;
+}
+
+int fmp_autotune(fmp_ctx* c, int precision, int reps, int* result) {
+    if (!valid_ctx(c) || !result || reps < 1 || precision < FMP_PREC_TF32 || precision > FMP_PREC_BF16)
+        return FMP_ERR_ARG;
+    if (int rc = latched(c)) return rc;
+    const int cand[4] = {1, 2, 4, 8};
+    const int saved = c->opt.precision;
+    c->opt.precision = precision;
+    float best = 1e30f;
+    int bs = c->ras.slab_group, bt = c->ras.tile_group;
+    cudaEvent_t e0 = c->ev[4], e1 = c->ev[5];
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+            FMP_CK(regroup(c->ras, c->h_boxes, cand[a], cand[b], c->stream));
+            int rc = fmp_precond(c, c->d_eps_edge, c->d_tmp2);   // warm-up; any nonzero field will do
+            if (rc != FMP_OK) { c->opt.precision = saved; return rc; }
+            FMP_CK(cudaEventRecord(e0, c->stream));
+            for (int r = 0; r < reps; ++r) {
+                rc = fmp_precond(c, c->d_eps_edge, c->d_tmp2);
+                if (rc != FMP_OK) { c->opt.precision = saved; return rc; }
+            }
+            FMP_CK(cudaEventRecord(e1, c->stream));
+            FMP_CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            FMP_CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) { best = ms; bs = cand[a]; bt = cand[b]; }
+        }
+    c->opt.precision = saved;
+    FMP_CK(regroup(c->ras, c->h_boxes, bs, bt, c->stream));
+    c->graph_valid = false;
+    result[0] = bs;
+    result[1] = bt;
+    result[2] = (int)(1000.f * best / reps);
     return FMP_OK;
 }
 

@@ -79,6 +79,8 @@ struct FmpPlan {
     int n_items_gc = 0;
     int max_m[3] = {0, 0, 0};
     long long scratch_doubles = 0;
+    int slab_group = FMP_MP_SLAB_GROUP;   // tuning of the grouped lists
+    int tile_group = FMP_MP_TILE_GROUP;
 };
 
 struct FmpCnn;
@@ -105,7 +107,9 @@ struct fmp_ctx {
     double* d_bscale = nullptr;   // per-box scale factors (fp16 transforms)
     double* d_eps_cell = nullptr; // cell permittivity [nz][ny][nx] (null: eps = 1)
     FmpCnn* cnn = nullptr;        // learned initial guess / correction (created on first use)
-    double* d_tmp3 = nullptr;     // third field-sized scratch (learned paths)
+    double* d_tmp3 = nullptr;     // field-sized scratch of the learned paths
+    double* d_tmp4 = nullptr;
+    double* d_tmp5 = nullptr;
 
     // Krylov workspace (allocated on first solve)
     int kry_restart = 0;

@@ -479,6 +479,15 @@ __global__ void k_bicg_scalars(double* sc, int which) {
         sc[SC_RHO_OLD] = sc[SC_RHO];
     }
 }
+// z += alpha n with alpha = d[0] / d[1] (0 when d[1] is not positive).
+__global__ void k_damped_axpy(double* __restrict__ z, const double* __restrict__ nn, size_t n, const double* d,
+                              const double* gate) {
+    if (gate && *gate != 0.0) return;
+    const double alpha = d[1] > 0.0 && isfinite(d[0] / d[1]) ? d[0] / d[1] : 0.0;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        z[e] = fma(alpha, nn[e], z[e]);
+}
+
 __global__ void k_bicg_reset(double* sc) {
     if (threadIdx.x || blockIdx.x) return;
     sc[SC_RHO_OLD] = sc[SC_ALPHA] = sc[SC_OMEGA] = 1.0;
@@ -558,6 +567,25 @@ int arnoldi_step(fmp_ctx* c, int j, fmp_solve_info* inf) {
         Timer tm(c, &inf->ms_precond);
         int rc = fmp_precond_gated(c, vj, zj, gate);
         if (rc != FMP_OK) return rc;
+        if (c->opt.use_learned >= 2 && c->cnn && c->d_tmp3) {
+            // learned coarse correction, damped by the minimal-residual weight:
+            // t = v - A z, n = N(t), q = A n, z += alpha n with
+            // alpha = <t, q> / <q, q>, so ||v - A z|| never grows
+            double* t = c->d_tmp3;
+            double* nn = c->d_tmp4;
+            double* q = c->d_tmp5;
+            c->launches += 2;
+            FMP_CK(fmp_launch_curlcurl(zj, c->d_eps_edge, t, -1.0, -c->beta, c->nx, c->ny, c->nz, s, gate, vj, 1.0));
+            FMP_CK(fmp_cnn_apply_dev(c, t, nn, 1.0, 0));
+            FMP_CK(fmp_launch_curlcurl(nn, c->d_eps_edge, q, 1.0, c->beta, c->nx, c->ny, c->nz, s, gate));
+            Pairs pr{};
+            pr.a[0] = t; pr.b[0] = q; pr.a[1] = q; pr.b[1] = q; pr.n = 2;
+            ++c->launches;
+            k_pairdots<<<grid_n(n), kT, 0, s>>>(pr, n, st + L.sc + SC_D2, c->d_partials, c->d_ticket);
+            ++c->launches;
+            k_damped_axpy<<<grid_n(n), kT, 0, s>>>(zj, nn, n, st + L.sc + SC_D2, gate);
+            FMP_CK(cudaGetLastError());
+        }
     }
     {
         Timer tm(c, &inf->ms_spmv);
@@ -645,6 +673,12 @@ int fmp_fgmres(fmp_ctx* c, const double* b, double* x, fmp_solve_info* info) {
     fmp_solve_info inf;
     std::memset(&inf, 0, sizeof(inf));
     FMP_CK(fmp_ensure_krylov(c));
+    if (c->opt.use_learned >= 2) {   // the in-FGMRES correction needs the network and scratch fields
+        if (!c->d_tmp3) FMP_CK(cudaMalloc(&c->d_tmp3, sizeof(double) * c->n_slots));
+        if (!c->d_tmp4) FMP_CK(cudaMalloc(&c->d_tmp4, sizeof(double) * c->n_slots));
+        if (!c->d_tmp5) FMP_CK(cudaMalloc(&c->d_tmp5, sizeof(double) * c->n_slots));
+        FMP_CK(fmp_cnn_create(c));
+    }
     const int R = c->kry_restart;
     const St L = st_layout(R);
     const size_t n = c->n_slots, ld = c->ld;

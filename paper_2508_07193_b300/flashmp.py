@@ -82,6 +82,9 @@ def lib():
         "fmp_get_eps_edge": (_I, [_P, _P]),
         "fmp_get_num_boxes": (_I, [_P, C.POINTER(_I)]),
         "fmp_get_launch_count": (_I, [_P, C.POINTER(C.c_longlong)]),
+        "fmp_set_tuning": (_I, [_P, _I, _I]),
+        "fmp_get_tuning": (_I, [_P, C.POINTER(_I), C.POINTER(_I)]),
+        "fmp_autotune": (_I, [_P, _I, _I, C.POINTER(_I)]),
         "fmp_get_box": (_I, [_P, _I, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I),
                              C.POINTER(_D)]),
         "fmp_curlcurl_apply": (_I, [_P, _P, _P, _D, _D]),
@@ -229,6 +232,46 @@ class Context:
     def eps_edge(self):
         out = self.empty_field()
         _check(lib().fmp_get_eps_edge(self._h, _ptr(out)), "fmp_get_eps_edge")
+        return out
+
+    def set_tuning(self, slab_group, tile_group):
+        _check(lib().fmp_set_tuning(self._h, int(slab_group), int(tile_group)), "fmp_set_tuning")
+
+    def get_tuning(self):
+        a, b = C.c_int(), C.c_int()
+        _check(lib().fmp_get_tuning(self._h, C.byref(a), C.byref(b)), "fmp_get_tuning")
+        return a.value, b.value
+
+    def autotune(self, precision="bf16", reps=5, cache=None):
+        """Pick the fastest work-list grouping for `precision` (fmp_autotune),
+        cached in the JSON file `cache` keyed by GPU name, grid, partition and
+        precision."""
+        import json
+        key = None
+        if cache:
+            name = torch.cuda.get_device_name(self.device)
+            key = f"{name}|{self.grid}|{self.num_boxes()}|{self.box(0)['m']}|{precision}"
+            try:
+                with open(cache) as f:
+                    table = json.load(f)
+            except (OSError, ValueError):
+                table = {}
+            if key in table:
+                self.set_tuning(*table[key][:2])
+                return tuple(table[key])
+        res = (C.c_int * 3)()
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        _check(lib().fmp_autotune(self._h, p, int(reps), res), "fmp_autotune")
+        out = (res[0], res[1], res[2])
+        if cache:
+            try:
+                with open(cache) as f:
+                    table = json.load(f)
+            except (OSError, ValueError):
+                table = {}
+            table[key] = list(out)
+            with open(cache, "w") as f:
+                json.dump(table, f, indent=1)
         return out
 
     def launch_count(self):

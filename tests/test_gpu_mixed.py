@@ -69,3 +69,21 @@ def test_fgmres_with_mixed_precond_reaches_fp64_residual(prec):
     ctx64 = context(w, rtol=1e-10)
     _, i64 = ctx64.krylov_solve(dev(w.rhs))
     assert info["iters"] <= i64["iters"] + 3
+
+
+def test_grouping_changes_speed_not_results_and_autotune_picks_one(tmp_path):
+    w = wl.small(grid=(24, 24, 24), cuts=((8, 8, 8),) * 3, overlap=3, seed=22, n_eps_boxes=6)
+    ctx = context(w, precision="bf16")
+    r = dev(w.rhs)
+    ctx.set_tuning(1, 1)
+    z1 = host(ctx.precond_apply(r))
+    ctx.set_tuning(8, 3)
+    assert ctx.get_tuning() == (8, 3)
+    z2 = host(ctx.precond_apply(r))
+    assert np.array_equal(z1, z2)
+    cache = str(tmp_path / "tune.json")
+    sg, tg, us = ctx.autotune("bf16", reps=2, cache=cache)
+    assert sg in (1, 2, 4, 8) and tg in (1, 2, 4, 8) and us > 0
+    assert ctx.get_tuning() == (sg, tg)
+    assert ctx.autotune("bf16", cache=cache) == (sg, tg, us)    # served from the cache
+    assert np.array_equal(host(ctx.precond_apply(r)), z1)
