@@ -73,6 +73,14 @@ __device__ __forceinline__ double fold_input(const FoldDims& d, int m, int q, Ge
     return v(d.off + qq) - v(m - 1 - qq);
 }
 
+// First inverse pair worth computing for an owned range [o0, o1): a pair
+// q < q0 puts both of its mirrored outputs (off + q and m - 1 - q) outside
+// the range (the overlap layers of the box).
+__device__ __forceinline__ int first_owned_pair(const FoldDims& d, int m, int o0, int o1) {
+    const int q0 = min(o0 - d.off, m - o1);
+    return q0 < 0 ? 0 : (q0 > d.npair ? d.npair : q0);
+}
+
 // Pass A: forward transforms along x and y of one z-slab of one component.
 __global__ void __launch_bounds__(kThreads)
 k_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox* __restrict__ boxes,
@@ -128,18 +136,28 @@ k_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox* _
         AB[t] = fold_input(dx, mx, q, [&](int i) { return row[i]; });
     }
     __syncthreads();
+    // Work index: all sym outputs (y, ks) first, then all anti (y, ka), so a
+    // warp takes one table class (a warp split by parity would run both FMA
+    // loops with half its lanes idle).
+    const int nsx = my * dx.nks;
     for (int t = threadIdx.x; t < nxy; t += blockDim.x) {
-        const int y = t / mx, kx = t - y * mx;
-        const double* a = AB + y * LX;
         double acc = 0.0;
-        if (((kx ^ dx.s0) & 1) == 0) {
-            const int ks = kx >> 1;
+        int y, kx;
+        if (t < nsx) {
+            y = t / dx.nks;
+            const int ks = t - y * dx.nks;
+            kx = 2 * ks + dx.s0;
+            const double* a = AB + y * LX;
             for (int q = 0; q < dx.la; ++q) acc = fma(TXS[q * dx.nks + ks], a[q], acc);
         } else {
-            const int ka = kx >> 1;
-            for (int q = 0; q < dx.lb; ++q) acc = fma(TXA[q * dx.nka + ka], a[dx.la + q], acc);
+            const int u = t - nsx;
+            y = u / dx.nka;
+            const int ka = u - y * dx.nka;
+            kx = 2 * ka + 1 - dx.s0;
+            const double* a = AB + y * LX + dx.la;
+            for (int q = 0; q < dx.lb; ++q) acc = fma(TXA[q * dx.nka + ka], a[q], acc);
         }
-        P[t] = acc;
+        P[y * mx + kx] = acc;
     }
     __syncthreads();
     const int LY = dy.la + dy.lb;
@@ -148,17 +166,26 @@ k_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox* _
         X[t] = fold_input(dy, my, q, [&](int y) { return P[y * mx + kx]; });
     }
     __syncthreads();
+    // sym rows (ks, kx) first, then anti rows (ka, kx): class-uniform warps
+    const int nsy = dy.nks * mx;
     for (int t = threadIdx.x; t < nxy; t += blockDim.x) {
-        const int ky = t / mx, kx = t - ky * mx;
         double acc = 0.0;
-        if (((ky ^ dy.s0) & 1) == 0) {
-            const double* f = fy.S + (ky >> 1) * dy.la;
+        int ky, kx;
+        if (t < nsy) {
+            const int ks = t / mx;
+            kx = t - ks * mx;
+            ky = 2 * ks + dy.s0;
+            const double* f = fy.S + ks * dy.la;
             for (int q = 0; q < dy.la; ++q) acc = fma(f[q], X[q * mx + kx], acc);
         } else {
-            const double* f = fy.A + (ky >> 1) * dy.lb;
+            const int u = t - nsy;
+            const int ka = u / mx;
+            kx = u - ka * mx;
+            ky = 2 * ka + 1 - dy.s0;
+            const double* f = fy.A + ka * dy.lb;
             for (int q = 0; q < dy.lb; ++q) acc = fma(f[q], X[(dy.la + q) * mx + kx], acc);
         }
-        dst[t] = acc;
+        dst[ky * mx + kx] = acc;
     }
 }
 
@@ -195,20 +222,26 @@ k_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int2
         AB[t] = q < d.la + d.lb ? fold_input(d, mz, q, [&](int z) { return in[z * CT]; }) : 0.0;
     }
     __syncthreads();
+    // per component, sym output rows first, then anti rows (class-uniform
+    // warps also when a warp spans two rows, CT = 16)
     for (int t = threadIdx.x; t < 3 * mz * CT; t += blockDim.x) {
         const int cz = t / CT, col = t - cz * CT;
-        const int c = cz / mz, kz = cz - c * mz;
+        const int c = cz / mz, r = cz - c * mz;
         const Fold& f = c == 2 ? fc : fs;
         const double* ab = AB + c * mz * CT + col;
         double acc = 0.0;
-        if (((kz ^ f.d.s0) & 1) == 0) {
-            const double* g = f.S + (kz >> 1) * f.d.la;
+        int kz;
+        if (r < f.d.nks) {
+            kz = 2 * r + f.d.s0;
+            const double* g = f.S + r * f.d.la;
             for (int q = 0; q < f.d.la; ++q) acc = fma(g[q], ab[q * CT], acc);
         } else {
-            const double* g = f.A + (kz >> 1) * f.d.lb;
+            const int ka = r - f.d.nks;
+            kz = 2 * ka + 1 - f.d.s0;
+            const double* g = f.A + ka * f.d.lb;
             for (int q = 0; q < f.d.lb; ++q) acc = fma(g[q], ab[(f.d.la + q) * CT], acc);
         }
-        Buf[t] = acc;
+        Buf[(c * mz + kz) * CT + col] = acc;
     }
     __syncthreads();
     const double* sgx = tabs + B.sig_off[0];
@@ -237,12 +270,14 @@ k_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int2
     // z = off + q and mz - 1 - q (E + O and E - O); the middle slab from E
     // alone; the DST wall slab z = 0 is zero. Only owned slabs are written.
     const int oz0 = B.own_lo[2], oz1 = B.own_lo[2] + B.own_n[2];
-    const int npq = fc.d.npair + fc.d.has_mid > fs.d.npair + fs.d.has_mid ? fc.d.npair + fc.d.has_mid
-                                                                          : fs.d.npair + fs.d.has_mid;
+    const int qc = first_owned_pair(fc.d, mz, oz0, oz1), qs = first_owned_pair(fs.d, mz, oz0, oz1);
+    const int nc = fc.d.npair + fc.d.has_mid - qc, ns = fs.d.npair + fs.d.has_mid - qs;
+    const int npq = nc > ns ? nc : ns;
     for (int t = threadIdx.x; t < 3 * npq * CT; t += blockDim.x) {
         const int cq = t / CT, col = t - cq * CT;
         if (col >= ncol) continue;
-        const int c = cq / npq, q = cq - c * npq;
+        const int c = cq / npq;
+        const int q = cq - c * npq + (c == 2 ? qc : qs);
         const Fold& f = c == 2 ? fc : fs;
         const FoldDims& d = f.d;
         const double* e = Buf + c * mz * CT + col;
@@ -290,9 +325,10 @@ k_inv_xy(const double* __restrict__ scr, double* __restrict__ zout, const FmpBox
     __syncthreads();
     {   // inverse along y, owned rows only
         const FoldDims& d = fy.d;
-        const int npq = d.npair + d.has_mid;
+        const int q0 = first_owned_pair(d, my, oy0, oy0 + ony);
+        const int npq = d.npair + d.has_mid - q0;
         for (int t = threadIdx.x; t < npq * mx; t += blockDim.x) {
-            const int q = t / mx, kx = t - q * mx;
+            const int q = t / mx + q0, kx = t - (q - q0) * mx;
             if (q < d.npair) {
                 double E = 0.0, O = 0.0;
                 for (int ks = 0; ks < d.nks; ++ks) E = fma(fy.S[ks * d.la + q], S[(2 * ks + d.s0) * mx + kx], E);
@@ -315,12 +351,16 @@ k_inv_xy(const double* __restrict__ scr, double* __restrict__ zout, const FmpBox
     double* dst = zout + (((long long)c * nz + gk) * ny + B.ext_lo[1] + oy0) * (long long)nx + B.ext_lo[0];
     {   // inverse along x, owned columns only
         const FoldDims& d = fx.d;
-        const int npq = d.npair + d.has_mid;
-        for (int t = threadIdx.x; t < ony * npq; t += blockDim.x) {
-            const int yy = t / npq, q = t - yy * npq;
-            const double* row = Q + yy * mx;
-            double* orow = dst + (long long)yy * nx;
-            if (q < d.npair) {
+        // all (row, pair) items first, then the rows' middle elements, so the
+        // pair warps do not wait on a middle lane's shorter loop
+        const int q0 = first_owned_pair(d, mx, ox0, ox0 + onx);
+        const int np = d.npair - q0;
+        const int npp = ony * np;
+        for (int t = threadIdx.x; t < npp + ony * d.has_mid; t += blockDim.x) {
+            if (t < npp) {
+                const int yy = t / np, q = t - yy * np + q0;
+                const double* row = Q + yy * mx;
+                double* orow = dst + (long long)yy * nx;
                 double E = 0.0, O = 0.0;
                 for (int ks = 0; ks < d.nks; ++ks) E = fma(fx.S[ks * d.la + q], row[2 * ks + d.s0], E);
                 for (int ka = 0; ka < d.nka; ++ka) O = fma(fx.A[ka * d.lb + q], row[2 * ka + 1 - d.s0], O);
@@ -328,12 +368,15 @@ k_inv_xy(const double* __restrict__ scr, double* __restrict__ zout, const FmpBox
                 if (x1 >= ox0 && x1 < ox0 + onx) orow[x1] = E + O;
                 if (x2 >= ox0 && x2 < ox0 + onx) orow[x2] = E - O;
             } else {
+                const int yy = t - npp;
+                const double* row = Q + yy * mx;
                 double E = 0.0;
                 for (int ks = 0; ks < d.nks; ++ks) E = fma(fx.S[ks * d.la + d.npair], row[2 * ks + d.s0], E);
-                if (d.mid >= ox0 && d.mid < ox0 + onx) orow[d.mid] = E;
+                if (d.mid >= ox0 && d.mid < ox0 + onx) dst[(long long)yy * nx + d.mid] = E;
             }
-            if (d.off == 1 && q == 0 && ox0 == 0) orow[0] = 0.0;
         }
+        if (d.off == 1 && ox0 == 0)
+            for (int yy = threadIdx.x; yy < ony; yy += blockDim.x) dst[(long long)yy * nx] = 0.0;
     }
 }
 

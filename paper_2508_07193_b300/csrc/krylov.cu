@@ -11,9 +11,8 @@
 // threshold 1/sqrt(2) fires at every step here: with a good preconditioner
 // A M^{-1} v_j is close to v_j, so most of w lies in the basis. The loss of
 // orthogonality of one classical pass grows like eps (||w|| / ||w - V h||)^2,
-// which stays below 1e-13 at the ratio used.) The vector
-// kernels stream contiguous 1024-element chunks of every basis vector per
-// block (16-byte loads), so DRAM pages and TLB entries are reused.
+// which stays below 1e-13 at the ratio used.) The basis passes take one
+// thread per element and keep the per-vector sums in registers.
 //
 // Reductions are deterministic: per-block partial sums reduced in block order
 // by the last block to finish (atomic ticket, no spinning). That last block
@@ -22,9 +21,10 @@
 // step returns at once when the flag is set, so a whole restart cycle can be
 // enqueued (or replayed as one CUDA graph) and read back once.
 #include "fmp_internal.h"
-#include "bulk.cuh"
 
+#include <array>
 #include <cmath>
+#include <utility>
 #include <cstring>
 
 namespace {
@@ -54,7 +54,7 @@ __host__ __device__ inline St st_layout(int R) {
 }
 enum {
     SC_BNORM = 0, SC_EST, SC_INV, SC_HN, SC_NRM, SC_DONE, SC_REORTH, SC_JDONE, SC_STATUS, SC_RTOL,
-    SC_BUDGET, SC_NREORTH, SC_KERR,
+    SC_BUDGET, SC_NREORTH,
     // BiCGSTAB scalars
     SC_RHO, SC_RHO_OLD, SC_ALPHA, SC_OMEGA, SC_BETA, SC_D0, SC_D1, SC_D2, SC_D3, SC_D4
 };
@@ -104,63 +104,14 @@ __device__ __forceinline__ bool gated(const double* st, int sc) { return st[sc +
 
 // ---- FGMRES kernels ---------------------------------------------------------
 
-// ---- streamed basis passes ----------------------------------------------
-// A block owns chunks blockIdx.x, blockIdx.x + gridDim.x, ... of kCH doubles.
-// For each chunk it streams w and then V_0..V_{nv-1} as 16 KB tiles through a
-// kNST-deep ring of shared-memory stages, each filled by one bulk copy whose
-// completion is signalled on that stage's mbarrier. The loads need no
-// registers while in flight, so each SM keeps 128-192 KB of reads pending.
-constexpr int kCH = 2048;
-constexpr int kNST = 4;
-constexpr int kPer = kCH / kT;
-constexpr size_t kStreamSmem = sizeof(double) * kNST * kCH;
-
-struct Ring {
-    uint64_t* bar;
-    double* stage;
-};
-
-// Issue tile t (thread 0): tile t of chunk-list position t / nt, vector t % nt
-// (0 = w, v >= 1 = V_{v-1}). Odd-length tails copy the even prefix; the last
-// element is read directly by its consumer.
-__device__ __forceinline__ void issue_tile(const Ring& rg, size_t t, int nt, const double* V, size_t ld,
-                                           const double* w, size_t n) {
-    const size_t cl = t / nt;
-    const int v = (int)(t - cl * nt);
-    const size_t e0 = ((size_t)blockIdx.x + cl * gridDim.x) * kCH;
-    const size_t len = n - e0 < (size_t)kCH ? n - e0 : (size_t)kCH;
-    const unsigned bytes = (unsigned)((len & ~(size_t)1) * sizeof(double));
-    const double* src = (v == 0 ? w : V + (size_t)(v - 1) * ld) + e0;
-    uint64_t* b = rg.bar + t % kNST;
-    fmp::fence_async_shared();
-    fmp::mbar_expect_tx(b, bytes);
-    if (bytes) fmp::bulk_g2s(rg.stage + (t % kNST) * kCH, src, bytes, b);
-}
-
-// Block-uniform bounded wait for tile t; false if any thread gave up.
-__device__ __forceinline__ bool wait_tile(const Ring& rg, size_t t) {
-    const bool ok = fmp::mbar_wait(rg.bar + t % kNST, (unsigned)((t / kNST) & 1));
-    return __syncthreads_and(ok) != 0;
-}
-
-__device__ __forceinline__ double tile_val(const double* sp, const double* g, size_t e0, size_t len, int idx) {
-    if ((size_t)idx >= len) return 0.0;
-    if ((len & 1) && (size_t)idx == len - 1) return g[e0 + idx];
-    return sp[idx];
-}
-
-// Give up: record the failure and drain the copies still in flight.
-__device__ void ring_abort(const Ring& rg, size_t t, size_t ntiles, double* st, int sc) {
-    if (threadIdx.x == 0) st[sc + SC_KERR] = 1.0;
-    for (size_t u = t + 1; u < ntiles && u < t + kNST; ++u) (void)fmp::mbar_wait(rg.bar + u % kNST, (unsigned)((u / kNST) & 1));
-    __syncthreads();
-}
-
-__device__ size_t my_tiles(size_t n, int nt) {
-    const size_t nchunks = (n + kCH - 1) / kCH;
-    const size_t mine = blockIdx.x < nchunks ? (nchunks - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
-    return mine * nt;
-}
+// ---- basis passes ----------------------------------------------------------
+// One thread per element (grid-stride): an element of w is loaded once and
+// meets the same element of every basis vector, each a coalesced 8-byte load
+// (16 independent loads in flight per thread keep HBM busy). G >= nv
+// per-vector sums sit in registers (the loop over vectors is unrolled, so
+// they are indexed statically). These passes do one float64 FMA per 8 bytes
+// read, so on this part the float64 pipe, not HBM, is their bound.
+constexpr int kBasisBlocksPerSM = 4;
 
 // Publish block totals tot[0..nv) as this block's partials; returns true in
 // the last block to finish.
@@ -175,64 +126,78 @@ __device__ bool block_publish(const double* tot, int nv, double* partials, unsig
     return last;
 }
 
-// out[i] = <V_i, w> for i < nv and out[nv] = <w, w>. mode 0: always (first
-// pass); mode 1: only when the re-orthogonalisation flag is up.
-__global__ void __launch_bounds__(kT)
-k_dots(const double* __restrict__ V, size_t ld, int nv, const double* __restrict__ w, size_t n, double* st,
-       int R, int out_off, int mode, double* partials, unsigned int* ticket) {
+// Butterfly reduce-scatter of v[0..G) (G a power of two <= 32) over the warp:
+// G - 1 (+1 when G = 16) float64 adds per lane instead of 5 G for G separate
+// shuffle trees. Returns the full warp sum of value slot(lane) in every lane
+// whose (lane & (32 / G - 1)) is 0.
+template <int G>
+__device__ __forceinline__ double warp_reduce_scatter(double (&v)[G], int lane, int& slot) {
+    slot = 0;
+#pragma unroll
+    for (int s = 0; (G >> (s + 1)) >= 1; ++s) {
+        const int o = 16 >> s;
+        const int half = G >> (s + 1);
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const double send = upper ? v[i] : v[i + half];
+            const double keep = upper ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+        if (upper) slot += half;
+    }
+    // lanes that differ only in the offsets not used above hold partial sums
+    // of the same slot
+#pragma unroll
+    for (int o = 16 / G; o >= 1; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+    return v[0];
+}
+
+// Smallest power of two >= n (n <= 32): the reduce-scatter width.
+__host__ __device__ constexpr int pow2_at_least(int n) {
+    return n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : 32;
+}
+__host__ __device__ constexpr int basis_blocks_per_sm(int nv) { return nv <= 16 ? kBasisBlocksPerSM : 2; }
+
+// out[i] = <V_i, w> for i < NV and out[NV] = <w, w>. mode 0: always (first
+// pass); mode 1: only when the re-orthogonalisation flag is up. One kernel
+// per basis size: a float64 FMA that is predicated off still takes its turn
+// in the float64 pipe, so the vector count is a compile-time constant.
+template <int NV>
+__global__ void __launch_bounds__(kT, basis_blocks_per_sm(NV))
+k_dots(const double* __restrict__ V, size_t ld, const double* __restrict__ w, size_t n, double* st, int R,
+       int out_off, int mode, double* partials, unsigned int* ticket) {
     const St L = st_layout(R);
     if (gated(st, L.sc) || (mode == 1 && st[L.sc + SC_REORTH] == 0.0)) return;
-    extern __shared__ __align__(128) double sm_stage[];
-    __shared__ __align__(8) uint64_t bars[kNST];
-    Ring rg{bars, sm_stage};
-    const int nt = nv + 1;
-    const size_t ntiles = my_tiles(n, nt);
-    if (threadIdx.x == 0) {
-        for (int q = 0; q < kNST; ++q) fmp::mbar_init(bars + q, 1);
-        fmp::mbar_init_fence();
+    constexpr int G = pow2_at_least(NV);
+    double acc[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) acc[g] = 0.0;
+    double ww = 0.0;
+    for (size_t e = (size_t)blockIdx.x * kT + threadIdx.x; e < n; e += (size_t)gridDim.x * kT) {
+        const double x = __ldg(w + e);
+        ww = fma(x, x, ww);
+#pragma unroll
+        for (int g = 0; g < NV; ++g) acc[g] = fma(__ldg(V + (size_t)g * ld + e), x, acc[g]);
     }
-    __syncthreads();
-    if (threadIdx.x == 0)
-        for (size_t t = 0; t < ntiles && t < (size_t)kNST; ++t) issue_tile(rg, t, nt, V, ld, w, n);
-    // per-warp running sums: slot v-1 for <V_{v-1}, w>, slot kMaxV for <w, w>
     __shared__ double wsum[kT / 32][kMaxV + 1];
-    for (int q = threadIdx.x; q < (kT / 32) * (kMaxV + 1); q += kT) (&wsum[0][0])[q] = 0.0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double wr[kPer];
-    for (size_t t = 0; t < ntiles; ++t) {
-        if (!wait_tile(rg, t)) { ring_abort(rg, t, ntiles, st, L.sc); return; }
-        const size_t cl = t / nt;
-        const int v = (int)(t - cl * nt);
-        const size_t e0 = ((size_t)blockIdx.x + cl * gridDim.x) * kCH;
-        const size_t len = n - e0 < (size_t)kCH ? n - e0 : (size_t)kCH;
-        const double* sp = rg.stage + (t % kNST) * kCH;
-        double p = 0.0;
-        if (v == 0) {
-#pragma unroll
-            for (int k = 0; k < kPer; ++k) {
-                wr[k] = tile_val(sp, w, e0, len, threadIdx.x + k * kT);
-                p = fma(wr[k], wr[k], p);
-            }
-        } else {
-            const double* g = V + (size_t)(v - 1) * ld;
-#pragma unroll
-            for (int k = 0; k < kPer; ++k) p = fma(tile_val(sp, g, e0, len, threadIdx.x + k * kT), wr[k], p);
-        }
-        p = warp_sum(p);
-        if (lane == 0) wsum[warp][v == 0 ? kMaxV : v - 1] += p;
-        __syncthreads();
-        if (threadIdx.x == 0 && t + kNST < ntiles) issue_tile(rg, t + kNST, nt, V, ld, w, n);
-    }
+    int slot;
+    const double v = warp_reduce_scatter<G>(acc, lane, slot);
+    if ((lane & (32 / G - 1)) == 0) wsum[warp][slot] = v;
+    const double wv = warp_sum(ww);
+    if (lane == 0) wsum[warp][kMaxV] = wv;
+    __syncthreads();
     __shared__ double tot[kMaxV + 2];
-    if (threadIdx.x <= nv) {
-        const int slot = threadIdx.x < nv ? threadIdx.x : kMaxV;   // <w,w> right after the nv dots
+    if (threadIdx.x <= NV) {
+        const int sl = threadIdx.x < NV ? threadIdx.x : kMaxV;   // <w,w> right after the NV dots
         double sum = 0.0;
-        for (int q = 0; q < kT / 32; ++q) sum += wsum[q][slot];
+        for (int q = 0; q < kT / 32; ++q) sum += wsum[q][sl];
         tot[threadIdx.x] = sum;
     }
     __syncthreads();
-    if (block_publish(tot, nv + 1, partials, ticket)) {
-        if (threadIdx.x <= nv) st[out_off + threadIdx.x] = block_total(partials, threadIdx.x);
+    if (block_publish(tot, NV + 1, partials, ticket)) {
+        if (threadIdx.x <= NV) st[out_off + threadIdx.x] = block_total(partials, threadIdx.x);
         __syncthreads();
         if (threadIdx.x == 0) *ticket = 0;
     }
@@ -281,58 +246,26 @@ __device__ void arnoldi_finish(double* st, const St& L, int j, const double* h, 
 
 // w -= V h. mode 0: h = h1, then the DGKS test decides between finishing the
 // column and raising the re-orthogonalisation flag. mode 1 (flag up only):
-// h = h2, then finish the column with h1 + h2. Streams tiles like k_dots; the
-// updated chunk of w is written back after its last basis tile.
-__global__ void __launch_bounds__(kT)
-k_update(const double* __restrict__ V, size_t ld, int nv, double* __restrict__ w, size_t n, double* st, int R,
-         int j, int mode, double* partials, unsigned int* ticket) {
+// h = h2, then finish the column with h1 + h2. One thread per element like
+// k_dots, h in registers; ||w - V h||^2 is accumulated on the way.
+template <int NV>
+__global__ void __launch_bounds__(kT, basis_blocks_per_sm(NV))
+k_update(const double* __restrict__ V, size_t ld, double* __restrict__ w, size_t n, double* st, int R, int j,
+         int mode, double* partials, unsigned int* ticket) {
+    constexpr int nv = NV;
     const St L = st_layout(R);
     if (gated(st, L.sc) || (mode == 1 && st[L.sc + SC_REORTH] == 0.0)) return;
-    extern __shared__ __align__(128) double sm_stage[];
-    __shared__ __align__(8) uint64_t bars[kNST];
-    __shared__ double hs[kMaxV];
-    Ring rg{bars, sm_stage};
     const double* h = st + (mode == 0 ? L.h1 : L.h2);
-    if (threadIdx.x < nv) hs[threadIdx.x] = h[threadIdx.x];
-    const int nt = nv + 1;
-    const size_t ntiles = my_tiles(n, nt);
-    if (threadIdx.x == 0) {
-        for (int q = 0; q < kNST; ++q) fmp::mbar_init(bars + q, 1);
-        fmp::mbar_init_fence();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0)
-        for (size_t t = 0; t < ntiles && t < (size_t)kNST; ++t) issue_tile(rg, t, nt, V, ld, w, n);
+    double hr[NV];
+#pragma unroll
+    for (int g = 0; g < NV; ++g) hr[g] = -h[g];
     double acc[1] = {0.0};
-    double wr[kPer];
-    for (size_t t = 0; t < ntiles; ++t) {
-        if (!wait_tile(rg, t)) { ring_abort(rg, t, ntiles, st, L.sc); return; }
-        const size_t cl = t / nt;
-        const int v = (int)(t - cl * nt);
-        const size_t e0 = ((size_t)blockIdx.x + cl * gridDim.x) * kCH;
-        const size_t len = n - e0 < (size_t)kCH ? n - e0 : (size_t)kCH;
-        const double* sp = rg.stage + (t % kNST) * kCH;
-        if (v == 0) {
+    for (size_t e = (size_t)blockIdx.x * kT + threadIdx.x; e < n; e += (size_t)gridDim.x * kT) {
+        double x = w[e];
 #pragma unroll
-            for (int k = 0; k < kPer; ++k) wr[k] = tile_val(sp, w, e0, len, threadIdx.x + k * kT);
-        } else {
-            const double* g = V + (size_t)(v - 1) * ld;
-            const double hv = hs[v - 1];
-#pragma unroll
-            for (int k = 0; k < kPer; ++k) wr[k] = fma(-hv, tile_val(sp, g, e0, len, threadIdx.x + k * kT), wr[k]);
-        }
-        if (v == nv) {
-#pragma unroll
-            for (int k = 0; k < kPer; ++k) {
-                const size_t idx = threadIdx.x + k * kT;
-                if (idx < len) {
-                    w[e0 + idx] = wr[k];
-                    acc[0] = fma(wr[k], wr[k], acc[0]);
-                }
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0 && t + kNST < ntiles) issue_tile(rg, t + kNST, nt, V, ld, w, n);
+        for (int g = 0; g < NV; ++g) x = fma(hr[g], __ldg(V + (size_t)g * ld + e), x);
+        w[e] = x;
+        acc[0] = fma(x, x, acc[0]);
     }
     if (block_partials(acc, 1, partials, ticket)) {
         if (threadIdx.x == 0) {
@@ -494,9 +427,55 @@ __global__ void k_bicg_reset(double* sc) {
 }
 
 
-int grid_stream(size_t n) {
-    size_t b = (n + kCH - 1) / kCH;
-    return (int)(b < 148 * 3 ? (b ? b : 1) : 148 * 3);   // 3 blocks per SM (64 KB ring each)
+// Basis passes: one instantiation per basis size 1..kMaxV, picked from a
+// table at launch.
+int grid_basis(size_t n, int per_sm) {
+    const size_t b = (n + kT - 1) / kT;
+    return (int)(b < (size_t)148 * per_sm ? (b ? b : 1) : 148 * per_sm);
+}
+struct BasisArgs {
+    const double* V;
+    size_t ld;
+    double* w;
+    size_t n;
+    double* st;
+    int R, j, out_off, mode;
+    double* partials;
+    unsigned int* ticket;
+};
+template <int NV>
+void launch_dots_nv(const BasisArgs& a, cudaStream_t s) {
+    k_dots<NV><<<grid_basis(a.n, basis_blocks_per_sm(NV)), kT, 0, s>>>(a.V, a.ld, a.w, a.n, a.st, a.R, a.out_off,
+                                                                        a.mode, a.partials, a.ticket);
+}
+template <int NV>
+void launch_update_nv(const BasisArgs& a, cudaStream_t s) {
+    k_update<NV><<<grid_basis(a.n, basis_blocks_per_sm(NV)), kT, 0, s>>>(a.V, a.ld, a.w, a.n, a.st, a.R, a.j,
+                                                                          a.mode, a.partials, a.ticket);
+}
+using BasisLaunch = void (*)(const BasisArgs&, cudaStream_t);
+template <int... I>
+constexpr std::array<BasisLaunch, sizeof...(I)> dots_table(std::integer_sequence<int, I...>) {
+    return {{&launch_dots_nv<I + 1>...}};
+}
+template <int... I>
+constexpr std::array<BasisLaunch, sizeof...(I)> update_table(std::integer_sequence<int, I...>) {
+    return {{&launch_update_nv<I + 1>...}};
+}
+constexpr auto kDots = dots_table(std::make_integer_sequence<int, kMaxV>{});
+constexpr auto kUpdates = update_table(std::make_integer_sequence<int, kMaxV>{});
+
+cudaError_t launch_dots(const double* V, size_t ld, int nv, const double* w, size_t n, double* st, int R,
+                        int out_off, int mode, fmp_ctx* c, cudaStream_t s) {
+    if (nv < 1 || nv > kMaxV) return cudaErrorInvalidValue;
+    kDots[nv - 1]({V, ld, const_cast<double*>(w), n, st, R, 0, out_off, mode, c->d_partials, c->d_ticket}, s);
+    return cudaGetLastError();
+}
+cudaError_t launch_update(const double* V, size_t ld, int nv, double* w, size_t n, double* st, int R, int j,
+                          int mode, fmp_ctx* c, cudaStream_t s) {
+    if (nv < 1 || nv > kMaxV) return cudaErrorInvalidValue;
+    kUpdates[nv - 1]({V, ld, w, n, st, R, j, 0, mode, c->d_partials, c->d_ticket}, s);
+    return cudaGetLastError();
 }
 int grid_n(size_t n) {
     size_t b = (n + kT - 1) / kT;
@@ -596,13 +575,13 @@ int arnoldi_step(fmp_ctx* c, int j, fmp_solve_info* inf) {
         Timer tm(c, &inf->ms_orth);
         const int nv = j + 1;
         ++c->launches;
-        k_dots<<<grid_stream(n), kT, kStreamSmem, s>>>(V, ld, nv, w, n, st, R, L.h1, 0, c->d_partials, c->d_ticket);
+        FMP_CK(launch_dots(V, ld, nv, w, n, st, R, L.h1, 0, c, s));
         ++c->launches;
-        k_update<<<grid_stream(n), kT, kStreamSmem, s>>>(V, ld, nv, w, n, st, R, j, 0, c->d_partials, c->d_ticket);
+        FMP_CK(launch_update(V, ld, nv, w, n, st, R, j, 0, c, s));
         ++c->launches;
-        k_dots<<<grid_stream(n), kT, kStreamSmem, s>>>(V, ld, nv, w, n, st, R, L.h2, 1, c->d_partials, c->d_ticket);
+        FMP_CK(launch_dots(V, ld, nv, w, n, st, R, L.h2, 1, c, s));
         ++c->launches;
-        k_update<<<grid_stream(n), kT, kStreamSmem, s>>>(V, ld, nv, w, n, st, R, j, 1, c->d_partials, c->d_ticket);
+        FMP_CK(launch_update(V, ld, nv, w, n, st, R, j, 1, c, s));
         ++c->launches;
         k_scale_next<<<grid_n(n), kT, 0, s>>>(w, n, st, R, j);
         FMP_CK(cudaGetLastError());
@@ -643,12 +622,8 @@ int run_cycle_graph(fmp_ctx* c) {
 
 }  // namespace
 
-// Opt the streamed kernels into their dynamic shared memory (at set-up).
-cudaError_t fmp_krylov_init() {
-    cudaError_t e = cudaFuncSetAttribute(k_dots, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStreamSmem);
-    if (e) return e;
-    return cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStreamSmem);
-}
+// Nothing to configure at set-up: the basis passes use static shared memory.
+cudaError_t fmp_krylov_init() { return cudaSuccess; }
 
 cudaError_t fmp_ensure_krylov(fmp_ctx* c) {
     const int R = c->opt.restart;
@@ -742,7 +717,6 @@ int fmp_fgmres(fmp_ctx* c, const double* b, double* x, fmp_solve_info* info) {
         inf.restarts++;
         inf.est_rel_res = hp[SC_EST];
         const int ds = (int)hp[SC_STATUS];
-        if (hp[SC_KERR] != 0.0) return fmp_latch(c, cudaErrorLaunchTimeout);
         if (ds == DS_NONFINITE) { status = FMP_ERR_NONFINITE; break; }
         if (ds == DS_BREAK) {
             FMP_CK(residual(c, b, x, V));

@@ -14,7 +14,7 @@
 // The kernels are memory bound: one thread per cell computes the three
 // components, x-fastest so warps read 256-byte rows; neighbour reads hit L1/L2.
 #include "fmp_internal.h"
-#include "bulk.cuh"
+#include "cp_async.cuh"
 
 namespace {
 
