@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define FMP_ABI_VERSION 1
+#define FMP_ABI_VERSION 2
 
 typedef struct fmp_ctx fmp_ctx; /* opaque, library-owned */
 
@@ -158,11 +158,24 @@ int fmp_get_launch_count(fmp_ctx* ctx, long long* n);
 int fmp_set_tuning(fmp_ctx* ctx, int slab_group, int tile_group);
 int fmp_get_tuning(fmp_ctx* ctx, int* slab_group, int* tile_group);
 
+/* Fused reduced-precision box solve (not in the paper; Algorithm 1 as one
+ * thread-block cluster of three CTAs per box, the box resident in shared
+ * memory): for bf16 and fp16, boxes whose extents are all <= max_extent take
+ * it, the others the three-pass kernels. max_extent in [0, 40]; 0 turns it
+ * off; default 40. tf32 always runs the three-pass kernels. Results agree
+ * within the reduced-precision error, not bitwise. */
+int fmp_set_fused(fmp_ctx* ctx, int max_extent);
+/* Current max_extent and (n_fused may be NULL) the number of fused boxes;
+ * HOST outputs. */
+int fmp_get_fused(fmp_ctx* ctx, int* max_extent, int* n_fused);
+
 /* Autotuner: time `reps` reduced-precision preconditioner applies (precision
- * FMP_PREC_TF32, _FP16 or _BF16) for every grouping in {1,2,4,8} x {1,2,4,8}
- * with CUDA events on the context's stream, keep the fastest, and return
- * result[0] = slab group, result[1] = tile group, result[2] = microseconds per
- * apply (HOST int[3]). Uses the context's own buffers; synchronises. */
+ * FMP_PREC_TF32, _FP16 or _BF16) with CUDA events on the context's stream for
+ * the fused kernel on and off (bf16 / fp16) and every grouping in
+ * {1,2,4,8} x {1,2,4,8} of the boxes left to the three-pass kernels, keep the
+ * fastest, and return result[0] = slab group, result[1] = tile group,
+ * result[2] = microseconds per apply, result[3] = fused max_extent (HOST
+ * int[4]). Uses the context's own buffers; synchronises. */
 int fmp_autotune(fmp_ctx* ctx, int precision, int reps, int* result);
 
 /* Number of subdomain boxes. */

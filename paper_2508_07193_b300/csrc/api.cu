@@ -111,35 +111,56 @@ void build_items(const std::vector<FmpBox>& boxes, int ct, std::vector<int4>& A,
     }
 }
 
-// Grouped work lists of the reduced-precision passes: sg z-slabs per CTA in
-// passes A and C, tg column tiles of ct columns per CTA in pass B.
-void group_items(const std::vector<FmpBox>& boxes, int ct, int sg, int tg, std::vector<int4>& GA,
-                 std::vector<int4>& GB, std::vector<int4>& GC) {
-    for (int b = 0; b < (int)boxes.size(); ++b) {
-        const FmpBox& x = boxes[b];
-        for (int c = 0; c < 3; ++c) {
-            for (int z = 0; z < x.m[2]; z += sg) GA.push_back(make_int4(b, c, z, std::min(sg, x.m[2] - z)));
-            const int o0 = x.own_lo[2], o1 = x.own_lo[2] + x.own_n[2];
-            for (int z = o0; z < o1; z += sg) GC.push_back(make_int4(b, c, z, std::min(sg, o1 - z)));
+// A box goes to the fused cluster kernel when all its extents are <= fmax.
+bool fusable(const FmpBox& x, int fmax) {
+    return fmax > 0 && x.m[0] <= fmax && x.m[1] <= fmax && x.m[2] <= fmax;
+}
+
+// Grouped work lists of the three-pass reduced-precision kernels: sg z-slabs
+// per CTA in passes A and C, tg column tiles of ct columns per CTA in pass B.
+// Boxes left to these kernels come first (rest[0..2] items), then the boxes
+// that the fused kernel takes for bf16 / fp16 (F lists them; tf32 still runs
+// the whole lists).
+void group_items(const std::vector<FmpBox>& boxes, int ct, int sg, int tg, int fmax, std::vector<int4>& GA,
+                 std::vector<int4>& GB, std::vector<int4>& GC, std::vector<int>& F, int (&rest)[3]) {
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int b = 0; b < (int)boxes.size(); ++b) {
+            const FmpBox& x = boxes[b];
+            if (fusable(x, fmax) != (pass == 1)) continue;
+            if (pass == 1) F.push_back(b);
+            for (int c = 0; c < 3; ++c) {
+                for (int z = 0; z < x.m[2]; z += sg) GA.push_back(make_int4(b, c, z, std::min(sg, x.m[2] - z)));
+                const int o0 = x.own_lo[2], o1 = x.own_lo[2] + x.own_n[2];
+                for (int z = o0; z < o1; z += sg) GC.push_back(make_int4(b, c, z, std::min(sg, o1 - z)));
+            }
+            const int nxy = x.m[0] * x.m[1], span = ct * tg;
+            for (int q = 0; q < nxy; q += span) GB.push_back(make_int4(b, q, std::min(span, nxy - q), 0));
         }
-        const int nxy = x.m[0] * x.m[1], span = ct * tg;
-        for (int q = 0; q < nxy; q += span) GB.push_back(make_int4(b, q, std::min(span, nxy - q), 0));
+        if (pass == 0) { rest[0] = (int)GA.size(); rest[1] = (int)GB.size(); rest[2] = (int)GC.size(); }
     }
 }
 
-// Rebuild only the grouped lists for a new (sg, tg).
-cudaError_t regroup(FmpPlan& p, const std::vector<FmpBox>& boxes, int sg, int tg, cudaStream_t s) {
+// Rebuild only the grouped and fused lists for a new (sg, tg, fmax).
+cudaError_t regroup(FmpPlan& p, const std::vector<FmpBox>& boxes, int sg, int tg, int fmax, cudaStream_t s) {
     std::vector<int4> GA, GB, GC;
-    group_items(boxes, fmp_column_tile(p.max_m), sg, tg, GA, GB, GC);
+    std::vector<int> F;
+    int rest[3];
+    group_items(boxes, fmp_column_tile(p.max_m), sg, tg, fmax, GA, GB, GC, F, rest);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e) return e;
-    cudaFree(p.d_items_ga); cudaFree(p.d_items_gb); cudaFree(p.d_items_gc);
+    cudaFree(p.d_items_ga); cudaFree(p.d_items_gb); cudaFree(p.d_items_gc); cudaFree(p.d_items_f);
     p.d_items_ga = p.d_items_gb = p.d_items_gc = nullptr;
-    p.slab_group = sg; p.tile_group = tg;
+    p.d_items_f = nullptr;
+    p.slab_group = sg; p.tile_group = tg; p.fused_max = fmax;
     p.n_items_ga = (int)GA.size(); p.n_items_gb = (int)GB.size(); p.n_items_gc = (int)GC.size();
+    p.n_ga_rest = rest[0]; p.n_gb_rest = rest[1]; p.n_gc_rest = rest[2];
+    p.n_items_f = (int)F.size();
+    p.fused_yz_max = 0;
+    for (int b : F) p.fused_yz_max = std::max(p.fused_yz_max, std::max(boxes[b].m[1], boxes[b].m[2]));
     if ((e = upload(&p.d_items_ga, GA, s))) return e;
     if ((e = upload(&p.d_items_gb, GB, s))) return e;
-    return upload(&p.d_items_gc, GC, s);
+    if ((e = upload(&p.d_items_gc, GC, s))) return e;
+    return F.empty() ? cudaSuccess : upload(&p.d_items_f, F, s);
 }
 
 cudaError_t make_plan(FmpPlan& p, const std::vector<FmpBox>& boxes, cudaStream_t s) {
@@ -156,23 +177,17 @@ cudaError_t make_plan(FmpPlan& p, const std::vector<FmpBox>& boxes, cudaStream_t
     const int ct = fmp_column_tile(p.max_m);
     build_items(boxes, ct, A, B, C);
     p.n_items_a = (int)A.size(); p.n_items_b = (int)B.size(); p.n_items_c = (int)C.size();
-    std::vector<int4> GA, GB, GC;
-    group_items(boxes, ct, p.slab_group, p.tile_group, GA, GB, GC);
-    p.n_items_ga = (int)GA.size(); p.n_items_gb = (int)GB.size(); p.n_items_gc = (int)GC.size();
     cudaError_t e;
     if ((e = upload(&p.d_boxes, boxes, s))) return e;
     if ((e = upload(&p.d_items_a, A, s))) return e;
     if ((e = upload(&p.d_items_b, B, s))) return e;
     if ((e = upload(&p.d_items_c, C, s))) return e;
-    if ((e = upload(&p.d_items_ga, GA, s))) return e;
-    if ((e = upload(&p.d_items_gb, GB, s))) return e;
-    if ((e = upload(&p.d_items_gc, GC, s))) return e;
-    return cudaSuccess;
+    return regroup(p, boxes, p.slab_group, p.tile_group, p.fused_max, s);
 }
 
 void free_plan(FmpPlan& p) {
     cudaFree(p.d_boxes); cudaFree(p.d_items_a); cudaFree(p.d_items_b); cudaFree(p.d_items_c);
-    cudaFree(p.d_items_ga); cudaFree(p.d_items_gb); cudaFree(p.d_items_gc);
+    cudaFree(p.d_items_ga); cudaFree(p.d_items_gb); cudaFree(p.d_items_gc); cudaFree(p.d_items_f);
     p = FmpPlan{};
 }
 
@@ -194,10 +209,24 @@ int fmp_precond_gated(fmp_ctx* c, const double* r, double* z, const double* gate
         case FMP_PREC_FP16:
         case FMP_PREC_TF32: {
             const int w = c->opt.precision == FMP_PREC_BF16 ? 0 : c->opt.precision == FMP_PREC_FP16 ? 1 : 2;
-            c->launches += c->opt.precision == FMP_PREC_FP16 ? 4 : 3;
-            FMP_CK(fmp_launch_transform_solve_mixed(c->opt.precision, c->ras, c->d_tab_mp[w], c->d_tabs, r, z,
-                                                    c->d_scratch, c->d_bscale, c->nx, c->ny, c->nz, c->beta,
-                                                    c->stream, gate));
+            const FmpPlan& p = c->ras;
+            // bf16 / fp16: boxes of the fused list go through one cluster each,
+            // the rest through the three-pass kernels; tf32: all three-pass
+            const bool fused = c->opt.precision != FMP_PREC_TF32 && p.n_items_f > 0;
+            const int na = fused ? p.n_ga_rest : p.n_items_ga, nb = fused ? p.n_gb_rest : p.n_items_gb,
+                      nc = fused ? p.n_gc_rest : p.n_items_gc;
+            if (na + nb + nc > 0) {
+                int nk = 0;
+                FMP_CK(fmp_launch_transform_solve_mixed(c->opt.precision, p, c->d_tab_mp[w], c->d_tabs, r, z,
+                                                        c->d_scratch, c->d_bscale, c->nx, c->ny, c->nz, c->beta,
+                                                        c->stream, gate, na, nb, nc, &nk));
+                c->launches += nk;
+            }
+            if (fused) {
+                ++c->launches;
+                FMP_CK(fmp_launch_fused(c->opt.precision, p, c->d_tab_mp[w], c->d_tabs, r, z, c->nx, c->ny, c->nz,
+                                        c->beta, c->stream, gate));
+            }
             return FMP_OK;
         }
         default:
@@ -388,6 +417,7 @@ int fmp_setup(fmp_ctx** out, fmp_grid g, const double* eps_cell, double beta, co
     SETUP_CK(make_plan(c->ras, boxes, c->stream));
     SETUP_CK(fmp_transform_init_fp64(c->ras));
     SETUP_CK(fmp_transform_init_mixed(c->ras));
+    SETUP_CK(fmp_fused_init());
     SETUP_CK(cudaMalloc(&c->d_bscale, sizeof(double) * boxes.size()));
     SETUP_CK(fmp_krylov_init());
     SETUP_CK(fmp_launch_eps_bar(c->d_eps_edge, c->ras.d_boxes, c->ras.n_boxes, g.nx, g.ny, g.nz, c->stream));
@@ -459,8 +489,24 @@ int fmp_set_tuning(fmp_ctx* c, int slab_group, int tile_group) {
     if (!valid_ctx(c) || slab_group < 1 || slab_group > 64 || tile_group < 1 || tile_group > 64) return FMP_ERR_ARG;
     if (int rc = latched(c)) return rc;
     if (slab_group == c->ras.slab_group && tile_group == c->ras.tile_group) return FMP_OK;
-    FMP_CK(regroup(c->ras, c->h_boxes, slab_group, tile_group, c->stream));
+    FMP_CK(regroup(c->ras, c->h_boxes, slab_group, tile_group, c->ras.fused_max, c->stream));
     c->graph_valid = false;
+    return FMP_OK;
+}
+
+int fmp_set_fused(fmp_ctx* c, int max_extent) {
+    if (!valid_ctx(c) || max_extent < 0 || max_extent > FMP_FUSED_MAX) return FMP_ERR_ARG;
+    if (int rc = latched(c)) return rc;
+    if (max_extent == c->ras.fused_max) return FMP_OK;
+    FMP_CK(regroup(c->ras, c->h_boxes, c->ras.slab_group, c->ras.tile_group, max_extent, c->stream));
+    c->graph_valid = false;
+    return FMP_OK;
+}
+
+int fmp_get_fused(fmp_ctx* c, int* max_extent, int* n_fused) {
+    if (!valid_ctx(c) || !max_extent) return FMP_ERR_ARG;
+    *max_extent = c->ras.fused_max;
+    if (n_fused) *n_fused = c->ras.n_items_f;
     return FMP_OK;
 }
 
@@ -479,30 +525,38 @@ int fmp_autotune(fmp_ctx* c, int precision, int reps, int* result) {
     const int saved = c->opt.precision;
     c->opt.precision = precision;
     float best = 1e30f;
-    int bs = c->ras.slab_group, bt = c->ras.tile_group;
+    int bs = c->ras.slab_group, bt = c->ras.tile_group, bf = c->ras.fused_max;
     cudaEvent_t e0 = c->ev[4], e1 = c->ev[5];
-    for (int a = 0; a < 4; ++a)
-        for (int b = 0; b < 4; ++b) {
-            FMP_CK(regroup(c->ras, c->h_boxes, cand[a], cand[b], c->stream));
-            int rc = fmp_precond(c, c->d_eps_edge, c->d_tmp2);   // warm-up; any nonzero field will do
-            if (rc != FMP_OK) { c->opt.precision = saved; return rc; }
-            FMP_CK(cudaEventRecord(e0, c->stream));
-            for (int r = 0; r < reps; ++r) {
-                rc = fmp_precond(c, c->d_eps_edge, c->d_tmp2);
+    // candidates: the fused cluster kernel on (bf16 / fp16 only) or off, and
+    // for the boxes left to the three-pass kernels every grouping
+    const int nf = precision == FMP_PREC_TF32 ? 1 : 2;
+    const int fopt[2] = {precision == FMP_PREC_TF32 ? c->ras.fused_max : FMP_FUSED_MAX, 0};
+    for (int f = 0; f < nf; ++f)
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b) {
+                FMP_CK(regroup(c->ras, c->h_boxes, cand[a], cand[b], fopt[f], c->stream));
+                const bool all_fused = precision != FMP_PREC_TF32 && c->ras.n_ga_rest == 0 && c->ras.n_items_f > 0;
+                if (all_fused && (a > 0 || b > 0)) continue;   // the grouping does not apply
+                int rc = fmp_precond(c, c->d_eps_edge, c->d_tmp2);   // warm-up; any nonzero field will do
                 if (rc != FMP_OK) { c->opt.precision = saved; return rc; }
+                FMP_CK(cudaEventRecord(e0, c->stream));
+                for (int r = 0; r < reps; ++r) {
+                    rc = fmp_precond(c, c->d_eps_edge, c->d_tmp2);
+                    if (rc != FMP_OK) { c->opt.precision = saved; return rc; }
+                }
+                FMP_CK(cudaEventRecord(e1, c->stream));
+                FMP_CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                FMP_CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) { best = ms; bs = cand[a]; bt = cand[b]; bf = fopt[f]; }
             }
-            FMP_CK(cudaEventRecord(e1, c->stream));
-            FMP_CK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            FMP_CK(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best) { best = ms; bs = cand[a]; bt = cand[b]; }
-        }
     c->opt.precision = saved;
-    FMP_CK(regroup(c->ras, c->h_boxes, bs, bt, c->stream));
+    FMP_CK(regroup(c->ras, c->h_boxes, bs, bt, bf, c->stream));
     c->graph_valid = false;
     result[0] = bs;
     result[1] = bt;
     result[2] = (int)(1000.f * best / reps);
+    result[3] = bf;
     return FMP_OK;
 }
 

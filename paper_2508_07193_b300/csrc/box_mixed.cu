@@ -353,30 +353,34 @@ k_mp_inv_xy(const void* __restrict__ scr_v, double* __restrict__ zout, const Fmp
 }
 
 // ---- fp16 scale: largest |r| over each extended box ---------------------
+// Magnitudes are compared as the sign-cleared high words of the doubles
+// (integer max, no float64 operations); the scale is that high word with a
+// zero low word, at most 2^-20 below the true maximum. All-zero or
+// non-finite boxes get 1.
 __global__ void k_mp_boxmax(const double* __restrict__ r, const FmpBox* __restrict__ boxes, double* __restrict__ out,
                             int nx, int ny, int nz, const double* __restrict__ gate) {
     if (gate && *gate != 0.0) return;
     const FmpBox B = boxes[blockIdx.x];
     const int mx = B.m[0], my = B.m[1], mz = B.m[2];
-    const long long nb = (long long)mx * my * mz;
-    double m = 0.0;
-    for (long long t = threadIdx.x; t < 3 * nb; t += blockDim.x) {
-        const int c = (int)(t / nb);
-        long long q = t - c * nb;
-        const int k = (int)(q / (mx * my));
-        q -= (long long)k * mx * my;
-        const int j = (int)(q / mx), i = (int)(q - (long long)j * mx);
-        m = fmax(m, fabs(r[(((long long)c * nz + B.ext_lo[2] + k) * ny + B.ext_lo[1] + j) * (long long)nx +
-                           B.ext_lo[0] + i]));
+    unsigned m = 0u;
+    for (int row = threadIdx.x >> 5; row < 3 * mz * my; row += blockDim.x >> 5) {
+        const int c = row / (mz * my), zy = row - c * mz * my;
+        const int z = zy / my, y = zy - z * my;
+        const unsigned* sp = reinterpret_cast<const unsigned*>(
+            r + (((long long)c * nz + B.ext_lo[2] + z) * ny + B.ext_lo[1] + y) * (long long)nx + B.ext_lo[0]);
+        for (int x = threadIdx.x & 31; x < mx; x += 32) m = max(m, __ldg(sp + 2 * x + 1) & 0x7FFFFFFFu);
     }
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
-    __shared__ double red[32];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    m = __reduce_max_sync(0xffffffffu, m);
+    __shared__ unsigned red;
+    if (threadIdx.x == 0) red = 0u;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) atomicMax(&red, m);
     __syncthreads();
     if (threadIdx.x == 0) {
-        double v = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmax(v, red[w]);
-        out[blockIdx.x] = (v > 0.0 && isfinite(v)) ? v : 1.0;
+        const unsigned hi = red;
+        out[blockIdx.x] = (hi != 0u && hi < 0x7FF00000u)
+                              ? __longlong_as_double((long long)((unsigned long long)hi << 32))
+                              : 1.0;
     }
 }
 
@@ -410,15 +414,25 @@ cudaError_t init_mp(const FmpPlan& p, int ct) {
 template <class Tr>
 cudaError_t launch_mp(const FmpPlan& p, const void* tabs, const double* tabs64, const double* r, double* z,
                       void* scratch, double* bscale, int nx, int ny, int nz, double beta, int ct, cudaStream_t s,
-                      const double* gate) {
+                      const double* gate, int na, int nb, int nc, int* nk) {
     using E = typename Tr::E;
-    if (bscale) k_mp_boxmax<<<p.n_boxes, 256, 0, s>>>(r, p.d_boxes, bscale, nx, ny, nz, gate);
-    k_mp_fwd_xy<Tr><<<p.n_items_ga, kT, smem_mp_a<E>(p.max_m), s>>>(r, scratch, p.d_boxes, p.d_items_ga, tabs,
-                                                                    bscale, nx, ny, nz, gate);
-    k_mp_z_solve<Tr><<<p.n_items_gb, kT, smem_mp_b<E>(p.max_m, ct), s>>>(scratch, p.d_boxes, p.d_items_gb, tabs,
-                                                                          tabs64, beta, ct, gate);
-    k_mp_inv_xy<Tr><<<p.n_items_gc, kT, smem_mp_c<E>(p.max_m), s>>>(scratch, z, p.d_boxes, p.d_items_gc, tabs,
-                                                                    bscale, nx, ny, nz, gate);
+    *nk = 0;
+    if (bscale) { k_mp_boxmax<<<p.n_boxes, 256, 0, s>>>(r, p.d_boxes, bscale, nx, ny, nz, gate); ++*nk; }
+    if (na > 0) {
+        k_mp_fwd_xy<Tr><<<na, kT, smem_mp_a<E>(p.max_m), s>>>(r, scratch, p.d_boxes, p.d_items_ga, tabs, bscale, nx,
+                                                              ny, nz, gate);
+        ++*nk;
+    }
+    if (nb > 0) {
+        k_mp_z_solve<Tr><<<nb, kT, smem_mp_b<E>(p.max_m, ct), s>>>(scratch, p.d_boxes, p.d_items_gb, tabs, tabs64,
+                                                                    beta, ct, gate);
+        ++*nk;
+    }
+    if (nc > 0) {
+        k_mp_inv_xy<Tr><<<nc, kT, smem_mp_c<E>(p.max_m), s>>>(scratch, z, p.d_boxes, p.d_items_gc, tabs, bscale, nx,
+                                                              ny, nz, gate);
+        ++*nk;
+    }
     return cudaGetLastError();
 }
 
@@ -436,15 +450,19 @@ cudaError_t fmp_transform_init_mixed(const FmpPlan& p) {
 
 cudaError_t fmp_launch_transform_solve_mixed(int precision, const FmpPlan& p, const void* tabs, const double* tabs64,
                                              const double* r, double* z, void* scratch, double* bscale, int nx,
-                                             int ny, int nz, double beta, cudaStream_t s, const double* gate) {
+                                             int ny, int nz, double beta, cudaStream_t s, const double* gate, int na,
+                                             int nb, int nc, int* nk) {
     const int ct = fmp_column_tile(p.max_m);
     switch (precision) {
         case FMP_PREC_BF16:
-            return launch_mp<BF16T>(p, tabs, tabs64, r, z, scratch, nullptr, nx, ny, nz, beta, ct, s, gate);
+            return launch_mp<BF16T>(p, tabs, tabs64, r, z, scratch, nullptr, nx, ny, nz, beta, ct, s, gate, na, nb,
+                                    nc, nk);
         case FMP_PREC_FP16:
-            return launch_mp<FP16T>(p, tabs, tabs64, r, z, scratch, bscale, nx, ny, nz, beta, ct, s, gate);
+            return launch_mp<FP16T>(p, tabs, tabs64, r, z, scratch, bscale, nx, ny, nz, beta, ct, s, gate, na, nb, nc,
+                                    nk);
         case FMP_PREC_TF32:
-            return launch_mp<TF32T>(p, tabs, tabs64, r, z, scratch, nullptr, nx, ny, nz, beta, ct, s, gate);
+            return launch_mp<TF32T>(p, tabs, tabs64, r, z, scratch, nullptr, nx, ny, nz, beta, ct, s, gate, na, nb,
+                                    nc, nk);
         default:
             return cudaErrorInvalidValue;
     }

@@ -13,6 +13,7 @@
 #define FMP_MAX_RESTART 32
 #define FMP_MP_SLAB_GROUP 4   // z-slabs per CTA in the reduced-precision passes A and C
 #define FMP_MP_TILE_GROUP 4   // column tiles per CTA in the reduced-precision pass B
+#define FMP_FUSED_MAX 40      // largest extent of a box solved by the fused cluster kernel
 
 // Device-side descriptor of one subdomain box (Sec. II-B). Coordinates are
 // in cells, ordered (x, y, z).
@@ -77,10 +78,17 @@ struct FmpPlan {
     int n_items_gb = 0;
     int4* d_items_gc = nullptr;
     int n_items_gc = 0;
+    // The grouped lists hold the boxes left to the three-pass kernels first
+    // (n_g*_rest items), then the boxes of the fused list.
+    int n_ga_rest = 0, n_gb_rest = 0, n_gc_rest = 0;
+    int* d_items_f = nullptr;   // boxes solved by one fused cluster each (bf16 / fp16)
+    int n_items_f = 0;
+    int fused_yz_max = 0;       // largest y or z extent among them
     int max_m[3] = {0, 0, 0};
     long long scratch_doubles = 0;
     int slab_group = FMP_MP_SLAB_GROUP;   // tuning of the grouped lists
     int tile_group = FMP_MP_TILE_GROUP;
+    int fused_max = FMP_FUSED_MAX;        // boxes with every extent <= this are fused (0: none)
 };
 
 struct FmpCnn;
@@ -153,9 +161,18 @@ cudaError_t fmp_launch_h_update(double* H, const double* En, const double* Eo, d
                                 int nx, int ny, int nz, cudaStream_t s);
 
 cudaError_t fmp_transform_init_mixed(const FmpPlan& p);
+// Three-pass reduced-precision solve of the first na / nb / nc grouped items
+// (all of them for tf32; the non-fused boxes for bf16 / fp16). fp16 first
+// computes every box's scale into bscale. Returns the kernels launched in *nk.
 cudaError_t fmp_launch_transform_solve_mixed(int precision, const FmpPlan& p, const void* tabs, const double* tabs64,
                                              const double* r, double* z, void* scratch, double* bscale, int nx,
-                                             int ny, int nz, double beta, cudaStream_t s, const double* gate);
+                                             int ny, int nz, double beta, cudaStream_t s, const double* gate, int na,
+                                             int nb, int nc, int* nk);
+cudaError_t fmp_fused_init();
+// bf16 / fp16 solve of the boxes of the fused list, one cluster of three CTAs
+// each (fp16 computes its per-box scale inside).
+cudaError_t fmp_launch_fused(int precision, const FmpPlan& p, const void* tabs, const double* tabs64, const double* r,
+                             double* z, int nx, int ny, int nz, double beta, cudaStream_t s, const double* gate);
 
 // Krylov building blocks (krylov.cu)
 int fmp_fgmres(fmp_ctx* c, const double* b, double* x, fmp_solve_info* info);

@@ -85,6 +85,8 @@ def lib():
         "fmp_set_tuning": (_I, [_P, _I, _I]),
         "fmp_get_tuning": (_I, [_P, C.POINTER(_I), C.POINTER(_I)]),
         "fmp_autotune": (_I, [_P, _I, _I, C.POINTER(_I)]),
+        "fmp_set_fused": (_I, [_P, _I]),
+        "fmp_get_fused": (_I, [_P, C.POINTER(_I), C.POINTER(_I)]),
         "fmp_get_box": (_I, [_P, _I, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I),
                              C.POINTER(_D)]),
         "fmp_curlcurl_apply": (_I, [_P, _P, _P, _D, _D]),
@@ -242,10 +244,19 @@ class Context:
         _check(lib().fmp_get_tuning(self._h, C.byref(a), C.byref(b)), "fmp_get_tuning")
         return a.value, b.value
 
+    def set_fused(self, max_extent):
+        _check(lib().fmp_set_fused(self._h, int(max_extent)), "fmp_set_fused")
+
+    def get_fused(self):
+        a, n = C.c_int(), C.c_int()
+        _check(lib().fmp_get_fused(self._h, C.byref(a), C.byref(n)), "fmp_get_fused")
+        return a.value, n.value
+
     def autotune(self, precision="bf16", reps=5, cache=None):
-        """Pick the fastest work-list grouping for `precision` (fmp_autotune),
-        cached in the JSON file `cache` keyed by GPU name, grid, partition and
-        precision."""
+        """Pick the fastest fused setting and work-list grouping for
+        `precision` (fmp_autotune), cached in the JSON file `cache` keyed by
+        GPU name, grid, partition and precision. Returns (slab group, tile
+        group, microseconds per apply, fused max extent)."""
         import json
         key = None
         if cache:
@@ -256,13 +267,14 @@ class Context:
                     table = json.load(f)
             except (OSError, ValueError):
                 table = {}
-            if key in table:
+            if key in table and len(table[key]) == 4:
                 self.set_tuning(*table[key][:2])
+                self.set_fused(table[key][3])
                 return tuple(table[key])
-        res = (C.c_int * 3)()
+        res = (C.c_int * 4)()
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         _check(lib().fmp_autotune(self._h, p, int(reps), res), "fmp_autotune")
-        out = (res[0], res[1], res[2])
+        out = (res[0], res[1], res[2], res[3])
         if cache:
             try:
                 with open(cache) as f:

@@ -22,10 +22,15 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("fused", [40, 0], ids=["fused", "three_pass"])
 @pytest.mark.parametrize("prec", ["bf16", "fp16", "tf32"])
 @pytest.mark.parametrize("w", CASES, ids=lambda w: "x".join(map(str, w.grid)))
-def test_mixed_precond_error(prec, w):
+def test_mixed_precond_error(prec, w, fused):
+    if prec == "tf32" and fused:
+        pytest.skip("tf32 always runs the three-pass kernels")
     ctx = context(w, precision=prec)
+    ctx.set_fused(fused)
+    assert ctx.get_fused() == (fused, ctx.num_boxes() if fused else 0)
     ee = yee.edge_eps(w.grid, w.eps_cell)
     ref = ras.precond_apply(w.rhs, ras.partition(w.grid, w.cuts, w.overlap), ee, w.beta)
     z = host(ctx.precond_apply(dev(w.rhs)))
@@ -75,6 +80,8 @@ def test_grouping_changes_speed_not_results_and_autotune_picks_one(tmp_path):
     w = wl.small(grid=(24, 24, 24), cuts=((8, 8, 8),) * 3, overlap=3, seed=22, n_eps_boxes=6)
     ctx = context(w, precision="bf16")
     r = dev(w.rhs)
+    zf = host(ctx.precond_apply(r))          # fused (default): the grouping does not apply
+    ctx.set_fused(0)
     ctx.set_tuning(1, 1)
     z1 = host(ctx.precond_apply(r))
     ctx.set_tuning(8, 3)
@@ -82,8 +89,40 @@ def test_grouping_changes_speed_not_results_and_autotune_picks_one(tmp_path):
     z2 = host(ctx.precond_apply(r))
     assert np.array_equal(z1, z2)
     cache = str(tmp_path / "tune.json")
-    sg, tg, us = ctx.autotune("bf16", reps=2, cache=cache)
-    assert sg in (1, 2, 4, 8) and tg in (1, 2, 4, 8) and us > 0
-    assert ctx.get_tuning() == (sg, tg)
-    assert ctx.autotune("bf16", cache=cache) == (sg, tg, us)    # served from the cache
-    assert np.array_equal(host(ctx.precond_apply(r)), z1)
+    sg, tg, us, fm = ctx.autotune("bf16", reps=2, cache=cache)
+    assert sg in (1, 2, 4, 8) and tg in (1, 2, 4, 8) and us > 0 and fm in (0, 40)
+    assert ctx.get_tuning() == (sg, tg) and ctx.get_fused()[0] == fm
+    assert ctx.autotune("bf16", cache=cache) == (sg, tg, us, fm)    # served from the cache
+    assert np.array_equal(host(ctx.precond_apply(r)), zf if fm else z1)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_fused_and_three_pass_boxes_in_one_apply(prec):
+    """x cuts (20, 60) with overlap 2 give boxes of extent 22 (fused) and 62
+    (three-pass) in the same preconditioner apply."""
+    w = wl.small(grid=(80, 24, 16), cuts=((20, 60), (12, 12), (16,)), overlap=2, seed=23, n_eps_boxes=5)
+    ctx = context(w, precision=prec)
+    assert ctx.get_fused() == (40, 2)
+    ee = yee.edge_eps(w.grid, w.eps_cell)
+    ref = ras.precond_apply(w.rhs, ras.partition(w.grid, w.cuts, w.overlap), ee, w.beta)
+    z = host(ctx.precond_apply(dev(w.rhs)))
+    assert rel(z, ref) <= BOUND[prec]
+    assert np.all(z[wl.edge_wall_mask(w.grid)] == 0.0)
+    ctx.set_fused(0)
+    z3 = host(ctx.precond_apply(dev(w.rhs)))
+    assert rel(z3, ref) <= BOUND[prec]
+
+
+def test_fused_box_extents_one_to_forty():
+    """Boxes of every extent class of the fused kernel: single cells, odd
+    extents, extents that are and are not multiples of 8 and 16, up to 40."""
+    for grid, cuts, ov in (((40, 40, 40), ((40,),) * 3, 0), ((9, 3, 17), ((9,), (3,), (17,)), 0),
+                           ((38, 30, 22), ((19, 19), (15, 15), (11, 11)), 2)):
+        w = wl.small(grid=grid, cuts=cuts, overlap=ov, seed=24, n_eps_boxes=3)
+        ctx = context(w, precision="bf16")
+        assert ctx.get_fused()[1] == ctx.num_boxes()
+        ee = yee.edge_eps(w.grid, w.eps_cell)
+        ref = ras.precond_apply(w.rhs, ras.partition(w.grid, w.cuts, w.overlap), ee, w.beta)
+        z = host(ctx.precond_apply(dev(w.rhs)))
+        assert rel(z, ref) <= BOUND["bf16"], grid
+        ctx.close()
