@@ -33,6 +33,15 @@ METRIC = "CN-FDTD step time to 1e-8 residual; subdomain DoF/s vs plain FP64 form
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_NOMINAL_TFLOPS = 1.25   # B300 float64 (vector and tensor) nominal
 
+# dram__bytes_read.sum + dram__bytes_write.sum of one preconditioner apply
+# (all of its kernels) from an ncu capture of the current kernels, per
+# (workload, precision); the capture is summarised in the profiles/ file named
+# beside each entry. Absent: not captured for this kernel version.
+TRAFFIC_BYTES = {
+    ("yee128_ras4x4x4_ol2", "fp64"): 209.6e6,   # transform_fp64_precond_grid128.md
+    ("yee128_ras4x4x4_ol2", "bf16"): 53.34e6,   # fused_bf16_precond_grid128.md
+}
+
 
 def parse():
     p = argparse.ArgumentParser()
@@ -45,6 +54,7 @@ def parse():
     p.add_argument("--graph", action="store_true", help="replay each FGMRES restart cycle as one CUDA graph")
     p.add_argument("--autotune", action="store_true", help="autotune the reduced-precision work lists first")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-forms", action="store_true", help="skip timing the other preconditioner precisions")
     p.add_argument("--case", default="step", choices=["step", "precond", "spmv"],
                    help="precond/spmv: only W + K applies of that operator (for profiler captures)")
     p.add_argument("--workload", default="grid128", choices=["grid128", "grid256", "uneven"])
@@ -139,6 +149,66 @@ def transform_bytes(ctx):
         tot += 3 * mx * my * mz * 8
     nx, ny, nz = ctx.grid
     return tot + 3 * nx * ny * nz * 8
+
+
+def _fold(m, dst):
+    """Even/odd folding of a DCT-II (dst False) or zero-padded DST-I table of
+    extent m: (offset, pairs, middle, sym rows, anti rows, sym length)."""
+    off = 1 if dst else 0
+    npair, mid = (m - off) // 2, (m - off) & 1
+    s0 = 1 if dst else 0
+    nks, nka = (m - s0 + 1) // 2, (m - (1 - s0) + 1) // 2
+    return off, npair, mid, nks, nka, npair + mid
+
+
+def transform_fp64_executed(ctx):
+    """Float64 operations the folded transform kernels execute per apply:
+    the half-size sym/anti products of each forward line, the pair products of
+    each inverse line (pairs with both outputs outside the owned range are
+    skipped), the fold additions and about 19 operations per mode for the
+    closed-form 3x3 (its reciprocal included)."""
+    tot = 0
+    for i in range(ctx.num_boxes()):
+        bx = ctx.box(i)
+        m = bx["m"]
+        lo = [bx["own_lo"][a] - bx["ext_lo"][a] for a in range(3)]
+        hi = [lo[a] + bx["own_n"][a] for a in range(3)]
+        mx, my, mz = m
+
+        def fwd(ma, dst):
+            _, _, _, nks, nka, la = _fold(ma, dst)
+            return nks * la + nka * (la - (_fold(ma, dst)[2])), la + _fold(ma, dst)[1]
+
+        def inv(ma, dst, a):
+            off, npair, mid, nks, nka, _ = _fold(ma, dst)
+            q0 = max(0, min(npair, min(lo[a] - off, ma - hi[a])))
+            return (npair - q0) * (nks + nka) + mid * nks
+
+        for c in range(3):
+            sx, sy, sz = c != 0, c != 1, c != 2
+            slabs = mz - (1 if c != 2 else 0)
+            fx, ax = fwd(mx, sx)
+            fy, ay = fwd(my, sy)
+            tot += slabs * (my * (fx + ax) + mx * (fy + ay))           # pass A
+            fz, az = fwd(mz, sz)
+            tot += mx * my * (fz + az + inv(mz, sz, 2))                  # pass B (z)
+            own_z = hi[2] - lo[2]
+            tot += own_z * (mx * inv(my, sy, 1) + (hi[1] - lo[1]) * inv(mx, sx, 0))   # pass C
+        tot += 19 * mx * my * mz                                         # 3x3 per mode
+    return tot
+
+
+def orth_flops(n, iters, restart=30):
+    """Float64 flops of classical Gram-Schmidt over FGMRES(restart) for
+    `iters` Arnoldi steps: per step j of a cycle, <V_i, w> and <w, w>
+    (2 (j + 2) n), w -= V h with ||w||^2 (2 (j + 2) n) and the scaling of
+    v_{j+1} (n); re-orthogonalisation passes are not counted."""
+    tot, done = 0, 0
+    while done < iters:
+        for j in range(min(restart, iters - done)):
+            tot += 4 * (j + 2) * n + n
+        done += restart
+    return tot
 
 
 def oracle_iteration_seconds(w, n_boxes=None, basis=15):
@@ -292,35 +362,51 @@ def run_ours(args):
     spmv_bytes = 72 * nx * ny * nz      # per cell: read x and eps_edge, write y (3 float64 each)
     pk = peaks()
     hbm = pk.get("hbm_gbs", 6400.0)
+    tb = transform_bytes(ctx)
+    traffic = TRAFFIC_BYTES.get((w.name, args.precision))
     if args.precision == "fp64":
         achieved = flops / (ms_p * 1e-3) / 1e12
+        executed = transform_fp64_executed(ctx) * 2 / (ms_p * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
+                "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": traffic,
+                "algorithmic_bytes": tb,
                 "kernel": "float64 transform solve (passes A+B+C = one preconditioner apply)",
-                "peak_source": "B300 nominal float64 rate (measured DFMA 1.13 TFLOP/s)"}
+                "peak_source": "B300 nominal float64 rate from the recipe (measured DFMA 1.13 TFLOP/s)",
+                "executed": {"tflops": executed, "frac": executed / FP64_NOMINAL_TFLOPS,
+                             "note": "achieved counts the dense 12(mx+my+mz)mxmymz flops; the even/odd "
+                                     "folded kernels execute about half of them, executed counts those "
+                                     "(FMA = 2 flops)"}}
     else:
-        tb = transform_bytes(ctx)
         achieved = tb / (ms_p * 1e-3) / 1e9
+        kern = ("fused cluster kernel (one 3-CTA cluster per box)" if args.precision != "tf32"
+                else "three-pass kernels")
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": f"{args.precision} transform solve (one preconditioner apply)",
+                "traffic": traffic, "algorithmic_bytes": tb,
+                "kernel": f"{args.precision} transform solve, {kern} (one preconditioner apply)",
                 "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)"}
     spmv_gbs = spmv_bytes / (ms_spmv * 1e-3) / 1e9
     roof_spmv = {"bound": "hbm", "achieved": spmv_gbs, "peak": hbm, "unit": "GB/s", "frac": spmv_gbs / hbm,
                  "kernel": "k_curlcurl (SpMV)", "peak_source": "of measured"}
 
-    # -- e2e: host buffers, H2D of the rhs, D2H of the solution each step --
-    hb = torch.empty_like(b, device="cpu").pin_memory()
-    hb.copy_(b.cpu())
-    hE = torch.empty_like(hb).pin_memory()
+    # -- e2e: the step's input J from pinned host memory (H2D) and its result
+    # E back to the host (D2H), every step; one untimed pass first so that
+    # first-use costs of the copies stay out of the timed region --
+    hJ = torch.empty_like(J, device="cpu").pin_memory()
+    hJ.copy_(J.cpu())
+    hE = torch.empty_like(hJ).pin_memory()
+
+    def e2e_step():
+        J.copy_(hJ, non_blocking=True)
+        E.zero_(); H.zero_()
+        ctx.cn_step(E, H, J, dt)
+        hE.copy_(E, non_blocking=True)
+
+    e2e_step()
     torch.cuda.synchronize()
     e0.record(stream)
     n_e = max(1, min(3, args.steps))
     for _ in range(n_e):
-        b.copy_(hb, non_blocking=True)
-        torch.mul(b, -1.0 / dt, out=J)
-        E.zero_(); H.zero_()
-        ctx.cn_step(E, H, J, dt)
-        hE.copy_(E, non_blocking=True)
+        e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = e0.elapsed_time(e1) / n_e
@@ -349,8 +435,8 @@ def run_ours(args):
         "spmv_ms": ms_spmv,
         "roofline": roof,
         "roofline_spmv": roof_spmv,
-        "e2e": {"value": world * dof / (ms_e2e * 1e-3), "unit": "DoF/s", "h2d_bytes_per_step": b.numel() * 8,
-                "d2h_bytes_per_step": E.numel() * 8},
+        "e2e": {"value": world * dof / (ms_e2e * 1e-3), "unit": "DoF/s", "h2d_bytes_per_step": J.numel() * 8,
+                "d2h_bytes_per_step": E.numel() * 8, "ms_per_step": ms_e2e},
         "gpu_launches": launches,
         "tuning": list(tuning) if tuning else list(ctx.get_tuning()),
         "clocks": clocks,
@@ -361,6 +447,44 @@ def run_ours(args):
     ph = ctx.cn_step(E, H, J, dt)
     ctx.set_options(timing=False)
     out["phase_ms"] = {k: ph[k] for k in ("ms_precond", "ms_spmv", "ms_orth", "ms_total")}
+    if args.krylov == "fgmres" and ph["ms_orth"] > 0:
+        of = orth_flops(dof, ph["iters"]) / (ph["ms_orth"] * 1e-3) / 1e12
+        out["roofline_orth"] = {"bound": "alu", "achieved": of, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                                "frac": of / FP64_NOMINAL_TFLOPS,
+                                "kernel": "Gram-Schmidt basis passes k_dots / k_update / k_scale_next (one step)",
+                                "note": "one float64 FMA per 8 bytes read: the float64 pipe, not HBM, bounds them"}
+    # the other preconditioner precisions on the same workload, same protocol
+    if not args.no_forms:
+        forms = {}
+        for p in ("fp64", "bf16", "fp16", "tf32"):
+            if p == args.precision:
+                forms[p] = {"ms_per_step": ms, "iters": iters[0] if iters else None, "true_rel_res_max": true_res,
+                            "precond_ms": ms_p}
+                continue
+            ctx.set_options(precision=p)
+            infos.clear()
+            for _ in range(args.warmup):
+                step()
+            infos.clear()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(args.steps):
+                step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            fm = e0.elapsed_time(e1) / args.steps
+            for _ in range(3):
+                ctx.precond_apply(r, z)
+            e0.record(stream)
+            for _ in range(n_p):
+                ctx.precond_apply(r, z)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            forms[p] = {"ms_per_step": fm, "iters": infos[0]["iters"],
+                        "true_rel_res_max": max(i["true_rel_res"] for i in infos),
+                        "precond_ms": e0.elapsed_time(e1) / n_p}
+        ctx.set_options(precision=args.precision)
+        out["forms"] = forms
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, iters[0] if iters else 1)
     if rank == 0:
