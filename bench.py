@@ -51,7 +51,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="fp64")
     p.add_argument("--krylov", default="fgmres", choices=["fgmres", "bicgstab"])
-    p.add_argument("--graph", action="store_true", help="replay each FGMRES restart cycle as one CUDA graph")
+    p.add_argument("--no-graph", dest="graph", action="store_false",
+                   help="enqueue each Arnoldi step instead of replaying the restart cycle as one CUDA graph")
     p.add_argument("--autotune", action="store_true", help="autotune the reduced-precision work lists first")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true", help="skip timing the other preconditioner precisions")
