@@ -202,7 +202,7 @@ int fmp_precond_gated(fmp_ctx* c, const double* r, double* z, const double* gate
     switch (c->opt.precision) {
         case FMP_PREC_FP64:
             c->launches += 3;
-            FMP_CK(fmp_launch_transform_solve_fp64(c->ras, c->d_tabs, r, z, c->d_scratch, c->nx, c->ny, c->nz,
+            FMP_CK(fmp_launch_transform_solve_fp64(c->ras, c->d_tabs, c->d_modeinv, r, z, c->d_scratch, c->nx, c->ny, c->nz,
                                                    c->beta, c->stream, gate));
             return FMP_OK;
         case FMP_PREC_BF16:
@@ -379,6 +379,7 @@ int fmp_setup(fmp_ctx** out, fmp_grid g, const double* eps_cell, double beta, co
             b.mps_off[a] = off_mps[b.m[a]];
         }
         b.scr_off = scr;
+        b.inv_off = scr / 3;
         scr += 3LL * b.m[0] * b.m[1] * b.m[2];
     }
     cudaError_t e;
@@ -425,6 +426,21 @@ int fmp_setup(fmp_ctx** out, fmp_grid g, const double* eps_cell, double beta, co
                              c->stream));
     SETUP_CK(cudaStreamSynchronize(c->stream));
     c->h_boxes = boxes;
+    {   // per box and mode: 1 / (eps_bar + beta |sigma|^2), the diagonal factor of the
+        // closed-form 3x3 inverse (Eq. 12), used by the float64 pass B
+        std::vector<double> inv((size_t)(c->ras.scratch_doubles / 3));
+        for (const FmpBox& b : boxes) {
+            const double* sx = tabs.data() + b.sig_off[0];
+            const double* sy = tabs.data() + b.sig_off[1];
+            const double* sz = tabs.data() + b.sig_off[2];
+            double* o = inv.data() + b.inv_off;
+            for (int kz = 0; kz < b.m[2]; ++kz)
+                for (int ky = 0; ky < b.m[1]; ++ky)
+                    for (int kx = 0; kx < b.m[0]; ++kx)
+                        *o++ = 1.0 / (b.eps_bar + beta * (sx[kx] * sx[kx] + sy[ky] * sy[ky] + sz[kz] * sz[kz]));
+        }
+        SETUP_CK(upload(&c->d_modeinv, inv, c->stream));
+    }
     SETUP_CK(cudaMalloc(&c->d_scratch, sizeof(double) * (size_t)c->ras.scratch_doubles));
     long long big = 0;
     for (const FmpBox& b : boxes) big = std::max(big, 3LL * b.m[0] * b.m[1] * b.m[2]);
@@ -446,6 +462,7 @@ void fmp_destroy(fmp_ctx* c) {
     free_plan(c->ras);
     free_plan(c->single);
     cudaFree(c->d_eps_edge); cudaFree(c->d_tabs); cudaFree(c->d_scratch); cudaFree(c->d_scratch1);
+    cudaFree(c->d_modeinv);
     cudaFree(c->d_V); cudaFree(c->d_Z); cudaFree(c->d_w); cudaFree(c->d_tmp); cudaFree(c->d_tmp2);
     cudaFree(c->d_partials); cudaFree(c->d_state); cudaFree(c->d_ticket);
     for (int t = 0; t < 3; ++t) cudaFree(c->d_tab_mp[t]);
@@ -617,7 +634,7 @@ int fmp_box_solve(fmp_ctx* c, int i, const double* r, double* x) {
         c->single_box = i;
     }
     c->launches += 3;
-    FMP_CK(fmp_launch_transform_solve_fp64(c->single, c->d_tabs, r, x, c->d_scratch1, b.m[0], b.m[1], b.m[2],
+    FMP_CK(fmp_launch_transform_solve_fp64(c->single, c->d_tabs, c->d_modeinv, r, x, c->d_scratch1, b.m[0], b.m[1], b.m[2],
                                            c->beta, c->stream, nullptr));
     return FMP_OK;
 }

@@ -193,7 +193,8 @@ k_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox* _
 template <int CT>
 __global__ void __launch_bounds__(kThreads)
 k_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int2* __restrict__ items,
-          const double* __restrict__ tabs, double beta, const double* __restrict__ gate) {
+          const double* __restrict__ tabs, const double* __restrict__ modeinv, double beta,
+          const double* __restrict__ gate) {
     if (gate && *gate != 0.0) return;
     extern __shared__ double sm[];
     const int2 it = items[blockIdx.x];
@@ -247,8 +248,10 @@ k_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int2
     const double* sgx = tabs + B.sig_off[0];
     const double* sgy = tabs + B.sig_off[1];
     const double* sgz = tabs + B.sig_off[2];
-    const double eb = B.eps_bar;
-    const double beb = beta / eb;
+    // e_c = inv (r_c + (beta / eps_bar) sigma_c (sigma . r)), inv = 1 / (eps_bar
+    // + beta |sigma|^2) read from the per-box mode table
+    const double beb = beta / B.eps_bar;
+    const double* inv_tab = modeinv + B.inv_off + col0;
     for (int t = threadIdx.x; t < mz * CT; t += blockDim.x) {
         const int kz = t / CT, col = t - kz * CT;
         if (col >= ncol) continue;
@@ -257,13 +260,12 @@ k_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int2
         const double sx = sgx[kx], sy = sgy[ky], sz = sgz[kz];
         double* o = Buf + kz * CT + col;
         const double r0 = o[0], r1 = o[mz * CT], r2 = o[2 * mz * CT];
+        const double inv = inv_tab[(long long)kz * nxy + col];
         const double sr = fma(sx, r0, fma(sy, r1, sz * r2));
-        const double s2 = fma(sx, sx, fma(sy, sy, sz * sz));
-        const double inv = 1.0 / fma(beta, s2, eb);
-        const double f = beb * sr;
-        o[0] = fma(f, sx, r0) * inv;
-        o[mz * CT] = fma(f, sy, r1) * inv;
-        o[2 * mz * CT] = fma(f, sz, r2) * inv;
+        const double f = (beb * inv) * sr;
+        o[0] = fma(f, sx, inv * r0);
+        o[mz * CT] = fma(f, sy, inv * r1);
+        o[2 * mz * CT] = fma(f, sz, inv * r2);
     }
     __syncthreads();
     // inverse along z: each (component, pair q) gives the two mirrored slabs
@@ -406,17 +408,17 @@ cudaError_t fmp_transform_init_fp64(const FmpPlan& p) {
                                 (int)smem_b<16>(p.max_m));
 }
 
-cudaError_t fmp_launch_transform_solve_fp64(const FmpPlan& p, const double* tabs, const double* r,
-                                            double* z, double* scratch, int nx, int ny, int nz,
+cudaError_t fmp_launch_transform_solve_fp64(const FmpPlan& p, const double* tabs, const double* modeinv,
+                                            const double* r, double* z, double* scratch, int nx, int ny, int nz,
                                             double beta, cudaStream_t s, const double* gate) {
     const size_t sa = smem_a(p.max_m), sc = smem_c(p.max_m);
     const bool wide = p.max_m[2] <= 64;
     const size_t sb = wide ? smem_b<32>(p.max_m) : smem_b<16>(p.max_m);
     k_fwd_xy<<<p.n_items_a, kThreads, sa, s>>>(r, scratch, p.d_boxes, p.d_items_a, tabs, nx, ny, nz, gate);
     if (wide)
-        k_z_solve<32><<<p.n_items_b, kThreads, sb, s>>>(scratch, p.d_boxes, p.d_items_b, tabs, beta, gate);
+        k_z_solve<32><<<p.n_items_b, kThreads, sb, s>>>(scratch, p.d_boxes, p.d_items_b, tabs, modeinv, beta, gate);
     else
-        k_z_solve<16><<<p.n_items_b, kThreads, sb, s>>>(scratch, p.d_boxes, p.d_items_b, tabs, beta, gate);
+        k_z_solve<16><<<p.n_items_b, kThreads, sb, s>>>(scratch, p.d_boxes, p.d_items_b, tabs, modeinv, beta, gate);
     k_inv_xy<<<p.n_items_c, kThreads, sc, s>>>(scratch, z, p.d_boxes, p.d_items_c, tabs, nx, ny, nz, gate);
     return cudaGetLastError();
 }

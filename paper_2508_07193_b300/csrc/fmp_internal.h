@@ -30,6 +30,7 @@ struct FmpBox {
     int mpc_off[3];    // reduced-precision DCT-II T and T^T (padded to 16) of axis a
     int mps_off[3];    // reduced-precision DST-I T and T^T of axis a
     long long scr_off; // offset (doubles) of the box's [3][mz][my][mx] scratch
+    long long inv_off; // offset of the box's [mz][my][mx] table 1 / (eps_bar + beta |sigma|^2)
     double eps_bar;    // subdomain-mean edge permittivity
 };
 
@@ -111,6 +112,7 @@ struct fmp_ctx {
     int single_box = -1;          // box index the single plan was built for
     double* d_scratch = nullptr;  // transform scratch for the RAS plan
     double* d_scratch1 = nullptr; // scratch for one box (fmp_box_solve)
+    double* d_modeinv = nullptr;  // per box and mode 1 / (eps_bar + beta |sigma|^2) (float64 pass B)
     void* d_tab_mp[3] = {};       // reduced-precision tables: bf16, fp16, tf32 (same layout)
     double* d_bscale = nullptr;   // per-box scale factors (fp16 transforms)
     double* d_eps_cell = nullptr; // cell permittivity [nz][ny][nx] (null: eps = 1)
@@ -147,8 +149,8 @@ cudaError_t fmp_launch_eps_bar(const double* eps_edge, FmpBox* d_boxes, int n_bo
                                int ny, int nz, cudaStream_t s);
 // gate: optional device flag; when *gate != 0 the kernels return at once.
 cudaError_t fmp_transform_init_fp64(const FmpPlan& p);
-cudaError_t fmp_launch_transform_solve_fp64(const FmpPlan& p, const double* tabs, const double* r,
-                                            double* z, double* scratch, int nx, int ny, int nz,
+cudaError_t fmp_launch_transform_solve_fp64(const FmpPlan& p, const double* tabs, const double* modeinv,
+                                            const double* r, double* z, double* scratch, int nx, int ny, int nz,
                                             double beta, cudaStream_t s, const double* gate);
 // y = s_b * b + c_eps * eps o x + c_k * K x  (b may be null)
 cudaError_t fmp_launch_curlcurl(const double* x, const double* eps, double* y, double c_eps,
