@@ -94,10 +94,20 @@ __device__ __forceinline__ bool block_partials(const double (&acc)[NV], int nv, 
     return last;
 }
 
-__device__ double block_total(const double* partials, int i) {
-    double s = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(partials + b * kPartStride + i);
-    return s;
+// In the last block: out[i] = sum over blocks of partials[block][i], i < nvals.
+// Warp w reduces values w, w + 8, ...; its lanes stride over the blocks (up
+// to 19 independent loads each at 592 blocks) and a shuffle tree adds the
+// lanes. The summation order is fixed, so results are reproducible. (One
+// thread per value walking all blocks in a dependent chain took about 55 us.)
+__device__ void block_totals(const double* partials, int nvals, double* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i < nvals; i += (int)(blockDim.x >> 5)) {
+        double s = 0.0;
+#pragma unroll 4
+        for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(partials + b * kPartStride + i);
+        s = warp_sum(s);
+        if (lane == 0) out[i] = s;
+    }
 }
 
 __device__ __forceinline__ bool gated(const double* st, int sc) { return st[sc + SC_DONE] != 0.0; }
@@ -158,6 +168,9 @@ __host__ __device__ constexpr int pow2_at_least(int n) {
     return n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : 32;
 }
 __host__ __device__ constexpr int basis_blocks_per_sm(int nv) { return nv <= 16 ? kBasisBlocksPerSM : 2; }
+// Elements per thread and pass: few basis vectors give few loads per element,
+// so small passes take several elements at once to keep enough loads in flight.
+__host__ __device__ constexpr int basis_unroll(int nv) { return nv <= 4 ? 4 : nv <= 8 ? 2 : 1; }
 
 // out[i] = <V_i, w> for i < NV and out[NV] = <w, w>. mode 0: always (first
 // pass); mode 1: only when the re-orthogonalisation flag is up. One kernel
@@ -170,15 +183,24 @@ k_dots(const double* __restrict__ V, size_t ld, const double* __restrict__ w, si
     const St L = st_layout(R);
     if (gated(st, L.sc) || (mode == 1 && st[L.sc + SC_REORTH] == 0.0)) return;
     constexpr int G = pow2_at_least(NV);
+    constexpr int U = basis_unroll(NV);
     double acc[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) acc[g] = 0.0;
     double ww = 0.0;
-    for (size_t e = (size_t)blockIdx.x * kT + threadIdx.x; e < n; e += (size_t)gridDim.x * kT) {
-        const double x = __ldg(w + e);
-        ww = fma(x, x, ww);
+    for (size_t e0 = (size_t)blockIdx.x * kT * U + threadIdx.x; e0 < n; e0 += (size_t)gridDim.x * kT * U) {
+        double x[U];
 #pragma unroll
-        for (int g = 0; g < NV; ++g) acc[g] = fma(__ldg(V + (size_t)g * ld + e), x, acc[g]);
+        for (int u = 0; u < U; ++u) x[u] = e0 + u * kT < n ? __ldg(w + e0 + u * kT) : 0.0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const size_t e = e0 + u * kT;
+            if (e < n) {
+                ww = fma(x[u], x[u], ww);
+#pragma unroll
+                for (int g = 0; g < NV; ++g) acc[g] = fma(__ldg(V + (size_t)g * ld + e), x[u], acc[g]);
+            }
+        }
     }
     __shared__ double wsum[kT / 32][kMaxV + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -197,7 +219,7 @@ k_dots(const double* __restrict__ V, size_t ld, const double* __restrict__ w, si
     }
     __syncthreads();
     if (block_publish(tot, NV + 1, partials, ticket)) {
-        if (threadIdx.x <= NV) st[out_off + threadIdx.x] = block_total(partials, threadIdx.x);
+        block_totals(partials, NV + 1, st + out_off);
         __syncthreads();
         if (threadIdx.x == 0) *ticket = 0;
     }
@@ -260,16 +282,28 @@ k_update(const double* __restrict__ V, size_t ld, double* __restrict__ w, size_t
 #pragma unroll
     for (int g = 0; g < NV; ++g) hr[g] = -h[g];
     double acc[1] = {0.0};
-    for (size_t e = (size_t)blockIdx.x * kT + threadIdx.x; e < n; e += (size_t)gridDim.x * kT) {
-        double x = w[e];
+    constexpr int U = basis_unroll(NV);
+    for (size_t e0 = (size_t)blockIdx.x * kT * U + threadIdx.x; e0 < n; e0 += (size_t)gridDim.x * kT * U) {
+        double x[U];
 #pragma unroll
-        for (int g = 0; g < NV; ++g) x = fma(hr[g], __ldg(V + (size_t)g * ld + e), x);
-        w[e] = x;
-        acc[0] = fma(x, x, acc[0]);
+        for (int u = 0; u < U; ++u) x[u] = e0 + u * kT < n ? w[e0 + u * kT] : 0.0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const size_t e = e0 + u * kT;
+            if (e < n) {
+#pragma unroll
+                for (int g = 0; g < NV; ++g) x[u] = fma(hr[g], __ldg(V + (size_t)g * ld + e), x[u]);
+                w[e] = x[u];
+                acc[0] = fma(x[u], x[u], acc[0]);
+            }
+        }
     }
     if (block_partials(acc, 1, partials, ticket)) {
+        __shared__ double tot;
+        block_totals(partials, 1, &tot);
+        __syncthreads();
         if (threadIdx.x == 0) {
-            const double nrm = sqrt(block_total(partials, 0));
+            const double nrm = sqrt(tot);
             *ticket = 0;
             if (mode == 0) {
                 const double wn = sqrt(st[L.h1 + nv]);   // ||w|| before projection
@@ -305,18 +339,32 @@ struct Pairs {
     const double* b[4];
     int n;
 };
+// N = p.n pairs, a compile-time count (a predicated-off float64 FMA still
+// takes its issue slot).
+template <int N>
 __global__ void __launch_bounds__(kT)
 k_pairdots(Pairs p, size_t len, double* out, double* partials, unsigned int* ticket) {
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    double acc[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) acc[k] = 0.0;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < len; e += (size_t)gridDim.x * blockDim.x) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (k < p.n) acc[k] = fma(p.a[k][e], p.b[k][e], acc[k]);
+        for (int k = 0; k < N; ++k) acc[k] = fma(p.a[k][e], p.b[k][e], acc[k]);
     }
-    if (block_partials(acc, p.n, partials, ticket)) {
-        if (threadIdx.x < p.n) out[threadIdx.x] = block_total(partials, threadIdx.x);
+    if (block_partials(acc, N, partials, ticket)) {
+        block_totals(partials, N, out);
         __syncthreads();
         if (threadIdx.x == 0) *ticket = 0;
+    }
+}
+
+void launch_pairdots(const Pairs& p, size_t len, double* out, double* partials, unsigned int* ticket, int grid,
+                     cudaStream_t s) {
+    switch (p.n) {
+        case 1: k_pairdots<1><<<grid, kT, 0, s>>>(p, len, out, partials, ticket); break;
+        case 2: k_pairdots<2><<<grid, kT, 0, s>>>(p, len, out, partials, ticket); break;
+        case 3: k_pairdots<3><<<grid, kT, 0, s>>>(p, len, out, partials, ticket); break;
+        default: k_pairdots<4><<<grid, kT, 0, s>>>(p, len, out, partials, ticket); break;
     }
 }
 
@@ -504,7 +552,7 @@ cudaError_t norm2(fmp_ctx* c, const double* v, double* slot) {
     Pairs p{};
     p.a[0] = v; p.b[0] = v; p.n = 1;
     ++c->launches;
-    k_pairdots<<<grid_n(c->n_slots), kT, 0, c->stream>>>(p, c->n_slots, slot, c->d_partials, c->d_ticket);
+    launch_pairdots(p, c->n_slots, slot, c->d_partials, c->d_ticket, grid_n(c->n_slots), c->stream);
     return cudaGetLastError();
 }
 
@@ -560,7 +608,7 @@ int arnoldi_step(fmp_ctx* c, int j, fmp_solve_info* inf) {
             Pairs pr{};
             pr.a[0] = t; pr.b[0] = q; pr.a[1] = q; pr.b[1] = q; pr.n = 2;
             ++c->launches;
-            k_pairdots<<<grid_n(n), kT, 0, s>>>(pr, n, st + L.sc + SC_D2, c->d_partials, c->d_ticket);
+            launch_pairdots(pr, n, st + L.sc + SC_D2, c->d_partials, c->d_ticket, grid_n(n), s);
             ++c->launches;
             k_damped_axpy<<<grid_n(n), kT, 0, s>>>(zj, nn, n, st + L.sc + SC_D2, gate);
             FMP_CK(cudaGetLastError());
@@ -758,7 +806,7 @@ int fmp_bicgstab(fmp_ctx* c, const double* b, double* x, fmp_solve_info* info) {
         pr.a[0] = a0; pr.b[0] = b0; pr.n = 1;
         if (a1) { pr.a[1] = a1; pr.b[1] = b1; pr.n = 2; }
         ++c->launches;
-        k_pairdots<<<grid_n(n), kT, 0, s>>>(pr, n, sc + k, c->d_partials, c->d_ticket);
+        launch_pairdots(pr, n, sc + k, c->d_partials, c->d_ticket, grid_n(n), s);
         return cudaGetLastError();
     };
     FMP_CK(norm2(c, b, sc + SC_NRM));
