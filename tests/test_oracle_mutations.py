@@ -75,3 +75,27 @@ def test_wrong_cn_half_step_is_caught(monkeypatch):
     orig = cn.h_update
     monkeypatch.setattr(cn, "h_update", lambda g, H, En, Eo, dt: orig(g, H, En, En, dt))
     _fails(tcn.test_energy_conserved_without_source)
+
+
+def test_dropped_boundary_weight_is_caught(monkeypatch):
+    """Step 4 without the Lambda weights (C = Q^T A_M^{-1} Q alone) is caught."""
+    from oracle import compact as cp
+    import tests.test_oracle_compact as tcp
+    orig = cp.correction_matrix
+
+    def bad(shape, eps_bar, beta, walls=None):
+        C, q = orig(shape, eps_bar, beta, walls)
+        _, dq, wq = cp.boundary(shape, walls)
+        return C - np.diag(np.where(wq, 0.0, 1.0 / (beta * dq))), q
+    monkeypatch.setattr(cp, "correction_matrix", bad)
+    grid, lo, shape = tcp.BOXES[0]
+    _fails(tcp.test_woodbury_solve_matches_dense_restricted_solve, grid, lo, shape, 2.3, 0.25)
+
+
+def test_upper_diagonal_difference_is_caught(monkeypatch):
+    """D^f with its +1 on the subdiagonal (a transposed difference) is caught."""
+    from oracle import compact as cp
+    import tests.test_oracle_compact as tcp
+    monkeypatch.setattr(cp, "difference", lambda n: -np.eye(n) + np.eye(n, k=-1))
+    grid, lo, shape = tcp.BOXES[0]
+    _fails(tcp.test_M_plus_lambda_is_the_restricted_double_curl, grid, lo, shape)
