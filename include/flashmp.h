@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define FMP_ABI_VERSION 2
+#define FMP_ABI_VERSION 3
 
 typedef struct fmp_ctx fmp_ctx; /* opaque, library-owned */
 
@@ -168,6 +168,28 @@ int fmp_set_fused(fmp_ctx* ctx, int max_extent);
 /* Current max_extent and (n_fused may be NULL) the number of fused boxes;
  * HOST outputs. */
 int fmp_get_fused(fmp_ctx* ctx, int* max_extent, int* n_fused);
+
+/* Subdomain form of the preconditioner's box solves.
+ * FMP_FORM_YEE_BOX (default): each extended box is a Yee box with PEC walls;
+ *   its tangential low-face slots are box walls and the DCT-II/DST-I
+ *   transforms diagonalise the box operator exactly (any precision).
+ * FMP_FORM_COMPACT: Algorithm 1 in full (Sec. III-A Steps 1-4). Every
+ *   component keeps all slots of the extended box as unknowns, the square
+ *   difference's SVD tables give the transform solve of eps_bar I + beta M,
+ *   and the Woodbury boundary correction with C = W^{-1} + Q^T (eps_bar I +
+ *   beta M)^{-1} Q (6m^2 - 3m columns per box of extent m) makes it the exact
+ *   inverse of eps_bar I + beta K restricted to the box. Global PEC wall slots
+ *   in a box are held at zero through W^{-1} = 0. float64 only.
+ * Selecting FMP_FORM_COMPACT builds C^{-1} for every box (one batched
+ * transform solve per boundary slot, then a Cholesky inverse): about
+ * 8 (6m^2 - 3m)^2 bytes and a few seconds per box of extent m ~ 36; it
+ * synchronises. Returns FMP_ERR_NOMEM if it does not fit and
+ * FMP_ERR_UNSUPPORTED for a box extent above 64. */
+enum fmp_subdomain_form { FMP_FORM_YEE_BOX = 0, FMP_FORM_COMPACT = 1 };
+int fmp_set_subdomain_form(fmp_ctx* ctx, int form);
+/* Current form and (bytes may be NULL) the device bytes of the compact
+ * correction matrices; HOST outputs. */
+int fmp_get_subdomain_form(fmp_ctx* ctx, int* form, long long* bytes);
 
 /* Autotuner: time `reps` reduced-precision preconditioner applies (precision
  * FMP_PREC_TF32, _FP16 or _BF16) with CUDA events on the context's stream for

@@ -64,7 +64,8 @@ def build(force=False, verbose=False, extra=()):
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
         list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
-        run([nvcc(), *ARCH, "-shared", "-o", LIB, *objs])
+        # cuSOLVER: the set-up Cholesky of the compact-layout correction matrices
+        run([nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcusolver"])
     return LIB
 
 

@@ -199,6 +199,13 @@ bool dt_matches(double beta, double dt) {
 }  // namespace
 
 int fmp_precond_gated(fmp_ctx* c, const double* r, double* z, const double* gate) {
+    if (c->subdomain_form == FMP_FORM_COMPACT) {
+        if (c->opt.precision != FMP_PREC_FP64 || !c->compact) return FMP_ERR_UNSUPPORTED;
+        int nk = 0;
+        FMP_CK(fmp_compact_precond(c, c->compact, r, z, gate, &nk));
+        c->launches += nk;
+        return FMP_OK;
+    }
     switch (c->opt.precision) {
         case FMP_PREC_FP64:
             c->launches += 3;
@@ -470,6 +477,8 @@ void fmp_destroy(fmp_ctx* c) {
     cudaFree(c->d_eps_cell);
     cudaFree(c->d_tmp3); cudaFree(c->d_tmp4); cudaFree(c->d_tmp5);
     fmp_cnn_free(c);
+    fmp_compact_free(c->compact);
+    c->compact = nullptr;
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
@@ -517,6 +526,30 @@ int fmp_set_fused(fmp_ctx* c, int max_extent) {
     if (max_extent == c->ras.fused_max) return FMP_OK;
     FMP_CK(regroup(c->ras, c->h_boxes, c->ras.slab_group, c->ras.tile_group, max_extent, c->stream));
     c->graph_valid = false;
+    return FMP_OK;
+}
+
+int fmp_set_subdomain_form(fmp_ctx* c, int form) {
+    if (!valid_ctx(c) || (form != FMP_FORM_YEE_BOX && form != FMP_FORM_COMPACT)) return FMP_ERR_ARG;
+    if (int rc = latched(c)) return rc;
+    if (form == FMP_FORM_COMPACT && !c->compact) {
+        FmpCompact* k = nullptr;
+        cudaError_t e = fmp_compact_create(c, &k);
+        if (e == cudaErrorMemoryAllocation) { (void)cudaGetLastError(); return FMP_ERR_NOMEM; }
+        if (e == cudaErrorInvalidValue) return FMP_ERR_BREAKDOWN;   // C not positive definite
+        if (e == cudaErrorNotSupported) return FMP_ERR_UNSUPPORTED; // a box extent above 64
+        FMP_CK(e);
+        c->compact = k;
+    }
+    if (form != c->subdomain_form) c->graph_valid = false;
+    c->subdomain_form = form;
+    return FMP_OK;
+}
+
+int fmp_get_subdomain_form(fmp_ctx* c, int* form, long long* bytes) {
+    if (!valid_ctx(c) || !form) return FMP_ERR_ARG;
+    *form = c->subdomain_form;
+    if (bytes) *bytes = (long long)fmp_compact_bytes(c->compact);
     return FMP_OK;
 }
 

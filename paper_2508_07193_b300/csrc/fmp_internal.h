@@ -93,6 +93,7 @@ struct FmpPlan {
 };
 
 struct FmpCnn;
+struct FmpCompact;
 
 struct fmp_ctx {
     int nx = 0, ny = 0, nz = 0;
@@ -117,6 +118,8 @@ struct fmp_ctx {
     double* d_bscale = nullptr;   // per-box scale factors (fp16 transforms)
     double* d_eps_cell = nullptr; // cell permittivity [nz][ny][nx] (null: eps = 1)
     FmpCnn* cnn = nullptr;        // learned initial guess / correction (created on first use)
+    FmpCompact* compact = nullptr;   // compact-layout boxes with the Woodbury correction
+    int subdomain_form = 0;       // FMP_FORM_YEE_BOX or FMP_FORM_COMPACT
     double* d_tmp3 = nullptr;     // field-sized scratch of the learned paths
     double* d_tmp4 = nullptr;
     double* d_tmp5 = nullptr;
@@ -184,6 +187,13 @@ int fmp_precond_gated(fmp_ctx* c, const double* r, double* z, const double* gate
 cudaError_t fmp_ensure_krylov(fmp_ctx* c);
 cudaError_t fmp_krylov_init();
 double fmp_norm(fmp_ctx* c, const double* v, cudaError_t* err);   // ||v||_2, synchronises
+
+// compact-layout subdomain solve with the Woodbury correction (box_compact.cu)
+cudaError_t fmp_compact_create(fmp_ctx* c, FmpCompact** out);
+void fmp_compact_free(FmpCompact* k);
+size_t fmp_compact_bytes(const FmpCompact* k);
+cudaError_t fmp_compact_precond(fmp_ctx* c, const FmpCompact* k, const double* r, double* z, const double* gate,
+                                int* nk);
 
 // learned component (cnn.cu)
 cudaError_t fmp_cnn_create(fmp_ctx* c);

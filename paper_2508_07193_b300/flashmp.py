@@ -86,6 +86,8 @@ def lib():
         "fmp_get_tuning": (_I, [_P, C.POINTER(_I), C.POINTER(_I)]),
         "fmp_autotune": (_I, [_P, _I, _I, C.POINTER(_I)]),
         "fmp_set_fused": (_I, [_P, _I]),
+        "fmp_set_subdomain_form": (_I, [_P, _I]),
+        "fmp_get_subdomain_form": (_I, [_P, C.POINTER(_I), C.POINTER(C.c_longlong)]),
         "fmp_get_fused": (_I, [_P, C.POINTER(_I), C.POINTER(_I)]),
         "fmp_get_box": (_I, [_P, _I, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I),
                              C.POINTER(_D)]),
@@ -243,6 +245,19 @@ class Context:
         a, b = C.c_int(), C.c_int()
         _check(lib().fmp_get_tuning(self._h, C.byref(a), C.byref(b)), "fmp_get_tuning")
         return a.value, b.value
+
+    FORMS = {"yee": 0, "compact": 1}
+
+    def set_subdomain_form(self, form):
+        """'yee' (Yee boxes with PEC walls, default) or 'compact' (Algorithm 1
+        with the Woodbury boundary correction; builds the correction matrices)."""
+        f = self.FORMS[form] if isinstance(form, str) else int(form)
+        _check(lib().fmp_set_subdomain_form(self._h, f), "fmp_set_subdomain_form")
+
+    def get_subdomain_form(self):
+        f, nb = C.c_int(), C.c_longlong()
+        _check(lib().fmp_get_subdomain_form(self._h, C.byref(f), C.byref(nb)), "fmp_get_subdomain_form")
+        return ("yee", "compact")[f.value], nb.value
 
     def set_fused(self, max_extent):
         _check(lib().fmp_set_fused(self._h, int(max_extent)), "fmp_set_fused")
