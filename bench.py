@@ -56,6 +56,9 @@ def parse():
     p.add_argument("--autotune", action="store_true", help="autotune the reduced-precision work lists first")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true", help="skip timing the other preconditioner precisions")
+    p.add_argument("--form", default="yee", choices=["yee", "compact"],
+                   help="subdomain form: Yee boxes with PEC walls, or the compact layout with the Woodbury "
+                        "boundary correction (float64 only)")
     p.add_argument("--case", default="step", choices=["step", "precond", "spmv"],
                    help="precond/spmv: only W + K applies of that operator (for profiler captures)")
     p.add_argument("--workload", default="grid128", choices=["grid128", "grid256", "uneven"])
@@ -199,6 +202,21 @@ def transform_fp64_executed(ctx):
     return tot
 
 
+def compact_apply_flops(ctx):
+    """Float64 flops of one compact-layout preconditioner apply (Algorithm 1
+    with Step 4): two dense transform solves, 12 (mx+my+mz) mx my mz flops per
+    box each, and the correction GEMV, 2 np^2 per box, np = the slots on each
+    component's two low transverse faces."""
+    dense = gemv = 0
+    for i in range(ctx.num_boxes()):
+        mx, my, mz = ctx.box(i)["m"]
+        dense += 12 * (mx + my + mz) * mx * my * mz
+        np_ = (mx * (my * mz - (my - 1) * (mz - 1)) + my * (mx * mz - (mx - 1) * (mz - 1))
+               + mz * (mx * my - (mx - 1) * (my - 1)))
+        gemv += 2 * np_ * np_
+    return 2 * dense + gemv
+
+
 def orth_flops(n, iters, restart=30):
     """Float64 flops of classical Gram-Schmidt over FGMRES(restart) for
     `iters` Arnoldi steps: per step j of a cycle, <V_i, w> and <w, w>
@@ -299,6 +317,11 @@ def run_ours(args):
     ctx = F.Context(w.grid, w.eps_cell, w.beta, w.cuts, w.overlap, precision=args.precision, restart=30,
                     rtol=1e-8, stream=stream, device=dev, krylov=args.krylov, use_graph=args.graph)
     dt = 2.0 * math.sqrt(w.beta)
+    setup_s = None
+    if args.form != "yee":
+        t0 = time.time()
+        ctx.set_subdomain_form(args.form)
+        setup_s = time.time() - t0
     tuning = None
     if args.autotune and args.precision != "fp64":
         tuning = ctx.autotune(args.precision, reps=3)
@@ -365,7 +388,15 @@ def run_ours(args):
     hbm = pk.get("hbm_gbs", 6400.0)
     tb = transform_bytes(ctx)
     traffic = TRAFFIC_BYTES.get((w.name, args.precision))
-    if args.precision == "fp64":
+    if args.form == "compact":
+        cf = compact_apply_flops(ctx) / (ms_p * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": cf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": cf / FP64_NOMINAL_TFLOPS, "traffic": None,
+                "correction_matrix_bytes": ctx.get_subdomain_form()[1],
+                "kernel": "compact-layout box solve: two dense float64 transform solves and the Woodbury "
+                          "correction GEMV (one preconditioner apply)",
+                "peak_source": "B300 nominal float64 rate from the recipe (measured DFMA 1.13 TFLOP/s)"}
+    elif args.precision == "fp64":
         achieved = flops / (ms_p * 1e-3) / 1e12
         executed = transform_fp64_executed(ctx) * 2 / (ms_p * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
@@ -428,7 +459,8 @@ def run_ours(args):
         "config": {"workload": w.name, "grid": list(w.grid), "subdomains": [len(c) for c in w.cuts],
                    "overlap": w.overlap, "beta": w.beta, "krylov": "FGMRES(30)" if args.krylov == "fgmres" else "BiCGSTAB",
                    "cuda_graph": bool(args.graph), "rtol": 1e-8,
-                   "precision": args.precision, "l2": "inputs (50 MB per field, 3.1 GB Krylov basis) exceed L2 across a step"},
+                   "precision": args.precision, "form": args.form,
+                   "l2": "inputs (50 MB per field, 3.1 GB Krylov basis) exceed L2 across a step"},
         "iters_per_step": iters,
         "true_rel_res_max": true_res,
         "precond_ms": ms_p,
@@ -439,6 +471,7 @@ def run_ours(args):
         "e2e": {"value": world * dof / (ms_e2e * 1e-3), "unit": "DoF/s", "h2d_bytes_per_step": J.numel() * 8,
                 "d2h_bytes_per_step": E.numel() * 8, "ms_per_step": ms_e2e},
         "gpu_launches": launches,
+        "form_setup_s": setup_s,
         "tuning": list(tuning) if tuning else list(ctx.get_tuning()),
         "clocks": clocks,
     }
@@ -455,7 +488,7 @@ def run_ours(args):
                                 "kernel": "Gram-Schmidt basis passes k_dots / k_update / k_scale_next (one step)",
                                 "note": "one float64 FMA per 8 bytes read: the float64 pipe, not HBM, bounds them"}
     # the other preconditioner precisions on the same workload, same protocol
-    if not args.no_forms:
+    if not args.no_forms and args.form == "yee":
         forms = {}
         for p in ("fp64", "bf16", "fp16", "tf32"):
             if p == args.precision:
@@ -520,6 +553,8 @@ def run_case(args):
 
     w = {"grid128": wl.grid128, "grid256": wl.grid256, "uneven": wl.grid_uneven}[args.workload]()
     ctx = F.Context(w.grid, w.eps_cell, w.beta, w.cuts, w.overlap, precision=args.precision)
+    if args.form != "yee":
+        ctx.set_subdomain_form(args.form)
     r = torch.as_tensor(w.rhs, device="cuda")
     z = ctx.empty_field()
     op = ctx.precond_apply if args.case == "precond" else ctx.curlcurl_apply
