@@ -43,20 +43,14 @@ void build_tables(int m, double* C, double* S, double* sig) {
     }
 }
 
-// Folded copy of a table (layout in FoldDims).
+// Two-level folded copy of a table (layout in Fold3).
 void fold_table(int m, bool dst, const double* T, double* F) {
-    const FoldDims f = fold_dims(m, dst);
-    double* FS = F;
-    double* FA = F + f.nks * f.la;
-    for (int ks = 0; ks < f.nks; ++ks) {
-        const int k = 2 * ks + f.s0;
-        for (int q = 0; q < f.npair; ++q) FS[ks * f.la + q] = T[k * m + f.off + q];
-        if (f.has_mid) FS[ks * f.la + f.npair] = T[k * m + f.mid];
-    }
-    for (int ka = 0; ka < f.nka; ++ka) {
-        const int k = 2 * ka + 1 - f.s0;
-        for (int q = 0; q < f.npair; ++q) FA[ka * f.lb + q] = T[k * m + f.off + q];
-    }
+    const Fold3 f = fold3(m, dst);
+    for (int c = 0; c < 3; ++c)
+        for (int j = 0; j < f.n[c]; ++j) {
+            const int k = f.k0[c] + f.kstep[c] * j;
+            for (int q = 0; q < f.len[c]; ++q) F[f.toff[c] + j * f.len[c] + q] = T[k * m + fold3_column(f, c, q)];
+        }
 }
 
 // Round a float to tf32 (10 explicit mantissa bits, to nearest, ties away).

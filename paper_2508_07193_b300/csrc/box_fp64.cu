@@ -13,18 +13,21 @@
 // The grid-major reordering P of Step 2 never materialises: pass B reads the
 // three components of a mode from their own planes.
 //
-// Tables (per extent m): DCT-II C[k][i] along a component's own axis,
-// zero-padded DST-I S[k][j] along the other two (Eq. 8 with U^T = C,
-// V^T = S), both used in their even/odd folded form (FoldDims): each
-// forward line is split into mirror sums and differences and transformed by
-// two half-size tables, each inverse pair of mirrored outputs comes from one
-// sum and one difference, which halves the float64 FMAs. The 3x3 block B = eps_bar I + beta(|s|^2 I - s s^T) is
+// Tables (per extent m): DCT-II along a component's own axis, zero-padded
+// DST-I along the other two (Eq. 8 with U^T = C, V^T = S), used in the
+// two-level folded form of Fold3, the first stages of a fast transform: a
+// forward line folds its inputs into mirror sums and differences (and, for
+// an even extent, folds one of those halves once more), and each of the three
+// mode classes is a dense product on its own folded inputs; an inverse line
+// produces its outputs in mirrored pairs (odd extents) or quadruples (even
+// extents) from the class products. About 3/8 m^2 FMAs per line of an even
+// extent instead of m^2. The 3x3 block B = eps_bar I + beta(|s|^2 I - s s^T) is
 // inverted by Sherman-Morrison: B^{-1} r = (r + (beta/eps_bar) s (s.r)) /
-// (eps_bar + beta |s|^2).
+// (eps_bar + beta |s|^2), the denominator read from a per-box mode table.
 //
-// These kernels are bound by the float64 FMA pipe (1/64 of the fp32 rate on
-// this part); shared-memory traffic (two 8-byte operands per FMA, all
-// conflict-free broadcasts or unit strides) stays below that bound.
+// These kernels are bound by the float64 pipe (1/64 of the fp32 rate on this
+// part). Work indices run class by class, so a warp never executes two classes'
+// loops with lanes idle in each.
 #include "fmp_internal.h"
 
 namespace {
@@ -35,50 +38,106 @@ __device__ __forceinline__ bool edge_wall(int c, int i, int j, int k) {
     return c == 0 ? (j == 0 || k == 0) : c == 1 ? (i == 0 || k == 0) : (i == 0 || j == 0);
 }
 
-// Shared-memory room for one folded table of extent m (nks la + nka lb never
+// Shared-memory room for one folded table of extent m (Fold3::tab never
 // exceeds (m^2 + 1) / 2).
 __host__ __device__ __forceinline__ int fold_room(int m) { return (m * m + 1) / 2; }
 
-// Folded table view (layout in FoldDims): FS[ks][q] then FA[ka][q].
-struct Fold {
-    FoldDims d;
-    const double* S;   // sym rows, stride d.la
-    const double* A;   // anti rows, stride d.lb
-};
-__device__ __forceinline__ Fold make_fold(const double* t, int m, bool dst) {
-    Fold f;
-    f.d = fold_dims(m, dst);
-    f.S = t;
-    f.A = t + f.d.nks * f.d.la;
-    return f;
-}
-// Copy a folded table to shared memory (as is).
-__device__ __forceinline__ Fold stage_fold(double* dst, const Fold& g) {
-    const int ns = g.d.nks * g.d.la, na = g.d.nka * g.d.lb;
-    for (int t = threadIdx.x; t < ns + na; t += blockDim.x) dst[t] = g.S[t];
-    Fold f = g;
-    f.S = dst;
-    f.A = dst + ns;
-    return f;
-}
-// Fold one line of length m (elements v(i)) into the sym/anti inputs: slot
-// q < la is the sym input, slot la + q the anti input.
+// Folded input q of class c for a line whose elements are v(i).
 template <class Get>
-__device__ __forceinline__ double fold_input(const FoldDims& d, int m, int q, Get v) {
-    if (q < d.la) {
-        if (q < d.npair) return v(d.off + q) + v(m - 1 - q);
-        return v(d.mid);
-    }
-    const int qq = q - d.la;
-    return v(d.off + qq) - v(m - 1 - qq);
+__device__ __forceinline__ double f3_input(const Fold3& f, int c, int q, Get v) {
+    auto fsym = [&](int p) { return p < f.npair ? v(f.off + p) + v(f.m - 1 - p) : v(f.mid); };
+    auto fanti = [&](int p) { return v(f.off + p) - v(f.m - 1 - p); };
+    if (!f.two) return c == 0 ? fsym(q) : fanti(q);
+    if (c == 2) return f.s2sym ? fanti(q) : fsym(q);
+    auto f2 = [&](int p) { return f.s2sym ? fsym(p) : fanti(p); };
+    if (c == 0) return q < f.L / 2 ? f2(q) + f2(f.L - 1 - q) : f2(q);
+    return f2(q) - f2(f.L - 1 - q);
 }
 
-// First inverse pair worth computing for an owned range [o0, o1): a pair
-// q < q0 puts both of its mirrored outputs (off + q and m - 1 - q) outside
-// the range (the overlap layers of the box).
-__device__ __forceinline__ int first_owned_pair(const FoldDims& d, int m, int o0, int o1) {
-    const int q0 = min(o0 - d.off, m - o1);
-    return q0 < 0 ? 0 : (q0 > d.npair ? d.npair : q0);
+// Class and in-class index of folded input slot s.
+__device__ __forceinline__ void f3_slot(const Fold3& f, int s, int& c, int& q) {
+    c = s < f.seg[1] ? 0 : (s < f.seg[2] ? 1 : 2);
+    q = s - f.seg[c];
+}
+
+// Class, row and mode of output row r (rows ordered class by class).
+__device__ __forceinline__ void f3_row(const Fold3& f, int r, int& c, int& j, int& k) {
+    c = r < f.n[0] ? 0 : (r < f.n[0] + f.n[1] ? 1 : 2);
+    j = r - (c == 0 ? 0 : (c == 1 ? f.n[0] : f.n[0] + f.n[1]));
+    k = f.k0[c] + f.kstep[c] * j;
+}
+
+// First inverse pair worth computing for an owned range [o0, o1) on an odd
+// extent: a pair q < q0 puts both mirrored outputs (off + q and m - 1 - q)
+// outside the range. Even extents work in quadruples that always reach the
+// owned centre, so they start at 0.
+__device__ __forceinline__ int first_owned_pair(const Fold3& f, int o0, int o1) {
+    if (f.two) return 0;
+    const int q0 = min(o0 - f.off, f.m - o1);
+    return q0 < 0 ? 0 : (q0 > f.npair ? f.npair : q0);
+}
+
+// Inverse items of a line: odd extents: pairs [q0, npair) then the middle;
+// even extents: quadruples [0, L/2), then the second-level middle (odd L),
+// then the first-level middle.
+__device__ __forceinline__ int f3_items(const Fold3& f, int q0) {
+    return f.two ? f.L / 2 + (f.L & 1) + f.has_mid : (f.npair - q0) + f.has_mid;
+}
+// Item it of an inverse line: Y(k) gives mode k, out(p, x) takes output p.
+template <class GetY, class Put>
+__device__ __forceinline__ void f3_inverse_item(const Fold3& f, const double* T, int q0, int it, GetY Y, Put out) {
+    const double* T0 = T + f.toff[0];
+    const double* T1 = T + f.toff[1];
+    const double* T2 = T + f.toff[2];
+    if (!f.two) {
+        if (it < f.npair - q0) {
+            const int q = q0 + it;
+            double E = 0.0, O = 0.0;
+            for (int j = 0; j < f.n[0]; ++j) E = fma(T0[j * f.len[0] + q], Y(f.k0[0] + 2 * j), E);
+            for (int j = 0; j < f.n[1]; ++j) O = fma(T1[j * f.len[1] + q], Y(f.k0[1] + 2 * j), O);
+            out(f.off + q, E + O);
+            out(f.m - 1 - q, E - O);
+        } else {
+            double E = 0.0;
+            for (int j = 0; j < f.n[0]; ++j) E = fma(T0[j * f.len[0] + f.npair], Y(f.k0[0] + 2 * j), E);
+            out(f.mid, E);
+        }
+        return;
+    }
+    const int nq = f.L / 2;
+    if (it < nq) {
+        const int q = it, qo = f.L - 1 - it;
+        double A = 0.0, B = 0.0, Gi = 0.0, Go = 0.0;
+        for (int j = 0; j < f.n[0]; ++j) A = fma(T0[j * f.len[0] + q], Y(f.k0[0] + 4 * j), A);
+        for (int j = 0; j < f.n[1]; ++j) B = fma(T1[j * f.len[1] + q], Y(f.k0[1] + 4 * j), B);
+        for (int j = 0; j < f.n[2]; ++j) {
+            const double y = Y(f.k0[2] + 2 * j);
+            Gi = fma(T2[j * f.len[2] + q], y, Gi);
+            Go = fma(T2[j * f.len[2] + qo], y, Go);
+        }
+        const double si = A + B, so = A - B;
+        const double Ei = f.s2sym ? si : Gi, Oi = f.s2sym ? Gi : si;
+        const double Eo = f.s2sym ? so : Go, Oo = f.s2sym ? Go : so;
+        out(f.off + q, Ei + Oi);
+        out(f.m - 1 - q, Ei - Oi);
+        out(f.off + qo, Eo + Oo);
+        out(f.m - 1 - qo, Eo - Oo);
+    } else if (it == nq && (f.L & 1)) {
+        double A = 0.0, G = 0.0;
+        for (int j = 0; j < f.n[0]; ++j) A = fma(T0[j * f.len[0] + nq], Y(f.k0[0] + 4 * j), A);
+        for (int j = 0; j < f.n[2]; ++j) G = fma(T2[j * f.len[2] + nq], Y(f.k0[2] + 2 * j), G);
+        const double E = f.s2sym ? A : G, O = f.s2sym ? G : A;
+        out(f.off + nq, E + O);
+        out(f.m - 1 - nq, E - O);
+    } else {   // the first-level middle: only the sym class contributes (class 2 here)
+        double E = 0.0;
+        for (int j = 0; j < f.n[2]; ++j) E = fma(T2[j * f.len[2] + f.npair], Y(f.k0[2] + 2 * j), E);
+        out(f.mid, E);
+    }
+}
+
+__device__ __forceinline__ void stage(double* dst, const double* src, int n) {
+    for (int t = threadIdx.x; t < n; t += blockDim.x) dst[t] = src[t];
 }
 
 // Pass A: forward transforms along x and y of one z-slab of one component.
@@ -99,29 +158,23 @@ k_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox* _
         return;
     }
     const bool sx = c != 0, sy = c != 1;   // DST along x / y?
-    const Fold gx = make_fold(tabs + (sx ? B.dstf_off[0] : B.dctf_off[0]), mx, sx);
-    const Fold gy = make_fold(tabs + (sy ? B.dstf_off[1] : B.dctf_off[1]), my, sy);
-    const FoldDims& dx = gx.d;
-    const FoldDims& dy = gy.d;
+    const Fold3 fx = fold3(mx, sx), fy = fold3(my, sy);
     double* X = sm;               // [my][mx] spatial slab, later the y-folded inputs
-    double* AB = X + nxy;         // [my][la+lb] x-folded inputs
+    double* AB = X + nxy;         // [my][LX] x-folded inputs
     double* P = AB + nxy;         // [my][kx] after the x pass
-    double* TX = P + nxy;         // x table transposed: sym [q][ks], then anti [q][ka]
+    double* TX = P + nxy;         // x table, per class transposed: [q][j]
     double* TY = TX + fold_room(mx);   // y table as is
     {
-        const int ns = dx.nks * dx.la, na = dx.nka * dx.lb;
-        for (int t = threadIdx.x; t < ns; t += blockDim.x) {
-            const int ks = t / dx.la, q = t - ks * dx.la;
-            TX[q * dx.nks + ks] = gx.S[t];
-        }
-        for (int t = threadIdx.x; t < na; t += blockDim.x) {
-            const int ka = t / dx.lb, q = t - ka * dx.lb;
-            TX[ns + q * dx.nka + ka] = gx.A[t];
+        const double* g = tabs + (sx ? B.dstf_off[0] : B.dctf_off[0]);
+        for (int cc = 0; cc < 3; ++cc) {
+            const int n = fx.n[cc], ln = fx.len[cc];
+            for (int t = threadIdx.x; t < n * ln; t += blockDim.x) {
+                const int j = t / ln, q = t - j * ln;
+                TX[fx.toff[cc] + q * n + j] = g[fx.toff[cc] + t];
+            }
         }
     }
-    const Fold fy = stage_fold(TY, gy);
-    const double* TXS = TX;
-    const double* TXA = TX + dx.nks * dx.la;
+    stage(TY, tabs + (sy ? B.dstf_off[1] : B.dctf_off[1]), fy.tab);
     const int gk = B.ext_lo[2] + kz;
     const double* src = r + (((long long)c * nz + gk) * ny + B.ext_lo[1]) * (long long)nx + B.ext_lo[0];
     for (int t = threadIdx.x; t < nxy; t += blockDim.x) {
@@ -129,64 +182,53 @@ k_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox* _
         X[t] = edge_wall(c, i, j, kz) ? 0.0 : src[(long long)j * nx + i];
     }
     __syncthreads();
-    const int LX = dx.la + dx.lb;
+    const int LX = fx.seg[2] + fx.len[2];
+    // folded inputs class by class ((y, q) of class 0, then 1, then 2): the
+    // classes fold with different numbers of additions
     for (int t = threadIdx.x; t < my * LX; t += blockDim.x) {
-        const int y = t / LX, q = t - y * LX;
+        int cc = 0, u = t;
+        while (cc < 2 && u >= my * fx.len[cc]) { u -= my * fx.len[cc]; ++cc; }
+        const int y = u / fx.len[cc], q = u - y * fx.len[cc];
         const double* row = X + y * mx;
-        AB[t] = fold_input(dx, mx, q, [&](int i) { return row[i]; });
+        AB[y * LX + fx.seg[cc] + q] = f3_input(fx, cc, q, [&](int i) { return row[i]; });
     }
     __syncthreads();
-    // Work index: all sym outputs (y, ks) first, then all anti (y, ka), so a
-    // warp takes one table class (a warp split by parity would run both FMA
-    // loops with half its lanes idle).
-    const int nsx = my * dx.nks;
-    for (int t = threadIdx.x; t < nxy; t += blockDim.x) {
+    // outputs class by class: rows (y, j) of class 0, then 1, then 2
+    for (int t = threadIdx.x; t < my * fx.nmodes; t += blockDim.x) {
+        int cc = 0, u = t;
+        while (cc < 2 && u >= my * fx.n[cc]) { u -= my * fx.n[cc]; ++cc; }
+        const int n = fx.n[cc], ln = fx.len[cc];
+        const int y = u / n, j = u - y * n;
+        const double* a = AB + y * LX + fx.seg[cc];
+        const double* tcol = TX + fx.toff[cc] + j;
         double acc = 0.0;
-        int y, kx;
-        if (t < nsx) {
-            y = t / dx.nks;
-            const int ks = t - y * dx.nks;
-            kx = 2 * ks + dx.s0;
-            const double* a = AB + y * LX;
-            for (int q = 0; q < dx.la; ++q) acc = fma(TXS[q * dx.nks + ks], a[q], acc);
-        } else {
-            const int u = t - nsx;
-            y = u / dx.nka;
-            const int ka = u - y * dx.nka;
-            kx = 2 * ka + 1 - dx.s0;
-            const double* a = AB + y * LX + dx.la;
-            for (int q = 0; q < dx.lb; ++q) acc = fma(TXA[q * dx.nka + ka], a[q], acc);
-        }
-        P[y * mx + kx] = acc;
+        for (int q = 0; q < ln; ++q) acc = fma(tcol[q * n], a[q], acc);
+        P[y * mx + fx.k0[cc] + fx.kstep[cc] * j] = acc;
     }
+    if (fx.nmodes < mx)   // the DST-I wall mode kx = 0
+        for (int y = threadIdx.x; y < my; y += blockDim.x) P[y * mx] = 0.0;
     __syncthreads();
-    const int LY = dy.la + dy.lb;
+    const int LY = fy.seg[2] + fy.len[2];
     for (int t = threadIdx.x; t < LY * mx; t += blockDim.x) {
-        const int q = t / mx, kx = t - q * mx;
-        X[t] = fold_input(dy, my, q, [&](int y) { return P[y * mx + kx]; });
+        const int s = t / mx, kx = t - s * mx;
+        int cc, q;
+        f3_slot(fy, s, cc, q);
+        X[t] = f3_input(fy, cc, q, [&](int y) { return P[y * mx + kx]; });
     }
     __syncthreads();
-    // sym rows (ks, kx) first, then anti rows (ka, kx): class-uniform warps
-    const int nsy = dy.nks * mx;
-    for (int t = threadIdx.x; t < nxy; t += blockDim.x) {
+    for (int t = threadIdx.x; t < fy.nmodes * mx; t += blockDim.x) {
+        int cc = 0, u = t;
+        while (cc < 2 && u >= fy.n[cc] * mx) { u -= fy.n[cc] * mx; ++cc; }
+        const int ln = fy.len[cc];
+        const int j = u / mx, kx = u - j * mx;
+        const double* trow = TY + fy.toff[cc] + j * ln;
+        const double* col = X + fy.seg[cc] * mx + kx;
         double acc = 0.0;
-        int ky, kx;
-        if (t < nsy) {
-            const int ks = t / mx;
-            kx = t - ks * mx;
-            ky = 2 * ks + dy.s0;
-            const double* f = fy.S + ks * dy.la;
-            for (int q = 0; q < dy.la; ++q) acc = fma(f[q], X[q * mx + kx], acc);
-        } else {
-            const int u = t - nsy;
-            const int ka = u / mx;
-            kx = u - ka * mx;
-            ky = 2 * ka + 1 - dy.s0;
-            const double* f = fy.A + ka * dy.lb;
-            for (int q = 0; q < dy.lb; ++q) acc = fma(f[q], X[(dy.la + q) * mx + kx], acc);
-        }
-        dst[ky * mx + kx] = acc;
+        for (int q = 0; q < ln; ++q) acc = fma(trow[q], col[q * mx], acc);
+        dst[(fy.k0[cc] + fy.kstep[cc] * j) * mx + kx] = acc;
     }
+    if (fy.nmodes < my)   // the DST-I wall mode ky = 0
+        for (int kx = threadIdx.x; kx < mx; kx += blockDim.x) dst[kx] = 0.0;
 }
 
 // Pass B: z transform, per-mode 3x3 solve, inverse z transform (owned z).
@@ -207,8 +249,9 @@ k_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int2
     double* AB = Buf + 3 * mz * CT;     // [3][mz][CT]: z-folded inputs
     double* TC = AB + 3 * mz * CT;      // folded DCT along z
     double* TS = TC + fold_room(mz);    // folded DST along z
-    const Fold fc = stage_fold(TC, make_fold(tabs + B.dctf_off[2], mz, false));
-    const Fold fs = stage_fold(TS, make_fold(tabs + B.dstf_off[2], mz, true));
+    const Fold3 fc = fold3(mz, false), fs = fold3(mz, true);
+    stage(TC, tabs + B.dctf_off[2], fc.tab);
+    stage(TS, tabs + B.dstf_off[2], fs.tab);
     double* base = scr + B.scr_off;
     for (int t = threadIdx.x; t < 3 * mz * CT; t += blockDim.x) {
         const int cz = t / CT, col = t - cz * CT;     // cz = c * mz + z
@@ -217,31 +260,33 @@ k_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int2
     __syncthreads();
     for (int t = threadIdx.x; t < 3 * mz * CT; t += blockDim.x) {
         const int cz = t / CT, col = t - cz * CT;
-        const int c = cz / mz, q = cz - c * mz;
-        const FoldDims& d = (c == 2 ? fc : fs).d;
+        const int c = cz / mz, s = cz - c * mz;
+        const Fold3& f = c == 2 ? fc : fs;
         const double* in = Buf + c * mz * CT + col;
-        AB[t] = q < d.la + d.lb ? fold_input(d, mz, q, [&](int z) { return in[z * CT]; }) : 0.0;
+        double v = 0.0;
+        if (s < f.seg[2] + f.len[2]) {
+            int cc, q;
+            f3_slot(f, s, cc, q);
+            v = f3_input(f, cc, q, [&](int z) { return in[z * CT]; });
+        }
+        AB[t] = v;
     }
     __syncthreads();
-    // per component, sym output rows first, then anti rows (class-uniform
-    // warps also when a warp spans two rows, CT = 16)
+    // per component, output rows class by class (a warp is one row when CT = 32)
     for (int t = threadIdx.x; t < 3 * mz * CT; t += blockDim.x) {
         const int cz = t / CT, col = t - cz * CT;
         const int c = cz / mz, r = cz - c * mz;
-        const Fold& f = c == 2 ? fc : fs;
-        const double* ab = AB + c * mz * CT + col;
-        double acc = 0.0;
-        int kz;
-        if (r < f.d.nks) {
-            kz = 2 * r + f.d.s0;
-            const double* g = f.S + r * f.d.la;
-            for (int q = 0; q < f.d.la; ++q) acc = fma(g[q], ab[q * CT], acc);
-        } else {
-            const int ka = r - f.d.nks;
-            kz = 2 * ka + 1 - f.d.s0;
-            const double* g = f.A + ka * f.d.lb;
-            for (int q = 0; q < f.d.lb; ++q) acc = fma(g[q], ab[(f.d.la + q) * CT], acc);
+        const Fold3& f = c == 2 ? fc : fs;
+        if (r >= f.nmodes) {   // the DST-I wall mode kz = 0
+            Buf[c * mz * CT + col] = 0.0;
+            continue;
         }
+        int cc, j, kz;
+        f3_row(f, r, cc, j, kz);
+        const double* g = (c == 2 ? TC : TS) + f.toff[cc] + j * f.len[cc];
+        const double* ab = AB + (c * mz + f.seg[cc]) * CT + col;
+        double acc = 0.0;
+        for (int q = 0; q < f.len[cc]; ++q) acc = fma(g[q], ab[q * CT], acc);
         Buf[(c * mz + kz) * CT + col] = acc;
     }
     __syncthreads();
@@ -268,35 +313,24 @@ k_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int2
         o[2 * mz * CT] = fma(f, sz, inv * r2);
     }
     __syncthreads();
-    // inverse along z: each (component, pair q) gives the two mirrored slabs
-    // z = off + q and mz - 1 - q (E + O and E - O); the middle slab from E
-    // alone; the DST wall slab z = 0 is zero. Only owned slabs are written.
+    // inverse along z, owned slabs only; the DST wall slab z = 0 is zero
     const int oz0 = B.own_lo[2], oz1 = B.own_lo[2] + B.own_n[2];
-    const int qc = first_owned_pair(fc.d, mz, oz0, oz1), qs = first_owned_pair(fs.d, mz, oz0, oz1);
-    const int nc = fc.d.npair + fc.d.has_mid - qc, ns = fs.d.npair + fs.d.has_mid - qs;
-    const int npq = nc > ns ? nc : ns;
-    for (int t = threadIdx.x; t < 3 * npq * CT; t += blockDim.x) {
-        const int cq = t / CT, col = t - cq * CT;
+    const int qc = first_owned_pair(fc, oz0, oz1), qs = first_owned_pair(fs, oz0, oz1);
+    const int nic = f3_items(fc, qc), nis = f3_items(fs, qs);
+    const int ni = nic > nis ? nic : nis;
+    for (int t = threadIdx.x; t < 3 * ni * CT; t += blockDim.x) {
+        const int ci = t / CT, col = t - ci * CT;
         if (col >= ncol) continue;
-        const int c = cq / npq;
-        const int q = cq - c * npq + (c == 2 ? qc : qs);
-        const Fold& f = c == 2 ? fc : fs;
-        const FoldDims& d = f.d;
+        const int c = ci / ni, item = ci - c * ni;
+        const Fold3& f = c == 2 ? fc : fs;
+        if (item >= (c == 2 ? nic : nis)) continue;
         const double* e = Buf + c * mz * CT + col;
         double* out = base + (long long)c * mz * nxy + col0 + col;
-        if (q < d.npair) {
-            double E = 0.0, O = 0.0;
-            for (int ks = 0; ks < d.nks; ++ks) E = fma(f.S[ks * d.la + q], e[(2 * ks + d.s0) * CT], E);
-            for (int ka = 0; ka < d.nka; ++ka) O = fma(f.A[ka * d.lb + q], e[(2 * ka + 1 - d.s0) * CT], O);
-            const int z1 = d.off + q, z2 = mz - 1 - q;
-            if (z1 >= oz0 && z1 < oz1) out[(long long)z1 * nxy] = E + O;
-            if (z2 >= oz0 && z2 < oz1) out[(long long)z2 * nxy] = E - O;
-        } else if (q == d.npair && d.has_mid) {
-            double E = 0.0;
-            for (int ks = 0; ks < d.nks; ++ks) E = fma(f.S[ks * d.la + d.npair], e[(2 * ks + d.s0) * CT], E);
-            if (d.mid >= oz0 && d.mid < oz1) out[(long long)d.mid * nxy] = E;
-        }
-        if (d.off == 1 && q == 0 && oz0 == 0) out[0] = 0.0;
+        f3_inverse_item(f, c == 2 ? TC : TS, c == 2 ? qc : qs, item, [&](int k) { return e[k * CT]; },
+                        [&](int z, double v) {
+                            if (z >= oz0 && z < oz1) out[(long long)z * nxy] = v;
+                        });
+        if (f.off == 1 && item == 0 && oz0 == 0) out[0] = 0.0;
     }
 }
 
@@ -316,68 +350,45 @@ k_inv_xy(const double* __restrict__ scr, double* __restrict__ zout, const FmpBox
     const int oy0 = B.own_lo[1], ony = B.own_n[1];
     const int ox0 = B.own_lo[0], onx = B.own_n[0];
     const bool sx = c != 0, sy = c != 1;
+    const Fold3 fx = fold3(mx, sx), fy = fold3(my, sy);
     double* S = sm;                  // [ky][kx]
     double* Q = S + nxy;             // [owned y][kx]
     double* TX = Q + ony * mx;
     double* TY = TX + fold_room(mx);
-    const Fold fx = stage_fold(TX, make_fold(tabs + (sx ? B.dstf_off[0] : B.dctf_off[0]), mx, sx));
-    const Fold fy = stage_fold(TY, make_fold(tabs + (sy ? B.dstf_off[1] : B.dctf_off[1]), my, sy));
+    stage(TX, tabs + (sx ? B.dstf_off[0] : B.dctf_off[0]), fx.tab);
+    stage(TY, tabs + (sy ? B.dstf_off[1] : B.dctf_off[1]), fy.tab);
     const double* src = scr + B.scr_off + ((long long)c * mz + zl) * nxy;
     for (int t = threadIdx.x; t < nxy; t += blockDim.x) S[t] = src[t];
     __syncthreads();
     {   // inverse along y, owned rows only
-        const FoldDims& d = fy.d;
-        const int q0 = first_owned_pair(d, my, oy0, oy0 + ony);
-        const int npq = d.npair + d.has_mid - q0;
-        for (int t = threadIdx.x; t < npq * mx; t += blockDim.x) {
-            const int q = t / mx + q0, kx = t - (q - q0) * mx;
-            if (q < d.npair) {
-                double E = 0.0, O = 0.0;
-                for (int ks = 0; ks < d.nks; ++ks) E = fma(fy.S[ks * d.la + q], S[(2 * ks + d.s0) * mx + kx], E);
-                for (int ka = 0; ka < d.nka; ++ka) O = fma(fy.A[ka * d.lb + q], S[(2 * ka + 1 - d.s0) * mx + kx], O);
-                const int y1 = d.off + q - oy0, y2 = my - 1 - q - oy0;
-                if (y1 >= 0 && y1 < ony) Q[y1 * mx + kx] = E + O;
-                if (y2 >= 0 && y2 < ony) Q[y2 * mx + kx] = E - O;
-            } else {
-                double E = 0.0;
-                for (int ks = 0; ks < d.nks; ++ks) E = fma(fy.S[ks * d.la + d.npair], S[(2 * ks + d.s0) * mx + kx], E);
-                const int y1 = d.mid - oy0;
-                if (y1 >= 0 && y1 < ony) Q[y1 * mx + kx] = E;
-            }
+        const int q0 = first_owned_pair(fy, oy0, oy0 + ony);
+        const int ni = f3_items(fy, q0);
+        for (int t = threadIdx.x; t < ni * mx; t += blockDim.x) {
+            const int item = t / mx, kx = t - item * mx;
+            f3_inverse_item(fy, TY, q0, item, [&](int k) { return S[k * mx + kx]; }, [&](int y, double v) {
+                const int yy = y - oy0;
+                if (yy >= 0 && yy < ony) Q[yy * mx + kx] = v;
+            });
         }
-        if (d.off == 1 && oy0 == 0)
+        if (fy.off == 1 && oy0 == 0)
             for (int kx = threadIdx.x; kx < mx; kx += blockDim.x) Q[kx] = 0.0;
     }
     __syncthreads();
     const int gk = B.ext_lo[2] + zl;
     double* dst = zout + (((long long)c * nz + gk) * ny + B.ext_lo[1] + oy0) * (long long)nx + B.ext_lo[0];
-    {   // inverse along x, owned columns only
-        const FoldDims& d = fx.d;
-        // all (row, pair) items first, then the rows' middle elements, so the
-        // pair warps do not wait on a middle lane's shorter loop
-        const int q0 = first_owned_pair(d, mx, ox0, ox0 + onx);
-        const int np = d.npair - q0;
-        const int npp = ony * np;
-        for (int t = threadIdx.x; t < npp + ony * d.has_mid; t += blockDim.x) {
-            if (t < npp) {
-                const int yy = t / np, q = t - yy * np + q0;
-                const double* row = Q + yy * mx;
-                double* orow = dst + (long long)yy * nx;
-                double E = 0.0, O = 0.0;
-                for (int ks = 0; ks < d.nks; ++ks) E = fma(fx.S[ks * d.la + q], row[2 * ks + d.s0], E);
-                for (int ka = 0; ka < d.nka; ++ka) O = fma(fx.A[ka * d.lb + q], row[2 * ka + 1 - d.s0], O);
-                const int x1 = d.off + q, x2 = mx - 1 - q;
-                if (x1 >= ox0 && x1 < ox0 + onx) orow[x1] = E + O;
-                if (x2 >= ox0 && x2 < ox0 + onx) orow[x2] = E - O;
-            } else {
-                const int yy = t - npp;
-                const double* row = Q + yy * mx;
-                double E = 0.0;
-                for (int ks = 0; ks < d.nks; ++ks) E = fma(fx.S[ks * d.la + d.npair], row[2 * ks + d.s0], E);
-                if (d.mid >= ox0 && d.mid < ox0 + onx) dst[(long long)yy * nx + d.mid] = E;
-            }
+    {   // inverse along x, owned columns only; items ordered item-major, so a
+        // warp takes one kind of item (pair, quadruple or middle) of many rows
+        const int q0 = first_owned_pair(fx, ox0, ox0 + onx);
+        const int ni = f3_items(fx, q0);
+        for (int t = threadIdx.x; t < ony * ni; t += blockDim.x) {
+            const int item = t / ony, yy = t - item * ony;
+            const double* row = Q + yy * mx;
+            double* orow = dst + (long long)yy * nx;
+            f3_inverse_item(fx, TX, q0, item, [&](int k) { return row[k]; }, [&](int x, double v) {
+                if (x >= ox0 && x < ox0 + onx) orow[x] = v;
+            });
         }
-        if (d.off == 1 && ox0 == 0)
+        if (fx.off == 1 && ox0 == 0)
             for (int yy = threadIdx.x; yy < ony; yy += blockDim.x) dst[(long long)yy * nx] = 0.0;
     }
 }

@@ -25,7 +25,7 @@ struct FmpBox {
     int dct_off[3];    // offset of the m x m DCT-II table of axis a in tabs
     int dst_off[3];    // offset of the m x m DST-I table of axis a in tabs
     int sig_off[3];    // offset of the m singular values of axis a in tabs
-    int dctf_off[3];   // folded DCT-II table of axis a (see FoldDims)
+    int dctf_off[3];   // folded DCT-II table of axis a (see Fold3)
     int dstf_off[3];   // folded DST-I table of axis a
     int mpc_off[3];    // reduced-precision DCT-II T and T^T (padded to 16) of axis a
     int mps_off[3];    // reduced-precision DST-I T and T^T of axis a
@@ -34,30 +34,77 @@ struct FmpBox {
     double eps_bar;    // subdomain-mean edge permittivity
 };
 
-// Even/odd folding of a 1-D table T (m x m) with the mirror symmetry
-// T[k][m-1-q'] = +-T[k][p_q] that DCT-II and (zero-padded) DST-I both have:
-// input pairs (p_q, p'_q) = (off + q, m - 1 - q), q < npair, plus a middle
-// index when m - off is odd; output rows split by the parity of k into a
-// 'sym' class (k = 2 ks + s0, combines x_p + x_p') and an 'anti' class
-// (k = 2 ka + 1 - s0, combines x_p - x_p'). The folded table is
-// FS[ks][q] = T[2ks+s0][p_q] (q < npair; column npair = T[k][mid] when
-// there is a middle) followed by FA[ka][q] = T[2ka+1-s0][p_q]. DCT-II: off = 0,
-// s0 = 0; DST-I: off = 1 (slot 0 is the wall), s0 = 1.
-struct FoldDims {
-    int off, npair, has_mid, mid, s0, nks, nka, la, lb;
+// Two-level even/odd folding of a DCT-II or zero-padded DST-I table T of
+// extent m (the first stages of a fast transform), as three classes of
+// output modes, each a dense product on its own folded inputs.
+// First level: input pairs (off + q, m - 1 - q), q < npair, plus a middle
+// index mid when m - off is odd. The sym class (modes k = 2 ks + s0) sees the
+// pair sums and the middle, the anti class (k = 2 ka + 1 - s0) the pair
+// differences. DCT-II: off = 0, s0 = 0; DST-I: off = 1 (slot 0 is the
+// wall), s0 = 1.
+// Second level (m even, m >= 4): one first-level class (DCT-II's sym class,
+// DST-I's anti class) has the mirror symmetry again over its L inputs. Its
+// modes split by the row's mirror sign: class 0 sees the second-level sums
+// (and the middle of an odd L), class 1 the differences, both with modes
+// k = k0 + 4 j. The other first-level class is class 2. The DST-I mode k = 0
+// (the wall) then belongs to no class and is zero.
+// m odd or < 4: class 0 = sym, class 1 = anti, class 2 empty.
+// Table layout: class c's rows T_c[j][q] (len[c] columns) at offset toff[c];
+// T_c[j][q] = T[k0[c] + kstep[c] j][first-level column of input q].
+struct Fold3 {
+    int m, off, npair, has_mid, mid;
+    int two;     // the second level applies
+    int s2sym;   // the class folded twice is the sym class (DCT-II) or the anti class (DST-I)
+    int L;       // that class's first-level input count
+    int n[3], len[3], k0[3], kstep[3], seg[3], toff[3];
+    int nmodes;  // modes produced (m, or m - 1 when the DST-I wall mode is skipped)
+    int tab;     // table size (doubles)
 };
-__host__ __device__ inline FoldDims fold_dims(int m, bool dst) {
-    FoldDims f;
+__host__ __device__ inline Fold3 fold3(int m, bool dst) {
+    Fold3 f{};
+    f.m = m;
     f.off = dst ? 1 : 0;
     f.npair = (m - f.off) / 2;
     f.has_mid = (m - f.off) & 1;
     f.mid = f.off + f.npair;
-    f.s0 = dst ? 1 : 0;
-    f.nks = (m - f.s0 + 1) / 2;
-    f.nka = (m - (1 - f.s0) + 1) / 2;
-    f.la = f.npair + f.has_mid;
-    f.lb = f.npair;
+    const int s0 = dst ? 1 : 0;
+    const int nks = (m - s0 + 1) / 2, nka = (m - (1 - s0) + 1) / 2;
+    const int la = f.npair + f.has_mid, lb = f.npair;
+    f.two = (m % 2 == 0 && m >= 4) ? 1 : 0;
+    if (!f.two) {
+        f.s2sym = 1;
+        f.L = 0;
+        f.n[0] = nks; f.len[0] = la; f.k0[0] = s0; f.kstep[0] = 2;
+        f.n[1] = nka; f.len[1] = lb; f.k0[1] = 1 - s0; f.kstep[1] = 2;
+        f.n[2] = 0; f.len[2] = 0; f.k0[2] = 0; f.kstep[2] = 0;
+    } else if (!dst) {
+        f.s2sym = 1;
+        f.L = la;
+        f.n[0] = (nks + 1) / 2; f.len[0] = la / 2 + (la & 1); f.k0[0] = 0; f.kstep[0] = 4;
+        f.n[1] = nks / 2; f.len[1] = la / 2; f.k0[1] = 2; f.kstep[1] = 4;
+        f.n[2] = nka; f.len[2] = lb; f.k0[2] = 1; f.kstep[2] = 2;
+    } else {
+        f.s2sym = 0;
+        f.L = lb;
+        f.n[0] = nka / 2; f.len[0] = lb / 2 + (lb & 1); f.k0[0] = 2; f.kstep[0] = 4;
+        f.n[1] = (nka - 1) / 2; f.len[1] = lb / 2; f.k0[1] = 4; f.kstep[1] = 4;
+        f.n[2] = nks; f.len[2] = la; f.k0[2] = 1; f.kstep[2] = 2;
+    }
+    f.seg[0] = 0;
+    f.seg[1] = f.len[0];
+    f.seg[2] = f.len[0] + f.len[1];
+    f.toff[0] = 0;
+    f.toff[1] = f.n[0] * f.len[0];
+    f.toff[2] = f.toff[1] + f.n[1] * f.len[1];
+    f.tab = f.toff[2] + f.n[2] * f.len[2];
+    f.nmodes = f.n[0] + f.n[1] + f.n[2];
     return f;
+}
+// First-level column of folded input q of class c (the table is read there).
+__host__ __device__ inline int fold3_column(const Fold3& f, int c, int q) {
+    const bool sym = !f.two ? c == 0 : (c == 2 ? !f.s2sym : f.s2sym);
+    if (sym) return q < f.npair ? f.off + q : f.mid;
+    return f.off + q;
 }
 
 // Launch-shape description of one batched transform solve (the three passes).
