@@ -168,8 +168,7 @@ cudaError_t make_plan(FmpPlan& p, const std::vector<FmpBox>& boxes, cudaStream_t
     p.scratch_doubles = scr;
     std::vector<int4> A, C;
     std::vector<int2> B;
-    const int ct = fmp_column_tile(p.max_m);
-    build_items(boxes, ct, A, B, C);
+    build_items(boxes, fmp_column_tile_fp64(p.max_m), A, B, C);
     p.n_items_a = (int)A.size(); p.n_items_b = (int)B.size(); p.n_items_c = (int)C.size();
     cudaError_t e;
     if ((e = upload(&p.d_boxes, boxes, s))) return e;

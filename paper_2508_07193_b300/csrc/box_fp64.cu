@@ -412,7 +412,7 @@ cudaError_t fmp_transform_init_fp64(const FmpPlan& p) {
         return e;
     if ((e = cudaFuncSetAttribute(k_inv_xy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c(p.max_m))))
         return e;
-    if (p.max_m[2] <= 64)
+    if (fmp_column_tile_fp64(p.max_m) == 32)
         return cudaFuncSetAttribute(k_z_solve<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem_b<32>(p.max_m));
     return cudaFuncSetAttribute(k_z_solve<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -423,7 +423,7 @@ cudaError_t fmp_launch_transform_solve_fp64(const FmpPlan& p, const double* tabs
                                             const double* r, double* z, double* scratch, int nx, int ny, int nz,
                                             double beta, cudaStream_t s, const double* gate) {
     const size_t sa = smem_a(p.max_m), sc = smem_c(p.max_m);
-    const bool wide = p.max_m[2] <= 64;
+    const bool wide = fmp_column_tile_fp64(p.max_m) == 32;
     const size_t sb = wide ? smem_b<32>(p.max_m) : smem_b<16>(p.max_m);
     k_fwd_xy<<<p.n_items_a, kThreads, sa, s>>>(r, scratch, p.d_boxes, p.d_items_a, tabs, nx, ny, nz, gate);
     if (wide)
@@ -435,3 +435,6 @@ cudaError_t fmp_launch_transform_solve_fp64(const FmpPlan& p, const double* tabs
 }
 
 int fmp_column_tile(const int* max_m) { return max_m[2] <= 64 ? 32 : 16; }
+// Float64 pass B: 16-column tiles (half the shared memory of 32, so twice the
+// CTAs per SM hide the latency of its barrier-separated phases).
+int fmp_column_tile_fp64(const int* max_m) { (void)max_m; return 16; }

@@ -199,6 +199,8 @@ cudaError_t fmp_launch_eps_bar(const double* eps_edge, FmpBox* d_boxes, int n_bo
                                int ny, int nz, cudaStream_t s);
 // gate: optional device flag; when *gate != 0 the kernels return at once.
 cudaError_t fmp_transform_init_fp64(const FmpPlan& p);
+int fmp_column_tile(const int* max_m);        // column tile of the reduced-precision pass B
+int fmp_column_tile_fp64(const int* max_m);   // column tile of the float64 pass B
 cudaError_t fmp_launch_transform_solve_fp64(const FmpPlan& p, const double* tabs, const double* modeinv,
                                             const double* r, double* z, double* scratch, int nx, int ny, int nz,
                                             double beta, cudaStream_t s, const double* gate);
