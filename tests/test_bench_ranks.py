@@ -1,0 +1,60 @@
+"""Host logic of bench.py's multi-GPU path on the CPU: two gloo ranks take
+the slowest rank's time and report the whole-job throughput of the replicas,
+and the reference arm runs on rank 0 only."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _rank(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    ms = 10.0 + 5.0 * rank                     # rank 1 is the slow one
+    slowest = bench.max_over_ranks(ms, world)
+    q.put((rank, slowest, bench.job_value(1000, world, slowest)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_report_the_slowest_rank_and_the_job_throughput():
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+    assert all(p.exitcode == 0 for p in procs)
+    got = sorted(q.get(timeout=10) for _ in range(2))
+    for rank, slowest, value in got:
+        assert slowest == 15.0
+        assert value == pytest.approx(2 * 1000 / 0.015)
+
+
+def test_one_rank_is_its_own_maximum():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(3.5, 1) == 3.5
+    assert bench.job_value(6, 1, 2.0) == pytest.approx(3000.0)
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    called = []
+    monkeypatch.setattr(bench, "oracle_iteration_seconds", lambda *a, **k: called.append(1) or (1.0, 0))
+    bench.run_reference(bench.argparse.Namespace(workload="grid128", steps=1, warmup=0))
+    assert not called and capsys.readouterr().out == ""
