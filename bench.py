@@ -72,6 +72,9 @@ def dist_env():
     return rank, world, local
 
 
+OZAKI_MAX_EXTENT = 40   # largest box extent of the digit-split float64 kernels
+
+
 def max_over_ranks(value, world, device="cpu"):
     """The largest `value` over the ranks of the default process group (the
     value itself for one rank): the timing rule takes the slowest rank."""
@@ -525,7 +528,10 @@ def run_ours(args):
     # the other preconditioner precisions on the same workload, same protocol
     if not args.no_forms and args.form == "yee":
         forms = {}
-        for p in ("fp64", "bf16", "fp16", "tf32"):
+        max_ext = max(max(ctx.box(i)["m"]) for i in range(ctx.num_boxes()))
+        for p in ("fp64", "fp64_ozaki", "bf16", "fp16", "tf32"):
+            if p == "fp64_ozaki" and max_ext > OZAKI_MAX_EXTENT:
+                continue
             if p == args.precision:
                 forms[p] = {"ms_per_step": ms, "iters": iters[0] if iters else None, "true_rel_res_max": true_res,
                             "precond_ms": ms_p}

@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define FMP_ABI_VERSION 3
+#define FMP_ABI_VERSION 4
 
 typedef struct fmp_ctx fmp_ctx; /* opaque, library-owned */
 
@@ -64,7 +64,17 @@ typedef enum fmp_precision {
     FMP_PREC_FP64 = 0,   /* plain float64 transforms                          */
     FMP_PREC_TF32 = 1,   /* tf32 tensor-core inputs, fp32 accumulation        */
     FMP_PREC_FP16 = 2,   /* fp16 tensor-core inputs (scaled), fp32 accumulate */
-    FMP_PREC_BF16 = 3    /* bf16 tensor-core inputs, fp32 accumulation        */
+    FMP_PREC_BF16 = 3,   /* bf16 tensor-core inputs, fp32 accumulation        */
+    FMP_PREC_FP64_OZAKI = 4 /* float64-accurate transforms on bf16 tensor cores:
+                             * each line in 48-bit fixed point relative to its
+                             * largest exponent, cut into six 8-bit digit planes
+                             * (Ozaki splitting); the 21 leading plane products
+                             * accumulate exactly in fp32 and are combined in
+                             * integer arithmetic; the 3x3 (Eq. 12) in float64.
+                             * Error of one axis transform <= about 2^-46 of the
+                             * line's largest value times its length. Every box
+                             * extent must be <= 40, else FMP_ERR_UNSUPPORTED
+                             * from the preconditioner calls.                  */
 } fmp_precision;
 
 typedef enum fmp_krylov_kind {

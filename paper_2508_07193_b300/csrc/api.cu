@@ -184,6 +184,11 @@ void free_plan(FmpPlan& p) {
     p = FmpPlan{};
 }
 
+// Every box extent fits the digit-split float64 kernels.
+bool ozaki_ok(const FmpPlan& p) {
+    return p.max_m[0] <= FMP_OZAKI_MAX && p.max_m[1] <= FMP_OZAKI_MAX && p.max_m[2] <= FMP_OZAKI_MAX;
+}
+
 bool dt_matches(double beta, double dt) {
     const double b2 = dt * dt / 4.0;
     return std::fabs(b2 - beta) <= 1e-12 * std::fabs(beta);
@@ -204,6 +209,12 @@ int fmp_precond_gated(fmp_ctx* c, const double* r, double* z, const double* gate
             c->launches += 3;
             FMP_CK(fmp_launch_transform_solve_fp64(c->ras, c->d_tabs, c->d_modeinv, r, z, c->d_scratch, c->nx, c->ny, c->nz,
                                                    c->beta, c->stream, gate));
+            return FMP_OK;
+        case FMP_PREC_FP64_OZAKI:
+            if (!ozaki_ok(c->ras)) return FMP_ERR_UNSUPPORTED;
+            c->launches += 3;
+            FMP_CK(fmp_launch_transform_solve_ozaki(c->ras, c->d_tab_oz, c->d_tabs, c->d_modeinv, r, z, c->d_scratch,
+                                                    c->nx, c->ny, c->nz, c->beta, c->stream, gate));
             return FMP_OK;
         case FMP_PREC_BF16:
         case FMP_PREC_FP16:
@@ -265,7 +276,7 @@ void fmp_default_options(fmp_options* o) {
 }
 
 static int check_options(const fmp_options* o) {
-    if (o->precision < FMP_PREC_FP64 || o->precision > FMP_PREC_BF16) return FMP_ERR_ARG;
+    if (o->precision < FMP_PREC_FP64 || o->precision > FMP_PREC_FP64_OZAKI) return FMP_ERR_ARG;
     if (o->krylov != FMP_KRYLOV_FGMRES && o->krylov != FMP_KRYLOV_BICGSTAB) return FMP_ERR_ARG;
     if (o->restart < 1 || o->restart > FMP_MAX_RESTART) return FMP_ERR_ARG;
     if (!(o->rtol > 0.0) || o->max_iters < 1) return FMP_ERR_ARG;
@@ -367,9 +378,22 @@ int fmp_setup(fmp_ctx** out, fmp_grid g, const double* eps_cell, double beta, co
         off_mps[m] = (int)mp.size() + 2 * M * M;
         mp_tables(m, &tabs[off_c[m]], &tabs[off_s[m]], mp);
     }
+    // digit planes of the digit-split float64 transforms (extents <= FMP_OZAKI_MAX)
+    std::vector<uint32_t> oz;
+    std::map<int, int> off_oz, exp_oz;
+    for (auto& kv : ext_index) {
+        const int m = kv.first;
+        if (m > FMP_OZAKI_MAX) continue;
+        off_oz[m] = (int)oz.size();
+        int F = 0;
+        fmp_ozaki_tables(m, &tabs[off_c[m]], &tabs[off_s[m]], oz, &F);
+        exp_oz[m] = F;
+    }
     long long scr = 0;
     for (FmpBox& b : boxes) {
         for (int a = 0; a < 3; ++a) {
+            b.oz_off[a] = off_oz.count(b.m[a]) ? off_oz[b.m[a]] : -1;
+            b.oz_F[a] = off_oz.count(b.m[a]) ? exp_oz[b.m[a]] : 0;
             b.dct_off[a] = off_c[b.m[a]];
             b.dst_off[a] = off_s[b.m[a]];
             b.sig_off[a] = off_sig[b.m[a]];
@@ -407,6 +431,7 @@ int fmp_setup(fmp_ctx** out, fmp_grid g, const double* eps_cell, double beta, co
         SETUP_CK(upload(&df, tf, c->stream));
         c->d_tab_mp[2] = df;
     }
+    if (!oz.empty()) SETUP_CK(upload(&c->d_tab_oz, oz, c->stream));
     c->tab_len = tabs.size();
     SETUP_CK(cudaMalloc(&c->d_eps_edge, sizeof(double) * c->n_slots));
     if (eps_cell) {
@@ -419,6 +444,7 @@ int fmp_setup(fmp_ctx** out, fmp_grid g, const double* eps_cell, double beta, co
     SETUP_CK(fmp_transform_init_fp64(c->ras));
     SETUP_CK(fmp_transform_init_mixed(c->ras));
     SETUP_CK(fmp_fused_init());
+    SETUP_CK(fmp_transform_init_ozaki());
     SETUP_CK(cudaMalloc(&c->d_bscale, sizeof(double) * boxes.size()));
     SETUP_CK(fmp_krylov_init());
     SETUP_CK(fmp_launch_eps_bar(c->d_eps_edge, c->ras.d_boxes, c->ras.n_boxes, g.nx, g.ny, g.nz, c->stream));
@@ -466,6 +492,7 @@ void fmp_destroy(fmp_ctx* c) {
     cudaFree(c->d_V); cudaFree(c->d_Z); cudaFree(c->d_w); cudaFree(c->d_tmp); cudaFree(c->d_tmp2);
     cudaFree(c->d_partials); cudaFree(c->d_state); cudaFree(c->d_ticket);
     for (int t = 0; t < 3; ++t) cudaFree(c->d_tab_mp[t]);
+    cudaFree(c->d_tab_oz);
     cudaFree(c->d_bscale);
     cudaFree(c->d_eps_cell);
     cudaFree(c->d_tmp3); cudaFree(c->d_tmp4); cudaFree(c->d_tmp5);
@@ -645,7 +672,8 @@ int fmp_precond_apply(fmp_ctx* c, const double* r, double* z) {
 int fmp_box_solve(fmp_ctx* c, int i, const double* r, double* x) {
     if (!valid_ctx(c) || !r || !x || r == x || i < 0 || i >= (int)c->h_boxes.size()) return FMP_ERR_ARG;
     if (int rc = latched(c)) return rc;
-    if (c->opt.precision != FMP_PREC_FP64) return FMP_ERR_UNSUPPORTED;
+    const bool oz = c->opt.precision == FMP_PREC_FP64_OZAKI;
+    if (c->opt.precision != FMP_PREC_FP64 && !oz) return FMP_ERR_UNSUPPORTED;
     // a one-box plan on the box-local array: the box is its own grid, owned = all
     FmpBox b = c->h_boxes[i];
     b.ext_lo[0] = b.ext_lo[1] = b.ext_lo[2] = 0;
@@ -659,9 +687,14 @@ int fmp_box_solve(fmp_ctx* c, int i, const double* r, double* x) {
         FMP_CK(fmp_transform_init_fp64(c->single));
         c->single_box = i;
     }
+    if (oz && !ozaki_ok(c->single)) return FMP_ERR_UNSUPPORTED;
     c->launches += 3;
-    FMP_CK(fmp_launch_transform_solve_fp64(c->single, c->d_tabs, c->d_modeinv, r, x, c->d_scratch1, b.m[0], b.m[1], b.m[2],
-                                           c->beta, c->stream, nullptr));
+    if (oz)
+        FMP_CK(fmp_launch_transform_solve_ozaki(c->single, c->d_tab_oz, c->d_tabs, c->d_modeinv, r, x, c->d_scratch1,
+                                                b.m[0], b.m[1], b.m[2], c->beta, c->stream, nullptr));
+    else
+        FMP_CK(fmp_launch_transform_solve_fp64(c->single, c->d_tabs, c->d_modeinv, r, x, c->d_scratch1, b.m[0], b.m[1],
+                                               b.m[2], c->beta, c->stream, nullptr));
     return FMP_OK;
 }
 

@@ -1,0 +1,514 @@
+// Float64-accurate batched subdomain exact solve on bf16 tensor cores: the
+// transforms of Algorithm 1 (exact_solve, Sec. III-A Steps 1-3) as exact
+// products of 8-bit digit planes (Ozaki et al.'s error-free splitting of a
+// matrix product), the closed-form 3x3 inverse per mode (Eq. 12) in float64.
+//
+// Splitting. A transform contracts lines x of K <= 40 values. Each line is
+// written in 48-bit fixed point relative to its largest binary exponent emax
+// (the biased float64 exponent field):
+//     X_k = round(x_k 2^(1069 - emax)),  |X_k| <= 2^47,
+// and X is cut into six balanced base-256 digits d_0 (most significant) ..
+// d_5, integers in [-128, 128], exact in bf16. Every table T of extent m
+// (|T| <= 2^F) gets the same treatment once on the host,
+//     Y = round(T 2^(47 - F)).
+// Digit planes p of the data and q of the table meet at weight
+// 256^(10 - p - q). The 21 plane pairs with p + q <= 5 are summed per class
+// g = p + q by mma.sync into six fp32 accumulators; with K <= 40 every partial
+// sum is an integer of magnitude below 6 * 40 * 2^14 < 2^22, so the tensor-core
+// accumulation is exact. The classes are combined in 64-bit integer
+// arithmetic, Z = sum_g acc_g 256^(5 - g), and Z 2^(emax + F - 1076) is rounded
+// once to float64. The dropped classes and the two input roundings bound the
+// error of one axis transform by about K 2^-46 of the line's largest value.
+// Apart from the 3x3, no float64 instruction is executed: float64 values are
+// taken apart and assembled with integer operations.
+//
+// Same three passes and work lists as the reduced-precision path (gather +
+// forward x/y per z-slab; forward z, 3x3 and inverse z per column tile;
+// inverse y/x per owned z-slab), with the intermediate field in float64.
+// Lines are the MMA rows (A operand, digit planes cut into shared memory),
+// table modes the columns (B operand: the tables' digit planes are stored in
+// mma fragment order and read straight from the L1/L2-resident table, one
+// 16-byte load per lane and plane pair, so shared memory holds only the
+// field and its digits and three CTAs fit per SM).
+#include "fmp_internal.h"
+
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+
+namespace {
+
+constexpr int kT = 256;   // 8 warps
+constexpr int kW = kT / 32;
+constexpr int kD = 6;     // digits per value
+constexpr int kCT = 16;   // pass B column tile (lines)
+constexpr int kMaxM = FMP_OZAKI_MAX;
+
+__host__ __device__ constexpr int rup(int v, int a) { return (v + a - 1) / a * a; }
+__host__ __device__ constexpr int oz_np(int m) { return rup(m, 8); }       // modes, padded to the MMA n
+__host__ __device__ constexpr int oz_kp(int m) { return rup(m, 16); }      // contraction, padded to the MMA k
+__host__ __device__ constexpr int oz_lk(int m) { return rup(m, 16) + 8; }  // shared row stride (conflict-free ldmatrix)
+// One table in fragment order: for mode tile nt (8 modes), k-step ks (16) and
+// plane pair qq, 32 lanes x uint4 = the B fragments of planes 2 qq and 2 qq + 1.
+// An extent holds [C][C^T][S][S^T] as Bt[n][k] (forward: n = mode; inverse:
+// n = slot). Sizes in 32-bit words.
+__host__ __device__ constexpr int oz_tabf(int m) { return (oz_np(m) / 8) * (oz_kp(m) / 16) * (kD / 2) * 32 * 4; }
+
+constexpr int kRows = rup(kMaxM, 16);              // lines per digit buffer
+constexpr int kDigS = kD * kRows * oz_lk(kMaxM);   // digit buffer (elements)
+constexpr int kLine = kMaxM | 1;                          // odd stride of float64 line buffers
+
+// ---- digits ----------------------------------------------------------------
+
+__device__ __forceinline__ int hexp(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
+
+// Balanced base-256 digits of v in 48-bit fixed point relative to emax, as
+// fp32 bit patterns f[p] of the integers d_p (p = 0 most significant). With
+// the bias C = 128 (256^6 - 1) / 255, the digits d_p + 128 of X + C are its
+// plain bytes, so all six come out independently (no carry chain).
+constexpr long long kBias = 128LL * ((1LL << 48) - 1) / 255;
+__device__ __forceinline__ void to_digits(double v, int emax, uint32_t (&f)[kD]) {
+    const int hi = __double2hiint(v);
+    const unsigned lo = (unsigned)__double2loint(v);
+    const int e = (hi >> 20) & 0x7ff;
+    const int sh = emax - e + 6;   // >= 6
+    long long X = 0;
+    if (e != 0 && sh < 60) {
+        const unsigned long long M = ((unsigned long long)(((unsigned)hi & 0xfffffu) | 0x100000u) << 32) | lo;
+        X = (long long)((M + (1ull << (sh - 1))) >> sh);
+        if (hi < 0) X = -X;
+    }
+    const unsigned long long Y = (unsigned long long)(X + kBias);
+    const unsigned yl = (unsigned)Y, yh = (unsigned)(Y >> 32);
+    // fp32 of (byte - 128) through the magic number 1.5 * 2^23 (exact)
+    f[5] = __float_as_uint(__uint_as_float(0x4B3FFF80u + (yl & 0xffu)) - 12582912.0f);
+    f[4] = __float_as_uint(__uint_as_float(0x4B3FFF80u + __byte_perm(yl, 0, 0x4441)) - 12582912.0f);
+    f[3] = __float_as_uint(__uint_as_float(0x4B3FFF80u + __byte_perm(yl, 0, 0x4442)) - 12582912.0f);
+    f[2] = __float_as_uint(__uint_as_float(0x4B3FFF80u + (yl >> 24)) - 12582912.0f);
+    f[1] = __float_as_uint(__uint_as_float(0x4B3FFF80u + (yh & 0xffu)) - 12582912.0f);
+    f[0] = __float_as_uint(__uint_as_float(0x4B3FFF80u + (yh >> 8)) - 12582912.0f);
+}
+
+// Ex[l] = the largest exponent field of line l < nlines (warp per line,
+// lanes over k < K <= 64).
+template <class Get>
+__device__ __forceinline__ void line_exponents(Get get, int nlines, int K, int* Ex) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int l = warp; l < nlines; l += kW) {
+        int e = lane < K ? hexp(get(l, lane)) : 0;
+        if (lane + 32 < K) e = max(e, hexp(get(l, lane + 32)));
+        e = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
+        if (lane == 0) Ex[l] = e;
+    }
+}
+
+// Digit planes of lines l < nlines at rows l of D ([kD][.][LK], plane stride
+// ps): one thread per element pair (2j, 2j + 1), bf16 pairs stored as one
+// word; pairs from (K + 1) / 2 to Kp / 2 get zero digits. get(l, k) is called
+// for k < K only.
+template <class Get>
+__device__ __forceinline__ void line_digits(Get get, int nlines, int K, int Kp, uint16_t* D, int ps, int LK,
+                                            const int* Ex) {
+    const int P = (K + 1) >> 1, lpp = kT / P;
+    const int lt = threadIdx.x / P, j = threadIdx.x - lt * P;
+    if (lt < lpp) {
+        const int k = 2 * j;
+        for (int l = lt; l < nlines; l += lpp) {
+            const double a = get(l, k);
+            const double b = k + 1 < K ? get(l, k + 1) : 0.0;
+            const int em = Ex[l];
+            uint32_t fa[kD], fb[kD];
+            to_digits(a, em, fa);
+            to_digits(b, em, fb);
+            uint32_t* row = reinterpret_cast<uint32_t*>(D + l * LK) + j;
+#pragma unroll
+            for (int p = 0; p < kD; ++p) row[p * (ps >> 1)] = __byte_perm(fa[p], fb[p], 0x7632);
+        }
+    }
+    const int P2 = Kp >> 1, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (P < P2)
+        for (int l = warp; l < nlines; l += kW)
+            for (int jj = P + lane; jj < P2; jj += 32)
+#pragma unroll
+                for (int p = 0; p < kD; ++p) reinterpret_cast<uint32_t*>(D + p * ps + l * LK)[jj] = 0u;
+}
+
+// Z 2^(emax + F - 1076) rounded to float64, Z = sum_g acc_g 256^(5 - g) with
+// acc_g exact integers below 2^22 in magnitude (integer operations only).
+__device__ __forceinline__ double combine(const float (&acc)[kD][4], int i, int emax, int F) {
+    if (emax >= 2047) return __longlong_as_double(0x7ff8000000000000LL);   // Inf / NaN in the line
+    // i_g = bits(acc_g + 1.5 * 2^23) - bits(1.5 * 2^23); pairs i_g 256 + i_(g+1)
+    // fit 31 bits (wrapping unsigned arithmetic, exact result)
+    unsigned u[kD];
+#pragma unroll
+    for (int g = 0; g < kD; ++g) u[g] = __float_as_uint(acc[g][i] + 12582912.0f);
+    const int A = (int)(u[0] * 256u + u[1] - 257u * 0x4B400000u);
+    const int Bq = (int)(u[2] * 256u + u[3] - 257u * 0x4B400000u);
+    const int Cq = (int)(u[4] * 256u + u[5] - 257u * 0x4B400000u);
+    const long long Z = (long long)((unsigned long long)(unsigned)A << 32) + (long long)Bq * 65536LL + (long long)Cq;
+    if (Z == 0) return 0.0;
+    const bool neg = Z < 0;
+    unsigned long long a = neg ? (unsigned long long)(-Z) : (unsigned long long)Z;
+    const int lz = __clzll((long long)a);
+    a <<= lz;
+    unsigned long long mant = (a >> 11) + ((a >> 10) & 1ull);   // 53 bits, rounded half up
+    int field = emax + F - lz + 10;
+    if (mant >> 53) { mant >>= 1; ++field; }
+    if (field <= 0) return 0.0;
+    const unsigned sgn = neg ? 0x80000000u : 0u;
+    if (field >= 2047) return __hiloint2double((int)(sgn | 0x7ff00000u), 0);
+    return __hiloint2double((int)(sgn | ((unsigned)field << 20) | ((unsigned)(mant >> 32) & 0xfffffu)),
+                            (int)(unsigned)mant);
+}
+
+// ---- MMA -------------------------------------------------------------------
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const uint16_t* p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// One 16-line x 8-mode tile: out(line, n) = sum_k Bt[n][k] x_line[k], from the
+// data digit planes D ([kD][.][LKd], plane stride dps) at rows m0.. and the
+// fragment-order table Tf at mode tile nt, over ksteps k16 steps. The data
+// planes stream through one fragment at a time (the six table planes stay in
+// registers). epi(line, n, value) gets the outputs with line < lhi and
+// nlo <= n < nhi.
+template <class Epi>
+__device__ __forceinline__ void oz_tile(const uint16_t* D, int dps, int LKd, const int* Ex,
+                                        const uint4* __restrict__ Tf, int F, int m0, int nt, int ksteps, int lhi,
+                                        int nlo, int nhi, Epi epi) {
+    const int lane = threadIdx.x & 31;
+    float acc[kD][4];
+#pragma unroll
+    for (int g = 0; g < kD; ++g) acc[g][0] = acc[g][1] = acc[g][2] = acc[g][3] = 0.f;
+    const uint16_t* ap = D + (m0 + (lane & 15)) * LKd + (lane >> 4) * 8;
+    const uint4* tp = Tf + (size_t)nt * ksteps * (kD / 2) * 32 + lane;
+    for (int ks = 0; ks < ksteps; ++ks) {
+        uint32_t b[kD][2];
+#pragma unroll
+        for (int qq = 0; qq < kD / 2; ++qq) {
+            const uint4 v = __ldg(tp + (ks * (kD / 2) + qq) * 32);
+            b[2 * qq][0] = v.x; b[2 * qq][1] = v.y; b[2 * qq + 1][0] = v.z; b[2 * qq + 1][1] = v.w;
+        }
+        // the 21 plane pairs with p + q <= 5
+#pragma unroll
+        for (int p = 0; p < kD; ++p) {
+            uint32_t a[4];
+            ldsm_x4(a, ap + p * dps + ks * 16);
+#pragma unroll
+            for (int g = p; g < kD; ++g) mma_bf16(acc[g], a, b[g - p][0], b[g - p][1]);
+        }
+    }
+    const int r = lane >> 2, cc = 2 * (lane & 3);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int line = m0 + r + (i >> 1) * 8, n = nt * 8 + cc + (i & 1);
+        if (line < lhi && n >= nlo && n < nhi) epi(line, n, combine(acc, i, Ex[line], F));
+    }
+}
+
+// ---- pass A: gather, forward x and y of a group of z-slabs ------------------
+// Shared: D (digits), Xs[y][x] / Pt[kx][y] (float64, one buffer: the slab is
+// dead once its digits are cut), Ex.
+constexpr size_t kSmemA = sizeof(uint16_t) * kDigS + sizeof(double) * kMaxM * kLine + sizeof(int) * kRows;
+
+__global__ void __launch_bounds__(kT, 3)
+k_oz_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox* __restrict__ boxes,
+            const int4* __restrict__ items, const uint4* __restrict__ otab, int nx, int ny, int nz,
+            const double* __restrict__ gate) {
+    if (gate && *gate != 0.0) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int4 it = items[blockIdx.x];
+    const FmpBox B = boxes[it.x];
+    const int c = it.y, z0 = it.z, zn = it.w;
+    const int mx = B.m[0], my = B.m[1], mz = B.m[2];
+    const int NX = oz_np(mx), NY = oz_np(my), KX = oz_kp(mx), KY = oz_kp(my), LX = oz_lk(mx), LY = oz_lk(my);
+    uint16_t* D = reinterpret_cast<uint16_t*>(smraw);
+    double* Pt = reinterpret_cast<double*>(D + kDigS);   // Xs[y][x], then Pt[kx][y]; stride kLine
+    int* Ex = reinterpret_cast<int*>(Pt + kMaxM * kLine);
+    const bool sx = c != 0, sy = c != 1;
+    // forward tables (C or S): Bt[k][x] = T[k][x]
+    const uint4* TX = otab + (B.oz_off[0] + (sx ? 2 : 0) * oz_tabf(mx)) / 4;
+    const uint4* TY = otab + (B.oz_off[1] + (sy ? 2 : 0) * oz_tabf(my)) / 4;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ps1 = kRows * LX, ps2 = kRows * LY;
+    const int mt1 = oz_kp(my) / 16, nt1 = NX / 8, mt2 = oz_kp(mx) / 16, nt2 = NY / 8;
+    for (int kz = z0; kz < z0 + zn; ++kz) {
+        const int gk = B.ext_lo[2] + kz;
+        const double* src = r + (((long long)c * nz + gk) * ny + B.ext_lo[1]) * (long long)nx + B.ext_lo[0];
+        const bool zwall = (c != 2) && kz == 0;
+        // lines y, contraction x: the slab row by row (the box's wall slots
+        // read as zero) with each row's exponent
+        for (int y = warp; y < my; y += kW) {
+            const bool rowok = !zwall && !(c == 0 && y == 0) && !(c == 2 && y == 0);
+            const double* srow = src + (long long)y * nx;
+            int e = 0;
+            for (int x = lane; x < mx; x += 32) {
+                const double v = rowok && !(c != 0 && x == 0) ? __ldg(srow + x) : 0.0;
+                Pt[y * kLine + x] = v;
+                e = max(e, hexp(v));
+            }
+            e = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
+            if (lane == 0) Ex[y] = e;
+        }
+        __syncthreads();
+        line_digits([&](int l, int k) { return Pt[l * kLine + k]; }, my, mx, KX, D, ps1, LX, Ex);
+        __syncthreads();
+        for (int t = warp; t < mt1 * nt1; t += kW)
+            oz_tile(D, ps1, LX, Ex, TX, B.oz_F[0], (t / nt1) * 16, t % nt1, KX / 16, my, 0, mx,
+                    [&](int y, int kx, double v) { Pt[kx * kLine + y] = v; });
+        __syncthreads();
+        // lines kx, contraction y
+        auto gp = [&](int l, int k) { return Pt[l * kLine + k]; };
+        line_exponents(gp, mx, my, Ex);
+        __syncthreads();
+        line_digits(gp, mx, my, KY, D, ps2, LY, Ex);
+        __syncthreads();
+        double* out = scr + B.scr_off + ((long long)c * mz + kz) * mx * my;
+        for (int t = warp; t < mt2 * nt2; t += kW)
+            oz_tile(D, ps2, LY, Ex, TY, B.oz_F[1], (t / nt2) * 16, t % nt2, KY / 16, mx, 0, my,
+                    [&](int kx, int ky, double v) { out[ky * mx + kx] = v; });
+        __syncthreads();
+    }
+}
+
+// ---- pass B: forward z, 3x3 (float64), inverse z on owned slabs ------------
+// Shared: the digits of 3 x kCT lines (row = component * kCT + column),
+// V[line][z] (float64, stride kLine), Ex[line].
+constexpr int kLB = 3 * kCT;   // lines of pass B
+constexpr size_t kSmemB = sizeof(uint16_t) * kD * kLB * oz_lk(kMaxM) + sizeof(double) * kLB * kLine +
+                          sizeof(int) * kLB;
+
+__global__ void __launch_bounds__(kT, 3)
+k_oz_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int4* __restrict__ items,
+             const uint4* __restrict__ otab, const double* __restrict__ tabs, const double* __restrict__ modeinv,
+             double beta, const double* __restrict__ gate) {
+    if (gate && *gate != 0.0) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int4 itb = items[blockIdx.x];
+    const FmpBox B = boxes[itb.x];
+    const int gcol0 = itb.y, gcols = itb.z;
+    const int mx = B.m[0], my = B.m[1], mz = B.m[2];
+    const int nxy = mx * my;
+    const int NZ = oz_np(mz), KZ = oz_kp(mz), LZ = oz_lk(mz);
+    uint16_t* D = reinterpret_cast<uint16_t*>(smraw);        // [kD][kLB][LZ]
+    double* V = reinterpret_cast<double*>(D + kD * kLB * oz_lk(kMaxM));   // [kLB][kLine]
+    int* Ex = reinterpret_cast<int*>(V + kLB * kLine);                    // [kLB]
+    const uint4* tb = otab + B.oz_off[2] / 4;
+    const int tf = oz_tabf(mz) / 4;
+    const uint4 *TCf = tb, *TCi = tb + tf, *TSf = tb + 2 * tf, *TSi = tb + 3 * tf;
+    const int F = B.oz_F[2];
+    const int ps = kLB * LZ;
+    const double* sgx = tabs + B.sig_off[0];
+    const double* sgy = tabs + B.sig_off[1];
+    const double* sgz = tabs + B.sig_off[2];
+    const double beb = beta / B.eps_bar;
+    const double* inv_tab = modeinv + B.inv_off;
+    double* S = scr + B.scr_off;
+    const int oz0 = B.own_lo[2], oz1 = B.own_lo[2] + B.own_n[2];
+    const int nlo = oz0 / 8, nn = rup(oz1, 8) / 8 - nlo, nf = NZ / 8;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    auto gv = [&](int l, int k) { return V[l * kLine + k]; };
+    for (int col0 = gcol0; col0 < gcol0 + gcols; col0 += kCT) {
+        const int ncol = min(kCT, gcol0 + gcols - col0);
+        // V[c * kCT + col][z]; lines past ncol hold stale values whose
+        // outputs are never stored
+        for (int cz = warp; cz < 3 * mz; cz += kW) {
+            const int cc = cz / mz, z = cz - cc * mz;
+            const double* srow = S + (long long)cz * nxy + col0;
+            for (int col = lane; col < ncol; col += 32) V[(cc * kCT + col) * kLine + z] = srow[col];
+        }
+        __syncthreads();
+        line_exponents(gv, kLB, mz, Ex);
+        __syncthreads();
+        line_digits(gv, kLB, mz, KZ, D, ps, LZ, Ex);
+        __syncthreads();
+        // forward z (DST-I for Ex, Ey; DCT-II for Ez), modes back into V
+        for (int t = warp; t < 3 * nf; t += kW) {
+            const int cc = t / nf, n0 = (t - cc * nf) * 8;
+            oz_tile(D, ps, LZ, Ex, cc == 2 ? TCf : TSf, F, cc * kCT, n0 / 8, KZ / 16, cc * kCT + ncol, 0, mz,
+                    [&](int l, int kz, double x) { V[l * kLine + kz] = x; });
+        }
+        __syncthreads();
+        // e_c = inv (r_c + (beta / eps_bar) sigma_c (sigma . r)), inv = 1 / (eps_bar
+        // + beta |sigma|^2) from the per-box mode table
+        for (int t = threadIdx.x; t < mz * ncol; t += kT) {
+            const int kz = t / ncol, col = t - kz * ncol;
+            const int q = col0 + col;
+            const int ky = q / mx, kx = q - ky * mx;
+            const double sx = sgx[kx], sy = sgy[ky], sz = sgz[kz];
+            double* o = V + col * kLine + kz;
+            const double r0 = o[0], r1 = o[kCT * kLine], r2 = o[2 * kCT * kLine];
+            const double inv = inv_tab[(long long)kz * nxy + q];
+            const double sr = fma(sx, r0, fma(sy, r1, sz * r2));
+            const double f = (beb * inv) * sr;
+            o[0] = fma(f, sx, inv * r0);
+            o[kCT * kLine] = fma(f, sy, inv * r1);
+            o[2 * kCT * kLine] = fma(f, sz, inv * r2);
+        }
+        __syncthreads();
+        line_exponents(gv, kLB, mz, Ex);
+        __syncthreads();
+        line_digits(gv, kLB, mz, KZ, D, ps, LZ, Ex);
+        __syncthreads();
+        // inverse z, owned slabs only
+        for (int t = warp; t < 3 * nn; t += kW) {
+            const int cc = t / nn, n0 = (nlo + t - cc * nn) * 8;
+            double* dst = S + (long long)cc * mz * nxy + col0 - (long long)cc * kCT;
+            oz_tile(D, ps, LZ, Ex, cc == 2 ? TCi : TSi, F, cc * kCT, n0 / 8, KZ / 16, cc * kCT + ncol, oz0, oz1,
+                    [&](int l, int z, double x) { dst[(long long)z * nxy + l] = x; });
+        }
+        __syncthreads();
+    }
+}
+
+// ---- pass C: inverse y and x of a group of owned z-slabs, owned scatter -----
+// Shared: D, Sm[ky][kx], Q[y][kx] (float64), Ex.
+constexpr size_t kSmemC = sizeof(uint16_t) * kDigS + sizeof(double) * 2 * kMaxM * kLine + sizeof(int) * kRows;
+
+__global__ void __launch_bounds__(kT, 3)
+k_oz_inv_xy(const double* __restrict__ scr, double* __restrict__ zout, const FmpBox* __restrict__ boxes,
+            const int4* __restrict__ items, const uint4* __restrict__ otab, int nx, int ny, int nz,
+            const double* __restrict__ gate) {
+    if (gate && *gate != 0.0) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int4 it = items[blockIdx.x];
+    const FmpBox B = boxes[it.x];
+    const int c = it.y, z0 = it.z, zn = it.w;
+    const int mx = B.m[0], my = B.m[1], mz = B.m[2];
+    const int NX = oz_np(mx), NY = oz_np(my), KX = oz_kp(mx), KY = oz_kp(my), LX = oz_lk(mx), LY = oz_lk(my);
+    const int oy0 = B.own_lo[1], ony = B.own_n[1], ox0 = B.own_lo[0], onx = B.own_n[0];
+    uint16_t* D = reinterpret_cast<uint16_t*>(smraw);
+    double* Sm = reinterpret_cast<double*>(D + kDigS);   // [ky][kx], stride kLine
+    double* Q = Sm + kMaxM * kLine;                     // [y - oy0][kx], stride kLine
+    int* Ex = reinterpret_cast<int*>(Q + kMaxM * kLine);
+    const bool sx = c != 0, sy = c != 1;
+    // inverse tables: Bt[i][k] = T[k][i]
+    const uint4* TYi = otab + (B.oz_off[1] + (sy ? 3 : 1) * oz_tabf(my)) / 4;
+    const uint4* TXi = otab + (B.oz_off[0] + (sx ? 3 : 1) * oz_tabf(mx)) / 4;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ps1 = kRows * LY, ps2 = kRows * LX;
+    const int mt1 = oz_kp(mx) / 16, ylo = oy0 / 8, nn1 = rup(oy0 + ony, 8) / 8 - ylo;
+    const int mt2 = rup(ony, 16) / 16, xlo = ox0 / 8, nn2 = rup(ox0 + onx, 8) / 8 - xlo;
+    auto gs = [&](int l, int k) { return Sm[k * kLine + l]; };   // line kx, element ky
+    auto gq = [&](int l, int k) { return Q[l * kLine + k]; };    // line y, element kx
+    for (int zl = z0; zl < z0 + zn; ++zl) {
+        const double* src = scr + B.scr_off + ((long long)c * mz + zl) * mx * my;
+        for (int ky = warp; ky < my; ky += kW)
+            for (int kx = lane; kx < mx; kx += 32) Sm[ky * kLine + kx] = src[ky * mx + kx];
+        __syncthreads();
+        line_exponents(gs, mx, my, Ex);
+        __syncthreads();
+        line_digits(gs, mx, my, KY, D, ps1, LY, Ex);
+        __syncthreads();
+        for (int t = warp; t < mt1 * nn1; t += kW)
+            oz_tile(D, ps1, LY, Ex, TYi, B.oz_F[1], (t / nn1) * 16, ylo + t % nn1, KY / 16, mx, oy0, oy0 + ony,
+                    [&](int kx, int y, double v) { Q[(y - oy0) * kLine + kx] = v; });
+        __syncthreads();
+        line_exponents(gq, ony, mx, Ex);
+        __syncthreads();
+        line_digits(gq, ony, mx, KX, D, ps2, LX, Ex);
+        __syncthreads();
+        const int gk = B.ext_lo[2] + zl;
+        double* dst = zout + (((long long)c * nz + gk) * ny + B.ext_lo[1] + oy0) * (long long)nx + B.ext_lo[0];
+        for (int t = warp; t < mt2 * nn2; t += kW)
+            oz_tile(D, ps2, LX, Ex, TXi, B.oz_F[0], (t / nn2) * 16, xlo + t % nn2, KX / 16, ony, ox0, ox0 + onx,
+                    [&](int yl, int x, double v) { dst[(long long)yl * nx + x] = v; });
+        __syncthreads();
+    }
+}
+
+// Host: balanced base-256 digits of round(t 2^(47 - F)), |t| <= 2^F.
+void host_digits(double t, int F, int (&d)[kD]) {
+    long long X = std::llround(std::ldexp(t, 47 - F));
+    for (int p = kD - 1; p > 0; --p) {
+        const int dp = (int)(signed char)(X & 0xff);
+        d[p] = dp;
+        X = (X - dp) >> 8;
+    }
+    d[0] = (int)X;
+}
+
+uint16_t host_bf16(int d) {
+    const float f = (float)d;   // |d| <= 256: exact, and exact in bf16
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return (uint16_t)(u >> 16);
+}
+
+}  // namespace
+
+int fmp_ozaki_table_len(int m) { return 4 * oz_tabf(m); }
+
+// The four tables of extent m as the column operand Bt[n][k] -- C (Bt =
+// C[k][i], forward), C^T (Bt[i][k] = C[k][i], inverse), S, S^T -- cut into
+// digit planes and stored in mma fragment order (oz_tabf), zero padded.
+// *F = the smallest exponent with every |T| <= 2^F.
+void fmp_ozaki_tables(int m, const double* C, const double* S, std::vector<uint32_t>& out, int* F) {
+    double mx = 0.0;
+    for (int q = 0; q < m * m; ++q) mx = std::fmax(mx, std::fmax(std::fabs(C[q]), std::fabs(S[q])));
+    int f = (int)std::ceil(std::log2(mx));
+    while (std::ldexp(1.0, f) < mx) ++f;
+    while (std::ldexp(1.0, f - 1) >= mx) --f;
+    *F = f;
+    const int NT = oz_np(m) / 8, KS = oz_kp(m) / 16;
+    const double* T[2] = {C, S};
+    for (int w = 0; w < 2; ++w)
+        for (int tr = 0; tr < 2; ++tr) {
+            // digit p of Bt[n][k] (zero outside n, k < m)
+            auto dig = [&](int n, int k, int p) -> uint32_t {
+                if (n >= m || k >= m) return 0u;
+                int d[kD];
+                host_digits(tr ? T[w][k * m + n] : T[w][n * m + k], f, d);
+                return host_bf16(d[p]);
+            };
+            const size_t base = out.size();
+            out.resize(base + (size_t)oz_tabf(m), 0u);
+            for (int nt = 0; nt < NT; ++nt)
+                for (int ks = 0; ks < KS; ++ks)
+                    for (int qq = 0; qq < kD / 2; ++qq)
+                        for (int lane = 0; lane < 32; ++lane)
+                            for (int j = 0; j < 4; ++j) {
+                                const int p = 2 * qq + (j >> 1);
+                                const int n = nt * 8 + lane / 4, k = ks * 16 + (j & 1) * 8 + 2 * (lane % 4);
+                                out[base + ((((size_t)nt * KS + ks) * (kD / 2) + qq) * 32 + lane) * 4 + j] =
+                                    dig(n, k, p) | (dig(n, k + 1, p) << 16);
+                            }
+        }
+}
+
+cudaError_t fmp_transform_init_ozaki() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_oz_fwd_xy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemA))) return e;
+    if ((e = cudaFuncSetAttribute(k_oz_z_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemB))) return e;
+    return cudaFuncSetAttribute(k_oz_inv_xy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemC);
+}
+
+cudaError_t fmp_launch_transform_solve_ozaki(const FmpPlan& p, const uint32_t* otab32, const double* tabs,
+                                             const double* modeinv, const double* r, double* z, double* scratch,
+                                             int nx, int ny, int nz, double beta, cudaStream_t s,
+                                             const double* gate) {
+    if (p.max_m[0] > kMaxM || p.max_m[1] > kMaxM || p.max_m[2] > kMaxM) return cudaErrorNotSupported;
+    const uint4* otab = reinterpret_cast<const uint4*>(otab32);
+    if (p.n_items_ga > 0)
+        k_oz_fwd_xy<<<p.n_items_ga, kT, kSmemA, s>>>(r, scratch, p.d_boxes, p.d_items_ga, otab, nx, ny, nz, gate);
+    if (p.n_items_gb > 0)
+        k_oz_z_solve<<<p.n_items_gb, kT, kSmemB, s>>>(scratch, p.d_boxes, p.d_items_gb, otab, tabs, modeinv, beta,
+                                                      gate);
+    if (p.n_items_gc > 0)
+        k_oz_inv_xy<<<p.n_items_gc, kT, kSmemC, s>>>(scratch, z, p.d_boxes, p.d_items_gc, otab, nx, ny, nz, gate);
+    return cudaGetLastError();
+}

@@ -14,6 +14,7 @@
 #define FMP_MP_SLAB_GROUP 4   // z-slabs per CTA in the reduced-precision passes A and C
 #define FMP_MP_TILE_GROUP 4   // column tiles per CTA in the reduced-precision pass B
 #define FMP_FUSED_MAX 40      // largest extent of a box solved by the fused cluster kernel
+#define FMP_OZAKI_MAX 40      // largest extent of the digit-split float64 kernels
 
 // Device-side descriptor of one subdomain box (Sec. II-B). Coordinates are
 // in cells, ordered (x, y, z).
@@ -29,6 +30,8 @@ struct FmpBox {
     int dstf_off[3];   // folded DST-I table of axis a
     int mpc_off[3];    // reduced-precision DCT-II T and T^T (padded to 16) of axis a
     int mps_off[3];    // reduced-precision DST-I T and T^T of axis a
+    int oz_off[3];     // digit-plane tables of the extent of axis a (32-bit words; digit-split float64), -1 above FMP_OZAKI_MAX
+    int oz_F[3];       // their table exponent: every |T| <= 2^F
     long long scr_off; // offset (doubles) of the box's [3][mz][my][mx] scratch
     long long inv_off; // offset of the box's [mz][my][mx] table 1 / (eps_bar + beta |sigma|^2)
     double eps_bar;    // subdomain-mean edge permittivity
@@ -162,6 +165,7 @@ struct fmp_ctx {
     double* d_scratch1 = nullptr; // scratch for one box (fmp_box_solve)
     double* d_modeinv = nullptr;  // per box and mode 1 / (eps_bar + beta |sigma|^2) (float64 pass B)
     void* d_tab_mp[3] = {};       // reduced-precision tables: bf16, fp16, tf32 (same layout)
+    uint32_t* d_tab_oz = nullptr; // digit-plane tables of the digit-split float64 transforms (fragment order)
     double* d_bscale = nullptr;   // per-box scale factors (fp16 transforms)
     double* d_eps_cell = nullptr; // cell permittivity [nz][ny][nx] (null: eps = 1)
     FmpCnn* cnn = nullptr;        // learned initial guess / correction (created on first use)
@@ -215,6 +219,15 @@ cudaError_t fmp_launch_h_update(double* H, const double* En, const double* Eo, d
                                 int nx, int ny, int nz, cudaStream_t s);
 
 cudaError_t fmp_transform_init_mixed(const FmpPlan& p);
+// Digit-split float64 solve (box_ozaki.cu): float64-accurate transforms as
+// exact products of bf16 digit planes. Every box extent must be <= FMP_OZAKI_MAX.
+cudaError_t fmp_transform_init_ozaki();
+void fmp_ozaki_tables(int m, const double* C, const double* S, std::vector<uint32_t>& out, int* F);
+int fmp_ozaki_table_len(int m);
+cudaError_t fmp_launch_transform_solve_ozaki(const FmpPlan& p, const uint32_t* otab, const double* tabs,
+                                             const double* modeinv, const double* r, double* z, double* scratch,
+                                             int nx, int ny, int nz, double beta, cudaStream_t s,
+                                             const double* gate);
 // Three-pass reduced-precision solve of the first na / nb / nc grouped items
 // (all of them for tf32; the non-fused boxes for bf16 / fp16). fp16 first
 // computes every box's scale into bscale. Returns the kernels launched in *nk.

@@ -24,7 +24,7 @@ FMP_ERR_BREAKDOWN = -5
 FMP_ERR_NONFINITE = -6
 FMP_ERR_UNSUPPORTED = -7
 
-PRECISIONS = {"fp64": 0, "tf32": 1, "fp16": 2, "bf16": 3}
+PRECISIONS = {"fp64": 0, "tf32": 1, "fp16": 2, "bf16": 3, "fp64_ozaki": 4}
 KRYLOV = {"fgmres": 0, "bicgstab": 1}
 
 
