@@ -175,12 +175,32 @@ cudaError_t make_plan(FmpPlan& p, const std::vector<FmpBox>& boxes, cudaStream_t
     if ((e = upload(&p.d_items_a, A, s))) return e;
     if ((e = upload(&p.d_items_b, B, s))) return e;
     if ((e = upload(&p.d_items_c, C, s))) return e;
+    {   // digit-split float64 lists
+        std::vector<int4> OA, OB, OC;
+        for (int b = 0; b < (int)boxes.size(); ++b) {
+            const FmpBox& x = boxes[b];
+            for (int c = 0; c < 3; ++c) {
+                for (int z = 0; z < x.m[2]; z += FMP_OZAKI_SLABS)
+                    OA.push_back(make_int4(b, c, z, std::min(FMP_OZAKI_SLABS, x.m[2] - z)));
+                const int o0 = x.own_lo[2], o1 = x.own_lo[2] + x.own_n[2];
+                for (int z = o0; z < o1; z += FMP_OZAKI_SLABS)
+                    OC.push_back(make_int4(b, c, z, std::min(FMP_OZAKI_SLABS, o1 - z)));
+            }
+            const int nxy = x.m[0] * x.m[1];
+            for (int q = 0; q < nxy; q += FMP_OZAKI_COLS) OB.push_back(make_int4(b, q, std::min(FMP_OZAKI_COLS, nxy - q), 0));
+        }
+        p.n_items_oa = (int)OA.size(); p.n_items_ob = (int)OB.size(); p.n_items_oc = (int)OC.size();
+        if ((e = upload(&p.d_items_oa, OA, s))) return e;
+        if ((e = upload(&p.d_items_ob, OB, s))) return e;
+        if ((e = upload(&p.d_items_oc, OC, s))) return e;
+    }
     return regroup(p, boxes, p.slab_group, p.tile_group, p.fused_max, s);
 }
 
 void free_plan(FmpPlan& p) {
     cudaFree(p.d_boxes); cudaFree(p.d_items_a); cudaFree(p.d_items_b); cudaFree(p.d_items_c);
     cudaFree(p.d_items_ga); cudaFree(p.d_items_gb); cudaFree(p.d_items_gc); cudaFree(p.d_items_f);
+    cudaFree(p.d_items_oa); cudaFree(p.d_items_ob); cudaFree(p.d_items_oc);
     p = FmpPlan{};
 }
 

@@ -42,7 +42,7 @@ namespace {
 constexpr int kT = 256;   // 8 warps
 constexpr int kW = kT / 32;
 constexpr int kD = 6;     // digits per value
-constexpr int kCT = 16;   // pass B column tile (lines)
+constexpr int kCT = FMP_OZAKI_COLS;   // pass B column tile (lines)
 constexpr int kMaxM = FMP_OZAKI_MAX;
 
 __host__ __device__ constexpr int rup(int v, int a) { return (v + a - 1) / a * a; }
@@ -63,7 +63,7 @@ constexpr int kLine = kMaxM | 1;                          // odd stride of float
 
 __device__ __forceinline__ int hexp(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
 
-// Balanced base-256 digits of v in 48-bit fixed point relative to emax, as
+// Balanced base-256 digits of v in 47-bit fixed point relative to emax, as
 // fp32 bit patterns f[p] of the integers d_p (p = 0 most significant). With
 // the bias C = 128 (256^6 - 1) / 255, the digits d_p + 128 of X + C are its
 // plain bytes, so all six come out independently (no carry chain).
@@ -72,11 +72,11 @@ __device__ __forceinline__ void to_digits(double v, int emax, uint32_t (&f)[kD])
     const int hi = __double2hiint(v);
     const unsigned lo = (unsigned)__double2loint(v);
     const int e = (hi >> 20) & 0x7ff;
-    const int sh = emax - e + 6;   // >= 6
+    const int sh = emax - e + 6;   // >= 6 when e <= emax (lines whose outputs are kept)
     long long X = 0;
-    if (e != 0 && sh < 60) {
+    if (e != 0 && sh >= 6 && sh < 60) {   // truncated: error below 2^-46 of the line's largest value
         const unsigned long long M = ((unsigned long long)(((unsigned)hi & 0xfffffu) | 0x100000u) << 32) | lo;
-        X = (long long)((M + (1ull << (sh - 1))) >> sh);
+        X = (long long)(M >> sh);
         if (hi < 0) X = -X;
     }
     const unsigned long long Y = (unsigned long long)(X + kBias);
@@ -88,19 +88,6 @@ __device__ __forceinline__ void to_digits(double v, int emax, uint32_t (&f)[kD])
     f[2] = __float_as_uint(__uint_as_float(0x4B3FFF80u + (yl >> 24)) - 12582912.0f);
     f[1] = __float_as_uint(__uint_as_float(0x4B3FFF80u + (yh & 0xffu)) - 12582912.0f);
     f[0] = __float_as_uint(__uint_as_float(0x4B3FFF80u + (yh >> 8)) - 12582912.0f);
-}
-
-// Ex[l] = the largest exponent field of line l < nlines (warp per line,
-// lanes over k < K <= 64).
-template <class Get>
-__device__ __forceinline__ void line_exponents(Get get, int nlines, int K, int* Ex) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int l = warp; l < nlines; l += kW) {
-        int e = lane < K ? hexp(get(l, lane)) : 0;
-        if (lane + 32 < K) e = max(e, hexp(get(l, lane + 32)));
-        e = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
-        if (lane == 0) Ex[l] = e;
-    }
 }
 
 // Digit planes of lines l < nlines at rows l of D ([kD][.][LK], plane stride
@@ -134,7 +121,7 @@ __device__ __forceinline__ void line_digits(Get get, int nlines, int K, int Kp, 
                 for (int p = 0; p < kD; ++p) reinterpret_cast<uint32_t*>(D + p * ps + l * LK)[jj] = 0u;
 }
 
-// Z 2^(emax + F - 1076) rounded to float64, Z = sum_g acc_g 256^(5 - g) with
+// Z 2^(emax + F - 1076) truncated to float64, Z = sum_g acc_g 256^(5 - g) with
 // acc_g exact integers below 2^22 in magnitude (integer operations only).
 __device__ __forceinline__ double combine(const float (&acc)[kD][4], int i, int emax, int F) {
     if (emax >= 2047) return __longlong_as_double(0x7ff8000000000000LL);   // Inf / NaN in the line
@@ -147,19 +134,16 @@ __device__ __forceinline__ double combine(const float (&acc)[kD][4], int i, int 
     const int Bq = (int)(u[2] * 256u + u[3] - 257u * 0x4B400000u);
     const int Cq = (int)(u[4] * 256u + u[5] - 257u * 0x4B400000u);
     const long long Z = (long long)((unsigned long long)(unsigned)A << 32) + (long long)Bq * 65536LL + (long long)Cq;
-    if (Z == 0) return 0.0;
     const bool neg = Z < 0;
     unsigned long long a = neg ? (unsigned long long)(-Z) : (unsigned long long)Z;
     const int lz = __clzll((long long)a);
-    a <<= lz;
-    unsigned long long mant = (a >> 11) + ((a >> 10) & 1ull);   // 53 bits, rounded half up
-    int field = emax + F - lz + 10;
-    if (mant >> 53) { mant >>= 1; ++field; }
-    if (field <= 0) return 0.0;
+    const unsigned long long mant = (a << lz) >> 11;   // 53 bits, truncated (below 1 ulp)
+    const int field = emax + F - lz + 10;
     const unsigned sgn = neg ? 0x80000000u : 0u;
-    if (field >= 2047) return __hiloint2double((int)(sgn | 0x7ff00000u), 0);
-    return __hiloint2double((int)(sgn | ((unsigned)field << 20) | ((unsigned)(mant >> 32) & 0xfffffu)),
-                            (int)(unsigned)mant);
+    unsigned hi = sgn | ((unsigned)field << 20) | ((unsigned)(mant >> 32) & 0xfffffu), lo = (unsigned)mant;
+    if (field >= 2047) { hi = sgn | 0x7ff00000u; lo = 0u; }
+    if (Z == 0 || field <= 0) { hi = 0u; lo = 0u; }
+    return __hiloint2double((int)hi, (int)lo);
 }
 
 // ---- MMA -------------------------------------------------------------------
@@ -186,10 +170,13 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
 // planes stream through one fragment at a time (the six table planes stay in
 // registers). epi(line, n, value) gets the outputs with line < lhi and
 // nlo <= n < nhi.
-template <class Epi>
+// With kExp, the largest exponent field of each output column n (the next
+// stage's line) is also folded into exo[n - eoff] (atomicMax; exo zeroed
+// beforehand).
+template <bool kExp, class Epi>
 __device__ __forceinline__ void oz_tile(const uint16_t* D, int dps, int LKd, const int* Ex,
                                         const uint4* __restrict__ Tf, int F, int m0, int nt, int ksteps, int lhi,
-                                        int nlo, int nhi, Epi epi) {
+                                        int nlo, int nhi, Epi epi, int* exo = nullptr, int eoff = 0) {
     const int lane = threadIdx.x & 31;
     float acc[kD][4];
 #pragma unroll
@@ -213,17 +200,37 @@ __device__ __forceinline__ void oz_tile(const uint16_t* D, int dps, int LKd, con
         }
     }
     const int r = lane >> 2, cc = 2 * (lane & 3);
+    int ea = 0, eb = 0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int line = m0 + r + (i >> 1) * 8, n = nt * 8 + cc + (i & 1);
-        if (line < lhi && n >= nlo && n < nhi) epi(line, n, combine(acc, i, Ex[line], F));
+        if (line < lhi && n >= nlo && n < nhi) {
+            const double v = combine(acc, i, Ex[line], F);
+            epi(line, n, v);
+            if (kExp) {
+                if (i & 1) eb = max(eb, hexp(v));
+                else ea = max(ea, hexp(v));
+            }
+        }
+    }
+    if (kExp) {
+#pragma unroll
+        for (int o = 4; o < 32; o <<= 1) {
+            ea = max(ea, __shfl_xor_sync(0xffffffffu, ea, o));
+            eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, o));
+        }
+        const int n = nt * 8 + cc;
+        if (r == 0) {
+            if (n >= nlo && n < nhi) atomicMax(exo + n - eoff, ea);
+            if (n + 1 >= nlo && n + 1 < nhi) atomicMax(exo + n + 1 - eoff, eb);
+        }
     }
 }
 
 // ---- pass A: gather, forward x and y of a group of z-slabs ------------------
 // Shared: D (digits), Xs[y][x] / Pt[kx][y] (float64, one buffer: the slab is
 // dead once its digits are cut), Ex.
-constexpr size_t kSmemA = sizeof(uint16_t) * kDigS + sizeof(double) * kMaxM * kLine + sizeof(int) * kRows;
+constexpr size_t kSmemA = sizeof(uint16_t) * kDigS + sizeof(double) * kMaxM * kLine + sizeof(int) * 2 * kRows;
 
 __global__ void __launch_bounds__(kT, 3)
 k_oz_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox* __restrict__ boxes,
@@ -238,7 +245,8 @@ k_oz_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox
     const int NX = oz_np(mx), NY = oz_np(my), KX = oz_kp(mx), KY = oz_kp(my), LX = oz_lk(mx), LY = oz_lk(my);
     uint16_t* D = reinterpret_cast<uint16_t*>(smraw);
     double* Pt = reinterpret_cast<double*>(D + kDigS);   // Xs[y][x], then Pt[kx][y]; stride kLine
-    int* Ex = reinterpret_cast<int*>(Pt + kMaxM * kLine);
+    int* Ex1 = reinterpret_cast<int*>(Pt + kMaxM * kLine);   // exponents of the x lines (rows y)
+    int* Ex2 = Ex1 + kRows;                                   // of the y lines (columns kx)
     const bool sx = c != 0, sy = c != 1;
     // forward tables (C or S): Bt[k][x] = T[k][x]
     const uint4* TX = otab + (B.oz_off[0] + (sx ? 2 : 0) * oz_tabf(mx)) / 4;
@@ -262,26 +270,25 @@ k_oz_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox
                 e = max(e, hexp(v));
             }
             e = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
-            if (lane == 0) Ex[y] = e;
+            if (lane == 0) Ex1[y] = e;
         }
         __syncthreads();
-        line_digits([&](int l, int k) { return Pt[l * kLine + k]; }, my, mx, KX, D, ps1, LX, Ex);
+        line_digits([&](int l, int k) { return Pt[l * kLine + k]; }, my, mx, KX, D, ps1, LX, Ex1);
+        for (int t = threadIdx.x; t < kRows; t += kT) Ex2[t] = 0;
         __syncthreads();
         for (int t = warp; t < mt1 * nt1; t += kW)
-            oz_tile(D, ps1, LX, Ex, TX, B.oz_F[0], (t / nt1) * 16, t % nt1, KX / 16, my, 0, mx,
-                    [&](int y, int kx, double v) { Pt[kx * kLine + y] = v; });
+            oz_tile<true>(D, ps1, LX, Ex1, TX, B.oz_F[0], (t / nt1) * 16, t % nt1, KX / 16, my, 0, mx,
+                          [&](int y, int kx, double v) { Pt[kx * kLine + y] = v; }, Ex2, 0);
         __syncthreads();
         // lines kx, contraction y
-        auto gp = [&](int l, int k) { return Pt[l * kLine + k]; };
-        line_exponents(gp, mx, my, Ex);
-        __syncthreads();
-        line_digits(gp, mx, my, KY, D, ps2, LY, Ex);
+        line_digits([&](int l, int k) { return Pt[l * kLine + k]; }, mx, my, KY, D, ps2, LY, Ex2);
         __syncthreads();
         double* out = scr + B.scr_off + ((long long)c * mz + kz) * mx * my;
         for (int t = warp; t < mt2 * nt2; t += kW)
-            oz_tile(D, ps2, LY, Ex, TY, B.oz_F[1], (t / nt2) * 16, t % nt2, KY / 16, mx, 0, my,
-                    [&](int kx, int ky, double v) { out[ky * mx + kx] = v; });
-        __syncthreads();
+            oz_tile<false>(D, ps2, LY, Ex2, TY, B.oz_F[1], (t / nt2) * 16, t % nt2, KY / 16, mx, 0, my,
+                           [&](int kx, int ky, double v) { out[ky * mx + kx] = v; });
+        // no barrier: the next slab's rows go to Pt and Ex1, which this
+        // stage no longer reads
     }
 }
 
@@ -290,7 +297,7 @@ k_oz_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox
 // V[line][z] (float64, stride kLine), Ex[line].
 constexpr int kLB = 3 * kCT;   // lines of pass B
 constexpr size_t kSmemB = sizeof(uint16_t) * kD * kLB * oz_lk(kMaxM) + sizeof(double) * kLB * kLine +
-                          sizeof(int) * kLB;
+                          sizeof(int) * 2 * kLB;
 
 __global__ void __launch_bounds__(kT, 3)
 k_oz_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int4* __restrict__ items,
@@ -306,7 +313,8 @@ k_oz_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const i
     const int NZ = oz_np(mz), KZ = oz_kp(mz), LZ = oz_lk(mz);
     uint16_t* D = reinterpret_cast<uint16_t*>(smraw);        // [kD][kLB][LZ]
     double* V = reinterpret_cast<double*>(D + kD * kLB * oz_lk(kMaxM));   // [kLB][kLine]
-    int* Ex = reinterpret_cast<int*>(V + kLB * kLine);                    // [kLB]
+    int* Ex1 = reinterpret_cast<int*>(V + kLB * kLine);   // exponents of the forward lines
+    int* Ex2 = Ex1 + kLB;                                 // of the inverse lines
     const uint4* tb = otab + B.oz_off[2] / 4;
     const int tf = oz_tabf(mz) / 4;
     const uint4 *TCf = tb, *TCi = tb + tf, *TSf = tb + 2 * tf, *TSi = tb + 3 * tf;
@@ -322,25 +330,30 @@ k_oz_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const i
     const int nlo = oz0 / 8, nn = rup(oz1, 8) / 8 - nlo, nf = NZ / 8;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     auto gv = [&](int l, int k) { return V[l * kLine + k]; };
+    for (int t = threadIdx.x; t < kLB; t += kT) Ex1[t] = 0;
+    __syncthreads();
     for (int col0 = gcol0; col0 < gcol0 + gcols; col0 += kCT) {
         const int ncol = min(kCT, gcol0 + gcols - col0);
-        // V[c * kCT + col][z]; lines past ncol hold stale values whose
-        // outputs are never stored
+        // V[c * kCT + col][z] with each line's exponent; lines past ncol keep
+        // stale values and exponent 0 (zero digits, outputs never stored)
         for (int cz = warp; cz < 3 * mz; cz += kW) {
             const int cc = cz / mz, z = cz - cc * mz;
             const double* srow = S + (long long)cz * nxy + col0;
-            for (int col = lane; col < ncol; col += 32) V[(cc * kCT + col) * kLine + z] = srow[col];
+            for (int col = lane; col < ncol; col += 32) {
+                const double v = srow[col];
+                V[(cc * kCT + col) * kLine + z] = v;
+                atomicMax(Ex1 + cc * kCT + col, hexp(v));
+            }
         }
         __syncthreads();
-        line_exponents(gv, kLB, mz, Ex);
-        __syncthreads();
-        line_digits(gv, kLB, mz, KZ, D, ps, LZ, Ex);
+        line_digits(gv, kLB, mz, KZ, D, ps, LZ, Ex1);
+        for (int t = threadIdx.x; t < kLB; t += kT) Ex2[t] = 0;
         __syncthreads();
         // forward z (DST-I for Ex, Ey; DCT-II for Ez), modes back into V
         for (int t = warp; t < 3 * nf; t += kW) {
             const int cc = t / nf, n0 = (t - cc * nf) * 8;
-            oz_tile(D, ps, LZ, Ex, cc == 2 ? TCf : TSf, F, cc * kCT, n0 / 8, KZ / 16, cc * kCT + ncol, 0, mz,
-                    [&](int l, int kz, double x) { V[l * kLine + kz] = x; });
+            oz_tile<false>(D, ps, LZ, Ex1, cc == 2 ? TCf : TSf, F, cc * kCT, n0 / 8, KZ / 16, cc * kCT + ncol, 0, mz,
+                           [&](int l, int kz, double x) { V[l * kLine + kz] = x; });
         }
         __syncthreads();
         // e_c = inv (r_c + (beta / eps_bar) sigma_c (sigma . r)), inv = 1 / (eps_bar
@@ -355,29 +368,33 @@ k_oz_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const i
             const double inv = inv_tab[(long long)kz * nxy + q];
             const double sr = fma(sx, r0, fma(sy, r1, sz * r2));
             const double f = (beb * inv) * sr;
-            o[0] = fma(f, sx, inv * r0);
-            o[kCT * kLine] = fma(f, sy, inv * r1);
-            o[2 * kCT * kLine] = fma(f, sz, inv * r2);
+            const double e0 = fma(f, sx, inv * r0), e1 = fma(f, sy, inv * r1), e2 = fma(f, sz, inv * r2);
+            o[0] = e0;
+            o[kCT * kLine] = e1;
+            o[2 * kCT * kLine] = e2;
+            atomicMax(Ex2 + col, hexp(e0));
+            atomicMax(Ex2 + kCT + col, hexp(e1));
+            atomicMax(Ex2 + 2 * kCT + col, hexp(e2));
         }
         __syncthreads();
-        line_exponents(gv, kLB, mz, Ex);
-        __syncthreads();
-        line_digits(gv, kLB, mz, KZ, D, ps, LZ, Ex);
+        line_digits(gv, kLB, mz, KZ, D, ps, LZ, Ex2);
+        for (int t = threadIdx.x; t < kLB; t += kT) Ex1[t] = 0;
         __syncthreads();
         // inverse z, owned slabs only
         for (int t = warp; t < 3 * nn; t += kW) {
             const int cc = t / nn, n0 = (nlo + t - cc * nn) * 8;
             double* dst = S + (long long)cc * mz * nxy + col0 - (long long)cc * kCT;
-            oz_tile(D, ps, LZ, Ex, cc == 2 ? TCi : TSi, F, cc * kCT, n0 / 8, KZ / 16, cc * kCT + ncol, oz0, oz1,
-                    [&](int l, int z, double x) { dst[(long long)z * nxy + l] = x; });
+            oz_tile<false>(D, ps, LZ, Ex2, cc == 2 ? TCi : TSi, F, cc * kCT, n0 / 8, KZ / 16, cc * kCT + ncol, oz0,
+                           oz1, [&](int l, int z, double x) { dst[(long long)z * nxy + l] = x; });
         }
-        __syncthreads();
+        // no barrier: the next tile writes V and Ex1, which this stage no
+        // longer reads
     }
 }
 
 // ---- pass C: inverse y and x of a group of owned z-slabs, owned scatter -----
 // Shared: D, Sm[ky][kx], Q[y][kx] (float64), Ex.
-constexpr size_t kSmemC = sizeof(uint16_t) * kDigS + sizeof(double) * 2 * kMaxM * kLine + sizeof(int) * kRows;
+constexpr size_t kSmemC = sizeof(uint16_t) * kDigS + sizeof(double) * 2 * kMaxM * kLine + sizeof(int) * 2 * kRows;
 
 __global__ void __launch_bounds__(kT, 3)
 k_oz_inv_xy(const double* __restrict__ scr, double* __restrict__ zout, const FmpBox* __restrict__ boxes,
@@ -394,7 +411,8 @@ k_oz_inv_xy(const double* __restrict__ scr, double* __restrict__ zout, const Fmp
     uint16_t* D = reinterpret_cast<uint16_t*>(smraw);
     double* Sm = reinterpret_cast<double*>(D + kDigS);   // [ky][kx], stride kLine
     double* Q = Sm + kMaxM * kLine;                     // [y - oy0][kx], stride kLine
-    int* Ex = reinterpret_cast<int*>(Q + kMaxM * kLine);
+    int* Ex1 = reinterpret_cast<int*>(Q + kMaxM * kLine);   // exponents of the ky lines (columns kx)
+    int* Ex2 = Ex1 + kRows;                                  // of the kx lines (owned rows y)
     const bool sx = c != 0, sy = c != 1;
     // inverse tables: Bt[i][k] = T[k][i]
     const uint4* TYi = otab + (B.oz_off[1] + (sy ? 3 : 1) * oz_tabf(my)) / 4;
@@ -405,29 +423,34 @@ k_oz_inv_xy(const double* __restrict__ scr, double* __restrict__ zout, const Fmp
     const int mt2 = rup(ony, 16) / 16, xlo = ox0 / 8, nn2 = rup(ox0 + onx, 8) / 8 - xlo;
     auto gs = [&](int l, int k) { return Sm[k * kLine + l]; };   // line kx, element ky
     auto gq = [&](int l, int k) { return Q[l * kLine + k]; };    // line y, element kx
+    for (int t = threadIdx.x; t < kRows; t += kT) Ex1[t] = 0;
+    __syncthreads();
     for (int zl = z0; zl < z0 + zn; ++zl) {
         const double* src = scr + B.scr_off + ((long long)c * mz + zl) * mx * my;
         for (int ky = warp; ky < my; ky += kW)
-            for (int kx = lane; kx < mx; kx += 32) Sm[ky * kLine + kx] = src[ky * mx + kx];
+            for (int kx = lane; kx < mx; kx += 32) {
+                const double v = src[ky * mx + kx];
+                Sm[ky * kLine + kx] = v;
+                atomicMax(Ex1 + kx, hexp(v));
+            }
         __syncthreads();
-        line_exponents(gs, mx, my, Ex);
-        __syncthreads();
-        line_digits(gs, mx, my, KY, D, ps1, LY, Ex);
+        line_digits(gs, mx, my, KY, D, ps1, LY, Ex1);
+        for (int t = threadIdx.x; t < kRows; t += kT) Ex2[t] = 0;
         __syncthreads();
         for (int t = warp; t < mt1 * nn1; t += kW)
-            oz_tile(D, ps1, LY, Ex, TYi, B.oz_F[1], (t / nn1) * 16, ylo + t % nn1, KY / 16, mx, oy0, oy0 + ony,
-                    [&](int kx, int y, double v) { Q[(y - oy0) * kLine + kx] = v; });
+            oz_tile<true>(D, ps1, LY, Ex1, TYi, B.oz_F[1], (t / nn1) * 16, ylo + t % nn1, KY / 16, mx, oy0, oy0 + ony,
+                          [&](int kx, int y, double v) { Q[(y - oy0) * kLine + kx] = v; }, Ex2, oy0);
         __syncthreads();
-        line_exponents(gq, ony, mx, Ex);
-        __syncthreads();
-        line_digits(gq, ony, mx, KX, D, ps2, LX, Ex);
+        line_digits(gq, ony, mx, KX, D, ps2, LX, Ex2);
+        for (int t = threadIdx.x; t < kRows; t += kT) Ex1[t] = 0;
         __syncthreads();
         const int gk = B.ext_lo[2] + zl;
         double* dst = zout + (((long long)c * nz + gk) * ny + B.ext_lo[1] + oy0) * (long long)nx + B.ext_lo[0];
         for (int t = warp; t < mt2 * nn2; t += kW)
-            oz_tile(D, ps2, LX, Ex, TXi, B.oz_F[0], (t / nn2) * 16, xlo + t % nn2, KX / 16, ony, ox0, ox0 + onx,
-                    [&](int yl, int x, double v) { dst[(long long)yl * nx + x] = v; });
-        __syncthreads();
+            oz_tile<false>(D, ps2, LX, Ex2, TXi, B.oz_F[0], (t / nn2) * 16, xlo + t % nn2, KX / 16, ony, ox0,
+                           ox0 + onx, [&](int yl, int x, double v) { dst[(long long)yl * nx + x] = v; });
+        // no barrier: the next slab writes Sm and Ex1, which this stage no
+        // longer reads
     }
 }
 
@@ -503,12 +526,12 @@ cudaError_t fmp_launch_transform_solve_ozaki(const FmpPlan& p, const uint32_t* o
                                              const double* gate) {
     if (p.max_m[0] > kMaxM || p.max_m[1] > kMaxM || p.max_m[2] > kMaxM) return cudaErrorNotSupported;
     const uint4* otab = reinterpret_cast<const uint4*>(otab32);
-    if (p.n_items_ga > 0)
-        k_oz_fwd_xy<<<p.n_items_ga, kT, kSmemA, s>>>(r, scratch, p.d_boxes, p.d_items_ga, otab, nx, ny, nz, gate);
-    if (p.n_items_gb > 0)
-        k_oz_z_solve<<<p.n_items_gb, kT, kSmemB, s>>>(scratch, p.d_boxes, p.d_items_gb, otab, tabs, modeinv, beta,
+    if (p.n_items_oa > 0)
+        k_oz_fwd_xy<<<p.n_items_oa, kT, kSmemA, s>>>(r, scratch, p.d_boxes, p.d_items_oa, otab, nx, ny, nz, gate);
+    if (p.n_items_ob > 0)
+        k_oz_z_solve<<<p.n_items_ob, kT, kSmemB, s>>>(scratch, p.d_boxes, p.d_items_ob, otab, tabs, modeinv, beta,
                                                       gate);
-    if (p.n_items_gc > 0)
-        k_oz_inv_xy<<<p.n_items_gc, kT, kSmemC, s>>>(scratch, z, p.d_boxes, p.d_items_gc, otab, nx, ny, nz, gate);
+    if (p.n_items_oc > 0)
+        k_oz_inv_xy<<<p.n_items_oc, kT, kSmemC, s>>>(scratch, z, p.d_boxes, p.d_items_oc, otab, nx, ny, nz, gate);
     return cudaGetLastError();
 }

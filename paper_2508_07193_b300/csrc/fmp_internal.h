@@ -15,6 +15,8 @@
 #define FMP_MP_TILE_GROUP 4   // column tiles per CTA in the reduced-precision pass B
 #define FMP_FUSED_MAX 40      // largest extent of a box solved by the fused cluster kernel
 #define FMP_OZAKI_MAX 40      // largest extent of the digit-split float64 kernels
+#define FMP_OZAKI_SLABS 2     // z-slabs per CTA in their passes A and C
+#define FMP_OZAKI_COLS 16     // columns per CTA (one tile) in their pass B
 
 // Device-side descriptor of one subdomain box (Sec. II-B). Coordinates are
 // in cells, ordered (x, y, z).
@@ -132,6 +134,15 @@ struct FmpPlan {
     // The grouped lists hold the boxes left to the three-pass kernels first
     // (n_g*_rest items), then the boxes of the fused list.
     int n_ga_rest = 0, n_gb_rest = 0, n_gc_rest = 0;
+    // work lists of the digit-split float64 kernels: (box, comp, first slab,
+    // slabs) for passes A and C (FMP_OZAKI_SLABS slabs), (box, first column,
+    // columns, 0) for pass B (one FMP_OZAKI_COLS-column tile)
+    int4* d_items_oa = nullptr;
+    int n_items_oa = 0;
+    int4* d_items_ob = nullptr;
+    int n_items_ob = 0;
+    int4* d_items_oc = nullptr;
+    int n_items_oc = 0;
     int* d_items_f = nullptr;   // boxes solved by one fused cluster each (bf16 / fp16)
     int n_items_f = 0;
     int fused_yz_max = 0;       // largest y or z extent among them
