@@ -137,7 +137,7 @@ __device__ __forceinline__ double combine(const float (&acc)[kD][4], int i, int 
     const bool neg = Z < 0;
     unsigned long long a = neg ? (unsigned long long)(-Z) : (unsigned long long)Z;
     const int lz = __clzll((long long)a);
-    const unsigned long long mant = (a << lz) >> 11;   // 53 bits, truncated (below 1 ulp)
+    const unsigned long long mant = (a << (lz & 63)) >> 11;   // 53 bits, truncated (below 1 ulp)
     const int field = emax + F - lz + 10;
     const unsigned sgn = neg ? 0x80000000u : 0u;
     unsigned hi = sgn | ((unsigned)field << 20) | ((unsigned)(mant >> 32) & 0xfffffu), lo = (unsigned)mant;
@@ -200,17 +200,22 @@ __device__ __forceinline__ void oz_tile(const uint16_t* D, int dps, int LKd, con
         }
     }
     const int r = lane >> 2, cc = 2 * (lane & 3);
+    // the four outputs are combined without branches (independent chains
+    // that interleave), then stored where valid
+    const int e0 = Ex[m0 + r], e1 = Ex[m0 + r + 8];
+    double v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = combine(acc, i, i < 2 ? e0 : e1, F);
     int ea = 0, eb = 0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int line = m0 + r + (i >> 1) * 8, n = nt * 8 + cc + (i & 1);
-        if (line < lhi && n >= nlo && n < nhi) {
-            const double v = combine(acc, i, Ex[line], F);
-            epi(line, n, v);
-            if (kExp) {
-                if (i & 1) eb = max(eb, hexp(v));
-                else ea = max(ea, hexp(v));
-            }
+        const bool ok = line < lhi && n >= nlo && n < nhi;
+        if (ok) epi(line, n, v[i]);
+        if (kExp) {
+            const int e = ok ? hexp(v[i]) : 0;
+            if (i & 1) eb = max(eb, e);
+            else ea = max(ea, e);
         }
     }
     if (kExp) {
@@ -260,6 +265,7 @@ k_oz_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox
         const bool zwall = (c != 2) && kz == 0;
         // lines y, contraction x: the slab row by row (the box's wall slots
         // read as zero) with each row's exponent
+#pragma unroll 2
         for (int y = warp; y < my; y += kW) {
             const bool rowok = !zwall && !(c == 0 && y == 0) && !(c == 2 && y == 0);
             const double* srow = src + (long long)y * nx;
@@ -336,11 +342,13 @@ k_oz_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const i
         const int ncol = min(kCT, gcol0 + gcols - col0);
         // V[c * kCT + col][z] with each line's exponent; lines past ncol keep
         // stale values and exponent 0 (zero digits, outputs never stored)
-        for (int cz = warp; cz < 3 * mz; cz += kW) {
-            const int cc = cz / mz, z = cz - cc * mz;
-            const double* srow = S + (long long)cz * nxy + col0;
-            for (int col = lane; col < ncol; col += 32) {
-                const double v = srow[col];
+        static_assert(kCT == 16, "two rows per warp below");
+#pragma unroll 4
+        for (int e = threadIdx.x; e < 3 * mz * kCT; e += kT) {
+            const int cz = e >> 4, col = e & 15;
+            if (col < ncol) {
+                const int cc = cz / mz, z = cz - cc * mz;
+                const double v = S[(long long)cz * nxy + col0 + col];
                 V[(cc * kCT + col) * kLine + z] = v;
                 atomicMax(Ex1 + cc * kCT + col, hexp(v));
             }
@@ -427,6 +435,7 @@ k_oz_inv_xy(const double* __restrict__ scr, double* __restrict__ zout, const Fmp
     __syncthreads();
     for (int zl = z0; zl < z0 + zn; ++zl) {
         const double* src = scr + B.scr_off + ((long long)c * mz + zl) * mx * my;
+#pragma unroll 2
         for (int ky = warp; ky < my; ky += kW)
             for (int kx = lane; kx < mx; kx += 32) {
                 const double v = src[ky * mx + kx];
