@@ -135,3 +135,31 @@ def test_fgmres_converges_like_float64():
     assert inf_o["true_rel_res"] <= 1e-10
     assert inf_o["iters"] == inf_n["iters"]
     assert rel(host(xo), host(xn)) <= 1e-9
+
+
+def test_bicgstab_and_graph_replay():
+    """BiCGSTAB reaches rtol with the split transforms; the graph-replayed
+    FGMRES cycle equals the host loop bit for bit."""
+    w = wl.small()
+    x, inf = context(w, rtol=1e-10, precision="fp64_ozaki", krylov="bicgstab").krylov_solve(dev(w.rhs))
+    assert inf["true_rel_res"] <= 1e-10
+    a, ia = context(w, rtol=1e-10, precision="fp64_ozaki", use_graph=False).krylov_solve(dev(w.rhs))
+    g, ig = context(w, rtol=1e-10, precision="fp64_ozaki", use_graph=True).krylov_solve(dev(w.rhs))
+    assert ia["iters"] == ig["iters"] and np.array_equal(host(a), host(g))
+
+
+def test_cn_steps_match_float64_kernels():
+    """Three CN steps with the split transforms stay within the solve
+    tolerance of the same steps with the float64 kernels."""
+    w = wl.small(grid=(24, 24, 24), cuts=((8, 8, 8),) * 3, overlap=2, seed=22, n_eps_boxes=6)
+    dt = 2.0 * np.sqrt(w.beta)
+    out = []
+    for prec in ("fp64", "fp64_ozaki"):
+        ctx = context(w, rtol=1e-11, precision=prec)
+        E, H = ctx.empty_field(), ctx.empty_field()
+        J = dev(-w.rhs / dt)
+        for _ in range(3):
+            info = ctx.cn_step(E, H, J, dt)
+            assert info["true_rel_res"] <= 1e-11
+        out.append((host(E), host(H)))
+    assert rel(out[1][0], out[0][0]) <= 1e-9 and rel(out[1][1], out[0][1]) <= 1e-9
