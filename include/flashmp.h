@@ -179,6 +179,15 @@ int fmp_set_fused(fmp_ctx* ctx, int max_extent);
  * HOST outputs. */
 int fmp_get_fused(fmp_ctx* ctx, int* max_extent, int* n_fused);
 
+/* Checked mode (layout contract): when on, every call that takes a field
+ * verifies that its wall slots are zero -- PEC edges for E-shaped fields
+ * (Ex at j = 0 or k = 0, Ey at i = 0 or k = 0, Ez at i = 0 or j = 0; for
+ * fmp_box_solve on the box's own grid) and Hx at i = 0, Hy at j = 0, Hz at
+ * k = 0 for H -- and returns FMP_ERR_ARG, computing nothing, if one is not.
+ * Each check is one pass over the field and synchronises the stream.
+ * on: 0 or 1. Default off; on in a library compiled with -DFMP_CHECKED. */
+int fmp_set_checked(fmp_ctx* ctx, int on);
+
 /* Subdomain form of the preconditioner's box solves.
  * FMP_FORM_YEE_BOX (default): each extended box is a Yee box with PEC walls;
  *   its tangential low-face slots are box walls and the DCT-II/DST-I

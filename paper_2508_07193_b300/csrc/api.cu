@@ -209,6 +209,26 @@ bool ozaki_ok(const FmpPlan& p) {
     return p.max_m[0] <= FMP_OZAKI_MAX && p.max_m[1] <= FMP_OZAKI_MAX && p.max_m[2] <= FMP_OZAKI_MAX;
 }
 
+// Checked mode: FMP_ERR_ARG when a field has a nonzero wall slot (synchronises).
+int check_walls(fmp_ctx* c, const double* x, int face, int nx, int ny, int nz) {
+    if (!c->checked || !x) return FMP_OK;
+    if (!c->d_check) FMP_CK(cudaMalloc(&c->d_check, sizeof(unsigned int)));
+    FMP_CK(cudaMemsetAsync(c->d_check, 0, sizeof(unsigned int), c->stream));
+    ++c->launches;
+    FMP_CK(fmp_launch_wall_count(x, face, nx, ny, nz, c->d_check, c->stream));
+    unsigned int n = 0;
+    FMP_CK(cudaMemcpyAsync(&n, c->d_check, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->stream));
+    FMP_CK(cudaStreamSynchronize(c->stream));
+    return n == 0 ? FMP_OK : FMP_ERR_ARG;
+}
+int check_edge(fmp_ctx* c, const double* x) { return check_walls(c, x, 0, c->nx, c->ny, c->nz); }
+int check_face(fmp_ctx* c, const double* x) { return check_walls(c, x, 1, c->nx, c->ny, c->nz); }
+
+int krylov_dispatch(fmp_ctx* c, const double* b, double* x, fmp_solve_info* info) {
+    if (c->opt.krylov == FMP_KRYLOV_BICGSTAB) return fmp_bicgstab(c, b, x, info);
+    return fmp_fgmres(c, b, x, info);
+}
+
 bool dt_matches(double beta, double dt) {
     const double b2 = dt * dt / 4.0;
     return std::fabs(b2 - beta) <= 1e-12 * std::fabs(beta);
@@ -513,6 +533,7 @@ void fmp_destroy(fmp_ctx* c) {
     cudaFree(c->d_partials); cudaFree(c->d_state); cudaFree(c->d_ticket);
     for (int t = 0; t < 3; ++t) cudaFree(c->d_tab_mp[t]);
     cudaFree(c->d_tab_oz);
+    cudaFree(c->d_check);
     cudaFree(c->d_bscale);
     cudaFree(c->d_eps_cell);
     cudaFree(c->d_tmp3); cudaFree(c->d_tmp4); cudaFree(c->d_tmp5);
@@ -583,6 +604,12 @@ int fmp_set_subdomain_form(fmp_ctx* c, int form) {
     }
     if (form != c->subdomain_form) c->graph_valid = false;
     c->subdomain_form = form;
+    return FMP_OK;
+}
+
+int fmp_set_checked(fmp_ctx* c, int on) {
+    if (!valid_ctx(c) || (on != 0 && on != 1)) return FMP_ERR_ARG;
+    c->checked = on;
     return FMP_OK;
 }
 
@@ -678,6 +705,7 @@ int fmp_get_box(fmp_ctx* c, int i, int* ext_lo, int* m, int* own_lo, int* own_n,
 int fmp_curlcurl_apply(fmp_ctx* c, const double* x, double* y, double c_eps, double c_k) {
     if (!valid_ctx(c) || !x || !y || x == y) return FMP_ERR_ARG;
     if (int rc = latched(c)) return rc;
+    if (int rc = check_edge(c, x)) return rc;
     ++c->launches;
     FMP_CK(fmp_launch_curlcurl(x, c->d_eps_edge, y, c_eps, c_k, c->nx, c->ny, c->nz, c->stream, nullptr));
     return FMP_OK;
@@ -686,6 +714,7 @@ int fmp_curlcurl_apply(fmp_ctx* c, const double* x, double* y, double c_eps, dou
 int fmp_precond_apply(fmp_ctx* c, const double* r, double* z) {
     if (!valid_ctx(c) || !r || !z || r == z) return FMP_ERR_ARG;
     if (int rc = latched(c)) return rc;
+    if (int rc = check_edge(c, r)) return rc;
     return fmp_precond(c, r, z);
 }
 
@@ -696,6 +725,7 @@ int fmp_box_solve(fmp_ctx* c, int i, const double* r, double* x) {
     if (c->opt.precision != FMP_PREC_FP64 && !oz) return FMP_ERR_UNSUPPORTED;
     // a one-box plan on the box-local array: the box is its own grid, owned = all
     FmpBox b = c->h_boxes[i];
+    if (int rc = check_walls(c, r, 0, b.m[0], b.m[1], b.m[2])) return rc;
     b.ext_lo[0] = b.ext_lo[1] = b.ext_lo[2] = 0;
     for (int a = 0; a < 3; ++a) { b.own_lo[a] = 0; b.own_n[a] = b.m[a]; }
     b.scr_off = 0;
@@ -721,13 +751,17 @@ int fmp_box_solve(fmp_ctx* c, int i, const double* r, double* x) {
 int fmp_krylov_solve(fmp_ctx* c, const double* b, double* x, fmp_solve_info* info) {
     if (!valid_ctx(c) || !b || !x || b == x) return FMP_ERR_ARG;
     if (int rc = latched(c)) return rc;
-    if (c->opt.krylov == FMP_KRYLOV_BICGSTAB) return fmp_bicgstab(c, b, x, info);
-    return fmp_fgmres(c, b, x, info);
+    if (int rc = check_edge(c, b)) return rc;
+    if (int rc = check_edge(c, x)) return rc;
+    return krylov_dispatch(c, b, x, info);
 }
 
 int fmp_cn_rhs(fmp_ctx* c, const double* E, const double* H, const double* J, double dt, double* R) {
     if (!valid_ctx(c) || !E || !H || !R || R == E || R == H || !dt_matches(c->beta, dt)) return FMP_ERR_ARG;
     if (int rc = latched(c)) return rc;
+    if (int rc = check_edge(c, E)) return rc;
+    if (int rc = check_face(c, H)) return rc;
+    if (int rc = check_edge(c, J)) return rc;
     ++c->launches;
     FMP_CK(fmp_launch_cn_rhs(E, H, J, c->d_eps_edge, c->beta, dt, R, c->nx, c->ny, c->nz, c->stream));
     return FMP_OK;
@@ -736,6 +770,9 @@ int fmp_cn_rhs(fmp_ctx* c, const double* E, const double* H, const double* J, do
 int fmp_h_update(fmp_ctx* c, double* H, const double* En, const double* Eo, double dt) {
     if (!valid_ctx(c) || !H || !En || !Eo || !std::isfinite(dt)) return FMP_ERR_ARG;
     if (int rc = latched(c)) return rc;
+    if (int rc = check_face(c, H)) return rc;
+    if (int rc = check_edge(c, En)) return rc;
+    if (int rc = check_edge(c, Eo)) return rc;
     ++c->launches;
     FMP_CK(fmp_launch_h_update(H, En, Eo, dt, c->nx, c->ny, c->nz, c->stream));
     return FMP_OK;
@@ -744,6 +781,9 @@ int fmp_h_update(fmp_ctx* c, double* H, const double* En, const double* Eo, doub
 int fmp_cn_step(fmp_ctx* c, double* E, double* H, const double* J, double dt, fmp_solve_info* info) {
     if (!valid_ctx(c) || !E || !H || E == H || !dt_matches(c->beta, dt)) return FMP_ERR_ARG;
     if (int rc = latched(c)) return rc;
+    if (int rc = check_edge(c, E)) return rc;
+    if (int rc = check_face(c, H)) return rc;
+    if (int rc = check_edge(c, J)) return rc;
     double* R = c->d_tmp;
     double* Eold = c->d_tmp2;
     c->launches += 2;   // rhs + H update
@@ -771,7 +811,7 @@ int fmp_cn_step(fmp_ctx* c, double* E, double* H, const double* J, double dt, fm
             fallback = 1;
         }
     }
-    int rc = fmp_krylov_solve(c, R, E, info);
+    int rc = krylov_dispatch(c, R, E, info);   // R and E were produced or checked above
     if (info) info->used_fallback = fallback;
     if (rc != FMP_OK && rc != FMP_ERR_NOT_CONVERGED) return rc;
     FMP_CK(fmp_launch_h_update(H, E, Eold, dt, c->nx, c->ny, c->nz, c->stream));

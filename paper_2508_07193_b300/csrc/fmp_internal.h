@@ -182,6 +182,12 @@ struct fmp_ctx {
     FmpCnn* cnn = nullptr;        // learned initial guess / correction (created on first use)
     FmpCompact* compact = nullptr;   // compact-layout boxes with the Woodbury correction
     int subdomain_form = 0;       // FMP_FORM_YEE_BOX or FMP_FORM_COMPACT
+#ifdef FMP_CHECKED
+    int checked = 1;              // verify the wall-slot layout of input fields
+#else
+    int checked = 0;
+#endif
+    unsigned int* d_check = nullptr;  // wall-slot counter of the checked mode
     double* d_tmp3 = nullptr;     // field-sized scratch of the learned paths
     double* d_tmp4 = nullptr;
     double* d_tmp5 = nullptr;
@@ -226,6 +232,9 @@ cudaError_t fmp_launch_curlcurl(const double* x, const double* eps, double* y, d
 cudaError_t fmp_launch_cn_rhs(const double* E, const double* H, const double* J,
                               const double* eps, double beta, double dt, double* R, int nx,
                               int ny, int nz, cudaStream_t s);
+// count += the number of nonzero wall slots of x (face = 0: edge field, 1: face field)
+cudaError_t fmp_launch_wall_count(const double* x, int face, int nx, int ny, int nz, unsigned int* count,
+                                  cudaStream_t s);
 cudaError_t fmp_launch_h_update(double* H, const double* En, const double* Eo, double dt,
                                 int nx, int ny, int nz, cudaStream_t s);
 

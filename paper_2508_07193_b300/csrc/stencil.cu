@@ -14,6 +14,8 @@
 // The kernels are memory bound: one thread per cell computes the three
 // components, x-fastest so warps read 256-byte rows; neighbour reads hit L1/L2.
 #include "fmp_internal.h"
+
+#include <algorithm>
 #include "cp_async.cuh"
 
 namespace {
@@ -282,6 +284,30 @@ k_h_update(double* __restrict__ H, const double* __restrict__ En, const double* 
     H[2 * d.comp + o] -= h * cz;
 }
 
+// Layout check: the number of nonzero wall slots of a field. Edge fields
+// (E and everything shaped like it): Ex at j = 0 or k = 0, Ey at i = 0 or
+// k = 0, Ez at i = 0 or j = 0 (PEC). Face fields (H): Hx at i = 0, Hy at
+// j = 0, Hz at k = 0.
+__global__ void __launch_bounds__(256)
+k_wall_count(const double* __restrict__ x, Dims d, int face, unsigned int* __restrict__ count) {
+    __shared__ unsigned int blk;
+    if (threadIdx.x == 0) blk = 0u;
+    __syncthreads();
+    unsigned int n = 0u;
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < d.comp;
+         o += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(o / d.plane), r = (int)(o - (long long)k * d.plane);
+        const int j = r / d.nx, i = r - j * d.nx;
+        const bool w0 = face ? i == 0 : (j == 0 || k == 0);
+        const bool w1 = face ? j == 0 : (i == 0 || k == 0);
+        const bool w2 = face ? k == 0 : (i == 0 || j == 0);
+        n += (w0 && x[o] != 0.0) + (w1 && x[d.comp + o] != 0.0) + (w2 && x[2 * d.comp + o] != 0.0);
+    }
+    if (n) atomicAdd(&blk, n);
+    __syncthreads();
+    if (threadIdx.x == 0 && blk) atomicAdd(count, blk);
+}
+
 Dims dims(int nx, int ny, int nz) {
     return Dims{nx, ny, nz, (long long)nx * ny, (long long)nx * ny * nz};
 }
@@ -318,6 +344,14 @@ cudaError_t fmp_launch_cn_rhs(const double* E, const double* H, const double* J,
                               double beta, double dt, double* R, int nx, int ny, int nz, cudaStream_t s) {
     dim3 b(64, 4, 1);
     k_cn_rhs<<<grid_of(nx, ny, nz, b), b, 0, s>>>(E, H, J, eps, beta, dt, R, dims(nx, ny, nz));
+    return cudaGetLastError();
+}
+
+cudaError_t fmp_launch_wall_count(const double* x, int face, int nx, int ny, int nz, unsigned int* count,
+                                  cudaStream_t s) {
+    const Dims d = dims(nx, ny, nz);
+    const int blocks = (int)std::min<long long>((d.comp + 255) / 256, 148LL * 8);
+    k_wall_count<<<blocks, 256, 0, s>>>(x, d, face, count);
     return cudaGetLastError();
 }
 

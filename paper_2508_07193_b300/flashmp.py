@@ -86,6 +86,7 @@ def lib():
         "fmp_get_tuning": (_I, [_P, C.POINTER(_I), C.POINTER(_I)]),
         "fmp_autotune": (_I, [_P, _I, _I, C.POINTER(_I)]),
         "fmp_set_fused": (_I, [_P, _I]),
+        "fmp_set_checked": (_I, [_P, _I]),
         "fmp_set_subdomain_form": (_I, [_P, _I]),
         "fmp_get_subdomain_form": (_I, [_P, C.POINTER(_I), C.POINTER(C.c_longlong)]),
         "fmp_get_fused": (_I, [_P, C.POINTER(_I), C.POINTER(_I)]),
@@ -258,6 +259,11 @@ class Context:
         f, nb = C.c_int(), C.c_longlong()
         _check(lib().fmp_get_subdomain_form(self._h, C.byref(f), C.byref(nb)), "fmp_get_subdomain_form")
         return ("yee", "compact")[f.value], nb.value
+
+    def set_checked(self, on=True):
+        """Checked mode: calls raise FlashMPError(FMP_ERR_ARG) on a field with a
+        nonzero wall slot (fmp_set_checked)."""
+        _check(lib().fmp_set_checked(self._h, int(bool(on))), "fmp_set_checked")
 
     def set_fused(self, max_extent):
         _check(lib().fmp_set_fused(self._h, int(max_extent)), "fmp_set_fused")
