@@ -4,6 +4,8 @@
 // include/flashmp.h.
 #include "fmp_internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cstdint>
@@ -209,6 +211,13 @@ bool ozaki_ok(const FmpPlan& p) {
     return p.max_m[0] <= FMP_OZAKI_MAX && p.max_m[1] <= FMP_OZAKI_MAX && p.max_m[2] <= FMP_OZAKI_MAX;
 }
 
+// NVTX range over one ABI call, named after the paper's phases (no cost
+// unless a profiler is attached).
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
+
 // Checked mode: FMP_ERR_ARG when a field has a nonzero wall slot (synchronises).
 int check_walls(fmp_ctx* c, const double* x, int face, int nx, int ny, int nz) {
     if (!c->checked || !x) return FMP_OK;
@@ -237,6 +246,10 @@ bool dt_matches(double beta, double dt) {
 }  // namespace
 
 int fmp_precond_gated(fmp_ctx* c, const double* r, double* z, const double* gate) {
+    // checked mode: poison the transform scratch with NaN so that a pass
+    // reading a slot its predecessor did not write shows in the output
+    if (c->checked && c->d_scratch)
+        FMP_CK(cudaMemsetAsync(c->d_scratch, 0xFF, sizeof(double) * (size_t)c->ras.scratch_doubles, c->stream));
     if (c->subdomain_form == FMP_FORM_COMPACT) {
         if (c->opt.precision != FMP_PREC_FP64 || !c->compact) return FMP_ERR_UNSUPPORTED;
         int nk = 0;
@@ -706,6 +719,7 @@ int fmp_curlcurl_apply(fmp_ctx* c, const double* x, double* y, double c_eps, dou
     if (!valid_ctx(c) || !x || !y || x == y) return FMP_ERR_ARG;
     if (int rc = latched(c)) return rc;
     if (int rc = check_edge(c, x)) return rc;
+    Range rg("matvec");
     ++c->launches;
     FMP_CK(fmp_launch_curlcurl(x, c->d_eps_edge, y, c_eps, c_k, c->nx, c->ny, c->nz, c->stream, nullptr));
     return FMP_OK;
@@ -715,6 +729,7 @@ int fmp_precond_apply(fmp_ctx* c, const double* r, double* z) {
     if (!valid_ctx(c) || !r || !z || r == z) return FMP_ERR_ARG;
     if (int rc = latched(c)) return rc;
     if (int rc = check_edge(c, r)) return rc;
+    Range rg("precond");
     return fmp_precond(c, r, z);
 }
 
@@ -753,6 +768,7 @@ int fmp_krylov_solve(fmp_ctx* c, const double* b, double* x, fmp_solve_info* inf
     if (int rc = latched(c)) return rc;
     if (int rc = check_edge(c, b)) return rc;
     if (int rc = check_edge(c, x)) return rc;
+    Range rg("krylov_solve");
     return krylov_dispatch(c, b, x, info);
 }
 
@@ -784,6 +800,7 @@ int fmp_cn_step(fmp_ctx* c, double* E, double* H, const double* J, double dt, fm
     if (int rc = check_edge(c, E)) return rc;
     if (int rc = check_face(c, H)) return rc;
     if (int rc = check_edge(c, J)) return rc;
+    Range rg("cn_step");
     double* R = c->d_tmp;
     double* Eold = c->d_tmp2;
     c->launches += 2;   // rhs + H update

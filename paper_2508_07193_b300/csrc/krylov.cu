@@ -22,6 +22,8 @@
 // enqueued (or replayed as one CUDA graph) and read back once.
 #include "fmp_internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <array>
 #include <cmath>
 #include <utility>
@@ -534,10 +536,12 @@ struct Timer {
     fmp_ctx* c;
     bool on;
     float* acc;
-    Timer(fmp_ctx* c_, float* a) : c(c_), on(c_->opt.timing != 0), acc(a) {
+    Timer(fmp_ctx* c_, float* a, const char* phase) : c(c_), on(c_->opt.timing != 0), acc(a) {
+        nvtxRangePushA(phase);   // the phase as an NVTX range (host-side marker only)
         if (on) cudaEventRecord(c->ev[0], c->stream);
     }
     ~Timer() {
+        nvtxRangePop();
         if (!on) return;
         cudaEventRecord(c->ev[1], c->stream);
         cudaEventSynchronize(c->ev[1]);
@@ -591,7 +595,7 @@ int arnoldi_step(fmp_ctx* c, int j, fmp_solve_info* inf) {
     double* w = V + (size_t)(j + 1) * ld;
     cudaStream_t s = c->stream;
     {
-        Timer tm(c, &inf->ms_precond);
+        Timer tm(c, &inf->ms_precond, "precond");
         int rc = fmp_precond_gated(c, vj, zj, gate);
         if (rc != FMP_OK) return rc;
         if (c->opt.use_learned >= 2 && c->cnn && c->d_tmp3) {
@@ -615,12 +619,12 @@ int arnoldi_step(fmp_ctx* c, int j, fmp_solve_info* inf) {
         }
     }
     {
-        Timer tm(c, &inf->ms_spmv);
+        Timer tm(c, &inf->ms_spmv, "matvec");
         ++c->launches;
         FMP_CK(fmp_launch_curlcurl(zj, c->d_eps_edge, w, 1.0, c->beta, c->nx, c->ny, c->nz, s, gate));
     }
     {
-        Timer tm(c, &inf->ms_orth);
+        Timer tm(c, &inf->ms_orth, "orth");
         const int nv = j + 1;
         ++c->launches;
         FMP_CK(launch_dots(V, ld, nv, w, n, st, R, L.h1, 0, c, s));
@@ -833,12 +837,12 @@ int fmp_bicgstab(fmp_ctx* c, const double* b, double* x, fmp_solve_info* info) {
             k_bicg_p<<<grid_n(n), kT, 0, s>>>(p, r, v, n, sc, first ? 1 : 0);
             first = false;
             {
-                Timer tm(c, &inf.ms_precond);
+                Timer tm(c, &inf.ms_precond, "precond");
                 int rc = fmp_precond_gated(c, p, ph, nullptr);
                 if (rc != FMP_OK) return rc;
             }
             {
-                Timer tm(c, &inf.ms_spmv);
+                Timer tm(c, &inf.ms_spmv, "matvec");
                 ++c->launches;
                 FMP_CK(fmp_launch_curlcurl(ph, c->d_eps_edge, v, 1.0, c->beta, c->nx, c->ny, c->nz, s, nullptr));
             }
@@ -848,12 +852,12 @@ int fmp_bicgstab(fmp_ctx* c, const double* b, double* x, fmp_solve_info* info) {
             ++c->launches;
             k_bicg_s<<<grid_n(n), kT, 0, s>>>(sv, r, v, n, sc);
             {
-                Timer tm(c, &inf.ms_precond);
+                Timer tm(c, &inf.ms_precond, "precond");
                 int rc = fmp_precond_gated(c, sv, sh, nullptr);
                 if (rc != FMP_OK) return rc;
             }
             {
-                Timer tm(c, &inf.ms_spmv);
+                Timer tm(c, &inf.ms_spmv, "matvec");
                 ++c->launches;
                 FMP_CK(fmp_launch_curlcurl(sh, c->d_eps_edge, t, 1.0, c->beta, c->nx, c->ny, c->nz, s, nullptr));
             }

@@ -81,3 +81,21 @@ def test_box_solve_checks_the_box_grid():
     r = w.rhs.copy()
     r[1, 0, 5, 5] = 1.0            # Ey at k = 0
     assert _err(lambda: ctx.box_solve(0, dev(r))) == F.FMP_ERR_ARG
+
+
+@pytest.mark.parametrize("prec, tol", [("fp64", 1e-11), ("fp64_ozaki", 1e-11), ("bf16", 3e-2), ("tf32", 5e-3)])
+def test_nan_canary_in_the_transform_scratch(prec, tol):
+    """Checked mode fills the transform scratch with NaN before every apply:
+    a pass that read a slot its predecessor did not write would turn the
+    output NaN. Ragged boxes, odd extents and a box with one-cell overlap."""
+    from oracle import ras, yee
+    w = wl.small(grid=(33, 17, 9), cuts=((11, 11, 11), (17,), (4, 5)), overlap=1, seed=21, n_eps_boxes=5)
+    ctx = context(w, precision=prec)
+    if prec == "bf16":
+        ctx.set_fused(0)   # the three-pass kernels are the ones that use the scratch
+    ctx.set_checked(True)
+    z = host(ctx.precond_apply(dev(w.rhs)))
+    assert np.all(np.isfinite(z))
+    ee = yee.edge_eps(w.grid, w.eps_cell)
+    ref = ras.precond_apply(w.rhs, ras.partition(w.grid, w.cuts, w.overlap), ee, w.beta)
+    assert np.linalg.norm(z - ref) / np.linalg.norm(ref) <= tol
