@@ -68,6 +68,7 @@ __device__ __forceinline__ int hexp(double v) { return (__double2hiint(v) >> 20)
 // the bias C = 128 (256^6 - 1) / 255, the digits d_p + 128 of X + C are its
 // plain bytes, so all six come out independently (no carry chain).
 constexpr long long kBias = 128LL * ((1LL << 48) - 1) / 255;
+__device__ __forceinline__ void bias_digits(long long X, uint32_t (&f)[kD]);
 __device__ __forceinline__ void to_digits(double v, int emax, uint32_t (&f)[kD]) {
     const int hi = __double2hiint(v);
     const unsigned lo = (unsigned)__double2loint(v);
@@ -79,6 +80,11 @@ __device__ __forceinline__ void to_digits(double v, int emax, uint32_t (&f)[kD])
         X = (long long)(M >> sh);
         if (hi < 0) X = -X;
     }
+    bias_digits(X, f);
+}
+
+// The digits of an integer |X| <= 2^47 (as in to_digits).
+__device__ __forceinline__ void bias_digits(long long X, uint32_t (&f)[kD]) {
     const unsigned long long Y = (unsigned long long)(X + kBias);
     const unsigned yl = (unsigned)Y, yh = (unsigned)(Y >> 32);
     // fp32 of (byte - 128) through the magic number 1.5 * 2^23 (exact)
@@ -90,24 +96,30 @@ __device__ __forceinline__ void to_digits(double v, int emax, uint32_t (&f)[kD])
     f[0] = __float_as_uint(__uint_as_float(0x4B3FFF80u + (yh >> 8)) - 12582912.0f);
 }
 
+// Digits of a class sum Z handed over from the previous axis transform:
+// X = Z 2^-s (s may be negative), |X| <= 2^47 for s = E + 7 - (source line
+// exponent + table exponent) with E the line's exponent field.
+__device__ __forceinline__ void z_digits(long long Z, int s, uint32_t (&f)[kD]) {
+    const long long X = s >= 0 ? (Z >> (s < 63 ? s : 63)) : (long long)((unsigned long long)Z << (-s < 63 ? -s : 63));
+    bias_digits(X, f);
+}
+
 // Digit planes of lines l < nlines at rows l of D ([kD][.][LK], plane stride
 // ps): one thread per element pair (2j, 2j + 1), bf16 pairs stored as one
 // word; pairs from (K + 1) / 2 to Kp / 2 get zero digits. get(l, k) is called
 // for k < K only.
-template <class Get>
-__device__ __forceinline__ void line_digits(Get get, int nlines, int K, int Kp, uint16_t* D, int ps, int LK,
-                                            const int* Ex) {
+// Cut(l, k, f) writes the digits of element k of line l (k < K) into f.
+template <class Cut>
+__device__ __forceinline__ void line_digits_by(Cut cut, int nlines, int K, int Kp, uint16_t* D, int ps, int LK) {
     const int P = (K + 1) >> 1, lpp = kT / P;
     const int lt = threadIdx.x / P, j = threadIdx.x - lt * P;
     if (lt < lpp) {
         const int k = 2 * j;
         for (int l = lt; l < nlines; l += lpp) {
-            const double a = get(l, k);
-            const double b = k + 1 < K ? get(l, k + 1) : 0.0;
-            const int em = Ex[l];
             uint32_t fa[kD], fb[kD];
-            to_digits(a, em, fa);
-            to_digits(b, em, fb);
+            cut(l, k, fa);
+            if (k + 1 < K) cut(l, k + 1, fb);
+            else bias_digits(0, fb);
             uint32_t* row = reinterpret_cast<uint32_t*>(D + l * LK) + j;
 #pragma unroll
             for (int p = 0; p < kD; ++p) row[p * (ps >> 1)] = __byte_perm(fa[p], fb[p], 0x7632);
@@ -121,19 +133,40 @@ __device__ __forceinline__ void line_digits(Get get, int nlines, int K, int Kp, 
                 for (int p = 0; p < kD; ++p) reinterpret_cast<uint32_t*>(D + p * ps + l * LK)[jj] = 0u;
 }
 
+// Lines of float64 values get(l, k), cut relative to Ex[l].
+template <class Get>
+__device__ __forceinline__ void line_digits(Get get, int nlines, int K, int Kp, uint16_t* D, int ps, int LK,
+                                            const int* Ex) {
+    line_digits_by([&](int l, int k, uint32_t (&f)[kD]) { to_digits(get(l, k), Ex[l], f); }, nlines, K, Kp, D, ps,
+                   LK);
+}
+
 // Z 2^(emax + F - 1076) truncated to float64, Z = sum_g acc_g 256^(5 - g) with
 // acc_g exact integers below 2^22 in magnitude (integer operations only).
-__device__ __forceinline__ double combine(const float (&acc)[kD][4], int i, int emax, int F) {
-    if (emax >= 2047) return __longlong_as_double(0x7ff8000000000000LL);   // Inf / NaN in the line
-    // i_g = bits(acc_g + 1.5 * 2^23) - bits(1.5 * 2^23); pairs i_g 256 + i_(g+1)
-    // fit 31 bits (wrapping unsigned arithmetic, exact result)
+// Z = sum_g acc_g 256^(5 - g): i_g = bits(acc_g + 1.5 * 2^23) - bits(1.5 * 2^23);
+// pairs i_g 256 + i_(g+1) fit 31 bits (wrapping unsigned arithmetic, exact).
+__device__ __forceinline__ long long class_sum(const float (&acc)[kD][4], int i) {
     unsigned u[kD];
 #pragma unroll
     for (int g = 0; g < kD; ++g) u[g] = __float_as_uint(acc[g][i] + 12582912.0f);
     const int A = (int)(u[0] * 256u + u[1] - 257u * 0x4B400000u);
     const int Bq = (int)(u[2] * 256u + u[3] - 257u * 0x4B400000u);
     const int Cq = (int)(u[4] * 256u + u[5] - 257u * 0x4B400000u);
-    const long long Z = (long long)((unsigned long long)(unsigned)A << 32) + (long long)Bq * 65536LL + (long long)Cq;
+    return (long long)((unsigned long long)(unsigned)A << 32) + (long long)Bq * 65536LL + (long long)Cq;
+}
+
+// The float64 exponent field of Z 2^(emax + F - 1076) (0 for Z = 0; 2047
+// when the line held Inf / NaN).
+__device__ __forceinline__ int z_field(long long Z, int emax, int F) {
+    if (emax >= 2047) return 2047;
+    if (Z == 0) return 0;
+    const unsigned long long a = Z < 0 ? (unsigned long long)(-Z) : (unsigned long long)Z;
+    return emax + F - __clzll((long long)a) + 10;
+}
+
+__device__ __forceinline__ double combine(const float (&acc)[kD][4], int i, int emax, int F) {
+    if (emax >= 2047) return __longlong_as_double(0x7ff8000000000000LL);   // Inf / NaN in the line
+    const long long Z = class_sum(acc, i);
     const bool neg = Z < 0;
     unsigned long long a = neg ? (unsigned long long)(-Z) : (unsigned long long)Z;
     const int lz = __clzll((long long)a);
@@ -170,10 +203,12 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
 // planes stream through one fragment at a time (the six table planes stay in
 // registers). epi(line, n, value) gets the outputs with line < lhi and
 // nlo <= n < nhi.
-// With kExp, the largest exponent field of each output column n (the next
-// stage's line) is also folded into exo[n - eoff] (atomicMax; exo zeroed
-// beforehand).
-template <bool kExp, class Epi>
+// With kZ, the tile hands the class sums Z (long long) to epi instead of
+// float64 values, for the next axis transform of the same kernel to cut
+// without a float64 round trip, and folds the largest exponent field of each
+// output column n (the next stage's line) into exo[n - eoff] (atomicMax; exo
+// zeroed beforehand).
+template <bool kZ, class Epi>
 __device__ __forceinline__ void oz_tile(const uint16_t* D, int dps, int LKd, const int* Ex,
                                         const uint4* __restrict__ Tf, int F, int m0, int nt, int ksteps, int lhi,
                                         int nlo, int nhi, Epi epi, int* exo = nullptr, int eoff = 0) {
@@ -200,25 +235,32 @@ __device__ __forceinline__ void oz_tile(const uint16_t* D, int dps, int LKd, con
         }
     }
     const int r = lane >> 2, cc = 2 * (lane & 3);
-    // the four outputs are combined without branches (independent chains
-    // that interleave), then stored where valid
+    // the four outputs are formed without branches (independent chains that
+    // interleave), then stored where valid
     const int e0 = Ex[m0 + r], e1 = Ex[m0 + r + 8];
-    double v[4];
+    if (!kZ) {
+        double v[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) v[i] = combine(acc, i, i < 2 ? e0 : e1, F);
-    int ea = 0, eb = 0;
+        for (int i = 0; i < 4; ++i) v[i] = combine(acc, i, i < 2 ? e0 : e1, F);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int line = m0 + r + (i >> 1) * 8, n = nt * 8 + cc + (i & 1);
-        const bool ok = line < lhi && n >= nlo && n < nhi;
-        if (ok) epi(line, n, v[i]);
-        if (kExp) {
-            const int e = ok ? hexp(v[i]) : 0;
+        for (int i = 0; i < 4; ++i) {
+            const int line = m0 + r + (i >> 1) * 8, n = nt * 8 + cc + (i & 1);
+            if (line < lhi && n >= nlo && n < nhi) epi(line, n, v[i]);
+        }
+    } else {
+        long long zv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) zv[i] = class_sum(acc, i);
+        int ea = 0, eb = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int line = m0 + r + (i >> 1) * 8, n = nt * 8 + cc + (i & 1);
+            const bool ok = line < lhi && n >= nlo && n < nhi;
+            if (ok) epi(line, n, zv[i]);
+            const int e = ok ? z_field(zv[i], i < 2 ? e0 : e1, F) : 0;
             if (i & 1) eb = max(eb, e);
             else ea = max(ea, e);
         }
-    }
-    if (kExp) {
 #pragma unroll
         for (int o = 4; o < 32; o <<= 1) {
             ea = max(ea, __shfl_xor_sync(0xffffffffu, ea, o));
@@ -282,12 +324,16 @@ k_oz_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox
         line_digits([&](int l, int k) { return Pt[l * kLine + k]; }, my, mx, KX, D, ps1, LX, Ex1);
         for (int t = threadIdx.x; t < kRows; t += kT) Ex2[t] = 0;
         __syncthreads();
+        long long* Zt = reinterpret_cast<long long*>(Pt);   // class sums Zt[kx][y]
         for (int t = warp; t < mt1 * nt1; t += kW)
             oz_tile<true>(D, ps1, LX, Ex1, TX, B.oz_F[0], (t / nt1) * 16, t % nt1, KX / 16, my, 0, mx,
-                          [&](int y, int kx, double v) { Pt[kx * kLine + y] = v; }, Ex2, 0);
+                          [&](int y, int kx, long long z) { Zt[kx * kLine + y] = z; }, Ex2, 0);
         __syncthreads();
-        // lines kx, contraction y
-        line_digits([&](int l, int k) { return Pt[l * kLine + k]; }, mx, my, KY, D, ps2, LY, Ex2);
+        // lines kx, contraction y: cut the class sums, element y of line kx
+        // weighs 2^(Ex1[y] + F_x - 1076)
+        line_digits_by([&](int l, int k, uint32_t (&f)[kD]) {
+            z_digits(Zt[l * kLine + k], Ex2[l] + 7 - Ex1[k] - B.oz_F[0], f);
+        }, mx, my, KY, D, ps2, LY);
         __syncthreads();
         double* out = scr + B.scr_off + ((long long)c * mz + kz) * mx * my;
         for (int t = warp; t < mt2 * nt2; t += kW)
@@ -430,7 +476,7 @@ k_oz_inv_xy(const double* __restrict__ scr, double* __restrict__ zout, const Fmp
     const int mt1 = oz_kp(mx) / 16, ylo = oy0 / 8, nn1 = rup(oy0 + ony, 8) / 8 - ylo;
     const int mt2 = rup(ony, 16) / 16, xlo = ox0 / 8, nn2 = rup(ox0 + onx, 8) / 8 - xlo;
     auto gs = [&](int l, int k) { return Sm[k * kLine + l]; };   // line kx, element ky
-    auto gq = [&](int l, int k) { return Q[l * kLine + k]; };    // line y, element kx
+    long long* Zq = reinterpret_cast<long long*>(Q);             // class sums Zq[y - oy0][kx]
     for (int t = threadIdx.x; t < kRows; t += kT) Ex1[t] = 0;
     __syncthreads();
     for (int zl = z0; zl < z0 + zn; ++zl) {
@@ -448,9 +494,12 @@ k_oz_inv_xy(const double* __restrict__ scr, double* __restrict__ zout, const Fmp
         __syncthreads();
         for (int t = warp; t < mt1 * nn1; t += kW)
             oz_tile<true>(D, ps1, LY, Ex1, TYi, B.oz_F[1], (t / nn1) * 16, ylo + t % nn1, KY / 16, mx, oy0, oy0 + ony,
-                          [&](int kx, int y, double v) { Q[(y - oy0) * kLine + kx] = v; }, Ex2, oy0);
+                          [&](int kx, int y, long long z) { Zq[(y - oy0) * kLine + kx] = z; }, Ex2, oy0);
         __syncthreads();
-        line_digits(gq, ony, mx, KX, D, ps2, LX, Ex2);
+        // lines y, contraction kx: element kx weighs 2^(Ex1[kx] + F_y - 1076)
+        line_digits_by([&](int l, int k, uint32_t (&f)[kD]) {
+            z_digits(Zq[l * kLine + k], Ex2[l] + 7 - Ex1[k] - B.oz_F[1], f);
+        }, ony, mx, KX, D, ps2, LX);
         for (int t = threadIdx.x; t < kRows; t += kT) Ex1[t] = 0;
         __syncthreads();
         const int gk = B.ext_lo[2] + zl;
