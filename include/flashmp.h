@@ -274,6 +274,14 @@ int fmp_h_update(fmp_ctx* ctx, double* H, const double* E_new,
 int fmp_cn_step(fmp_ctx* ctx, double* E, double* H, const double* J, double dt,
                 fmp_solve_info* info);
 
+/* fmp_cn_step with the solve started from the linear extrapolation of the
+ * two previous steps, 2 E^n - E_prev (E_prev: DEVICE, E^(n-1), read only; NULL
+ * gives fmp_cn_step). R and the H update still use E^n. With use_learned >= 1
+ * the learned correction is added on top of this guess and kept only when it
+ * lowers the residual. Not in the paper: a time-stepping initial guess. */
+int fmp_cn_step_guess(fmp_ctx* ctx, double* E, double* H, const double* J, double dt,
+                      const double* E_prev, fmp_solve_info* info);
+
 /* ---- Learned initial guess / coarse correction (not in the paper) -------
  * A 3-D CNN N (4 conv layers, 3x3x3 kernels, channels 4 -> 16 -> 16 -> 16 -> 3,
  * ReLU between layers, bf16 tensor-core convolutions with fp32 accumulation)

@@ -77,15 +77,19 @@ def run(args):
             ctx.cnn_set_params(ck["params"])
     log = {"grid": list(w.grid), "precision": args.precision, "rtol": args.rtol, "phase1": [], "plain": [],
            "learned": [], "learned_mode": args.learned_mode}
-    # phase 1: plain steps with recorded pairs
+    # phase 1: plain steps with recorded pairs (E_prev: the field one step back)
     t0 = time.time()
+    E_prev = E.clone()
+    if args.resume and ck.get("E_prev") is not None:
+        E_prev.copy_(ck["E_prev"].to(dev))
     for n in range(step0, min(args.train_until, args.steps)):
+        E_prev.copy_(E)
         info = plain_step_with_pair(ctx, E, H, current(w, n, dt, dev), dt, record=True)
         log["phase1"].append({"step": n, "iters": info["iters"], "ms": info["ms_total"]})
     torch.cuda.synchronize()
     log["phase1_s"] = time.time() - t0
     if args.checkpoint:
-        save(args.checkpoint, E=E, H=H, step=max(step0, args.train_until), params=ctx.cnn_get_params())
+        save(args.checkpoint, E=E, H=H, E_prev=E_prev, step=max(step0, args.train_until), params=ctx.cnn_get_params())
     # phase 2: training
     t0 = time.time()
     if ctx.cnn_num_samples() > 0 and args.train_iters > 0:
@@ -93,15 +97,26 @@ def run(args):
     torch.cuda.synchronize()
     log["train_s"] = time.time() - t0
     ctx.cnn_clear_samples()
-    # phase 3: the same steps twice from the same state
-    E0, H0 = E.clone(), H.clone()
-    for mode, key in ((0, "plain"), (args.learned_mode, "learned")):
-        E.copy_(E0); H.copy_(H0)
+    # phase 3: the same steps from the same state, once per initial guess:
+    # E^n (plain), N on top of E^n (learned); with --extrapolate also
+    # 2 E^n - E^(n-1) and N on top of that
+    E0, H0, P0 = E.clone(), H.clone(), E_prev.clone()
+    runs = [(0, False, "plain"), (args.learned_mode, False, "learned")]
+    if args.extrapolate:
+        runs += [(0, True, "extrap"), (args.learned_mode, True, "learned_extrap")]
+        log.update({"extrap": [], "learned_extrap": []})
+    for mode, extrap, key in runs:
+        E.copy_(E0); H.copy_(H0); E_prev.copy_(P0)
         ctx.set_options(use_learned=mode)
         torch.cuda.synchronize()
         t0 = time.time()
         for n in range(max(step0, args.train_until), args.steps):
-            info = ctx.cn_step(E, H, current(w, n, dt, dev), dt)
+            if extrap:
+                E_cur = E.clone()
+                info = ctx.cn_step(E, H, current(w, n, dt, dev), dt, E_prev=E_prev)
+                E_prev.copy_(E_cur)
+            else:
+                info = ctx.cn_step(E, H, current(w, n, dt, dev), dt)
             log[key].append({"step": n, "iters": info["iters"], "ms": info["ms_total"],
                              "fallback": info["used_fallback"], "res": info["true_rel_res"]})
         torch.cuda.synchronize()
@@ -125,6 +140,8 @@ def main():
     p.add_argument("--precision", default="bf16")
     p.add_argument("--rtol", type=float, default=1e-8)
     p.add_argument("--learned-mode", type=int, default=1)
+    p.add_argument("--extrapolate", action="store_true",
+                   help="also run the steps from the extrapolated guess 2 E^n - E^(n-1), plain and learned")
     p.add_argument("--checkpoint", default=None)
     p.add_argument("--resume", default=None)
     p.add_argument("--out", default=None)

@@ -795,17 +795,27 @@ int fmp_h_update(fmp_ctx* c, double* H, const double* En, const double* Eo, doub
 }
 
 int fmp_cn_step(fmp_ctx* c, double* E, double* H, const double* J, double dt, fmp_solve_info* info) {
-    if (!valid_ctx(c) || !E || !H || E == H || !dt_matches(c->beta, dt)) return FMP_ERR_ARG;
+    return fmp_cn_step_guess(c, E, H, J, dt, nullptr, info);
+}
+
+int fmp_cn_step_guess(fmp_ctx* c, double* E, double* H, const double* J, double dt, const double* E_prev,
+                      fmp_solve_info* info) {
+    if (!valid_ctx(c) || !E || !H || E == H || E_prev == H || !dt_matches(c->beta, dt)) return FMP_ERR_ARG;
     if (int rc = latched(c)) return rc;
     if (int rc = check_edge(c, E)) return rc;
     if (int rc = check_face(c, H)) return rc;
     if (int rc = check_edge(c, J)) return rc;
+    if (int rc = check_edge(c, E_prev)) return rc;
     Range rg("cn_step");
     double* R = c->d_tmp;
     double* Eold = c->d_tmp2;
     c->launches += 2;   // rhs + H update
     FMP_CK(fmp_launch_cn_rhs(E, H, J, c->d_eps_edge, c->beta, dt, R, c->nx, c->ny, c->nz, c->stream));
     FMP_CK(cudaMemcpyAsync(Eold, E, sizeof(double) * c->n_slots, cudaMemcpyDeviceToDevice, c->stream));
+    if (E_prev) {   // initial guess 2 E^n - E^(n-1)
+        ++c->launches;
+        FMP_CK(fmp_launch_extrapolate(E, Eold, E_prev, (long long)c->n_slots, c->stream));
+    }
     int fallback = 0;
     if (c->opt.use_learned >= 1) {
         // learned initial guess x0 = E^n + N(R - A E^n), kept only if it lowers the residual

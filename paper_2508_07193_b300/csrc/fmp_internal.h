@@ -232,6 +232,8 @@ cudaError_t fmp_launch_curlcurl(const double* x, const double* eps, double* y, d
 cudaError_t fmp_launch_cn_rhs(const double* E, const double* H, const double* J,
                               const double* eps, double beta, double dt, double* R, int nx,
                               int ny, int nz, cudaStream_t s);
+// x = 2 E - E_prev over n values (the extrapolated initial guess of a CN step)
+cudaError_t fmp_launch_extrapolate(double* x, const double* E, const double* E_prev, long long n, cudaStream_t s);
 // count += the number of nonzero wall slots of x (face = 0: edge field, 1: face field)
 cudaError_t fmp_launch_wall_count(const double* x, int face, int nx, int ny, int nz, unsigned int* count,
                                   cudaStream_t s);

@@ -284,6 +284,13 @@ k_h_update(double* __restrict__ H, const double* __restrict__ En, const double* 
     H[2 * d.comp + o] -= h * cz;
 }
 
+// Extrapolated initial guess x = 2 E - E_prev (one value per thread, grid-stride).
+__global__ void __launch_bounds__(256)
+k_extrapolate(double* __restrict__ x, const double* __restrict__ E, const double* __restrict__ Ep, long long n) {
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < n; o += (long long)gridDim.x * blockDim.x)
+        x[o] = 2.0 * E[o] - Ep[o];
+}
+
 // Layout check: the number of nonzero wall slots of a field. Edge fields
 // (E and everything shaped like it): Ex at j = 0 or k = 0, Ey at i = 0 or
 // k = 0, Ez at i = 0 or j = 0 (PEC). Face fields (H): Hx at i = 0, Hy at
@@ -344,6 +351,12 @@ cudaError_t fmp_launch_cn_rhs(const double* E, const double* H, const double* J,
                               double beta, double dt, double* R, int nx, int ny, int nz, cudaStream_t s) {
     dim3 b(64, 4, 1);
     k_cn_rhs<<<grid_of(nx, ny, nz, b), b, 0, s>>>(E, H, J, eps, beta, dt, R, dims(nx, ny, nz));
+    return cudaGetLastError();
+}
+
+cudaError_t fmp_launch_extrapolate(double* x, const double* E, const double* E_prev, long long n, cudaStream_t s) {
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 148LL * 16);
+    k_extrapolate<<<blocks, 256, 0, s>>>(x, E, E_prev, n);
     return cudaGetLastError();
 }
 

@@ -99,6 +99,7 @@ def lib():
         "fmp_cn_rhs": (_I, [_P, _P, _P, _P, _D, _P]),
         "fmp_h_update": (_I, [_P, _P, _P, _P, _D]),
         "fmp_cn_step": (_I, [_P, _P, _P, _P, _D, C.POINTER(SolveInfo)]),
+        "fmp_cn_step_guess": (_I, [_P, _P, _P, _P, _D, _P, C.POINTER(SolveInfo)]),
         "fmp_cnn_num_params": (_I, []),
         "fmp_cnn_set_params": (_I, [_P, _P]),
         "fmp_cnn_get_params": (_I, [_P, _P]),
@@ -368,12 +369,19 @@ class Context:
         _check(lib().fmp_h_update(self._h, _ptr(H), _ptr(E_new), _ptr(E_old), float(dt)), "fmp_h_update")
         return H
 
-    def cn_step(self, E, H, J, dt, check=True):
+    def cn_step(self, E, H, J, dt, check=True, E_prev=None):
+        """One CN step; with E_prev (E^(n-1)) the solve starts from 2 E - E_prev
+        (fmp_cn_step_guess)."""
         _field(E, self.shape, "E"); _field(H, self.shape, "H")
         if J is not None:
             _field(J, self.shape, "J")
         info = SolveInfo()
-        rc = lib().fmp_cn_step(self._h, _ptr(E), _ptr(H), _ptr(J), float(dt), C.byref(info))
+        if E_prev is not None:
+            _field(E_prev, self.shape, "E_prev")
+            rc = lib().fmp_cn_step_guess(self._h, _ptr(E), _ptr(H), _ptr(J), float(dt), _ptr(E_prev),
+                                         C.byref(info))
+        else:
+            rc = lib().fmp_cn_step(self._h, _ptr(E), _ptr(H), _ptr(J), float(dt), C.byref(info))
         if check:
             _check(rc, "fmp_cn_step")
         return info.as_dict()
