@@ -42,16 +42,26 @@ def current(w, step, dt, dev):
     return torch.as_tensor(J, device=dev)
 
 
-def plain_step_with_pair(ctx, E, H, J, dt, record=True):
-    """One CN step from the ABI pieces; returns (info, r0, e) and updates E, H."""
+def plain_step_with_pair(ctx, E, H, J, dt, record=True, E_prev=None, ext_pairs=None):
+    """One CN step from the ABI pieces (updates E, H). With record, the pair
+    (R - A E^n, E^(n+1) - E^n) goes to the library's sample pool; with
+    ext_pairs, the pair of the extrapolated guess G = 2 E^n - E^(n-1),
+    (R - A G, E^(n+1) - G), is appended to that list."""
     R = ctx.cn_rhs(E, H, J, dt)
     r0 = ctx.curlcurl_apply(E, c_eps=-1.0, c_k=-ctx.beta)
     r0 += R
+    G = None
+    if ext_pairs is not None:
+        G = 2.0 * E - E_prev
+        rg = ctx.curlcurl_apply(G, c_eps=-1.0, c_k=-ctx.beta)
+        rg += R
     E_old = E.clone()
     x, info = ctx.krylov_solve(R, E)
     ctx.h_update(H, E, E_old, dt)
     if record:
         ctx.cnn_add_sample(r0, (E - E_old).contiguous())
+    if ext_pairs is not None:
+        ext_pairs.append((rg, (E - G).contiguous()))
     return info
 
 
@@ -82,21 +92,37 @@ def run(args):
     E_prev = E.clone()
     if args.resume and ck.get("E_prev") is not None:
         E_prev.copy_(ck["E_prev"].to(dev))
+    ext_pairs = [] if args.extrapolate else None
     for n in range(step0, min(args.train_until, args.steps)):
-        E_prev.copy_(E)
-        info = plain_step_with_pair(ctx, E, H, current(w, n, dt, dev), dt, record=True)
+        cur = E.clone()
+        info = plain_step_with_pair(ctx, E, H, current(w, n, dt, dev), dt, record=True, E_prev=E_prev,
+                                    ext_pairs=ext_pairs if n > step0 else None)
+        E_prev.copy_(cur)
         log["phase1"].append({"step": n, "iters": info["iters"], "ms": info["ms_total"]})
     torch.cuda.synchronize()
     log["phase1_s"] = time.time() - t0
     if args.checkpoint:
         save(args.checkpoint, E=E, H=H, E_prev=E_prev, step=max(step0, args.train_until), params=ctx.cnn_get_params())
-    # phase 2: training
+    # phase 2: training (with --extrapolate, a second network from the same
+    # initial parameters on the extrapolated guess's pairs)
     t0 = time.time()
+    params0 = ctx.cnn_get_params()
     if ctx.cnn_num_samples() > 0 and args.train_iters > 0:
         log["train_loss"] = ctx.cnn_train(args.train_iters, args.crop, lr=args.lr, seed=args.seed)
+    params_plain = ctx.cnn_get_params()
+    ctx.cnn_clear_samples()
+    params_ext = params_plain
+    if ext_pairs:
+        ctx.cnn_set_params(params0)
+        for r0, e in ext_pairs:
+            ctx.cnn_add_sample(r0, e)
+        if args.train_iters > 0:
+            log["train_loss_extrap"] = ctx.cnn_train(args.train_iters, args.crop, lr=args.lr, seed=args.seed)
+        params_ext = ctx.cnn_get_params()
+        ctx.cnn_clear_samples()
+        ext_pairs.clear()
     torch.cuda.synchronize()
     log["train_s"] = time.time() - t0
-    ctx.cnn_clear_samples()
     # phase 3: the same steps from the same state, once per initial guess:
     # E^n (plain), N on top of E^n (learned); with --extrapolate also
     # 2 E^n - E^(n-1) and N on top of that
@@ -107,6 +133,7 @@ def run(args):
         log.update({"extrap": [], "learned_extrap": []})
     for mode, extrap, key in runs:
         E.copy_(E0); H.copy_(H0); E_prev.copy_(P0)
+        ctx.cnn_set_params(params_ext if extrap else params_plain)
         ctx.set_options(use_learned=mode)
         torch.cuda.synchronize()
         t0 = time.time()
