@@ -73,7 +73,7 @@ def dist_env():
     return rank, world, local
 
 
-OZAKI_MAX_EXTENT = 40   # largest box extent of the digit-split float64 kernels
+OZAKI_MAX_EXTENT = 80   # largest box extent of the digit-split float64 kernels
 
 
 def max_over_ranks(value, world, device="cpu"):

@@ -72,9 +72,10 @@ typedef enum fmp_precision {
                              * accumulate exactly in fp32 and are combined in
                              * integer arithmetic; the 3x3 (Eq. 12) in float64.
                              * Error of one axis transform <= about 2^-46 of the
-                             * line's largest value times its length. Every box
-                             * extent must be <= 40, else FMP_ERR_UNSUPPORTED
-                             * from the preconditioner calls.                  */
+                             * line's largest value times its length. Lines
+                             * longer than 40 accumulate in fp32 partials of two
+                             * k-steps moved into 64-bit sums. All extents the
+                             * library accepts (<= 80) are supported.          */
 } fmp_precision;
 
 typedef enum fmp_krylov_kind {

@@ -34,6 +34,7 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -43,7 +44,6 @@ constexpr int kT = 256;   // 8 warps
 constexpr int kW = kT / 32;
 constexpr int kD = 6;     // digits per value
 constexpr int kCT = FMP_OZAKI_COLS;   // pass B column tile (lines)
-constexpr int kMaxM = FMP_OZAKI_MAX;
 
 __host__ __device__ constexpr int rup(int v, int a) { return (v + a - 1) / a * a; }
 __host__ __device__ constexpr int oz_np(int m) { return rup(m, 8); }       // modes, padded to the MMA n
@@ -55,9 +55,16 @@ __host__ __device__ constexpr int oz_lk(int m) { return rup(m, 16) + 8; }  // sh
 // n = slot). Sizes in 32-bit words.
 __host__ __device__ constexpr int oz_tabf(int m) { return (oz_np(m) / 8) * (oz_kp(m) / 16) * (kD / 2) * 32 * 4; }
 
-constexpr int kRows = rup(kMaxM, 16);              // lines per digit buffer
-constexpr int kDigS = kD * kRows * oz_lk(kMaxM);   // digit buffer (elements)
-constexpr int kLine = kMaxM | 1;                          // odd stride of float64 line buffers
+// Buffer sizes of one size class (largest extent M: 40 or FMP_OZAKI_MAX).
+template <int M>
+struct Sz {
+    static constexpr int kRows = rup(M, 16);              // lines per digit buffer
+    static constexpr int kLK = oz_lk(M);                  // its row stride
+    static constexpr int kDigS = kD * kRows * kLK;        // digit buffer (elements)
+    static constexpr int kLine = M | 1;                   // odd stride of float64 line buffers
+    static constexpr bool kSplit = M > 40;                // contractions may exceed 40
+    static constexpr int kMinBlocks = M > 40 ? 2 : 3;
+};
 
 // ---- digits ----------------------------------------------------------------
 
@@ -141,8 +148,7 @@ __device__ __forceinline__ void line_digits(Get get, int nlines, int K, int Kp, 
                    LK);
 }
 
-// Z 2^(emax + F - 1076) truncated to float64, Z = sum_g acc_g 256^(5 - g) with
-// acc_g exact integers below 2^22 in magnitude (integer operations only).
+// Z 2^(emax + F - 1076) truncated to float64 (integer operations only).
 // Z = sum_g acc_g 256^(5 - g): i_g = bits(acc_g + 1.5 * 2^23) - bits(1.5 * 2^23);
 // pairs i_g 256 + i_(g+1) fit 31 bits (wrapping unsigned arithmetic, exact).
 __device__ __forceinline__ long long class_sum(const float (&acc)[kD][4], int i) {
@@ -164,9 +170,8 @@ __device__ __forceinline__ int z_field(long long Z, int emax, int F) {
     return emax + F - __clzll((long long)a) + 10;
 }
 
-__device__ __forceinline__ double combine(const float (&acc)[kD][4], int i, int emax, int F) {
+__device__ __forceinline__ double z_to_double(long long Z, int emax, int F) {
     if (emax >= 2047) return __longlong_as_double(0x7ff8000000000000LL);   // Inf / NaN in the line
-    const long long Z = class_sum(acc, i);
     const bool neg = Z < 0;
     unsigned long long a = neg ? (unsigned long long)(-Z) : (unsigned long long)Z;
     const int lz = __clzll((long long)a);
@@ -208,7 +213,10 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
 // without a float64 round trip, and folds the largest exponent field of each
 // output column n (the next stage's line) into exo[n - eoff] (atomicMax; exo
 // zeroed beforehand).
-template <bool kZ, class Epi>
+// With kSplit (contractions longer than 40), the fp32 classes are moved into
+// 64-bit partial sums every two k-steps, so that every fp32 partial stays an
+// exact integer below 2^22 (6 * 32 * 2^14); |Z| stays below K 2^54.
+template <bool kZ, bool kSplit, class Epi>
 __device__ __forceinline__ void oz_tile(const uint16_t* D, int dps, int LKd, const int* Ex,
                                         const uint4* __restrict__ Tf, int F, int m0, int nt, int ksteps, int lhi,
                                         int nlo, int nhi, Epi epi, int* exo = nullptr, int eoff = 0) {
@@ -216,6 +224,7 @@ __device__ __forceinline__ void oz_tile(const uint16_t* D, int dps, int LKd, con
     float acc[kD][4];
 #pragma unroll
     for (int g = 0; g < kD; ++g) acc[g][0] = acc[g][1] = acc[g][2] = acc[g][3] = 0.f;
+    long long zp[4] = {0, 0, 0, 0};
     const uint16_t* ap = D + (m0 + (lane & 15)) * LKd + (lane >> 4) * 8;
     const uint4* tp = Tf + (size_t)nt * ksteps * (kD / 2) * 32 + lane;
     for (int ks = 0; ks < ksteps; ++ks) {
@@ -233,24 +242,30 @@ __device__ __forceinline__ void oz_tile(const uint16_t* D, int dps, int LKd, con
 #pragma unroll
             for (int g = p; g < kD; ++g) mma_bf16(acc[g], a, b[g - p][0], b[g - p][1]);
         }
+        if (kSplit && (ks & 1) && ks + 1 < ksteps) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) zp[i] += class_sum(acc, i);
+#pragma unroll
+            for (int g = 0; g < kD; ++g) acc[g][0] = acc[g][1] = acc[g][2] = acc[g][3] = 0.f;
+        }
     }
     const int r = lane >> 2, cc = 2 * (lane & 3);
     // the four outputs are formed without branches (independent chains that
     // interleave), then stored where valid
     const int e0 = Ex[m0 + r], e1 = Ex[m0 + r + 8];
+    long long zv[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) zv[i] = kSplit ? zp[i] + class_sum(acc, i) : class_sum(acc, i);
     if (!kZ) {
         double v[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) v[i] = combine(acc, i, i < 2 ? e0 : e1, F);
+        for (int i = 0; i < 4; ++i) v[i] = z_to_double(zv[i], i < 2 ? e0 : e1, F);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int line = m0 + r + (i >> 1) * 8, n = nt * 8 + cc + (i & 1);
             if (line < lhi && n >= nlo && n < nhi) epi(line, n, v[i]);
         }
     } else {
-        long long zv[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) zv[i] = class_sum(acc, i);
         int ea = 0, eb = 0;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -277,13 +292,16 @@ __device__ __forceinline__ void oz_tile(const uint16_t* D, int dps, int LKd, con
 // ---- pass A: gather, forward x and y of a group of z-slabs ------------------
 // Shared: D (digits), Xs[y][x] / Pt[kx][y] (float64, one buffer: the slab is
 // dead once its digits are cut), Ex.
-constexpr size_t kSmemA = sizeof(uint16_t) * kDigS + sizeof(double) * kMaxM * kLine + sizeof(int) * 2 * kRows;
+template <int M, class SZ = Sz<M>>
+constexpr size_t kSmemA = sizeof(uint16_t) * SZ::kDigS + sizeof(double) * M * SZ::kLine + sizeof(int) * 2 * SZ::kRows;
 
-__global__ void __launch_bounds__(kT, 3)
+template <int M>
+__global__ void __launch_bounds__(kT, Sz<M>::kMinBlocks)
 k_oz_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox* __restrict__ boxes,
             const int4* __restrict__ items, const uint4* __restrict__ otab, int nx, int ny, int nz,
             const double* __restrict__ gate) {
     if (gate && *gate != 0.0) return;
+    using SZ = Sz<M>;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int4 it = items[blockIdx.x];
     const FmpBox B = boxes[it.x];
@@ -291,15 +309,15 @@ k_oz_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox
     const int mx = B.m[0], my = B.m[1], mz = B.m[2];
     const int NX = oz_np(mx), NY = oz_np(my), KX = oz_kp(mx), KY = oz_kp(my), LX = oz_lk(mx), LY = oz_lk(my);
     uint16_t* D = reinterpret_cast<uint16_t*>(smraw);
-    double* Pt = reinterpret_cast<double*>(D + kDigS);   // Xs[y][x], then Pt[kx][y]; stride kLine
-    int* Ex1 = reinterpret_cast<int*>(Pt + kMaxM * kLine);   // exponents of the x lines (rows y)
-    int* Ex2 = Ex1 + kRows;                                   // of the y lines (columns kx)
+    double* Pt = reinterpret_cast<double*>(D + SZ::kDigS);   // Xs[y][x], then Pt[kx][y]; stride SZ::kLine
+    int* Ex1 = reinterpret_cast<int*>(Pt + M * SZ::kLine);   // exponents of the x lines (rows y)
+    int* Ex2 = Ex1 + SZ::kRows;                                   // of the y lines (columns kx)
     const bool sx = c != 0, sy = c != 1;
     // forward tables (C or S): Bt[k][x] = T[k][x]
     const uint4* TX = otab + (B.oz_off[0] + (sx ? 2 : 0) * oz_tabf(mx)) / 4;
     const uint4* TY = otab + (B.oz_off[1] + (sy ? 2 : 0) * oz_tabf(my)) / 4;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ps1 = kRows * LX, ps2 = kRows * LY;
+    const int ps1 = SZ::kRows * LX, ps2 = SZ::kRows * LY;
     const int mt1 = oz_kp(my) / 16, nt1 = NX / 8, mt2 = oz_kp(mx) / 16, nt2 = NY / 8;
     for (int kz = z0; kz < z0 + zn; ++kz) {
         const int gk = B.ext_lo[2] + kz;
@@ -314,30 +332,30 @@ k_oz_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox
             int e = 0;
             for (int x = lane; x < mx; x += 32) {
                 const double v = rowok && !(c != 0 && x == 0) ? __ldg(srow + x) : 0.0;
-                Pt[y * kLine + x] = v;
+                Pt[y * SZ::kLine + x] = v;
                 e = max(e, hexp(v));
             }
             e = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
             if (lane == 0) Ex1[y] = e;
         }
         __syncthreads();
-        line_digits([&](int l, int k) { return Pt[l * kLine + k]; }, my, mx, KX, D, ps1, LX, Ex1);
-        for (int t = threadIdx.x; t < kRows; t += kT) Ex2[t] = 0;
+        line_digits([&](int l, int k) { return Pt[l * SZ::kLine + k]; }, my, mx, KX, D, ps1, LX, Ex1);
+        for (int t = threadIdx.x; t < SZ::kRows; t += kT) Ex2[t] = 0;
         __syncthreads();
         long long* Zt = reinterpret_cast<long long*>(Pt);   // class sums Zt[kx][y]
         for (int t = warp; t < mt1 * nt1; t += kW)
-            oz_tile<true>(D, ps1, LX, Ex1, TX, B.oz_F[0], (t / nt1) * 16, t % nt1, KX / 16, my, 0, mx,
-                          [&](int y, int kx, long long z) { Zt[kx * kLine + y] = z; }, Ex2, 0);
+            oz_tile<true, SZ::kSplit>(D, ps1, LX, Ex1, TX, B.oz_F[0], (t / nt1) * 16, t % nt1, KX / 16, my, 0, mx,
+                          [&](int y, int kx, long long z) { Zt[kx * SZ::kLine + y] = z; }, Ex2, 0);
         __syncthreads();
         // lines kx, contraction y: cut the class sums, element y of line kx
         // weighs 2^(Ex1[y] + F_x - 1076)
         line_digits_by([&](int l, int k, uint32_t (&f)[kD]) {
-            z_digits(Zt[l * kLine + k], Ex2[l] + 7 - Ex1[k] - B.oz_F[0], f);
+            z_digits(Zt[l * SZ::kLine + k], Ex2[l] + 7 - Ex1[k] - B.oz_F[0], f);
         }, mx, my, KY, D, ps2, LY);
         __syncthreads();
         double* out = scr + B.scr_off + ((long long)c * mz + kz) * mx * my;
         for (int t = warp; t < mt2 * nt2; t += kW)
-            oz_tile<false>(D, ps2, LY, Ex2, TY, B.oz_F[1], (t / nt2) * 16, t % nt2, KY / 16, mx, 0, my,
+            oz_tile<false, SZ::kSplit>(D, ps2, LY, Ex2, TY, B.oz_F[1], (t / nt2) * 16, t % nt2, KY / 16, mx, 0, my,
                            [&](int kx, int ky, double v) { out[ky * mx + kx] = v; });
         // no barrier: the next slab's rows go to Pt and Ex1, which this
         // stage no longer reads
@@ -346,16 +364,19 @@ k_oz_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox
 
 // ---- pass B: forward z, 3x3 (float64), inverse z on owned slabs ------------
 // Shared: the digits of 3 x kCT lines (row = component * kCT + column),
-// V[line][z] (float64, stride kLine), Ex[line].
+// V[line][z] (float64, stride SZ::kLine), Ex[line].
 constexpr int kLB = 3 * kCT;   // lines of pass B
-constexpr size_t kSmemB = sizeof(uint16_t) * kD * kLB * oz_lk(kMaxM) + sizeof(double) * kLB * kLine +
+template <int M, class SZ = Sz<M>>
+constexpr size_t kSmemB = sizeof(uint16_t) * kD * kLB * SZ::kLK + sizeof(double) * kLB * SZ::kLine +
                           sizeof(int) * 2 * kLB;
 
-__global__ void __launch_bounds__(kT, 3)
+template <int M>
+__global__ void __launch_bounds__(kT, Sz<M>::kMinBlocks)
 k_oz_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int4* __restrict__ items,
              const uint4* __restrict__ otab, const double* __restrict__ tabs, const double* __restrict__ modeinv,
              double beta, const double* __restrict__ gate) {
     if (gate && *gate != 0.0) return;
+    using SZ = Sz<M>;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int4 itb = items[blockIdx.x];
     const FmpBox B = boxes[itb.x];
@@ -364,8 +385,8 @@ k_oz_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const i
     const int nxy = mx * my;
     const int NZ = oz_np(mz), KZ = oz_kp(mz), LZ = oz_lk(mz);
     uint16_t* D = reinterpret_cast<uint16_t*>(smraw);        // [kD][kLB][LZ]
-    double* V = reinterpret_cast<double*>(D + kD * kLB * oz_lk(kMaxM));   // [kLB][kLine]
-    int* Ex1 = reinterpret_cast<int*>(V + kLB * kLine);   // exponents of the forward lines
+    double* V = reinterpret_cast<double*>(D + kD * kLB * SZ::kLK);   // [kLB][SZ::kLine]
+    int* Ex1 = reinterpret_cast<int*>(V + kLB * SZ::kLine);   // exponents of the forward lines
     int* Ex2 = Ex1 + kLB;                                 // of the inverse lines
     const uint4* tb = otab + B.oz_off[2] / 4;
     const int tf = oz_tabf(mz) / 4;
@@ -381,7 +402,7 @@ k_oz_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const i
     const int oz0 = B.own_lo[2], oz1 = B.own_lo[2] + B.own_n[2];
     const int nlo = oz0 / 8, nn = rup(oz1, 8) / 8 - nlo, nf = NZ / 8;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    auto gv = [&](int l, int k) { return V[l * kLine + k]; };
+    auto gv = [&](int l, int k) { return V[l * SZ::kLine + k]; };
     for (int t = threadIdx.x; t < kLB; t += kT) Ex1[t] = 0;
     __syncthreads();
     for (int col0 = gcol0; col0 < gcol0 + gcols; col0 += kCT) {
@@ -395,7 +416,7 @@ k_oz_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const i
             if (col < ncol) {
                 const int cc = cz / mz, z = cz - cc * mz;
                 const double v = S[(long long)cz * nxy + col0 + col];
-                V[(cc * kCT + col) * kLine + z] = v;
+                V[(cc * kCT + col) * SZ::kLine + z] = v;
                 atomicMax(Ex1 + cc * kCT + col, hexp(v));
             }
         }
@@ -406,8 +427,8 @@ k_oz_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const i
         // forward z (DST-I for Ex, Ey; DCT-II for Ez), modes back into V
         for (int t = warp; t < 3 * nf; t += kW) {
             const int cc = t / nf, n0 = (t - cc * nf) * 8;
-            oz_tile<false>(D, ps, LZ, Ex1, cc == 2 ? TCf : TSf, F, cc * kCT, n0 / 8, KZ / 16, cc * kCT + ncol, 0, mz,
-                           [&](int l, int kz, double x) { V[l * kLine + kz] = x; });
+            oz_tile<false, SZ::kSplit>(D, ps, LZ, Ex1, cc == 2 ? TCf : TSf, F, cc * kCT, n0 / 8, KZ / 16, cc * kCT + ncol, 0, mz,
+                           [&](int l, int kz, double x) { V[l * SZ::kLine + kz] = x; });
         }
         __syncthreads();
         // e_c = inv (r_c + (beta / eps_bar) sigma_c (sigma . r)), inv = 1 / (eps_bar
@@ -417,15 +438,15 @@ k_oz_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const i
             const int q = col0 + col;
             const int ky = q / mx, kx = q - ky * mx;
             const double sx = sgx[kx], sy = sgy[ky], sz = sgz[kz];
-            double* o = V + col * kLine + kz;
-            const double r0 = o[0], r1 = o[kCT * kLine], r2 = o[2 * kCT * kLine];
+            double* o = V + col * SZ::kLine + kz;
+            const double r0 = o[0], r1 = o[kCT * SZ::kLine], r2 = o[2 * kCT * SZ::kLine];
             const double inv = inv_tab[(long long)kz * nxy + q];
             const double sr = fma(sx, r0, fma(sy, r1, sz * r2));
             const double f = (beb * inv) * sr;
             const double e0 = fma(f, sx, inv * r0), e1 = fma(f, sy, inv * r1), e2 = fma(f, sz, inv * r2);
             o[0] = e0;
-            o[kCT * kLine] = e1;
-            o[2 * kCT * kLine] = e2;
+            o[kCT * SZ::kLine] = e1;
+            o[2 * kCT * SZ::kLine] = e2;
             atomicMax(Ex2 + col, hexp(e0));
             atomicMax(Ex2 + kCT + col, hexp(e1));
             atomicMax(Ex2 + 2 * kCT + col, hexp(e2));
@@ -438,7 +459,7 @@ k_oz_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const i
         for (int t = warp; t < 3 * nn; t += kW) {
             const int cc = t / nn, n0 = (nlo + t - cc * nn) * 8;
             double* dst = S + (long long)cc * mz * nxy + col0 - (long long)cc * kCT;
-            oz_tile<false>(D, ps, LZ, Ex2, cc == 2 ? TCi : TSi, F, cc * kCT, n0 / 8, KZ / 16, cc * kCT + ncol, oz0,
+            oz_tile<false, SZ::kSplit>(D, ps, LZ, Ex2, cc == 2 ? TCi : TSi, F, cc * kCT, n0 / 8, KZ / 16, cc * kCT + ncol, oz0,
                            oz1, [&](int l, int z, double x) { dst[(long long)z * nxy + l] = x; });
         }
         // no barrier: the next tile writes V and Ex1, which this stage no
@@ -448,13 +469,16 @@ k_oz_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const i
 
 // ---- pass C: inverse y and x of a group of owned z-slabs, owned scatter -----
 // Shared: D, Sm[ky][kx], Q[y][kx] (float64), Ex.
-constexpr size_t kSmemC = sizeof(uint16_t) * kDigS + sizeof(double) * 2 * kMaxM * kLine + sizeof(int) * 2 * kRows;
+template <int M, class SZ = Sz<M>>
+constexpr size_t kSmemC = sizeof(uint16_t) * SZ::kDigS + sizeof(double) * 2 * M * SZ::kLine + sizeof(int) * 2 * SZ::kRows;
 
-__global__ void __launch_bounds__(kT, 3)
+template <int M>
+__global__ void __launch_bounds__(kT, Sz<M>::kMinBlocks)
 k_oz_inv_xy(const double* __restrict__ scr, double* __restrict__ zout, const FmpBox* __restrict__ boxes,
             const int4* __restrict__ items, const uint4* __restrict__ otab, int nx, int ny, int nz,
             const double* __restrict__ gate) {
     if (gate && *gate != 0.0) return;
+    using SZ = Sz<M>;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int4 it = items[blockIdx.x];
     const FmpBox B = boxes[it.x];
@@ -463,21 +487,21 @@ k_oz_inv_xy(const double* __restrict__ scr, double* __restrict__ zout, const Fmp
     const int NX = oz_np(mx), NY = oz_np(my), KX = oz_kp(mx), KY = oz_kp(my), LX = oz_lk(mx), LY = oz_lk(my);
     const int oy0 = B.own_lo[1], ony = B.own_n[1], ox0 = B.own_lo[0], onx = B.own_n[0];
     uint16_t* D = reinterpret_cast<uint16_t*>(smraw);
-    double* Sm = reinterpret_cast<double*>(D + kDigS);   // [ky][kx], stride kLine
-    double* Q = Sm + kMaxM * kLine;                     // [y - oy0][kx], stride kLine
-    int* Ex1 = reinterpret_cast<int*>(Q + kMaxM * kLine);   // exponents of the ky lines (columns kx)
-    int* Ex2 = Ex1 + kRows;                                  // of the kx lines (owned rows y)
+    double* Sm = reinterpret_cast<double*>(D + SZ::kDigS);   // [ky][kx], stride SZ::kLine
+    double* Q = Sm + M * SZ::kLine;                     // [y - oy0][kx], stride SZ::kLine
+    int* Ex1 = reinterpret_cast<int*>(Q + M * SZ::kLine);   // exponents of the ky lines (columns kx)
+    int* Ex2 = Ex1 + SZ::kRows;                                  // of the kx lines (owned rows y)
     const bool sx = c != 0, sy = c != 1;
     // inverse tables: Bt[i][k] = T[k][i]
     const uint4* TYi = otab + (B.oz_off[1] + (sy ? 3 : 1) * oz_tabf(my)) / 4;
     const uint4* TXi = otab + (B.oz_off[0] + (sx ? 3 : 1) * oz_tabf(mx)) / 4;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ps1 = kRows * LY, ps2 = kRows * LX;
+    const int ps1 = SZ::kRows * LY, ps2 = SZ::kRows * LX;
     const int mt1 = oz_kp(mx) / 16, ylo = oy0 / 8, nn1 = rup(oy0 + ony, 8) / 8 - ylo;
     const int mt2 = rup(ony, 16) / 16, xlo = ox0 / 8, nn2 = rup(ox0 + onx, 8) / 8 - xlo;
-    auto gs = [&](int l, int k) { return Sm[k * kLine + l]; };   // line kx, element ky
+    auto gs = [&](int l, int k) { return Sm[k * SZ::kLine + l]; };   // line kx, element ky
     long long* Zq = reinterpret_cast<long long*>(Q);             // class sums Zq[y - oy0][kx]
-    for (int t = threadIdx.x; t < kRows; t += kT) Ex1[t] = 0;
+    for (int t = threadIdx.x; t < SZ::kRows; t += kT) Ex1[t] = 0;
     __syncthreads();
     for (int zl = z0; zl < z0 + zn; ++zl) {
         const double* src = scr + B.scr_off + ((long long)c * mz + zl) * mx * my;
@@ -485,27 +509,27 @@ k_oz_inv_xy(const double* __restrict__ scr, double* __restrict__ zout, const Fmp
         for (int ky = warp; ky < my; ky += kW)
             for (int kx = lane; kx < mx; kx += 32) {
                 const double v = src[ky * mx + kx];
-                Sm[ky * kLine + kx] = v;
+                Sm[ky * SZ::kLine + kx] = v;
                 atomicMax(Ex1 + kx, hexp(v));
             }
         __syncthreads();
         line_digits(gs, mx, my, KY, D, ps1, LY, Ex1);
-        for (int t = threadIdx.x; t < kRows; t += kT) Ex2[t] = 0;
+        for (int t = threadIdx.x; t < SZ::kRows; t += kT) Ex2[t] = 0;
         __syncthreads();
         for (int t = warp; t < mt1 * nn1; t += kW)
-            oz_tile<true>(D, ps1, LY, Ex1, TYi, B.oz_F[1], (t / nn1) * 16, ylo + t % nn1, KY / 16, mx, oy0, oy0 + ony,
-                          [&](int kx, int y, long long z) { Zq[(y - oy0) * kLine + kx] = z; }, Ex2, oy0);
+            oz_tile<true, SZ::kSplit>(D, ps1, LY, Ex1, TYi, B.oz_F[1], (t / nn1) * 16, ylo + t % nn1, KY / 16, mx, oy0, oy0 + ony,
+                          [&](int kx, int y, long long z) { Zq[(y - oy0) * SZ::kLine + kx] = z; }, Ex2, oy0);
         __syncthreads();
         // lines y, contraction kx: element kx weighs 2^(Ex1[kx] + F_y - 1076)
         line_digits_by([&](int l, int k, uint32_t (&f)[kD]) {
-            z_digits(Zq[l * kLine + k], Ex2[l] + 7 - Ex1[k] - B.oz_F[1], f);
+            z_digits(Zq[l * SZ::kLine + k], Ex2[l] + 7 - Ex1[k] - B.oz_F[1], f);
         }, ony, mx, KX, D, ps2, LX);
-        for (int t = threadIdx.x; t < kRows; t += kT) Ex1[t] = 0;
+        for (int t = threadIdx.x; t < SZ::kRows; t += kT) Ex1[t] = 0;
         __syncthreads();
         const int gk = B.ext_lo[2] + zl;
         double* dst = zout + (((long long)c * nz + gk) * ny + B.ext_lo[1] + oy0) * (long long)nx + B.ext_lo[0];
         for (int t = warp; t < mt2 * nn2; t += kW)
-            oz_tile<false>(D, ps2, LX, Ex2, TXi, B.oz_F[0], (t / nn2) * 16, xlo + t % nn2, KX / 16, ony, ox0,
+            oz_tile<false, SZ::kSplit>(D, ps2, LX, Ex2, TXi, B.oz_F[0], (t / nn2) * 16, xlo + t % nn2, KX / 16, ony, ox0,
                            ox0 + onx, [&](int yl, int x, double v) { dst[(long long)yl * nx + x] = v; });
         // no barrier: the next slab writes Sm and Ex1, which this stage no
         // longer reads
@@ -531,8 +555,6 @@ uint16_t host_bf16(int d) {
 }
 
 }  // namespace
-
-int fmp_ozaki_table_len(int m) { return 4 * oz_tabf(m); }
 
 // The four tables of extent m as the column operand Bt[n][k] -- C (Bt =
 // C[k][i], forward), C^T (Bt[i][k] = C[k][i], inverse), S, S^T -- cut into
@@ -571,25 +593,47 @@ void fmp_ozaki_tables(int m, const double* C, const double* S, std::vector<uint3
         }
 }
 
-cudaError_t fmp_transform_init_ozaki() {
+namespace {
+
+template <int M>
+cudaError_t init_size() {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_oz_fwd_xy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemA))) return e;
-    if ((e = cudaFuncSetAttribute(k_oz_z_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemB))) return e;
-    return cudaFuncSetAttribute(k_oz_inv_xy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemC);
+    if ((e = cudaFuncSetAttribute(k_oz_fwd_xy<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemA<M>)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_oz_z_solve<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemB<M>)))
+        return e;
+    return cudaFuncSetAttribute(k_oz_inv_xy<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemC<M>);
+}
+
+template <int M>
+void launch_size(const FmpPlan& p, const uint4* otab, const double* tabs, const double* modeinv, const double* r,
+                 double* z, double* scratch, int nx, int ny, int nz, double beta, cudaStream_t s, const double* gate) {
+    if (p.n_items_oa > 0)
+        k_oz_fwd_xy<M><<<p.n_items_oa, kT, kSmemA<M>, s>>>(r, scratch, p.d_boxes, p.d_items_oa, otab, nx, ny, nz,
+                                                            gate);
+    if (p.n_items_ob > 0)
+        k_oz_z_solve<M><<<p.n_items_ob, kT, kSmemB<M>, s>>>(scratch, p.d_boxes, p.d_items_ob, otab, tabs, modeinv,
+                                                             beta, gate);
+    if (p.n_items_oc > 0)
+        k_oz_inv_xy<M><<<p.n_items_oc, kT, kSmemC<M>, s>>>(scratch, z, p.d_boxes, p.d_items_oc, otab, nx, ny, nz,
+                                                            gate);
+}
+
+}  // namespace
+
+cudaError_t fmp_transform_init_ozaki() {
+    cudaError_t e = init_size<40>();
+    return e ? e : init_size<FMP_OZAKI_MAX>();
 }
 
 cudaError_t fmp_launch_transform_solve_ozaki(const FmpPlan& p, const uint32_t* otab32, const double* tabs,
                                              const double* modeinv, const double* r, double* z, double* scratch,
                                              int nx, int ny, int nz, double beta, cudaStream_t s,
                                              const double* gate) {
-    if (p.max_m[0] > kMaxM || p.max_m[1] > kMaxM || p.max_m[2] > kMaxM) return cudaErrorNotSupported;
+    const int mmax = std::max(p.max_m[0], std::max(p.max_m[1], p.max_m[2]));
+    if (mmax > FMP_OZAKI_MAX) return cudaErrorNotSupported;
     const uint4* otab = reinterpret_cast<const uint4*>(otab32);
-    if (p.n_items_oa > 0)
-        k_oz_fwd_xy<<<p.n_items_oa, kT, kSmemA, s>>>(r, scratch, p.d_boxes, p.d_items_oa, otab, nx, ny, nz, gate);
-    if (p.n_items_ob > 0)
-        k_oz_z_solve<<<p.n_items_ob, kT, kSmemB, s>>>(scratch, p.d_boxes, p.d_items_ob, otab, tabs, modeinv, beta,
-                                                      gate);
-    if (p.n_items_oc > 0)
-        k_oz_inv_xy<<<p.n_items_oc, kT, kSmemC, s>>>(scratch, z, p.d_boxes, p.d_items_oc, otab, nx, ny, nz, gate);
+    if (mmax <= 40) launch_size<40>(p, otab, tabs, modeinv, r, z, scratch, nx, ny, nz, beta, s, gate);
+    else launch_size<FMP_OZAKI_MAX>(p, otab, tabs, modeinv, r, z, scratch, nx, ny, nz, beta, s, gate);
     return cudaGetLastError();
 }

@@ -14,7 +14,7 @@
 #define FMP_MP_SLAB_GROUP 4   // z-slabs per CTA in the reduced-precision passes A and C
 #define FMP_MP_TILE_GROUP 4   // column tiles per CTA in the reduced-precision pass B
 #define FMP_FUSED_MAX 40      // largest extent of a box solved by the fused cluster kernel
-#define FMP_OZAKI_MAX 40      // largest extent of the digit-split float64 kernels
+#define FMP_OZAKI_MAX 80      // largest extent of the digit-split float64 kernels
 #define FMP_OZAKI_SLABS 2     // z-slabs per CTA in their passes A and C
 #define FMP_OZAKI_COLS 16     // columns per CTA (one tile) in their pass B
 
@@ -245,7 +245,6 @@ cudaError_t fmp_transform_init_mixed(const FmpPlan& p);
 // exact products of bf16 digit planes. Every box extent must be <= FMP_OZAKI_MAX.
 cudaError_t fmp_transform_init_ozaki();
 void fmp_ozaki_tables(int m, const double* C, const double* S, std::vector<uint32_t>& out, int* F);
-int fmp_ozaki_table_len(int m);
 cudaError_t fmp_launch_transform_solve_ozaki(const FmpPlan& p, const uint32_t* otab, const double* tabs,
                                              const double* modeinv, const double* r, double* z, double* scratch,
                                              int nx, int ny, int nz, double beta, cudaStream_t s,

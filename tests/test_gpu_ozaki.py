@@ -46,13 +46,38 @@ def test_box32_error_against_native_float64():
     assert r <= 1e-12
 
 
-def test_extent_above_limit_is_unsupported():
-    from paper_2508_07193_b300 import flashmp as F
-    ctx = _box_ctx((41, 8, 8), 2.0)
-    r = np.zeros((3, 8, 8, 41))
-    with pytest.raises(F.FlashMPError) as e:
-        ctx.box_solve(0, dev(r))
-    assert e.value.status == F.FMP_ERR_UNSUPPORTED
+@pytest.mark.parametrize("grid", [(48, 48, 48), (80, 9, 12), (64, 33, 41), (41, 5, 70)])
+def test_box_solve_long_lines_match_oracle(grid):
+    """Extents 41-80: the contraction is accumulated in two-k-step fp32
+    partials moved into 64-bit sums (each partial exact)."""
+    rng = np.random.default_rng(sum(grid))
+    eps = rng.uniform(1, 10)
+    w = wl.make_workload("box", grid, seed=sum(grid), uniform_eps=True, overlap=0)
+    x = host(_box_ctx(grid, eps).box_solve(0, dev(w.rhs)))
+    ref = box.exact_solve(w.rhs, eps, 0.25)
+    assert rel(x, ref) <= FP64_TOL
+    assert np.all(x[ras.box_wall(grid)] == 0.0)
+
+
+def test_uneven_workload_sampled_boxes_and_native_agreement():
+    """The 320 x 256 x 192 uneven workload (extents 28-68): owned blocks of
+    three boxes against the oracle, the whole field against the float64 kernels."""
+    w = wl.grid_uneven()
+    ctx = context(w, precision="fp64_ozaki")
+    z = host(ctx.precond_apply(dev(w.rhs)))
+    ee = yee.edge_eps(w.grid, w.eps_cell)
+    boxes = ras.partition(w.grid, w.cuts, w.overlap)
+    big = max(range(len(boxes)), key=lambda i: max(boxes[i].ext_hi[a] - boxes[i].ext_lo[a] for a in range(3)))
+    for i in (0, big, len(boxes) - 1):
+        b = boxes[i]
+        eb = box.exact_solve(ras.restrict(w.rhs, b), ras.eps_bar(ee, b), w.beta)
+        part = np.zeros_like(w.rhs)
+        ras.prolong_owned(part, eb, b)
+        (x0, y0, z0), (x1, y1, z1) = b.own_lo, b.own_hi
+        sl = (slice(None), slice(z0, z1), slice(y0, y1), slice(x0, x1))
+        assert rel(z[sl], part[sl]) <= FP64_TOL
+    zn = host(context(w).precond_apply(dev(w.rhs)))
+    assert rel(z, zn) <= 1e-13
 
 
 @pytest.mark.parametrize("w", [
