@@ -92,7 +92,8 @@ def run(args):
     E_prev = E.clone()
     if args.resume and ck.get("E_prev") is not None:
         E_prev.copy_(ck["E_prev"].to(dev))
-    ext_pairs = [] if args.extrapolate else None
+    extrapolate = getattr(args, "extrapolate", False)
+    ext_pairs = [] if extrapolate else None
     for n in range(step0, min(args.train_until, args.steps)):
         cur = E.clone()
         info = plain_step_with_pair(ctx, E, H, current(w, n, dt, dev), dt, record=True, E_prev=E_prev,
@@ -128,7 +129,7 @@ def run(args):
     # 2 E^n - E^(n-1) and N on top of that
     E0, H0, P0 = E.clone(), H.clone(), E_prev.clone()
     runs = [(0, False, "plain"), (args.learned_mode, False, "learned")]
-    if args.extrapolate:
+    if extrapolate:
         runs += [(0, True, "extrap"), (args.learned_mode, True, "learned_extrap")]
         log.update({"extrap": [], "learned_extrap": []})
     for mode, extrap, key in runs:

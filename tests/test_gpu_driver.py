@@ -20,9 +20,11 @@ def test_dipole_run_plain_and_learned_converge(tmp_path):
         checkpoint = str(tmp_path / "ck.pt")
         resume = None
         out = None
+        extrapolate = True
     log = D.run(A)
-    assert len(log["phase1"]) == 5 and len(log["plain"]) == 5 and len(log["learned"]) == 5
-    assert log["plain_max_res"] <= 1e-8 and log["learned_max_res"] <= 1e-8
+    for key in ("plain", "learned", "extrap", "learned_extrap"):
+        assert len(log[key]) == 5 and log[key + "_max_res"] <= 1e-8
+    assert len(log["phase1"]) == 5
     assert os.path.exists(A.checkpoint)
 
 
