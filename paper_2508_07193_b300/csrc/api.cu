@@ -498,6 +498,7 @@ int fmp_setup(fmp_ctx** out, fmp_grid g, const double* eps_cell, double beta, co
     SETUP_CK(fmp_transform_init_mixed(c->ras));
     SETUP_CK(fmp_fused_init());
     SETUP_CK(fmp_transform_init_ozaki());
+    SETUP_CK(fmp_stencil_init());
     SETUP_CK(cudaMalloc(&c->d_bscale, sizeof(double) * boxes.size()));
     SETUP_CK(fmp_krylov_init());
     SETUP_CK(fmp_launch_eps_bar(c->d_eps_edge, c->ras.d_boxes, c->ras.n_boxes, g.nx, g.ny, g.nz, c->stream));

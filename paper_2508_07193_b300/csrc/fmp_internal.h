@@ -225,6 +225,7 @@ int fmp_column_tile_fp64(const int* max_m);   // column tile of the float64 pass
 cudaError_t fmp_launch_transform_solve_fp64(const FmpPlan& p, const double* tabs, const double* modeinv,
                                             const double* r, double* z, double* scratch, int nx, int ny, int nz,
                                             double beta, cudaStream_t s, const double* gate);
+cudaError_t fmp_stencil_init();   // kernel attributes of the operator apply
 // y = s_b * b + c_eps * eps o x + c_k * K x  (b may be null)
 cudaError_t fmp_launch_curlcurl(const double* x, const double* eps, double* y, double c_eps,
                                 double c_k, int nx, int ny, int nz, cudaStream_t s,

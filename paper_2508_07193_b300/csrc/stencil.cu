@@ -11,8 +11,10 @@
 // slot; slots beyond the grid are PEC walls and read as zero). This is
 // grad div - Laplacian on the staggered grid.
 //
-// The kernels are memory bound: one thread per cell computes the three
-// components, x-fastest so warps read 256-byte rows; neighbour reads hit L1/L2.
+// One thread per cell computes the three components, x-fastest so warps read
+// 256-byte rows; neighbour reads hit L1/L2. The operator apply evaluates K x
+// exactly in 64-bit fixed point per tile (see k_curlcurl_fx), which moves it
+// off the float64 pipe that bounded a float64 evaluation.
 #include "fmp_internal.h"
 
 #include <algorithm>
@@ -120,20 +122,17 @@ __global__ void k_eps_bar(const double* __restrict__ ee, FmpBox* boxes, Dims d) 
     }
 }
 
-// Tiled, k-marching double-curl apply, factored as K x = C^T (C x).
-// A block owns a 32 x 8 (i, j) tile and KC consecutive k-planes. The three
-// components of E at planes k and k+1 (one-cell halo in i and j, zero outside
-// the grid) sit in a shared-memory ring filled by cp.async two planes ahead.
-// Per plane the face values H = C x are formed once on the tile plus a
-// one-cell halo at the low i / j side, kept for two planes, and each output
-// takes its four faces per component:
+// Tiled double-curl apply, factored as K x = C^T (C x). A block owns a 32 x 8
+// (i, j) tile and a few consecutive k-planes; the three components of E on
+// those planes plus a one-cell halo (zero outside the grid) are copied to
+// shared memory by cp.async. Per plane the face values H = C x are formed once
+// on the tile plus a one-cell halo at the low i / j side, kept for two planes,
+// and each output takes its four faces per component:
 //   (C^T H)_x = Hz(j) - Hz(j-1) + Hy(k-1) - Hy(k)
 //   (C^T H)_y = Hx(k) - Hx(k-1) - Hz(i) + Hz(i-1)
 //   (C^T H)_z = -Hx(j) + Hx(j-1) + Hy(i) - Hy(i-1)
-// About 25 float64 operations per cell instead of 48 for the 13-point form:
-// on this part the float64 pipe, not HBM, bounds the apply.
 // y = s_b * b + c_eps * eps o x + c_k * K x  (b may be null), walls -> 0.
-constexpr int TX = 32, TY = 8, KC = 8;
+constexpr int TX = 32, TY = 8;
 constexpr int PX = TX + 2, PY = TY + 2, PLANE = 3 * PX * PY;   // E tile with halo
 constexpr int FX = TX + 1, FY = TY + 1, FPLANE = 3 * FX * FY;  // faces, low halo
 
@@ -149,92 +148,136 @@ __device__ __forceinline__ double cc_edge(double e, double xv, double kv, const 
     return bp ? fma(s_b, *bp, v) : v;
 }
 
-template <int FORM>
+// ---- the double curl in 64-bit fixed point ----------------------------------
+// K has integer coefficients, so K x is evaluated exactly in integers. The
+// tile's values (with halo, all KCN + 2 planes) are written in fixed point
+// relative to the tile's largest exponent field emax,
+//     X = trunc(x 2^(1080 - emax)),  |X| < 2^58,
+// so every value within 2^5 of the largest keeps all 53 bits and smaller ones
+// lose only the bits below 2^-58 of the largest. Faces C X and edges C^T C X
+// are integer sums, |K X| <= 16 * 2^58 = 2^62, rounded once to float64 (to
+// nearest); y = c_eps eps o x + c_k (K x) then takes two float64 operations
+// per component with the original x. The error of K x is at most
+// 16 * 2^-58 max|x_tile| plus half an ulp: below the rounding error of the
+// float64 sum of its 13 terms, at 6 float64 operations per cell instead of 31.
+__device__ __forceinline__ int hexp_d(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
+
+__device__ __forceinline__ long long to_fixed(double v, int emax) {
+    const int hi = __double2hiint(v);
+    const unsigned lo = (unsigned)__double2loint(v);
+    const int e = (hi >> 20) & 0x7ff;
+    if (e == 0) return 0;   // zero (and subnormals, below 2^-1022)
+    const unsigned long long M = ((unsigned long long)(((unsigned)hi & 0xfffffu) | 0x100000u) << 32) | lo;
+    const int sh = emax - e - 5;
+    const unsigned long long X = sh >= 0 ? (sh < 64 ? M >> sh : 0ull) : M << (-sh);
+    return hi < 0 ? -(long long)X : (long long)X;
+}
+
+// K 2^(emax - 1080) rounded to float64 (half up); NaN when the tile held Inf/NaN.
+__device__ __forceinline__ double from_fixed(long long K, int emax) {
+    if (emax >= 2047) return __longlong_as_double(0x7ff8000000000000LL);
+    const bool neg = K < 0;
+    const unsigned long long a = neg ? (unsigned long long)(-K) : (unsigned long long)K;
+    int lz = __clzll((long long)a);
+    unsigned long long mant = ((a << (lz & 63)) + 0x400ull) >> 11;
+    if (mant >> 53) { mant >>= 1; --lz; }
+    const int field = emax - lz + 6;
+    unsigned hi = (neg ? 0x80000000u : 0u) | ((unsigned)field << 20) | ((unsigned)(mant >> 32) & 0xfffffu);
+    unsigned lo = (unsigned)mant;
+    if (K == 0 || field <= 0) { hi = 0u; lo = 0u; }
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+template <int KCN>
+constexpr size_t fx_smem() { return sizeof(long long) * ((KCN + 2) * PLANE + 2 * FPLANE); }
+
+template <int FORM, int KCN>
 __global__ void __launch_bounds__(TX * TY)
-k_curlcurl(const double* __restrict__ x, const double* __restrict__ eps, double* __restrict__ y,
-           const double* __restrict__ b, double s_b, double c_eps, double c_k, Dims d,
-           const double* __restrict__ gate) {
+k_curlcurl_fx(const double* __restrict__ x, const double* __restrict__ eps, double* __restrict__ y,
+              const double* __restrict__ b, double s_b, double c_eps, double c_k, Dims d,
+              const double* __restrict__ gate) {
     if (gate && *gate != 0.0) return;
-    __shared__ __align__(16) double P[4 * PLANE];    // E planes in flight / in use
-    __shared__ double Fc[2 * FPLANE];                // faces of planes k-1 and k
-    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * KC;
+    constexpr int NPL = KCN + 2;   // E planes k0 - 1 .. k0 + KCN
+    extern __shared__ __align__(16) unsigned char smraw[];
+    long long* T = reinterpret_cast<long long*>(smraw);   // [NPL][PLANE]: doubles, then fixed point
+    long long* Fc = T + NPL * PLANE;                        // [2][FPLANE] faces (fixed point)
+    __shared__ int emax_s;
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * KCN;
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-    auto issue = [&](int slot, int k) {
-        double* dst = P + slot * PLANE;
-        for (int t = threadIdx.x; t < PLANE; t += TX * TY) {
-            const int c = t / (PX * PY), r = t - c * PX * PY;
-            const int jj = r / PX, ii = r - jj * PX;
-            const int gi = i0 + ii - 1, gj = j0 + jj - 1;
-            const bool ok = k >= 0 && k < d.nz && gi >= 0 && gi < d.nx && gj >= 0 && gj < d.ny;
-            const double* src = ok ? x + c * d.comp + k * d.plane + (long long)gj * d.nx + gi : x;
-            fmp::cp_async8(dst + t, src, ok);
-        }
-        fmp::cp_async_commit();
-    };
-    // faces of one plane from E planes (Ec = plane k, En = plane k+1); face
-    // cell (fj, fi) is (j0 - 1 + fj, i0 - 1 + fi), E index offset +1 in the tile
-    auto faces = [&](double* F, const double* Ec, const double* En) {
+    if (threadIdx.x == 0) emax_s = 0;
+    for (int t = threadIdx.x; t < NPL * PLANE; t += TX * TY) {
+        const int pl = t / PLANE, q = t - pl * PLANE;
+        const int c = q / (PX * PY), r = q - c * PX * PY;
+        const int jj = r / PX, ii = r - jj * PX;
+        const int k = k0 - 1 + pl, gi = i0 + ii - 1, gj = j0 + jj - 1;
+        const bool ok = k >= 0 && k < d.nz && gi >= 0 && gi < d.nx && gj >= 0 && gj < d.ny;
+        const double* src = ok ? x + c * d.comp + k * d.plane + (long long)gj * d.nx + gi : x;
+        fmp::cp_async8(T + t, src, ok);
+    }
+    fmp::cp_async_commit();
+    fmp::cp_async_wait<0>();
+    __syncthreads();
+    {
+        int e = 0;
+        for (int t = threadIdx.x; t < NPL * PLANE; t += TX * TY) e = max(e, hexp_d(__longlong_as_double(T[t])));
+        e = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
+        if ((threadIdx.x & 31) == 0) atomicMax(&emax_s, e);
+    }
+    __syncthreads();
+    const int emax = emax_s;
+    for (int t = threadIdx.x; t < NPL * PLANE; t += TX * TY) T[t] = to_fixed(__longlong_as_double(T[t]), emax);
+    __syncthreads();
+    // faces of one plane (integer): Ec = plane k, En = plane k + 1
+    auto faces = [&](long long* F, const long long* Ec, const long long* En) {
         for (int t = threadIdx.x; t < FX * FY; t += TX * TY) {
             const int fj = t / FX, fi = t - fj * FX;
-            const int e = fj * PX + fi;   // E(j0-1+fj, i0-1+fi) in the halo tile
-            auto Ex = [&](const double* Q, int o) { return Q[e + o]; };
-            auto Ey = [&](const double* Q, int o) { return Q[PX * PY + e + o]; };
-            auto Ez = [&](const double* Q, int o) { return Q[2 * PX * PY + e + o]; };
-            F[t] = (Ez(Ec, PX) - Ez(Ec, 0)) - (Ey(En, 0) - Ey(Ec, 0));                  // Hx
-            F[FX * FY + t] = (Ex(En, 0) - Ex(Ec, 0)) - (Ez(Ec, 1) - Ez(Ec, 0));          // Hy
-            F[2 * FX * FY + t] = (Ey(Ec, 1) - Ey(Ec, 0)) - (Ex(Ec, PX) - Ex(Ec, 0));     // Hz
+            const int e = fj * PX + fi;
+            const long long* Exc = Ec;
+            const long long* Eyc = Ec + PX * PY;
+            const long long* Ezc = Ec + 2 * PX * PY;
+            F[t] = (Ezc[e + PX] - Ezc[e]) - (En[PX * PY + e] - Eyc[e]);                 // Hx
+            F[FX * FY + t] = (En[e] - Exc[e]) - (Ezc[e + 1] - Ezc[e]);                  // Hy
+            F[2 * FX * FY + t] = (Eyc[e + 1] - Eyc[e]) - (Exc[e + PX] - Exc[e]);        // Hz
         }
     };
-    issue(0, k0 - 1);
-    issue(1, k0);
-    issue(2, k0 + 1);
-    fmp::cp_async_wait<1>();   // planes k0-1 and k0 are in
-    __syncthreads();
-    faces(Fc, P, P + PLANE);   // faces of plane k0-1 into slot 0
+    faces(Fc, T, T + PLANE);   // plane k0 - 1
     const int gi = i0 + tx, gj = j0 + ty;
     const bool live = gi < d.nx && gj < d.ny;
-    const int fo = (ty + 1) * FX + tx + 1;       // this cell's face index
-    const int eo = (ty + 1) * PX + tx + 1;       // this cell's E index
-    for (int kk = 0; kk < KC && k0 + kk < d.nz; ++kk) {
+    const int fo = (ty + 1) * FX + tx + 1;
+    for (int kk = 0; kk < KCN && k0 + kk < d.nz; ++kk) {
         const int k = k0 + kk;
-        issue((kk + 3) & 3, k + 2);   // prefetch
-        fmp::cp_async_wait<1>();      // E planes k and k+1 have landed
+        long long* Fm = Fc + (kk & 1) * FPLANE;         // faces of plane k - 1
+        long long* Fk = Fc + ((kk + 1) & 1) * FPLANE;   // faces of plane k
         __syncthreads();
-        const double* Ec = P + ((kk + 1) & 3) * PLANE;
-        const double* En = P + ((kk + 2) & 3) * PLANE;
-        double* Fm = Fc + (kk & 1) * FPLANE;         // faces of plane k-1
-        double* Fk = Fc + ((kk + 1) & 1) * FPLANE;   // faces of plane k (computed now)
-        faces(Fk, Ec, En);
+        faces(Fk, T + (kk + 1) * PLANE, T + (kk + 2) * PLANE);
         __syncthreads();
         if (live) {
             const long long o = k * d.plane + (long long)gj * d.nx + gi;
-            const double* Hxk = Fk;
-            const double* Hyk = Fk + FX * FY;
-            const double* Hzk = Fk + 2 * FX * FY;
-            const double* Hxm = Fm;
-            const double* Hym = Fm + FX * FY;
+            const long long* Hxk = Fk;
+            const long long* Hyk = Fk + FX * FY;
+            const long long* Hzk = Fk + 2 * FX * FY;
+            const long long* Hxm = Fm;
+            const long long* Hym = Fm + FX * FY;
             double vx = 0.0, vy = 0.0, vz = 0.0;
             if (gj >= 1 && k >= 1) {
-                const double kx = (Hzk[fo] - Hzk[fo - FX]) + (Hym[fo] - Hyk[fo]);
-                vx = cc_edge<FORM>(eps[o], Ec[eo], kx, b ? b + o : nullptr, s_b, c_eps, c_k);
+                const long long kx = (Hzk[fo] - Hzk[fo - FX]) + (Hym[fo] - Hyk[fo]);
+                vx = cc_edge<FORM>(eps[o], __ldg(x + o), from_fixed(kx, emax), b ? b + o : nullptr, s_b, c_eps, c_k);
             }
             if (gi >= 1 && k >= 1) {
-                const double ky = (Hxk[fo] - Hxm[fo]) - (Hzk[fo] - Hzk[fo - 1]);
-                vy = cc_edge<FORM>(eps[d.comp + o], Ec[PX * PY + eo], ky, b ? b + d.comp + o : nullptr, s_b,
-                                   c_eps, c_k);
+                const long long ky = (Hxk[fo] - Hxm[fo]) - (Hzk[fo] - Hzk[fo - 1]);
+                vy = cc_edge<FORM>(eps[d.comp + o], __ldg(x + d.comp + o), from_fixed(ky, emax),
+                                   b ? b + d.comp + o : nullptr, s_b, c_eps, c_k);
             }
             if (gi >= 1 && gj >= 1) {
-                const double kz = (Hxk[fo - FX] - Hxk[fo]) + (Hyk[fo] - Hyk[fo - 1]);
-                vz = cc_edge<FORM>(eps[2 * d.comp + o], Ec[2 * PX * PY + eo], kz, b ? b + 2 * d.comp + o : nullptr,
-                                   s_b, c_eps, c_k);
+                const long long kz = (Hxk[fo - FX] - Hxk[fo]) + (Hyk[fo] - Hyk[fo - 1]);
+                vz = cc_edge<FORM>(eps[2 * d.comp + o], __ldg(x + 2 * d.comp + o), from_fixed(kz, emax),
+                                   b ? b + 2 * d.comp + o : nullptr, s_b, c_eps, c_k);
             }
             y[o] = vx;
             y[d.comp + o] = vy;
             y[2 * d.comp + o] = vz;
         }
-        __syncthreads();
     }
-    fmp::cp_async_wait<0>();   // no copy may outlive the block
 }
 
 __global__ void __launch_bounds__(256)
@@ -335,15 +378,30 @@ cudaError_t fmp_launch_eps_bar(const double* eps_edge, FmpBox* d_boxes, int n_bo
     return cudaGetLastError();
 }
 
+constexpr int KFX = 4;   // planes per CTA of the fixed-point kernel
+
+cudaError_t fmp_stencil_init() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_curlcurl_fx<0, KFX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)fx_smem<KFX>())))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_curlcurl_fx<1, KFX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)fx_smem<KFX>())))
+        return e;
+    return cudaFuncSetAttribute(k_curlcurl_fx<2, KFX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)fx_smem<KFX>());
+}
+
 cudaError_t fmp_launch_curlcurl(const double* x, const double* eps, double* y, double c_eps, double c_k, int nx,
                                 int ny, int nz, cudaStream_t s, const double* gate, const double* b, double s_b) {
-    dim3 g((nx + TX - 1) / TX, (ny + TY - 1) / TY, (nz + KC - 1) / KC);
+    const dim3 g((nx + TX - 1) / TX, (ny + TY - 1) / TY, (nz + KFX - 1) / KFX);
+    const size_t sm = fx_smem<KFX>();
     if (c_eps == 1.0 && !b)
-        k_curlcurl<1><<<g, TX * TY, 0, s>>>(x, eps, y, b, s_b, c_eps, c_k, dims(nx, ny, nz), gate);
+        k_curlcurl_fx<1, KFX><<<g, TX * TY, sm, s>>>(x, eps, y, b, s_b, c_eps, c_k, dims(nx, ny, nz), gate);
     else if (c_eps == -1.0 && b && s_b == 1.0)
-        k_curlcurl<2><<<g, TX * TY, 0, s>>>(x, eps, y, b, s_b, c_eps, c_k, dims(nx, ny, nz), gate);
+        k_curlcurl_fx<2, KFX><<<g, TX * TY, sm, s>>>(x, eps, y, b, s_b, c_eps, c_k, dims(nx, ny, nz), gate);
     else
-        k_curlcurl<0><<<g, TX * TY, 0, s>>>(x, eps, y, b, s_b, c_eps, c_k, dims(nx, ny, nz), gate);
+        k_curlcurl_fx<0, KFX><<<g, TX * TY, sm, s>>>(x, eps, y, b, s_b, c_eps, c_k, dims(nx, ny, nz), gate);
     return cudaGetLastError();
 }
 
