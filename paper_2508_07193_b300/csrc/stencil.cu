@@ -173,7 +173,8 @@ __device__ __forceinline__ long long to_fixed(double v, int emax) {
     return hi < 0 ? -(long long)X : (long long)X;
 }
 
-// K 2^(emax - 1080) rounded to float64 (half up); NaN when the tile held Inf/NaN.
+// K 2^(emax - 1080) rounded to float64 (to nearest, ties up) with integer
+// operations; NaN when the tile held Inf/NaN.
 __device__ __forceinline__ double from_fixed(long long K, int emax) {
     if (emax >= 2047) return __longlong_as_double(0x7ff8000000000000LL);
     const bool neg = K < 0;
@@ -205,21 +206,39 @@ k_curlcurl_fx(const double* __restrict__ x, const double* __restrict__ eps, doub
     const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * KCN;
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     if (threadIdx.x == 0) emax_s = 0;
-    for (int t = threadIdx.x; t < NPL * PLANE; t += TX * TY) {
-        const int pl = t / PLANE, q = t - pl * PLANE;
-        const int c = q / (PX * PY), r = q - c * PX * PY;
-        const int jj = r / PX, ii = r - jj * PX;
-        const int k = k0 - 1 + pl, gi = i0 + ii - 1, gj = j0 + jj - 1;
-        const bool ok = k >= 0 && k < d.nz && gi >= 0 && gi < d.nx && gj >= 0 && gj < d.ny;
-        const double* src = ok ? x + c * d.comp + k * d.plane + (long long)gj * d.nx + gi : x;
-        fmp::cp_async8(T + t, src, ok);
+    {
+        // this thread's slots of a plane (the same on every plane): up to
+        // ceil(PLANE / 256) of them, offsets within the field's plane
+        constexpr int NQ = (PLANE + TX * TY - 1) / (TX * TY);
+        long long off[NQ];
+        bool in[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int t = threadIdx.x + q * TX * TY;
+            const int c = t / (PX * PY), r = t - c * PX * PY;
+            const int jj = r / PX, ii = r - jj * PX;
+            const int gi = i0 + ii - 1, gj = j0 + jj - 1;
+            in[q] = t < PLANE && gi >= 0 && gi < d.nx && gj >= 0 && gj < d.ny;
+            off[q] = c * d.comp + (long long)gj * d.nx + gi;
+        }
+        for (int pl = 0; pl < NPL; ++pl) {
+            const int k = k0 - 1 + pl;
+            const bool kin = k >= 0 && k < d.nz;
+            const double* xk = x + (long long)k * d.plane;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int t = threadIdx.x + q * TX * TY;
+                if (t < PLANE) fmp::cp_async8(T + pl * PLANE + t, kin && in[q] ? xk + off[q] : x, kin && in[q]);
+            }
+        }
     }
     fmp::cp_async_commit();
     fmp::cp_async_wait<0>();
     __syncthreads();
     {
+        const unsigned* hw = reinterpret_cast<const unsigned*>(T) + 1;   // high words
         int e = 0;
-        for (int t = threadIdx.x; t < NPL * PLANE; t += TX * TY) e = max(e, hexp_d(__longlong_as_double(T[t])));
+        for (int t = threadIdx.x; t < NPL * PLANE; t += TX * TY) e = max(e, (int)((hw[2 * t] >> 20) & 0x7ffu));
         e = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
         if ((threadIdx.x & 31) == 0) atomicMax(&emax_s, e);
     }
