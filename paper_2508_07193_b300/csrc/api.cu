@@ -556,6 +556,7 @@ void fmp_destroy(fmp_ctx* c) {
     c->compact = nullptr;
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->bicg_graph_exec) cudaGraphExecDestroy(c->bicg_graph_exec);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     for (int t = 0; t < 8; ++t)
         if (c->ev[t]) cudaEventDestroy(c->ev[t]);
@@ -567,7 +568,7 @@ int fmp_set_options(fmp_ctx* c, const fmp_options* o) {
     if (!valid_ctx(c) || !o) return FMP_ERR_ARG;
     int rc = check_options(o);
     if (rc != FMP_OK) return rc;
-    if (o->precision != c->opt.precision || o->restart != c->opt.restart) c->graph_valid = false;
+    if (o->precision != c->opt.precision || o->restart != c->opt.restart) fmp_invalidate_graphs(c);
     c->opt = *o;
     return FMP_OK;
 }
@@ -591,7 +592,7 @@ int fmp_set_tuning(fmp_ctx* c, int slab_group, int tile_group) {
     if (int rc = latched(c)) return rc;
     if (slab_group == c->ras.slab_group && tile_group == c->ras.tile_group) return FMP_OK;
     FMP_CK(regroup(c->ras, c->h_boxes, slab_group, tile_group, c->ras.fused_max, c->stream));
-    c->graph_valid = false;
+    fmp_invalidate_graphs(c);
     return FMP_OK;
 }
 
@@ -600,7 +601,7 @@ int fmp_set_fused(fmp_ctx* c, int max_extent) {
     if (int rc = latched(c)) return rc;
     if (max_extent == c->ras.fused_max) return FMP_OK;
     FMP_CK(regroup(c->ras, c->h_boxes, c->ras.slab_group, c->ras.tile_group, max_extent, c->stream));
-    c->graph_valid = false;
+    fmp_invalidate_graphs(c);
     return FMP_OK;
 }
 
@@ -616,13 +617,14 @@ int fmp_set_subdomain_form(fmp_ctx* c, int form) {
         FMP_CK(e);
         c->compact = k;
     }
-    if (form != c->subdomain_form) c->graph_valid = false;
+    if (form != c->subdomain_form) fmp_invalidate_graphs(c);
     c->subdomain_form = form;
     return FMP_OK;
 }
 
 int fmp_set_checked(fmp_ctx* c, int on) {
     if (!valid_ctx(c) || (on != 0 && on != 1)) return FMP_ERR_ARG;
+    if (on != c->checked) fmp_invalidate_graphs(c);   // the scratch canary is part of a captured apply
     c->checked = on;
     return FMP_OK;
 }
@@ -683,7 +685,7 @@ int fmp_autotune(fmp_ctx* c, int precision, int reps, int* result) {
             }
     c->opt.precision = saved;
     FMP_CK(regroup(c->ras, c->h_boxes, bs, bt, bf, c->stream));
-    c->graph_valid = false;
+    fmp_invalidate_graphs(c);
     result[0] = bs;
     result[1] = bt;
     result[2] = (int)(1000.f * best / reps);

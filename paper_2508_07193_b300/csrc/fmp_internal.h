@@ -197,6 +197,10 @@ struct fmp_ctx {
     int kry_nv = 0, kry_nz = 0;   // vectors allocated in d_V, d_Z
     bool graph_valid = false;     // restart-cycle graph matches the buffers
     cudaGraphExec_t graph_exec = nullptr;
+    int graph_gen = 0;            // bumped whenever the kernels or buffers a graph holds change
+    cudaGraphExec_t bicg_graph_exec = nullptr;   // a chunk of BiCGSTAB iterations
+    int bicg_graph_gen = -1;
+    long long bicg_graph_kernels = 0;
     cudaStream_t capture_stream = nullptr;
     long long graph_kernels = 0;  // kernel nodes in the cycle graph
     long long launches = 0;       // kernels launched by this context (graph nodes included)
@@ -292,3 +296,9 @@ cudaError_t fmp_cnn_apply_dev(fmp_ctx* c, const double* r, double* out, double a
     } while (0)
 
 int fmp_latch(fmp_ctx* c, cudaError_t e);
+
+// Every captured graph is stale after this (new kernels, tuning or buffers).
+inline void fmp_invalidate_graphs(fmp_ctx* c) {
+    c->graph_valid = false;
+    ++c->graph_gen;
+}

@@ -57,8 +57,9 @@ __host__ __device__ inline St st_layout(int R) {
 enum {
     SC_BNORM = 0, SC_EST, SC_INV, SC_HN, SC_NRM, SC_DONE, SC_REORTH, SC_JDONE, SC_STATUS, SC_RTOL,
     SC_BUDGET, SC_NREORTH,
-    // BiCGSTAB scalars
-    SC_RHO, SC_RHO_OLD, SC_ALPHA, SC_OMEGA, SC_BETA, SC_D0, SC_D1, SC_D2, SC_D3, SC_D4
+    // BiCGSTAB scalars (SC_DONE is its gate and SC_STATUS its device status too)
+    SC_RHO, SC_RHO_OLD, SC_ALPHA, SC_OMEGA, SC_BETA, SC_D0, SC_D1, SC_D2, SC_D3, SC_D4,
+    SC_BITER, SC_BFIRST, SC_BTOL2, SC_BBUDGET
 };
 // SC_STATUS codes written by the device
 enum { DS_RUN = 0, DS_CONV = 1, DS_BUDGET = 2, DS_LUCKY = 3, DS_BREAK = 4, DS_NONFINITE = 5 };
@@ -345,7 +346,8 @@ struct Pairs {
 // takes its issue slot).
 template <int N>
 __global__ void __launch_bounds__(kT)
-k_pairdots(Pairs p, size_t len, double* out, double* partials, unsigned int* ticket) {
+k_pairdots(Pairs p, size_t len, double* out, double* partials, unsigned int* ticket, const double* gate) {
+    if (gate && *gate != 0.0) return;
     double acc[N];
 #pragma unroll
     for (int k = 0; k < N; ++k) acc[k] = 0.0;
@@ -361,12 +363,12 @@ k_pairdots(Pairs p, size_t len, double* out, double* partials, unsigned int* tic
 }
 
 void launch_pairdots(const Pairs& p, size_t len, double* out, double* partials, unsigned int* ticket, int grid,
-                     cudaStream_t s) {
+                     cudaStream_t s, const double* gate = nullptr) {
     switch (p.n) {
-        case 1: k_pairdots<1><<<grid, kT, 0, s>>>(p, len, out, partials, ticket); break;
-        case 2: k_pairdots<2><<<grid, kT, 0, s>>>(p, len, out, partials, ticket); break;
-        case 3: k_pairdots<3><<<grid, kT, 0, s>>>(p, len, out, partials, ticket); break;
-        default: k_pairdots<4><<<grid, kT, 0, s>>>(p, len, out, partials, ticket); break;
+        case 1: k_pairdots<1><<<grid, kT, 0, s>>>(p, len, out, partials, ticket, gate); break;
+        case 2: k_pairdots<2><<<grid, kT, 0, s>>>(p, len, out, partials, ticket, gate); break;
+        case 3: k_pairdots<3><<<grid, kT, 0, s>>>(p, len, out, partials, ticket, gate); break;
+        default: k_pairdots<4><<<grid, kT, 0, s>>>(p, len, out, partials, ticket, gate); break;
     }
 }
 
@@ -423,45 +425,84 @@ __global__ void k_maxpy(double* __restrict__ x, const double* __restrict__ Z, si
 }
 
 // ---- BiCGSTAB kernels (van der Vorst's right-preconditioned form) -------
-// p = r + beta (p - omega v); first iteration p = r.
+// Every kernel of an iteration returns at once while the gate sc[SC_DONE] is
+// up, so chunks of iterations replay as one CUDA graph and stop on the device.
+// Each vector kernel also forms the scalar it is the first to need (every
+// thread computes it from the dot slots; block 0 records it), so no separate
+// scalar kernels run between them.
+// p = r + beta (p - omega v), beta = (rho / rho_old)(alpha / omega) with
+// rho = <rhat, r> in D0; p = r on the first iteration (SC_BFIRST).
 __global__ void k_bicg_p(double* __restrict__ p, const double* __restrict__ r, const double* __restrict__ v,
-                         size_t n, const double* sc, int first) {
-    const double beta = first ? 0.0 : sc[SC_BETA];
+                         size_t n, double* sc) {
+    if (sc[SC_DONE] != 0.0) return;
+    const bool first = sc[SC_BFIRST] != 0.0;
+    const double rho = sc[SC_D0];
     const double omega = sc[SC_OMEGA];
+    const double beta = first ? 0.0 : (rho / sc[SC_RHO_OLD]) * (sc[SC_ALPHA] / omega);
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
         p[e] = first ? r[e] : fma(beta, fma(-omega, v[e], p[e]), r[e]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) { sc[SC_RHO] = rho; sc[SC_BETA] = beta; }
 }
-// s = r - alpha v
+// s = r - alpha v, alpha = rho / <rhat, v> (D0); clears the first-iteration flag
 __global__ void k_bicg_s(double* __restrict__ s, const double* __restrict__ r, const double* __restrict__ v,
-                         size_t n, const double* sc) {
-    const double alpha = sc[SC_ALPHA];
+                         size_t n, double* sc) {
+    if (sc[SC_DONE] != 0.0) return;
+    const double alpha = sc[SC_RHO] / sc[SC_D0];
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
         s[e] = fma(-alpha, v[e], r[e]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) { sc[SC_ALPHA] = alpha; sc[SC_BFIRST] = 0.0; }
 }
-// x += alpha phat + omega shat ; r = s - omega t
-__global__ void k_bicg_xr(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ ph,
-                          const double* __restrict__ sh, const double* __restrict__ s, const double* __restrict__ t,
-                          size_t n, const double* sc) {
-    const double alpha = sc[SC_ALPHA], omega = sc[SC_OMEGA];
+// omega = <t, s> / <t, t> (D0, D1); x += alpha phat + omega shat; r = s - omega t;
+// then the next iteration's <rhat, r> and <r, r> into D0, D1 in the same pass
+// (the last block sums them, after every block has read the old D0, D1). The
+// last block also counts the iteration and raises the gate on convergence of
+// the recursive residual (<r, r> <= (rtol ||b||)^2), breakdown, a non-finite
+// value or the iteration budget, with the reason in SC_STATUS.
+__global__ void __launch_bounds__(kT)
+k_bicg_xr(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ ph,
+          const double* __restrict__ sh, const double* __restrict__ s, const double* __restrict__ t,
+          const double* __restrict__ rh, size_t n, double* sc, double* partials, unsigned int* ticket) {
+    if (sc[SC_DONE] != 0.0) return;
+    const double alpha = sc[SC_ALPHA];
+    const double omega = sc[SC_D1] != 0.0 ? sc[SC_D0] / sc[SC_D1] : 0.0;
+    double acc[2] = {0.0, 0.0};
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
         x[e] = fma(omega, sh[e], fma(alpha, ph[e], x[e]));
-        r[e] = fma(-omega, t[e], s[e]);
+        const double rn = fma(-omega, t[e], s[e]);
+        r[e] = rn;
+        acc[0] = fma(rh[e], rn, acc[0]);
+        acc[1] = fma(rn, rn, acc[1]);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) { sc[SC_OMEGA] = omega; sc[SC_RHO_OLD] = sc[SC_RHO]; }
+    if (block_partials(acc, 2, partials, ticket)) {
+        block_totals(partials, 2, sc + SC_D0);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            *ticket = 0;
+            const double it = sc[SC_BITER] + 1.0, rho = sc[SC_D0], rn2 = sc[SC_D1];
+            sc[SC_BITER] = it;
+            int status = DS_RUN;
+            if (!isfinite(rn2) || !isfinite(omega) || !isfinite(rho)) status = DS_NONFINITE;
+            else if (rn2 <= sc[SC_BTOL2]) status = DS_CONV;
+            else if (omega == 0.0 || rho == 0.0) status = DS_BREAK;
+            else if (it >= sc[SC_BBUDGET]) status = DS_BUDGET;
+            if (status != DS_RUN) { sc[SC_STATUS] = status; sc[SC_DONE] = 1.0; }
+        }
     }
 }
-// scalar updates from the dot slots D0, D1
-__global__ void k_bicg_scalars(double* sc, int which) {
+// (Re)start: rho_old = alpha = omega = 1, first iteration, gate down, the
+// squared tolerance and the iteration budget.
+__global__ void k_bicg_start(double* sc, double tol2, double budget) {
     if (threadIdx.x || blockIdx.x) return;
-    if (which == 0) {            // rho = <rhat, r> in D0: beta
-        const double rho = sc[SC_D0];
-        sc[SC_BETA] = (rho / sc[SC_RHO_OLD]) * (sc[SC_ALPHA] / sc[SC_OMEGA]);
-        sc[SC_RHO] = rho;
-    } else if (which == 1) {     // <rhat, v> in D0: alpha
-        sc[SC_ALPHA] = sc[SC_RHO] / sc[SC_D0];
-    } else {                     // <t, s> in D0, <t, t> in D1: omega
-        sc[SC_OMEGA] = sc[SC_D1] != 0.0 ? sc[SC_D0] / sc[SC_D1] : 0.0;
-        sc[SC_RHO_OLD] = sc[SC_RHO];
-    }
+    sc[SC_RHO_OLD] = sc[SC_ALPHA] = sc[SC_OMEGA] = 1.0;
+    sc[SC_BFIRST] = 1.0;
+    sc[SC_DONE] = 0.0;
+    sc[SC_STATUS] = DS_RUN;
+    sc[SC_BITER] = 0.0;
+    sc[SC_BTOL2] = tol2;
+    sc[SC_BBUDGET] = budget;
 }
+
 // z += alpha n with alpha = d[0] / d[1] (0 when d[1] is not positive).
 __global__ void k_damped_axpy(double* __restrict__ z, const double* __restrict__ nn, size_t n, const double* d,
                               const double* gate) {
@@ -471,10 +512,6 @@ __global__ void k_damped_axpy(double* __restrict__ z, const double* __restrict__
         z[e] = fma(alpha, nn[e], z[e]);
 }
 
-__global__ void k_bicg_reset(double* sc) {
-    if (threadIdx.x || blockIdx.x) return;
-    sc[SC_RHO_OLD] = sc[SC_ALPHA] = sc[SC_OMEGA] = 1.0;
-}
 
 
 // Basis passes: one instantiation per basis size 1..kMaxV, picked from a
@@ -679,13 +716,13 @@ cudaError_t fmp_krylov_init() { return cudaSuccess; }
 
 cudaError_t fmp_ensure_krylov(fmp_ctx* c) {
     const int R = c->opt.restart;
-    const int need_v = R + 1 > 8 ? R + 1 : 8;   // BiCGSTAB uses 8: r, rhat, p, v, s, t, phat, shat
+    const int need_v = R + 1 > 9 ? R + 1 : 9;   // BiCGSTAB uses 9: r, rhat, p, v, s, t, phat, shat, x
     const int need_z = c->opt.krylov == FMP_KRYLOV_BICGSTAB ? 0 : R;
     if (c->d_V && c->kry_restart == R && c->kry_nv >= need_v && c->kry_nz >= need_z) return cudaSuccess;
     cudaFree(c->d_V); cudaFree(c->d_Z); cudaFree(c->d_state);
     c->d_V = c->d_Z = c->d_state = nullptr;
     c->kry_nv = c->kry_nz = c->kry_restart = 0;
-    c->graph_valid = false;
+    fmp_invalidate_graphs(c);
     c->ld = (c->n_slots + 31) / 32 * 32;
     cudaError_t e;
     if ((e = cudaMalloc(&c->d_V, sizeof(double) * c->ld * need_v))) return e;
@@ -787,6 +824,92 @@ int fmp_fgmres(fmp_ctx* c, const double* b, double* x, fmp_solve_info* info) {
     return status;
 }
 
+namespace {
+
+constexpr int kBicgChunk = 8;   // BiCGSTAB iterations per replayed graph
+
+// One gated BiCGSTAB iteration on the context's stream (Sec. IV-A): p, phat =
+// M^-1 p, v = A phat, alpha, s, shat = M^-1 s, t = A shat, omega, x, r and the
+// next <rhat, r>, <r, r>. x is the solver's own copy (slot 8 of d_V).
+int bicg_iteration(fmp_ctx* c, fmp_solve_info* inf) {
+    const size_t n = c->n_slots, ld = c->ld;
+    cudaStream_t s = c->stream;
+    double* sc = c->d_state + st_layout(c->kry_restart).sc;
+    const double* gate = sc + SC_DONE;
+    double *r = c->d_V, *rh = r + ld, *p = rh + ld, *v = p + ld, *sv = v + ld, *t = sv + ld, *ph = t + ld,
+           *sh = ph + ld, *xi = sh + ld;
+    auto dots = [&](const double* a0, const double* b0, const double* a1 = nullptr, const double* b1 = nullptr) {
+        Pairs pr{};
+        pr.a[0] = a0; pr.b[0] = b0; pr.n = 1;
+        if (a1) { pr.a[1] = a1; pr.b[1] = b1; pr.n = 2; }
+        ++c->launches;
+        launch_pairdots(pr, n, sc + SC_D0, c->d_partials, c->d_ticket, grid_n(n), s, gate);
+    };
+    ++c->launches;
+    k_bicg_p<<<grid_n(n), kT, 0, s>>>(p, r, v, n, sc);
+    {
+        Timer tm(c, &inf->ms_precond, "precond");
+        int rc = fmp_precond_gated(c, p, ph, gate);
+        if (rc != FMP_OK) return rc;
+    }
+    {
+        Timer tm(c, &inf->ms_spmv, "matvec");
+        ++c->launches;
+        FMP_CK(fmp_launch_curlcurl(ph, c->d_eps_edge, v, 1.0, c->beta, c->nx, c->ny, c->nz, s, gate));
+    }
+    dots(rh, v);
+    ++c->launches;
+    k_bicg_s<<<grid_n(n), kT, 0, s>>>(sv, r, v, n, sc);
+    {
+        Timer tm(c, &inf->ms_precond, "precond");
+        int rc = fmp_precond_gated(c, sv, sh, gate);
+        if (rc != FMP_OK) return rc;
+    }
+    {
+        Timer tm(c, &inf->ms_spmv, "matvec");
+        ++c->launches;
+        FMP_CK(fmp_launch_curlcurl(sh, c->d_eps_edge, t, 1.0, c->beta, c->nx, c->ny, c->nz, s, gate));
+    }
+    dots(t, sv, t, t);
+    ++c->launches;
+    k_bicg_xr<<<grid_n(n), kT, 0, s>>>(xi, r, ph, sh, sv, t, rh, n, sc, c->d_partials, c->d_ticket);
+    FMP_CK(cudaGetLastError());
+    return FMP_OK;
+}
+
+// kBicgChunk gated iterations, captured into a CUDA graph on first use (or
+// after anything it holds changed) and replayed.
+int run_bicg_graph(fmp_ctx* c) {
+    if (!c->bicg_graph_exec || c->bicg_graph_gen != c->graph_gen) {
+        if (c->bicg_graph_exec) { cudaGraphExecDestroy(c->bicg_graph_exec); c->bicg_graph_exec = nullptr; }
+        cudaStream_t orig = c->stream;
+        if (!c->capture_stream) FMP_CK(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+        c->stream = c->capture_stream;
+        cudaError_t e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal);
+        if (e) { c->stream = orig; return fmp_latch(c, e); }
+        fmp_solve_info dummy{};
+        int rc = FMP_OK;
+        const long long before = c->launches;
+        for (int k = 0; k < kBicgChunk && rc == FMP_OK; ++k) rc = bicg_iteration(c, &dummy);
+        c->bicg_graph_kernels = c->launches - before;
+        c->launches = before;
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(c->capture_stream, &g);
+        c->stream = orig;
+        if (rc != FMP_OK) { if (g) cudaGraphDestroy(g); return rc; }
+        FMP_CK(e);
+        e = cudaGraphInstantiate(&c->bicg_graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        FMP_CK(e);
+        c->bicg_graph_gen = c->graph_gen;
+    }
+    FMP_CK(cudaGraphLaunch(c->bicg_graph_exec, c->stream));
+    c->launches += c->bicg_graph_kernels;
+    return FMP_OK;
+}
+
+}  // namespace
+
 int fmp_bicgstab(fmp_ctx* c, const double* b, double* x, fmp_solve_info* info) {
     fmp_solve_info inf;
     std::memset(&inf, 0, sizeof(inf));
@@ -796,22 +919,12 @@ int fmp_bicgstab(fmp_ctx* c, const double* b, double* x, fmp_solve_info* info) {
     const St L = st_layout(c->kry_restart);
     double* sc = c->d_state + L.sc;
     double* hp = c->h_pinned;
-    double *r = c->d_V, *rh = r + ld, *p = rh + ld, *v = p + ld, *sv = v + ld, *t = sv + ld, *ph = t + ld,
-           *sh = ph + ld;
+    double *r = c->d_V, *rh = r + ld, *t = rh + 4 * ld, *xi = rh + 7 * ld;
     cudaEvent_t t0 = c->ev[2], t1 = c->ev[3];
     FMP_CK(cudaEventRecord(t0, s));
     auto read_sc = [&]() -> cudaError_t {
-        cudaError_t e = cudaMemcpyAsync(hp, sc, 24 * sizeof(double), cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaMemcpyAsync(hp, sc, 32 * sizeof(double), cudaMemcpyDeviceToHost, s);
         return e ? e : cudaStreamSynchronize(s);
-    };
-    auto dots = [&](int k, const double* a0, const double* b0, const double* a1 = nullptr,
-                    const double* b1 = nullptr) -> cudaError_t {
-        Pairs pr{};
-        pr.a[0] = a0; pr.b[0] = b0; pr.n = 1;
-        if (a1) { pr.a[1] = a1; pr.b[1] = b1; pr.n = 2; }
-        ++c->launches;
-        launch_pairdots(pr, n, sc + k, c->d_partials, c->d_ticket, grid_n(n), s);
-        return cudaGetLastError();
     };
     FMP_CK(norm2(c, b, sc + SC_NRM));
     FMP_CK(read_sc());
@@ -821,77 +934,53 @@ int fmp_bicgstab(fmp_ctx* c, const double* b, double* x, fmp_solve_info* info) {
     if (bnorm == 0.0) {
         FMP_CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
     } else if (status == FMP_OK) {
-        FMP_CK(residual(c, b, x, r));
-        FMP_CK(cudaMemcpyAsync(rh, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-        ++c->launches;
-        k_bicg_reset<<<1, 1, 0, s>>>(sc);
-        FMP_CK(dots(SC_D0, rh, r, r, r));   // rho, ||r||^2
-        FMP_CK(read_sc());
-        inf.true_rel_res = std::sqrt(hp[SC_D1]) / bnorm;
-        bool first = true;
-        while (inf.true_rel_res > c->opt.rtol) {
-            if (inf.iters >= c->opt.max_iters) { status = FMP_ERR_NOT_CONVERGED; break; }
-            ++c->launches;
-            k_bicg_scalars<<<1, 1, 0, s>>>(sc, 0);
-            ++c->launches;
-            k_bicg_p<<<grid_n(n), kT, 0, s>>>(p, r, v, n, sc, first ? 1 : 0);
-            first = false;
-            {
-                Timer tm(c, &inf.ms_precond, "precond");
-                int rc = fmp_precond_gated(c, p, ph, nullptr);
-                if (rc != FMP_OK) return rc;
-            }
-            {
-                Timer tm(c, &inf.ms_spmv, "matvec");
-                ++c->launches;
-                FMP_CK(fmp_launch_curlcurl(ph, c->d_eps_edge, v, 1.0, c->beta, c->nx, c->ny, c->nz, s, nullptr));
-            }
-            FMP_CK(dots(SC_D0, rh, v));
-            ++c->launches;
-            k_bicg_scalars<<<1, 1, 0, s>>>(sc, 1);
-            ++c->launches;
-            k_bicg_s<<<grid_n(n), kT, 0, s>>>(sv, r, v, n, sc);
-            {
-                Timer tm(c, &inf.ms_precond, "precond");
-                int rc = fmp_precond_gated(c, sv, sh, nullptr);
-                if (rc != FMP_OK) return rc;
-            }
-            {
-                Timer tm(c, &inf.ms_spmv, "matvec");
-                ++c->launches;
-                FMP_CK(fmp_launch_curlcurl(sh, c->d_eps_edge, t, 1.0, c->beta, c->nx, c->ny, c->nz, s, nullptr));
-            }
-            FMP_CK(dots(SC_D0, t, sv, t, t));
-            ++c->launches;
-            k_bicg_scalars<<<1, 1, 0, s>>>(sc, 2);
-            ++c->launches;
-            k_bicg_xr<<<grid_n(n), kT, 0, s>>>(x, r, ph, sh, sv, t, n, sc);
-            FMP_CK(dots(SC_D0, rh, r, r, r));
-            FMP_CK(read_sc());
-            inf.iters++;
-            inf.est_rel_res = std::sqrt(hp[SC_D1]) / bnorm;
-            if (!std::isfinite(inf.est_rel_res) || !std::isfinite(hp[SC_OMEGA])) {
-                status = FMP_ERR_NONFINITE;
-                break;
-            }
-            if (inf.est_rel_res <= c->opt.rtol) {
-                FMP_CK(residual(c, b, x, t));
-                FMP_CK(norm2(c, t, sc + SC_NRM));
-                FMP_CK(read_sc());
-                inf.true_rel_res = std::sqrt(hp[SC_NRM]) / bnorm;
-                if (inf.true_rel_res <= c->opt.rtol) break;
-                // the recursive residual drifted from the true one: restart from it
-                FMP_CK(cudaMemcpyAsync(r, t, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        FMP_CK(cudaMemcpyAsync(xi, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        const bool graph = c->opt.use_graph && !c->opt.timing;
+        bool restart = true;
+        while (status == FMP_OK) {
+            if (restart) {   // from the true residual of xi (start, or the recursive one drifted)
+                FMP_CK(residual(c, b, xi, r));
                 FMP_CK(cudaMemcpyAsync(rh, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+                Pairs pr{};
+                pr.a[0] = rh; pr.b[0] = r; pr.a[1] = r; pr.b[1] = r; pr.n = 2;
                 ++c->launches;
-                k_bicg_reset<<<1, 1, 0, s>>>(sc);
-                FMP_CK(dots(SC_D0, rh, r, r, r));
-                first = true;
-                continue;
+                launch_pairdots(pr, n, sc + SC_D0, c->d_partials, c->d_ticket, grid_n(n), s);
+                const double tol = c->opt.rtol * bnorm;
+                ++c->launches;
+                k_bicg_start<<<1, 1, 0, s>>>(sc, tol * tol, (double)(c->opt.max_iters - inf.iters));
+                FMP_CK(cudaGetLastError());
+                FMP_CK(read_sc());
+                inf.true_rel_res = std::sqrt(hp[SC_D1]) / bnorm;
+                if (!std::isfinite(inf.true_rel_res)) { status = FMP_ERR_NONFINITE; break; }
+                if (inf.true_rel_res <= c->opt.rtol) break;
+                if (inf.iters >= c->opt.max_iters) { status = FMP_ERR_NOT_CONVERGED; break; }
+                restart = false;
             }
-            if (hp[SC_OMEGA] == 0.0 || hp[SC_D0] == 0.0) { status = FMP_ERR_BREAKDOWN; break; }
-            inf.true_rel_res = inf.est_rel_res;
+            const int done_before = (int)hp[SC_BITER];
+            if (graph) {
+                int rc = run_bicg_graph(c);
+                if (rc != FMP_OK) return rc;
+            } else {
+                int rc = bicg_iteration(c, &inf);
+                if (rc != FMP_OK) return rc;
+            }
+            FMP_CK(read_sc());
+            inf.iters += (int)hp[SC_BITER] - done_before;
+            inf.est_rel_res = std::sqrt(hp[SC_D1]) / bnorm;
+            if (hp[SC_DONE] == 0.0) continue;
+            const int ds = (int)hp[SC_STATUS];
+            if (ds == DS_NONFINITE) { status = FMP_ERR_NONFINITE; break; }
+            if (ds == DS_BREAK) { status = FMP_ERR_BREAKDOWN; break; }
+            if (ds == DS_BUDGET) { status = FMP_ERR_NOT_CONVERGED; inf.true_rel_res = inf.est_rel_res; break; }
+            // the recursive residual converged: check the true one
+            FMP_CK(residual(c, b, xi, t));
+            FMP_CK(norm2(c, t, sc + SC_NRM));
+            FMP_CK(read_sc());
+            inf.true_rel_res = std::sqrt(hp[SC_NRM]) / bnorm;
+            if (inf.true_rel_res <= c->opt.rtol) break;
+            restart = true;
         }
+        FMP_CK(cudaMemcpyAsync(x, xi, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     }
     FMP_CK(cudaEventRecord(t1, s));
     FMP_CK(cudaEventSynchronize(t1));
