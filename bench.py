@@ -504,22 +504,51 @@ def run_ours(args):
     # -- e2e: the step's input J from pinned host memory (H2D) and its result
     # E back to the host (D2H), every step; one untimed pass first so that
     # first-use costs of the copies stay out of the timed region --
+    # The copies overlap the compute the way a time-stepping caller would run
+    # them: step n+1's J uploads on a copy stream while step n solves, and
+    # step n's E, snapshotted on the device, downloads while step n+1 solves.
+    # Two buffers each; events order every reuse; all copies complete inside
+    # the timed region.
     hJ = torch.empty_like(J, device="cpu").pin_memory()
     hJ.copy_(J.cpu())
-    hE = torch.empty_like(hJ).pin_memory()
+    hE = [torch.empty_like(hJ).pin_memory() for _ in range(2)]
+    Jd = [torch.empty_like(J) for _ in range(2)]
+    Es = [torch.empty_like(E) for _ in range(2)]
+    cps = torch.cuda.Stream(device=dev)
+    ev = lambda: torch.cuda.Event()
+    up, used, snap, down = [ev(), ev()], [ev(), ev()], [ev(), ev()], [ev(), ev()]
 
-    def e2e_step():
-        J.copy_(hJ, non_blocking=True)
-        E.zero_(); H.zero_()
-        ctx.cn_step(E, H, J, dt)
-        hE.copy_(E, non_blocking=True)
+    def e2e_run(k):
+        with torch.cuda.stream(cps):
+            Jd[0].copy_(hJ, non_blocking=True)
+            up[0].record(cps)
+        for n in range(k):
+            b = n % 2
+            if n + 1 < k:   # upload the next step's input once step n-1 no longer reads that buffer
+                with torch.cuda.stream(cps):
+                    if n >= 1:
+                        cps.wait_event(used[1 - b])
+                    Jd[1 - b].copy_(hJ, non_blocking=True)
+                    up[1 - b].record(cps)
+            stream.wait_event(up[b])
+            if n >= 2:
+                stream.wait_event(down[b])   # Es[b] free again
+            E.zero_(); H.zero_()
+            ctx.cn_step(E, H, Jd[b], dt)
+            used[b].record(stream)
+            Es[b].copy_(E)
+            snap[b].record(stream)
+            with torch.cuda.stream(cps):
+                cps.wait_event(snap[b])
+                hE[b].copy_(Es[b], non_blocking=True)
+                down[b].record(cps)
+        stream.wait_stream(cps)
 
-    e2e_step()
+    e2e_run(2)
     torch.cuda.synchronize()
     e0.record(stream)
-    n_e = max(1, min(3, args.steps))
-    for _ in range(n_e):
-        e2e_step()
+    n_e = max(2, min(4, args.steps))
+    e2e_run(n_e)
     e1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = max_over_ranks(e0.elapsed_time(e1) / n_e, world, dev)
@@ -552,7 +581,9 @@ def run_ours(args):
         "roofline": roof,
         "roofline_spmv": roof_spmv,
         "e2e": {"value": job_value(dof, world, ms_e2e), "unit": "DoF/s", "h2d_bytes_per_step": J.numel() * 8,
-                "d2h_bytes_per_step": E.numel() * 8, "ms_per_step": ms_e2e},
+                "d2h_bytes_per_step": E.numel() * 8, "ms_per_step": ms_e2e,
+                "copies": "pinned host J in and E out every step, on a copy stream overlapping the neighbouring "
+                          "steps' compute (double buffers), all complete inside the timed region"},
         "gpu_launches": launches,
         "form_setup_s": setup_s,
         "tuning": list(tuning) if tuning else list(ctx.get_tuning()),
