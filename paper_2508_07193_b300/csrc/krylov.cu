@@ -38,7 +38,7 @@ constexpr double kReorthRatio = 0.05;
 
 // ---- device state (doubles) ---------------------------------------------
 struct St {
-    int R, H, cs, sn, g, h1, h2, y, sc, total;
+    int R, H, cs, sn, g, h1, h2, y, sv, sc, total;
 };
 __host__ __device__ inline St st_layout(int R) {
     St s;
@@ -50,7 +50,8 @@ __host__ __device__ inline St st_layout(int R) {
     s.h1 = s.g + R + 1;           // R+2 (last slot: ||w||^2)
     s.h2 = s.h1 + R + 2;          // R+2
     s.y = s.h2 + R + 2;           // R
-    s.sc = s.y + R;
+    s.sv = s.y + R;               // R+1: basis vector j is stored unnormalised, v_j = sv[j] V[j]
+    s.sc = s.sv + R + 1;
     s.total = s.sc + 32;
     return s;
 }
@@ -224,6 +225,8 @@ k_dots(const double* __restrict__ V, size_t ld, const double* __restrict__ w, si
     if (block_publish(tot, NV + 1, partials, ticket)) {
         block_totals(partials, NV + 1, st + out_off);
         __syncthreads();
+        // <v_i, w> = sv[i] <V_i, w> for the unnormalised stored vectors
+        if (threadIdx.x < NV) st[out_off + threadIdx.x] *= st[L.sv + threadIdx.x];
         if (threadIdx.x == 0) *ticket = 0;
     }
 }
@@ -283,7 +286,7 @@ k_update(const double* __restrict__ V, size_t ld, double* __restrict__ w, size_t
     const double* h = st + (mode == 0 ? L.h1 : L.h2);
     double hr[NV];
 #pragma unroll
-    for (int g = 0; g < NV; ++g) hr[g] = -h[g];
+    for (int g = 0; g < NV; ++g) hr[g] = -h[g] * st[L.sv + g];   // w -= h_i v_i = h_i sv_i V_i
     double acc[1] = {0.0};
     constexpr int U = basis_unroll(NV);
     for (size_t e0 = (size_t)blockIdx.x * kT * U + threadIdx.x; e0 < n; e0 += (size_t)gridDim.x * kT * U) {
@@ -313,6 +316,7 @@ k_update(const double* __restrict__ V, size_t ld, double* __restrict__ w, size_t
                 if (nrm >= kReorthRatio * wn || !isfinite(nrm)) {
                     st[L.sc + SC_REORTH] = 0.0;
                     arnoldi_finish(st, L, j, st + L.h1, nrm);
+                    st[L.sv + j + 1] = st[L.sc + SC_INV];   // V[j+1] = w, unnormalised
                 } else {
                     st[L.sc + SC_REORTH] = 1.0;
                     st[L.sc + SC_NREORTH] += 1.0;
@@ -322,19 +326,12 @@ k_update(const double* __restrict__ V, size_t ld, double* __restrict__ w, size_t
                 for (int i = 0; i <= j; ++i) hsum[i] = st[L.h1 + i] + st[L.h2 + i];
                 st[L.sc + SC_REORTH] = 0.0;
                 arnoldi_finish(st, L, j, hsum, nrm);
+                st[L.sv + j + 1] = st[L.sc + SC_INV];
             }
         }
     }
 }
 
-// v_{j+1} = w / h_{j+1,j}; skipped for a step that did not run.
-__global__ void k_scale_next(double* __restrict__ w, size_t n, const double* st, int R, int j) {
-    const St L = st_layout(R);
-    if ((int)st[L.sc + SC_JDONE] != j + 1) return;
-    const double a = st[L.sc + SC_INV];
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
-        w[e] *= a;
-}
 
 // Dots of up to four vector pairs: out[k] = <a_k, b_k>.
 struct Pairs {
@@ -379,6 +376,7 @@ __global__ void k_cycle_init(double* st, int R, double rtol, int budget) {
     for (int i = 0; i <= R; ++i) st[L.g + i] = 0.0;
     st[L.g] = nr;
     st[L.sc + SC_INV] = nr > 0.0 ? 1.0 / nr : 0.0;
+    st[L.sv] = st[L.sc + SC_INV];   // V[0] = r0 unnormalised
     st[L.sc + SC_DONE] = 0.0;
     st[L.sc + SC_REORTH] = 0.0;
     st[L.sc + SC_STATUS] = DS_RUN;
@@ -388,12 +386,6 @@ __global__ void k_cycle_init(double* st, int R, double rtol, int budget) {
 }
 
 // v_0 = r / ||r|| in place
-__global__ void k_scale_first(double* __restrict__ w, size_t n, const double* st, int R) {
-    const St L = st_layout(R);
-    const double a = st[L.sc + SC_INV];
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
-        w[e] *= a;
-}
 
 // y = H(0:J,0:J)^{-1} g(0:J), J = jdone, by back substitution.
 __global__ void k_trisolve(double* st, int R) {
@@ -671,9 +663,7 @@ int arnoldi_step(fmp_ctx* c, int j, fmp_solve_info* inf) {
         FMP_CK(launch_dots(V, ld, nv, w, n, st, R, L.h2, 1, c, s));
         ++c->launches;
         FMP_CK(launch_update(V, ld, nv, w, n, st, R, j, 1, c, s));
-        ++c->launches;
-        k_scale_next<<<grid_n(n), kT, 0, s>>>(w, n, st, R, j);
-        FMP_CK(cudaGetLastError());
+        // no scaling pass: V[j+1] = w stays unnormalised, with sv[j+1] = 1 / h(j+1, j)
     }
     return FMP_OK;
 }
@@ -781,8 +771,6 @@ int fmp_fgmres(fmp_ctx* c, const double* b, double* x, fmp_solve_info* info) {
         const int budget = c->opt.max_iters - inf.iters;
         ++c->launches;
         k_cycle_init<<<1, 1, 0, s>>>(st, R, c->opt.rtol, budget);
-        ++c->launches;
-        k_scale_first<<<grid_n(n), kT, 0, s>>>(V, n, st, R);
         FMP_CK(cudaGetLastError());
         if (c->opt.use_graph && !c->opt.timing && c->opt.use_learned < 2) {
             int rc = run_cycle_graph(c);
