@@ -3,33 +3,36 @@
 // products of 8-bit digit planes (Ozaki et al.'s error-free splitting of a
 // matrix product), the closed-form 3x3 inverse per mode (Eq. 12) in float64.
 //
-// Splitting. A transform contracts lines x of K <= 40 values. Each line is
-// written in 48-bit fixed point relative to its largest binary exponent emax
-// (the biased float64 exponent field):
-//     X_k = round(x_k 2^(1069 - emax)),  |X_k| <= 2^47,
+// Splitting. A transform contracts lines x of K <= 80 values. Each line is
+// written in fixed point relative to its largest binary exponent emax (the
+// biased float64 exponent field):
+//     X_k = trunc(x_k 2^(1069 - emax)),  |X_k| < 2^47,
 // and X is cut into six balanced base-256 digits d_0 (most significant) ..
 // d_5, integers in [-128, 128], exact in bf16. Every table T of extent m
 // (|T| <= 2^F) gets the same treatment once on the host,
 //     Y = round(T 2^(47 - F)).
 // Digit planes p of the data and q of the table meet at weight
 // 256^(10 - p - q). The 21 plane pairs with p + q <= 5 are summed per class
-// g = p + q by mma.sync into six fp32 accumulators; with K <= 40 every partial
-// sum is an integer of magnitude below 6 * 40 * 2^14 < 2^22, so the tensor-core
+// g = p + q by mma.sync into six fp32 accumulators. Every partial sum is an
+// integer of magnitude below 6 * 32 * 2^14 < 2^22 (lines longer than 40 move
+// their classes into 64-bit partials every two k-steps), so the tensor-core
 // accumulation is exact. The classes are combined in 64-bit integer
-// arithmetic, Z = sum_g acc_g 256^(5 - g), and Z 2^(emax + F - 1076) is rounded
-// once to float64. The dropped classes and the two input roundings bound the
-// error of one axis transform by about K 2^-46 of the line's largest value.
-// Apart from the 3x3, no float64 instruction is executed: float64 values are
-// taken apart and assembled with integer operations.
+// arithmetic, Z = sum_g acc_g 256^(5 - g), and Z 2^(emax + F - 1076) is
+// truncated once to float64, or handed as an integer to the next axis
+// transform of the same pass. The dropped classes and the input truncations
+// bound the error of one axis transform by about K 2^-46 of the line's largest
+// value. Apart from the 3x3, no float64 instruction is executed: float64 values
+// are taken apart and assembled with integer operations.
 //
-// Same three passes and work lists as the reduced-precision path (gather +
-// forward x/y per z-slab; forward z, 3x3 and inverse z per column tile;
-// inverse y/x per owned z-slab), with the intermediate field in float64.
-// Lines are the MMA rows (A operand, digit planes cut into shared memory),
-// table modes the columns (B operand: the tables' digit planes are stored in
-// mma fragment order and read straight from the L1/L2-resident table, one
-// 16-byte load per lane and plane pair, so shared memory holds only the
-// field and its digits and three CTAs fit per SM).
+// Same three passes as the reduced-precision path (gather + forward x/y per
+// z-slab; forward z, 3x3 and inverse z per column tile; inverse y/x per owned
+// z-slab), with the intermediate field in float64, on work lists of their own
+// (two z-slabs or one 16-column tile per CTA). Lines are the MMA rows (A
+// operand, digit planes cut into shared memory), table modes the columns (B
+// operand: the tables' digit planes are stored in mma fragment order and read
+// straight from the L1/L2-resident table, one 16-byte load per lane and plane
+// pair, so shared memory holds only the field and its digits). Two size
+// classes: extents <= 40 (three CTAs per SM) and <= 80.
 #include "fmp_internal.h"
 
 #include <cuda_bf16.h>
