@@ -44,6 +44,11 @@ TRAFFIC_BYTES = {
 }
 
 
+# one network evaluation, per voxel: 2 x 27 taps x C_in x C_out for the layers
+# 4 -> 16, 16 -> 16, 16 -> 16, 16 -> 3
+CNN_FLOPS_PER_VOXEL = 2 * 27 * (4 * 16 + 16 * 16 + 16 * 16 + 16 * 3)
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -60,9 +65,12 @@ def parse():
     p.add_argument("--form", default="yee", choices=["yee", "compact"],
                    help="subdomain form: Yee boxes with PEC walls, or the compact layout with the Woodbury "
                         "boundary correction (float64 only)")
-    p.add_argument("--case", default="step", choices=["step", "precond", "spmv"],
-                   help="precond/spmv: only W + K applies of that operator (for profiler captures)")
+    p.add_argument("--case", default="step", choices=["step", "precond", "spmv", "cnn"],
+                   help="precond/spmv/cnn: only W + K applies of that operator (for profiler captures), "
+                        "the K timed with CUDA events")
     p.add_argument("--workload", default="grid128", choices=["grid128", "grid256", "uneven"])
+    p.add_argument("--cnn-mma-sync", action="store_true",
+                   help="--case cnn: the mma.sync convolution kernels instead of tcgen05")
     return p.parse_args()
 
 
@@ -671,6 +679,7 @@ def cpu_baseline(w, iters_gpu, n_boxes_sample=8):
 
 def run_case(args):
     """W + K applies of one operator on a workload, for profiler captures."""
+    import numpy as np
     import torch
 
     from paper_2508_07193_b300 import flashmp as F
@@ -682,11 +691,27 @@ def run_case(args):
         ctx.set_subdomain_form(args.form)
     r = torch.as_tensor(w.rhs, device="cuda")
     z = ctx.empty_field()
-    op = ctx.precond_apply if args.case == "precond" else ctx.curlcurl_apply
-    for _ in range(args.warmup + args.steps):
+    op = {"precond": ctx.precond_apply, "spmv": ctx.curlcurl_apply, "cnn": ctx.cnn_apply}[args.case]
+    if args.case == "cnn":
+        ctx.cnn_set_params(np.random.default_rng(0).normal(0.0, 0.05, ctx.cnn_num_params()).astype(np.float32))
+        ctx.cnn_set_tc(not args.cnn_mma_sync)
+    for _ in range(args.warmup):
         op(r, z)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    print(json.dumps({"case": args.case, "workload": w.name, "applies": args.warmup + args.steps}))
+    e0.record(ctx.stream)
+    for _ in range(args.steps):
+        op(r, z)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    out = {"case": args.case, "workload": w.name, "applies": args.warmup + args.steps, "ms_per_apply": ms}
+    if args.case == "cnn":
+        nx, ny, nz = w.grid
+        flops = CNN_FLOPS_PER_VOXEL * nx * ny * nz
+        out.update({"tflops": flops / (ms * 1e-3) / 1e12, "flops_per_apply": flops,
+                    "kernels": "mma.sync" if args.cnn_mma_sync else "tcgen05 (16-channel layers)"})
+    print(json.dumps(out))
     ctx.close()
 
 

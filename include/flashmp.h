@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define FMP_ABI_VERSION 4
+#define FMP_ABI_VERSION 5
 
 typedef struct fmp_ctx fmp_ctx; /* opaque, library-owned */
 
@@ -305,8 +305,17 @@ int fmp_cnn_set_params(fmp_ctx* ctx, const float* params);
 int fmp_cnn_get_params(fmp_ctx* ctx, float* params);
 
 /* out = N(r) over the full grid (DEVICE edge fields, no aliasing; wall slots
- * of out are 0). */
+ * of out are 0). Synchronises the context's stream. The 16-channel layers
+ * run on the tcgen05 tensor cores (bf16 operands, fp32 accumulation) unless
+ * fmp_cnn_set_tc(ctx, 0) selects the mma.sync kernels that training uses;
+ * both give the same network up to the fp32 summation order. FMP_ERR_CUDA
+ * without a latched context: a tcgen05 convolution timed out waiting for its
+ * copies (the output is then undefined). */
 int fmp_cnn_apply(fmp_ctx* ctx, const double* r, double* out);
+
+/* on = 1 (default) or 0: the convolution kernels of fmp_cnn_apply and of the
+ * learned guess / correction of fmp_cn_step and fmp_krylov_solve. */
+int fmp_cnn_set_tc(fmp_ctx* ctx, int on);
 
 /* Append one training pair to the device pool: input r (a residual) and
  * target correction e (DEVICE edge fields), stored normalised by s = rms(r). */

@@ -235,7 +235,11 @@ int check_face(fmp_ctx* c, const double* x) { return check_walls(c, x, 1, c->nx,
 
 int krylov_dispatch(fmp_ctx* c, const double* b, double* x, fmp_solve_info* info) {
     if (c->opt.krylov == FMP_KRYLOV_BICGSTAB) return fmp_bicgstab(c, b, x, info);
-    return fmp_fgmres(c, b, x, info);
+    const int rc = fmp_fgmres(c, b, x, info);
+    // the in-FGMRES learned correction: report a convolution that gave up
+    if (c->opt.use_learned >= 2 && (rc == FMP_OK || rc == FMP_ERR_NOT_CONVERGED))
+        if (int rk = fmp_cnn_check(c)) return rk;
+    return rc;
 }
 
 bool dt_matches(double beta, double dt) {
@@ -836,6 +840,7 @@ int fmp_cn_step_guess(fmp_ctx* c, double* E, double* H, const double* J, double 
                                    nullptr, R, 1.0));
         const double n1 = fmp_norm(c, c->d_tmp3, &err);
         FMP_CK(err);
+        if (int rc = fmp_cnn_check(c)) return rc;
         if (!(n1 < n0)) {   // includes NaN: revert to the plain guess
             FMP_CK(cudaMemcpyAsync(E, Eold, sizeof(double) * c->n_slots, cudaMemcpyDeviceToDevice, c->stream));
             fallback = 1;

@@ -54,7 +54,8 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
 // Y[co] = act(b[co] + sum_{ci, tap} Wk[co][tap][ci] X[ci](v + d(tap))), zero
 // padding. Wk: bf16 [NP][KP] (k = tap * CINP + ci, zero beyond 27 taps / CIN).
 // X: bf16 [CIN][vol]. Y: OutT [COUT][vol]. bias may be null.
-template <int CIN, int COUT, bool RELU, class OutT>
+// CL: Y channel-last [vol][COUT] instead.
+template <int CIN, int COUT, bool RELU, class OutT, bool CL = false>
 __global__ void __launch_bounds__(kT)
 k_conv_fwd(const bf16* __restrict__ X, const bf16* __restrict__ Wk, const float* __restrict__ bias,
            OutT* __restrict__ Y, Vol v) {
@@ -120,7 +121,8 @@ k_conv_fwd(const bf16* __restrict__ X, const bf16* __restrict__ Wk, const float*
             if (co < COUT && gx < v.W && gy < v.H) {
                 float val = acc[j][e] + (bias ? bias[co] : 0.f);
                 if (RELU) val = fmaxf(val, 0.f);
-                const long long o = co * v.n() + z * v.plane() + (long long)gy * v.W + gx;
+                const long long vox = z * v.plane() + (long long)gy * v.W + gx;
+                const long long o = CL ? vox * COUT + co : co * v.n() + vox;
                 if constexpr (sizeof(OutT) == 2)
                     Y[o] = __float2bfloat16(val);
                 else
@@ -352,6 +354,10 @@ struct FmpCnn {
     int adam_t = 0;
     bf16* wk[4] = {};          // forward weights [NP][KP] per layer
     bf16* wt[4] = {};          // input-gradient weights (swapped, flipped) per layer
+    bf16* wtc[4] = {};         // layers 1-3 as the tcgen05 B operand (cnn_tc.cu)
+    int* tc_err = nullptr;     // set by a tcgen05 convolution that gave up waiting
+    int use_tc = 1;            // full-volume applies on tcgen05 (else the mma.sync kernels)
+    int nsm = 0;
     long long cap = 0;         // voxels the activation buffers hold
     bf16* x0 = nullptr;        // [4][vol]
     bf16* a[3] = {};           // [16][vol]
@@ -426,6 +432,8 @@ __global__ void k_pack(const float* __restrict__ w, bf16* __restrict__ f, bf16* 
 
 cudaError_t pack_weights(FmpCnn* n, cudaStream_t s) {
     for (int l = 0; l < 4; ++l) k_pack<<<1, 1024, 0, s>>>(n->w + layer_off(l), n->wk[l], n->wt[l], kCin[l], kCout[l]);
+    for (int l = 1; l < 4; ++l)
+        if (cudaError_t e = fmp_conv_tc_pack(n->w + layer_off(l), kCout[l], n->wtc[l], s)) return e;
     return cudaGetLastError();
 }
 
@@ -438,6 +446,24 @@ cudaError_t net_forward(FmpCnn* n, const Vol& v, cudaStream_t s) {
     k_conv_fwd<16, 16, true, bf16><<<g, kT, 0, s>>>(n->a[1], n->wk[2], bias_of(n, 2), n->a[2], v);
     k_conv_fwd<16, 3, false, float><<<g, kT, 0, s>>>(n->a[2], n->wk[3], bias_of(n, 3), n->out, v);
     return cudaGetLastError();
+}
+
+// The same network on a full volume with the 16-channel layers on tcgen05:
+// layer 0 (4 -> 16, mma.sync) writes channel-last activations, layers 1-2
+// read and write them through TMA, layer 3 writes the fp32 output. The
+// activation buffers a[0], a[1] hold channel-last data here.
+cudaError_t net_forward_tc(FmpCnn* n, const Vol& v, cudaStream_t s) {
+    const int D = v.D, H = v.H, W = v.W;
+    FmpTmap m0, m1;
+    cudaError_t e;
+    if ((e = fmp_conv_tc_map(&m0, n->a[0], D, H, W))) return e;
+    if ((e = fmp_conv_tc_map(&m1, n->a[1], D, H, W))) return e;
+    k_conv_fwd<4, 16, true, bf16, true><<<conv_grid(v), kT, 0, s>>>(n->x0, n->wk[0], bias_of(n, 0), n->a[0], v);
+    if ((e = fmp_conv_tc_launch(m0, n->wtc[1], bias_of(n, 1), n->a[1], 16, true, false, D, H, W, n->nsm, n->tc_err, s)))
+        return e;
+    if ((e = fmp_conv_tc_launch(m1, n->wtc[2], bias_of(n, 2), n->a[0], 16, true, false, D, H, W, n->nsm, n->tc_err, s)))
+        return e;
+    return fmp_conv_tc_launch(m0, n->wtc[3], bias_of(n, 3), n->out, 3, false, true, D, H, W, n->nsm, n->tc_err, s);
 }
 
 template <int CIN, int COUT>
@@ -525,6 +551,14 @@ cudaError_t fmp_cnn_create(fmp_ctx* c) {
         if ((e = cudaMalloc(&n->wk[l], sizeof(bf16) * f))) return e;
         if ((e = cudaMalloc(&n->wt[l], sizeof(bf16) * b))) return e;
     }
+    for (int l = 1; l < 4; ++l)
+        if ((e = cudaMalloc(&n->wtc[l], sizeof(bf16) * fmp_conv_tc_weight_elems()))) return e;
+    if ((e = cudaMalloc(&n->tc_err, sizeof(int)))) return e;
+    if ((e = cudaMemsetAsync(n->tc_err, 0, sizeof(int), c->stream))) return e;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev))) return e;
+    if ((e = cudaDeviceGetAttribute(&n->nsm, cudaDevAttrMultiProcessorCount, dev))) return e;
+    if ((e = fmp_conv_tc_init())) return e;
     if ((e = cudaMalloc(&n->wtmp, sizeof(float) * (16 * 27 * 16 + 16)))) return e;
     if ((e = cudaMalloc(&n->scal, sizeof(double) * (8 + kRmsBlocks)))) return e;
     if ((e = cudaMalloc(&n->bbox, sizeof(int) * 8))) return e;
@@ -546,7 +580,8 @@ void fmp_cnn_free(fmp_ctx* c) {
     FmpCnn* n = c->cnn;
     if (!n) return;
     cudaFree(n->w); cudaFree(n->g); cudaFree(n->m); cudaFree(n->v2);
-    for (int l = 0; l < 4; ++l) { cudaFree(n->wk[l]); cudaFree(n->wt[l]); }
+    for (int l = 0; l < 4; ++l) { cudaFree(n->wk[l]); cudaFree(n->wt[l]); cudaFree(n->wtc[l]); }
+    cudaFree(n->tc_err);
     cudaFree(n->x0); for (auto& p : n->a) cudaFree(p); cudaFree(n->out);
     cudaFree(n->gf[0]); cudaFree(n->gf[1]); cudaFree(n->gbf); cudaFree(n->tgt);
     cudaFree(n->part); cudaFree(n->wtmp); cudaFree(n->scal); cudaFree(n->bbox);
@@ -566,10 +601,23 @@ cudaError_t fmp_cnn_apply_dev(fmp_ctx* c, const double* r, double* out, double a
     k_rms_part<<<kRmsBlocks, 256, 0, c->stream>>>(r, (long long)c->n_slots, n->scal + 8);
     k_rms_final<<<1, 32, 0, c->stream>>>(n->scal + 8, kRmsBlocks, (long long)c->n_slots, n->scal);
     k_cnn_input<<<grid1(v.n()), 256, 0, c->stream>>>(r, c->d_eps_cell, n->scal, n->x0, c->nx, c->ny, c->nz, 0, 0, 0, v);
-    if ((e = net_forward(n, v, c->stream))) return e;
+    if ((e = n->use_tc ? net_forward_tc(n, v, c->stream) : net_forward(n, v, c->stream))) return e;
     k_cnn_output<<<grid1(3 * v.n()), 256, 0, c->stream>>>(n->out, n->scal, out, c->nx, c->ny, c->nz, alpha, accumulate);
     c->launches += 8;
     return cudaGetLastError();
+}
+
+int fmp_cnn_check(fmp_ctx* c) {
+    FmpCnn* n = c->cnn;
+    if (!n || !n->use_tc) return FMP_OK;
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, n->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return fmp_latch(c, e);
+    if (!h) return FMP_OK;
+    // the kernel gave up and returned cleanly: report, keep the context usable
+    if ((e = cudaMemsetAsync(n->tc_err, 0, sizeof(int), c->stream))) return fmp_latch(c, e);
+    return FMP_ERR_CUDA;
 }
 
 #define CNN_CK(x) do { cudaError_t _e = (x); if (_e != cudaSuccess) return fmp_latch(c, _e); } while (0)
@@ -605,6 +653,14 @@ int fmp_cnn_apply(fmp_ctx* c, const double* r, double* out) {
     if (c->latched) return FMP_ERR_CUDA;
     CNN_CK(fmp_cnn_create(c));
     CNN_CK(fmp_cnn_apply_dev(c, r, out, 1.0, 0));
+    return fmp_cnn_check(c);
+}
+
+int fmp_cnn_set_tc(fmp_ctx* c, int on) {
+    if (!c || (on != 0 && on != 1)) return FMP_ERR_ARG;
+    if (c->latched) return FMP_ERR_CUDA;
+    CNN_CK(fmp_cnn_create(c));
+    c->cnn->use_tc = on;
     return FMP_OK;
 }
 

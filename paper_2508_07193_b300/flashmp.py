@@ -104,6 +104,7 @@ def lib():
         "fmp_cnn_set_params": (_I, [_P, _P]),
         "fmp_cnn_get_params": (_I, [_P, _P]),
         "fmp_cnn_apply": (_I, [_P, _P, _P]),
+        "fmp_cnn_set_tc": (_I, [_P, _I]),
         "fmp_cnn_add_sample": (_I, [_P, _P, _P]),
         "fmp_cnn_num_samples": (_I, [_P, C.POINTER(_I)]),
         "fmp_cnn_clear_samples": (_I, [_P]),
@@ -408,6 +409,10 @@ class Context:
         out = self.empty_field() if out is None else _field(out, self.shape, "out")
         _check(lib().fmp_cnn_apply(self._h, _ptr(r), _ptr(out)), "fmp_cnn_apply")
         return out
+
+    def cnn_set_tc(self, on=True):
+        """Full-volume convolutions on tcgen05 (True, default) or mma.sync."""
+        _check(lib().fmp_cnn_set_tc(self._h, 1 if on else 0), "fmp_cnn_set_tc")
 
     def cnn_add_sample(self, r, e):
         _field(r, self.shape, "r"); _field(e, self.shape, "e")

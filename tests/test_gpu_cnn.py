@@ -114,3 +114,78 @@ def test_learned_cn_steps_solve_to_tolerance(mode):
         E, H = cn.step(g, ee, E, H, J, dt)
         assert info["used_fallback"] in (0, 1)
     assert rel(host(Ed), E) <= 1e-8 and rel(host(Hd), H) <= 1e-8
+
+
+def _oracle_out(params, w, r, s):
+    """The oracle network on the whole volume, rescaled, walls zeroed."""
+    eps = np.ones(w.grid[::-1]) if w.eps_cell is None else w.eps_cell
+    y, _ = cnn.forward(params, np.concatenate([r / s, eps[None] * 0.1]))
+    y = y * s
+    y[wl.edge_wall_mask(w.grid)] = 0.0
+    return y
+
+
+@pytest.mark.parametrize("grid,xcuts", [((20, 18, 14), (20,)), ((131, 19, 7), (44, 44, 43)),
+                                        ((129, 9, 3), (43, 43, 43)), ((5, 3, 2), (5,))],
+                         ids=["small", "two-x-tiles-ragged", "x-tail-one", "tiny"])
+def test_cnn_apply_tcgen05_matches_oracle(grid, xcuts):
+    """The full-volume apply (16-channel layers on tcgen05, TMA zero fill as
+    the convolution's padding) on volumes with ragged x tiles (128 voxels),
+    ragged y tiles (8 rows) and short z-columns."""
+    w = wl.make_workload("cnn", grid, seed=sum(grid), n_eps_boxes=3, cuts=(xcuts, (grid[1],), (grid[2],)),
+                         overlap=1 if len(xcuts) > 1 else 0)
+    ctx = context(w)
+    f, params = seeded_params()
+    ctx.cnn_set_params(f)
+    out = host(ctx.cnn_apply(dev(w.rhs)))
+    s = np.sqrt(np.mean(w.rhs ** 2))
+    ref = _oracle_out(params, w, w.rhs, s)
+    assert rel(out, ref) <= 3e-2
+    assert np.all(out[wl.edge_wall_mask(w.grid)] == 0.0)
+
+
+def test_cnn_apply_tcgen05_agrees_with_mma_sync():
+    """tcgen05 and mma.sync evaluate the same bf16 network; they differ only in
+    the fp32 summation order (and the bf16 roundings that flips)."""
+    w = wl.small(grid=(140, 21, 9), cuts=((70, 70), (21,), (9,)), overlap=1, seed=31, n_eps_boxes=4)
+    ctx = context(w)
+    f, _ = seeded_params()
+    ctx.cnn_set_params(f)
+    a = host(ctx.cnn_apply(dev(w.rhs)))
+    ctx.cnn_set_tc(False)
+    b = host(ctx.cnn_apply(dev(w.rhs)))
+    ctx.cnn_set_tc(True)
+    c = host(ctx.cnn_apply(dev(w.rhs)))
+    assert np.array_equal(a, c)   # deterministic
+    assert rel(a, b) <= 1e-2
+
+
+def test_cnn_apply_128_sampled_voxels_match_oracle():
+    """The 128^3 workload: sampled output voxels, each against the oracle
+    network on the 9^3 neighbourhood that determines it (clipped at the
+    volume, where the padding is the volume's own)."""
+    w = wl.grid128()
+    ctx = context(w)
+    f, params = seeded_params()
+    ctx.cnn_set_params(f)
+    out = host(ctx.cnn_apply(dev(w.rhs)))
+    s = np.sqrt(np.mean(w.rhs ** 2))
+    eps = w.eps_cell
+    nx, ny, nz = w.grid
+    rng = np.random.default_rng(11)
+    pts = [(0, 0, 0), (nz - 1, ny - 1, nx - 1), (0, 64, 127), (127, 7, 8), (64, 8, 0), (3, 127, 126)]
+    pts += [tuple(int(v) for v in rng.integers(0, 128, 3)) for _ in range(10)]
+    got, want = [], []
+    for k, j, i in pts:
+        lo = [max(0, k - 4), max(0, j - 4), max(0, i - 4)]
+        hi = [min(nz, k + 5), min(ny, j + 5), min(nx, i + 5)]
+        sl = tuple(slice(a, b) for a, b in zip(lo, hi))
+        x = np.concatenate([w.rhs[(slice(None),) + sl] / s, eps[sl][None] * 0.1])
+        y, _ = cnn.forward(params, x)
+        want.append(y[:, k - lo[0], j - lo[1], i - lo[2]] * s)
+        got.append(out[:, k, j, i])
+    want = np.array(want)
+    mask = wl.edge_wall_mask(w.grid)
+    for q, (k, j, i) in enumerate(pts):
+        want[q][mask[:, k, j, i]] = 0.0
+    assert rel(np.array(got), want) <= 3e-2
