@@ -4,25 +4,37 @@
 // ring. Used by the full-volume network evaluation for the 16 -> 16 and
 // 16 -> 3 layers (about 90 % of its flops).
 //
-// Implicit GEMM, one output z-plane at a time: D[voxel][co] = sum over the 27
-// taps of A_tap[voxel][ci] B_tap[ci][co], M = 128 voxels along x, N = 16
-// output channels, K = 16 input channels per tap (one MMA per tap and M-tile).
-// Activations are channel-last bf16 [z][y][x][16] (32 bytes per voxel), so a
-// TMA box of 8 channels x 130 x x 10 y x 1 z lands in shared memory as rows of
-// 16 bytes, voxel after voxel: exactly the K-major core-matrix layout the
-// tensor core reads (8 voxels x 16 bytes per core matrix; the two 8-channel
-// halves are two boxes, the K step between them the leading byte offset).
-// Each tap's A operand is then only a shifted start address into the plane
-// tile ((dy, dx) shift by rows of 130 voxels and by single voxels), and the
-// zero padding of the convolution is the TMA's zero fill outside the volume.
+// Implicit GEMM. Activations are channel-last bf16 [z][y][x][16] (32 bytes per
+// voxel), so a TMA box of 8 channels x 130 x x 6 y x 1 z lands in shared
+// memory as rows of 16 bytes, voxel after voxel: the K-major core-matrix
+// layout the tensor core reads (8 voxels x 16 bytes per core matrix; the two
+// 8-channel halves are two boxes, the K step between them the leading byte
+// offset). The zero padding of the convolution is the TMA's zero fill outside
+// the volume.
 //
-// A persistent CTA (256 threads, one per SM) walks work items of 128 x 8
-// voxels x lz planes: a ring of four input planes (z - 1, z, z + 1 read by the
-// MMAs of plane z while z + 2 loads), 8 M-tiles x 27 taps of MMAs issued by
-// one thread into one of two tensor-memory buffers, and the epilogue of plane
-// z - 1 (tcgen05.ld, bias, ReLU, bf16 channel-last or fp32 channel-major
-// store) overlapping the MMAs of plane z. Every wait is bounded: on time-out
-// the kernel sets *err, drains what it issued and frees its tensor memory.
+// The MMAs run over INPUT planes. Input plane p feeds output planes p + 1,
+// p and p - 1 through the taps dz = 0, 1, 2, so for each in-plane tap (dy, dx)
+// and each row of 128 voxels one MMA with M = 128 voxels, K = 16 input
+// channels and N = 48 = three output planes x 16 channels accumulates into
+// three adjacent 16-column blocks of tensor memory: output plane o sits at
+// column 16 (z1 - 1 - o) of its row's block, so the three blocks an input
+// plane touches are always contiguous, in the order of dz. The A operand of
+// a tap is a shifted start address into the plane tile (dy by rows of 130
+// voxels, dx by single voxels); the B operand is the (dy, dx) slice of the
+// weights with its three dz blocks stacked along N. Per input plane and row:
+// 9 MMAs (10 where the first contribution to an output plane has to reset its
+// accumulator), against 27 per output plane with one tap per MMA, and a third
+// of the shared-memory operand traffic.
+//
+// A persistent CTA (256 threads, one per SM) walks work items of 128 x 4
+// voxels x 4 planes. One thread issues the MMAs; all threads stream the
+// finished output planes out of tensor memory (tcgen05.ld, bias, ReLU, bf16
+// channel-last or fp32 channel-major store). The input planes of successive
+// items form one stream through a ring of four stages (three loads in
+// flight), and the items alternate between two tensor-memory buffers, so the
+// output planes of one item drain while the next item's MMAs run. Every wait
+// is bounded: on time-out the kernel sets *err, drains what it issued and
+// frees its tensor memory.
 #include "fmp_internal.h"
 
 #include <cuda.h>
@@ -36,16 +48,23 @@ namespace {
 using bf16 = __nv_bfloat16;
 
 constexpr int kM = 128;                    // voxels per MMA tile (x)
-constexpr int kR = 8;                      // rows (y) per work item = M-tiles per plane
+constexpr int kR = 4;                      // rows (y) per work item = MMA tiles per plane
+constexpr int kLz = 4;                     // output planes per work item
 constexpr int kHX = kM + 2, kHY = kR + 2;  // plane tile with its halo
-constexpr int kBox = kHY * kHX * 16;       // bytes of one 8-channel box (20,800)
+constexpr int kBox = kHY * kHX * 16;       // bytes of one 8-channel box (12,480)
 constexpr int kHalf = (kBox + 127) / 128 * 128;
 constexpr int kStage = 2 * kHalf;          // one input plane, both channel halves
 constexpr int kNS = 4;                     // ring of input planes
 constexpr int kWB = 27 * 512;              // weights: per tap 16 x 16 bf16 in core-matrix order
-constexpr int kCols = 2 * kR * 16;         // two plane accumulators
+constexpr int kRowCols = kLz * 16;         // tensor-memory columns of one row of an item
+constexpr int kBufCols = kR * kRowCols;    // one item
+constexpr int kCols = 2 * kBufCols;        // two items
+static_assert(kCols == 512, "tensor memory allocation");
 constexpr int kThreads = 256;
-constexpr size_t kSmem = 128 + (size_t)kNS * kStage + kWB + 8 * (kNS + 2) + 16;
+constexpr size_t kSmemUse = 128 + (size_t)kNS * kStage + kWB + 8 * (kNS + 2) + 16;
+// more than half of the SM's shared memory: one CTA per SM, which the full
+// tensor-memory allocation needs
+constexpr size_t kSmem = kSmemUse > 120 * 1024 ? kSmemUse : 120 * 1024;
 static_assert(kSmem <= 227 * 1024, "shared memory");
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -77,20 +96,19 @@ __device__ __forceinline__ void tma_4d(void* dst, const CUtensorMap* map, int c0
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(sa(b))
         : "memory");
 }
-// Shared-memory matrix descriptor, no swizzle: start, leading (K) and stride
-// (M/N, 8-row groups) byte offsets, descriptor version 1.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo & 0x3FFFF) >> 4) << 16) |
-           ((uint64_t)((sbo & 0x3FFFF) >> 4) << 32) | (1ull << 46);
-}
 // kind::f16 instruction descriptor: f32 accumulator, bf16 A and B, both
-// K-major, N = 16, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
-
-__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
-    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-                 "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+// K-major, M = 128, N = 16 n16 (n16 = 1, 2, 3).
+__device__ __forceinline__ uint32_t idesc(int n16) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(2 * n16) << 17) | ((128u >> 4) << 24);
+}
+// One MMA. The descriptors are passed as their 32-bit halves: the low half
+// (start address and leading byte offset) varies per MMA, the high half
+// (stride byte offset, version) is fixed.
+__device__ __forceinline__ void mma(uint32_t d, uint32_t alo, uint32_t ahi, uint32_t blo, uint32_t bhi, uint32_t id,
+                                    uint32_t acc) {
+    asm volatile("{\n .reg .pred p;\n .reg .b64 ad, bd;\n setp.ne.b32 p, %6, 0;\n mov.b64 ad, {%1, %2};\n"
+                 " mov.b64 bd, {%3, %4};\n tcgen05.mma.cta_group::1.kind::f16 [%0], ad, bd, %5, p;\n}\n" ::"r"(d),
+                 "r"(alo), "r"(ahi), "r"(blo), "r"(bhi), "r"(id), "r"(acc)
                  : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* b) {
@@ -107,8 +125,51 @@ __device__ __forceinline__ void ld16(uint32_t taddr, uint32_t (&r)[16]) {
 }
 
 struct Items {
-    int nxt, nyt, lz, n;   // x tiles, y tiles, planes per item, items
+    int nxt, nyt, n;   // x tiles, y tiles, items (z-chunks of kLz planes outermost)
 };
+
+// One work item: 128 x kR voxels from (x0, y0), output planes [z0, z1),
+// input planes [pf, pl].
+struct Geo {
+    int x0, y0, z0, z1, pf, pl;
+};
+__device__ __forceinline__ Geo geo(const Items& it, int item, int D) {
+    int rr = item;
+    const int xt = rr % it.nxt;
+    rr /= it.nxt;
+    const int yt = rr % it.nyt;
+    Geo g;
+    g.x0 = xt * kM;
+    g.y0 = yt * kR;
+    g.z0 = (rr / it.nyt) * kLz;
+    g.z1 = min(D, g.z0 + kLz);
+    g.pf = max(g.z0 - 1, 0);
+    g.pl = min(g.z1, D - 1);
+    return g;
+}
+
+// Position in the stream of (item, input plane) steps of one CTA.
+struct Cursor {
+    int item, ord, p;   // item index, its ordinal in this CTA (tensor-memory buffer ord & 1), input plane
+    Geo g;
+};
+__device__ __forceinline__ Cursor first_step(const Items& it, int D) {
+    Cursor c;
+    c.item = blockIdx.x;
+    c.ord = 0;
+    c.g = geo(it, c.item < it.n ? c.item : 0, D);
+    c.p = c.g.pf;
+    return c;
+}
+__device__ __forceinline__ void next_step(Cursor& c, const Items& it, int D) {
+    if (++c.p <= c.g.pl) return;
+    c.item += gridDim.x;
+    ++c.ord;
+    if (c.item < it.n) {
+        c.g = geo(it, c.item, D);
+        c.p = c.g.pf;
+    }
+}
 
 // OUT_F32: fp32 channel-major [cout][vol] output (the last layer); else bf16
 // channel-last [vol][16].
@@ -120,15 +181,15 @@ k_conv16_tc(const __grid_constant__ CUtensorMap tmap, const bf16* __restrict__ w
     unsigned char* sm = raw + ((128u - (sa(raw) & 127u)) & 127u);
     unsigned char* stages = sm;
     unsigned char* wsm = sm + kNS * kStage;
-    uint64_t* full = reinterpret_cast<uint64_t*>(wsm + kWB);   // [kNS] input planes landed
-    uint64_t* done = full + kNS;                                 // [2] MMAs of a buffer complete
+    uint64_t* full = reinterpret_cast<uint64_t*>(wsm + kWB);   // [kNS] input plane landed
+    uint64_t* done = full + kNS;                                 // [2] MMAs of a step complete (step parity)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 2);
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
 
     for (int i = t; i < kWB / 16; i += kThreads)
         reinterpret_cast<uint4*>(wsm)[i] = __ldg(reinterpret_cast<const uint4*>(wtc) + i);
     if (t == 0) {
-        for (int s = 0; s < kNS; ++s) mbar_init(full + s, 1);
+        for (int q = 0; q < kNS; ++q) mbar_init(full + q, 1);
         mbar_init(done, 1);
         mbar_init(done + 1, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -147,25 +208,31 @@ k_conv16_tc(const __grid_constant__ CUtensorMap tmap, const bf16* __restrict__ w
     float bv[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) bv[c] = c < cout ? __ldg(bias + c) : 0.f;
-    const uint32_t wbase = sa(wsm), sbase = sa(stages);
     const long long nvol = (long long)D * H * W;
-    unsigned fph = 0, dph = 0;   // phase bits: per stage (bit s), per accumulator buffer (bit b)
-    unsigned fpend = 0, dpend = 0;   // loads / commits issued and not yet waited
-    bool bad = false;
+    // descriptor halves: A (K step = one channel half), B (K step 128 B, 8-row groups 256 B)
+    const uint32_t a_lo0 = ((sa(stages) & 0x3FFFFu) >> 4) | ((uint32_t)(kHalf >> 4) << 16);
+    const uint32_t a_hi = (128u >> 4) | (1u << 14);
+    const uint32_t b_lo0 = ((sa(wsm) & 0x3FFFFu) >> 4) | ((128u >> 4) << 16);
+    const uint32_t b_hi = (256u >> 4) | (1u << 14);
 
-    // 16 accumulators of voxel x0 + 32 (warp & 3) + lane, M-tile ty, to memory
-    auto store = [&](int b, int x0, int y0, int z) {
-        const int x = x0 + 32 * (warp & 3) + lane;
-        uint32_t r[4][16];
+    // output plane o of the item g (tensor-memory buffer buf) to memory: 16
+    // channels of voxel x0 + 32 (warp & 3) + lane on rows 2 (warp >> 2) + q
+    auto drain = [&](const Geo& g, int buf, int o) {
+        const int x = g.x0 + 32 * (warp & 3) + lane;
+        uint32_t r[2][16];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(b * kR * 16 + ((warp >> 2) * 4 + q) * 16), r[q]);
+        for (int q = 0; q < 2; ++q) {
+            const int ty = 2 * (warp >> 2) + q;
+            ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) +
+                     (uint32_t)(buf * kBufCols + ty * kRowCols + 16 * (g.z1 - 1 - o)),
+                 r[q]);
+        }
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int y = y0 + (warp >> 2) * 4 + q;
+        for (int q = 0; q < 2; ++q) {
+            const int y = g.y0 + 2 * (warp >> 2) + q;
             if (x >= W || y >= H) continue;
-            const long long v = ((long long)z * H + y) * W + x;
+            const long long v = ((long long)o * H + y) * W + x;
             float f[16];
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
@@ -173,118 +240,132 @@ k_conv16_tc(const __grid_constant__ CUtensorMap tmap, const bf16* __restrict__ w
                 if (RELU) f[c] = fmaxf(f[c], 0.f);
             }
             if constexpr (OUT_F32) {
-                float* o = static_cast<float*>(out);
+                float* op = static_cast<float*>(out);
 #pragma unroll
                 for (int c = 0; c < 16; ++c)
-                    if (c < cout) o[c * nvol + v] = f[c];
+                    if (c < cout) op[c * nvol + v] = f[c];
             } else {
-                uint4 p[2];
-                uint32_t* pw = reinterpret_cast<uint32_t*>(p);
+                uint4 pk[2];
+                uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     const __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * c], f[2 * c + 1]);
                     pw[c] = *reinterpret_cast<const uint32_t*>(&h);
                 }
-                uint4* o = reinterpret_cast<uint4*>(static_cast<bf16*>(out) + v * 16);
-                o[0] = p[0];
-                o[1] = p[1];
+                uint4* dst = reinterpret_cast<uint4*>(static_cast<bf16*>(out) + v * 16);
+                dst[0] = pk[0];
+                dst[1] = pk[1];
             }
         }
     };
-
-    for (int item = blockIdx.x; item < it.n && !bad; item += gridDim.x) {
-        int rr = item;
-        const int xt = rr % it.nxt;
-        rr /= it.nxt;
-        const int yt = rr % it.nyt;
-        const int z0 = (rr / it.nyt) * it.lz;
-        const int z1 = min(D, z0 + it.lz);
-        const int x0 = xt * kM, y0 = yt * kR;
-        auto stage = [&](int p) { return (p - z0 + 1) & (kNS - 1); };   // planes z0 - 1 ..
-        auto load = [&](int p) {   // thread 0; plane p in [0, D)
-            const int s = stage(p);
-            unsigned char* dst = stages + s * kStage;
-            mbar_expect(full + s, 2 * kBox);
-            tma_4d(dst, &tmap, 0, x0 - 1, y0 - 1, p, full + s);
-            tma_4d(dst + kHalf, &tmap, 8, x0 - 1, y0 - 1, p, full + s);
-        };
-        auto need = [&](int p) { return p >= 0 && p < D && p <= z1; };
-        auto wait_plane = [&](int p) {
-            if (!need(p)) return;
-            const int s = stage(p);
-            if (!mbar_wait(full + s, (fph >> s) & 1u)) bad = true;
-            fph ^= 1u << s;
-            fpend &= ~(1u << s);
-        };
-        for (int p = z0 - 1; p <= z0 + 2; ++p)
-            if (need(p)) {
-                if (t == 0) load(p);
-                fpend |= 1u << stage(p);
-            }
-        wait_plane(z0 - 1);
-        wait_plane(z0);
-        for (int z = z0; z < z1; ++z) {
-            const int j = z - z0, b = j & 1;
-            wait_plane(z + 1);
-            if (__syncthreads_or(bad)) { bad = true; break; }
-            if (t == 0) {
-                tc_after();
-                for (int ty = 0; ty < kR; ++ty) {
-                    uint32_t acc = 0;
-                    const uint32_t d = tmem + (uint32_t)(b * kR * 16 + ty * 16);
-                    for (int dz = 0; dz < 3; ++dz) {
-                        const int p = z - 1 + dz;
-                        if (p < 0 || p >= D) continue;
-                        const uint32_t pl = sbase + stage(p) * kStage;
-                        for (int dy = 0; dy < 3; ++dy)
-                            for (int dx = 0; dx < 3; ++dx) {
-                                const int tap = (dz * 3 + dy) * 3 + dx;
-                                const uint64_t ad = sdesc(pl + ((ty + dy) * kHX + dx) * 16, kHalf, 128);
-                                const uint64_t bd = sdesc(wbase + tap * 512, 128, 256);
-                                mma(d, ad, bd, acc);
-                                acc = 1;
-                            }
+    // the MMAs of one step: input plane c.p (ring stage s) into the item's buffer
+    auto issue = [&](const Cursor& c, int s) {
+        const Geo& g = c.g;
+        const int p = c.p;
+        const int hi = min(p + 1, g.z1 - 1), lo = max(p - 1, g.z0);   // output planes fed, hi first
+        const int a0 = max(lo, p == 0 ? 0 : p + 1);                    // from a0 up: first contribution
+        const uint32_t dcol = tmem + (uint32_t)((c.ord & 1) * kBufCols + 16 * (g.z1 - 1 - hi));
+        const uint32_t abase = a_lo0 + (uint32_t)((s * kStage) >> 4);
+        const uint32_t bbase = b_lo0 + (uint32_t)(((p + 1 - hi) * 512) >> 4);
+        const uint32_t id_all = idesc(hi - lo + 1);
+#pragma unroll 1
+        for (int ty = 0; ty < kR; ++ty) {
+            const uint32_t d = dcol + (uint32_t)(ty * kRowCols);
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx) {
+                    const uint32_t al = abase + (uint32_t)((((ty + dy) * kHX + dx) * 16) >> 4);
+                    const uint32_t bl = bbase + (uint32_t)(((dy * 3 + dx) * 1536) >> 4);
+                    if (dy == 0 && dx == 0 && a0 <= hi) {
+                        // planes [a0, hi] start here (reset), [lo, a0) accumulate
+                        mma(d, al, a_hi, bl, b_hi, idesc(hi - a0 + 1), 0u);
+                        if (lo < a0)
+                            mma(d + (uint32_t)(16 * (hi - a0 + 1)), al, a_hi,
+                                bl + (uint32_t)(((hi - a0 + 1) * 512) >> 4), b_hi, idesc(a0 - lo), 1u);
+                    } else {
+                        mma(d, al, a_hi, bl, b_hi, id_all, 1u);
                     }
                 }
-                mma_commit(done + b);
-            }
-            dpend |= 1u << b;
-            if (j > 0) {
-                // the MMAs of plane z - 1 are done: its accumulators are
-                // final and plane z - 2's stage is free for plane z + 2
-                if (!mbar_wait(done + (b ^ 1), (dph >> (b ^ 1)) & 1u)) bad = true;
-                dph ^= 1u << (b ^ 1);
-                dpend &= ~(1u << (b ^ 1));
-                if (__syncthreads_or(bad)) { bad = true; break; }
-                tc_after();
-                if (need(z + 2)) {
-                    if (t == 0) load(z + 2);
-                    fpend |= 1u << stage(z + 2);
-                }
-                store(b ^ 1, x0, y0, z - 1);
-            }
-            tc_before();
-            __syncthreads();
         }
-        if (bad) break;
-        // the last plane's accumulators
-        const int bl = (z1 - 1 - z0) & 1;
-        if (!mbar_wait(done + bl, (dph >> bl) & 1u)) bad = true;
-        dph ^= 1u << bl;
-        dpend &= ~(1u << bl);
+    };
+
+    unsigned fph = 0, dph = 0;       // phase bits: per stage (bit s), per step parity (bit b)
+    unsigned fpend = 0, dpend = 0;   // loads / commits issued and not yet waited
+    bool bad = false;
+    auto load = [&](const Cursor& c, int s) {   // thread 0
+        unsigned char* dst = stages + s * kStage;
+        mbar_expect(full + s, 2 * kBox);
+        tma_4d(dst, &tmap, 0, c.g.x0 - 1, c.g.y0 - 1, c.p, full + s);
+        tma_4d(dst + kHalf, &tmap, 8, c.g.x0 - 1, c.g.y0 - 1, c.p, full + s);
+    };
+    Cursor prod = first_step(it, D), cons = prod, prev = prod;
+    long long kl = 0;   // loads issued (all threads track it)
+    for (; kl < kNS - 1 && prod.item < it.n; ++kl) {
+        if (t == 0) load(prod, (int)(kl % kNS));
+        fpend |= 1u << (kl % kNS);
+        next_step(prod, it, D);
+    }
+    long long k = 0;   // steps consumed
+    int next_o = 0;    // next output plane of prev's item to drain
+    while (cons.item < it.n) {
+        const int s = (int)(k % kNS);
+        if (!mbar_wait(full + s, (fph >> s) & 1u)) bad = true;
+        fph ^= 1u << s;
+        fpend &= ~(1u << s);
         if (__syncthreads_or(bad)) { bad = true; break; }
         tc_after();
-        store(bl, x0, y0, z1 - 1);
+        if (t == 0) {
+            issue(cons, s);
+            mma_commit(done + (k & 1));
+        }
+        dpend |= 1u << (k & 1);
+        if (k > 0) {
+            const int pb = (int)((k - 1) & 1);
+            if (!mbar_wait(done + pb, (dph >> pb) & 1u)) bad = true;
+            dph ^= 1u << pb;
+            dpend &= ~(1u << pb);
+            if (__syncthreads_or(bad)) { bad = true; break; }
+            tc_after();
+            // the step before is complete: its stage takes the next load
+            if (prod.item < it.n) {
+                if (t == 0) load(prod, (int)(kl % kNS));
+                fpend |= 1u << (kl % kNS);
+                ++kl;
+                next_step(prod, it, D);
+            }
+            // output planes of prev's item final after its step: below its
+            // input plane, or all of them after the item's last step
+            const int bound = prev.p == prev.g.pl ? prev.g.z1 - 1 : prev.p - 1;
+            for (; next_o <= bound; ++next_o) drain(prev.g, prev.ord & 1, next_o);
+            if (prev.item != cons.item) next_o = cons.g.z0;
+        } else {
+            next_o = cons.g.z0;
+        }
         tc_before();
-        __syncthreads();
+        prev = cons;
+        next_step(cons, it, D);
+        ++k;
+    }
+    if (!bad && k > 0) {
+        const int pb = (int)((k - 1) & 1);
+        if (!mbar_wait(done + pb, (dph >> pb) & 1u)) bad = true;
+        dph ^= 1u << pb;
+        dpend &= ~(1u << pb);
+        if (!__syncthreads_or(bad)) {
+            tc_after();
+            for (; next_o <= prev.g.z1 - 1; ++next_o) drain(prev.g, prev.ord & 1, next_o);
+        } else {
+            bad = true;
+        }
     }
     if (bad) {
         if (t == 0) atomicExch(err, 1);
         // drain what this CTA issued before freeing its tensor memory
-        for (int s = 0; s < kNS; ++s)
-            if (fpend >> s & 1u) mbar_wait(full + s, (fph >> s) & 1u);
-        for (int b = 0; b < 2; ++b)
-            if (dpend >> b & 1u) mbar_wait(done + b, (dph >> b) & 1u);
+        for (int q = 0; q < kNS; ++q)
+            if (fpend >> q & 1u) mbar_wait(full + q, (fph >> q) & 1u);
+        for (int q = 0; q < 2; ++q)
+            if (dpend >> q & 1u) mbar_wait(done + q, (dph >> q) & 1u);
     }
     tc_before();
     __syncthreads();
@@ -293,15 +374,19 @@ k_conv16_tc(const __grid_constant__ CUtensorMap tmap, const bf16* __restrict__ w
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
 }
 
-// Weights of one layer (float master W[co][16][27]) as the tensor-core B
-// operand: per tap, core matrix (co group g, ci half h) at byte
-// tap * 512 + g * 256 + h * 128, row co % 8, column ci % 8; co >= cout zero.
+// Weights of one layer (float master W[co][16][27], tap = (dz 3 + dy) 3 + dx)
+// as the tensor-core B operand: per in-plane tap (dy, dx) a 48 x 16 matrix,
+// its rows the output channels of dz = 0, 1, 2 in turn; core matrix (co
+// group g, ci half h) of block dz at byte ((dy 3 + dx) 3 + dz) 512 + g 256 +
+// h 128, row co % 8, column ci % 8; co >= cout zero.
 __global__ void k_pack_tc(const float* __restrict__ w, int cout, bf16* __restrict__ out) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;   // element of [27][2][2][8][8]
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;   // element of [9][3][2][2][8][8]
     if (e >= 27 * 256) return;
-    const int tap = e / 256, r = e % 256;
+    const int blk = e / 256, r = e % 256;
+    const int dydx = blk / 3, dz = blk % 3;
     const int g = r / 128, h = (r / 64) % 2, row = (r / 8) % 8, col = r % 8;
     const int co = g * 8 + row, ci = h * 8 + col;
+    const int tap = dz * 9 + dydx;
     out[e] = __float2bfloat16(co < cout ? w[((size_t)co * 16 + ci) * 27 + tap] : 0.f);
 }
 
@@ -318,24 +403,11 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
     return fn;
 }
 
-Items make_items(int D, int H, int W, int nsm) {
+Items make_items(int D, int H, int W) {
     Items it;
     it.nxt = (W + kM - 1) / kM;
     it.nyt = (H + kR - 1) / kR;
-    const int cols = it.nxt * it.nyt;
-    // planes per item: the longest (least halo re-reading) that still leaves
-    // the last wave of the persistent grid at least 90 % full
-    it.lz = 2;
-    for (int lz : {16, 8, 4}) {
-        const long long n = (long long)cols * ((D + lz - 1) / lz);
-        const long long waves = (n + nsm - 1) / nsm;
-        if (n >= nsm && (double)n / (double)(waves * nsm) >= 0.9) {
-            it.lz = lz;
-            break;
-        }
-    }
-    it.lz = std::min(it.lz, D);
-    it.n = cols * ((D + it.lz - 1) / it.lz);
+    it.n = it.nxt * it.nyt * ((D + kLz - 1) / kLz);
     return it;
 }
 
@@ -371,7 +443,7 @@ cudaError_t fmp_conv_tc_map(FmpTmap* map, const __nv_bfloat16* act, int D, int H
 
 cudaError_t fmp_conv_tc_launch(const FmpTmap& map, const __nv_bfloat16* wtc, const float* bias, void* out, int cout,
                                bool relu, bool out_f32, int D, int H, int W, int nsm, int* err, cudaStream_t s) {
-    const Items it = make_items(D, H, W, nsm);
+    const Items it = make_items(D, H, W);
     const int grid = std::min(it.n, nsm);
     const CUtensorMap& tm = *reinterpret_cast<const CUtensorMap*>(map.b);
     if (relu && !out_f32)
