@@ -54,7 +54,8 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
 // Y[co] = act(b[co] + sum_{ci, tap} Wk[co][tap][ci] X[ci](v + d(tap))), zero
 // padding. Wk: bf16 [NP][KP] (k = tap * CINP + ci, zero beyond 27 taps / CIN).
 // X: bf16 [CIN][vol]. Y: OutT [COUT][vol]. bias may be null.
-// CL: Y channel-last [vol][COUT] instead.
+// CL: Y in two channel-last halves [COUT / 8][vol][8] instead (the layout
+// of the tcgen05 convolutions' inputs).
 template <int CIN, int COUT, bool RELU, class OutT, bool CL = false>
 __global__ void __launch_bounds__(kT)
 k_conv_fwd(const bf16* __restrict__ X, const bf16* __restrict__ Wk, const float* __restrict__ bias,
@@ -122,7 +123,7 @@ k_conv_fwd(const bf16* __restrict__ X, const bf16* __restrict__ Wk, const float*
                 float val = acc[j][e] + (bias ? bias[co] : 0.f);
                 if (RELU) val = fmaxf(val, 0.f);
                 const long long vox = z * v.plane() + (long long)gy * v.W + gx;
-                const long long o = CL ? vox * COUT + co : co * v.n() + vox;
+                const long long o = CL ? ((co >> 3) * v.n() + vox) * 8 + (co & 7) : co * v.n() + vox;
                 if constexpr (sizeof(OutT) == 2)
                     Y[o] = __float2bfloat16(val);
                 else
@@ -449,9 +450,9 @@ cudaError_t net_forward(FmpCnn* n, const Vol& v, cudaStream_t s) {
 }
 
 // The same network on a full volume with the 16-channel layers on tcgen05:
-// layer 0 (4 -> 16, mma.sync) writes channel-last activations, layers 1-2
-// read and write them through TMA, layer 3 writes the fp32 output. The
-// activation buffers a[0], a[1] hold channel-last data here.
+// layer 0 (4 -> 16, mma.sync) writes split channel-last activations
+// [2][vol][8], layers 1-2 read and write them through TMA, layer 3 writes the
+// fp32 output. The activation buffers a[0], a[1] hold that layout here.
 cudaError_t net_forward_tc(FmpCnn* n, const Vol& v, cudaStream_t s) {
     const int D = v.D, H = v.H, W = v.W;
     FmpTmap m0, m1;

@@ -4,13 +4,14 @@
 // ring. Used by the full-volume network evaluation for the 16 -> 16 and
 // 16 -> 3 layers (about 90 % of its flops).
 //
-// Implicit GEMM. Activations are channel-last bf16 [z][y][x][16] (32 bytes per
-// voxel), so a TMA box of 8 channels x 130 x x 6 y x 1 z lands in shared
-// memory as rows of 16 bytes, voxel after voxel: the K-major core-matrix
-// layout the tensor core reads (8 voxels x 16 bytes per core matrix; the two
-// 8-channel halves are two boxes, the K step between them the leading byte
-// offset). The zero padding of the convolution is the TMA's zero fill outside
-// the volume.
+// Implicit GEMM. Activations are bf16 in two channel-last halves,
+// [2][z][y][x][8] (16 contiguous bytes per voxel and half), so a TMA box of
+// 8 channels x 130 x x 6 y x 1 z is one contiguous run per row in memory and
+// lands in shared memory as rows of 16 bytes, voxel after voxel: the K-major
+// core-matrix layout the tensor core reads (8 voxels x 16 bytes per core
+// matrix; the two halves are two boxes, the K step between them the leading
+// byte offset). The zero padding of the convolution is the TMA's zero fill
+// outside the volume.
 //
 // The MMAs run over INPUT planes. Input plane p feeds output planes p + 1,
 // p and p - 1 through the taps dz = 0, 1, 2, so for each in-plane tap (dy, dx)
@@ -26,15 +27,19 @@
 // accumulator), against 27 per output plane with one tap per MMA, and a third
 // of the shared-memory operand traffic.
 //
-// A persistent CTA (256 threads, one per SM) walks work items of 128 x 4
-// voxels x 4 planes. One thread issues the MMAs; all threads stream the
-// finished output planes out of tensor memory (tcgen05.ld, bias, ReLU, bf16
-// channel-last or fp32 channel-major store). The input planes of successive
-// items form one stream through a ring of four stages (three loads in
-// flight), and the items alternate between two tensor-memory buffers, so the
-// output planes of one item drain while the next item's MMAs run. Every wait
-// is bounded: on time-out the kernel sets *err, drains what it issued and
-// frees its tensor memory.
+// A persistent CTA (one per SM) walks work items of 128 x 4 voxels x 4
+// planes with specialised warps. One thread of warp 0 streams the input planes
+// of successive items through a ring of four stages (TMA); it and one thread
+// of each of warps 9-11 issue the MMAs, one row each (a single thread cannot
+// issue these small MMAs as fast as the tensor pipe runs them), and each
+// step's completion is committed to an mbarrier that waits for all four. Warps 1-8, two per
+// tensor-memory lane quarter, drain each output plane as soon as its last
+// input plane's MMAs complete (tcgen05.ld, bias, ReLU, bf16 or fp32 store).
+// Items alternate between two tensor-memory buffers, so one item drains while
+// the next one's MMAs run, and a stage is refilled two steps after its MMAs
+// were issued, so the issuing thread never waits for the tensor pipe it
+// feeds. Every wait is bounded: on time-out the kernel sets *err, lets what it
+// issued finish and frees its tensor memory.
 #include "fmp_internal.h"
 
 #include <cuda.h>
@@ -60,8 +65,11 @@ constexpr int kRowCols = kLz * 16;         // tensor-memory columns of one row o
 constexpr int kBufCols = kR * kRowCols;    // one item
 constexpr int kCols = 2 * kBufCols;        // two items
 static_assert(kCols == 512, "tensor memory allocation");
-constexpr int kThreads = 256;
-constexpr size_t kSmemUse = 128 + (size_t)kNS * kStage + kWB + 8 * (kNS + 2) + 16;
+constexpr int kEpiWarps = 8;     // two per tensor-memory lane quarter, kR / 2 rows each
+constexpr int kIss = 4;          // MMA-issuing threads (lane 0 of warp 0 and of warps 9 ..), kR / kIss rows each
+constexpr int kThreads = 32 * (1 + kEpiWarps + kIss - 1);
+constexpr int kRing = 16;        // per-step completion barriers
+constexpr size_t kSmemUse = 128 + (size_t)kNS * kStage + kWB + 8 * (3 * kNS + kRing + 2) + 16;
 // more than half of the SM's shared memory: one CTA per SM, which the full
 // tensor-memory allocation needs
 constexpr size_t kSmem = kSmemUse > 120 * 1024 ? kSmemUse : 120 * 1024;
@@ -72,8 +80,10 @@ __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_
 __device__ __forceinline__ void mbar_init(uint64_t* b, unsigned n) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(b)), "r"(n) : "memory");
 }
-// Waits for phase parity par of b; false after about a second.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned par) {
+// Waits for phase parity par of b. False after about a second (then *abort
+// is raised for the other roles) or as soon as another role raised *abort
+// (abort may be null: wait regardless of the others).
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned par, volatile int* abort) {
     const long long t0 = clock64();
     for (;;) {
         unsigned ok;
@@ -83,17 +93,25 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned par) {
                      : "r"(sa(b)), "r"(par)
                      : "memory");
         if (ok) return true;
-        if (clock64() - t0 > 2000000000LL) return false;
+        if (abort && *abort) return false;
+        if (clock64() - t0 > 2000000000LL) {
+            if (abort) *abort = 1;
+            return false;
+        }
     }
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(b)) : "memory");
 }
 __device__ __forceinline__ void mbar_expect(uint64_t* b, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(b)), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void tma_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, uint64_t* b) {
+__device__ __forceinline__ void tma_5d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
+                                       uint64_t* b) {
     asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-        "[%6];" ::"r"(sa(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(sa(b))
+        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], "
+        "[%7];" ::"r"(sa(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(sa(b))
         : "memory");
 }
 // kind::f16 instruction descriptor: f32 accumulator, bf16 A and B, both
@@ -172,7 +190,7 @@ __device__ __forceinline__ void next_step(Cursor& c, const Items& it, int D) {
 }
 
 // OUT_F32: fp32 channel-major [cout][vol] output (the last layer); else bf16
-// channel-last [vol][16].
+// split channel-last [2][vol][8].
 template <bool RELU, bool OUT_F32>
 __global__ void __launch_bounds__(kThreads, 1)
 k_conv16_tc(const __grid_constant__ CUtensorMap tmap, const bf16* __restrict__ wtc, const float* __restrict__ bias,
@@ -181,17 +199,25 @@ k_conv16_tc(const __grid_constant__ CUtensorMap tmap, const bf16* __restrict__ w
     unsigned char* sm = raw + ((128u - (sa(raw) & 127u)) & 127u);
     unsigned char* stages = sm;
     unsigned char* wsm = sm + kNS * kStage;
-    uint64_t* full = reinterpret_cast<uint64_t*>(wsm + kWB);   // [kNS] input plane landed
-    uint64_t* done = full + kNS;                                 // [2] MMAs of a step complete (step parity)
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 2);
+    uint64_t* full = reinterpret_cast<uint64_t*>(wsm + kWB);   // [kNS] input plane landed (TMA)
+    uint64_t* sfree = full + kNS;                                // [kNS] its MMAs done: stage reusable
+    uint64_t* sdone = sfree + kNS;                               // [kRing] MMAs of step k done (epilogue)
+    uint64_t* tempty = sdone + kRing;                            // [2] item buffer drained (epilogue warps)
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(tempty + 2);
+    volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
 
     for (int i = t; i < kWB / 16; i += kThreads)
         reinterpret_cast<uint4*>(wsm)[i] = __ldg(reinterpret_cast<const uint4*>(wtc) + i);
     if (t == 0) {
-        for (int q = 0; q < kNS; ++q) mbar_init(full + q, 1);
-        mbar_init(done, 1);
-        mbar_init(done + 1, 1);
+        for (int q = 0; q < kNS; ++q) {
+            mbar_init(full + q, 1);
+            mbar_init(sfree + q, kIss);   // one commit per issuing thread
+        }
+        for (int q = 0; q < kRing; ++q) mbar_init(sdone + q, kIss);
+        mbar_init(tempty, kEpiWarps);
+        mbar_init(tempty + 1, kEpiWarps);
+        *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // weights: generic writes, tensor-core reads
@@ -205,173 +231,164 @@ k_conv16_tc(const __grid_constant__ CUtensorMap tmap, const bf16* __restrict__ w
     tc_after();
     const uint32_t tmem = *tslot;
 
-    float bv[16];
-#pragma unroll
-    for (int c = 0; c < 16; ++c) bv[c] = c < cout ? __ldg(bias + c) : 0.f;
-    const long long nvol = (long long)D * H * W;
-    // descriptor halves: A (K step = one channel half), B (K step 128 B, 8-row groups 256 B)
-    const uint32_t a_lo0 = ((sa(stages) & 0x3FFFFu) >> 4) | ((uint32_t)(kHalf >> 4) << 16);
-    const uint32_t a_hi = (128u >> 4) | (1u << 14);
-    const uint32_t b_lo0 = ((sa(wsm) & 0x3FFFFu) >> 4) | ((128u >> 4) << 16);
-    const uint32_t b_hi = (256u >> 4) | (1u << 14);
-
-    // output plane o of the item g (tensor-memory buffer buf) to memory: 16
-    // channels of voxel x0 + 32 (warp & 3) + lane on rows 2 (warp >> 2) + q
-    auto drain = [&](const Geo& g, int buf, int o) {
-        const int x = g.x0 + 32 * (warp & 3) + lane;
-        uint32_t r[2][16];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int ty = 2 * (warp >> 2) + q;
-            ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) +
-                     (uint32_t)(buf * kBufCols + ty * kRowCols + 16 * (g.z1 - 1 - o)),
-                 r[q]);
-        }
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int y = g.y0 + 2 * (warp >> 2) + q;
-            if (x >= W || y >= H) continue;
-            const long long v = ((long long)o * H + y) * W + x;
-            float f[16];
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                f[c] = __uint_as_float(r[q][c]) + bv[c];
-                if (RELU) f[c] = fmaxf(f[c], 0.f);
-            }
-            if constexpr (OUT_F32) {
-                float* op = static_cast<float*>(out);
-#pragma unroll
-                for (int c = 0; c < 16; ++c)
-                    if (c < cout) op[c * nvol + v] = f[c];
-            } else {
-                uint4 pk[2];
-                uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * c], f[2 * c + 1]);
-                    pw[c] = *reinterpret_cast<const uint32_t*>(&h);
+    static_assert(kEpiWarps == 8 && kR % 2 == 0 && kR % kIss == 0, "warp roles");
+    if (warp == 0 || warp > kEpiWarps) {
+        // ---- MMA issue: lane 0 of warp 0 and of warps 9 .., kR / kIss rows each; warp 0's also loads ----
+        if (lane == 0) {
+            const int j = warp == 0 ? 0 : warp - kEpiWarps;
+            const uint32_t a_lo0 = ((sa(stages) & 0x3FFFFu) >> 4) | ((uint32_t)(kHalf >> 4) << 16);
+            const uint32_t a_hi = (128u >> 4) | (1u << 14);
+            const uint32_t b_lo0 = ((sa(wsm) & 0x3FFFFu) >> 4) | ((128u >> 4) << 16);
+            const uint32_t b_hi = (256u >> 4) | (1u << 14);
+            auto load = [&](const Cursor& c, int s) {
+                unsigned char* dst = stages + s * kStage;
+                mbar_expect(full + s, 2 * kBox);
+                tma_5d(dst, &tmap, 0, c.g.x0 - 1, c.g.y0 - 1, c.p, 0, full + s);
+                tma_5d(dst + kHalf, &tmap, 0, c.g.x0 - 1, c.g.y0 - 1, c.p, 1, full + s);
+            };
+            Cursor prod = first_step(it, D), cons = prod;
+            long long kl = 0, k = 0;   // loads issued, steps issued
+            if (j == 0)
+                for (; kl < kNS && prod.item < it.n; ++kl) {
+                    load(prod, (int)(kl % kNS));
+                    next_step(prod, it, D);
                 }
-                uint4* dst = reinterpret_cast<uint4*>(static_cast<bf16*>(out) + v * 16);
-                dst[0] = pk[0];
-                dst[1] = pk[1];
+            bool ok = true;
+            for (; cons.item < it.n; ++k) {
+                const int s = (int)(k % kNS);
+                if (!(ok = mbar_wait(full + s, (unsigned)(k / kNS) & 1u, abort))) break;
+                if (cons.p == cons.g.pf && cons.ord >= 2 &&
+                    !(ok = mbar_wait(tempty + (cons.ord & 1), (unsigned)((cons.ord >> 1) - 1) & 1u, abort)))
+                    break;
+                tc_after();
+                // input plane cons.p into the item's buffer: output planes [lo, hi]
+                const Geo& g = cons.g;
+                const int p = cons.p;
+                const int hi = min(p + 1, g.z1 - 1), lo = max(p - 1, g.z0);
+                const int a0 = max(lo, p == 0 ? 0 : p + 1);   // from a0 up: first contribution (reset)
+                const uint32_t dcol = tmem + (uint32_t)((cons.ord & 1) * kBufCols + 16 * (g.z1 - 1 - hi));
+                const uint32_t abase = a_lo0 + (uint32_t)((s * kStage) >> 4);
+                const uint32_t bbase = b_lo0 + (uint32_t)(((p + 1 - hi) * 512) >> 4);
+                const uint32_t id_all = idesc(hi - lo + 1);
+#pragma unroll 1
+                for (int ty = j * (kR / kIss); ty < (j + 1) * (kR / kIss); ++ty) {
+                    const uint32_t d = dcol + (uint32_t)(ty * kRowCols);
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                        for (int dx = 0; dx < 3; ++dx) {
+                            const uint32_t al = abase + (uint32_t)((((ty + dy) * kHX + dx) * 16) >> 4);
+                            const uint32_t bl = bbase + (uint32_t)(((dy * 3 + dx) * 1536) >> 4);
+                            if (dy == 0 && dx == 0 && a0 <= hi) {
+                                mma(d, al, a_hi, bl, b_hi, idesc(hi - a0 + 1), 0u);
+                                if (lo < a0)
+                                    mma(d + (uint32_t)(16 * (hi - a0 + 1)), al, a_hi,
+                                        bl + (uint32_t)(((hi - a0 + 1) * 512) >> 4), b_hi, idesc(a0 - lo), 1u);
+                            } else {
+                                mma(d, al, a_hi, bl, b_hi, id_all, 1u);
+                            }
+                        }
+                }
+                mma_commit(sfree + s);
+                mma_commit(sdone + (int)(k % kRing));
+                // refill the stage of the step before last (its MMAs are long
+                // done: the issue never waits on the tensor pipe it feeds)
+                if (j == 0 && k > 1 && prod.item < it.n) {
+                    const int s1 = (int)((k - 2) % kNS);
+                    if (!(ok = mbar_wait(sfree + s1, (unsigned)((k - 2) / kNS) & 1u, abort))) {
+                        ++k;
+                        break;
+                    }
+                    load(prod, s1);
+                    ++kl;
+                    next_step(prod, it, D);
+                }
+                next_step(cons, it, D);
+            }
+            if (!ok) {
+                // let what was issued finish before the tensor memory goes
+                atomicExch(err, 1);
+                *abort = 1;
+                for (long long q = k; q < kl; ++q) mbar_wait(full + (int)(q % kNS), (unsigned)(q / kNS) & 1u, nullptr);
+                if (k > 0) mbar_wait(sdone + (int)((k - 1) % kRing), (unsigned)((k - 1) / kRing) & 1u, nullptr);
             }
         }
-    };
-    // the MMAs of one step: input plane c.p (ring stage s) into the item's buffer
-    auto issue = [&](const Cursor& c, int s) {
-        const Geo& g = c.g;
-        const int p = c.p;
-        const int hi = min(p + 1, g.z1 - 1), lo = max(p - 1, g.z0);   // output planes fed, hi first
-        const int a0 = max(lo, p == 0 ? 0 : p + 1);                    // from a0 up: first contribution
-        const uint32_t dcol = tmem + (uint32_t)((c.ord & 1) * kBufCols + 16 * (g.z1 - 1 - hi));
-        const uint32_t abase = a_lo0 + (uint32_t)((s * kStage) >> 4);
-        const uint32_t bbase = b_lo0 + (uint32_t)(((p + 1 - hi) * 512) >> 4);
-        const uint32_t id_all = idesc(hi - lo + 1);
-#pragma unroll 1
-        for (int ty = 0; ty < kR; ++ty) {
-            const uint32_t d = dcol + (uint32_t)(ty * kRowCols);
+    } else {
+        // ---- epilogue (warps 1-8): tensor-memory lanes 32 (warp & 3) .. + 31, rows ty0 .. ty0 + kR / 2 - 1 ----
+        const int lg = warp & 3;
+        const int ty0 = ((warp - 1) >> 2) * (kR / 2);
+        float bv[16];
 #pragma unroll
-            for (int dy = 0; dy < 3; ++dy)
+        for (int c = 0; c < 16; ++c) bv[c] = c < cout ? __ldg(bias + c) : 0.f;
+        const long long nvol = (long long)D * H * W;
+        Cursor cons = first_step(it, D);
+        int next_o = 0;
+        for (long long k = 0; cons.item < it.n; ++k) {
+            if (!mbar_wait(sdone + (int)(k % kRing), (unsigned)(k / kRing) & 1u, abort)) {
+                if (lane == 0) atomicExch(err, 1);
+                break;
+            }
+            tc_after();
+            const Geo& g = cons.g;
+            if (cons.p == g.pf) next_o = g.z0;
+            const int bound = cons.p == g.pl ? g.z1 - 1 : cons.p - 1;   // final output planes
+            const int buf = cons.ord & 1;
+            const int x = g.x0 + 32 * lg + lane;
+            for (; next_o <= bound; ++next_o) {
+                const int o = next_o;
+                uint32_t r[kR / 2][16];
 #pragma unroll
-                for (int dx = 0; dx < 3; ++dx) {
-                    const uint32_t al = abase + (uint32_t)((((ty + dy) * kHX + dx) * 16) >> 4);
-                    const uint32_t bl = bbase + (uint32_t)(((dy * 3 + dx) * 1536) >> 4);
-                    if (dy == 0 && dx == 0 && a0 <= hi) {
-                        // planes [a0, hi] start here (reset), [lo, a0) accumulate
-                        mma(d, al, a_hi, bl, b_hi, idesc(hi - a0 + 1), 0u);
-                        if (lo < a0)
-                            mma(d + (uint32_t)(16 * (hi - a0 + 1)), al, a_hi,
-                                bl + (uint32_t)(((hi - a0 + 1) * 512) >> 4), b_hi, idesc(a0 - lo), 1u);
+                for (int q = 0; q < kR / 2; ++q)
+                    ld16(tmem + ((uint32_t)(32 * lg) << 16) +
+                             (uint32_t)(buf * kBufCols + (ty0 + q) * kRowCols + 16 * (g.z1 - 1 - o)),
+                         r[q]);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < kR / 2; ++q) {
+                    const int ty = ty0 + q;
+                    const int y = g.y0 + ty;
+                    if (x >= W || y >= H) continue;
+                    const long long v = ((long long)o * H + y) * W + x;
+                    float f[16];
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        f[c] = __uint_as_float(r[q][c]) + bv[c];
+                        if (RELU) f[c] = fmaxf(f[c], 0.f);
+                    }
+                    if constexpr (OUT_F32) {
+                        float* op = static_cast<float*>(out);
+#pragma unroll
+                        for (int c = 0; c < 16; ++c)
+                            if (c < cout) op[c * nvol + v] = f[c];
                     } else {
-                        mma(d, al, a_hi, bl, b_hi, id_all, 1u);
+                        uint4 pk[2];
+                        uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            const __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * c], f[2 * c + 1]);
+                            pw[c] = *reinterpret_cast<const uint32_t*>(&h);
+                        }
+                        bf16* ob = static_cast<bf16*>(out);
+                        *reinterpret_cast<uint4*>(ob + v * 8) = pk[0];
+                        *reinterpret_cast<uint4*>(ob + (nvol + v) * 8) = pk[1];
                     }
                 }
-        }
-    };
-
-    unsigned fph = 0, dph = 0;       // phase bits: per stage (bit s), per step parity (bit b)
-    unsigned fpend = 0, dpend = 0;   // loads / commits issued and not yet waited
-    bool bad = false;
-    auto load = [&](const Cursor& c, int s) {   // thread 0
-        unsigned char* dst = stages + s * kStage;
-        mbar_expect(full + s, 2 * kBox);
-        tma_4d(dst, &tmap, 0, c.g.x0 - 1, c.g.y0 - 1, c.p, full + s);
-        tma_4d(dst + kHalf, &tmap, 8, c.g.x0 - 1, c.g.y0 - 1, c.p, full + s);
-    };
-    Cursor prod = first_step(it, D), cons = prod, prev = prod;
-    long long kl = 0;   // loads issued (all threads track it)
-    for (; kl < kNS - 1 && prod.item < it.n; ++kl) {
-        if (t == 0) load(prod, (int)(kl % kNS));
-        fpend |= 1u << (kl % kNS);
-        next_step(prod, it, D);
-    }
-    long long k = 0;   // steps consumed
-    int next_o = 0;    // next output plane of prev's item to drain
-    while (cons.item < it.n) {
-        const int s = (int)(k % kNS);
-        if (!mbar_wait(full + s, (fph >> s) & 1u)) bad = true;
-        fph ^= 1u << s;
-        fpend &= ~(1u << s);
-        if (__syncthreads_or(bad)) { bad = true; break; }
-        tc_after();
-        if (t == 0) {
-            issue(cons, s);
-            mma_commit(done + (k & 1));
-        }
-        dpend |= 1u << (k & 1);
-        if (k > 0) {
-            const int pb = (int)((k - 1) & 1);
-            if (!mbar_wait(done + pb, (dph >> pb) & 1u)) bad = true;
-            dph ^= 1u << pb;
-            dpend &= ~(1u << pb);
-            if (__syncthreads_or(bad)) { bad = true; break; }
-            tc_after();
-            // the step before is complete: its stage takes the next load
-            if (prod.item < it.n) {
-                if (t == 0) load(prod, (int)(kl % kNS));
-                fpend |= 1u << (kl % kNS);
-                ++kl;
-                next_step(prod, it, D);
             }
-            // output planes of prev's item final after its step: below its
-            // input plane, or all of them after the item's last step
-            const int bound = prev.p == prev.g.pl ? prev.g.z1 - 1 : prev.p - 1;
-            for (; next_o <= bound; ++next_o) drain(prev.g, prev.ord & 1, next_o);
-            if (prev.item != cons.item) next_o = cons.g.z0;
-        } else {
-            next_o = cons.g.z0;
+            if (cons.p == g.pl) {   // the item is drained: its buffer is free
+                tc_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty + buf);
+            }
+            next_step(cons, it, D);
         }
-        tc_before();
-        prev = cons;
-        next_step(cons, it, D);
-        ++k;
-    }
-    if (!bad && k > 0) {
-        const int pb = (int)((k - 1) & 1);
-        if (!mbar_wait(done + pb, (dph >> pb) & 1u)) bad = true;
-        dph ^= 1u << pb;
-        dpend &= ~(1u << pb);
-        if (!__syncthreads_or(bad)) {
-            tc_after();
-            for (; next_o <= prev.g.z1 - 1; ++next_o) drain(prev.g, prev.ord & 1, next_o);
-        } else {
-            bad = true;
-        }
-    }
-    if (bad) {
-        if (t == 0) atomicExch(err, 1);
-        // drain what this CTA issued before freeing its tensor memory
-        for (int q = 0; q < kNS; ++q)
-            if (fpend >> q & 1u) mbar_wait(full + q, (fph >> q) & 1u);
-        for (int q = 0; q < 2; ++q)
-            if (dpend >> q & 1u) mbar_wait(done + q, (dph >> q) & 1u);
     }
     tc_before();
     __syncthreads();
     tc_after();
-    if (warp == 0)
+    if (warp == 0) {
+        __syncwarp();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+    }
 }
 
 // Weights of one layer (float master W[co][16][27], tap = (dz 3 + dy) 3 + dx)
@@ -431,10 +448,12 @@ cudaError_t fmp_conv_tc_map(FmpTmap* map, const __nv_bfloat16* act, int D, int H
     PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
     if (!enc) return cudaErrorNotSupported;
     static_assert(sizeof(FmpTmap) >= sizeof(CUtensorMap), "tensor map storage");
-    cuuint64_t dims[4] = {16, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D};
-    cuuint64_t strides[3] = {32, (cuuint64_t)W * 32, (cuuint64_t)H * W * 32};
-    cuuint32_t box[4] = {8, (cuuint32_t)kHX, (cuuint32_t)kHY, 1}, es[4] = {1, 1, 1, 1};
-    const CUresult r = enc(reinterpret_cast<CUtensorMap*>(map->b), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
+    // [2 halves][D][H][W][8 channels], 16 bytes per voxel and half
+    const cuuint64_t vol = (cuuint64_t)D * H * W;
+    cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, 2};
+    cuuint64_t strides[4] = {16, (cuuint64_t)W * 16, (cuuint64_t)H * W * 16, vol * 16};
+    cuuint32_t box[5] = {8, (cuuint32_t)kHX, (cuuint32_t)kHY, 1, 1}, es[5] = {1, 1, 1, 1, 1};
+    const CUresult r = enc(reinterpret_cast<CUtensorMap*>(map->b), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5,
                            const_cast<__nv_bfloat16*>(act), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

@@ -292,8 +292,9 @@ cudaError_t fmp_cnn_apply_dev(fmp_ctx* c, const double* r, double* out, double a
 // apply gave up waiting (synchronises the stream; clears the flag)
 int fmp_cnn_check(fmp_ctx* c);
 
-// 16-channel 3x3x3 convolutions on tcgen05 (cnn_tc.cu). Activations are
-// channel-last bf16 [D][H][W][16]; FmpTmap holds the TMA descriptor of one.
+// 16-channel 3x3x3 convolutions on tcgen05 (cnn_tc.cu). Activations are bf16
+// in two channel-last halves [2][D][H][W][8]; FmpTmap holds the TMA
+// descriptor of one.
 struct __nv_bfloat16;
 struct FmpTmap {
     alignas(64) unsigned char b[128];
@@ -303,7 +304,7 @@ size_t fmp_conv_tc_weight_elems();   // bf16 elements of one packed layer
 // w: float master weights of a 16-input-channel layer, [cout][16][27]
 cudaError_t fmp_conv_tc_pack(const float* w, int cout, __nv_bfloat16* out, cudaStream_t s);
 cudaError_t fmp_conv_tc_map(FmpTmap* map, const __nv_bfloat16* act, int D, int H, int W);
-// relu && !out_f32: bf16 channel-last out (16 channels); !relu && out_f32:
+// relu && !out_f32: bf16 out in the same split layout; !relu && out_f32:
 // fp32 channel-major out [cout][D H W]. *err is set (and never cleared) when
 // a wait gives up.
 cudaError_t fmp_conv_tc_launch(const FmpTmap& map, const __nv_bfloat16* wtc, const float* bias, void* out, int cout,
