@@ -710,7 +710,7 @@ def run_case(args):
         nx, ny, nz = w.grid
         flops = CNN_FLOPS_PER_VOXEL * nx * ny * nz
         out.update({"tflops": flops / (ms * 1e-3) / 1e12, "flops_per_apply": flops,
-                    "kernels": "mma.sync" if args.cnn_mma_sync else "tcgen05 (16-channel layers)"})
+                    "kernels": "mma.sync" if args.cnn_mma_sync else "tcgen05 (all four layers)"})
     print(json.dumps(out))
     ctx.close()
 

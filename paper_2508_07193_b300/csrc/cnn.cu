@@ -54,9 +54,7 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
 // Y[co] = act(b[co] + sum_{ci, tap} Wk[co][tap][ci] X[ci](v + d(tap))), zero
 // padding. Wk: bf16 [NP][KP] (k = tap * CINP + ci, zero beyond 27 taps / CIN).
 // X: bf16 [CIN][vol]. Y: OutT [COUT][vol]. bias may be null.
-// CL: Y in two channel-last halves [COUT / 8][vol][8] instead (the layout
-// of the tcgen05 convolutions' inputs).
-template <int CIN, int COUT, bool RELU, class OutT, bool CL = false>
+template <int CIN, int COUT, bool RELU, class OutT>
 __global__ void __launch_bounds__(kT)
 k_conv_fwd(const bf16* __restrict__ X, const bf16* __restrict__ Wk, const float* __restrict__ bias,
            OutT* __restrict__ Y, Vol v) {
@@ -122,8 +120,7 @@ k_conv_fwd(const bf16* __restrict__ X, const bf16* __restrict__ Wk, const float*
             if (co < COUT && gx < v.W && gy < v.H) {
                 float val = acc[j][e] + (bias ? bias[co] : 0.f);
                 if (RELU) val = fmaxf(val, 0.f);
-                const long long vox = z * v.plane() + (long long)gy * v.W + gx;
-                const long long o = CL ? ((co >> 3) * v.n() + vox) * 8 + (co & 7) : co * v.n() + vox;
+                const long long o = co * v.n() + z * v.plane() + (long long)gy * v.W + gx;
                 if constexpr (sizeof(OutT) == 2)
                     Y[o] = __float2bfloat16(val);
                 else
@@ -228,6 +225,25 @@ __global__ void k_cnn_input(const double* __restrict__ r, const double* __restri
         const long long g = (long long)(z0 + k) * ny * nx + (long long)(y0 + j) * nx + (x0 + i);
         for (int c = 0; c < 3; ++c) X[c * v.n() + e] = __float2bfloat16((float)(r[c * N + g] * inv));
         X[3 * v.n() + e] = __float2bfloat16(eps_cell ? (float)(eps_cell[g] * 0.1) : 0.1f);
+    }
+}
+
+// The same input over the full grid, channel-last with 8 channels per voxel
+// ([vol][8]: r / s, eps / 10, then four zeros): the first tcgen05 layer's input.
+__global__ void k_cnn_input8(const double* __restrict__ r, const double* __restrict__ eps_cell, const double* rms,
+                             bf16* __restrict__ X, long long n) {
+    const double s = *rms;
+    const double inv = s > 0.0 ? 1.0 / s : 0.0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const __nv_bfloat162 a = __floats2bfloat162_rn((float)(r[e] * inv), (float)(r[n + e] * inv));
+        const __nv_bfloat162 b =
+            __floats2bfloat162_rn((float)(r[2 * n + e] * inv), eps_cell ? (float)(eps_cell[e] * 0.1) : 0.1f);
+        uint4 q;
+        q.x = *reinterpret_cast<const uint32_t*>(&a);
+        q.y = *reinterpret_cast<const uint32_t*>(&b);
+        q.z = 0u;
+        q.w = 0u;
+        reinterpret_cast<uint4*>(X)[e] = q;
     }
 }
 
@@ -355,7 +371,8 @@ struct FmpCnn {
     int adam_t = 0;
     bf16* wk[4] = {};          // forward weights [NP][KP] per layer
     bf16* wt[4] = {};          // input-gradient weights (swapped, flipped) per layer
-    bf16* wtc[4] = {};         // layers 1-3 as the tcgen05 B operand (cnn_tc.cu)
+    bf16* wtc[4] = {};         // all layers as the tcgen05 B operand (cnn_tc.cu)
+    bf16* x8 = nullptr;        // [vol][8] network input of the tcgen05 path
     int* tc_err = nullptr;     // set by a tcgen05 convolution that gave up waiting
     int use_tc = 1;            // full-volume applies on tcgen05 (else the mma.sync kernels)
     int nsm = 0;
@@ -397,13 +414,15 @@ size_t layer_off(int l) {
 
 cudaError_t ensure_vol(FmpCnn* n, long long vol) {
     if (vol <= n->cap) return cudaSuccess;
-    cudaFree(n->x0); for (auto& p : n->a) cudaFree(p); cudaFree(n->out);
+    cudaFree(n->x0); cudaFree(n->x8); for (auto& p : n->a) cudaFree(p); cudaFree(n->out);
     cudaFree(n->gf[0]); cudaFree(n->gf[1]); cudaFree(n->gbf); cudaFree(n->tgt);
-    n->x0 = nullptr; n->a[0] = n->a[1] = n->a[2] = nullptr; n->out = nullptr;
+    n->x0 = nullptr;
+    n->x8 = nullptr; n->a[0] = n->a[1] = n->a[2] = nullptr; n->out = nullptr;
     n->gf[0] = n->gf[1] = nullptr; n->gbf = nullptr; n->tgt = nullptr;
     n->cap = 0;
     cudaError_t e;
     if ((e = cudaMalloc(&n->x0, sizeof(bf16) * 4 * vol))) return e;
+    if ((e = cudaMalloc(&n->x8, sizeof(bf16) * 8 * vol))) return e;
     for (auto& p : n->a)
         if ((e = cudaMalloc(&p, sizeof(bf16) * 16 * vol))) return e;
     if ((e = cudaMalloc(&n->out, sizeof(float) * 3 * vol))) return e;
@@ -433,8 +452,8 @@ __global__ void k_pack(const float* __restrict__ w, bf16* __restrict__ f, bf16* 
 
 cudaError_t pack_weights(FmpCnn* n, cudaStream_t s) {
     for (int l = 0; l < 4; ++l) k_pack<<<1, 1024, 0, s>>>(n->w + layer_off(l), n->wk[l], n->wt[l], kCin[l], kCout[l]);
-    for (int l = 1; l < 4; ++l)
-        if (cudaError_t e = fmp_conv_tc_pack(n->w + layer_off(l), kCout[l], n->wtc[l], s)) return e;
+    for (int l = 0; l < 4; ++l)
+        if (cudaError_t e = fmp_conv_tc_pack(n->w + layer_off(l), kCin[l], kCout[l], n->wtc[l], s)) return e;
     return cudaGetLastError();
 }
 
@@ -449,22 +468,26 @@ cudaError_t net_forward(FmpCnn* n, const Vol& v, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// The same network on a full volume with the 16-channel layers on tcgen05:
-// layer 0 (4 -> 16, mma.sync) writes split channel-last activations
-// [2][vol][8], layers 1-2 read and write them through TMA, layer 3 writes the
-// fp32 output. The activation buffers a[0], a[1] hold that layout here.
+// The same network on a full volume with every layer on tcgen05: the input
+// as [vol][8] (x8), the hidden activations in two channel-last halves
+// [2][vol][8] (a[0], a[1]), the output fp32 channel-major (out).
 cudaError_t net_forward_tc(FmpCnn* n, const Vol& v, cudaStream_t s) {
     const int D = v.D, H = v.H, W = v.W;
-    FmpTmap m0, m1;
+    FmpTmap mx, m0, m1;
     cudaError_t e;
-    if ((e = fmp_conv_tc_map(&m0, n->a[0], D, H, W))) return e;
-    if ((e = fmp_conv_tc_map(&m1, n->a[1], D, H, W))) return e;
-    k_conv_fwd<4, 16, true, bf16, true><<<conv_grid(v), kT, 0, s>>>(n->x0, n->wk[0], bias_of(n, 0), n->a[0], v);
-    if ((e = fmp_conv_tc_launch(m0, n->wtc[1], bias_of(n, 1), n->a[1], 16, true, false, D, H, W, n->nsm, n->tc_err, s)))
+    if ((e = fmp_conv_tc_map(&mx, n->x8, 1, D, H, W))) return e;
+    if ((e = fmp_conv_tc_map(&m0, n->a[0], 2, D, H, W))) return e;
+    if ((e = fmp_conv_tc_map(&m1, n->a[1], 2, D, H, W))) return e;
+    if ((e = fmp_conv_tc_launch(mx, n->wtc[0], bias_of(n, 0), n->a[0], 4, 16, true, false, D, H, W, n->nsm, n->tc_err,
+                                s)))
         return e;
-    if ((e = fmp_conv_tc_launch(m1, n->wtc[2], bias_of(n, 2), n->a[0], 16, true, false, D, H, W, n->nsm, n->tc_err, s)))
+    if ((e = fmp_conv_tc_launch(m0, n->wtc[1], bias_of(n, 1), n->a[1], 16, 16, true, false, D, H, W, n->nsm,
+                                n->tc_err, s)))
         return e;
-    return fmp_conv_tc_launch(m0, n->wtc[3], bias_of(n, 3), n->out, 3, false, true, D, H, W, n->nsm, n->tc_err, s);
+    if ((e = fmp_conv_tc_launch(m1, n->wtc[2], bias_of(n, 2), n->a[0], 16, 16, true, false, D, H, W, n->nsm,
+                                n->tc_err, s)))
+        return e;
+    return fmp_conv_tc_launch(m0, n->wtc[3], bias_of(n, 3), n->out, 16, 3, false, true, D, H, W, n->nsm, n->tc_err, s);
 }
 
 template <int CIN, int COUT>
@@ -552,7 +575,7 @@ cudaError_t fmp_cnn_create(fmp_ctx* c) {
         if ((e = cudaMalloc(&n->wk[l], sizeof(bf16) * f))) return e;
         if ((e = cudaMalloc(&n->wt[l], sizeof(bf16) * b))) return e;
     }
-    for (int l = 1; l < 4; ++l)
+    for (int l = 0; l < 4; ++l)
         if ((e = cudaMalloc(&n->wtc[l], sizeof(bf16) * fmp_conv_tc_weight_elems()))) return e;
     if ((e = cudaMalloc(&n->tc_err, sizeof(int)))) return e;
     if ((e = cudaMemsetAsync(n->tc_err, 0, sizeof(int), c->stream))) return e;
@@ -583,7 +606,7 @@ void fmp_cnn_free(fmp_ctx* c) {
     cudaFree(n->w); cudaFree(n->g); cudaFree(n->m); cudaFree(n->v2);
     for (int l = 0; l < 4; ++l) { cudaFree(n->wk[l]); cudaFree(n->wt[l]); cudaFree(n->wtc[l]); }
     cudaFree(n->tc_err);
-    cudaFree(n->x0); for (auto& p : n->a) cudaFree(p); cudaFree(n->out);
+    cudaFree(n->x0); cudaFree(n->x8); for (auto& p : n->a) cudaFree(p); cudaFree(n->out);
     cudaFree(n->gf[0]); cudaFree(n->gf[1]); cudaFree(n->gbf); cudaFree(n->tgt);
     cudaFree(n->part); cudaFree(n->wtmp); cudaFree(n->scal); cudaFree(n->bbox);
     for (auto p : n->pool_x) cudaFree(p);
@@ -601,8 +624,14 @@ cudaError_t fmp_cnn_apply_dev(fmp_ctx* c, const double* r, double* out, double a
     if ((e = ensure_vol(n, v.n()))) return e;
     k_rms_part<<<kRmsBlocks, 256, 0, c->stream>>>(r, (long long)c->n_slots, n->scal + 8);
     k_rms_final<<<1, 32, 0, c->stream>>>(n->scal + 8, kRmsBlocks, (long long)c->n_slots, n->scal);
-    k_cnn_input<<<grid1(v.n()), 256, 0, c->stream>>>(r, c->d_eps_cell, n->scal, n->x0, c->nx, c->ny, c->nz, 0, 0, 0, v);
-    if ((e = n->use_tc ? net_forward_tc(n, v, c->stream) : net_forward(n, v, c->stream))) return e;
+    if (n->use_tc) {
+        k_cnn_input8<<<grid1(v.n()), 256, 0, c->stream>>>(r, c->d_eps_cell, n->scal, n->x8, v.n());
+        if ((e = net_forward_tc(n, v, c->stream))) return e;
+    } else {
+        k_cnn_input<<<grid1(v.n()), 256, 0, c->stream>>>(r, c->d_eps_cell, n->scal, n->x0, c->nx, c->ny, c->nz, 0, 0, 0,
+                                                       v);
+        if ((e = net_forward(n, v, c->stream))) return e;
+    }
     k_cnn_output<<<grid1(3 * v.n()), 256, 0, c->stream>>>(n->out, n->scal, out, c->nx, c->ny, c->nz, alpha, accumulate);
     c->launches += 8;
     return cudaGetLastError();

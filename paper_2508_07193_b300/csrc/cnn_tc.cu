@@ -1,8 +1,8 @@
-// The 16-input-channel 3x3x3 convolutions of the learned component on the
-// fifth-generation tensor cores: tcgen05.mma with the accumulators in tensor
-// memory, inputs streamed by TMA (cp.async.bulk.tensor) through an mbarrier
-// ring. Used by the full-volume network evaluation for the 16 -> 16 and
-// 16 -> 3 layers (about 90 % of its flops).
+// The 3x3x3 convolutions of the learned component on the fifth-generation
+// tensor cores: tcgen05.mma with the accumulators in tensor memory, inputs
+// streamed by TMA (cp.async.bulk.tensor) through an mbarrier ring. Used by
+// the full-volume network evaluation for all four layers (4 -> 16, 16 -> 16,
+// 16 -> 16, 16 -> 3).
 //
 // Implicit GEMM. Activations are bf16 in two channel-last halves,
 // [2][z][y][x][8] (16 contiguous bytes per voxel and half), so a TMA box of
@@ -191,7 +191,12 @@ __device__ __forceinline__ void next_step(Cursor& c, const Items& it, int D) {
 
 // OUT_F32: fp32 channel-major [cout][vol] output (the last layer); else bf16
 // split channel-last [2][vol][8].
-template <bool RELU, bool OUT_F32>
+// C8: the first layer, whose input has 4 channels stored as 8 (channels 4-7
+// zero) in one half [vol][8]. Its K = 16 per MMA then spans two x-taps: the
+// second 8-channel K chunk is the next voxel, 16 bytes on (the leading byte
+// offset). Per (dy) two MMAs cover dx = 1, 2 and dx = 0 (the second chunk of
+// the latter with zero weights), against nine with 16 channels.
+template <bool RELU, bool OUT_F32, bool C8>
 __global__ void __launch_bounds__(kThreads, 1)
 k_conv16_tc(const __grid_constant__ CUtensorMap tmap, const bf16* __restrict__ wtc, const float* __restrict__ bias,
             void* __restrict__ out, int cout, int D, int H, int W, Items it, int* __restrict__ err) {
@@ -236,15 +241,15 @@ k_conv16_tc(const __grid_constant__ CUtensorMap tmap, const bf16* __restrict__ w
         // ---- MMA issue: lane 0 of warp 0 and of warps 9 .., kR / kIss rows each; warp 0's also loads ----
         if (lane == 0) {
             const int j = warp == 0 ? 0 : warp - kEpiWarps;
-            const uint32_t a_lo0 = ((sa(stages) & 0x3FFFFu) >> 4) | ((uint32_t)(kHalf >> 4) << 16);
+            const uint32_t a_lo0 = ((sa(stages) & 0x3FFFFu) >> 4) | ((uint32_t)((C8 ? 16 : kHalf) >> 4) << 16);
             const uint32_t a_hi = (128u >> 4) | (1u << 14);
             const uint32_t b_lo0 = ((sa(wsm) & 0x3FFFFu) >> 4) | ((128u >> 4) << 16);
             const uint32_t b_hi = (256u >> 4) | (1u << 14);
             auto load = [&](const Cursor& c, int s) {
                 unsigned char* dst = stages + s * kStage;
-                mbar_expect(full + s, 2 * kBox);
+                mbar_expect(full + s, (C8 ? 1 : 2) * kBox);
                 tma_5d(dst, &tmap, 0, c.g.x0 - 1, c.g.y0 - 1, c.p, 0, full + s);
-                tma_5d(dst + kHalf, &tmap, 0, c.g.x0 - 1, c.g.y0 - 1, c.p, 1, full + s);
+                if (!C8) tma_5d(dst + kHalf, &tmap, 0, c.g.x0 - 1, c.g.y0 - 1, c.p, 1, full + s);
             };
             Cursor prod = first_step(it, D), cons = prod;
             long long kl = 0, k = 0;   // loads issued, steps issued
@@ -273,12 +278,15 @@ k_conv16_tc(const __grid_constant__ CUtensorMap tmap, const bf16* __restrict__ w
 #pragma unroll 1
                 for (int ty = j * (kR / kIss); ty < (j + 1) * (kR / kIss); ++ty) {
                     const uint32_t d = dcol + (uint32_t)(ty * kRowCols);
+                    constexpr int kTx = C8 ? 2 : 3;   // MMAs per dy: x-taps, or x-tap pairs
 #pragma unroll
                     for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-                        for (int dx = 0; dx < 3; ++dx) {
-                            const uint32_t al = abase + (uint32_t)((((ty + dy) * kHX + dx) * 16) >> 4);
-                            const uint32_t bl = bbase + (uint32_t)(((dy * 3 + dx) * 1536) >> 4);
+                        for (int dx = 0; dx < kTx; ++dx) {
+                            // C8: dx = 0 -> taps (1, 2) from voxel + 1; dx = 1 -> tap 0 from voxel + 0
+                            const int x_off = C8 ? 1 - dx : dx;
+                            const uint32_t al = abase + (uint32_t)((((ty + dy) * kHX + x_off) * 16) >> 4);
+                            const uint32_t bl = bbase + (uint32_t)(((dy * kTx + dx) * 1536) >> 4);
                             if (dy == 0 && dx == 0 && a0 <= hi) {
                                 mma(d, al, a_hi, bl, b_hi, idesc(hi - a0 + 1), 0u);
                                 if (lo < a0)
@@ -407,6 +415,26 @@ __global__ void k_pack_tc(const float* __restrict__ w, int cout, bf16* __restric
     out[e] = __float2bfloat16(co < cout ? w[((size_t)co * 16 + ci) * 27 + tap] : 0.f);
 }
 
+// The first layer (W[16][4][27]) for the C8 kernel: per (dy, pair) a 48 x 16
+// matrix (rows: output channels of dz = 0, 1, 2), K chunk 0 = channels of
+// x-tap 1 (pair 0) or 0 (pair 1), chunk 1 = channels of x-tap 2 (pair 0) or
+// zero (pair 1); input channels 4-7 zero. Same core-matrix order as
+// k_pack_tc; the buffer's tail past the 6 blocks is zeroed.
+__global__ void k_pack_tc0(const float* __restrict__ w, bf16* __restrict__ out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;   // element of [3][2][3][2][2][8][8], then the tail
+    if (e >= 27 * 256) return;
+    float v = 0.f;
+    if (e < 18 * 256) {
+        const int blk = e / 256, r = e % 256;
+        const int dy = blk / 6, pair = (blk / 3) % 2, dz = blk % 3;
+        const int g = r / 128, h = (r / 64) % 2, row = (r / 8) % 8, col = r % 8;
+        const int co = g * 8 + row, ci = col;
+        const int dx = pair == 0 ? 1 + h : (h == 0 ? 0 : -1);
+        if (ci < 4 && dx >= 0) v = w[((size_t)co * 4 + ci) * 27 + (dz * 3 + dy) * 3 + dx];
+    }
+    out[e] = __float2bfloat16(v);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -433,24 +461,34 @@ Items make_items(int D, int H, int W) {
 size_t fmp_conv_tc_weight_elems() { return 27 * 256; }
 
 cudaError_t fmp_conv_tc_init() {
-    cudaError_t e = cudaFuncSetAttribute(k_conv16_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSmem);
-    if (e) return e;
-    return cudaFuncSetAttribute(k_conv16_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_conv16_tc<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kSmem)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_conv16_tc<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kSmem)))
+        return e;
+    return cudaFuncSetAttribute(k_conv16_tc<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kSmem);
 }
 
-cudaError_t fmp_conv_tc_pack(const float* w, int cout, __nv_bfloat16* out, cudaStream_t s) {
-    k_pack_tc<<<(27 * 256 + 255) / 256, 256, 0, s>>>(w, cout, out);
+cudaError_t fmp_conv_tc_pack(const float* w, int cin, int cout, __nv_bfloat16* out, cudaStream_t s) {
+    if (cin == 4 && cout == 16)
+        k_pack_tc0<<<(27 * 256 + 255) / 256, 256, 0, s>>>(w, out);
+    else if (cin == 16)
+        k_pack_tc<<<(27 * 256 + 255) / 256, 256, 0, s>>>(w, cout, out);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
-cudaError_t fmp_conv_tc_map(FmpTmap* map, const __nv_bfloat16* act, int D, int H, int W) {
+cudaError_t fmp_conv_tc_map(FmpTmap* map, const __nv_bfloat16* act, int halves, int D, int H, int W) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
     if (!enc) return cudaErrorNotSupported;
     static_assert(sizeof(FmpTmap) >= sizeof(CUtensorMap), "tensor map storage");
-    // [2 halves][D][H][W][8 channels], 16 bytes per voxel and half
+    // [halves][D][H][W][8 channels], 16 bytes per voxel and half
     const cuuint64_t vol = (cuuint64_t)D * H * W;
-    cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, 2};
+    cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)halves};
     cuuint64_t strides[4] = {16, (cuuint64_t)W * 16, (cuuint64_t)H * W * 16, vol * 16};
     cuuint32_t box[5] = {8, (cuuint32_t)kHX, (cuuint32_t)kHY, 1, 1}, es[5] = {1, 1, 1, 1, 1};
     const CUresult r = enc(reinterpret_cast<CUtensorMap*>(map->b), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5,
@@ -460,15 +498,18 @@ cudaError_t fmp_conv_tc_map(FmpTmap* map, const __nv_bfloat16* act, int D, int H
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t fmp_conv_tc_launch(const FmpTmap& map, const __nv_bfloat16* wtc, const float* bias, void* out, int cout,
-                               bool relu, bool out_f32, int D, int H, int W, int nsm, int* err, cudaStream_t s) {
+cudaError_t fmp_conv_tc_launch(const FmpTmap& map, const __nv_bfloat16* wtc, const float* bias, void* out, int cin,
+                               int cout, bool relu, bool out_f32, int D, int H, int W, int nsm, int* err,
+                               cudaStream_t s) {
     const Items it = make_items(D, H, W);
     const int grid = std::min(it.n, nsm);
     const CUtensorMap& tm = *reinterpret_cast<const CUtensorMap*>(map.b);
-    if (relu && !out_f32)
-        k_conv16_tc<true, false><<<grid, kThreads, kSmem, s>>>(tm, wtc, bias, out, cout, D, H, W, it, err);
-    else if (!relu && out_f32)
-        k_conv16_tc<false, true><<<grid, kThreads, kSmem, s>>>(tm, wtc, bias, out, cout, D, H, W, it, err);
+    if (cin == 4 && relu && !out_f32)
+        k_conv16_tc<true, false, true><<<grid, kThreads, kSmem, s>>>(tm, wtc, bias, out, cout, D, H, W, it, err);
+    else if (cin == 16 && relu && !out_f32)
+        k_conv16_tc<true, false, false><<<grid, kThreads, kSmem, s>>>(tm, wtc, bias, out, cout, D, H, W, it, err);
+    else if (cin == 16 && !relu && out_f32)
+        k_conv16_tc<false, true, false><<<grid, kThreads, kSmem, s>>>(tm, wtc, bias, out, cout, D, H, W, it, err);
     else
         return cudaErrorNotSupported;
     return cudaGetLastError();

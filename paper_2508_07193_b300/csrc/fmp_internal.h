@@ -292,22 +292,25 @@ cudaError_t fmp_cnn_apply_dev(fmp_ctx* c, const double* r, double* out, double a
 // apply gave up waiting (synchronises the stream; clears the flag)
 int fmp_cnn_check(fmp_ctx* c);
 
-// 16-channel 3x3x3 convolutions on tcgen05 (cnn_tc.cu). Activations are bf16
-// in two channel-last halves [2][D][H][W][8]; FmpTmap holds the TMA
-// descriptor of one.
+// 3x3x3 convolutions on tcgen05 (cnn_tc.cu). Activations are bf16 in
+// channel-last halves [halves][D][H][W][8] (two halves for 16 channels; one,
+// channels 4-7 zero, for the network input); FmpTmap holds the TMA descriptor
+// of one.
 struct __nv_bfloat16;
 struct FmpTmap {
     alignas(64) unsigned char b[128];
 };
 cudaError_t fmp_conv_tc_init();
 size_t fmp_conv_tc_weight_elems();   // bf16 elements of one packed layer
-// w: float master weights of a 16-input-channel layer, [cout][16][27]
-cudaError_t fmp_conv_tc_pack(const float* w, int cout, __nv_bfloat16* out, cudaStream_t s);
-cudaError_t fmp_conv_tc_map(FmpTmap* map, const __nv_bfloat16* act, int D, int H, int W);
-// relu && !out_f32: bf16 out in the same split layout; !relu && out_f32:
-// fp32 channel-major out [cout][D H W]. *err is set (and never cleared) when
-// a wait gives up.
-cudaError_t fmp_conv_tc_launch(const FmpTmap& map, const __nv_bfloat16* wtc, const float* bias, void* out, int cout,
+// w: float master weights [cout][cin][27] of a layer with cin = 16, or the
+// first layer (cin = 4, cout = 16)
+cudaError_t fmp_conv_tc_pack(const float* w, int cin, int cout, __nv_bfloat16* out, cudaStream_t s);
+cudaError_t fmp_conv_tc_map(FmpTmap* map, const __nv_bfloat16* act, int halves, int D, int H, int W);
+// relu && !out_f32: bf16 out in the split 16-channel layout; !relu && out_f32
+// (cin = 16): fp32 channel-major out [cout][D H W]. *err is set (and never
+// cleared) when a wait gives up.
+cudaError_t fmp_conv_tc_launch(const FmpTmap& map, const __nv_bfloat16* wtc, const float* bias, void* out, int cin,
+                               int cout,
                                bool relu, bool out_f32, int D, int H, int W, int nsm, int* err, cudaStream_t s);
 
 #define FMP_CK(expr)                                                   \
