@@ -314,7 +314,11 @@ int fmp_cnn_get_params(fmp_ctx* ctx, float* params);
 int fmp_cnn_apply(fmp_ctx* ctx, const double* r, double* out);
 
 /* on = 1 (default) or 0: the convolution kernels of fmp_cnn_apply and of the
- * learned guess / correction of fmp_cn_step and fmp_krylov_solve. */
+ * learned guess / correction of fmp_cn_step and fmp_krylov_solve. on = 2
+ * tests the tcgen05 kernels' bounded waits: as 1, but the first layer waits
+ * for 16 bytes per input plane that no copy delivers, so its waits run out
+ * (about a second each), the kernel returns cleanly and the apply reports
+ * FMP_ERR_CUDA with the context still usable. Any other value: FMP_ERR_ARG. */
 int fmp_cnn_set_tc(fmp_ctx* ctx, int on);
 
 /* Append one training pair to the device pool: input r (a residual) and

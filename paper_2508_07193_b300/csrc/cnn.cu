@@ -375,6 +375,7 @@ struct FmpCnn {
     bf16* x8 = nullptr;        // [vol][8] network input of the tcgen05 path
     int* tc_err = nullptr;     // set by a tcgen05 convolution that gave up waiting
     int use_tc = 1;            // full-volume applies on tcgen05 (else the mma.sync kernels)
+    int tc_tx_extra = 0;       // > 0: the first layer's waits run out (time-out path test)
     int nsm = 0;
     long long cap = 0;         // voxels the activation buffers hold
     bf16* x0 = nullptr;        // [4][vol]
@@ -479,7 +480,7 @@ cudaError_t net_forward_tc(FmpCnn* n, const Vol& v, cudaStream_t s) {
     if ((e = fmp_conv_tc_map(&m0, n->a[0], 2, D, H, W))) return e;
     if ((e = fmp_conv_tc_map(&m1, n->a[1], 2, D, H, W))) return e;
     if ((e = fmp_conv_tc_launch(mx, n->wtc[0], bias_of(n, 0), n->a[0], 4, 16, true, false, D, H, W, n->nsm, n->tc_err,
-                                s)))
+                                s, n->tc_tx_extra)))
         return e;
     if ((e = fmp_conv_tc_launch(m0, n->wtc[1], bias_of(n, 1), n->a[1], 16, 16, true, false, D, H, W, n->nsm,
                                 n->tc_err, s)))
@@ -687,10 +688,11 @@ int fmp_cnn_apply(fmp_ctx* c, const double* r, double* out) {
 }
 
 int fmp_cnn_set_tc(fmp_ctx* c, int on) {
-    if (!c || (on != 0 && on != 1)) return FMP_ERR_ARG;
+    if (!c || on < 0 || on > 2) return FMP_ERR_ARG;
     if (c->latched) return FMP_ERR_CUDA;
     CNN_CK(fmp_cnn_create(c));
-    c->cnn->use_tc = on;
+    c->cnn->use_tc = on != 0;
+    c->cnn->tc_tx_extra = on == 2 ? 16 : 0;
     return FMP_OK;
 }
 

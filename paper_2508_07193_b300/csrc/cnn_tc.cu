@@ -199,7 +199,7 @@ __device__ __forceinline__ void next_step(Cursor& c, const Items& it, int D) {
 template <bool RELU, bool OUT_F32, bool C8>
 __global__ void __launch_bounds__(kThreads, 1)
 k_conv16_tc(const __grid_constant__ CUtensorMap tmap, const bf16* __restrict__ wtc, const float* __restrict__ bias,
-            void* __restrict__ out, int cout, int D, int H, int W, Items it, int* __restrict__ err) {
+            void* __restrict__ out, int cout, int D, int H, int W, Items it, int* __restrict__ err, int tx_extra) {
     extern __shared__ __align__(128) unsigned char raw[];
     unsigned char* sm = raw + ((128u - (sa(raw) & 127u)) & 127u);
     unsigned char* stages = sm;
@@ -247,7 +247,8 @@ k_conv16_tc(const __grid_constant__ CUtensorMap tmap, const bf16* __restrict__ w
             const uint32_t b_hi = (256u >> 4) | (1u << 14);
             auto load = [&](const Cursor& c, int s) {
                 unsigned char* dst = stages + s * kStage;
-                mbar_expect(full + s, (C8 ? 1 : 2) * kBox);
+                // tx_extra > 0 (a test of the time-out path only): bytes that never arrive
+                mbar_expect(full + s, (C8 ? 1 : 2) * kBox + tx_extra);
                 tma_5d(dst, &tmap, 0, c.g.x0 - 1, c.g.y0 - 1, c.p, 0, full + s);
                 if (!C8) tma_5d(dst + kHalf, &tmap, 0, c.g.x0 - 1, c.g.y0 - 1, c.p, 1, full + s);
             };
@@ -500,16 +501,16 @@ cudaError_t fmp_conv_tc_map(FmpTmap* map, const __nv_bfloat16* act, int halves, 
 
 cudaError_t fmp_conv_tc_launch(const FmpTmap& map, const __nv_bfloat16* wtc, const float* bias, void* out, int cin,
                                int cout, bool relu, bool out_f32, int D, int H, int W, int nsm, int* err,
-                               cudaStream_t s) {
+                               cudaStream_t s, int tx_extra) {
     const Items it = make_items(D, H, W);
     const int grid = std::min(it.n, nsm);
     const CUtensorMap& tm = *reinterpret_cast<const CUtensorMap*>(map.b);
     if (cin == 4 && relu && !out_f32)
-        k_conv16_tc<true, false, true><<<grid, kThreads, kSmem, s>>>(tm, wtc, bias, out, cout, D, H, W, it, err);
+        k_conv16_tc<true, false, true><<<grid, kThreads, kSmem, s>>>(tm, wtc, bias, out, cout, D, H, W, it, err, tx_extra);
     else if (cin == 16 && relu && !out_f32)
-        k_conv16_tc<true, false, false><<<grid, kThreads, kSmem, s>>>(tm, wtc, bias, out, cout, D, H, W, it, err);
+        k_conv16_tc<true, false, false><<<grid, kThreads, kSmem, s>>>(tm, wtc, bias, out, cout, D, H, W, it, err, tx_extra);
     else if (cin == 16 && !relu && out_f32)
-        k_conv16_tc<false, true, false><<<grid, kThreads, kSmem, s>>>(tm, wtc, bias, out, cout, D, H, W, it, err);
+        k_conv16_tc<false, true, false><<<grid, kThreads, kSmem, s>>>(tm, wtc, bias, out, cout, D, H, W, it, err, tx_extra);
     else
         return cudaErrorNotSupported;
     return cudaGetLastError();

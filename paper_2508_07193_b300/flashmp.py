@@ -411,8 +411,10 @@ class Context:
         return out
 
     def cnn_set_tc(self, on=True):
-        """Full-volume convolutions on tcgen05 (True, default) or mma.sync."""
-        _check(lib().fmp_cnn_set_tc(self._h, 1 if on else 0), "fmp_cnn_set_tc")
+        """Full-volume convolutions on tcgen05 (True, default) or mma.sync
+        (False); 2 tests the tcgen05 kernels' bounded waits (fmp_cnn_set_tc)."""
+        mode = on if isinstance(on, int) and not isinstance(on, bool) else (1 if on else 0)
+        _check(lib().fmp_cnn_set_tc(self._h, mode), "fmp_cnn_set_tc")
 
     def cnn_add_sample(self, r, e):
         _field(r, self.shape, "r"); _field(e, self.shape, "e")

@@ -189,3 +189,24 @@ def test_cnn_apply_128_sampled_voxels_match_oracle():
     for q, (k, j, i) in enumerate(pts):
         want[q][mask[:, k, j, i]] = 0.0
     assert rel(np.array(got), want) <= 3e-2
+
+
+def test_cnn_tcgen05_wait_runs_out_cleanly():
+    """The tcgen05 kernels' bounded waits: with every input-plane wait of the
+    first layer expecting bytes that never arrive, the waits run out, the
+    kernel returns, the apply reports FMP_ERR_CUDA, and the context still
+    works (the next applies are exact again)."""
+    from paper_2508_07193_b300 import flashmp as F
+    w = wl.small()
+    ctx = context(w)
+    f, _ = seeded_params()
+    ctx.cnn_set_params(f)
+    good = host(ctx.cnn_apply(dev(w.rhs)))
+    ctx.cnn_set_tc(2)
+    with pytest.raises(F.FlashMPError) as ei:
+        ctx.cnn_apply(dev(w.rhs))
+    assert "FMP_ERR_CUDA" in str(ei.value)
+    ctx.cnn_set_tc(True)
+    assert np.array_equal(host(ctx.cnn_apply(dev(w.rhs))), good)
+    z = host(ctx.precond_apply(dev(w.rhs)))
+    assert np.isfinite(z).all()
