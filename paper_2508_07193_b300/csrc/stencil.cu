@@ -18,7 +18,6 @@
 #include "fmp_internal.h"
 
 #include <algorithm>
-#include "cp_async.cuh"
 
 namespace {
 
@@ -162,19 +161,22 @@ __device__ __forceinline__ double cc_edge(double e, double xv, double kv, const 
 // float64 sum of its 13 terms, at 6 float64 operations per cell instead of 31.
 __device__ __forceinline__ int hexp_d(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
 
+// x 2^(1080 - emax) truncated, for a value whose exponent field is <= emax:
+// the 58-bit mantissa (implicit one, 5 guard bits) shifted right by emax - e.
 __device__ __forceinline__ long long to_fixed(double v, int emax) {
     const int hi = __double2hiint(v);
     const unsigned lo = (unsigned)__double2loint(v);
     const int e = (hi >> 20) & 0x7ff;
-    if (e == 0) return 0;   // zero (and subnormals, below 2^-1022)
-    const unsigned long long M = ((unsigned long long)(((unsigned)hi & 0xfffffu) | 0x100000u) << 32) | lo;
-    const int sh = emax - e - 5;
-    const unsigned long long X = sh >= 0 ? (sh < 64 ? M >> sh : 0ull) : M << (-sh);
+    const unsigned long long M =
+        ((unsigned long long)(((unsigned)hi & 0xfffffu) | 0x100000u) << 37) | ((unsigned long long)lo << 5);
+    const int sh = emax - e;
+    const unsigned long long X = (e == 0 || sh > 63) ? 0ull : (M >> sh);   // zero and subnormals: 0
     return hi < 0 ? -(long long)X : (long long)X;
 }
 
 // K 2^(emax - 1080) rounded to float64 (to nearest, ties up) with integer
-// operations; NaN when the tile held Inf/NaN.
+// operations (a hardware int64 -> float64 conversion would occupy the float64
+// pipe); NaN when the tile held Inf/NaN.
 __device__ __forceinline__ double from_fixed(long long K, int emax) {
     if (emax >= 2047) return __longlong_as_double(0x7ff8000000000000LL);
     const bool neg = K < 0;
@@ -199,17 +201,18 @@ k_curlcurl_fx(const double* __restrict__ x, const double* __restrict__ eps, doub
               const double* __restrict__ gate) {
     if (gate && *gate != 0.0) return;
     constexpr int NPL = KCN + 2;   // E planes k0 - 1 .. k0 + KCN
+    constexpr int NQ = (PLANE + TX * TY - 1) / (TX * TY);   // tile slots per thread and plane
     extern __shared__ __align__(16) unsigned char smraw[];
-    long long* T = reinterpret_cast<long long*>(smraw);   // [NPL][PLANE]: doubles, then fixed point
+    long long* T = reinterpret_cast<long long*>(smraw);   // [NPL][PLANE] fixed point
     long long* Fc = T + NPL * PLANE;                        // [2][FPLANE] faces (fixed point)
     __shared__ int emax_s;
     const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * KCN;
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     if (threadIdx.x == 0) emax_s = 0;
+    // the tile into registers (this thread's slots, the same on every plane),
+    // its largest exponent, then fixed point into shared memory
+    double v[NPL][NQ];
     {
-        // this thread's slots of a plane (the same on every plane): up to
-        // ceil(PLANE / 256) of them, offsets within the field's plane
-        constexpr int NQ = (PLANE + TX * TY - 1) / (TX * TY);
         long long off[NQ];
         bool in[NQ];
 #pragma unroll
@@ -221,36 +224,47 @@ k_curlcurl_fx(const double* __restrict__ x, const double* __restrict__ eps, doub
             in[q] = t < PLANE && gi >= 0 && gi < d.nx && gj >= 0 && gj < d.ny;
             off[q] = c * d.comp + (long long)gj * d.nx + gi;
         }
+        int e = 0;
+#pragma unroll
         for (int pl = 0; pl < NPL; ++pl) {
             const int k = k0 - 1 + pl;
             const bool kin = k >= 0 && k < d.nz;
-            const double* xk = x + (long long)k * d.plane;
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
-                const int t = threadIdx.x + q * TX * TY;
-                if (t < PLANE) fmp::cp_async8(T + pl * PLANE + t, kin && in[q] ? xk + off[q] : x, kin && in[q]);
+                v[pl][q] = kin && in[q] ? __ldg(x + (long long)k * d.plane + off[q]) : 0.0;
+                e = max(e, hexp_d(v[pl][q]));
             }
         }
-    }
-    fmp::cp_async_commit();
-    fmp::cp_async_wait<0>();
-    __syncthreads();
-    {
-        const unsigned* hw = reinterpret_cast<const unsigned*>(T) + 1;   // high words
-        int e = 0;
-        for (int t = threadIdx.x; t < NPL * PLANE; t += TX * TY) e = max(e, (int)((hw[2 * t] >> 20) & 0x7ffu));
         e = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
+        __syncthreads();   // emax_s initialised
         if ((threadIdx.x & 31) == 0) atomicMax(&emax_s, e);
     }
     __syncthreads();
     const int emax = emax_s;
-    for (int t = threadIdx.x; t < NPL * PLANE; t += TX * TY) T[t] = to_fixed(__longlong_as_double(T[t]), emax);
+#pragma unroll
+    for (int pl = 0; pl < NPL; ++pl)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int t = threadIdx.x + q * TX * TY;
+            if (t < PLANE) T[pl * PLANE + t] = to_fixed(v[pl][q], emax);
+        }
     __syncthreads();
+    // this thread's face slots (the same on every plane)
+    constexpr int NFQ = (FX * FY + TX * TY - 1) / (TX * TY);
+    int fe[NFQ];
+#pragma unroll
+    for (int q = 0; q < NFQ; ++q) {
+        const int t = threadIdx.x + q * TX * TY;
+        const int fj = t / FX, fi = t - fj * FX;
+        fe[q] = t < FX * FY ? fj * PX + fi : -1;
+    }
     // faces of one plane (integer): Ec = plane k, En = plane k + 1
     auto faces = [&](long long* F, const long long* Ec, const long long* En) {
-        for (int t = threadIdx.x; t < FX * FY; t += TX * TY) {
-            const int fj = t / FX, fi = t - fj * FX;
-            const int e = fj * PX + fi;
+#pragma unroll
+        for (int q = 0; q < NFQ; ++q) {
+            const int e = fe[q];
+            if (e < 0) continue;
+            const int t = threadIdx.x + q * TX * TY;
             const long long* Exc = Ec;
             const long long* Eyc = Ec + PX * PY;
             const long long* Ezc = Ec + 2 * PX * PY;
