@@ -123,8 +123,9 @@ __global__ void k_eps_bar(const double* __restrict__ ee, FmpBox* boxes, Dims d) 
 
 // Tiled double-curl apply, factored as K x = C^T (C x). A block owns a 32 x 8
 // (i, j) tile and a few consecutive k-planes; the three components of E on
-// those planes plus a one-cell halo (zero outside the grid) are copied to
-// shared memory by cp.async. Per plane the face values H = C x are formed once
+// those planes plus a one-cell halo (zero outside the grid) are loaded into
+// registers and stored to shared memory in fixed point (below). Per plane the
+// face values H = C x are formed once
 // on the tile plus a one-cell halo at the low i / j side, kept for two planes,
 // and each output takes its four faces per component:
 //   (C^T H)_x = Hz(j) - Hz(j-1) + Hy(k-1) - Hy(k)
