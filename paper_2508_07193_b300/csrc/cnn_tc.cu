@@ -60,7 +60,7 @@ constexpr int kBox = kHY * kHX * 16;       // bytes of one 8-channel box (12,480
 constexpr int kHalf = (kBox + 127) / 128 * 128;
 constexpr int kStage = 2 * kHalf;          // one input plane, both channel halves
 constexpr int kNS = 4;                     // ring of input planes
-constexpr int kWB = 27 * 512;              // weights: per tap 16 x 16 bf16 in core-matrix order
+constexpr int kWB = 27 * 512;              // weights: 27 blocks of 16 x 16 bf16 (per in-plane tap, dz = 0, 1, 2), core-matrix order
 constexpr int kRowCols = kLz * 16;         // tensor-memory columns of one row of an item
 constexpr int kBufCols = kR * kRowCols;    // one item
 constexpr int kCols = 2 * kBufCols;        // two items
