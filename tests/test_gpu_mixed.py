@@ -126,3 +126,50 @@ def test_fused_box_extents_one_to_forty():
         z = host(ctx.precond_apply(dev(w.rhs)))
         assert rel(z, ref) <= BOUND["bf16"], grid
         ctx.close()
+
+
+def _oracle_owned(w, ee, b):
+    """The oracle's exact solve of box b, its owned block (slices, values)."""
+    from oracle import box
+    eb = box.exact_solve(ras.restrict(w.rhs, b), ras.eps_bar(ee, b), w.beta)
+    part = np.zeros_like(w.rhs)
+    ras.prolong_owned(part, eb, b)
+    (x0, y0, z0), (x1, y1, z1) = b.own_lo, b.own_hi
+    sl = (slice(None), slice(z0, z1), slice(y0, y1), slice(x0, x1))
+    return sl, part[sl]
+
+
+def test_precond_256_sampled_boxes_all_precisions():
+    """The 256^3 workload (8^3 boxes of 32^3) in its launch configuration:
+    owned blocks of sampled boxes against the oracle one by one, float64 at
+    the float64 bar and each reduced precision within its stated bound."""
+    w = wl.grid256()
+    ee = yee.edge_eps(w.grid, w.eps_cell)
+    boxes = ras.partition(w.grid, w.cuts, w.overlap)
+    refs = [_oracle_owned(w, ee, boxes[i]) for i in (0, 273, len(boxes) - 1)]
+    r = dev(w.rhs)
+    for prec, bound in (("fp64", 1e-11), ("bf16", BOUND["bf16"]), ("fp16", BOUND["fp16"]),
+                        ("tf32", BOUND["tf32"])):
+        ctx = context(w, precision=prec)
+        z = host(ctx.precond_apply(r))
+        for sl, ref in refs:
+            assert rel(z[sl], ref) <= bound, prec
+        ctx.close()
+
+
+def test_uneven_bf16_fused_and_three_pass_boxes():
+    """The uneven 320 x 256 x 192 workload in bf16: boxes with every extent
+    <= 40 go to the fused cluster kernel, the rest to the three-pass kernels;
+    a box of each kind against the oracle."""
+    w = wl.grid_uneven()
+    ee = yee.edge_eps(w.grid, w.eps_cell)
+    boxes = ras.partition(w.grid, w.cuts, w.overlap)
+    ext = [max(b.ext_hi[a] - b.ext_lo[a] for a in range(3)) for b in boxes]
+    big = max(range(len(boxes)), key=lambda i: ext[i])
+    small = min(range(len(boxes)), key=lambda i: ext[i])
+    assert ext[big] > 40 and ext[small] <= 40
+    ctx = context(w, precision="bf16")
+    z = host(ctx.precond_apply(dev(w.rhs)))
+    for i in (small, big):
+        sl, ref = _oracle_owned(w, ee, boxes[i])
+        assert rel(z[sl], ref) <= BOUND["bf16"], i
