@@ -66,7 +66,8 @@ struct Sz {
     static constexpr int kDigS = kD * kRows * kLK;        // digit buffer (elements)
     static constexpr int kLine = M | 1;                   // odd stride of float64 line buffers
     static constexpr bool kSplit = M > 40;                // contractions may exceed 40
-    static constexpr int kMinBlocks = M > 40 ? 2 : 3;
+    static constexpr int kMinBlocks = M > 40 ? 2 : 4;    // passes A, B (pass C: shared memory allows 3)
+    static constexpr int kMinBlocksC = M > 40 ? 2 : 3;
 };
 
 // ---- digits ----------------------------------------------------------------
@@ -476,7 +477,7 @@ template <int M, class SZ = Sz<M>>
 constexpr size_t kSmemC = sizeof(uint16_t) * SZ::kDigS + sizeof(double) * 2 * M * SZ::kLine + sizeof(int) * 2 * SZ::kRows;
 
 template <int M>
-__global__ void __launch_bounds__(kT, Sz<M>::kMinBlocks)
+__global__ void __launch_bounds__(kT, Sz<M>::kMinBlocksC)
 k_oz_inv_xy(const double* __restrict__ scr, double* __restrict__ zout, const FmpBox* __restrict__ boxes,
             const int4* __restrict__ items, const uint4* __restrict__ otab, int nx, int ny, int nz,
             const double* __restrict__ gate) {
