@@ -66,8 +66,7 @@ struct Sz {
     static constexpr int kDigS = kD * kRows * kLK;        // digit buffer (elements)
     static constexpr int kLine = M | 1;                   // odd stride of float64 line buffers
     static constexpr bool kSplit = M > 40;                // contractions may exceed 40
-    static constexpr int kMinBlocks = M > 40 ? 2 : 4;    // passes A, B (pass C: shared memory allows 3)
-    static constexpr int kMinBlocksC = M > 40 ? 2 : 3;
+    static constexpr int kMinBlocks = M > 40 ? 2 : 4;
 };
 
 // ---- digits ----------------------------------------------------------------
@@ -472,12 +471,14 @@ k_oz_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const i
 }
 
 // ---- pass C: inverse y and x of a group of owned z-slabs, owned scatter -----
-// Shared: D, Sm[ky][kx], Q[y][kx] (float64), Ex.
+// Shared: D, Sm[ky][kx] (float64) and Q[y][kx] (class sums) in one buffer --
+// the slab is dead once its digits are cut, and the next slab is written
+// only after the last read of Q -- and Ex.
 template <int M, class SZ = Sz<M>>
-constexpr size_t kSmemC = sizeof(uint16_t) * SZ::kDigS + sizeof(double) * 2 * M * SZ::kLine + sizeof(int) * 2 * SZ::kRows;
+constexpr size_t kSmemC = sizeof(uint16_t) * SZ::kDigS + sizeof(double) * M * SZ::kLine + sizeof(int) * 2 * SZ::kRows;
 
 template <int M>
-__global__ void __launch_bounds__(kT, Sz<M>::kMinBlocksC)
+__global__ void __launch_bounds__(kT, Sz<M>::kMinBlocks)
 k_oz_inv_xy(const double* __restrict__ scr, double* __restrict__ zout, const FmpBox* __restrict__ boxes,
             const int4* __restrict__ items, const uint4* __restrict__ otab, int nx, int ny, int nz,
             const double* __restrict__ gate) {
@@ -492,8 +493,8 @@ k_oz_inv_xy(const double* __restrict__ scr, double* __restrict__ zout, const Fmp
     const int oy0 = B.own_lo[1], ony = B.own_n[1], ox0 = B.own_lo[0], onx = B.own_n[0];
     uint16_t* D = reinterpret_cast<uint16_t*>(smraw);
     double* Sm = reinterpret_cast<double*>(D + SZ::kDigS);   // [ky][kx], stride SZ::kLine
-    double* Q = Sm + M * SZ::kLine;                     // [y - oy0][kx], stride SZ::kLine
-    int* Ex1 = reinterpret_cast<int*>(Q + M * SZ::kLine);   // exponents of the ky lines (columns kx)
+    double* Q = Sm;                                      // [y - oy0][kx], stride SZ::kLine (after the cut of Sm)
+    int* Ex1 = reinterpret_cast<int*>(Sm + M * SZ::kLine);   // exponents of the ky lines (columns kx)
     int* Ex2 = Ex1 + SZ::kRows;                                  // of the kx lines (owned rows y)
     const bool sx = c != 0, sy = c != 1;
     // inverse tables: Bt[i][k] = T[k][i]
