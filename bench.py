@@ -38,7 +38,7 @@ FP64_NOMINAL_TFLOPS = 1.25   # B300 float64 (vector and tensor) nominal
 # (workload, precision); the capture is summarised in the profiles/ file named
 # beside each entry. Absent: not captured for this kernel version.
 TRAFFIC_BYTES = {
-    ("yee128_ras4x4x4_ol2", "fp64"): 442.7e6,   # transform_fp64_precond_grid128.md
+    ("yee128_ras4x4x4_ol2", "fp64"): 228.9e6,   # transform_fp64_precond_grid128.md
     ("yee128_ras4x4x4_ol2", "bf16"): 53.34e6,   # fused_bf16_precond_grid128.md
     ("yee128_ras4x4x4_ol2", "fp64_ozaki"): 251.4e6,   # transform_fp64_ozaki_precond_grid128.md
 }

@@ -42,6 +42,10 @@ __device__ __forceinline__ bool edge_wall(int c, int i, int j, int k) {
 // exceeds (m^2 + 1) / 2).
 __host__ __device__ __forceinline__ int fold_room(int m) { return (m * m + 1) / 2; }
 
+// Element c of a three-entry field of Fold3, by selects: a runtime subscript
+// would keep the whole struct in local memory.
+__device__ __forceinline__ int pick(const int (&a)[3], int c) { return c == 0 ? a[0] : (c == 1 ? a[1] : a[2]); }
+
 // Folded input q of class c for a line whose elements are v(i).
 template <class Get>
 __device__ __forceinline__ double f3_input(const Fold3& f, int c, int q, Get v) {
@@ -57,14 +61,14 @@ __device__ __forceinline__ double f3_input(const Fold3& f, int c, int q, Get v) 
 // Class and in-class index of folded input slot s.
 __device__ __forceinline__ void f3_slot(const Fold3& f, int s, int& c, int& q) {
     c = s < f.seg[1] ? 0 : (s < f.seg[2] ? 1 : 2);
-    q = s - f.seg[c];
+    q = s - pick(f.seg, c);
 }
 
 // Class, row and mode of output row r (rows ordered class by class).
 __device__ __forceinline__ void f3_row(const Fold3& f, int r, int& c, int& j, int& k) {
     c = r < f.n[0] ? 0 : (r < f.n[0] + f.n[1] ? 1 : 2);
     j = r - (c == 0 ? 0 : (c == 1 ? f.n[0] : f.n[0] + f.n[1]));
-    k = f.k0[c] + f.kstep[c] * j;
+    k = pick(f.k0, c) + pick(f.kstep, c) * j;
 }
 
 // First inverse pair worth computing for an owned range [o0, o1) on an odd
@@ -167,10 +171,10 @@ k_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox* _
     {
         const double* g = tabs + (sx ? B.dstf_off[0] : B.dctf_off[0]);
         for (int cc = 0; cc < 3; ++cc) {
-            const int n = fx.n[cc], ln = fx.len[cc];
+            const int n = pick(fx.n, cc), ln = pick(fx.len, cc);
             for (int t = threadIdx.x; t < n * ln; t += blockDim.x) {
                 const int j = t / ln, q = t - j * ln;
-                TX[fx.toff[cc] + q * n + j] = g[fx.toff[cc] + t];
+                TX[pick(fx.toff, cc) + q * n + j] = g[pick(fx.toff, cc) + t];
             }
         }
     }
@@ -187,23 +191,23 @@ k_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox* _
     // classes fold with different numbers of additions
     for (int t = threadIdx.x; t < my * LX; t += blockDim.x) {
         int cc = 0, u = t;
-        while (cc < 2 && u >= my * fx.len[cc]) { u -= my * fx.len[cc]; ++cc; }
-        const int y = u / fx.len[cc], q = u - y * fx.len[cc];
+        while (cc < 2 && u >= my * pick(fx.len, cc)) { u -= my * pick(fx.len, cc); ++cc; }
+        const int y = u / pick(fx.len, cc), q = u - y * pick(fx.len, cc);
         const double* row = X + y * mx;
-        AB[y * LX + fx.seg[cc] + q] = f3_input(fx, cc, q, [&](int i) { return row[i]; });
+        AB[y * LX + pick(fx.seg, cc) + q] = f3_input(fx, cc, q, [&](int i) { return row[i]; });
     }
     __syncthreads();
     // outputs class by class: rows (y, j) of class 0, then 1, then 2
     for (int t = threadIdx.x; t < my * fx.nmodes; t += blockDim.x) {
         int cc = 0, u = t;
-        while (cc < 2 && u >= my * fx.n[cc]) { u -= my * fx.n[cc]; ++cc; }
-        const int n = fx.n[cc], ln = fx.len[cc];
+        while (cc < 2 && u >= my * pick(fx.n, cc)) { u -= my * pick(fx.n, cc); ++cc; }
+        const int n = pick(fx.n, cc), ln = pick(fx.len, cc);
         const int y = u / n, j = u - y * n;
-        const double* a = AB + y * LX + fx.seg[cc];
-        const double* tcol = TX + fx.toff[cc] + j;
+        const double* a = AB + y * LX + pick(fx.seg, cc);
+        const double* tcol = TX + pick(fx.toff, cc) + j;
         double acc = 0.0;
         for (int q = 0; q < ln; ++q) acc = fma(tcol[q * n], a[q], acc);
-        P[y * mx + fx.k0[cc] + fx.kstep[cc] * j] = acc;
+        P[y * mx + pick(fx.k0, cc) + pick(fx.kstep, cc) * j] = acc;
     }
     if (fx.nmodes < mx)   // the DST-I wall mode kx = 0
         for (int y = threadIdx.x; y < my; y += blockDim.x) P[y * mx] = 0.0;
@@ -218,14 +222,14 @@ k_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox* _
     __syncthreads();
     for (int t = threadIdx.x; t < fy.nmodes * mx; t += blockDim.x) {
         int cc = 0, u = t;
-        while (cc < 2 && u >= fy.n[cc] * mx) { u -= fy.n[cc] * mx; ++cc; }
-        const int ln = fy.len[cc];
+        while (cc < 2 && u >= pick(fy.n, cc) * mx) { u -= pick(fy.n, cc) * mx; ++cc; }
+        const int ln = pick(fy.len, cc);
         const int j = u / mx, kx = u - j * mx;
-        const double* trow = TY + fy.toff[cc] + j * ln;
-        const double* col = X + fy.seg[cc] * mx + kx;
+        const double* trow = TY + pick(fy.toff, cc) + j * ln;
+        const double* col = X + pick(fy.seg, cc) * mx + kx;
         double acc = 0.0;
         for (int q = 0; q < ln; ++q) acc = fma(trow[q], col[q * mx], acc);
-        dst[(fy.k0[cc] + fy.kstep[cc] * j) * mx + kx] = acc;
+        dst[(pick(fy.k0, cc) + pick(fy.kstep, cc) * j) * mx + kx] = acc;
     }
     if (fy.nmodes < my)   // the DST-I wall mode ky = 0
         for (int kx = threadIdx.x; kx < mx; kx += blockDim.x) dst[kx] = 0.0;
@@ -283,10 +287,10 @@ k_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int2
         }
         int cc, j, kz;
         f3_row(f, r, cc, j, kz);
-        const double* g = (c == 2 ? TC : TS) + f.toff[cc] + j * f.len[cc];
-        const double* ab = AB + (c * mz + f.seg[cc]) * CT + col;
+        const double* g = (c == 2 ? TC : TS) + pick(f.toff, cc) + j * pick(f.len, cc);
+        const double* ab = AB + (c * mz + pick(f.seg, cc)) * CT + col;
         double acc = 0.0;
-        for (int q = 0; q < f.len[cc]; ++q) acc = fma(g[q], ab[q * CT], acc);
+        for (int q = 0; q < pick(f.len, cc); ++q) acc = fma(g[q], ab[q * CT], acc);
         Buf[(c * mz + kz) * CT + col] = acc;
     }
     __syncthreads();
