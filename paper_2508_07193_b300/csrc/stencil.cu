@@ -282,11 +282,20 @@ k_curlcurl_fx(const double* __restrict__ x, const double* __restrict__ eps, doub
         const int k = k0 + kk;
         long long* Fm = Fc + (kk & 1) * FPLANE;         // faces of plane k - 1
         long long* Fk = Fc + ((kk + 1) & 1) * FPLANE;   // faces of plane k
+        // this plane's eps and x, loaded before the faces so that their
+        // latency overlaps the integer work
+        const long long o = k * d.plane + (long long)gj * d.nx + gi;
+        double ev[3] = {0.0, 0.0, 0.0}, xv[3] = {0.0, 0.0, 0.0};
+        if (live)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                ev[q] = __ldg(eps + q * d.comp + o);
+                xv[q] = __ldg(x + q * d.comp + o);
+            }
         __syncthreads();
         faces(Fk, T + (kk + 1) * PLANE, T + (kk + 2) * PLANE);
         __syncthreads();
         if (live) {
-            const long long o = k * d.plane + (long long)gj * d.nx + gi;
             const long long* Hxk = Fk;
             const long long* Hyk = Fk + FX * FY;
             const long long* Hzk = Fk + 2 * FX * FY;
@@ -295,16 +304,16 @@ k_curlcurl_fx(const double* __restrict__ x, const double* __restrict__ eps, doub
             double vx = 0.0, vy = 0.0, vz = 0.0;
             if (gj >= 1 && k >= 1) {
                 const long long kx = (Hzk[fo] - Hzk[fo - FX]) + (Hym[fo] - Hyk[fo]);
-                vx = cc_edge<FORM>(eps[o], __ldg(x + o), from_fixed(kx, emax), b ? b + o : nullptr, s_b, c_eps, c_k);
+                vx = cc_edge<FORM>(ev[0], xv[0], from_fixed(kx, emax), b ? b + o : nullptr, s_b, c_eps, c_k);
             }
             if (gi >= 1 && k >= 1) {
                 const long long ky = (Hxk[fo] - Hxm[fo]) - (Hzk[fo] - Hzk[fo - 1]);
-                vy = cc_edge<FORM>(eps[d.comp + o], __ldg(x + d.comp + o), from_fixed(ky, emax),
+                vy = cc_edge<FORM>(ev[1], xv[1], from_fixed(ky, emax),
                                    b ? b + d.comp + o : nullptr, s_b, c_eps, c_k);
             }
             if (gi >= 1 && gj >= 1) {
                 const long long kz = (Hxk[fo - FX] - Hxk[fo]) + (Hyk[fo] - Hyk[fo - 1]);
-                vz = cc_edge<FORM>(eps[2 * d.comp + o], __ldg(x + 2 * d.comp + o), from_fixed(kz, emax),
+                vz = cc_edge<FORM>(ev[2], xv[2], from_fixed(kz, emax),
                                    b ? b + 2 * d.comp + o : nullptr, s_b, c_eps, c_k);
             }
             y[o] = vx;
