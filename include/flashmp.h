@@ -55,7 +55,7 @@ typedef enum fmp_status {
     FMP_ERR_NOT_CONVERGED = -4,   /* max_iters reached; best x written         */
     FMP_ERR_BREAKDOWN = -5,       /* Krylov breakdown before convergence       */
     FMP_ERR_NONFINITE = -6,       /* NaN/Inf met in a residual or coefficient  */
-    FMP_ERR_UNSUPPORTED = -7      /* option not available in this build        */
+    FMP_ERR_UNSUPPORTED = -7      /* option not available in this library      */
 } fmp_status;
 
 /* Arithmetic of the transforms inside the preconditioner. The Krylov side
