@@ -529,6 +529,9 @@ k_fused_solve(const double* __restrict__ r, double* __restrict__ zout, const Fmp
         double* dst0 = zout + ((long long)c * nz + B.ext_lo[2]) * (long long)ny * nx + (long long)B.ext_lo[1] * nx +
                        B.ext_lo[0];
         const int nlo = ox0 >> 3, nhi = (ox0 + onx + 7) >> 3;
+        // element pairs (x, x + 1) start 16-byte aligned when the output is,
+        // every row starts aligned (nx even) and the box's first x is even
+        const bool pair16 = (reinterpret_cast<uintptr_t>(zout) & 15u) == 0 && (nx & 1) == 0 && (B.ext_lo[0] & 1) == 0;
         row_pass<Tr, Sh>(
             Dbase, f, acc, onz * ony,
             [oz0, oy0, ony](int i) { return (oz0 + i / ony) * kSlab + (oy0 + i % ony) * kFL; }, kdx, nlo, nhi,
@@ -541,11 +544,17 @@ k_fused_solve(const double* __restrict__ r, double* __restrict__ zout, const Fmp
                 for (int n = 0; n < kNT; ++n) {
                     if (n >= nlo && n < nhi) {
                         const int x = n * 8 + 2 * t;
-#pragma unroll
-                        for (int e = 0; e < 2; ++e) {
-                            const bool own = x + e >= ox0 && x + e < ox0 + onx;
-                            if (ok0 && own) q0[x + e] = f32_to_f64(a[n][e] * s);
-                            if (ok1 && own) q1[x + e] = f32_to_f64(a[n][2 + e] * s);
+                        const bool own0 = x >= ox0 && x < ox0 + onx, own1 = x + 1 >= ox0 && x + 1 < ox0 + onx;
+                        const double v00 = f32_to_f64(a[n][0] * s), v01 = f32_to_f64(a[n][1] * s);
+                        const double v10 = f32_to_f64(a[n][2] * s), v11 = f32_to_f64(a[n][3] * s);
+                        if (pair16 && own0 && own1) {   // one 16-byte store per row
+                            if (ok0) *reinterpret_cast<double2*>(q0 + x) = make_double2(v00, v01);
+                            if (ok1) *reinterpret_cast<double2*>(q1 + x) = make_double2(v10, v11);
+                        } else {
+                            if (ok0 && own0) q0[x] = v00;
+                            if (ok0 && own1) q0[x + 1] = v01;
+                            if (ok1 && own0) q1[x] = v10;
+                            if (ok1 && own1) q1[x + 1] = v11;
                         }
                     }
                 }
