@@ -471,8 +471,9 @@ cudaError_t net_forward(FmpCnn* n, const Vol& v, cudaStream_t s) {
 
 // The same network on a full volume with every layer on tcgen05: the input
 // as [vol][8] (x8), the hidden activations in two channel-last halves
-// [2][vol][8] (a[0], a[1]), the output fp32 channel-major (out).
-cudaError_t net_forward_tc(FmpCnn* n, const Vol& v, cudaStream_t s) {
+// [2][vol][8] (a[0], a[1]); the last layer writes out = (accumulate ? out :
+// 0) + alpha s N (the float64 edge field, walls as k_cnn_output leaves them).
+cudaError_t net_forward_tc(FmpCnn* n, const Vol& v, double* out, double alpha, int accumulate, cudaStream_t s) {
     const int D = v.D, H = v.H, W = v.W;
     FmpTmap mx, m0, m1;
     cudaError_t e;
@@ -488,7 +489,8 @@ cudaError_t net_forward_tc(FmpCnn* n, const Vol& v, cudaStream_t s) {
     if ((e = fmp_conv_tc_launch(m1, n->wtc[2], bias_of(n, 2), n->a[0], 16, 16, true, false, D, H, W, n->nsm,
                                 n->tc_err, s)))
         return e;
-    return fmp_conv_tc_launch(m0, n->wtc[3], bias_of(n, 3), n->out, 16, 3, false, true, D, H, W, n->nsm, n->tc_err, s);
+    return fmp_conv_tc_launch(m0, n->wtc[3], bias_of(n, 3), out, 16, 3, false, true, D, H, W, n->nsm, n->tc_err, s, 0,
+                              n->scal, alpha, accumulate);
 }
 
 template <int CIN, int COUT>
@@ -627,14 +629,16 @@ cudaError_t fmp_cnn_apply_dev(fmp_ctx* c, const double* r, double* out, double a
     k_rms_final<<<1, 32, 0, c->stream>>>(n->scal + 8, kRmsBlocks, (long long)c->n_slots, n->scal);
     if (n->use_tc) {
         k_cnn_input8<<<grid1(v.n()), 256, 0, c->stream>>>(r, c->d_eps_cell, n->scal, n->x8, v.n());
-        if ((e = net_forward_tc(n, v, c->stream))) return e;
+        if ((e = net_forward_tc(n, v, out, alpha, accumulate, c->stream))) return e;
+        c->launches += 7;
     } else {
         k_cnn_input<<<grid1(v.n()), 256, 0, c->stream>>>(r, c->d_eps_cell, n->scal, n->x0, c->nx, c->ny, c->nz, 0, 0, 0,
                                                        v);
         if ((e = net_forward(n, v, c->stream))) return e;
+        k_cnn_output<<<grid1(3 * v.n()), 256, 0, c->stream>>>(n->out, n->scal, out, c->nx, c->ny, c->nz, alpha,
+                                                            accumulate);
+        c->launches += 8;
     }
-    k_cnn_output<<<grid1(3 * v.n()), 256, 0, c->stream>>>(n->out, n->scal, out, c->nx, c->ny, c->nz, alpha, accumulate);
-    c->launches += 8;
     return cudaGetLastError();
 }
 

@@ -189,17 +189,20 @@ __device__ __forceinline__ void next_step(Cursor& c, const Items& it, int D) {
     }
 }
 
-// OUT_F32: fp32 channel-major [cout][vol] output (the last layer); else bf16
-// split channel-last [2][vol][8].
+// OUT_EDGE: the last layer, written straight into the float64 edge field
+// [cout][vol] as (accumulate ? out : 0) + (*rms) alpha y with the PEC wall
+// slots left at zero / untouched (the network's output map); else bf16 split
+// channel-last [2][vol][8].
 // C8: the first layer, whose input has 4 channels stored as 8 (channels 4-7
 // zero) in one half [vol][8]. Its K = 16 per MMA then spans two x-taps: the
 // second 8-channel K chunk is the next voxel, 16 bytes on (the leading byte
 // offset). Per (dy) two MMAs cover dx = 1, 2 and dx = 0 (the second chunk of
 // the latter with zero weights), against nine with 16 channels.
-template <bool RELU, bool OUT_F32, bool C8>
+template <bool RELU, bool OUT_EDGE, bool C8>
 __global__ void __launch_bounds__(kThreads, 1)
 k_conv16_tc(const __grid_constant__ CUtensorMap tmap, const bf16* __restrict__ wtc, const float* __restrict__ bias,
-            void* __restrict__ out, int cout, int D, int H, int W, Items it, int* __restrict__ err, int tx_extra) {
+            void* __restrict__ out, int cout, int D, int H, int W, Items it, int* __restrict__ err, int tx_extra,
+            const double* __restrict__ rms, double alpha, int accumulate) {
     extern __shared__ __align__(128) unsigned char raw[];
     unsigned char* sm = raw + ((128u - (sa(raw) & 127u)) & 127u);
     unsigned char* stages = sm;
@@ -330,6 +333,7 @@ k_conv16_tc(const __grid_constant__ CUtensorMap tmap, const bf16* __restrict__ w
 #pragma unroll
         for (int c = 0; c < 16; ++c) bv[c] = c < cout ? __ldg(bias + c) : 0.f;
         const long long nvol = (long long)D * H * W;
+        const double oscale = OUT_EDGE ? *rms * alpha : 1.0;
         Cursor cons = first_step(it, D);
         int next_o = 0;
         for (long long k = 0; cons.item < it.n; ++k) {
@@ -364,11 +368,16 @@ k_conv16_tc(const __grid_constant__ CUtensorMap tmap, const bf16* __restrict__ w
                         f[c] = __uint_as_float(r[q][c]) + bv[c];
                         if (RELU) f[c] = fmaxf(f[c], 0.f);
                     }
-                    if constexpr (OUT_F32) {
-                        float* op = static_cast<float*>(out);
+                    if constexpr (OUT_EDGE) {
+                        double* op = static_cast<double*>(out);
 #pragma unroll
                         for (int c = 0; c < 16; ++c)
-                            if (c < cout) op[c * nvol + v] = f[c];
+                            if (c < cout) {
+                                const bool wall = c == 0 ? (y == 0 || o == 0) : c == 1 ? (x == 0 || o == 0) : (x == 0 || y == 0);
+                                const double val = wall ? 0.0 : oscale * (double)f[c];
+                                const long long q = c * nvol + v;
+                                op[q] = accumulate ? op[q] + val : val;
+                            }
                     } else {
                         uint4 pk[2];
                         uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
@@ -500,17 +509,20 @@ cudaError_t fmp_conv_tc_map(FmpTmap* map, const __nv_bfloat16* act, int halves, 
 }
 
 cudaError_t fmp_conv_tc_launch(const FmpTmap& map, const __nv_bfloat16* wtc, const float* bias, void* out, int cin,
-                               int cout, bool relu, bool out_f32, int D, int H, int W, int nsm, int* err,
-                               cudaStream_t s, int tx_extra) {
+                               int cout, bool relu, bool out_edge, int D, int H, int W, int nsm, int* err,
+                               cudaStream_t s, int tx_extra, const double* rms, double alpha, int accumulate) {
     const Items it = make_items(D, H, W);
     const int grid = std::min(it.n, nsm);
     const CUtensorMap& tm = *reinterpret_cast<const CUtensorMap*>(map.b);
-    if (cin == 4 && relu && !out_f32)
-        k_conv16_tc<true, false, true><<<grid, kThreads, kSmem, s>>>(tm, wtc, bias, out, cout, D, H, W, it, err, tx_extra);
-    else if (cin == 16 && relu && !out_f32)
-        k_conv16_tc<true, false, false><<<grid, kThreads, kSmem, s>>>(tm, wtc, bias, out, cout, D, H, W, it, err, tx_extra);
-    else if (cin == 16 && !relu && out_f32)
-        k_conv16_tc<false, true, false><<<grid, kThreads, kSmem, s>>>(tm, wtc, bias, out, cout, D, H, W, it, err, tx_extra);
+    if (cin == 4 && relu && !out_edge)
+        k_conv16_tc<true, false, true><<<grid, kThreads, kSmem, s>>>(tm, wtc, bias, out, cout, D, H, W, it, err,
+                                                                    tx_extra, rms, alpha, accumulate);
+    else if (cin == 16 && relu && !out_edge)
+        k_conv16_tc<true, false, false><<<grid, kThreads, kSmem, s>>>(tm, wtc, bias, out, cout, D, H, W, it, err,
+                                                                     tx_extra, rms, alpha, accumulate);
+    else if (cin == 16 && !relu && out_edge && rms)
+        k_conv16_tc<false, true, false><<<grid, kThreads, kSmem, s>>>(tm, wtc, bias, out, cout, D, H, W, it, err,
+                                                                     tx_extra, rms, alpha, accumulate);
     else
         return cudaErrorNotSupported;
     return cudaGetLastError();

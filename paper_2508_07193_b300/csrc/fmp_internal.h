@@ -306,14 +306,17 @@ size_t fmp_conv_tc_weight_elems();   // bf16 elements of one packed layer
 // first layer (cin = 4, cout = 16)
 cudaError_t fmp_conv_tc_pack(const float* w, int cin, int cout, __nv_bfloat16* out, cudaStream_t s);
 cudaError_t fmp_conv_tc_map(FmpTmap* map, const __nv_bfloat16* act, int halves, int D, int H, int W);
-// relu && !out_f32: bf16 out in the split 16-channel layout; !relu && out_f32
-// (cin = 16): fp32 channel-major out [cout][D H W]. *err is set (and never
-// cleared) when a wait gives up. tx_extra > 0 makes every input-plane wait
-// expect that many bytes more than the copies deliver, so the waits run out
-// (a test of the time-out path; 0 otherwise).
+// relu && !out_edge: bf16 out in the split 16-channel layout; !relu &&
+// out_edge (cin = 16): out is the float64 edge field [cout][D H W], written
+// as (accumulate ? out : 0) + (*rms) alpha y with PEC wall slots zero (or
+// untouched when accumulating). *err is set (and never cleared) when a wait
+// gives up. tx_extra > 0 makes every input-plane wait expect that many bytes
+// more than the copies deliver, so the waits run out (a test of the time-out
+// path; 0 otherwise).
 cudaError_t fmp_conv_tc_launch(const FmpTmap& map, const __nv_bfloat16* wtc, const float* bias, void* out, int cin,
-                               int cout, bool relu, bool out_f32, int D, int H, int W, int nsm, int* err,
-                               cudaStream_t s, int tx_extra = 0);
+                               int cout, bool relu, bool out_edge, int D, int H, int W, int nsm, int* err,
+                               cudaStream_t s, int tx_extra = 0, const double* rms = nullptr, double alpha = 1.0,
+                               int accumulate = 0);
 
 #define FMP_CK(expr)                                                   \
     do {                                                               \
