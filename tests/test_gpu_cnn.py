@@ -210,3 +210,7 @@ def test_cnn_tcgen05_wait_runs_out_cleanly():
     assert np.array_equal(host(ctx.cnn_apply(dev(w.rhs))), good)
     z = host(ctx.precond_apply(dev(w.rhs)))
     assert np.isfinite(z).all()
+    for bad in (3, -1):
+        with pytest.raises(F.FlashMPError) as ei:
+            ctx.cnn_set_tc(bad)
+        assert "FMP_ERR_ARG" in str(ei.value)
