@@ -196,7 +196,7 @@ template <int KCN>
 constexpr size_t fx_smem() { return sizeof(long long) * ((KCN + 2) * PLANE + 2 * FPLANE); }
 
 template <int FORM, int KCN>
-__global__ void __launch_bounds__(TX * TY)
+__global__ void __launch_bounds__(TX * TY, 4)
 k_curlcurl_fx(const double* __restrict__ x, const double* __restrict__ eps, double* __restrict__ y,
               const double* __restrict__ b, double s_b, double c_eps, double c_k, Dims d,
               const double* __restrict__ gate) {
@@ -421,7 +421,10 @@ cudaError_t fmp_launch_eps_bar(const double* eps_edge, FmpBox* d_boxes, int n_bo
     return cudaGetLastError();
 }
 
-constexpr int KFX = 4;   // planes per CTA of the fixed-point kernel
+// Planes per CTA of the fixed-point kernel. Two planes (45.8 KB of shared
+// memory, at most 64 registers) let four CTAs share an SM; four planes held
+// 63.2 KB and 80 registers, three CTAs per SM, and ran 2 % slower.
+constexpr int KFX = 2;
 
 cudaError_t fmp_stencil_init() {
     cudaError_t e;

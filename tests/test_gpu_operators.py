@@ -85,7 +85,7 @@ def test_curlcurl_is_exact_on_integer_fields():
 
 
 def test_curlcurl_wide_dynamic_range_and_tiny_tiles():
-    """Values 2^-300 .. 2^300 across and inside the 32 x 8 x 4 tiles: the
+    """Values 2^-300 .. 2^300 across and inside the 32 x 8 x 2 tiles: the
     error stays below the float64 bar relative to the field; a field of
     values near 2^-1000 (tile exponents below the split scale) too."""
     w = CASES[0]
