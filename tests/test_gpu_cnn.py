@@ -144,6 +144,22 @@ def test_cnn_apply_tcgen05_matches_oracle(grid, xcuts):
     assert np.all(out[wl.edge_wall_mask(w.grid)] == 0.0)
 
 
+def test_cnn_apply_scales_exactly_with_the_residual():
+    """The input is r / rms(r) and the output is rescaled by rms(r), so a
+    residual scaled by 2^400 or 2^-400 gives the same bf16 input and an
+    output scaled by exactly that power of two (the input conversion's
+    exponent arithmetic over a wide range)."""
+    w = wl.small(grid=(40, 12, 6), cuts=((40,), (12,), (6,)), overlap=0, seed=33, n_eps_boxes=2)
+    ctx = context(w)
+    f, _ = seeded_params()
+    ctx.cnn_set_params(f)
+    a = host(ctx.cnn_apply(dev(w.rhs)))
+    assert np.any(a)
+    for p in (400, -400):
+        b = host(ctx.cnn_apply(dev(np.ldexp(w.rhs, p))))
+        assert np.array_equal(b, np.ldexp(a, p)), p
+
+
 def test_cnn_apply_tcgen05_agrees_with_mma_sync():
     """tcgen05 and mma.sync evaluate the same bf16 network; they differ only in
     the fp32 summation order (and the bf16 roundings that flips)."""
