@@ -43,7 +43,7 @@ def _stale(target, deps):
 
 def build(force=False, verbose=False, extra=()):
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(ROOT, "include", "flashmp.h"))
     jobs = []
     objs = []

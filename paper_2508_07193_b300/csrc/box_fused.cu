@@ -30,6 +30,7 @@
 // Rounding: as the three-pass path, the field is held in the 16-bit type
 // between the axis passes and the mode solve runs in fp32.
 #include "fmp_internal.h"
+#include "fp_convert.cuh"
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -152,36 +153,11 @@ __device__ __forceinline__ void st_cluster(uint32_t a, const uint4& v) {
                  : "memory");
 }
 
-// Conversions between float64 and fp32 by integer operations: on this part
-// the float64 pipe runs at 1/64 of the fp32 rate, and a converting
-// instruction occupies it like any float64 operation.
-// f64 -> f32 rounded to odd (truncate, then set the last bit when any dropped
-// bit is set): a later round-to-nearest-even to a 16-bit type, with 16 more
-// bits dropped, then equals the direct rounding of the double. Magnitudes
-// below the fp32 normal range go to zero, above it to infinity.
-__device__ __forceinline__ float f64_to_f32_odd(double v) {
-    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
-    const unsigned sign = static_cast<unsigned>(b >> 32) & 0x80000000u;
-    const int e = static_cast<int>((b >> 52) & 0x7FF);
-    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
-    unsigned f = (static_cast<unsigned>(e - 1023 + 127) << 23) | static_cast<unsigned>(m >> 29) |
-                 static_cast<unsigned>((m & 0x1FFFFFFFull) != 0);
-    f = e < 1023 - 126 ? 0u : f;
-    f = e > 1023 + 127 ? 0x7F800000u : f;
-    f = e == 0x7FF ? (0x7F800000u | (m != 0 ? 0x400000u : 0u)) : f;
-    return __uint_as_float(sign | f);
-}
-// f32 -> f64, exact for normal numbers, infinities and NaN; fp32 subnormals go to zero.
-__device__ __forceinline__ double f32_to_f64(float x) {
-    const unsigned u = __float_as_uint(x);
-    const unsigned e = (u >> 23) & 0xFF;
-    const unsigned long long sign = static_cast<unsigned long long>(u & 0x80000000u) << 32;
-    const unsigned long long mant = static_cast<unsigned long long>(u & 0x7FFFFFu) << 29;
-    unsigned long long d = sign | (static_cast<unsigned long long>(e + 1023 - 127) << 52) | mant;
-    d = e == 0 ? sign : d;
-    d = e == 0xFF ? (sign | (0x7FFull << 52) | mant) : d;
-    return __longlong_as_double(static_cast<long long>(d));
-}
+// float64 <-> fp32 by integer operations (the float64 pipe runs at 1/64 of
+// the fp32 rate). Rounding to odd: the later rounding to the 16-bit type
+// then equals the direct rounding of the double.
+__device__ __forceinline__ float f64_to_f32_odd(double v) { return fmp::f64_to_f32_scaled<true>(v, 0); }
+__device__ __forceinline__ double f32_to_f64(float x) { return fmp::f32_to_f64_scaled(x, 0); }
 
 __device__ __forceinline__ bool edge_wall(int c, int i, int j, int k) {
     return c == 0 ? (j == 0 || k == 0) : c == 1 ? (i == 0 || k == 0) : (i == 0 || j == 0);

@@ -16,6 +16,7 @@
 // tap-flipped weights; the weight gradient is a per-block reduction over
 // voxels on CUDA cores, summed deterministically by a second kernel.
 #include "fmp_internal.h"
+#include "fp_convert.cuh"
 
 #include <cuda_bf16.h>
 
@@ -228,45 +229,22 @@ __global__ void k_cnn_input(const double* __restrict__ r, const double* __restri
     }
 }
 
-// x * 2^k rounded to float (nearest, ties to even) with integer operations
-// only: on this part the float64 pipe runs at 1/64 of the fp32 rate, and a
-// float64 multiply plus a float64 -> float conversion per value would bound
-// the input kernel. Zero and subnormal x, and results below 2^-126, give a
-// signed zero; results above the float range give infinity; inf and NaN stay
-// inf and NaN.
-__device__ __forceinline__ float f64_to_f32_pow2(double x, int k) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-    const int ex = (int)(b >> 52) & 0x7ff;
-    unsigned long long m = b & 0xfffffffffffffull;
-    if (ex == 0x7ff) return __int_as_float(sign | 0x7f800000u | (m ? 0x400000u : 0u));
-    if (ex == 0) return __int_as_float(sign);
-    m += (1ull << 28) - 1ull + ((m >> 29) & 1ull);   // 52 -> 23 fraction bits
-    const int e = ex - 1023 + 127 + k + (int)(m >> 52);   // the carry of a round-up
-    if (e >= 255) return __int_as_float(sign | 0x7f800000u);
-    if (e <= 0) return __int_as_float(sign);
-    return __int_as_float(sign | ((unsigned)e << 23) | ((unsigned)(m >> 29) & 0x7fffffu));
-}
-
 // The same input over the full grid, channel-last with 8 channels per voxel
 // ([vol][8]: r / s, eps / 10, then four zeros): the first tcgen05 layer's input.
-// 1 / s = 2^k m with m in [1, 2): each r is scaled by 2^k in the integer
-// conversion and by m in fp32, then rounded to bf16.
+// 1 / s = 2^k m with m in [1, 2]: each r is scaled by 2^k in the integer
+// conversion to fp32 (the float64 pipe runs at 1/64 of the fp32 rate) and by
+// m in fp32, then rounded to bf16. Values below 2^-126 s give zero.
 __global__ void k_cnn_input8(const double* __restrict__ r, const double* __restrict__ eps_cell, const double* rms,
                              bf16* __restrict__ X, long long n) {
     const double s = *rms;
-    const double inv = s > 0.0 ? 1.0 / s : 0.0;
-    int k = 0;
-    float m = 0.0f;
-    if (inv > 0.0 && inv < INFINITY) {
-        k = (int)((unsigned long long)__double_as_longlong(inv) >> 52) - 1023;   // s is a normal number
-        m = f64_to_f32_pow2(inv, -k);
-    }
+    int k;
+    float m;
+    fmp::split_pow2(s > 0.0 ? 1.0 / s : 0.0, k, m);
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         const __nv_bfloat162 a =
-            __floats2bfloat162_rn(f64_to_f32_pow2(r[e], k) * m, f64_to_f32_pow2(r[n + e], k) * m);
-        const __nv_bfloat162 b = __floats2bfloat162_rn(f64_to_f32_pow2(r[2 * n + e], k) * m,
-                                                       eps_cell ? f64_to_f32_pow2(eps_cell[e], 0) * 0.1f : 0.1f);
+            __floats2bfloat162_rn(fmp::f64_to_f32_scaled<false>(r[e], k) * m, fmp::f64_to_f32_scaled<false>(r[n + e], k) * m);
+        const __nv_bfloat162 b = __floats2bfloat162_rn(fmp::f64_to_f32_scaled<false>(r[2 * n + e], k) * m,
+                                                       eps_cell ? fmp::f64_to_f32_scaled<false>(eps_cell[e], 0) * 0.1f : 0.1f);
         uint4 q;
         q.x = *reinterpret_cast<const uint32_t*>(&a);
         q.y = *reinterpret_cast<const uint32_t*>(&b);
