@@ -271,13 +271,23 @@ __global__ void k_cnn_output(const float* __restrict__ Y, const double* rms, dou
     }
 }
 
-// rms of a vector into *out: per-block partial sums, then one block adds
-// them in block order (deterministic).
-constexpr int kRmsBlocks = 296;
-__global__ void k_rms_part(const double* __restrict__ r, long long n, double* __restrict__ part) {
-    double s = 0.0;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-        s = fma(r[e], r[e], s);
+// rms of a vector into *out: per-block partial sums over a fixed grid (eight
+// blocks per SM, four independent loads in flight per thread), then one warp
+// adds them in a fixed order (deterministic).
+constexpr int kRmsBlocks = 148 * 8;
+__global__ void __launch_bounds__(256) k_rms_part(const double* __restrict__ r, long long n, double* __restrict__ part) {
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (; e + 3 * stride < n; e += 4 * stride) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = __ldg(r + e + u * stride);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = fma(v[u], v[u], a[u]);
+    }
+    for (; e < n; e += stride) a[0] = fma(r[e], r[e], a[0]);
+    double s = (a[0] + a[1]) + (a[2] + a[3]);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     __shared__ double red[32];
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -288,12 +298,13 @@ __global__ void k_rms_part(const double* __restrict__ r, long long n, double* __
         part[blockIdx.x] = t;
     }
 }
+// one warp (launched with 32 threads): lane l adds partials l, l + 32, ...,
+// then a fixed shuffle tree
 __global__ void k_rms_final(const double* __restrict__ part, int nb, long long n, double* out) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double t = 0.0;
-        for (int b = 0; b < nb; ++b) t += part[b];
-        *out = sqrt(t / (double)n);
-    }
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 32) t += part[b];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) *out = sqrt(t / (double)n);
 }
 
 // Loss L = sum (p - t)^2 / sum t^2 and dL/dp into g (two calls: phase 0
