@@ -39,7 +39,7 @@ FP64_NOMINAL_TFLOPS = 1.25   # B300 float64 (vector and tensor) nominal
 # beside each entry. Absent: not captured for this kernel version.
 TRAFFIC_BYTES = {
     ("yee128_ras4x4x4_ol2", "fp64"): 228.9e6,   # transform_fp64_precond_grid128.md
-    ("yee128_ras4x4x4_ol2", "bf16"): 53.34e6,   # fused_bf16_precond_grid128.md
+    ("yee128_ras4x4x4_ol2", "bf16"): 52.70e6,   # fused_bf16_precond_grid128.md
     ("yee128_ras4x4x4_ol2", "fp64_ozaki"): 246.8e6,   # transform_fp64_ozaki_precond_grid128.md
 }
 
