@@ -72,7 +72,7 @@ def test_grid128_solve_true_residual():
     b = w.rhs.reshape(-1)
     true = np.linalg.norm(b - A @ host(x).reshape(-1)) / np.linalg.norm(b)
     # the oracle's own FGMRES(30) on this workload, recorded by
-    # oracle/record_grid128.py: same iteration count within 2, same residual
+    # oracle/record_fgmres.py: same iteration count within 2, same residual
     import json, os
     rec = json.load(open(os.path.join(os.path.dirname(__file__), "..", "oracle", "recorded", "grid128_fgmres.json")))
     assert true <= 1e-8 and abs(info["iters"] - rec["iters"]) <= 2

@@ -99,3 +99,49 @@ def test_upper_diagonal_difference_is_caught(monkeypatch):
     monkeypatch.setattr(cp, "difference", lambda n: -np.eye(n) + np.eye(n, k=-1))
     grid, lo, shape = tcp.BOXES[0]
     _fails(tcp.test_M_plus_lambda_is_the_restricted_double_curl, grid, lo, shape)
+
+
+def test_prolong_with_owned_corner_for_extended_corner_is_caught(monkeypatch):
+    """S_i^0T reading the box solution at (owned corner) instead of (extended
+    corner) offsets: caught by the slot-by-slot prolongation pin."""
+    from oracle import ras
+    import tests.test_oracle_ras as tras
+
+    def bad(z, eb, b):
+        (x0, y0, z0) = b.own_lo
+        (ox0, oy0, oz0), (ox1, oy1, oz1) = b.own_lo, b.own_hi
+        z[:, oz0:oz1, oy0:oy1, ox0:ox1] = eb[:, oz0 - z0:oz1 - z0, oy0 - y0:oy1 - y0, ox0 - x0:ox1 - x0]
+    monkeypatch.setattr(ras, "prolong_owned", bad)
+    _fails(tras.test_prolong_owned_slot_by_slot_on_clipped_ragged_boxes)
+
+
+def test_restrict_with_swapped_wall_masks_is_caught(monkeypatch):
+    """S_i^gamma zeroing Ey's walls on Ex and Ex's on Ey: caught by the
+    slot-by-slot restriction pin."""
+    from oracle import ras
+    import tests.test_oracle_ras as tras
+    orig = ras.box_wall
+
+    def bad(m):
+        w = orig(m)
+        return w[[1, 0, 2]]
+    monkeypatch.setattr(ras, "box_wall", bad)
+    _fails(tras.test_restrict_slot_by_slot_on_clipped_ragged_boxes)
+
+
+def test_restrict_without_clipping_offset_is_caught(monkeypatch):
+    """S_i^gamma copying from the owned corner instead of the extended one
+    (the halo dropped on the low side): caught by the restriction pin."""
+    from oracle import ras
+    import tests.test_oracle_ras as tras
+
+    def bad(r, b):
+        (x0, y0, z0) = b.own_lo
+        m = b.m
+        rb = np.zeros((3, m[2], m[1], m[0]))
+        src = r[:, z0:z0 + m[2], y0:y0 + m[1], x0:x0 + m[0]]
+        rb[:, :src.shape[1], :src.shape[2], :src.shape[3]] = src
+        rb[ras.box_wall(m)] = 0.0
+        return rb
+    monkeypatch.setattr(ras, "restrict", bad)
+    _fails(tras.test_restrict_slot_by_slot_on_clipped_ragged_boxes)

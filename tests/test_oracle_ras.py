@@ -78,3 +78,82 @@ def test_eps_bar_brute_force_over_box_edges():
                     if not on_wall:
                         vals.append(ee[c, k, j, i])
     assert ras.eps_bar(ee, b) == pytest.approx(np.mean(vals), rel=1e-14)
+
+
+def _cut_edges(sizes):
+    """Owned cell intervals [a, a + n) of one axis, from its cut sizes."""
+    out, a = [], 0
+    for n in sizes:
+        out.append((a, a + n))
+        a += n
+    return out
+
+
+RAGGED = ((11, 9, 7), ((4, 3, 4), (5, 4), (2, 5)), 2)
+
+
+def test_restrict_slot_by_slot_on_clipped_ragged_boxes():
+    """S_i^gamma enumerated slot by slot with plain index loops, using neither
+    restrict nor the partition's boxes: every slot of a box's extended array
+    holds the global slot at (extended low corner + local index), the
+    extended corner being the owned corner minus gamma clipped at 0, and the
+    box's own wall slots (local j = 0 or k = 0 for Ex, i = 0 or k = 0 for Ey,
+    i = 0 or j = 0 for Ez) are 0. Global values are distinct, so a shifted
+    or transposed copy fails."""
+    g, cuts, ov = RAGGED
+    nx, ny, nz = g
+    r = np.arange(1, 3 * nz * ny * nx + 1, dtype=np.float64).reshape(3, nz, ny, nx)
+    boxes = ras.partition(g, cuts, ov)
+    t = 0
+    for (az, bz) in _cut_edges(cuts[2]):
+        for (ay, by) in _cut_edges(cuts[1]):
+            for (ax, bx) in _cut_edges(cuts[0]):
+                lo = (max(0, ax - ov), max(0, ay - ov), max(0, az - ov))
+                hi = (min(nx, bx + ov), min(ny, by + ov), min(nz, bz + ov))
+                rb = ras.restrict(r, boxes[t])
+                assert rb.shape == (3, hi[2] - lo[2], hi[1] - lo[1], hi[0] - lo[0])
+                for c in range(3):
+                    for kl in range(hi[2] - lo[2]):
+                        for jl in range(hi[1] - lo[1]):
+                            for il in range(hi[0] - lo[0]):
+                                wall = ((jl == 0 or kl == 0), (il == 0 or kl == 0), (il == 0 or jl == 0))[c]
+                                want = 0.0 if wall else r[c, lo[2] + kl, lo[1] + jl, lo[0] + il]
+                                assert rb[c, kl, jl, il] == want, (t, c, kl, jl, il)
+                t += 1
+    assert t == len(boxes)
+
+
+def test_prolong_owned_slot_by_slot_on_clipped_ragged_boxes():
+    """S_i^0T enumerated slot by slot: each global slot (c, k, j, i) receives
+    the value that its owning box (the one whose owned cell intervals contain
+    (i, j, k), found by walking the cut sizes) holds at local index
+    (i, j, k) - that box's extended low corner. Box-local values encode
+    (box, local slot), so taking the owned corner for the extended one, or
+    writing overlap cells, fails."""
+    g, cuts, ov = RAGGED
+    nx, ny, nz = g
+    boxes = ras.partition(g, cuts, ov)
+    sols = []
+    z = np.zeros((3, nz, ny, nx))
+    for t, b in enumerate(boxes):
+        m = b.m
+        eb = (1000.0 * (t + 1) + np.arange(3 * m[2] * m[1] * m[0], dtype=np.float64)).reshape(3, m[2], m[1], m[0])
+        sols.append(eb)
+        ras.prolong_owned(z, eb, b)
+    ex, ey, ez = (_cut_edges(c) for c in cuts)
+
+    def owner(v, edges):
+        for q, (a, b) in enumerate(edges):
+            if a <= v < b:
+                return q, a
+        raise AssertionError(v)
+    for c in range(3):
+        for k in range(nz):
+            qz, az = owner(k, ez)
+            for j in range(ny):
+                qy, ay = owner(j, ey)
+                for i in range(nx):
+                    qx, ax = owner(i, ex)
+                    t = (qz * len(ey) + qy) * len(ex) + qx
+                    lo = (max(0, ax - ov), max(0, ay - ov), max(0, az - ov))
+                    assert z[c, k, j, i] == sols[t][c, k - lo[2], j - lo[1], i - lo[0]], (c, k, j, i)
