@@ -354,14 +354,20 @@ int fmp_cnn_train(fmp_ctx* ctx, int steps, int crop, float lr,
  *   mx, my, mz: box extents, each in [2, 64]; anything larger (or smaller)
  *               returns FMP_ERR_ARG and launches nothing.
  *   eps_bar, beta: > 0. stream: cudaStream_t (NULL = legacy default stream).
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture. Every call on a device uses the same array, which keeps the last
- * call's contents, so calls that may overlap on the GPU (other streams, or
- * other host threads without ordering) race and corrupt each other's
- * results: order them. Nothing in the array needs clearing: each call writes
- * every value it reads before reading it. Asynchronous on `stream`.
- * Errors: FMP_ERR_ARG, FMP_ERR_CUDA. */
+ * The first call on a device does a one-time set-up with that device
+ * current: it looks up the array's device address and sets the kernels'
+ * shared-memory limits for the largest box. It runs once per device and
+ * CUDA context, so after a device reset (cudaDeviceReset) the next call runs
+ * it again in the new context. Make the first call on each device (and the
+ * first after a reset) before any stream capture. Every call on a device
+ * uses the same array, which keeps the last call's contents, so calls that
+ * may overlap on the GPU (other streams, or other host threads without
+ * ordering) race and corrupt each other's results: order them. Nothing in
+ * the array needs clearing: each call writes every value it reads before
+ * reading it. Asynchronous on `stream`.
+ * Errors: FMP_ERR_ARG; FMP_ERR_CUDA, also returned, with nothing queued and
+ * the error left pending, when a CUDA error from earlier work is pending on
+ * entry (cudaPeekAtLastError). */
 int fmp_box_solve_static(const double* r, double* x, int mx, int my, int mz,
                          double eps_bar, double beta, void* stream);
 

@@ -18,6 +18,8 @@
 // per-call upload is needed.
 #include "fmp_internal.h"
 
+#include <cudaTypedefs.h>
+
 #include <mutex>
 
 #define FMP_STATIC_MAX_EXTENT 64
@@ -31,9 +33,16 @@ constexpr long long kTabLen = 3LL * (2 * FMP_STATIC_MAX_EXTENT * FMP_STATIC_MAX_
 // Shared by every call on a device: [box scratch | tables for x | y | z].
 static __device__ __align__(256) double g_static_scratch[kMaxBox + kTabLen];
 
-// Host-side address of g_static_scratch per device, looked up once per device.
+// Per device: the context the set-up below ran in, and the device address of
+// g_static_scratch in it. A device reset (cudaDeviceReset) ends that context;
+// the next call sees a different current context and runs the set-up again,
+// so no address from the ended context is ever passed to a kernel.
 std::mutex g_mu;
-double* g_addr[128] = {};
+struct DevState {
+    CUcontext ctx = nullptr;
+    double* addr = nullptr;
+};
+DevState g_dev[128];
 
 struct StaticBox {
     int m[3];
@@ -195,20 +204,59 @@ __global__ void __launch_bounds__(kT) k_static_inv_xy(const double* scr, double*
     }
 }
 
-// Device address of g_static_scratch on the current device (looked up once).
+// Shared-memory sizes of the three transform kernels for the largest box.
+constexpr int kSmemXYMax =
+    (int)sizeof(double) * (2 * FMP_STATIC_MAX_EXTENT * FMP_STATIC_MAX_EXTENT + 2 * FMP_STATIC_MAX_EXTENT * FMP_STATIC_MAX_EXTENT);
+constexpr int kSmemZMax =
+    (int)sizeof(double) * (6 * FMP_STATIC_MAX_EXTENT * 32 + 2 * FMP_STATIC_MAX_EXTENT * FMP_STATIC_MAX_EXTENT);
+
+PFN_cuCtxGetCurrent_v4000 ctx_getter() {
+    static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+    }
+    return fn;
+}
+
+// Set-up, once per device and context, under the lock, with the device
+// current: the device address of g_static_scratch (host code cannot use the
+// symbol itself, which names a host-side stand-in) and the kernels' dynamic
+// shared-memory limits for the largest box, so that no call changes them.
 cudaError_t static_scratch(double** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    PFN_cuCtxGetCurrent_v4000 get = ctx_getter();
+    CUcontext ctx = nullptr;
+    if (!get || get(&ctx) != CUDA_SUCCESS) return cudaErrorInitializationError;
+    if (!ctx) {
+        // no context current on this thread yet: cudaSetDevice creates and
+        // binds the device's primary context (it allocates nothing)
+        e = cudaSetDevice(dev);
+        if (e != cudaSuccess) return e;
+        if (get(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorInitializationError;
+    }
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
+    DevState& d = g_dev[dev];
+    if (d.ctx != ctx || !d.addr) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) return e;
-        g_addr[dev] = static_cast<double*>(p);
+        e = cudaFuncSetAttribute(k_static_fwd_xy, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemXYMax);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_static_inv_xy, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemXYMax);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_static_z, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemZMax);
+        if (e != cudaSuccess) return e;
+        d.ctx = ctx;
+        d.addr = static_cast<double*>(p);
     }
-    *out = g_addr[dev];
+    *out = d.addr;
     return cudaSuccess;
 }
 
@@ -221,6 +269,9 @@ extern "C" int fmp_box_solve_static(const double* r, double* x, int mx, int my, 
         mz > FMP_STATIC_MAX_EXTENT)
         return FMP_ERR_ARG;
     if (!(eps_bar > 0.0) || !(beta > 0.0)) return FMP_ERR_ARG;
+    // an error left pending by earlier, unrelated work is the caller's: report
+    // it without queueing anything and without clearing it
+    if (cudaPeekAtLastError() != cudaSuccess) return FMP_ERR_CUDA;
     double* base = nullptr;
     if (static_scratch(&base) != cudaSuccess) { (void)cudaGetLastError(); return FMP_ERR_CUDA; }
     cudaStream_t s = (cudaStream_t)stream;
@@ -231,16 +282,13 @@ extern "C" int fmp_box_solve_static(const double* r, double* x, int mx, int my, 
     for (int a = 0; a < 3; ++a) { B.tab[a] = off; off += 2LL * B.m[a] * B.m[a] + B.m[a]; }
     const size_t sa = sizeof(double) * (2 * mx * my + mx * mx + my * my);
     const size_t sb = sizeof(double) * (6 * mz * 32 + 2 * mz * mz);
-    if (cudaFuncSetAttribute(k_static_fwd_xy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa) ||
-        cudaFuncSetAttribute(k_static_inv_xy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa) ||
-        cudaFuncSetAttribute(k_static_z, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb)) {
-        (void)cudaGetLastError();
-        return FMP_ERR_CUDA;
-    }
     const int mmax = mx > my ? (mx > mz ? mx : mz) : (my > mz ? my : mz);
     k_static_tables<<<dim3((mmax * mmax + kT - 1) / kT, 3), kT, 0, s>>>(base, B);
+    if (cudaGetLastError() != cudaSuccess) return FMP_ERR_CUDA;
     k_static_fwd_xy<<<3 * mz, kT, sa, s>>>(r, base, B);
+    if (cudaGetLastError() != cudaSuccess) return FMP_ERR_CUDA;
     k_static_z<<<(mx * my + 31) / 32, kT, sb, s>>>(base, B, eps_bar, beta);
+    if (cudaGetLastError() != cudaSuccess) return FMP_ERR_CUDA;
     k_static_inv_xy<<<3 * mz, kT, sa, s>>>(base, x, B);
     if (cudaGetLastError() != cudaSuccess) return FMP_ERR_CUDA;
     return FMP_OK;
