@@ -30,11 +30,12 @@ from . import flashmp as F
 from . import workloads as wl
 
 
-def dipole_workload(n, seed=4):
-    """n^3 grid, 16 eps boxes from the seed, 8^3 (or n/32) subdomains, overlap 2."""
+def dipole_workload(n, seed=4, beta=0.25):
+    """n^3 grid, 16 eps boxes from the seed, 8^3 (or n/32) subdomains, overlap
+    2; beta = (dt / 2)^2 in grid units (0.25: dt = 1)."""
     parts = max(2, n // 32)
     return wl.make_workload(f"dipole{n}", (n, n, n), seed=seed, n_eps_boxes=16,
-                            cuts=[wl.even_cuts(n, parts)] * 3, overlap=2)
+                            cuts=[wl.even_cuts(n, parts)] * 3, overlap=2, beta=beta)
 
 
 def current(w, step, dt, dev):
@@ -72,7 +73,7 @@ def save(path, **state):
 def run(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    w = dipole_workload(args.grid)
+    w = dipole_workload(args.grid, beta=getattr(args, "beta", 0.25))
     dt = 2.0 * math.sqrt(w.beta)
     ctx = F.Context(w.grid, w.eps_cell, w.beta, w.cuts, w.overlap, precision=args.precision,
                     rtol=args.rtol, restart=30)
@@ -85,7 +86,7 @@ def run(args):
         step0 = int(ck["step"])
         if ck.get("params") is not None:
             ctx.cnn_set_params(ck["params"])
-    log = {"grid": list(w.grid), "precision": args.precision, "rtol": args.rtol, "phase1": [], "plain": [],
+    log = {"grid": list(w.grid), "beta": w.beta, "precision": args.precision, "rtol": args.rtol, "phase1": [], "plain": [],
            "learned": [], "learned_mode": args.learned_mode}
     # phase 1: plain steps with recorded pairs (E_prev: the field one step back)
     t0 = time.time()
@@ -135,7 +136,7 @@ def run(args):
     for mode, extrap, key in runs:
         E.copy_(E0); H.copy_(H0); E_prev.copy_(P0)
         ctx.cnn_set_params(params_ext if extrap else params_plain)
-        ctx.set_options(use_learned=mode)
+        ctx.set_options(use_learned=mode, experimental=mode >= 2)
         torch.cuda.synchronize()
         t0 = time.time()
         for n in range(max(step0, args.train_until), args.steps):
@@ -166,6 +167,8 @@ def main():
     p.add_argument("--lr", type=float, default=2e-3)
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--precision", default="bf16")
+    p.add_argument("--beta", type=float, default=0.25,
+                   help="(dt / 2)^2 in grid units; the time step is dt = 2 sqrt(beta)")
     p.add_argument("--rtol", type=float, default=1e-8)
     p.add_argument("--learned-mode", type=int, default=1)
     p.add_argument("--extrapolate", action="store_true",

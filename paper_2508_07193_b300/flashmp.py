@@ -153,7 +153,7 @@ class Context:
 
     def __init__(self, grid, eps_cell=None, beta=0.25, cuts=None, overlap=0, *, precision="fp64",
                  krylov="fgmres", restart=30, rtol=1e-8, max_iters=1000, timing=False, use_graph=False,
-                 use_learned=0, stream=None, device=None):
+                 use_learned=0, experimental=False, stream=None, device=None):
         L = lib()
         if not torch.cuda.is_available():
             raise RuntimeError("flashmp needs a CUDA device")
@@ -163,7 +163,7 @@ class Context:
         self.shape = (3, nz, ny, nx)
         self.beta = float(beta)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        o = self._options(precision, krylov, restart, rtol, max_iters, timing, use_graph, use_learned)
+        o = self._options(precision, krylov, restart, rtol, max_iters, timing, use_graph, use_learned, experimental)
         sd = None
         self._cut_arrays = None
         if cuts is not None:
@@ -189,8 +189,14 @@ class Context:
         self._opts = o
 
     @staticmethod
-    def _options(precision, krylov, restart, rtol, max_iters, timing, use_graph, use_learned=0):
+    def _options(precision, krylov, restart, rtol, max_iters, timing, use_graph, use_learned=0,
+                 experimental=False):
         o = default_options()
+        if int(use_learned) >= 2 and not experimental:
+            # the in-FGMRES learned correction measured 2.7x the iterations of
+            # the plain solver on the dipole runs; it stays for experiments
+            raise ValueError("use_learned=2 (learned correction inside FGMRES) is experimental: it measured "
+                             "2.7x the iterations of the plain solver; pass experimental=True to use it")
         o.use_learned = int(use_learned)
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         o.krylov = KRYLOV[krylov] if isinstance(krylov, str) else int(krylov)
@@ -222,7 +228,8 @@ class Context:
     def set_options(self, **kw):
         cur = dict(precision=self._opts.precision, krylov=self._opts.krylov, restart=self._opts.restart,
                    rtol=self._opts.rtol, max_iters=self._opts.max_iters, timing=self._opts.timing,
-                   use_graph=self._opts.use_graph, use_learned=self._opts.use_learned)
+                   use_graph=self._opts.use_graph, use_learned=self._opts.use_learned,
+                   experimental=self._opts.use_learned >= 2)
         cur.update(kw)
         o = self._options(**cur)
         _check(lib().fmp_set_options(self._h, C.byref(o)), "fmp_set_options")

@@ -55,6 +55,6 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     monkeypatch.setenv("RANK", "1")
     monkeypatch.setenv("WORLD_SIZE", "2")
     called = []
-    monkeypatch.setattr(bench, "oracle_iteration_seconds", lambda *a, **k: called.append(1) or (1.0, 0))
+    monkeypatch.setattr(bench, "OracleIteration", lambda *a, **k: called.append(1))
     bench.run_reference(bench.argparse.Namespace(workload="grid128", steps=1, warmup=0))
     assert not called and capsys.readouterr().out == ""

@@ -6,7 +6,7 @@ import pytest
 
 from oracle import box, ras, yee
 from paper_2508_07193_b300 import workloads as wl
-from tests._gpu import FP64_TOL, context, dev, host, rel
+from tests._gpu import FP64_TOL, box_rel2, context, dev, host, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -47,8 +47,10 @@ def test_precond_apply_matches_oracle(w):
     ctx = context(w)
     ee = yee.edge_eps(w.grid, w.eps_cell)
     z = host(ctx.precond_apply(dev(w.rhs)))
-    ref = ras.precond_apply(w.rhs, ras.partition(w.grid, w.cuts, w.overlap), ee, w.beta)
+    boxes = ras.partition(w.grid, w.cuts, w.overlap)
+    ref = ras.precond_apply(w.rhs, boxes, ee, w.beta)
     assert rel(z, ref) <= FP64_TOL
+    assert box_rel2(z, ref, boxes) <= FP64_TOL
     # run twice: scratch reuse must not leak state between applies
     z2 = host(ctx.precond_apply(dev(w.rhs)))
     assert np.array_equal(z, z2)

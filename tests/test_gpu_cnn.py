@@ -105,7 +105,7 @@ def test_learned_cn_steps_solve_to_tolerance(mode):
     g = w.grid
     ee = yee.edge_eps(g, w.eps_cell)
     dt = 2.0 * np.sqrt(w.beta)
-    ctx = context(w, rtol=1e-11, use_learned=mode)
+    ctx = context(w, rtol=1e-11, use_learned=mode, experimental=mode >= 2)
     E = np.zeros_like(w.rhs); H = np.zeros_like(E)
     Ed, Hd = dev(E), dev(H)
     for n in range(3):
@@ -230,3 +230,14 @@ def test_cnn_tcgen05_wait_runs_out_cleanly():
         with pytest.raises(F.FlashMPError) as ei:
             ctx.cnn_set_tc(bad)
         assert "FMP_ERR_ARG" in str(ei.value)
+
+
+def test_in_fgmres_correction_needs_the_experimental_flag():
+    w = wl.small(grid=(16, 14, 12), cuts=((8, 8), (7, 7), (12,)), overlap=2, seed=31, n_eps_boxes=3)
+    with pytest.raises(ValueError):
+        context(w, use_learned=2)
+    ctx = context(w, use_learned=1)
+    with pytest.raises(ValueError):
+        ctx.set_options(use_learned=2)
+    ctx.set_options(use_learned=2, experimental=True)
+    ctx.close()

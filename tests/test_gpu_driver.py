@@ -28,6 +28,32 @@ def test_dipole_run_plain_and_learned_converge(tmp_path):
     assert os.path.exists(A.checkpoint)
 
 
+def test_learned_guess_keeps_the_fallback_promise(tmp_path, record_property):
+    """What the trained network gains over the method without it, on a small
+    dipole run: the same steps from the same state with the plain guess E^n,
+    the learned guess, the extrapolation 2 E^n - E^(n-1) and the learned
+    guess on top of the extrapolation. The iteration deltas are recorded;
+    the fallback (a network guess is kept only when it lowers the starting
+    residual) promises that the learned runs cost at most 1 % more
+    iterations than the runs they start from."""
+    class A:
+        grid, steps, train_until, train_iters, crop, lr, seed = 32, 24, 12, 300, 16, 2e-3, 0
+        precision, rtol, learned_mode, beta = "bf16", 1e-8, 1, 0.25
+        checkpoint = None
+        resume = None
+        out = None
+        extrapolate = True
+    log = D.run(A)
+    it = {k: log[k + "_iters"] for k in ("plain", "learned", "extrap", "learned_extrap")}
+    record_property("iterations_steps_12_to_23", it)
+    record_property("learned_minus_plain_pct", 100.0 * (it["learned"] - it["plain"]) / it["plain"])
+    print("iterations", it)
+    for key in it:
+        assert log[key + "_max_res"] <= 1e-8
+    assert it["learned"] <= math.ceil(1.01 * it["plain"]), it
+    assert it["learned_extrap"] <= math.ceil(1.01 * it["extrap"]), it
+
+
 def test_checkpoint_resume_is_bitwise():
     w = D.dipole_workload(32)
     dt = 2.0 * math.sqrt(w.beta)

@@ -6,14 +6,30 @@ import pytest
 
 from oracle import ras, yee
 from paper_2508_07193_b300 import workloads as wl
-from tests._gpu import context, dev, host, rel
+from tests._gpu import box_rel2, context, dev, host, maxrel, rel2
 
 pytestmark = pytest.mark.gpu
 
-# relative 2-norm error of M^{-1} r against the float64 oracle; each bound
-# is a few times the unit roundoff of the input type (bf16 2^-9, fp16 and
-# tf32 2^-12) accumulated over six rounded GEMM stages
-BOUND = {"bf16": 3e-2, "fp16": 5e-3, "tf32": 5e-3}
+# Error of M^{-1} r against the float64 oracle, about twice the largest
+# measured over these cases and the full-size workloads (measured: bf16
+# 4.5e-3 to 6.3e-3 in 2-norm, up to 1.25e-2 element-wise; fp16 and tf32,
+# which both keep 10 mantissa bits, 6.6e-4 to 9.2e-4 and up to 1.65e-3):
+# BOUND for the relative 2-norm of the whole field and of every box's owned
+# block (BOX_BOUND), MAX_BOUND for max |z - ref| / max |ref|.
+BOUND = {"bf16": 1.25e-2, "fp16": 2e-3, "tf32": 2e-3}
+BOX_BOUND = {"bf16": 1.5e-2, "fp16": 2.5e-3, "tf32": 2.5e-3}
+MAX_BOUND = {"bf16": 2.5e-2, "fp16": 3.5e-3, "tf32": 3.5e-3}
+
+
+def check(z, ref, prec, boxes=None):
+    """2-norm, element-wise and (with boxes) per-box bounds of precision prec."""
+    e2, em = rel2(z, ref), maxrel(z, ref)
+    assert e2 <= BOUND[prec], (prec, e2)
+    assert em <= MAX_BOUND[prec], (prec, em)
+    if boxes is not None:
+        eb = box_rel2(z, ref, boxes)
+        assert eb <= BOX_BOUND[prec], (prec, eb)
+    return e2
 
 CASES = [
     wl.small(),
@@ -32,14 +48,14 @@ def test_mixed_precond_error(prec, w, fused):
     ctx.set_fused(fused)
     assert ctx.get_fused() == (fused, ctx.num_boxes() if fused else 0)
     ee = yee.edge_eps(w.grid, w.eps_cell)
-    ref = ras.precond_apply(w.rhs, ras.partition(w.grid, w.cuts, w.overlap), ee, w.beta)
+    boxes = ras.partition(w.grid, w.cuts, w.overlap)
+    ref = ras.precond_apply(w.rhs, boxes, ee, w.beta)
     z = host(ctx.precond_apply(dev(w.rhs)))
-    err = rel(z, ref)
-    assert err <= BOUND[prec], err
+    check(z, ref, prec, boxes)
     assert np.all(z[wl.edge_wall_mask(w.grid)] == 0.0)
     # linear in r: scaling the input by 1e-6 scales the output (fp16 uses a per-box scale)
     z2 = host(ctx.precond_apply(dev(w.rhs * 1e-6)))
-    assert rel(z2 * 1e6, ref) <= BOUND[prec]
+    check(z2 * 1e6, ref, prec, boxes)
 
 
 def test_mixed_precond_128_sampled_boxes():
@@ -57,7 +73,7 @@ def test_mixed_precond_128_sampled_boxes():
             ras.prolong_owned(part, eb, b)
             (x0, y0, z0), (x1, y1, z1) = b.own_lo, b.own_hi
             sl = (slice(None), slice(z0, z1), slice(y0, y1), slice(x0, x1))
-            assert rel(z[sl], part[sl]) <= BOUND[prec]
+            check(z[sl], part[sl], prec)
         ctx.close()
 
 
@@ -104,13 +120,14 @@ def test_fused_and_three_pass_boxes_in_one_apply(prec):
     ctx = context(w, precision=prec)
     assert ctx.get_fused() == (40, 2)
     ee = yee.edge_eps(w.grid, w.eps_cell)
-    ref = ras.precond_apply(w.rhs, ras.partition(w.grid, w.cuts, w.overlap), ee, w.beta)
+    boxes = ras.partition(w.grid, w.cuts, w.overlap)
+    ref = ras.precond_apply(w.rhs, boxes, ee, w.beta)
     z = host(ctx.precond_apply(dev(w.rhs)))
-    assert rel(z, ref) <= BOUND[prec]
+    check(z, ref, prec, boxes)
     assert np.all(z[wl.edge_wall_mask(w.grid)] == 0.0)
     ctx.set_fused(0)
     z3 = host(ctx.precond_apply(dev(w.rhs)))
-    assert rel(z3, ref) <= BOUND[prec]
+    check(z3, ref, prec, boxes)
 
 
 def test_fused_box_extents_one_to_forty():
@@ -122,9 +139,10 @@ def test_fused_box_extents_one_to_forty():
         ctx = context(w, precision="bf16")
         assert ctx.get_fused()[1] == ctx.num_boxes()
         ee = yee.edge_eps(w.grid, w.eps_cell)
-        ref = ras.precond_apply(w.rhs, ras.partition(w.grid, w.cuts, w.overlap), ee, w.beta)
+        boxes = ras.partition(w.grid, w.cuts, w.overlap)
+        ref = ras.precond_apply(w.rhs, boxes, ee, w.beta)
         z = host(ctx.precond_apply(dev(w.rhs)))
-        assert rel(z, ref) <= BOUND["bf16"], grid
+        check(z, ref, "bf16", boxes)
         ctx.close()
 
 
@@ -148,12 +166,14 @@ def test_precond_256_sampled_boxes_all_precisions():
     boxes = ras.partition(w.grid, w.cuts, w.overlap)
     refs = [_oracle_owned(w, ee, boxes[i]) for i in (0, 273, len(boxes) - 1)]
     r = dev(w.rhs)
-    for prec, bound in (("fp64", 1e-11), ("bf16", BOUND["bf16"]), ("fp16", BOUND["fp16"]),
-                        ("tf32", BOUND["tf32"])):
+    for prec in ("fp64", "bf16", "fp16", "tf32"):
         ctx = context(w, precision=prec)
         z = host(ctx.precond_apply(r))
         for sl, ref in refs:
-            assert rel(z[sl], ref) <= bound, prec
+            if prec == "fp64":
+                assert max(rel2(z[sl], ref), maxrel(z[sl], ref)) <= 1e-11
+            else:
+                check(z[sl], ref, prec)
         ctx.close()
 
 
@@ -172,4 +192,4 @@ def test_uneven_bf16_fused_and_three_pass_boxes():
     z = host(ctx.precond_apply(dev(w.rhs)))
     for i in (small, big):
         sl, ref = _oracle_owned(w, ee, boxes[i])
-        assert rel(z[sl], ref) <= BOUND["bf16"], i
+        check(z[sl], ref, "bf16")
