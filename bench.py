@@ -1,9 +1,15 @@
-"""Benchmark: one Crank-Nicolson FDTD step on the 128^3 Yee workload.
+"""Benchmark: one Crank-Nicolson FDTD step on the 256^3 Yee workload.
 
-Workload (seeded, synthetic): 128^3 cells with PEC walls, eps_r piecewise
-constant over 16 random boxes in [1, 10], beta = 0.25, restricted additive
-Schwarz over 4x4x4 subdomains of 32^3 with overlap 2 (extended extents 34/36),
-restarted FGMRES(30) to a 1e-8 true relative residual, float64 transforms.
+Workload (seeded, synthetic): 256^3 cells with PEC walls (50.3 M unknowns),
+eps_r piecewise constant over 16 random boxes in [1, 10], beta = 0.25,
+restricted additive Schwarz over 8x8x8 subdomains of 32^3 with overlap 2
+(extended extents 34/36), restarted FGMRES(30) to a 1e-8 true relative
+residual, float64 transforms (the plain FP64 form); the same step with the
+preconditioner's transforms in the other precisions is timed beside it
+(`forms`), each with its measured preconditioner error against float64.
+`--workload grid128` runs the 128^3 workload (4x4x4 subdomains),
+`--workload uneven` the 320x256x192 uneven one, and `--case box` times the
+exact solve of the single 32^3 PEC box.
 A step is one fmp_cn_step from E = H = 0 with the impressed current
 J = -b/dt, so that its right-hand side is the seeded uniform field b:
 right-hand-side stencil, the preconditioned Krylov solve (transform box
@@ -32,6 +38,17 @@ sys.path.insert(0, ROOT)
 METRIC = "CN-FDTD step time to 1e-8 residual; subdomain DoF/s vs plain FP64 form"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_NOMINAL_TFLOPS = 1.25   # B300 float64 (vector and tensor) nominal
+# float64 pipe issue rate: 2 lane-operations (an FMA or an add each) per clock
+# per SM (1.25 TFLOP/s nominal / 2 flops per FMA / 148 SMs ~ 2.1 GHz x 2)
+FP64_OPS_PER_CLK_SM = 2
+N_SMS = 148
+SM_MAX_MHZ = 2032.0
+
+
+def fp64_issue_peak_tops(sm_mhz=None):
+    """Float64 operations per second the float64 pipes of all SMs issue at
+    `sm_mhz` (default the maximum SM clock), in units of 1e12."""
+    return FP64_OPS_PER_CLK_SM * N_SMS * (sm_mhz or SM_MAX_MHZ) * 1e6 / 1e12
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one preconditioner apply
 # (all of its kernels) from an ncu capture of the current kernels, per
@@ -39,9 +56,26 @@ FP64_NOMINAL_TFLOPS = 1.25   # B300 float64 (vector and tensor) nominal
 # beside each entry. Absent: not captured for this kernel version.
 TRAFFIC_BYTES = {
     ("yee128_ras4x4x4_ol2", "fp64"): 228.9e6,   # transform_fp64_precond_grid128.md
-    ("yee128_ras4x4x4_ol2", "bf16"): 52.70e6,   # fused_bf16_precond_grid128.md
     ("yee128_ras4x4x4_ol2", "fp64_ozaki"): 246.8e6,   # transform_fp64_ozaki_precond_grid128.md
 }
+
+WORKLOADS = ("grid128", "grid256", "uneven", "box32")
+
+
+def workload(name):
+    from paper_2508_07193_b300 import workloads as wl
+    return {"grid128": wl.grid128, "grid256": wl.grid256, "uneven": wl.grid_uneven, "box32": wl.box32}[name]()
+
+
+def bench_config(w, args):
+    """The `config` object of both arms' JSON lines (same keys and values)."""
+    l2 = (f"inputs exceed L2 across a step ({8 * w.n_slots / 1e6:.0f} MB per field, "
+          f"{61 * 8 * w.n_slots / 1e9:.1f} GB Krylov basis)")
+    return {"workload": w.name, "grid": list(w.grid), "subdomains": [len(c) for c in w.cuts],
+            "overlap": w.overlap, "beta": w.beta,
+            "krylov": "FGMRES(30)" if args.krylov == "fgmres" else "BiCGSTAB",
+            "cuda_graph": bool(args.graph), "rtol": 1e-8, "precision": args.precision, "form": args.form,
+            "l2": l2}
 
 
 # one network evaluation, per voxel: 2 x 27 taps x C_in x C_out for the layers
@@ -65,10 +99,10 @@ def parse():
     p.add_argument("--form", default="yee", choices=["yee", "compact"],
                    help="subdomain form: Yee boxes with PEC walls, or the compact layout with the Woodbury "
                         "boundary correction (float64 only)")
-    p.add_argument("--case", default="step", choices=["step", "precond", "spmv", "cnn"],
+    p.add_argument("--case", default="step", choices=["step", "precond", "spmv", "cnn", "box"],
                    help="precond/spmv/cnn: only W + K applies of that operator (for profiler captures), "
-                        "the K timed with CUDA events")
-    p.add_argument("--workload", default="grid128", choices=["grid128", "grid256", "uneven"])
+                        "the K timed with CUDA events; box: the exact solve of the 32^3 PEC box")
+    p.add_argument("--workload", default="grid256", choices=["grid128", "grid256", "uneven", "box32"])
     p.add_argument("--cnn-mma-sync", action="store_true",
                    help="--case cnn: the mma.sync convolution kernels instead of tcgen05")
     return p.parse_args()
@@ -312,71 +346,111 @@ def orth_flops(n, iters, restart=30):
     return tot
 
 
-def oracle_iteration_seconds(w, n_boxes=None, basis=15):
-    """Time one Arnoldi iteration of the float64 CPU oracle on the workload:
-    the RAS apply over all (or n_boxes of the) subdomains, one sparse SpMV and
-    modified Gram-Schmidt against `basis` vectors (the mean basis size of a
-    restart-30 cycle)."""
-    import numpy as np
+class OracleIteration:
+    """One Arnoldi iteration of the float64 CPU oracle on a workload, as a
+    bounded sample: the oracle's exact box solves of `n_boxes` of the
+    subdomains (their time scaled to all of them), one sparse SpMV with the
+    oracle's assembled operator and modified Gram-Schmidt of the result
+    against `basis` vectors (the mean basis size of a restart-30 cycle).
+    The operator, the partition and the basis are built once (untimed)."""
 
-    from oracle import box as obox, ras, yee
-    ee = yee.edge_eps(w.grid, w.eps_cell)
-    boxes = ras.partition(w.grid, w.cuts, w.overlap)
-    A = yee.system_matrix(w.grid, ee, w.beta)
-    sample = boxes if n_boxes is None else boxes[:n_boxes]
-    x = w.rhs.reshape(-1)
-    V = np.random.default_rng(0).standard_normal((basis, x.size)) / np.sqrt(x.size)
-    t0 = time.perf_counter()
-    for b in sample:
-        obox.exact_solve(ras.restrict(w.rhs, b), ras.eps_bar(ee, b), w.beta)
-    t_pre = (time.perf_counter() - t0) * len(boxes) / len(sample)
-    t0 = time.perf_counter()
-    y = A @ x
-    for i in range(basis):
-        h = float(np.dot(y, V[i]))
-        y = y - h * V[i]
-    t_rest = time.perf_counter() - t0
-    return t_pre + t_rest, t_pre, t_rest, len(sample), len(boxes)
+    def __init__(self, w, n_boxes=8, basis=15):
+        import numpy as np
+
+        from oracle import ras, yee
+        self.w = w
+        self.ee = yee.edge_eps(w.grid, w.eps_cell)
+        self.boxes = ras.partition(w.grid, w.cuts, w.overlap)
+        self.A = yee.system_matrix(w.grid, self.ee, w.beta)
+        self.sample = self.boxes[:: max(1, len(self.boxes) // n_boxes)][:n_boxes]
+        self.x = w.rhs.reshape(-1)
+        rng = np.random.default_rng(0)
+        self.V = [rng.standard_normal(self.x.size) / np.sqrt(self.x.size) for _ in range(basis)]
+
+    def seconds(self):
+        """(total, box-solve part scaled to all boxes, SpMV + MGS part)."""
+        import numpy as np
+
+        from oracle import box as obox, ras
+        w = self.w
+        t0 = time.perf_counter()
+        for b in self.sample:
+            obox.exact_solve(ras.restrict(w.rhs, b), ras.eps_bar(self.ee, b), w.beta)
+        t_pre = (time.perf_counter() - t0) * len(self.boxes) / len(self.sample)
+        t0 = time.perf_counter()
+        y = self.A @ self.x
+        for v in self.V:
+            h = float(np.dot(y, v))
+            y = y - h * v
+        t_rest = time.perf_counter() - t0
+        return t_pre + t_rest, t_pre, t_rest
+
+    def describe(self, t_it, iters, src):
+        return (f"one oracle Arnoldi iteration: {len(self.sample)} of {len(self.boxes)} box solves (scaled to all), "
+                f"sparse SpMV, MGS against {len(self.V)} vectors ({t_it:.2f} s); scaled to {iters} iterations "
+                f"({src})")
 
 
-def recorded_oracle_iters():
-    path = os.path.join(ROOT, "oracle", "recorded", "grid128_fgmres.json")
-    return json.load(open(path))
+def oracle_iters(w, iters_gpu=None):
+    """FGMRES(30) iteration count of the workload for scaling the oracle's
+    per-iteration time: the oracle's own recorded run where one exists
+    (oracle/record_fgmres.py), else the GPU float64 run's count, stated as an
+    extrapolation."""
+    name = {"yee128_ras4x4x4_ol2": "grid128", "yee256_ras8x8x8_ol2": "grid256"}.get(w.name)
+    path = os.path.join(ROOT, "oracle", "recorded", f"{name}_fgmres.json")
+    if name and os.path.exists(path):
+        rec = json.load(open(path))
+        return rec["iters"], f"the oracle's own FGMRES(30) count on this workload, oracle/recorded/{name}_fgmres.json"
+    if iters_gpu is None:
+        raise RuntimeError(f"no recorded oracle iteration count for {w.name}")
+    return iters_gpu, "extrapolation: the GPU float64 run's iteration count (no recorded oracle run)"
 
 
 def run_reference(args):
     """Reference arm: the float64 CPU oracle on the host cores, same workload,
-    metric and unit; one timed step = one oracle Arnoldi iteration, scaled to
-    a full solve by the oracle's recorded FGMRES(30) iteration count."""
-    from paper_2508_07193_b300 import workloads as wl
+    metric, unit and config; one timed step = one sampled oracle Arnoldi
+    iteration, scaled to a full solve by the oracle's recorded FGMRES(30)
+    iteration count on that workload."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    w = {"grid128": wl.grid128, "grid256": wl.grid256, "uneven": wl.grid_uneven}[args.workload]()
-    rec = recorded_oracle_iters()
-    iters = rec["iters"]
+    w = workload(args.workload)
+    iters, src = oracle_iters(w)
+    it = OracleIteration(w)
     for _ in range(args.warmup):
-        oracle_iteration_seconds(w, n_boxes=8)
-    ts = [oracle_iteration_seconds(w, n_boxes=8)[0] for _ in range(args.steps)]
+        it.seconds()
+    ts = [it.seconds()[0] for _ in range(args.steps)]
     t_it = sum(ts) / len(ts)
     nx, ny, nz = w.grid
     dof = 3 * nx * ny * nz
     value = dof / (iters * t_it)
     unit = "DoF/s"
-    sample = (f"per step: the oracle's box solves of 8 of the {w.n_boxes} subdomains (scaled to all), one sparse "
-              f"SpMV and MGS against 15 vectors; scaled to the {iters} FGMRES(30) iterations the oracle itself "
-              f"needs on the 128^3 workload (oracle/recorded/grid128_fgmres.json)")
+    sample = ("per timed step (ms_per_step): " + it.describe(t_it, iters, src) +
+              "; value = DoF / the extrapolated solve time")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": iters * t_it * 1e3, "higher_is_better": True,
+           "warmup": args.warmup, "ms_per_step": t_it * 1e3, "ms_per_solve_extrapolated": iters * t_it * 1e3,
+           "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded eps boxes and uniform rhs)",
-           "config": {"workload": w.name, "grid": list(w.grid), "subdomains": [len(c) for c in w.cuts],
-                      "overlap": w.overlap, "beta": w.beta, "krylov": "FGMRES(30)", "rtol": 1e-8,
-                      "precision": "fp64"},
+           "config": bench_config(w, args),
            "cpu_baseline": {"value": value, "unit": unit, "cores": os.cpu_count(), "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+
+
+def precond_error(z, ref, boxes):
+    """Error of a preconditioner output z against the float64 kernels' ref:
+    relative 2-norm, max |z - ref| / max |ref|, and the largest relative
+    2-norm over the boxes' owned blocks."""
+    d = z - ref
+    worst = 0.0
+    for b in boxes:
+        (x0, y0, z0), n = b["own_lo"], b["own_n"]
+        sl = (slice(None), slice(z0, z0 + n[2]), slice(y0, y0 + n[1]), slice(x0, x0 + n[0]))
+        worst = max(worst, float(d[sl].norm() / ref[sl].norm()))
+    return {"rel_2norm": float(d.norm() / ref.norm()), "max_rel": float(d.abs().max() / ref.abs().max()),
+            "max_box_rel_2norm": worst}
 
 
 def run_ours(args):
@@ -392,7 +466,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = {"grid128": wl.grid128, "grid256": wl.grid256, "uneven": wl.grid_uneven}[args.workload]()
+    w = workload(args.workload)
     nx, ny, nz = w.grid
     dof = 3 * nx * ny * nz
     stream = torch.cuda.current_stream(dev)
@@ -487,17 +561,21 @@ def run_ours(args):
                         "are bound by the integer issue of cutting and recombining digits, not by the tensor pipe",
                 "dense_fp64_equivalent_tflops": flops / (ms_p * 1e-3) / 1e12}
     elif args.precision == "fp64":
-        achieved = flops / (ms_p * 1e-3) / 1e12
-        executed = transform_fp64_executed(ctx) * 2 / (ms_p * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": traffic,
-                "algorithmic_bytes": tb,
+        ops = transform_fp64_executed(ctx)
+        sm_mhz = clocks.get("sm_mhz") or SM_MAX_MHZ
+        peak_ops = fp64_issue_peak_tops(sm_mhz)
+        achieved = ops / (ms_p * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Top/s (float64 operations)",
+                "frac": achieved / peak_ops, "traffic": traffic, "algorithmic_bytes": tb,
                 "kernel": "float64 transform solve (passes A+B+C = one preconditioner apply)",
-                "peak_source": "B300 nominal float64 rate from the recipe (measured DFMA 1.13 TFLOP/s)",
-                "executed": {"tflops": executed, "frac": executed / FP64_NOMINAL_TFLOPS,
-                             "note": "achieved counts the dense 12(mx+my+mz)mxmymz flops; the two-level "
-                                     "folded kernels execute about 40 % of them, executed counts those "
-                                     "(each float64 operation counted as 2 flops, like an FMA)"}}
+                "peak_source": f"float64 issue rate derived from the recipe's unit counts and clocks: "
+                               f"{FP64_OPS_PER_CLK_SM} operations per clock per SM x {N_SMS} SMs x {sm_mhz:.0f} MHz "
+                               f"(the median SM clock sampled in the timed region)",
+                "executed_ops_per_apply": ops,
+                "dense_equivalent_tflops": flops / (ms_p * 1e-3) / 1e12,
+                "note": "achieved counts the float64 operations (FMAs and additions) the two-level folded "
+                        "kernels execute; dense_equivalent_tflops counts the dense 12(mx+my+mz)mxmymz formula, "
+                        "which the folding cuts to about 40 % of its FMAs"}
     else:
         achieved = tb / (ms_p * 1e-3) / 1e9
         kern = ("fused cluster kernel (one 3-CTA cluster per box)" if args.precision != "tf32"
@@ -577,11 +655,7 @@ def run_ours(args):
                   "f64 (preconditioner transforms float64-accurate on bf16 digit planes, exact fp32 accumulation)"
                   if args.precision == "fp64_ozaki" else f"f64 (preconditioner transforms {args.precision})"),
         "data": "synthetic (seeded eps boxes and uniform rhs)",
-        "config": {"workload": w.name, "grid": list(w.grid), "subdomains": [len(c) for c in w.cuts],
-                   "overlap": w.overlap, "beta": w.beta, "krylov": "FGMRES(30)" if args.krylov == "fgmres" else "BiCGSTAB",
-                   "cuda_graph": bool(args.graph), "rtol": 1e-8,
-                   "precision": args.precision, "form": args.form,
-                   "l2": "inputs (50 MB per field, 3.1 GB Krylov basis) exceed L2 across a step"},
+        "config": bench_config(w, args),
         "iters_per_step": iters,
         "true_rel_res_max": true_res,
         "precond_ms": ms_p,
@@ -605,51 +679,59 @@ def run_ours(args):
     ctx.set_options(timing=False)
     out["phase_ms"] = {k: ph[k] for k in ("ms_precond", "ms_spmv", "ms_orth", "ms_total")}
     if args.krylov == "fgmres" and ph["ms_orth"] > 0:
-        of = orth_flops(dof, ph["iters"]) / (ph["ms_orth"] * 1e-3) / 1e12
-        out["roofline_orth"] = {"bound": "alu", "achieved": of, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                                "frac": of / FP64_NOMINAL_TFLOPS,
+        of = orth_flops(dof, ph["iters"]) / 2 / (ph["ms_orth"] * 1e-3) / 1e12
+        pk_ops = fp64_issue_peak_tops(clocks.get("sm_mhz"))
+        ob = orth_flops(dof, ph["iters"]) / 2 * 8 / (ph["ms_orth"] * 1e-3) / 1e9
+        out["roofline_orth"] = {"bound": "alu", "achieved": of, "peak": pk_ops, "unit": "Top/s (float64 FMAs)",
+                                "frac": of / pk_ops, "achieved_gbs": ob, "hbm_frac": ob / hbm,
                                 "kernel": "Gram-Schmidt basis passes k_dots / k_update (one step)",
-                                "note": "one float64 FMA per 8 bytes read: the float64 pipe, not HBM, bounds them"}
-    # the other preconditioner precisions on the same workload, same protocol
+                                "note": "one float64 FMA per 8-byte basis element read: the float64 pipe, not "
+                                        "HBM, bounds them"}
+    # the other preconditioner precisions on the same workload, same protocol,
+    # each with its preconditioner error against the float64 kernels (which
+    # the parity tests hold within 1e-11 of the float64 oracle) on r = b
     if not args.no_forms and args.form == "yee":
         forms = {}
         max_ext = max(max(ctx.box(i)["m"]) for i in range(ctx.num_boxes()))
+        ctx.set_options(precision="fp64")
+        ctx.precond_apply(r, z)
+        z64 = z.clone()
+        owned = [ctx.box(i) for i in range(ctx.num_boxes())]
         for p in ("fp64", "fp64_ozaki", "bf16", "fp16", "tf32"):
             if p == "fp64_ozaki" and max_ext > OZAKI_MAX_EXTENT:
                 continue
             if p == args.precision:
                 forms[p] = {"ms_per_step": ms, "iters": iters[0] if iters else None, "true_rel_res_max": true_res,
                             "precond_ms": ms_p}
-                continue
-            ctx.set_options(precision=p)
-            infos.clear()
-            for _ in range(args.warmup):
-                step()
-            infos.clear()
-            torch.cuda.synchronize()
-            e0.record(stream)
-            for _ in range(args.steps):
-                step()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            fm = e0.elapsed_time(e1) / args.steps
-            for _ in range(3):
+            else:
+                ctx.set_options(precision=p)
+                infos.clear()
+                for _ in range(args.warmup):
+                    step()
+                infos.clear()
+                torch.cuda.synchronize()
+                e0.record(stream)
+                for _ in range(args.steps):
+                    step()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                fm = e0.elapsed_time(e1) / args.steps
+                for _ in range(3):
+                    ctx.precond_apply(r, z)
+                e0.record(stream)
+                for _ in range(n_p):
+                    ctx.precond_apply(r, z)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                forms[p] = {"ms_per_step": fm, "iters": infos[0]["iters"],
+                            "true_rel_res_max": max(i["true_rel_res"] for i in infos),
+                            "precond_ms": e0.elapsed_time(e1) / n_p}
+            if p != "fp64":
+                ctx.set_options(precision=p)
                 ctx.precond_apply(r, z)
-            e0.record(stream)
-            for _ in range(n_p):
-                ctx.precond_apply(r, z)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            forms[p] = {"ms_per_step": fm, "iters": infos[0]["iters"],
-                        "true_rel_res_max": max(i["true_rel_res"] for i in infos),
-                        "precond_ms": e0.elapsed_time(e1) / n_p}
+                forms[p]["precond_err_vs_fp64"] = precond_error(z, z64, owned)
             if p == "fp64_ozaki":
                 forms[p]["mma_tflops"] = ozaki_mma_flops(ctx) / (forms[p]["precond_ms"] * 1e-3) / 1e12
-            if p == "fp64_ozaki" and "fp64" in forms:
-                z_oz = z.clone()
-                ctx.set_options(precision="fp64")
-                ctx.precond_apply(r, z)
-                forms[p]["precond_rel_diff_vs_fp64"] = float((z_oz - z).norm() / z.norm())
         ctx.set_options(precision=args.precision)
         out["forms"] = forms
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -661,37 +743,38 @@ def run_ours(args):
     ctx.close()
 
 
-def cpu_baseline(w, iters_gpu, n_boxes_sample=8):
+def cpu_baseline(w, iters_gpu):
     """The float64 CPU oracle as it stands, timed on a bounded sample of the
     step (one Arnoldi iteration with 8 of the box solves), scaled to the
-    oracle's own recorded iteration count."""
-    t_it, t_pre, t_rest, ns, nb = oracle_iteration_seconds(w, n_boxes=n_boxes_sample)
-    try:
-        iters = recorded_oracle_iters()["iters"]
-        src = "the oracle's recorded FGMRES(30) count"
-    except Exception:
-        iters, src = iters_gpu, "the GPU run's count"
+    oracle's own recorded iteration count (or the GPU run's, stated)."""
+    it = OracleIteration(w)
+    t_it = it.seconds()[0]
+    iters, src = oracle_iters(w, iters_gpu)
     nx, ny, nz = w.grid
     return {"value": 3 * nx * ny * nz / (iters * t_it), "unit": "DoF/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"one oracle Arnoldi iteration: {ns} of {nb} box solves (scaled), sparse SpMV, MGS against 15 "
-                      f"vectors ({t_it:.2f} s); scaled to {iters} iterations ({src})"}
+            "sample": it.describe(t_it, iters, src)}
 
 
 def run_case(args):
-    """W + K applies of one operator on a workload, for profiler captures."""
+    """W + K applies of one operator on a workload, for profiler captures;
+    `--case box` times the exact solve of the single 32^3 PEC box (the plain
+    float64 transform solve of one box, fmp_box_solve)."""
     import numpy as np
     import torch
 
     from paper_2508_07193_b300 import flashmp as F
-    from paper_2508_07193_b300 import workloads as wl
 
-    w = {"grid128": wl.grid128, "grid256": wl.grid256, "uneven": wl.grid_uneven}[args.workload]()
+    name = "box32" if args.case == "box" else args.workload
+    w = workload(name)
     ctx = F.Context(w.grid, w.eps_cell, w.beta, w.cuts, w.overlap, precision=args.precision)
     if args.form != "yee":
         ctx.set_subdomain_form(args.form)
     r = torch.as_tensor(w.rhs, device="cuda")
     z = ctx.empty_field()
-    op = {"precond": ctx.precond_apply, "spmv": ctx.curlcurl_apply, "cnn": ctx.cnn_apply}[args.case]
+    if args.case == "box":
+        op = lambda a, b: ctx.box_solve(0, a, b)
+    else:
+        op = {"precond": ctx.precond_apply, "spmv": ctx.curlcurl_apply, "cnn": ctx.cnn_apply}[args.case]
     if args.case == "cnn":
         ctx.cnn_set_params(np.random.default_rng(0).normal(0.0, 0.05, ctx.cnn_num_params()).astype(np.float32))
         ctx.cnn_set_tc(not args.cnn_mma_sync)
@@ -706,11 +789,19 @@ def run_case(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / max(args.steps, 1)
     out = {"case": args.case, "workload": w.name, "applies": args.warmup + args.steps, "ms_per_apply": ms}
+    nx, ny, nz = w.grid
     if args.case == "cnn":
-        nx, ny, nz = w.grid
         flops = CNN_FLOPS_PER_VOXEL * nx * ny * nz
         out.update({"tflops": flops / (ms * 1e-3) / 1e12, "flops_per_apply": flops,
                     "kernels": "mma.sync" if args.cnn_mma_sync else "tcgen05 (all four layers)"})
+    if args.case in ("box", "precond"):
+        out.update({"subdomain_dof_per_s": 3 * nx * ny * nz / (ms * 1e-3),
+                    "dense_equivalent_tflops": transform_flops(ctx) / (ms * 1e-3) / 1e12,
+                    "precision": args.precision})
+        if args.precision == "fp64":
+            ops = transform_fp64_executed(ctx)
+            out.update({"executed_ops_per_apply": ops, "executed_tops": ops / (ms * 1e-3) / 1e12,
+                        "fp64_issue_frac_at_max_clock": ops / (ms * 1e-3) / 1e12 / fp64_issue_peak_tops()})
     print(json.dumps(out))
     ctx.close()
 
