@@ -105,6 +105,11 @@ def parse():
                    help="precond/spmv/cnn: only W + K applies of that operator (for profiler captures), "
                         "the K timed with CUDA events; box: the exact solve of the 32^3 PEC box")
     p.add_argument("--workload", default="grid256", choices=["grid128", "grid256", "uneven", "box32"])
+    p.add_argument("--fused", type=int, default=None,
+                   help="bf16/fp16: largest extent of the fused cluster kernel (0: none; default 40)")
+    p.add_argument("--streamed", type=int, default=None,
+                   help="bf16/fp16 boxes outside the fused list: 1 one persistent streamed launch (default), "
+                        "0 the three-pass kernels")
     p.add_argument("--cnn-mma-sync", action="store_true",
                    help="--case cnn: the mma.sync convolution kernels instead of tcgen05")
     return p.parse_args()
@@ -480,6 +485,10 @@ def run_ours(args):
         t0 = time.time()
         ctx.set_subdomain_form(args.form)
         setup_s = time.time() - t0
+    if args.fused is not None:
+        ctx.set_fused(args.fused)
+    if args.streamed is not None:
+        ctx.set_streamed(args.streamed)
     tuning = None
     if args.autotune and args.precision != "fp64":
         tuning = ctx.autotune(args.precision, reps=3)
@@ -771,6 +780,10 @@ def run_case(args):
     ctx = F.Context(w.grid, w.eps_cell, w.beta, w.cuts, w.overlap, precision=args.precision)
     if args.form != "yee":
         ctx.set_subdomain_form(args.form)
+    if args.fused is not None:
+        ctx.set_fused(args.fused)
+    if args.streamed is not None:
+        ctx.set_streamed(args.streamed)
     r = torch.as_tensor(w.rhs, device="cuda")
     z = ctx.empty_field()
     if args.case == "box":
@@ -797,6 +810,7 @@ def run_case(args):
         out.update({"tflops": flops / (ms * 1e-3) / 1e12, "flops_per_apply": flops,
                     "kernels": "mma.sync" if args.cnn_mma_sync else "tcgen05 (all four layers)"})
     if args.case in ("box", "precond"):
+        out.update({"fused": ctx.get_fused(), "streamed": ctx.get_streamed()})
         out.update({"subdomain_dof_per_s": 3 * nx * ny * nz / (ms * 1e-3),
                     "dense_equivalent_tflops": transform_flops(ctx) / (ms * 1e-3) / 1e12,
                     "precision": args.precision})

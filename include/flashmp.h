@@ -172,13 +172,37 @@ int fmp_get_tuning(fmp_ctx* ctx, int* slab_group, int* tile_group);
 /* Fused reduced-precision box solve (not in the paper; Algorithm 1 as one
  * thread-block cluster of three CTAs per box, the box resident in shared
  * memory): for bf16 and fp16, boxes whose extents are all <= max_extent take
- * it, the others the three-pass kernels. max_extent in [0, 40]; 0 turns it
- * off; default 40. tf32 always runs the three-pass kernels. Results agree
- * within the reduced-precision error, not bitwise. */
+ * it, the others the streamed solve (below) or the three-pass kernels.
+ * max_extent in [0, 40]; 0 turns it off; default 40. tf32 always runs the
+ * three-pass kernels. Results agree within the reduced-precision error, not
+ * bitwise. */
 int fmp_set_fused(fmp_ctx* ctx, int max_extent);
 /* Current max_extent and (n_fused may be NULL) the number of fused boxes;
  * HOST outputs. */
 int fmp_get_fused(fmp_ctx* ctx, int* max_extent, int* n_fused);
+
+/* Streamed reduced-precision box solve (not in the paper; Algorithm 1 over
+ * subdomains of uneven size, extents 2 .. 80, in one persistent launch): for
+ * bf16 and fp16, the boxes the fused kernel does not take (all boxes with
+ * fmp_set_fused(ctx, 0)) are solved by one launch whose CTAs pull work items
+ * -- (box, component, z-slabs) of the gather and x/y transforms, (box, lines)
+ * of the z transform, 3x3 and inverse z, (box, component, owned z-slabs) of
+ * the inverse y/x and the owned scatter -- from one atomic counter; an item
+ * waits, with a bound of about a second, only for the items of its box's
+ * previous pass, which running CTAs have already taken. mode: 1 on
+ * (default), 0 off (the three-pass kernels, three launches), 2 a test of the
+ * bounded waits (one box's last pass waits for an item that never comes:
+ * its owned cells get NaN and the error word is set). The intermediate
+ * field is held in the 16-bit type, as in the three-pass kernels; results
+ * agree with them within the reduced-precision error. */
+int fmp_set_streamed(fmp_ctx* ctx, int mode);
+/* Current mode and the number of boxes in the streamed list; HOST outputs. */
+int fmp_get_streamed(fmp_ctx* ctx, int* mode, int* n_boxes);
+/* FMP_ERR_CUDA when a dependency wait of the streamed solve ran out since
+ * the last check (the output of that apply holds NaN in the affected box's
+ * owned cells), else FMP_OK; clears the error, and the context stays usable.
+ * fmp_krylov_solve and fmp_cn_step check it themselves. Synchronises. */
+int fmp_stream_check(fmp_ctx* ctx);
 
 /* Checked mode (layout contract): when on, every call that takes a field
  * verifies that its wall slots are zero -- PEC edges for E-shaped fields

@@ -156,7 +156,29 @@ cudaError_t regroup(FmpPlan& p, const std::vector<FmpBox>& boxes, int sg, int tg
     if ((e = upload(&p.d_items_ga, GA, s))) return e;
     if ((e = upload(&p.d_items_gb, GB, s))) return e;
     if ((e = upload(&p.d_items_gc, GC, s))) return e;
-    return F.empty() ? cudaSuccess : upload(&p.d_items_f, F, s);
+    if (!F.empty() && (e = upload(&p.d_items_f, F, s))) return e;
+    // streamed list: the boxes the fused kernel does not take
+    cudaFree(p.d_items_s); cudaFree(p.d_sbox);
+    p.d_items_s = nullptr; p.d_sbox = nullptr;
+    p.n_items_s = 0; p.n_boxes_s = 0;
+    if (p.streamed) {
+        std::vector<int> sel;
+        for (int b = 0; b < (int)boxes.size(); ++b)
+            if (!fusable(boxes[b], fmax)) sel.push_back(b);
+        if (!sel.empty() && fmp_stream_scratch_elems(boxes, sel) <= 4 * p.scratch_doubles) {
+            std::vector<int4> SI;
+            std::vector<FmpStreamBox> SB;
+            fmp_stream_items(boxes, sel, SI, SB, p.streamed == 2 ? 1 : 0);
+            p.n_items_s = (int)SI.size();
+            p.n_boxes_s = (int)sel.size();
+            if ((e = upload(&p.d_items_s, SI, s))) return e;
+            if ((e = upload(&p.d_sbox, SB, s))) return e;
+            if (!p.d_sync_s && (e = cudaMalloc(&p.d_sync_s, sizeof(int) * (1 + 3 * (size_t)boxes.size())))) return e;
+            if (p.grid_s == 0) p.grid_s = std::min(fmp_stream_grid(FMP_PREC_BF16), fmp_stream_grid(FMP_PREC_FP16));
+            if (p.grid_s <= 0) return cudaErrorInvalidConfiguration;
+        }
+    }
+    return cudaSuccess;
 }
 
 cudaError_t make_plan(FmpPlan& p, const std::vector<FmpBox>& boxes, cudaStream_t s) {
@@ -200,6 +222,7 @@ cudaError_t make_plan(FmpPlan& p, const std::vector<FmpBox>& boxes, cudaStream_t
 }
 
 void free_plan(FmpPlan& p) {
+    cudaFree(p.d_items_s); cudaFree(p.d_sbox); cudaFree(p.d_sync_s);
     cudaFree(p.d_boxes); cudaFree(p.d_items_a); cudaFree(p.d_items_b); cudaFree(p.d_items_c);
     cudaFree(p.d_items_ga); cudaFree(p.d_items_gb); cudaFree(p.d_items_gc); cudaFree(p.d_items_f);
     cudaFree(p.d_items_oa); cudaFree(p.d_items_ob); cudaFree(p.d_items_oc);
@@ -233,7 +256,33 @@ int check_walls(fmp_ctx* c, const double* x, int face, int nx, int ny, int nz) {
 int check_edge(fmp_ctx* c, const double* x) { return check_walls(c, x, 0, c->nx, c->ny, c->nz); }
 int check_face(fmp_ctx* c, const double* x) { return check_walls(c, x, 1, c->nx, c->ny, c->nz); }
 
+// FMP_ERR_CUDA when a dependency wait of the streamed solve ran out since
+// the last check (that apply's output holds NaN); clears the word. Synchronises.
+int stream_check(fmp_ctx* c) {
+    int v = 0;
+    FMP_CK(cudaMemcpyAsync(&v, c->d_serr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    FMP_CK(cudaStreamSynchronize(c->stream));
+    if (v == 0) return FMP_OK;
+    FMP_CK(cudaMemsetAsync(c->d_serr, 0, sizeof(int), c->stream));
+    FMP_CK(cudaStreamSynchronize(c->stream));
+    return FMP_ERR_CUDA;
+}
+
+bool uses_stream(const fmp_ctx* c) {
+    return (c->opt.precision == FMP_PREC_BF16 || c->opt.precision == FMP_PREC_FP16) && c->ras.n_items_s > 0 &&
+           c->subdomain_form != FMP_FORM_COMPACT;
+}
+
+int krylov_dispatch_inner(fmp_ctx* c, const double* b, double* x, fmp_solve_info* info);
+
 int krylov_dispatch(fmp_ctx* c, const double* b, double* x, fmp_solve_info* info) {
+    const int rc = krylov_dispatch_inner(c, b, x, info);
+    if (uses_stream(c))
+        if (int rs = stream_check(c)) return rs;
+    return rc;
+}
+
+int krylov_dispatch_inner(fmp_ctx* c, const double* b, double* x, fmp_solve_info* info) {
     if (c->opt.krylov == FMP_KRYLOV_BICGSTAB) return fmp_bicgstab(c, b, x, info);
     const int rc = fmp_fgmres(c, b, x, info);
     // the in-FGMRES learned correction: report a convolution that gave up
@@ -279,11 +328,18 @@ int fmp_precond_gated(fmp_ctx* c, const double* r, double* z, const double* gate
             const int w = c->opt.precision == FMP_PREC_BF16 ? 0 : c->opt.precision == FMP_PREC_FP16 ? 1 : 2;
             const FmpPlan& p = c->ras;
             // bf16 / fp16: boxes of the fused list go through one cluster each,
-            // the rest through the three-pass kernels; tf32: all three-pass
+            // the rest through one persistent streamed launch (or, with the
+            // streamed solve off, the three-pass kernels); tf32: all three-pass
             const bool fused = c->opt.precision != FMP_PREC_TF32 && p.n_items_f > 0;
+            const bool streamed = c->opt.precision != FMP_PREC_TF32 && p.n_items_s > 0;
             const int na = fused ? p.n_ga_rest : p.n_items_ga, nb = fused ? p.n_gb_rest : p.n_items_gb,
                       nc = fused ? p.n_gc_rest : p.n_items_gc;
-            if (na + nb + nc > 0) {
+            if (streamed) {
+                int nk = 0;
+                FMP_CK(fmp_launch_stream(c->opt.precision, p, c->d_tab_mp[w], c->d_tabs, r, z, c->d_scratch, c->d_serr,
+                                         c->nx, c->ny, c->nz, c->beta, c->stream, gate, &nk));
+                c->launches += nk;
+            } else if (na + nb + nc > 0) {
                 int nk = 0;
                 FMP_CK(fmp_launch_transform_solve_mixed(c->opt.precision, p, c->d_tab_mp[w], c->d_tabs, r, z,
                                                         c->d_scratch, c->d_bscale, c->nx, c->ny, c->nz, c->beta,
@@ -497,10 +553,13 @@ int fmp_setup(fmp_ctx** out, fmp_grid g, const double* eps_cell, double beta, co
                                  c->stream));
     }
     SETUP_CK(fmp_launch_eps_edge(eps_cell, c->d_eps_edge, g.nx, g.ny, g.nz, c->stream));
+    SETUP_CK(fmp_stream_init());   // before the plans: their launch grid comes from its occupancy
     SETUP_CK(make_plan(c->ras, boxes, c->stream));
     SETUP_CK(fmp_transform_init_fp64(c->ras));
     SETUP_CK(fmp_transform_init_mixed(c->ras));
     SETUP_CK(fmp_fused_init());
+    SETUP_CK(cudaMalloc(&c->d_serr, sizeof(int)));
+    SETUP_CK(cudaMemsetAsync(c->d_serr, 0, sizeof(int), c->stream));
     SETUP_CK(fmp_transform_init_ozaki());
     SETUP_CK(fmp_stencil_init());
     SETUP_CK(cudaMalloc(&c->d_bscale, sizeof(double) * boxes.size()));
@@ -553,6 +612,7 @@ void fmp_destroy(fmp_ctx* c) {
     cudaFree(c->d_tab_oz);
     cudaFree(c->d_check);
     cudaFree(c->d_bscale);
+    cudaFree(c->d_serr);
     cudaFree(c->d_eps_cell);
     cudaFree(c->d_tmp3); cudaFree(c->d_tmp4); cudaFree(c->d_tmp5);
     fmp_cnn_free(c);
@@ -645,6 +705,29 @@ int fmp_get_fused(fmp_ctx* c, int* max_extent, int* n_fused) {
     *max_extent = c->ras.fused_max;
     if (n_fused) *n_fused = c->ras.n_items_f;
     return FMP_OK;
+}
+
+int fmp_set_streamed(fmp_ctx* c, int mode) {
+    if (!valid_ctx(c) || mode < 0 || mode > 2) return FMP_ERR_ARG;
+    if (int rc = latched(c)) return rc;
+    if (mode == c->ras.streamed) return FMP_OK;
+    c->ras.streamed = mode;
+    FMP_CK(regroup(c->ras, c->h_boxes, c->ras.slab_group, c->ras.tile_group, c->ras.fused_max, c->stream));
+    fmp_invalidate_graphs(c);
+    return FMP_OK;
+}
+
+int fmp_get_streamed(fmp_ctx* c, int* mode, int* n_boxes) {
+    if (!valid_ctx(c) || !mode || !n_boxes) return FMP_ERR_ARG;
+    *mode = c->ras.streamed;
+    *n_boxes = c->ras.n_boxes_s;
+    return FMP_OK;
+}
+
+int fmp_stream_check(fmp_ctx* c) {
+    if (!valid_ctx(c)) return FMP_ERR_ARG;
+    if (int rc = latched(c)) return rc;
+    return stream_check(c);
 }
 
 int fmp_get_tuning(fmp_ctx* c, int* slab_group, int* tile_group) {

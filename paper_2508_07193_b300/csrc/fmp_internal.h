@@ -112,6 +112,15 @@ __host__ __device__ inline int fold3_column(const Fold3& f, int c, int q) {
     return f.off + q;
 }
 
+// Per box of the streamed reduced-precision list (box_stream.cu): offset of
+// its [3][mz][my][round_up(mx, 8)] 16-bit scratch (elements) and the item
+// counts of its passes A and B that its B and C items wait for.
+struct FmpStreamBox {
+    long long soff;
+    int need_a;
+    int need_b;
+};
+
 // Launch-shape description of one batched transform solve (the three passes).
 struct FmpPlan {
     FmpBox* d_boxes = nullptr;  // device array of boxes
@@ -148,6 +157,16 @@ struct FmpPlan {
     int fused_yz_max = 0;       // largest y or z extent among them
     int max_m[3] = {0, 0, 0};
     long long scratch_doubles = 0;
+    // streamed reduced-precision solve (bf16 / fp16): one persistent launch
+    // over the boxes the fused kernel does not take (all of them without
+    // it); items (box, pass * 4 + comp, first, count) in pass order
+    int streamed = 1;                     // 0 off (three-pass kernels), 1 on, 2 test of the bounded waits
+    int4* d_items_s = nullptr;
+    int n_items_s = 0;
+    FmpStreamBox* d_sbox = nullptr;
+    int* d_sync_s = nullptr;              // next item, per-box A and B items done, fp16 box maxima (zeroed per apply)
+    int grid_s = 0;                       // resident CTAs of the persistent kernel
+    int n_boxes_s = 0;                    // boxes in the streamed list
     int slab_group = FMP_MP_SLAB_GROUP;   // tuning of the grouped lists
     int tile_group = FMP_MP_TILE_GROUP;
     int fused_max = FMP_FUSED_MAX;        // boxes with every extent <= this are fused (0: none)
@@ -178,6 +197,7 @@ struct fmp_ctx {
     void* d_tab_mp[3] = {};       // reduced-precision tables: bf16, fp16, tf32 (same layout)
     uint32_t* d_tab_oz = nullptr; // digit-plane tables of the digit-split float64 transforms (fragment order)
     double* d_bscale = nullptr;   // per-box scale factors (fp16 transforms)
+    int* d_serr = nullptr;        // error word of the streamed solve (a dependency wait ran out)
     double* d_eps_cell = nullptr; // cell permittivity [nz][ny][nx] (null: eps = 1)
     FmpCnn* cnn = nullptr;        // learned initial guess / correction (created on first use)
     FmpCompact* compact = nullptr;   // compact-layout boxes with the Woodbury correction
@@ -262,6 +282,17 @@ cudaError_t fmp_launch_transform_solve_mixed(int precision, const FmpPlan& p, co
                                              int ny, int nz, double beta, cudaStream_t s, const double* gate, int na,
                                              int nb, int nc, int* nk);
 cudaError_t fmp_fused_init();
+// Streamed bf16 / fp16 solve of the boxes of the plan's streamed list: one
+// persistent launch (box_stream.cu) after a reset of its counters.
+cudaError_t fmp_stream_init();
+void fmp_stream_items(const std::vector<FmpBox>& boxes, const std::vector<int>& sel, std::vector<int4>& items,
+                      std::vector<FmpStreamBox>& sb, int test_extra);
+long long fmp_stream_scratch_elems(const std::vector<FmpBox>& boxes, const std::vector<int>& sel);
+int fmp_stream_grid(int precision);
+// Kernels launched (the fp16 box maxima, the solve) in *nk.
+cudaError_t fmp_launch_stream(int precision, const FmpPlan& p, const void* tabs, const double* tabs64,
+                              const double* r, double* z, void* scratch, int* err, int nx, int ny, int nz, double beta,
+                              cudaStream_t s, const double* gate, int* nk);
 // bf16 / fp16 solve of the boxes of the fused list, one cluster of three CTAs
 // each (fp16 computes its per-box scale inside).
 cudaError_t fmp_launch_fused(int precision, const FmpPlan& p, const void* tabs, const double* tabs64, const double* r,

@@ -90,6 +90,9 @@ def lib():
         "fmp_set_subdomain_form": (_I, [_P, _I]),
         "fmp_get_subdomain_form": (_I, [_P, C.POINTER(_I), C.POINTER(C.c_longlong)]),
         "fmp_get_fused": (_I, [_P, C.POINTER(_I), C.POINTER(_I)]),
+        "fmp_set_streamed": (_I, [_P, _I]),
+        "fmp_get_streamed": (_I, [_P, C.POINTER(_I), C.POINTER(_I)]),
+        "fmp_stream_check": (_I, [_P]),
         "fmp_get_box": (_I, [_P, _I, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I),
                              C.POINTER(_D)]),
         "fmp_curlcurl_apply": (_I, [_P, _P, _P, _D, _D]),
@@ -281,6 +284,22 @@ class Context:
         a, n = C.c_int(), C.c_int()
         _check(lib().fmp_get_fused(self._h, C.byref(a), C.byref(n)), "fmp_get_fused")
         return a.value, n.value
+
+    def set_streamed(self, mode):
+        """bf16 / fp16 boxes outside the fused list: 1 one persistent streamed
+        launch (default), 0 the three-pass kernels, 2 a test of its bounded
+        waits (fmp_set_streamed)."""
+        _check(lib().fmp_set_streamed(self._h, int(mode)), "fmp_set_streamed")
+
+    def get_streamed(self):
+        m, n = C.c_int(), C.c_int()
+        _check(lib().fmp_get_streamed(self._h, C.byref(m), C.byref(n)), "fmp_get_streamed")
+        return m.value, n.value
+
+    def stream_check(self):
+        """FMP_OK, or FMP_ERR_CUDA when a wait of the streamed solve ran out
+        since the last check (returned, not raised; fmp_stream_check)."""
+        return lib().fmp_stream_check(self._h)
 
     def autotune(self, precision="bf16", reps=5, cache=None):
         """Pick the fastest fused setting and work-list grouping for

@@ -73,4 +73,6 @@ def test_setup_rejects_bad_arguments_before_touching_the_device(so):
     # null context
     assert L.fmp_precond_apply(None, None, None) == F.FMP_ERR_ARG
     assert L.fmp_krylov_solve(None, None, None, None) == F.FMP_ERR_ARG
+    assert L.fmp_set_streamed(None, 1) == F.FMP_ERR_ARG
+    assert L.fmp_stream_check(None) == F.FMP_ERR_ARG
     L.fmp_destroy(None)
