@@ -238,7 +238,8 @@ int fmp_get_subdomain_form(fmp_ctx* ctx, int* form, long long* bytes);
 /* Autotuner: time `reps` reduced-precision preconditioner applies (precision
  * FMP_PREC_TF32, _FP16 or _BF16) with CUDA events on the context's stream for
  * the fused kernel on and off (bf16 / fp16) and every grouping in
- * {1,2,4,8} x {1,2,4,8} of the boxes left to the three-pass kernels, keep the
+ * {1,2,4,8} x {1,2,4,8} of the boxes left to the three-pass kernels (one
+ * grouping only where the streamed solve takes those boxes), keep the
  * fastest, and return result[0] = slab group, result[1] = tile group,
  * result[2] = microseconds per apply, result[3] = fused max_extent (HOST
  * int[4]). Uses the context's own buffers; synchronises. */

@@ -756,7 +756,10 @@ int fmp_autotune(fmp_ctx* c, int precision, int reps, int* result) {
             for (int b = 0; b < 4; ++b) {
                 FMP_CK(regroup(c->ras, c->h_boxes, cand[a], cand[b], fopt[f], c->stream));
                 const bool all_fused = precision != FMP_PREC_TF32 && c->ras.n_ga_rest == 0 && c->ras.n_items_f > 0;
-                if (all_fused && (a > 0 || b > 0)) continue;   // the grouping does not apply
+                // bf16 / fp16 boxes outside the fused list go to the streamed
+                // solve when it is on: the grouping does not apply either
+                const bool streamed = precision != FMP_PREC_TF32 && c->ras.n_items_s > 0;
+                if ((all_fused || streamed) && (a > 0 || b > 0)) continue;
                 int rc = fmp_precond(c, c->d_eps_edge, c->d_tmp2);   // warm-up; any nonzero field will do
                 if (rc != FMP_OK) { c->opt.precision = saved; return rc; }
                 FMP_CK(cudaEventRecord(e0, c->stream));
