@@ -8,6 +8,7 @@ to this file so that it ships with the source tree.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import hashlib
 import os
 import shutil
 import subprocess
@@ -34,24 +35,45 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def _stale(target, deps):
-    if not os.path.exists(target):
+def _digest(paths, flags):
+    """SHA-256 of the files' contents and the compile flags."""
+    h = hashlib.sha256(" ".join(flags).encode())
+    for p in paths:
+        h.update(p.encode())
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def _stale(target, digest):
+    """The target is missing, or was built from other contents than those
+    that give `digest` (recorded beside it): a shipped library newer than its
+    sources is rebuilt all the same when they differ."""
+    stamp = target + ".sha256"
+    if not os.path.exists(target) or not os.path.exists(stamp):
         return True
-    t = os.path.getmtime(target)
-    return any(os.path.getmtime(d) > t for d in deps)
+    with open(stamp) as f:
+        return f.read().strip() != digest
+
+
+def _stamp(target, digest):
+    with open(target + ".sha256", "w") as f:
+        f.write(digest + "\n")
 
 
 def build(force=False, verbose=False, extra=()):
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
+    headers = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh")))
     headers.append(os.path.join(ROOT, "include", "flashmp.h"))
     jobs = []
     objs = []
+    digests = {}
     for src in sources():
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
-        if force or _stale(obj, [src] + headers):
-            jobs.append([nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj])
+        digests[obj] = _digest([src] + headers, ARCH + FLAGS + list(extra))
+        if force or _stale(obj, digests[obj]):
+            jobs.append(([nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj], obj))
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -61,11 +83,18 @@ def build(force=False, verbose=False, extra=()):
             print(r.stdout + r.stderr)
         return r
 
+    def compile_one(job):
+        cmd, obj = job
+        run(cmd)
+        _stamp(obj, digests[obj])
+
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
-        list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
+        list(ex.map(compile_one, jobs))
+    lib_digest = hashlib.sha256("".join(digests[o] for o in objs).encode()).hexdigest()
+    if force or jobs or _stale(LIB, lib_digest):
         # cuSOLVER: the set-up Cholesky of the compact-layout correction matrices
         run([nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcusolver"])
+        _stamp(LIB, lib_digest)
     return LIB
 
 
