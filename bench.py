@@ -110,6 +110,8 @@ def parse():
     p.add_argument("--streamed", type=int, default=None,
                    help="bf16/fp16 boxes outside the fused list: 1 one persistent streamed launch (default), "
                         "0 the three-pass kernels")
+    p.add_argument("--orth", default=None, choices=["fixed", "float64"],
+                   help="Gram-Schmidt arithmetic of FGMRES: float64 FMAs (default) or exact fixed point")
     p.add_argument("--cnn-mma-sync", action="store_true",
                    help="--case cnn: the mma.sync convolution kernels instead of tcgen05")
     return p.parse_args()
@@ -489,6 +491,8 @@ def run_ours(args):
         ctx.set_fused(args.fused)
     if args.streamed is not None:
         ctx.set_streamed(args.streamed)
+    if args.orth is not None:
+        ctx.set_orth(args.orth == "fixed")
     tuning = None
     if args.autotune and args.precision != "fp64":
         tuning = ctx.autotune(args.precision, reps=3)

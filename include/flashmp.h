@@ -181,6 +181,20 @@ int fmp_set_fused(fmp_ctx* ctx, int max_extent);
  * HOST outputs. */
 int fmp_get_fused(fmp_ctx* ctx, int* max_extent, int* n_fused);
 
+/* Gram-Schmidt arithmetic of FGMRES (Table 3's dots and AXPYs per
+ * iteration): fixed_point = 0 (default) runs the float64 FMA passes;
+ * fixed_point = 1 runs the basis dot and update passes with exact 64-bit
+ * integer products on fixed-point copies of the basis vectors (each relative
+ * to its own largest element; the float64 basis stays the preconditioner's
+ * input; 8 more bytes per basis slot), off the float64 pipe: every product
+ * is exact, each dot is rounded to float64 once per thread, each update
+ * correction once per element. On this part the integer passes measured
+ * slower than the float64 ones (the conversions and 64 x 64-bit multiplies
+ * cost more issue slots than the float64 FMAs they replace). Results agree
+ * to rounding, not bitwise. */
+int fmp_set_orth(fmp_ctx* ctx, int fixed_point);
+int fmp_get_orth(fmp_ctx* ctx, int* fixed_point);
+
 /* Streamed reduced-precision box solve (not in the paper; Algorithm 1 over
  * subdomains of uneven size, extents 2 .. 80, in one persistent launch): for
  * bf16 and fp16, the boxes the fused kernel does not take (all boxes with
@@ -316,9 +330,12 @@ int fmp_cn_step_guess(fmp_ctx* ctx, double* E, double* H, const double* J, doubl
  * s = sqrt(mean r^2); the output is multiplied by s. Parameters are float32,
  * per layer W[co][ci][3][3][3] then b[co], layers in order. With
  * fmp_options.use_learned = 1 fmp_cn_step starts the solve from
- * E^n + N(R - A E^n) when that lowers the residual (else from E^n, reported
- * as used_fallback = 1); with use_learned = 2 FGMRES also adds
- * N(v - A M^{-1} v) to every preconditioner output. The network is created
+ * g + N(R - A g), g the plain guess E^n (or, with fmp_cn_step_guess, the
+ * extrapolation 2 E^n - E^(n-1)), when that at least halves the starting
+ * residual; otherwise from g itself, reported as used_fallback = 1 (smaller
+ * reductions were measured to cost iterations). With use_learned = 2
+ * (experimental; it measured 2.7x the iterations of the plain solver) FGMRES
+ * also adds N(v - A M^{-1} v) to every preconditioner output. The network is created
  * (Kaiming-uniform, fixed seed) on first use. */
 
 /* Number of float32 parameters of the network. */

@@ -607,6 +607,7 @@ void fmp_destroy(fmp_ctx* c) {
     cudaFree(c->d_eps_edge); cudaFree(c->d_tabs); cudaFree(c->d_scratch); cudaFree(c->d_scratch1);
     cudaFree(c->d_modeinv);
     cudaFree(c->d_V); cudaFree(c->d_Z); cudaFree(c->d_w); cudaFree(c->d_tmp); cudaFree(c->d_tmp2);
+    cudaFree(c->d_X); cudaFree(c->d_vmax);
     cudaFree(c->d_partials); cudaFree(c->d_state); cudaFree(c->d_ticket);
     for (int t = 0; t < 3; ++t) cudaFree(c->d_tab_mp[t]);
     cudaFree(c->d_tab_oz);
@@ -704,6 +705,22 @@ int fmp_get_fused(fmp_ctx* c, int* max_extent, int* n_fused) {
     if (!valid_ctx(c) || !max_extent) return FMP_ERR_ARG;
     *max_extent = c->ras.fused_max;
     if (n_fused) *n_fused = c->ras.n_items_f;
+    return FMP_OK;
+}
+
+int fmp_set_orth(fmp_ctx* c, int fixed_point) {
+    if (!valid_ctx(c) || fixed_point < 0 || fixed_point > 1) return FMP_ERR_ARG;
+    if (int rc = latched(c)) return rc;
+    if (fixed_point == c->gs_fixed) return FMP_OK;
+    FMP_CK(cudaStreamSynchronize(c->stream));
+    c->gs_fixed = fixed_point;
+    fmp_invalidate_graphs(c);
+    return FMP_OK;
+}
+
+int fmp_get_orth(fmp_ctx* c, int* fixed_point) {
+    if (!valid_ctx(c) || !fixed_point) return FMP_ERR_ARG;
+    *fixed_point = c->gs_fixed;
     return FMP_OK;
 }
 
@@ -911,7 +928,7 @@ int fmp_cn_step_guess(fmp_ctx* c, double* E, double* H, const double* J, double 
     }
     int fallback = 0;
     if (c->opt.use_learned >= 1) {
-        // learned initial guess x0 = E^n + N(R - A E^n), kept only if it lowers the residual
+        // learned initial guess x0 = g + N(R - A g) on the plain or extrapolated guess g
         FMP_CK(fmp_ensure_krylov(c));
         if (!c->d_tmp3) FMP_CK(cudaMalloc(&c->d_tmp3, sizeof(double) * c->n_slots));
         FMP_CK(fmp_cnn_create(c));
@@ -927,8 +944,17 @@ int fmp_cn_step_guess(fmp_ctx* c, double* E, double* H, const double* J, double 
         const double n1 = fmp_norm(c, c->d_tmp3, &err);
         FMP_CK(err);
         if (int rc = fmp_cnn_check(c)) return rc;
-        if (!(n1 < n0)) {   // includes NaN: revert to the plain guess
-            FMP_CK(cudaMemcpyAsync(E, Eold, sizeof(double) * c->n_slots, cudaMemcpyDeviceToDevice, c->stream));
+        // kept only when it at least halves the starting residual: smaller
+        // reductions were measured to cost iterations (the network's error
+        // converges more slowly than what it removes); NaN fails the test too.
+        // The fallback is the guess the network started from.
+        if (!(n1 < 0.5 * n0)) {
+            if (E_prev) {
+                ++c->launches;
+                FMP_CK(fmp_launch_extrapolate(E, Eold, E_prev, (long long)c->n_slots, c->stream));
+            } else {
+                FMP_CK(cudaMemcpyAsync(E, Eold, sizeof(double) * c->n_slots, cudaMemcpyDeviceToDevice, c->stream));
+            }
             fallback = 1;
         }
     }

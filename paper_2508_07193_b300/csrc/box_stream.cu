@@ -138,10 +138,6 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
     return v;
 }
 
-__device__ __forceinline__ bool edge_wall(int c, int i, int j, int k) {
-    return c == 0 ? (j == 0 || k == 0) : c == 1 ? (i == 0 || k == 0) : (i == 0 || j == 0);
-}
-
 // B fragments of n-tile n, k16 step s from a table in shared memory (rows of
 // kLT elements). TRANS = false: Bt[n][k] = T[n][k] (forward transform, modes
 // from positions); TRANS = true: Bt[n][k] = T[k][n] (inverse, positions from
@@ -357,12 +353,15 @@ __device__ void pass_a(const StreamArgs& A, int bi, const FmpBox& B, long long s
             const int q = q0 + u * kW;
             const int sl = q / MYp, y = q - sl * MYp, kz = z0 + sl;
             const double* sp = src0 + ((long long)kz * A.ny + y) * A.nx;
-            const bool row = q < zn * MYp && y < my;
+            // box walls: Ex rows y = 0 or z = 0, Ey rows z = 0 and column x = 0,
+            // Ez rows y = 0 and column x = 0
+            const bool row = q < zn * MYp && y < my && !(c != 1 && y == 0) && !(c != 2 && kz == 0);
+            const int x_first = c != 0 ? 1 : 0;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int x = 2 * (lane + 32 * h);
-                v[u][h][0] = row && x < mx && !edge_wall(c, x, y, kz) ? __ldg(sp + x) : 0.0;
-                v[u][h][1] = row && x + 1 < mx && !edge_wall(c, x + 1, y, kz) ? __ldg(sp + x + 1) : 0.0;
+                v[u][h][0] = row && x < mx && x >= x_first ? __ldg(sp + x) : 0.0;
+                v[u][h][1] = row && x + 1 < mx ? __ldg(sp + x + 1) : 0.0;
             }
         }
 #pragma unroll
@@ -426,7 +425,7 @@ __device__ void pass_b(const StreamArgs& A, const FmpBox& B, long long soff, int
         const int a = q / kMaxP, k = q - a * kMaxP;
         const int ma = a == 0 ? mx : a == 1 ? my : mz;
         const int so = a == 0 ? B.sig_off[0] : a == 1 ? B.sig_off[1] : B.sig_off[2];
-        sig[q] = k < ma ? (float)A.tabs64[so + k] : 0.f;
+        sig[q] = k < ma ? fmp::f64_to_f32_scaled<false>(A.tabs64[so + k], 0) : 0.f;
     }
     E* scr = reinterpret_cast<E*>(A.scratch) + soff;
     // this thread's octet slot is fixed (kT is a multiple of kQ)
@@ -452,7 +451,8 @@ __device__ void pass_b(const StreamArgs& A, const FmpBox& B, long long soff, int
     __syncthreads();
     // per-mode 3x3 (Eq. 12): e = (r + (beta / eps_bar) sigma (sigma . r)) / (eps_bar + beta |sigma|^2)
     {
-        const float eb = (float)B.eps_bar, bt = (float)A.beta, beb = (float)(A.beta / B.eps_bar);
+        const float eb = fmp::f64_to_f32_scaled<false>(B.eps_bar, 0), bt = fmp::f64_to_f32_scaled<false>(A.beta, 0);
+        const float beb = bt / eb;
         for (int t = threadIdx.x; t < mz * nl; t += kT) {
             const int kz = t / nl, q = t - kz * nl;
             const int l = l0 + q, ky = l / NXo, xo = l - ky * NXo;
@@ -473,7 +473,9 @@ __device__ void pass_b(const StreamArgs& A, const FmpBox& B, long long soff, int
                 for (int e = 0; e < 2; ++e) {
                     const float sx = sig[8 * xo + 2 * h + e];
                     const float fr = beb * fmaf(sx, r0[e], fmaf(sy, r1[e], sz * r2[e]));
-                    const float inv = 1.f / fmaf(bt, fmaf(sx, sx, syz2), eb);
+                    // the denominator is >= eps_bar > 0; its fp32 reciprocal is far
+                    // finer than the 16-bit rounding that follows
+                    const float inv = __frcp_rn(fmaf(bt, fmaf(sx, sx, syz2), eb));
                     r0[e] = fmaf(fr, sx, r0[e]) * inv;
                     r1[e] = fmaf(fr, sy, r1[e]) * inv;
                     r2[e] = fmaf(fr, sz, r2[e]) * inv;

@@ -226,6 +226,9 @@ struct fmp_ctx {
     long long launches = 0;       // kernels launched by this context (graph nodes included)
     size_t ld = 0;                // padded vector length
     double* d_V = nullptr;        // (restart+1) x ld
+    int gs_fixed = 0;             // Gram-Schmidt passes in exact fixed point (1) or float64 (0, default)
+    long long* d_X = nullptr;     // (restart+1) x ld fixed-point copies of the FGMRES basis
+    unsigned* d_vmax = nullptr;   // restart+2: largest |V_i| as sign-cleared high words
     double* d_Z = nullptr;        // restart x ld
     double* d_w = nullptr;        // ld
     double* d_tmp = nullptr;      // ld (CN: R / old E)

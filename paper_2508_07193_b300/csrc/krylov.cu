@@ -333,6 +333,270 @@ k_update(const double* __restrict__ V, size_t ld, double* __restrict__ w, size_t
 }
 
 
+// ---- fixed-point basis passes (fmp_set_orth(ctx, 1); float64 by default) ---
+// The same dot and update passes with exact integer products, off the float64
+// pipe (it bounds the passes above at one FMA per 8 bytes, about 0.70 of
+// HBM on this part). A bare dot of int64 vectors reaches 0.93 of HBM; with
+// the conversions the basis needs (float64 in, fixed point kept beside it)
+// and 64 x 64-bit products of several instructions each, these passes
+// measured slower than the float64 ones (238 against 185 ms of a 256^3
+// step), so they are an option, not the default.
+//
+// Each basis vector V_i (float64, the preconditioner's input) has a
+// fixed-point copy X_i = trunc(V_i 2^(1084 - ex_i)), |X_i| < 2^62, where ex_i
+// is the exponent field of max |V_i| (vmax[i], the sign-cleared high word of
+// the largest element, tracked by the pass that writes V_i): every element
+// within 2^9 of the largest keeps all 53 bits, smaller ones lose only the
+// bits below 2^-62 of the largest. The dot pass of step j writes X_j while it
+// reads V_j.
+//
+// Dots: w enters as W = w 2^(1075 - Rw), its 53-bit mantissa shifted right
+// by Rw - e(w), Rw the exponent field of max |w| (the SpMV's output is
+// scanned for it by k_absmax; the update pass tracks it). sum X_i W accumulates exactly
+// in 128 bits (products < 2^115; the launch gives a thread at most 2048
+// elements, below the 2^12 terms that could overflow), and the per-thread
+// totals go to float64 once (scaled by 2^(ex_i + Rw - 2159)) for the block
+// sums of the float64 passes. <w, w> stays one float64 FMA per element.
+// Error: below 2^-53 of max|w| per product, and no rounding in the sums.
+//
+// Update: w += sum c_i V_i with c_i = -h_i sv_i. The coefficients become
+// D_i 2^(G - 57), |D_i| < 2^57, one exponent G for all (each thread derives
+// the same D_i from the same h), so S = sum D_i X_i (< 2^124) is an exact
+// 128-bit sum per element, taken to float64 (its two 64-bit halves
+// converted and joined by one FMA, then scaled and added to w in another:
+// a relative error of a few 2^-53 of the correction, the order of one
+// float64 FMA's) for six float64 operations per element instead of NV + 1.
+
+struct I128 {
+    unsigned long long lo;
+    long long hi;
+};
+__device__ __forceinline__ void mac128(I128& a, long long x, long long y) {
+    const unsigned long long pl = (unsigned long long)x * (unsigned long long)y;
+    const long long ph = __mul64hi(x, y);
+    asm("add.cc.u64 %0, %0, %2;\n\taddc.s64 %1, %1, %3;" : "+l"(a.lo), "+l"(a.hi) : "l"(pl), "l"(ph));
+}
+// arithmetic shift right by s >= 0
+__device__ __forceinline__ void sar128(I128& a, int s) {
+    if (s <= 0) return;
+    if (s >= 127) {
+        a.lo = (unsigned long long)(a.hi >> 63);
+        a.hi >>= 63;
+    } else if (s >= 64) {
+        a.lo = (unsigned long long)(a.hi >> (s - 64));
+        a.hi >>= 63;
+    } else {
+        a.lo = (a.lo >> s) | ((unsigned long long)a.hi << (64 - s));
+        a.hi >>= s;
+    }
+}
+__device__ __forceinline__ double i128_fp64(const I128& a) {
+    return fma((double)a.hi, 0x1p64, (double)a.lo);
+}
+// a 2^k rounded to float64 (to nearest, ties to even) with integer
+// operations; results below 2^-1022 flush to zero
+__device__ __forceinline__ double i128_round(I128 a, int k) {
+    const bool neg = a.hi < 0;
+    unsigned long long hi = (unsigned long long)a.hi, lo = a.lo;
+    if (neg) {
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+    if ((hi | lo) == 0ull) return 0.0;
+    const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+    unsigned long long top, rest;
+    if (lz == 0) { top = hi; rest = lo; }
+    else if (lz < 64) { top = (hi << lz) | (lo >> (64 - lz)); rest = lo << lz; }
+    else { top = lo << (lz - 64); rest = 0ull; }
+    unsigned long long mant = top >> 11;
+    const unsigned long long low = top & 0x7FFull;
+    mant += (low > 0x400ull || (low == 0x400ull && (rest != 0ull || (mant & 1ull)))) ? 1ull : 0ull;
+    int e2 = 127 - lz;   // magnitude in [2^e2, 2^(e2 + 1))
+    if (mant >> 53) { mant >>= 1; ++e2; }
+    const int field = e2 + k + 1023;
+    if (field <= 0) return neg ? -0.0 : 0.0;
+    if (field >= 2047) return neg ? -__longlong_as_double(0x7FF0000000000000LL) : __longlong_as_double(0x7FF0000000000000LL);
+    return __longlong_as_double((long long)(((unsigned long long)neg << 63) | ((unsigned long long)field << 52) |
+                                            (mant & 0xFFFFFFFFFFFFFull)));
+}
+// X = trunc(v 2^(1084 - ex)) for |v| < 2^(ex - 1022): the 62-bit mantissa
+// (implicit one, 9 guard bits) shifted right by ex - e; zero and subnormals 0
+__device__ __forceinline__ long long fix62(double v, int ex) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)(b >> 52) & 0x7FF;
+    const unsigned long long m = ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 9;
+    const int sh = ex - e;
+    const long long X = (e == 0 || sh > 63 || sh < 0) ? 0LL : (long long)(m >> sh);
+    return (b >> 63) ? -X : X;
+}
+__device__ __forceinline__ unsigned abs_hi(double v) { return (unsigned)__double2hiint(v) & 0x7FFFFFFFu; }
+
+// one block per SM for large bases (128-bit sums in registers)
+__host__ __device__ constexpr int fx_blocks_per_sm(int nv) { return nv <= 6 ? 4 : nv <= 16 ? 2 : 1; }
+constexpr int kFold = 2048;   // most elements per thread of a dot pass (sums < 2^126)
+
+// out[i] = <V_i, w> for i < NV and out[NV] = <w, w>; mode 0 also writes
+// X_{NV-1} from V_{NV-1} and clears vmax[NV] for the update passes; mode 1
+// (re-orthogonalisation, flag up only) reads X_{NV-1}.
+template <int NV>
+__global__ void __launch_bounds__(kT, fx_blocks_per_sm(NV))
+k_dots_fx(const double* __restrict__ V, long long* __restrict__ X, size_t ld, const double* __restrict__ w, size_t n,
+          double* st, int R, int out_off, int mode, unsigned* vmax, double* partials, unsigned int* ticket) {
+    const St L = st_layout(R);
+    if (gated(st, L.sc) || (mode == 1 && st[L.sc + SC_REORTH] == 0.0)) return;
+    const int exn = (int)(vmax[NV - 1] >> 20);
+    // w's largest exponent field: the SpMV's output (mode 0, slot R + 1) or
+    // the update pass's (mode 1, slot NV)
+    const int rw = (int)(vmax[mode == 0 ? R + 1 : NV] >> 20);
+    const double* vn = V + (size_t)(NV - 1) * ld;
+    long long* xn = X + (size_t)(NV - 1) * ld;
+    I128 acc[NV];
+#pragma unroll
+    for (int g = 0; g < NV; ++g) { acc[g].lo = 0ull; acc[g].hi = 0; }
+    double ww = 0.0;
+    // the launch gives every thread at most kFold elements
+    for (size_t e = (size_t)blockIdx.x * kT + threadIdx.x; e < n; e += (size_t)gridDim.x * kT) {
+        const double wv = __ldg(w + e);
+        ww = fma(wv, wv, ww);
+        // W = w 2^(1075 - rw): the 53-bit mantissa shifted right by rw - e(w)
+        const unsigned long long wb = (unsigned long long)__double_as_longlong(wv);
+        const int ew = (int)(wb >> 52) & 0x7FF;
+        const int sh = rw - ew;
+        long long W = (ew == 0 || sh > 63 || sh < 0) ? 0LL
+                                                      : (long long)(((wb & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> sh);
+        W = (wb >> 63) ? -W : W;
+#pragma unroll
+        for (int g = 0; g < NV - 1; ++g) mac128(acc[g], __ldg(X + (size_t)g * ld + e), W);
+        long long x;
+        if (mode == 0) {
+            x = fix62(__ldg(vn + e), exn);
+            xn[e] = x;
+        } else {
+            x = __ldg(xn + e);
+        }
+        mac128(acc[NV - 1], x, W);
+    }
+    constexpr int G = pow2_at_least(NV);
+    double dv[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) dv[g] = 0.0;
+#pragma unroll
+    for (int g = 0; g < NV; ++g) dv[g] = ldexp(i128_fp64(acc[g]), (int)(vmax[g] >> 20) + rw - 2159);
+    // mode 0 clears the slot the update passes track the next vector's
+    // largest |w| in (no block of this pass reads it); mode 1 reads that
+    // slot as w's scale, so the update after it only raises it (a bound)
+    if (mode == 0 && blockIdx.x == 0 && threadIdx.x == 0) vmax[NV] = 0u;
+    __shared__ double wsum[kT / 32][kMaxV + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int slot;
+    const double v = warp_reduce_scatter<G>(dv, lane, slot);
+    if ((lane & (32 / G - 1)) == 0) wsum[warp][slot] = v;
+    const double wvs = warp_sum(ww);
+    if (lane == 0) wsum[warp][kMaxV] = wvs;
+    __syncthreads();
+    __shared__ double tot[kMaxV + 2];
+    if (threadIdx.x <= NV) {
+        const int sl = threadIdx.x < NV ? threadIdx.x : kMaxV;
+        double sum = 0.0;
+        for (int q = 0; q < kT / 32; ++q) sum += wsum[q][sl];
+        tot[threadIdx.x] = sum;
+    }
+    __syncthreads();
+    if (block_publish(tot, NV + 1, partials, ticket)) {
+        block_totals(partials, NV + 1, st + out_off);
+        __syncthreads();
+        if (threadIdx.x < NV) st[out_off + threadIdx.x] *= st[L.sv + threadIdx.x];
+        if (threadIdx.x == 0) *ticket = 0;
+    }
+}
+
+// w -= V h with the fixed-point copies X_0 .. X_{NV-1}; the rest as k_update,
+// plus the largest |w| into vmax[j + 1].
+template <int NV>
+__global__ void __launch_bounds__(kT, fx_blocks_per_sm(NV))
+k_update_fx(const long long* __restrict__ X, size_t ld, double* __restrict__ w, size_t n, double* st, int R, int j,
+            int mode, unsigned* vmax, double* partials, unsigned int* ticket) {
+    constexpr int nv = NV;
+    const St L = st_layout(R);
+    if (gated(st, L.sc) || (mode == 1 && st[L.sc + SC_REORTH] == 0.0)) return;
+    const double* h = st + (mode == 0 ? L.h1 : L.h2);
+    // c_g = -h_g sv_g 2^(ex_g - 1084) = D_g 2^(G - 57)
+    double c[NV];
+    int G = -4000;
+#pragma unroll
+    for (int g = 0; g < NV; ++g) {
+        c[g] = ldexp(-h[g] * st[L.sv + g], (int)(vmax[g] >> 20) - 1084);
+        int eg = 0;
+        if (c[g] != 0.0 && isfinite(c[g])) { frexp(c[g], &eg); G = max(G, eg); }
+    }
+    long long D[NV];
+#pragma unroll
+    for (int g = 0; g < NV; ++g) D[g] = isfinite(c[g]) ? (long long)ldexp(c[g], 57 - G) : 0LL;
+    const double sc = ldexp(1.0, G - 57);
+    double acc[1] = {0.0};
+    unsigned mx = 0u;
+    for (size_t e = (size_t)blockIdx.x * kT + threadIdx.x; e < n; e += (size_t)gridDim.x * kT) {
+        I128 s;
+        s.lo = 0ull;
+        s.hi = 0;
+#pragma unroll
+        for (int g = 0; g < NV; ++g) mac128(s, D[g], __ldg(X + (size_t)g * ld + e));
+        const double r = fma(i128_fp64(s), sc, w[e]);
+        w[e] = r;
+        acc[0] = fma(r, r, acc[0]);
+        mx = max(mx, abs_hi(r));
+    }
+    // the largest |w| (integer max of the high words) for the next step's X
+    {
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        if ((threadIdx.x & 31) == 0 && mx != 0u) atomicMax(vmax + j + 1, mx);
+    }
+    if (block_partials(acc, 1, partials, ticket)) {
+        __shared__ double tot;
+        block_totals(partials, 1, &tot);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const double nrm = sqrt(tot);
+            *ticket = 0;
+            if (mode == 0) {
+                const double wn = sqrt(st[L.h1 + nv]);   // ||w|| before projection
+                if (nrm >= kReorthRatio * wn || !isfinite(nrm)) {
+                    st[L.sc + SC_REORTH] = 0.0;
+                    arnoldi_finish(st, L, j, st + L.h1, nrm);
+                    st[L.sv + j + 1] = st[L.sc + SC_INV];   // V[j+1] = w, unnormalised
+                } else {
+                    st[L.sc + SC_REORTH] = 1.0;
+                    st[L.sc + SC_NREORTH] += 1.0;
+                }
+            } else {
+                double hsum[kMaxV];
+                for (int i = 0; i <= j; ++i) hsum[i] = st[L.h1 + i] + st[L.h2 + i];
+                st[L.sc + SC_REORTH] = 0.0;
+                arnoldi_finish(st, L, j, hsum, nrm);
+                st[L.sv + j + 1] = st[L.sc + SC_INV];
+            }
+        }
+    }
+}
+
+// *out = the largest |v| (high words), after a cleared *out.
+__global__ void k_absmax_gated(const double* __restrict__ v, size_t n, unsigned* out, const double* gate) {
+    if (gate && *gate != 0.0) return;
+    unsigned m = 0u;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        m = max(m, abs_hi(__ldg(v + e)));
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && m != 0u) atomicMax(out, m);
+}
+__global__ void k_absmax(const double* __restrict__ v, size_t n, unsigned* out) {
+    unsigned m = 0u;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        m = max(m, abs_hi(v[e]));
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && m != 0u) atomicMax(out, m);
+}
+
+
 // Dots of up to four vector pairs: out[k] = <a_k, b_k>.
 struct Pairs {
     const double* a[4];
@@ -541,6 +805,45 @@ template <int... I>
 constexpr std::array<BasisLaunch, sizeof...(I)> update_table(std::integer_sequence<int, I...>) {
     return {{&launch_update_nv<I + 1>...}};
 }
+struct FxArgs {
+    const double* V;
+    long long* X;
+    size_t ld;
+    double* w;
+    size_t n;
+    double* st;
+    int R, j, out_off, mode;
+    unsigned* vmax;
+    double* partials;
+    unsigned int* ticket;
+};
+// enough blocks that no thread of a dot pass takes more than kFold elements
+int grid_fx(size_t n, int per_sm) {
+    const int g = grid_basis(n, per_sm);
+    const size_t need = (n + (size_t)kT * kFold - 1) / ((size_t)kT * kFold);
+    return (size_t)g < need ? (int)need : g;
+}
+template <int NV>
+void launch_dots_fx_nv(const FxArgs& a, cudaStream_t s) {
+    k_dots_fx<NV><<<grid_fx(a.n, fx_blocks_per_sm(NV)), kT, 0, s>>>(a.V, a.X, a.ld, a.w, a.n, a.st, a.R, a.out_off,
+                                                                       a.mode, a.vmax, a.partials, a.ticket);
+}
+template <int NV>
+void launch_update_fx_nv(const FxArgs& a, cudaStream_t s) {
+    k_update_fx<NV><<<grid_basis(a.n, fx_blocks_per_sm(NV)), kT, 0, s>>>(a.X, a.ld, a.w, a.n, a.st, a.R, a.j, a.mode,
+                                                                         a.vmax, a.partials, a.ticket);
+}
+using FxLaunch = void (*)(const FxArgs&, cudaStream_t);
+template <int... I>
+constexpr std::array<FxLaunch, sizeof...(I)> dots_fx_table(std::integer_sequence<int, I...>) {
+    return {{&launch_dots_fx_nv<I + 1>...}};
+}
+template <int... I>
+constexpr std::array<FxLaunch, sizeof...(I)> update_fx_table(std::integer_sequence<int, I...>) {
+    return {{&launch_update_fx_nv<I + 1>...}};
+}
+constexpr auto kDotsFx = dots_fx_table(std::make_integer_sequence<int, kMaxV>{});
+constexpr auto kUpdatesFx = update_fx_table(std::make_integer_sequence<int, kMaxV>{});
 constexpr auto kDots = dots_table(std::make_integer_sequence<int, kMaxV>{});
 constexpr auto kUpdates = update_table(std::make_integer_sequence<int, kMaxV>{});
 
@@ -655,14 +958,31 @@ int arnoldi_step(fmp_ctx* c, int j, fmp_solve_info* inf) {
     {
         Timer tm(c, &inf->ms_orth, "orth");
         const int nv = j + 1;
-        ++c->launches;
-        FMP_CK(launch_dots(V, ld, nv, w, n, st, R, L.h1, 0, c, s));
-        ++c->launches;
-        FMP_CK(launch_update(V, ld, nv, w, n, st, R, j, 0, c, s));
-        ++c->launches;
-        FMP_CK(launch_dots(V, ld, nv, w, n, st, R, L.h2, 1, c, s));
-        ++c->launches;
-        FMP_CK(launch_update(V, ld, nv, w, n, st, R, j, 1, c, s));
+        if (c->gs_fixed && c->d_X) {
+            // the largest |w| of the SpMV's output, for the dots' common scale
+            FMP_CK(cudaMemsetAsync(c->d_vmax + R + 1, 0, sizeof(unsigned), s));
+            ++c->launches;
+            k_absmax_gated<<<grid_n(n), kT, 0, s>>>(w, n, c->d_vmax + R + 1, gate);
+            FxArgs a{V, c->d_X, ld, w, n, st, R, j, L.h1, 0, c->d_vmax, c->d_partials, c->d_ticket};
+            c->launches += 2;
+            kDotsFx[nv - 1](a, s);
+            kUpdatesFx[nv - 1](a, s);
+            a.out_off = L.h2;
+            a.mode = 1;
+            c->launches += 2;
+            kDotsFx[nv - 1](a, s);
+            kUpdatesFx[nv - 1](a, s);
+            FMP_CK(cudaGetLastError());
+        } else {
+            ++c->launches;
+            FMP_CK(launch_dots(V, ld, nv, w, n, st, R, L.h1, 0, c, s));
+            ++c->launches;
+            FMP_CK(launch_update(V, ld, nv, w, n, st, R, j, 0, c, s));
+            ++c->launches;
+            FMP_CK(launch_dots(V, ld, nv, w, n, st, R, L.h2, 1, c, s));
+            ++c->launches;
+            FMP_CK(launch_update(V, ld, nv, w, n, st, R, j, 1, c, s));
+        }
         // no scaling pass: V[j+1] = w stays unnormalised, with sv[j+1] = 1 / h(j+1, j)
     }
     return FMP_OK;
@@ -708,9 +1028,13 @@ cudaError_t fmp_ensure_krylov(fmp_ctx* c) {
     const int R = c->opt.restart;
     const int need_v = R + 1 > 9 ? R + 1 : 9;   // BiCGSTAB uses 9: r, rhat, p, v, s, t, phat, shat, x
     const int need_z = c->opt.krylov == FMP_KRYLOV_BICGSTAB ? 0 : R;
-    if (c->d_V && c->kry_restart == R && c->kry_nv >= need_v && c->kry_nz >= need_z) return cudaSuccess;
-    cudaFree(c->d_V); cudaFree(c->d_Z); cudaFree(c->d_state);
+    const bool need_x = c->opt.krylov != FMP_KRYLOV_BICGSTAB && c->gs_fixed;
+    if (c->d_V && c->kry_restart == R && c->kry_nv >= need_v && c->kry_nz >= need_z && (!need_x || c->d_X))
+        return cudaSuccess;
+    cudaFree(c->d_V); cudaFree(c->d_Z); cudaFree(c->d_state); cudaFree(c->d_X); cudaFree(c->d_vmax);
     c->d_V = c->d_Z = c->d_state = nullptr;
+    c->d_X = nullptr;
+    c->d_vmax = nullptr;
     c->kry_nv = c->kry_nz = c->kry_restart = 0;
     fmp_invalidate_graphs(c);
     c->ld = (c->n_slots + 31) / 32 * 32;
@@ -718,6 +1042,10 @@ cudaError_t fmp_ensure_krylov(fmp_ctx* c) {
     if ((e = cudaMalloc(&c->d_V, sizeof(double) * c->ld * need_v))) return e;
     if (need_z && (e = cudaMalloc(&c->d_Z, sizeof(double) * c->ld * need_z))) return e;
     if ((e = cudaMalloc(&c->d_state, sizeof(double) * st_layout(R).total))) return e;
+    if (need_x) {   // fixed-point copies of the basis and their largest magnitudes
+        if ((e = cudaMalloc(&c->d_X, sizeof(long long) * c->ld * (R + 1)))) return e;
+        if ((e = cudaMalloc(&c->d_vmax, sizeof(unsigned) * (R + 2)))) return e;
+    }
     if ((e = cudaMemsetAsync(c->d_state, 0, sizeof(double) * st_layout(R).total, c->stream))) return e;
     c->kry_nv = need_v; c->kry_nz = need_z; c->kry_restart = R;
     return cudaSuccess;
@@ -772,6 +1100,12 @@ int fmp_fgmres(fmp_ctx* c, const double* b, double* x, fmp_solve_info* info) {
         ++c->launches;
         k_cycle_init<<<1, 1, 0, s>>>(st, R, c->opt.rtol, budget);
         FMP_CK(cudaGetLastError());
+        if (c->gs_fixed && c->d_X) {   // the largest |V_0| for its fixed-point copy
+            FMP_CK(cudaMemsetAsync(c->d_vmax, 0, sizeof(unsigned), s));
+            ++c->launches;
+            k_absmax<<<grid_n(n), kT, 0, s>>>(V, n, c->d_vmax);
+            FMP_CK(cudaGetLastError());
+        }
         if (c->opt.use_graph && !c->opt.timing && c->opt.use_learned < 2) {
             int rc = run_cycle_graph(c);
             if (rc != FMP_OK) return rc;

@@ -91,6 +91,8 @@ def lib():
         "fmp_get_subdomain_form": (_I, [_P, C.POINTER(_I), C.POINTER(C.c_longlong)]),
         "fmp_get_fused": (_I, [_P, C.POINTER(_I), C.POINTER(_I)]),
         "fmp_set_streamed": (_I, [_P, _I]),
+        "fmp_set_orth": (_I, [_P, _I]),
+        "fmp_get_orth": (_I, [_P, C.POINTER(_I)]),
         "fmp_get_streamed": (_I, [_P, C.POINTER(_I), C.POINTER(_I)]),
         "fmp_stream_check": (_I, [_P]),
         "fmp_get_box": (_I, [_P, _I, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I),
@@ -295,6 +297,15 @@ class Context:
         m, n = C.c_int(), C.c_int()
         _check(lib().fmp_get_streamed(self._h, C.byref(m), C.byref(n)), "fmp_get_streamed")
         return m.value, n.value
+
+    def set_orth(self, fixed_point=True):
+        """Gram-Schmidt passes in exact fixed point, or float64 (the default; fmp_set_orth)."""
+        _check(lib().fmp_set_orth(self._h, int(bool(fixed_point))), "fmp_set_orth")
+
+    def get_orth(self):
+        v = C.c_int()
+        _check(lib().fmp_get_orth(self._h, C.byref(v)), "fmp_get_orth")
+        return bool(v.value)
 
     def stream_check(self):
         """FMP_OK, or FMP_ERR_CUDA when a wait of the streamed solve ran out

@@ -143,3 +143,23 @@ def test_grid256_solve_matches_the_oracle_run():
     assert info["true_rel_res"] <= 1e-8 and abs(info["iters"] - rec["iters"]) <= 2
     assert info["true_rel_res"] == pytest.approx(rec["true_rel_res"], rel=1e-4)
     ctx.close()
+
+
+def test_fixed_point_orthogonalisation_agrees_with_float64():
+    """The Gram-Schmidt passes in exact fixed point (fmp_set_orth(1)) against
+    the float64 FMA passes (the default) on the 128^3 workload: the same
+    iteration count, the same true residual to 1e-6 relative and solutions
+    within 1e-10 of each other (both are rounded float64 Arnoldi processes of
+    the same Krylov space; the fixed-point one has exact products and sums)."""
+    from tests._gpu import rel2
+    w = wl.grid128()
+    ctx = context(w)
+    assert not ctx.get_orth()
+    x0, i0 = ctx.krylov_solve(dev(w.rhs))
+    ctx.set_orth(True)
+    assert ctx.get_orth()
+    x1, i1 = ctx.krylov_solve(dev(w.rhs))
+    assert i1["iters"] == i0["iters"]
+    assert i1["true_rel_res"] == pytest.approx(i0["true_rel_res"], rel=1e-6)
+    assert rel2(host(x1), host(x0)) <= 1e-10
+    ctx.close()

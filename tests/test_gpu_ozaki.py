@@ -8,7 +8,7 @@ import pytest
 
 from oracle import box, ras, yee
 from paper_2508_07193_b300 import workloads as wl
-from tests._gpu import FP64_TOL, context, dev, host, rel
+from tests._gpu import FP64_TOL, context, dev, host, maxrel, rel, rel2
 
 pytestmark = pytest.mark.gpu
 
@@ -40,7 +40,7 @@ def test_box32_error_against_native_float64():
     oz = context(w, precision="fp64_ozaki")
     a = host(nat.box_solve(0, dev(w.rhs)))
     b = host(oz.box_solve(0, dev(w.rhs)))
-    assert rel(b, a) <= 1e-13
+    assert rel2(b, a) <= 1e-13 and maxrel(b, a) <= 3e-13
     A = yee.system_matrix(w.grid, yee.edge_eps(w.grid, None), w.beta)
     r = np.linalg.norm(A @ b.reshape(-1) - w.rhs.reshape(-1)) / np.linalg.norm(w.rhs)
     assert r <= 1e-12
@@ -77,7 +77,7 @@ def test_uneven_workload_sampled_boxes_and_native_agreement():
         sl = (slice(None), slice(z0, z1), slice(y0, y1), slice(x0, x1))
         assert rel(z[sl], part[sl]) <= FP64_TOL
     zn = host(context(w).precond_apply(dev(w.rhs)))
-    assert rel(z, zn) <= 1e-13
+    assert rel2(z, zn) <= 1e-13 and maxrel(z, zn) <= 3e-13
 
 
 @pytest.mark.parametrize("w", [
@@ -114,7 +114,7 @@ def test_precond_128_sampled_boxes_and_native_agreement():
         sl = (slice(None), slice(z0, z1), slice(y0, y1), slice(x0, x1))
         assert rel(z[sl], part[sl]) <= FP64_TOL
     zn = host(context(w).precond_apply(dev(w.rhs)))
-    assert rel(z, zn) <= 1e-13
+    assert rel2(z, zn) <= 1e-13 and maxrel(z, zn) <= 3e-13
 
 
 def test_power_of_two_scaling_is_exact_and_zero_stays_zero():
