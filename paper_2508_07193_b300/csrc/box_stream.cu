@@ -45,22 +45,29 @@ constexpr int kT = 256;                    // threads (8 warps)
 constexpr int kW = kT / 32;
 constexpr int kMaxP = 80;                  // largest padded extent: round_up(FMP_MAX_EXTENT, 16)
 constexpr int kLT = kMaxP + 8;             // row stride (elements) of tables and slabs: 176 B
-constexpr int kQ = 16;                     // x-octet lines per B item
+constexpr int kQ = 8;                      // x-octet lines per B item
 constexpr int kPS = kQ * 8 + 8;            // z-row stride (elements) of the B tile: 272 B
-constexpr int kSG = 4;                     // z-slabs per A / C item
+constexpr int kSGMax = 8;                  // most z-slabs per A / C item
 constexpr long long kWaitLimit = 1LL << 23;   // x ~128 ns: about a second
 
 constexpr size_t kTabBytes = 2ull * kMaxP * kLT * 2;
 constexpr size_t kSigBytes = 3ull * kMaxP * 4;
 constexpr size_t kSlabBytes = (size_t)kMaxP * kLT * 2;
 constexpr size_t kTileBytes = 3ull * kMaxP * kPS * 2;
-constexpr size_t kDataBytes = kTileBytes > kSG * kSlabBytes ? kTileBytes : kSG * kSlabBytes;
-constexpr int kSlab = kMaxP * kLT;         // elements of one slab buffer
+constexpr size_t kDataBytes = kTileBytes > 3 * kSlabBytes ? kTileBytes : 3 * kSlabBytes;
 constexpr size_t kSmem = kTabBytes + kSigBytes + kDataBytes;
 static_assert(FMP_MAX_EXTENT <= kMaxP, "tables and slabs are sized for the largest extent");
+static_assert(kSmem + 1024 <= 227 * 1024 / 3, "three CTAs per SM");
 static_assert(kLT * 2 % 16 == 0 && kPS * 2 % 16 == 0, "16-byte rows");
 
 __host__ __device__ __forceinline__ int rup16(int v) { return (v + 15) & ~15; }
+
+// z-slabs of an A or C item of a box with y extent my: as many slab buffers
+// of round_up(my, 16) rows as the data region holds (3 at my = 80, 5 at 48)
+__host__ __device__ __forceinline__ int slabs_per_item(int my) {
+    const int n = (int)(kDataBytes / ((size_t)rup16(my) * kLT * 2));
+    return n < kSGMax ? n : kSGMax;
+}
 
 struct BF16S {
     using E = __nv_bfloat16;
@@ -329,15 +336,15 @@ __device__ __forceinline__ float box_scale(const unsigned* bmax, int bi) {
 }
 
 // ---- pass A: gather, TrX, TrY of z-slabs [z0, z0 + zn) of component c ------
-// The zn <= kSG slabs are processed together (one buffer each, transformed
-// in place), so every phase has tiles for all warps.
+// The zn slabs (slabs_per_item) are processed together (one buffer each,
+// transformed in place), so every phase has tiles for all warps.
 template <class Tr>
 __device__ void pass_a(const StreamArgs& A, int bi, const FmpBox& B, long long soff, int c, int z0, int zn,
                        typename Tr::E* T0, typename Tr::E* T1, typename Tr::E* D, int* staged) {
     using E = typename Tr::E;
     const int mx = B.m[0], my = B.m[1], mz = B.m[2];
     const int MXp = rup16(mx), MYp = rup16(my), NXo = (mx + 7) >> 3, NYo = (my + 7) >> 3;
-    const int mxp = NXo * 8, npairs = MXp >> 1;
+    const int mxp = NXo * 8, npairs = MXp >> 1, kSlab = MYp * kLT;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, t = lane & 3;
     stage_tables<E>(T0, T1, reinterpret_cast<const E*>(A.tabs), c == 0 ? B.mpc_off[0] : B.mps_off[0], MXp,
                     c == 1 ? B.mpc_off[1] : B.mps_off[1], MYp, staged);
@@ -512,7 +519,7 @@ __device__ void pass_c(const StreamArgs& A, int bi, const FmpBox& B, long long s
                        typename Tr::E* T0, typename Tr::E* T1, typename Tr::E* D, int* staged, bool poison) {
     using E = typename Tr::E;
     const int mx = B.m[0], my = B.m[1], mz = B.m[2];
-    const int MXp = rup16(mx), MYp = rup16(my), NXo = (mx + 7) >> 3, mxp = NXo * 8;
+    const int MXp = rup16(mx), MYp = rup16(my), NXo = (mx + 7) >> 3, mxp = NXo * 8, kSlab = MYp * kLT;
     const int oy0 = B.own_lo[1], ony = B.own_n[1], ox0 = B.own_lo[0], onx = B.own_n[0];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, t = lane & 3;
     double* dst0 = A.z + ((long long)c * A.nz + B.ext_lo[2]) * A.ny * (long long)A.nx + (long long)B.ext_lo[1] * A.nx +
@@ -578,14 +585,14 @@ __device__ void pass_c(const StreamArgs& A, int bi, const FmpBox& B, long long s
 }
 
 template <class Tr>
-__global__ void __launch_bounds__(kT, 2) k_stream_solve(StreamArgs A) {
+__global__ void __launch_bounds__(kT, 3) k_stream_solve(StreamArgs A) {
     using E = typename Tr::E;
     if (A.gate && *A.gate != 0.0) return;
     extern __shared__ __align__(128) unsigned char smraw[];
     E* T0 = reinterpret_cast<E*>(smraw);
     E* T1 = T0 + kMaxP * kLT;
     float* sig = reinterpret_cast<float*>(T1 + kMaxP * kLT);
-    E* D = reinterpret_cast<E*>(sig + 3 * kMaxP);   // kSG slab buffers, or pass B's tile
+    E* D = reinterpret_cast<E*>(sig + 3 * kMaxP);   // slab buffers, or pass B's tile
     __shared__ int s_item, s_ok;
     __shared__ int staged[4];
     if (threadIdx.x == 0) { staged[0] = staged[1] = staged[2] = staged[3] = -1; }
@@ -693,13 +700,16 @@ void fmp_stream_items(const std::vector<FmpBox>& boxes, const std::vector<int>& 
         const int nxo = (x.m[0] + 7) / 8;
         sb[b].soff = off;
         off += (3LL * x.m[2] * x.m[1] * nxo * 8 + 7) / 8 * 8;
-        sb[b].need_a = 3 * ((x.m[2] + kSG - 1) / kSG);
+        const int sg = slabs_per_item(x.m[1]);
+        sb[b].need_a = 3 * ((x.m[2] + sg - 1) / sg);
         sb[b].need_b = (x.m[1] * nxo + kQ - 1) / kQ;
     }
     items.clear();
-    for (int b : order)
+    for (int b : order) {
+        const int sg = slabs_per_item(boxes[b].m[1]);
         for (int c = 0; c < 3; ++c)
-            for (int z = 0; z < boxes[b].m[2]; z += kSG) items.push_back(make_int4(b, c, z, std::min(kSG, boxes[b].m[2] - z)));
+            for (int z = 0; z < boxes[b].m[2]; z += sg) items.push_back(make_int4(b, c, z, std::min(sg, boxes[b].m[2] - z)));
+    }
     // pass B by z extent (its tables depend on it alone)
     std::vector<int> byz(order);
     std::stable_sort(byz.begin(), byz.end(), [&](int a, int b) { return boxes[a].m[2] > boxes[b].m[2]; });
@@ -709,9 +719,9 @@ void fmp_stream_items(const std::vector<FmpBox>& boxes, const std::vector<int>& 
     }
     for (int b : order) {
         const FmpBox& x = boxes[b];
-        const int o0 = x.own_lo[2], o1 = o0 + x.own_n[2];
+        const int o0 = x.own_lo[2], o1 = o0 + x.own_n[2], sg = slabs_per_item(x.m[1]);
         for (int c = 0; c < 3; ++c)
-            for (int z = o0; z < o1; z += kSG) items.push_back(make_int4(b, 8 + c, z, std::min(kSG, o1 - z)));
+            for (int z = o0; z < o1; z += sg) items.push_back(make_int4(b, 8 + c, z, std::min(sg, o1 - z)));
     }
     if (test_extra > 0 && !order.empty()) sb[order.front()].need_b += test_extra;
 }
