@@ -22,6 +22,11 @@
 // the error word, and its C item writes NaN to its owned cells instead of a
 // result, so a failed apply never passes for a correct one.
 //
+// Conversions between float64 and fp32 are integer bit operations (rounded
+// to odd on the way in, so that the later rounding to the 16-bit type equals
+// the direct one): the hardware conversions, which run on the float64 pipe,
+// measured slower here (0.86 -> 0.91 ms per uneven apply).
+//
 // GEMMs: mma.sync m16n8k16 (bf16 or fp16 inputs, fp32 accumulation) with
 // every operand moved by ldmatrix / stmatrix. A "row" contraction takes its
 // lines as rows of a slab (k contiguous); an "octet" contraction takes 8
@@ -628,10 +633,13 @@ __global__ void __launch_bounds__(kT, 3) k_stream_solve(StreamArgs A) {
             pass_b<Tr>(A, B, S.soff, w.z, w.w, T0, T1, sig, D, staged);
         else if (kind == 2)
             pass_c<Tr>(A, bi, B, S.soff, c, w.z, w.w, T0, T1, D, staged, !ok);
-        // publish: every thread's scratch writes before the box's count moves
-        __threadfence();
+        // publish: the barrier orders every thread's scratch writes before
+        // thread 0's release of the box's count (a cumulative gpu-scope fence)
         __syncthreads();
-        if (threadIdx.x == 0 && kind < 2 && ok) atomicAdd(A.sync + 1 + kind * A.n_boxes + bi, 1);
+        if (threadIdx.x == 0 && kind < 2 && ok) {
+            __threadfence();
+            atomicAdd(A.sync + 1 + kind * A.n_boxes + bi, 1);
+        }
     }
 }
 
