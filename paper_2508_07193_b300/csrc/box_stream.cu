@@ -74,8 +74,52 @@ __host__ __device__ __forceinline__ int slabs_per_item(int my) {
     return n < kSGMax ? n : kSGMax;
 }
 
+// The index q = q0, q0 + step, ... of a loop over [0, n1 n2 n3) as
+// (i1, i2, i3), q = (i1 n2 + i2) n3 + i3, advanced by carries instead of a
+// division per step (divisions once, at the start).
+struct Walk3 {
+    int i1, i2, i3, d1, d2, d3, n2, n3;
+    __device__ __forceinline__ Walk3(int q0, int step, int n2_, int n3_) : n2(n2_), n3(n3_) {
+        i3 = q0 % n3; int t = q0 / n3; i2 = t % n2; i1 = t / n2;
+        d3 = step % n3; t = step / n3; d2 = t % n2; d1 = t / n2;
+    }
+    __device__ __forceinline__ void next() {
+        i3 += d3;
+        int c = i3 >= n3;
+        i3 -= c ? n3 : 0;
+        i2 += d2 + c;
+        c = i2 >= n2;
+        i2 -= c ? n2 : 0;
+        i1 += d1 + c;
+    }
+};
+
+// x rounded to bf16 (to nearest, ties to even) by integer operations, as
+// the 16-bit pattern: the same value as rounding to fp32 by odd and then to
+// bf16. Results below 2^-126 give a signed zero, above the range infinity;
+// NaN stays NaN.
+__device__ __forceinline__ uint32_t f64_bf16_bits(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const uint32_t hi = (uint32_t)(b >> 32);
+    const int ex = (int)(hi >> 20) & 0x7FF;
+    const int e = ex - 1023 + 127;
+    const uint32_t m7 = (hi >> 13) & 0x7Fu;
+    const uint32_t sticky = ((hi & 0xFFFu) | (uint32_t)b) != 0u ? 1u : 0u;
+    uint32_t v = ((uint32_t)e << 7) + m7;
+    v += ((hi >> 12) & 1u) & (sticky | (m7 & 1u));   // a carry moves into the exponent
+    v = (e <= 0 || ex == 0) ? 0u : v;
+    v = (e >= 255) ? 0x7F80u : v;
+    v = ex == 0x7FF ? (0x7F80u | (((hi & 0xFFFFFu) | (uint32_t)b) != 0u ? 0x40u : 0u)) : v;
+    return ((hi >> 16) & 0x8000u) | v;
+}
+
 struct BF16S {
     using E = __nv_bfloat16;
+    static constexpr bool kScaled = false;
+    // the pair (a, b) of float64 values rounded to bf16, a in the low half
+    static __device__ __forceinline__ uint32_t pack64(double a, double b, float) {
+        return f64_bf16_bits(a) | (f64_bf16_bits(b) << 16);
+    }
     static __device__ __forceinline__ uint32_t pack(float a, float b) {
         const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
         return *reinterpret_cast<const uint32_t*>(&h);
@@ -93,6 +137,11 @@ struct BF16S {
 };
 struct FP16S {
     using E = __half;
+    static constexpr bool kScaled = true;
+    // the pair (a, b) scaled by inv_s and rounded to fp16 (to odd in fp32 first)
+    static __device__ __forceinline__ uint32_t pack64(double a, double b, float inv_s) {
+        return pack(fmp::f64_to_f32_scaled<true>(a, 0) * inv_s, fmp::f64_to_f32_scaled<true>(b, 0) * inv_s);
+    }
     static __device__ __forceinline__ uint32_t pack(float a, float b) {
         const __half2 h = __floats2half2_rn(a, b);
         return *reinterpret_cast<const uint32_t*>(&h);
@@ -386,9 +435,7 @@ __device__ void pass_a(const StreamArgs& A, int bi, const FmpBox& B, long long s
             for (int h = 0; h < 2; ++h) {
                 const int p = lane + 32 * h;
                 if (p < npairs)
-                    *reinterpret_cast<uint32_t*>(row + 2 * p) =
-                        Tr::pack(fmp::f64_to_f32_scaled<true>(v[u][h][0], 0) * inv_s,
-                                 fmp::f64_to_f32_scaled<true>(v[u][h][1], 0) * inv_s);
+                    *reinterpret_cast<uint32_t*>(row + 2 * p) = Tr::pack64(v[u][h][0], v[u][h][1], inv_s);
             }
         }
     }
@@ -416,11 +463,11 @@ __device__ void pass_a(const StreamArgs& A, int bi, const FmpBox& B, long long s
     }
     __syncthreads();
     E* out = reinterpret_cast<E*>(A.scratch) + soff + ((long long)c * mz + z0) * my * mxp;
-    const int per = my * NXo;
-    for (int q = threadIdx.x; q < zn * per; q += kT) {
-        const int sl = q / per, rem = q - sl * per, ky = rem / NXo, xo = rem - ky * NXo;
-        *reinterpret_cast<uint4*>(out + ((long long)sl * my + ky) * mxp + 8 * xo) =
-            *reinterpret_cast<const uint4*>(D + sl * kSlab + ky * kLT + 8 * xo);
+    {
+        Walk3 it(threadIdx.x, kT, my, NXo);   // (slab, ky, x octet)
+        for (int q = threadIdx.x; q < zn * my * NXo; q += kT, it.next())
+            *reinterpret_cast<uint4*>(out + ((long long)it.i1 * my + it.i2) * mxp + 8 * it.i3) =
+                *reinterpret_cast<const uint4*>(D + it.i1 * kSlab + it.i2 * kLT + 8 * it.i3);
     }
 }
 
@@ -440,15 +487,25 @@ __device__ void pass_b(const StreamArgs& A, const FmpBox& B, long long soff, int
         sig[q] = k < ma ? fmp::f64_to_f32_scaled<false>(A.tabs64[so + k], 0) : 0.f;
     }
     E* scr = reinterpret_cast<E*>(A.scratch) + soff;
-    // this thread's octet slot is fixed (kT is a multiple of kQ)
+    // (ky, x octet) of each line of the item, and this thread's octet slot,
+    // fixed since kT is a multiple of kQ
+    __shared__ int s_ky[kQ], s_xo[kQ];
+    if (threadIdx.x < kQ) {
+        const int l = l0 + (int)threadIdx.x;
+        s_ky[threadIdx.x] = l / NXo;
+        s_xo[threadIdx.x] = l % NXo;
+    }
     const int qt = threadIdx.x % kQ;
     const int lt = l0 + qt, kyt = lt / NXo, xot = lt - kyt * NXo;
     const bool qok = qt < nl;
-    for (int t = threadIdx.x; t < 3 * MZp * kQ; t += kT) {
-        const int cz = t / kQ, c = cz / MZp, zz = cz - c * MZp;
-        const bool ok = qok && zz < mz;
-        const E* s = ok ? scr + (((long long)c * mz + zz) * my + kyt) * mxp + 8 * xot : scr;
-        cp16(saddr(P + cz * kPS + qt * 8), s, ok ? 16 : 0);
+    {
+        Walk3 it(threadIdx.x / kQ, kT / kQ, 3, MZp);   // (unused, component, z) of row cz = t / kQ
+        for (int t = threadIdx.x; t < 3 * MZp * kQ; t += kT, it.next()) {
+            const int c = it.i2, zz = it.i3, cz = c * MZp + zz;
+            const bool ok = qok && zz < mz;
+            const E* s = ok ? scr + (((long long)c * mz + zz) * my + kyt) * mxp + 8 * xot : scr;
+            cp16(saddr(P + cz * kPS + qt * 8), s, ok ? 16 : 0);
+        }
     }
     cp_wait_all();
     __syncthreads();
@@ -465,9 +522,10 @@ __device__ void pass_b(const StreamArgs& A, const FmpBox& B, long long soff, int
     {
         const float eb = fmp::f64_to_f32_scaled<false>(B.eps_bar, 0), bt = fmp::f64_to_f32_scaled<false>(A.beta, 0);
         const float beb = bt / eb;
-        for (int t = threadIdx.x; t < mz * nl; t += kT) {
-            const int kz = t / nl, q = t - kz * nl;
-            const int l = l0 + q, ky = l / NXo, xo = l - ky * NXo;
+        Walk3 it(threadIdx.x, kT, mz, nl);   // (0, kz, line)
+        for (int t = threadIdx.x; t < mz * nl; t += kT, it.next()) {
+            const int kz = it.i2, q = it.i3;
+            const int ky = s_ky[q], xo = s_xo[q];
             E* p0 = P + kz * kPS + q * 8;
             uint4 u[3];
 #pragma unroll
@@ -509,11 +567,14 @@ __device__ void pass_b(const StreamArgs& A, const FmpBox& B, long long soff, int
         oct_tile<Tr, true>(mt, nl, base, kPS, c == 2 ? t0 : t1, MZp, oz0 >> 3, (oz0 + onz + 7) >> 3, base, kPS);
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < 3 * onz * kQ; t += kT) {
-        const int cz = t / kQ, c = cz / onz, zz = oz0 + (cz - c * onz);
-        if (qok)
-            *reinterpret_cast<uint4*>(scr + (((long long)c * mz + zz) * my + kyt) * mxp + 8 * xot) =
-                *reinterpret_cast<const uint4*>(P + (c * MZp + zz) * kPS + qt * 8);
+    {
+        Walk3 it(threadIdx.x / kQ, kT / kQ, 3, onz);   // (unused, component, owned z)
+        for (int t = threadIdx.x; t < 3 * onz * kQ; t += kT, it.next()) {
+            const int c = it.i2, zz = oz0 + it.i3;
+            if (qok)
+                *reinterpret_cast<uint4*>(scr + (((long long)c * mz + zz) * my + kyt) * mxp + 8 * xot) =
+                    *reinterpret_cast<const uint4*>(P + (c * MZp + zz) * kPS + qt * 8);
+        }
     }
     __syncthreads();
 }
@@ -543,12 +604,15 @@ __device__ void pass_c(const StreamArgs& A, int bi, const FmpBox& B, long long s
     const float s = box_scale(A.bmax, bi);
     const E* scr = reinterpret_cast<const E*>(A.scratch) + soff + ((long long)c * mz + z0) * my * mxp;
     // slabs: rows ky < MYp, 16-byte chunks < MXp / 8 (zero beyond the box)
-    const int cpr = MXp >> 3, per = MYp * cpr;
-    for (int q = threadIdx.x; q < zn * per; q += kT) {
-        const int sl = q / per, rem = q - sl * per, ky = rem / cpr, ch = rem - ky * cpr;
-        const bool ok = ky < my && ch < NXo;
-        cp16(saddr(D + sl * kSlab + ky * kLT + 8 * ch), ok ? scr + ((long long)sl * my + ky) * mxp + 8 * ch : scr,
-             ok ? 16 : 0);
+    const int cpr = MXp >> 3;
+    {
+        Walk3 it(threadIdx.x, kT, MYp, cpr);   // (slab, ky, 16-byte chunk)
+        for (int q = threadIdx.x; q < zn * MYp * cpr; q += kT, it.next()) {
+            const int sl = it.i1, ky = it.i2, ch = it.i3;
+            const bool ok = ky < my && ch < NXo;
+            cp16(saddr(D + sl * kSlab + ky * kLT + 8 * ch), ok ? scr + ((long long)sl * my + ky) * mxp + 8 * ch : scr,
+                 ok ? 16 : 0);
+        }
     }
     cp_wait_all();
     __syncthreads();
@@ -598,11 +662,19 @@ __global__ void __launch_bounds__(kT, 3) k_stream_solve(StreamArgs A) {
     E* T1 = T0 + kMaxP * kLT;
     float* sig = reinterpret_cast<float*>(T1 + kMaxP * kLT);
     E* D = reinterpret_cast<E*>(sig + 3 * kMaxP);   // slab buffers, or pass B's tile
-    __shared__ int s_item, s_ok;
+    __shared__ int s_item, s_next, s_ok;
     __shared__ int staged[4];
-    if (threadIdx.x == 0) { staged[0] = staged[1] = staged[2] = staged[3] = -1; }
+    if (threadIdx.x == 0) {
+        staged[0] = staged[1] = staged[2] = staged[3] = -1;
+        s_next = atomicAdd(A.sync, 1);
+    }
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(A.sync, 1);
+        // take the item fetched during the previous one, and fetch the next
+        // (the counter's round trip overlaps this item's work)
+        if (threadIdx.x == 0) {
+            s_item = s_next;
+            if (s_item < A.n_items) s_next = atomicAdd(A.sync, 1);
+        }
         __syncthreads();
         const int it = s_item;
         if (it >= A.n_items) break;
