@@ -55,9 +55,7 @@ def fp64_issue_peak_tops(sm_mhz=None):
 # (workload, precision); the capture is summarised in the profiles/ file named
 # beside each entry. Absent: not captured for this kernel version.
 TRAFFIC_BYTES = {
-    ("yee256_ras8x8x8_ol2", "fp64"): 2969.1e6,   # transform_fp64_precond_grid256.md
     ("yee256_ras8x8x8_ol2", "bf16"): 748.3e6,    # fused_bf16_precond_grid256.md
-    ("yee128_ras4x4x4_ol2", "fp64"): 228.9e6,   # transform_fp64_precond_grid128.md
     ("yee128_ras4x4x4_ol2", "fp64_ozaki"): 246.8e6,   # transform_fp64_ozaki_precond_grid128.md
 }
 
@@ -228,71 +226,119 @@ def transform_bytes(ctx):
     return tot + 3 * nx * ny * nz * 8
 
 
-def _fold3(m, dst):
-    """Class structure of the two-level folded table (the library's Fold3):
-    rows n, input lengths len per class, plus the first-level pairs, middle,
-    and the second-level length L (0 when the second level does not apply)."""
+def _fold2(m, dst):
+    """Class structure of the library's two-level fold (Fold3 without the
+    third level): rows n, input lengths len per class, the first-level pairs
+    and middle, and the second-level length L (0 when it does not apply)."""
     off = 1 if dst else 0
     npair, mid = (m - off) // 2, (m - off) & 1
     s0 = 1 if dst else 0
     nks, nka = (m - s0 + 1) // 2, (m - (1 - s0) + 1) // 2
     la, lb = npair + mid, npair
     if m % 2 or m < 4:
-        return dict(n=(nks, nka, 0), len=(la, lb, 0), npair=npair, mid=mid, L=0, off=off)
+        return dict(n=(nks, nka, 0), len=(la, lb, 0), npair=npair, mid=mid, L=0, off=off, m=m)
     if not dst:
         return dict(n=((nks + 1) // 2, nks // 2, nka), len=(la // 2 + la % 2, la // 2, lb), npair=npair, mid=mid,
-                    L=la, off=off)
+                    L=la, off=off, m=m)
     return dict(n=(nka // 2, (nka - 1) // 2, nks), len=(lb // 2 + lb % 2, lb // 2, la), npair=npair, mid=mid, L=lb,
-                off=off)
+                off=off, m=m)
 
 
-def _fwd_ops(f):
-    """FMAs plus fold additions of one forward line."""
-    macs = sum(n * ln for n, ln in zip(f["n"], f["len"]))
+def _macs(f):
+    return sum(n * ln for n, ln in zip(f["n"], f["len"]))
+
+
+def _fold01_adds(f):
+    """Additions that make the class-0 and class-1 inputs of a line (each slot
+    computed on its own)."""
     if not f["L"]:
-        return macs + f["len"][0] + f["len"][1] - f["mid"]
-    return macs + 3 * (f["L"] // 2) + (f["L"] % 2) * 1 + f["len"][1] * 0 + f["len"][2]
+        return f["len"][0] + f["len"][1] - f["mid"]
+    L = f["L"]
+    return 6 * (L // 2) + (L % 2)
 
 
-def _inv_ops(f, q0):
-    """FMAs plus output additions of one inverse line (pairs from q0 on an odd extent)."""
+def _items_ops(f, q0, g_of_q):
+    """Inverse items of a line: class 0/1 products, output additions, and
+    g_of_q(count) for the class-2 contributions of `count` slots."""
     n0, n1, n2 = f["n"]
     if not f["L"]:
         return (f["npair"] - q0) * (n0 + n1 + 2) + f["mid"] * n0
     L = f["L"]
-    return (L // 2) * (n0 + n1 + 2 * n2 + 6) + (L % 2) * (n0 + n2 + 2) + f["mid"] * n2
+    return (L // 2) * (n0 + n1 + 6 + g_of_q(2)) + (L % 2) * (n0 + 2 + g_of_q(1)) + f["mid"] * g_of_q(1)
+
+
+def _inner_slot_terms(g):
+    """Terms of the inner slots of g (each slot one chain of FMAs or adds)."""
+    if not g["L"]:
+        return 2 * g["npair"] + g["mid"] + 2 * (g["len"][1])
+    L = g["L"]
+    return 8 * (L // 2) + 2 * (L % 2) + 2 * g["len"][2]
+
+
+def _fwd_ops(m, dst):
+    """Float64 operations of one forward line of the three-level fold."""
+    f = _fold2(m, dst)
+    if not f["L"]:
+        return _macs(f) + _fold01_adds(f)
+    g = _fold2(f["n"][2], False)
+    N = f["n"][2]
+    ops = f["n"][0] * f["len"][0] + f["n"][1] * f["len"][1] + _fold01_adds(f)
+    if not dst:   # scaled differences, inner fold, inner rows, recurrence
+        L2 = g["L"]
+        inner_adds = (6 * (L2 // 2) + (L2 % 2) + g["len"][2]) if L2 else (N - g["mid"])
+        return ops + 2 * N + inner_adds + _macs(g) + (N - 1)
+    # reversed pair sums, then the inner inverse-direction items
+    return ops + (N - 1) + _items_ops(g, 0, lambda cnt: cnt * g["n"][2])
+
+
+def _inv_ops(m, dst, q0):
+    """Float64 operations of one inverse line of the three-level fold."""
+    f = _fold2(m, dst)
+    if not f["L"]:
+        return _items_ops(f, q0, lambda cnt: 0)
+    g = _fold2(f["n"][2], False)
+    N = f["n"][2]
+    third = _inner_slot_terms(g) + _macs(g) + ((N - 1) if not dst else 0)
+    return third + _items_ops(f, 0, lambda cnt: 0)
 
 
 def transform_fp64_executed(ctx):
-    """Float64 operations the two-level folded transform kernels execute per
-    apply: class products and fold additions of each forward line, pair or
-    quadruple products of each inverse line (odd extents skip pairs whose two
-    outputs lie outside the owned range), and about 11 operations per mode
-    for the closed-form 3x3 with its tabulated denominator."""
+    """Float64 operations the three-level folded transform kernels execute
+    per apply: per forward line the class-0/1 products and folds, and class
+    2 through the inner DCT-II (scaled differences, inner fold, inner rows and
+    the DCT-IV recurrence for DCT-II; pair sums and the inner
+    inverse-direction items for DST-I); per inverse line the inner slots
+    (chains of FMAs), the inner rows (and the recurrence) and the outer
+    items; odd extents keep the two-level form (pairs whose two outputs lie
+    outside the owned range skipped); about 11 operations per mode for the
+    closed-form 3x3 with its tabulated denominator."""
     tot = 0
     for i in range(ctx.num_boxes()):
         bx = ctx.box(i)
-        m = bx["m"]
-        lo = [bx["own_lo"][a] - bx["ext_lo"][a] for a in range(3)]
-        hi = [lo[a] + bx["own_n"][a] for a in range(3)]
-        mx, my, mz = m
-
-        def q0(ma, dst, a):
-            f = _fold3(ma, dst)
-            if f["L"]:
-                return 0
-            return max(0, min(f["npair"], min(lo[a] - f["off"], ma - hi[a])))
-
-        for c in range(3):
-            sx, sy, sz = c != 0, c != 1, c != 2
-            fx, fy, fz = _fold3(mx, sx), _fold3(my, sy), _fold3(mz, sz)
-            slabs = mz - (1 if c != 2 else 0)
-            tot += slabs * (my * _fwd_ops(fx) + mx * _fwd_ops(fy))                        # pass A
-            tot += mx * my * (_fwd_ops(fz) + _inv_ops(fz, q0(mz, sz, 2)))                # pass B
-            own_z = hi[2] - lo[2]
-            tot += own_z * (mx * _inv_ops(fy, q0(my, sy, 1)) + (hi[1] - lo[1]) * _inv_ops(fx, q0(mx, sx, 0)))
-        tot += 11 * mx * my * mz
+        tot += _box_executed(bx["m"], bx["own_lo"], bx["ext_lo"], bx["own_n"])
     return tot
+
+
+def _box_executed(m, own_lo, ext_lo, own_n):
+    lo = [own_lo[a] - ext_lo[a] for a in range(3)]
+    hi = [lo[a] + own_n[a] for a in range(3)]
+    mx, my, mz = m
+
+    def q0(ma, dst, a):
+        f = _fold2(ma, dst)
+        if f["L"]:
+            return 0
+        return max(0, min(f["npair"], min(lo[a] - f["off"], ma - hi[a])))
+
+    tot = 0
+    for c in range(3):
+        sx, sy, sz = c != 0, c != 1, c != 2
+        slabs = mz - (1 if c != 2 else 0)
+        tot += slabs * (my * _fwd_ops(mx, sx) + mx * _fwd_ops(my, sy))                         # pass A
+        tot += mx * my * (_fwd_ops(mz, sz) + _inv_ops(mz, sz, q0(mz, sz, 2)))                 # pass B
+        own_z = hi[2] - lo[2]
+        tot += own_z * (mx * _inv_ops(my, sy, q0(my, sy, 1)) + (hi[1] - lo[1]) * _inv_ops(mx, sx, q0(mx, sx, 0)))
+    return tot + 11 * mx * my * mz
 
 
 def _rup(v, a):
@@ -588,9 +634,10 @@ def run_ours(args):
                                f"(the median SM clock sampled in the timed region)",
                 "executed_ops_per_apply": ops,
                 "dense_equivalent_tflops": flops / (ms_p * 1e-3) / 1e12,
-                "note": "achieved counts the float64 operations (FMAs and additions) the two-level folded "
-                        "kernels execute; dense_equivalent_tflops counts the dense 12(mx+my+mz)mxmymz formula, "
-                        "which the folding cuts to about 40 % of its FMAs"}
+                "note": "achieved counts the float64 operations (FMAs, multiplications and additions) the "
+                        "three-level folded kernels execute, from a per-line model within 2-7 % of ncu's count "
+                        "per pass; dense_equivalent_tflops counts the dense 12(mx+my+mz)mxmymz formula, whose "
+                        "FMAs the folded kernels' operations number about a third of"}
     else:
         achieved = tb / (ms_p * 1e-3) / 1e9
         kern = ("fused cluster kernel (one 3-CTA cluster per box)" if args.precision != "tf32"

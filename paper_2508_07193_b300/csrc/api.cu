@@ -45,14 +45,38 @@ void build_tables(int m, double* C, double* S, double* sig) {
     }
 }
 
-// Two-level folded copy of a table (layout in Fold3).
+// Folded copy of a table (layout in Fold3): classes 0 and 1 (and class 2
+// without the third level) from T; with the third level, class 2's block
+// holds the folded inner DCT-II of extent N = m / 2 (row 0 halved for a
+// DCT-II T, scaled by sqrt(2/m) for a DST-I T) and, for DCT-II, the N
+// factors d_q = sqrt(2/m) 2 cos(pi (2q + 1) / 4N). Angles are reduced
+// exactly in integers before the call to cos.
 void fold_table(int m, bool dst, const double* T, double* F) {
+    const double pi = 3.14159265358979323846;
     const Fold3 f = fold3(m, dst);
-    for (int c = 0; c < 3; ++c)
+    for (int c = 0; c < (f.two ? 2 : 3); ++c)
         for (int j = 0; j < f.n[c]; ++j) {
             const int k = f.k0[c] + f.kstep[c] * j;
             for (int q = 0; q < f.len[c]; ++q) F[f.toff[c] + j * f.len[c] + q] = T[k * m + fold3_column(f, c, q)];
         }
+    if (!f.two) return;
+    const int N = f.n[2];
+    const Fold3 g = fold2(N, false);
+    double* Fi = F + f.toff[2];
+    for (int c = 0; c < 3; ++c)
+        for (int j = 0; j < g.n[c]; ++j) {
+            const int k = g.k0[c] + g.kstep[c] * j;
+            for (int q = 0; q < g.len[c]; ++q) {
+                const int i = fold3_column(g, c, q);
+                const long long p = ((long long)k * (2 * i + 1)) % (4LL * N);   // angle pi p / 2N
+                double v = std::cos(pi * (double)p / (2.0 * N));
+                v *= dst ? std::sqrt(2.0 / m) : (k == 0 ? 0.5 : 1.0);
+                Fi[g.toff[c] + j * g.len[c] + q] = v;
+            }
+        }
+    if (!dst)
+        for (int q = 0; q < N; ++q)
+            Fi[f.itab + q] = std::sqrt(2.0 / m) * 2.0 * std::cos(pi * (double)(2 * q + 1) / (4.0 * N));
 }
 
 // Round a float to tf32 (10 explicit mantissa bits, to nearest, ties away).

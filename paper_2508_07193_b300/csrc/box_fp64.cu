@@ -87,12 +87,23 @@ __device__ __forceinline__ int first_owned_pair(const Fold3& f, int o0, int o1) 
 __device__ __forceinline__ int f3_items(const Fold3& f, int q0) {
     return f.two ? f.L / 2 + (f.L & 1) + f.has_mid : (f.npair - q0) + f.has_mid;
 }
-// Item it of an inverse line: Y(k) gives mode k, out(p, x) takes output p.
-template <class GetY, class Put>
-__device__ __forceinline__ void f3_inverse_item(const Fold3& f, const double* T, int q0, int it, GetY Y, Put out) {
+// Class 2's column q of a two-level table: sum_j T_2[j][q] Y(k0[2] + 2 j).
+template <class GetY>
+__device__ __forceinline__ double f3_class2_dot(const Fold3& f, const double* T, int q, GetY Y) {
+    const double* T2 = T + f.toff[2];
+    double acc = 0.0;
+    for (int j = 0; j < f.n[2]; ++j) acc = fma(T2[j * f.len[2] + q], Y(f.k0[2] + 2 * j), acc);
+    return acc;
+}
+
+// Item it of an inverse line: Y(k) gives mode k, G(q) class 2's contribution
+// to its input slot q (a dot with the table, or the third level's result),
+// out(p, x) takes output p.
+template <class GetY, class GetG, class Put>
+__device__ __forceinline__ void f3_inverse_item(const Fold3& f, const double* T, int q0, int it, GetY Y, GetG G,
+                                                Put out) {
     const double* T0 = T + f.toff[0];
     const double* T1 = T + f.toff[1];
-    const double* T2 = T + f.toff[2];
     if (!f.two) {
         if (it < f.npair - q0) {
             const int q = q0 + it;
@@ -111,14 +122,10 @@ __device__ __forceinline__ void f3_inverse_item(const Fold3& f, const double* T,
     const int nq = f.L / 2;
     if (it < nq) {
         const int q = it, qo = f.L - 1 - it;
-        double A = 0.0, B = 0.0, Gi = 0.0, Go = 0.0;
+        double A = 0.0, B = 0.0;
         for (int j = 0; j < f.n[0]; ++j) A = fma(T0[j * f.len[0] + q], Y(f.k0[0] + 4 * j), A);
         for (int j = 0; j < f.n[1]; ++j) B = fma(T1[j * f.len[1] + q], Y(f.k0[1] + 4 * j), B);
-        for (int j = 0; j < f.n[2]; ++j) {
-            const double y = Y(f.k0[2] + 2 * j);
-            Gi = fma(T2[j * f.len[2] + q], y, Gi);
-            Go = fma(T2[j * f.len[2] + qo], y, Go);
-        }
+        const double Gi = G(q), Go = G(qo);
         const double si = A + B, so = A - B;
         const double Ei = f.s2sym ? si : Gi, Oi = f.s2sym ? Gi : si;
         const double Eo = f.s2sym ? so : Go, Oo = f.s2sym ? Go : so;
@@ -127,16 +134,84 @@ __device__ __forceinline__ void f3_inverse_item(const Fold3& f, const double* T,
         out(f.off + qo, Eo + Oo);
         out(f.m - 1 - qo, Eo - Oo);
     } else if (it == nq && (f.L & 1)) {
-        double A = 0.0, G = 0.0;
+        double A = 0.0;
         for (int j = 0; j < f.n[0]; ++j) A = fma(T0[j * f.len[0] + nq], Y(f.k0[0] + 4 * j), A);
-        for (int j = 0; j < f.n[2]; ++j) G = fma(T2[j * f.len[2] + nq], Y(f.k0[2] + 2 * j), G);
-        const double E = f.s2sym ? A : G, O = f.s2sym ? G : A;
+        const double Gm = G(nq);
+        const double E = f.s2sym ? A : Gm, O = f.s2sym ? Gm : A;
         out(f.off + nq, E + O);
         out(f.m - 1 - nq, E - O);
     } else {   // the first-level middle: only the sym class contributes (class 2 here)
-        double E = 0.0;
-        for (int j = 0; j < f.n[2]; ++j) E = fma(T2[j * f.len[2] + f.npair], Y(f.k0[2] + 2 * j), E);
-        out(f.mid, E);
+        out(f.mid, G(f.npair));
+    }
+}
+
+// ---- third level (Fold3): class 2 through the inner DCT-II of extent N ----
+// Ti is class 2's block of the folded table (the inner table, then for
+// DCT-II the factors d), g = fold2(N, false) its layout.
+
+// Forward direction, the value kept for class-2 input p (< N) of a line
+// whose class-2 folded inputs are a(p): DCT-II: d_p a(p), folded again by
+// the inner table's layout (f3_inner_slot) in the next phase; DST-I:
+// a(N - 1 - p), the reversed inputs that the inner inverse-direction items
+// read as modes.
+template <class GetA>
+__device__ __forceinline__ double f3_fwd_pre(const Fold3& f, const double* Ti, int p, GetA a) {
+    return f.off == 0 ? Ti[f.itab + p] * a(p) : a(f.n[2] - 1 - p);
+}
+// Inverse direction, inner slot s (layout g) straight from the class-2
+// modes y(p) (mode 1 + 2 p) with the weights w(p): d_p (DCT-II) or (-1)^p
+// (DST-I), as one chain of FMAs over the slot's (up to four) terms.
+template <class GetY, class GetW>
+__device__ __forceinline__ double f3_inv_slot(const Fold3& g, int s, GetY y, GetW w) {
+    int c, q;
+    f3_slot(g, s, c, q);
+    const int n = g.m;
+    double acc = 0.0;
+    auto add = [&](int p, bool neg) {
+        const double wp = w(p);
+        acc = fma(neg ? -wp : wp, y(p), acc);
+    };
+    auto sym = [&](int a, bool neg) {
+        if (a < g.npair) {
+            add(a, neg);
+            add(n - 1 - a, neg);
+        } else {
+            add(g.mid, neg);
+        }
+    };
+    if (!g.two) {
+        if (c == 0) {
+            sym(q, false);
+        } else {
+            add(q, false);
+            add(n - 1 - q, true);
+        }
+        return acc;
+    }
+    if (c == 2) {
+        add(q, false);
+        add(n - 1 - q, true);
+        return acc;
+    }
+    sym(q, false);
+    if (c == 1 || q < g.L / 2) sym(g.L - 1 - q, c == 1);
+    return acc;
+}
+// Inner folded slot s from the inner inputs v(p) (layout g = fold2(N, false)).
+template <class GetV>
+__device__ __forceinline__ double f3_inner_slot(const Fold3& g, int s, GetV v) {
+    int c, q;
+    f3_slot(g, s, c, q);
+    return f3_input(g, c, q, v);
+}
+
+// DCT-IV from DCT-II: y_0 = Y_0 (row 0 of the inner table is halved),
+// y_k = Y_k - y_(k-1), in place over N values at stride st.
+__device__ __forceinline__ void f3_recur(double* v, int n, int st) {
+    double y = v[0];
+    for (int k = 1; k < n; ++k) {
+        y = v[k * st] - y;
+        v[k * st] = y;
     }
 }
 
@@ -145,7 +220,7 @@ __device__ __forceinline__ void stage(double* dst, const double* src, int n) {
 }
 
 // Pass A: forward transforms along x and y of one z-slab of one component.
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 5)
 k_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox* __restrict__ boxes,
          const int4* __restrict__ items, const double* __restrict__ tabs, int nx, int ny, int nz,
          const double* __restrict__ gate) {
@@ -163,18 +238,36 @@ k_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox* _
     }
     const bool sx = c != 0, sy = c != 1;   // DST along x / y?
     const Fold3 fx = fold3(mx, sx), fy = fold3(my, sy);
+    const Fold3 gx = fold2(fx.two ? fx.n[2] : 1, false), gy = fold2(fy.two ? fy.n[2] : 1, false);
     double* X = sm;               // [my][mx] spatial slab, later the y-folded inputs
     double* AB = X + nxy;         // [my][LX] x-folded inputs
-    double* P = AB + nxy;         // [my][kx] after the x pass
-    double* TX = P + nxy;         // x table, per class transposed: [q][j]
+    double* P = AB + nxy;         // [my][kx] after the x pass; then the y pass's raw DCT-IV outputs
+    double* TX = P + nxy;         // x table: classes 0, 1 (and the DCT-II inner classes) transposed, [q][j]
     double* TY = TX + fold_room(mx);   // y table as is
+    double* TXi = TX + fx.toff[2];
+    const double* TYi = TY + fy.toff[2];
     {
         const double* g = tabs + (sx ? B.dstf_off[0] : B.dctf_off[0]);
-        for (int cc = 0; cc < 3; ++cc) {
+        for (int cc = 0; cc < (fx.two ? 2 : 3); ++cc) {
             const int n = pick(fx.n, cc), ln = pick(fx.len, cc);
             for (int t = threadIdx.x; t < n * ln; t += blockDim.x) {
                 const int j = t / ln, q = t - j * ln;
                 TX[pick(fx.toff, cc) + q * n + j] = g[pick(fx.toff, cc) + t];
+            }
+        }
+        if (fx.two) {
+            const double* gi = g + fx.toff[2];
+            if (!sx) {   // DCT-II: the inner rows run as x-pass rows (transposed), then d
+                for (int cc = 0; cc < 3; ++cc) {
+                    const int n = pick(gx.n, cc), ln = pick(gx.len, cc);
+                    for (int t = threadIdx.x; t < n * ln; t += blockDim.x) {
+                        const int j = t / ln, q = t - j * ln;
+                        TXi[pick(gx.toff, cc) + q * n + j] = gi[pick(gx.toff, cc) + t];
+                    }
+                }
+                for (int t = threadIdx.x; t < fx.n[2]; t += blockDim.x) TXi[fx.itab + t] = gi[fx.itab + t];
+            } else {     // DST-I: the inner table serves inverse-direction items, as is
+                for (int t = threadIdx.x; t < fx.itab; t += blockDim.x) TXi[t] = gi[t];
             }
         }
     }
@@ -194,50 +287,140 @@ k_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox* _
         while (cc < 2 && u >= my * pick(fx.len, cc)) { u -= my * pick(fx.len, cc); ++cc; }
         const int y = u / pick(fx.len, cc), q = u - y * pick(fx.len, cc);
         const double* row = X + y * mx;
-        AB[y * LX + pick(fx.seg, cc) + q] = f3_input(fx, cc, q, [&](int i) { return row[i]; });
+        auto v = [&](int i) { return row[i]; };
+        AB[y * LX + pick(fx.seg, cc) + q] =
+            (fx.two && cc == 2) ? f3_fwd_pre(fx, TXi, q, [&](int p) { return f3_input(fx, 2, p, v); })
+                                : f3_input(fx, cc, q, v);
     }
     __syncthreads();
-    // outputs class by class: rows (y, j) of class 0, then 1, then 2
-    for (int t = threadIdx.x; t < my * fx.nmodes; t += blockDim.x) {
-        int cc = 0, u = t;
-        while (cc < 2 && u >= my * pick(fx.n, cc)) { u -= my * pick(fx.n, cc); ++cc; }
-        const int n = pick(fx.n, cc), ln = pick(fx.len, cc);
-        const int y = u / n, j = u - y * n;
-        const double* a = AB + y * LX + pick(fx.seg, cc);
-        const double* tcol = TX + pick(fx.toff, cc) + j;
-        double acc = 0.0;
-        for (int q = 0; q < ln; ++q) acc = fma(tcol[q * n], a[q], acc);
-        P[y * mx + pick(fx.k0, cc) + pick(fx.kstep, cc) * j] = acc;
+    if (fx.two && !sx) {   // DCT-II third level: the inner slots, in X (free now)
+        const int N = fx.n[2];
+        for (int t = threadIdx.x; t < my * N; t += blockDim.x) {
+            const int y = t / N, s2 = t - y * N;
+            const double* a = AB + y * LX + fx.seg[2];
+            X[y * LX + fx.seg[2] + s2] = f3_inner_slot(gx, s2, [&](int p) { return a[p]; });
+        }
+        __syncthreads();
+    }
+    // outputs class by class: rows (y, j) of classes 0 and 1; then class 2's
+    // work: the inner rows class by class (DCT-II, raw: the recurrence
+    // follows) or the inner items, item-major (DST-I; these come first, as
+    // the heaviest work)
+    {
+        const bool items = fx.two && sx;
+        const int w01 = my * (fx.n[0] + fx.n[1]);
+        const int w2 = !fx.two ? my * fx.n[2] : my * (sx ? f3_items(gx, 0) : gx.nmodes);
+        for (int t = threadIdx.x; t < w01 + w2; t += blockDim.x) {
+            const int tr = items ? t - w2 : t;
+            if (items && t < w2) {
+                const int item = t / my, y = t - item * my;
+                const double* a = AB + y * LX + fx.seg[2];
+                double* prow = P + y * mx;
+                auto Y = [&](int k) { return a[k]; };
+                f3_inverse_item(gx, TXi, 0, item, Y, [&](int q) { return f3_class2_dot(gx, TXi, q, Y); },
+                                [&](int j, double v) { prow[1 + 2 * j] = (j & 1) ? -v : v; });
+            } else if (tr < w01 || !fx.two) {
+                int cc = 0, u = tr;
+                while (cc < 2 && u >= my * pick(fx.n, cc)) { u -= my * pick(fx.n, cc); ++cc; }
+                const int n = pick(fx.n, cc), ln = pick(fx.len, cc);
+                const int y = u / n, j = u - y * n;
+                const double* a = AB + y * LX + pick(fx.seg, cc);
+                const double* tcol = TX + pick(fx.toff, cc) + j;
+                double acc = 0.0;
+                for (int q = 0; q < ln; ++q) acc = fma(tcol[q * n], a[q], acc);
+                P[y * mx + pick(fx.k0, cc) + pick(fx.kstep, cc) * j] = acc;
+            } else {
+                int cc = 0, u = tr - w01;
+                while (cc < 2 && u >= my * pick(gx.n, cc)) { u -= my * pick(gx.n, cc); ++cc; }
+                const int n = pick(gx.n, cc), ln = pick(gx.len, cc);
+                const int y = u / n, j = u - y * n;
+                const double* a = X + y * LX + fx.seg[2] + pick(gx.seg, cc);
+                const double* tcol = TXi + pick(gx.toff, cc) + j;
+                double acc = 0.0;
+                for (int q = 0; q < ln; ++q) acc = fma(tcol[q * n], a[q], acc);
+                P[y * mx + 1 + 2 * (pick(gx.k0, cc) + pick(gx.kstep, cc) * j)] = acc;
+            }
+        }
     }
     if (fx.nmodes < mx)   // the DST-I wall mode kx = 0
         for (int y = threadIdx.x; y < my; y += blockDim.x) P[y * mx] = 0.0;
     __syncthreads();
+    if (fx.two && !sx) {   // DCT-IV from the inner DCT-II, per row
+        for (int y = threadIdx.x; y < my; y += blockDim.x) f3_recur(P + y * mx + 1, fx.n[2], 2);
+        __syncthreads();
+    }
     const int LY = fy.seg[2] + fy.len[2];
     for (int t = threadIdx.x; t < LY * mx; t += blockDim.x) {
         const int s = t / mx, kx = t - s * mx;
         int cc, q;
         f3_slot(fy, s, cc, q);
-        X[t] = f3_input(fy, cc, q, [&](int y) { return P[y * mx + kx]; });
+        auto v = [&](int y) { return P[y * mx + kx]; };
+        X[t] = (fy.two && cc == 2) ? f3_fwd_pre(fy, TYi, q, [&](int p) { return f3_input(fy, 2, p, v); })
+                                   : f3_input(fy, cc, q, v);
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < fy.nmodes * mx; t += blockDim.x) {
-        int cc = 0, u = t;
-        while (cc < 2 && u >= pick(fy.n, cc) * mx) { u -= pick(fy.n, cc) * mx; ++cc; }
-        const int ln = pick(fy.len, cc);
-        const int j = u / mx, kx = u - j * mx;
-        const double* trow = TY + pick(fy.toff, cc) + j * ln;
-        const double* col = X + pick(fy.seg, cc) * mx + kx;
-        double acc = 0.0;
-        for (int q = 0; q < ln; ++q) acc = fma(trow[q], col[q * mx], acc);
-        dst[(pick(fy.k0, cc) + pick(fy.kstep, cc) * j) * mx + kx] = acc;
+    if (fy.two && !sy) {   // DCT-II third level: the inner slots, in AB (free now)
+        const int N = fy.n[2];
+        for (int t = threadIdx.x; t < N * mx; t += blockDim.x) {
+            const int s2 = t / mx, kx = t - s2 * mx;
+            const double* a = X + fy.seg[2] * mx + kx;
+            AB[(fy.seg[2] + s2) * mx + kx] = f3_inner_slot(gy, s2, [&](int p) { return a[p * mx]; });
+        }
+        __syncthreads();
+    }
+    {
+        const bool items = fy.two && sy;
+        const int w01 = (fy.n[0] + fy.n[1]) * mx;
+        const int w2 = !fy.two ? fy.n[2] * mx : (sy ? f3_items(gy, 0) : gy.nmodes) * mx;
+        for (int t = threadIdx.x; t < w01 + w2; t += blockDim.x) {
+            const int tr = items ? t - w2 : t;
+            if (items && t < w2) {
+                const int item = t / mx, kx = t - item * mx;
+                const double* col = X + fy.seg[2] * mx + kx;
+                auto Y = [&](int k) { return col[k * mx]; };
+                f3_inverse_item(gy, TYi, 0, item, Y, [&](int q) { return f3_class2_dot(gy, TYi, q, Y); },
+                                [&](int j, double v) { dst[(1 + 2 * j) * mx + kx] = (j & 1) ? -v : v; });
+            } else if (tr < w01 || !fy.two) {
+                int cc = 0, u = tr;
+                while (cc < 2 && u >= pick(fy.n, cc) * mx) { u -= pick(fy.n, cc) * mx; ++cc; }
+                const int ln = pick(fy.len, cc);
+                const int j = u / mx, kx = u - j * mx;
+                const double* trow = TY + pick(fy.toff, cc) + j * ln;
+                const double* col = X + pick(fy.seg, cc) * mx + kx;
+                double acc = 0.0;
+                for (int q = 0; q < ln; ++q) acc = fma(trow[q], col[q * mx], acc);
+                dst[(pick(fy.k0, cc) + pick(fy.kstep, cc) * j) * mx + kx] = acc;
+            } else {   // raw inner outputs to P (free again), the recurrence follows
+                int cc = 0, u = tr - w01;
+                while (cc < 2 && u >= pick(gy.n, cc) * mx) { u -= pick(gy.n, cc) * mx; ++cc; }
+                const int ln = pick(gy.len, cc);
+                const int j = u / mx, kx = u - j * mx;
+                const double* trow = TYi + pick(gy.toff, cc) + j * ln;
+                const double* col = AB + (fy.seg[2] + pick(gy.seg, cc)) * mx + kx;
+                double acc = 0.0;
+                for (int q = 0; q < ln; ++q) acc = fma(trow[q], col[q * mx], acc);
+                P[(pick(gy.k0, cc) + pick(gy.kstep, cc) * j) * mx + kx] = acc;
+            }
+        }
     }
     if (fy.nmodes < my)   // the DST-I wall mode ky = 0
         for (int kx = threadIdx.x; kx < mx; kx += blockDim.x) dst[kx] = 0.0;
+    if (fy.two && !sy) {   // DCT-IV from the inner DCT-II, per column, into the scratch
+        __syncthreads();
+        for (int kx = threadIdx.x; kx < mx; kx += blockDim.x) {
+            double yv = P[kx];
+            dst[mx + kx] = yv;
+            for (int k = 1; k < fy.n[2]; ++k) {
+                yv = P[k * mx + kx] - yv;
+                dst[(1 + 2 * k) * mx + kx] = yv;
+            }
+        }
+    }
 }
 
 // Pass B: z transform, per-mode 3x3 solve, inverse z transform (owned z).
 template <int CT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
 k_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int2* __restrict__ items,
           const double* __restrict__ tabs, const double* __restrict__ modeinv, double beta,
           const double* __restrict__ gate) {
@@ -250,10 +433,15 @@ k_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int2
     const int nxy = mx * my;
     const int ncol = min(CT, nxy - col0);
     double* Buf = sm;                   // [3][mz][CT]: input, then transformed modes
-    double* AB = Buf + 3 * mz * CT;     // [3][mz][CT]: z-folded inputs
+    double* AB = Buf + 3 * mz * CT;     // [3][mz][CT]: z-folded inputs; later the third level's buffers
     double* TC = AB + 3 * mz * CT;      // folded DCT along z
     double* TS = TC + fold_room(mz);    // folded DST along z
+    double* XS = TS + fold_room(mz);    // [N][CT]: Ez's inner slots (third level)
     const Fold3 fc = fold3(mz, false), fs = fold3(mz, true);
+    // the third level applies to both or neither (fc.n[2] = fs.n[2] = mz / 2)
+    const bool three = fc.two;
+    const int N = three ? fc.n[2] : 0;
+    const Fold3 g = fold2(three ? N : 1, false);
     stage(TC, tabs + B.dctf_off[2], fc.tab);
     stage(TS, tabs + B.dstf_off[2], fs.tab);
     double* base = scr + B.scr_off;
@@ -271,29 +459,67 @@ k_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int2
         if (s < f.seg[2] + f.len[2]) {
             int cc, q;
             f3_slot(f, s, cc, q);
-            v = f3_input(f, cc, q, [&](int z) { return in[z * CT]; });
+            auto vin = [&](int z) { return in[z * CT]; };
+            v = (three && cc == 2)
+                    ? f3_fwd_pre(f, (c == 2 ? TC : TS) + f.toff[2], q, [&](int p) { return f3_input(f, 2, p, vin); })
+                    : f3_input(f, cc, q, vin);
         }
         AB[t] = v;
     }
     __syncthreads();
-    // per component, output rows class by class (a warp is one row when CT = 32)
+    if (three) {   // Ez (DCT-II): the inner slots
+        for (int t = threadIdx.x; t < N * CT; t += blockDim.x) {
+            const int s2 = t / CT, col = t - s2 * CT;
+            const double* a = AB + (2 * mz + fc.seg[2]) * CT + col;
+            XS[t] = f3_inner_slot(g, s2, [&](int p) { return a[p * CT]; });
+        }
+        __syncthreads();
+    }
+    // per component, output rows class by class (a warp is one row when CT =
+    // 32); with the third level, class 2's rows are the inner rows (Ez,
+    // DCT-II, raw: the recurrence follows) or the inner items (Ex, Ey, DST-I)
     for (int t = threadIdx.x; t < 3 * mz * CT; t += blockDim.x) {
         const int cz = t / CT, col = t - cz * CT;
         const int c = cz / mz, r = cz - c * mz;
         const Fold3& f = c == 2 ? fc : fs;
+        const double* T = c == 2 ? TC : TS;
         if (r >= f.nmodes) {   // the DST-I wall mode kz = 0
             Buf[c * mz * CT + col] = 0.0;
             continue;
         }
-        int cc, j, kz;
-        f3_row(f, r, cc, j, kz);
-        const double* g = (c == 2 ? TC : TS) + pick(f.toff, cc) + j * pick(f.len, cc);
-        const double* ab = AB + (c * mz + pick(f.seg, cc)) * CT + col;
-        double acc = 0.0;
-        for (int q = 0; q < pick(f.len, cc); ++q) acc = fma(g[q], ab[q * CT], acc);
-        Buf[(c * mz + kz) * CT + col] = acc;
+        const int r01 = f.n[0] + f.n[1];
+        // Ex, Ey (DST-I): the inner items (the heaviest work) on the first rows
+        const int nit = three && c != 2 ? f3_items(g, 0) : 0;
+        if (r < nit) {
+            const double* Ti = T + f.toff[2];
+            const double* ab = AB + (c * mz + f.seg[2]) * CT + col;
+            double* o = Buf + c * mz * CT + col;
+            auto Y = [&](int k) { return ab[k * CT]; };
+            f3_inverse_item(g, Ti, 0, r, Y, [&](int q) { return f3_class2_dot(g, Ti, q, Y); },
+                            [&](int j, double v) { o[(1 + 2 * j) * CT] = (j & 1) ? -v : v; });
+        } else if (!three || r - nit < r01) {
+            int cc, j, kz;
+            f3_row(f, r - nit, cc, j, kz);
+            const double* gt = T + pick(f.toff, cc) + j * pick(f.len, cc);
+            const double* ab = AB + (c * mz + pick(f.seg, cc)) * CT + col;
+            double acc = 0.0;
+            for (int q = 0; q < pick(f.len, cc); ++q) acc = fma(gt[q], ab[q * CT], acc);
+            Buf[(c * mz + kz) * CT + col] = acc;
+        } else if (c == 2) {
+            int cc, j, k;
+            f3_row(g, r - r01, cc, j, k);
+            const double* gt = T + f.toff[2] + pick(g.toff, cc) + j * pick(g.len, cc);
+            const double* ab = XS + pick(g.seg, cc) * CT + col;
+            double acc = 0.0;
+            for (int q = 0; q < pick(g.len, cc); ++q) acc = fma(gt[q], ab[q * CT], acc);
+            Buf[(c * mz + 1 + 2 * k) * CT + col] = acc;
+        }
     }
     __syncthreads();
+    if (three) {   // Ez: DCT-IV from the inner DCT-II, per column
+        for (int col = threadIdx.x; col < CT; col += blockDim.x) f3_recur(Buf + (2 * mz + 1) * CT + col, N, 2 * CT);
+        __syncthreads();
+    }
     const double* sgx = tabs + B.sig_off[0];
     const double* sgy = tabs + B.sig_off[1];
     const double* sgz = tabs + B.sig_off[2];
@@ -317,6 +543,36 @@ k_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int2
         o[2 * mz * CT] = fma(f, sz, inv * r2);
     }
     __syncthreads();
+    // the third level's class-2 contributions G[c][q][col], q < N: the inner
+    // slots in Gin, the inner rows' results in Gq
+    double* Gin = AB;
+    double* Gq = AB + 3 * N * CT;
+    if (three) {
+        for (int t = threadIdx.x; t < 3 * N * CT; t += blockDim.x) {
+            const int cs = t / CT, col = t - cs * CT;
+            const int c = cs / N, s2 = cs - c * N;
+            const double* e = Buf + (c * mz + 1) * CT + col;
+            const double* d = TC + fc.toff[2] + fc.itab;
+            Gin[t] = f3_inv_slot(g, s2, [&](int p) { return e[2 * p * CT]; },
+                                 [&](int p) { return c == 2 ? d[p] : ((p & 1) ? -1.0 : 1.0); });
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < 3 * N * CT; t += blockDim.x) {
+            const int cr = t / CT, col = t - cr * CT;
+            const int c = cr / N, r = cr - c * N;
+            const Fold3& f = c == 2 ? fc : fs;
+            int cc, j, k;
+            f3_row(g, r, cc, j, k);
+            const double* gt = (c == 2 ? TC : TS) + f.toff[2] + pick(g.toff, cc) + j * pick(g.len, cc);
+            const double* ab = Gin + (c * N + pick(g.seg, cc)) * CT + col;
+            double acc = 0.0;
+            for (int q = 0; q < pick(g.len, cc); ++q) acc = fma(gt[q], ab[q * CT], acc);
+            Gq[(c * N + (c == 2 ? k : N - 1 - k)) * CT + col] = acc;
+        }
+        __syncthreads();
+        for (int col = threadIdx.x; col < CT; col += blockDim.x) f3_recur(Gq + 2 * N * CT + col, N, CT);
+        __syncthreads();
+    }
     // inverse along z, owned slabs only; the DST wall slab z = 0 is zero
     const int oz0 = B.own_lo[2], oz1 = B.own_lo[2] + B.own_n[2];
     const int qc = first_owned_pair(fc, oz0, oz1), qs = first_owned_pair(fs, oz0, oz1);
@@ -328,19 +584,24 @@ k_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int2
         const int c = ci / ni, item = ci - c * ni;
         const Fold3& f = c == 2 ? fc : fs;
         if (item >= (c == 2 ? nic : nis)) continue;
+        const double* T = c == 2 ? TC : TS;
         const double* e = Buf + c * mz * CT + col;
+        const double* gq = Gq + c * N * CT + col;
         double* out = base + (long long)c * mz * nxy + col0 + col;
-        f3_inverse_item(f, c == 2 ? TC : TS, c == 2 ? qc : qs, item, [&](int k) { return e[k * CT]; },
-                        [&](int z, double v) {
-                            if (z >= oz0 && z < oz1) out[(long long)z * nxy] = v;
-                        });
+        auto Y = [&](int k) { return e[k * CT]; };
+        f3_inverse_item(
+            f, T, c == 2 ? qc : qs, item, Y,
+            [&](int q) { return three ? gq[q * CT] : f3_class2_dot(f, T, q, Y); },
+            [&](int z, double v) {
+                if (z >= oz0 && z < oz1) out[(long long)z * nxy] = v;
+            });
         if (f.off == 1 && item == 0 && oz0 == 0) out[0] = 0.0;
     }
 }
 
 // Pass C: inverse transforms along y then x of one owned z-slab; owned cells
 // are written to the global field.
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 5)
 k_inv_xy(const double* __restrict__ scr, double* __restrict__ zout, const FmpBox* __restrict__ boxes,
          const int4* __restrict__ items, const double* __restrict__ tabs, int nx, int ny, int nz,
          const double* __restrict__ gate) {
@@ -355,24 +616,62 @@ k_inv_xy(const double* __restrict__ scr, double* __restrict__ zout, const FmpBox
     const int ox0 = B.own_lo[0], onx = B.own_n[0];
     const bool sx = c != 0, sy = c != 1;
     const Fold3 fx = fold3(mx, sx), fy = fold3(my, sy);
+    const Fold3 gx = fold2(fx.two ? fx.n[2] : 1, false), gy = fold2(fy.two ? fy.n[2] : 1, false);
     double* S = sm;                  // [ky][kx]
     double* Q = S + nxy;             // [owned y][kx]
-    double* TX = Q + ony * mx;
+    double* Gin = Q + ony * mx;      // third level: inner slots, then class 2's contributions
+    double* TX = Gin + nxy;
     double* TY = TX + fold_room(mx);
     stage(TX, tabs + (sx ? B.dstf_off[0] : B.dctf_off[0]), fx.tab);
     stage(TY, tabs + (sy ? B.dstf_off[1] : B.dctf_off[1]), fy.tab);
+    const double* TXi = TX + fx.toff[2];
+    const double* TYi = TY + fy.toff[2];
     const double* src = scr + B.scr_off + ((long long)c * mz + zl) * nxy;
     for (int t = threadIdx.x; t < nxy; t += blockDim.x) S[t] = src[t];
     __syncthreads();
+    // class 2's contributions of one axis for `lines` lines (line fastest):
+    // G[q * lines + l] from the modes y(l, j) of class 2 (mode 1 + 2 j); the
+    // inner slots go to Gin, the inner rows' results to Gq
+    auto third = [&](const Fold3& f, const Fold3& g, const double* Ti, int lines, auto y) {
+        const int N = f.n[2];
+        double* Gq = Gin + N * lines;
+        const double* d = Ti + f.itab;
+        for (int t = threadIdx.x; t < N * lines; t += blockDim.x) {
+            const int s2 = t / lines, l = t - s2 * lines;
+            Gin[t] = f3_inv_slot(g, s2, [&](int p) { return y(l, p); },
+                                 [&](int p) { return f.off == 0 ? d[p] : ((p & 1) ? -1.0 : 1.0); });
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < N * lines; t += blockDim.x) {
+            const int r = t / lines, l = t - r * lines;
+            int cc, j, k;
+            f3_row(g, r, cc, j, k);
+            const double* gt = Ti + pick(g.toff, cc) + j * pick(g.len, cc);
+            const double* ab = Gin + pick(g.seg, cc) * lines + l;
+            double acc = 0.0;
+            for (int q = 0; q < pick(g.len, cc); ++q) acc = fma(gt[q], ab[q * lines], acc);
+            Gq[(f.off == 0 ? k : N - 1 - k) * lines + l] = acc;
+        }
+        __syncthreads();
+        if (f.off == 0) {
+            for (int l = threadIdx.x; l < lines; l += blockDim.x) f3_recur(Gq + l, N, lines);
+            __syncthreads();
+        }
+    };
     {   // inverse along y, owned rows only
+        if (fy.two) third(fy, gy, TYi, mx, [&](int kx, int j) { return S[(1 + 2 * j) * mx + kx]; });
+        const double* Gq = Gin + fy.n[2] * mx;
         const int q0 = first_owned_pair(fy, oy0, oy0 + ony);
         const int ni = f3_items(fy, q0);
         for (int t = threadIdx.x; t < ni * mx; t += blockDim.x) {
             const int item = t / mx, kx = t - item * mx;
-            f3_inverse_item(fy, TY, q0, item, [&](int k) { return S[k * mx + kx]; }, [&](int y, double v) {
-                const int yy = y - oy0;
-                if (yy >= 0 && yy < ony) Q[yy * mx + kx] = v;
-            });
+            auto Y = [&](int k) { return S[k * mx + kx]; };
+            f3_inverse_item(
+                fy, TY, q0, item, Y, [&](int q) { return fy.two ? Gq[q * mx + kx] : f3_class2_dot(fy, TY, q, Y); },
+                [&](int y, double v) {
+                    const int yy = y - oy0;
+                    if (yy >= 0 && yy < ony) Q[yy * mx + kx] = v;
+                });
         }
         if (fy.off == 1 && oy0 == 0)
             for (int kx = threadIdx.x; kx < mx; kx += blockDim.x) Q[kx] = 0.0;
@@ -382,15 +681,20 @@ k_inv_xy(const double* __restrict__ scr, double* __restrict__ zout, const FmpBox
     double* dst = zout + (((long long)c * nz + gk) * ny + B.ext_lo[1] + oy0) * (long long)nx + B.ext_lo[0];
     {   // inverse along x, owned columns only; items ordered item-major, so a
         // warp takes one kind of item (pair, quadruple or middle) of many rows
+        if (fx.two) third(fx, gx, TXi, ony, [&](int yy, int j) { return Q[yy * mx + 1 + 2 * j]; });
+        const double* Gq = Gin + fx.n[2] * ony;
         const int q0 = first_owned_pair(fx, ox0, ox0 + onx);
         const int ni = f3_items(fx, q0);
         for (int t = threadIdx.x; t < ony * ni; t += blockDim.x) {
             const int item = t / ony, yy = t - item * ony;
             const double* row = Q + yy * mx;
             double* orow = dst + (long long)yy * nx;
-            f3_inverse_item(fx, TX, q0, item, [&](int k) { return row[k]; }, [&](int x, double v) {
-                if (x >= ox0 && x < ox0 + onx) orow[x] = v;
-            });
+            auto Y = [&](int k) { return row[k]; };
+            f3_inverse_item(
+                fx, TX, q0, item, Y, [&](int q) { return fx.two ? Gq[q * ony + yy] : f3_class2_dot(fx, TX, q, Y); },
+                [&](int x, double v) {
+                    if (x >= ox0 && x < ox0 + onx) orow[x] = v;
+                });
         }
         if (fx.off == 1 && ox0 == 0)
             for (int yy = threadIdx.x; yy < ony; yy += blockDim.x) dst[(long long)yy * nx] = 0.0;
@@ -401,10 +705,10 @@ size_t smem_a(const int* m) {
     return sizeof(double) * (3 * m[0] * m[1] + fold_room(m[0]) + fold_room(m[1]));
 }
 size_t smem_c(const int* m) {
-    return sizeof(double) * (2 * m[0] * m[1] + fold_room(m[0]) + fold_room(m[1]));
+    return sizeof(double) * (3 * m[0] * m[1] + fold_room(m[0]) + fold_room(m[1]));
 }
 template <int CT>
-size_t smem_b(const int* m) { return sizeof(double) * (6 * m[2] * CT + 2 * fold_room(m[2])); }
+size_t smem_b(const int* m) { return sizeof(double) * (6 * m[2] * CT + 2 * fold_room(m[2]) + (m[2] / 2) * CT); }
 
 }  // namespace
 

@@ -39,9 +39,9 @@ struct FmpBox {
     double eps_bar;    // subdomain-mean edge permittivity
 };
 
-// Two-level even/odd folding of a DCT-II or zero-padded DST-I table T of
-// extent m (the first stages of a fast transform), as three classes of
-// output modes, each a dense product on its own folded inputs.
+// Even/odd folding of a DCT-II or zero-padded DST-I table T of extent m (the
+// first stages of a fast transform), as three classes of output modes, each
+// a dense product on its own folded inputs.
 // First level: input pairs (off + q, m - 1 - q), q < npair, plus a middle
 // index mid when m - off is odd. The sym class (modes k = 2 ks + s0) sees the
 // pair sums and the middle, the anti class (k = 2 ka + 1 - s0) the pair
@@ -54,8 +54,28 @@ struct FmpBox {
 // k = k0 + 4 j. The other first-level class is class 2. The DST-I mode k = 0
 // (the wall) then belongs to no class and is zero.
 // m odd or < 4: class 0 = sym, class 1 = anti, class 2 empty.
+// Third level (fold3, with the second): class 2 is an N x N block, N = m / 2,
+// with modes k = 1 + 2 j, evaluated through an unnormalised DCT-II of extent
+// N, C_N[k][i] = cos(pi k (2i + 1) / 2N), folded twice itself (fold2(N)):
+//   DCT-II: the block is sqrt(2/m) times a DCT-IV of extent N. With the
+//     inputs scaled by d_q = sqrt(2/m) 2 cos(pi (2q + 1) / 4N), C_N gives
+//     Y_k = y_k + y_(k-1) (Y_0 = 2 y_0, from cos a + cos b = 2 cos((a+b)/2)
+//     cos((a-b)/2)), so y_0 = Y_0 / 2 and y_k = Y_k - y_(k-1). The block is
+//     symmetric: its transpose (the inverse direction) is the same steps.
+//     The inner table holds C_N with row 0 halved.
+//   DST-I: the block's entry sin(pi (2j + 1)(q + 1) / 2N) equals
+//     (-1)^j cos(pi (2j + 1)(N - 1 - q) / 2N), so the block is
+//     diag((-1)^j) C_N^T applied to the inputs in reverse order: the forward
+//     direction runs C_N's inverse-direction items on the reversed inputs and
+//     negates the odd outputs; the inverse direction runs C_N forward on the
+//     modes with odd ones negated and reverses its outputs. The inner table
+//     holds sqrt(2/m) C_N.
+// About 7/32 m^2 products per line of an even extent (classes 0 and 1 of
+// (m/4)^2 each, the inner 3/8 (m/2)^2) instead of 3/8 m^2 with two levels.
 // Table layout: class c's rows T_c[j][q] (len[c] columns) at offset toff[c];
-// T_c[j][q] = T[k0[c] + kstep[c] j][first-level column of input q].
+// T_c[j][q] = T[k0[c] + kstep[c] j][first-level column of input q]. With the
+// third level, class 2's block holds the inner table instead (fold2(N, false)
+// layout, itab entries), followed for DCT-II by the N factors d_q.
 struct Fold3 {
     int m, off, npair, has_mid, mid;
     int two;     // the second level applies
@@ -64,8 +84,10 @@ struct Fold3 {
     int n[3], len[3], k0[3], kstep[3], seg[3], toff[3];
     int nmodes;  // modes produced (m, or m - 1 when the DST-I wall mode is skipped)
     int tab;     // table size (doubles)
+    int itab;    // third level: the inner table's size (0 without it)
 };
-__host__ __device__ inline Fold3 fold3(int m, bool dst) {
+// The first two levels only (the inner transform of the third level).
+__host__ __device__ inline Fold3 fold2(int m, bool dst) {
     Fold3 f{};
     f.m = m;
     f.off = dst ? 1 : 0;
@@ -102,7 +124,17 @@ __host__ __device__ inline Fold3 fold3(int m, bool dst) {
     f.toff[1] = f.n[0] * f.len[0];
     f.toff[2] = f.toff[1] + f.n[1] * f.len[1];
     f.tab = f.toff[2] + f.n[2] * f.len[2];
+    f.itab = 0;
     f.nmodes = f.n[0] + f.n[1] + f.n[2];
+    return f;
+}
+// All three levels (the third whenever the second applies).
+__host__ __device__ inline Fold3 fold3(int m, bool dst) {
+    Fold3 f = fold2(m, dst);
+    if (f.two) {
+        f.itab = fold2(f.n[2], false).tab;
+        f.tab = f.toff[2] + f.itab + (dst ? 0 : f.n[2]);
+    }
     return f;
 }
 // First-level column of folded input q of class c (the table is read there).
