@@ -208,9 +208,13 @@ cudaError_t regroup(FmpPlan& p, const std::vector<FmpBox>& boxes, int sg, int tg
 cudaError_t make_plan(FmpPlan& p, const std::vector<FmpBox>& boxes, cudaStream_t s) {
     p.n_boxes = (int)boxes.size();
     p.max_m[0] = p.max_m[1] = p.max_m[2] = 0;
+    p.max_room = 0;
     long long scr = 0;
     for (const FmpBox& b : boxes) {
-        for (int a = 0; a < 3; ++a) p.max_m[a] = b.m[a] > p.max_m[a] ? b.m[a] : p.max_m[a];
+        for (int a = 0; a < 3; ++a) {
+            p.max_m[a] = b.m[a] > p.max_m[a] ? b.m[a] : p.max_m[a];
+            p.max_room = std::max(p.max_room, fold3_room(b.m[a]));
+        }
         scr = b.scr_off + 3LL * b.m[0] * b.m[1] * b.m[2] > scr ? b.scr_off + 3LL * b.m[0] * b.m[1] * b.m[2] : scr;
     }
     p.scratch_doubles = scr;

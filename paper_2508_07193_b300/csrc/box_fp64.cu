@@ -38,9 +38,6 @@ __device__ __forceinline__ bool edge_wall(int c, int i, int j, int k) {
     return c == 0 ? (j == 0 || k == 0) : c == 1 ? (i == 0 || k == 0) : (i == 0 || j == 0);
 }
 
-// Shared-memory room for one folded table of extent m (Fold3::tab never
-// exceeds (m^2 + 1) / 2).
-__host__ __device__ __forceinline__ int fold_room(int m) { return (m * m + 1) / 2; }
 
 // Element c of a three-entry field of Fold3, by selects: a runtime subscript
 // would keep the whole struct in local memory.
@@ -220,7 +217,7 @@ __device__ __forceinline__ void stage(double* dst, const double* src, int n) {
 }
 
 // Pass A: forward transforms along x and y of one z-slab of one component.
-__global__ void __launch_bounds__(kThreads, 5)
+__global__ void __launch_bounds__(kThreads, 6)
 k_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox* __restrict__ boxes,
          const int4* __restrict__ items, const double* __restrict__ tabs, int nx, int ny, int nz,
          const double* __restrict__ gate) {
@@ -243,7 +240,7 @@ k_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox* _
     double* AB = X + nxy;         // [my][LX] x-folded inputs
     double* P = AB + nxy;         // [my][kx] after the x pass; then the y pass's raw DCT-IV outputs
     double* TX = P + nxy;         // x table: classes 0, 1 (and the DCT-II inner classes) transposed, [q][j]
-    double* TY = TX + fold_room(mx);   // y table as is
+    double* TY = TX + fold3_room(mx);   // y table as is
     double* TXi = TX + fx.toff[2];
     const double* TYi = TY + fy.toff[2];
     {
@@ -420,7 +417,7 @@ k_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox* _
 
 // Pass B: z transform, per-mode 3x3 solve, inverse z transform (owned z).
 template <int CT>
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(kThreads, 5)
 k_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int2* __restrict__ items,
           const double* __restrict__ tabs, const double* __restrict__ modeinv, double beta,
           const double* __restrict__ gate) {
@@ -435,8 +432,8 @@ k_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int2
     double* Buf = sm;                   // [3][mz][CT]: input, then transformed modes
     double* AB = Buf + 3 * mz * CT;     // [3][mz][CT]: z-folded inputs; later the third level's buffers
     double* TC = AB + 3 * mz * CT;      // folded DCT along z
-    double* TS = TC + fold_room(mz);    // folded DST along z
-    double* XS = TS + fold_room(mz);    // [N][CT]: Ez's inner slots (third level)
+    double* TS = TC + fold3_room(mz);    // folded DST along z
+    double* XS = TS + fold3_room(mz);    // [N][CT]: Ez's inner slots (third level)
     const Fold3 fc = fold3(mz, false), fs = fold3(mz, true);
     // the third level applies to both or neither (fc.n[2] = fs.n[2] = mz / 2)
     const bool three = fc.two;
@@ -601,7 +598,7 @@ k_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int2
 
 // Pass C: inverse transforms along y then x of one owned z-slab; owned cells
 // are written to the global field.
-__global__ void __launch_bounds__(kThreads, 5)
+__global__ void __launch_bounds__(kThreads, 6)
 k_inv_xy(const double* __restrict__ scr, double* __restrict__ zout, const FmpBox* __restrict__ boxes,
          const int4* __restrict__ items, const double* __restrict__ tabs, int nx, int ny, int nz,
          const double* __restrict__ gate) {
@@ -621,7 +618,7 @@ k_inv_xy(const double* __restrict__ scr, double* __restrict__ zout, const FmpBox
     double* Q = S + nxy;             // [owned y][kx]
     double* Gin = Q + ony * mx;      // third level: inner slots, then class 2's contributions
     double* TX = Gin + nxy;
-    double* TY = TX + fold_room(mx);
+    double* TY = TX + fold3_room(mx);
     stage(TX, tabs + (sx ? B.dstf_off[0] : B.dctf_off[0]), fx.tab);
     stage(TY, tabs + (sy ? B.dstf_off[1] : B.dctf_off[1]), fy.tab);
     const double* TXi = TX + fx.toff[2];
@@ -701,14 +698,14 @@ k_inv_xy(const double* __restrict__ scr, double* __restrict__ zout, const FmpBox
     }
 }
 
-size_t smem_a(const int* m) {
-    return sizeof(double) * (3 * m[0] * m[1] + fold_room(m[0]) + fold_room(m[1]));
-}
-size_t smem_c(const int* m) {
-    return sizeof(double) * (3 * m[0] * m[1] + fold_room(m[0]) + fold_room(m[1]));
-}
+// Shared memory of the passes: the largest box's slab buffers plus two tables
+// of the largest folded size among the boxes' extents.
+size_t smem_a(const FmpPlan& p) { return sizeof(double) * (3 * p.max_m[0] * p.max_m[1] + 2 * p.max_room); }
+size_t smem_c(const FmpPlan& p) { return sizeof(double) * (3 * p.max_m[0] * p.max_m[1] + 2 * p.max_room); }
 template <int CT>
-size_t smem_b(const int* m) { return sizeof(double) * (6 * m[2] * CT + 2 * fold_room(m[2]) + (m[2] / 2) * CT); }
+size_t smem_b(const FmpPlan& p) {
+    return sizeof(double) * (6 * p.max_m[2] * CT + 2 * p.max_room + (p.max_m[2] / 2) * CT);
+}
 
 }  // namespace
 
@@ -716,23 +713,23 @@ size_t smem_b(const int* m) { return sizeof(double) * (6 * m[2] * CT + 2 * fold_
 // set-up, outside any stream capture).
 cudaError_t fmp_transform_init_fp64(const FmpPlan& p) {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_fwd_xy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a(p.max_m))))
+    if ((e = cudaFuncSetAttribute(k_fwd_xy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a(p))))
         return e;
-    if ((e = cudaFuncSetAttribute(k_inv_xy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c(p.max_m))))
+    if ((e = cudaFuncSetAttribute(k_inv_xy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c(p))))
         return e;
     if (fmp_column_tile_fp64(p.max_m) == 32)
         return cudaFuncSetAttribute(k_z_solve<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem_b<32>(p.max_m));
+                                    (int)smem_b<32>(p));
     return cudaFuncSetAttribute(k_z_solve<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_b<16>(p.max_m));
+                                (int)smem_b<16>(p));
 }
 
 cudaError_t fmp_launch_transform_solve_fp64(const FmpPlan& p, const double* tabs, const double* modeinv,
                                             const double* r, double* z, double* scratch, int nx, int ny, int nz,
                                             double beta, cudaStream_t s, const double* gate) {
-    const size_t sa = smem_a(p.max_m), sc = smem_c(p.max_m);
+    const size_t sa = smem_a(p), sc = smem_c(p);
     const bool wide = fmp_column_tile_fp64(p.max_m) == 32;
-    const size_t sb = wide ? smem_b<32>(p.max_m) : smem_b<16>(p.max_m);
+    const size_t sb = wide ? smem_b<32>(p) : smem_b<16>(p);
     k_fwd_xy<<<p.n_items_a, kThreads, sa, s>>>(r, scratch, p.d_boxes, p.d_items_a, tabs, nx, ny, nz, gate);
     if (wide)
         k_z_solve<32><<<p.n_items_b, kThreads, sb, s>>>(scratch, p.d_boxes, p.d_items_b, tabs, modeinv, beta, gate);

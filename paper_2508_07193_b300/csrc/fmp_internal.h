@@ -137,6 +137,11 @@ __host__ __device__ inline Fold3 fold3(int m, bool dst) {
     }
     return f;
 }
+// Table room (doubles) that holds the folded DCT-II or DST-I table of extent m.
+__host__ __device__ inline int fold3_room(int m) {
+    const int a = fold3(m, false).tab, b = fold3(m, true).tab;
+    return a > b ? a : b;
+}
 // First-level column of folded input q of class c (the table is read there).
 __host__ __device__ inline int fold3_column(const Fold3& f, int c, int q) {
     const bool sym = !f.two ? c == 0 : (c == 2 ? !f.s2sym : f.s2sym);
@@ -188,6 +193,7 @@ struct FmpPlan {
     int n_items_f = 0;
     int fused_yz_max = 0;       // largest y or z extent among them
     int max_m[3] = {0, 0, 0};
+    int max_room = 0;           // largest folded float64 table among the boxes' extents (fold3_room)
     long long scratch_doubles = 0;
     // streamed reduced-precision solve (bf16 / fp16): one persistent launch
     // over the boxes the fused kernel does not take (all of them without
