@@ -94,31 +94,12 @@ struct Walk3 {
     }
 };
 
-// x rounded to bf16 (to nearest, ties to even) by integer operations, as
-// the 16-bit pattern: the same value as rounding to fp32 by odd and then to
-// bf16. Results below 2^-126 give a signed zero, above the range infinity;
-// NaN stays NaN.
-__device__ __forceinline__ uint32_t f64_bf16_bits(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const uint32_t hi = (uint32_t)(b >> 32);
-    const int ex = (int)(hi >> 20) & 0x7FF;
-    const int e = ex - 1023 + 127;
-    const uint32_t m7 = (hi >> 13) & 0x7Fu;
-    const uint32_t sticky = ((hi & 0xFFFu) | (uint32_t)b) != 0u ? 1u : 0u;
-    uint32_t v = ((uint32_t)e << 7) + m7;
-    v += ((hi >> 12) & 1u) & (sticky | (m7 & 1u));   // a carry moves into the exponent
-    v = (e <= 0 || ex == 0) ? 0u : v;
-    v = (e >= 255) ? 0x7F80u : v;
-    v = ex == 0x7FF ? (0x7F80u | (((hi & 0xFFFFFu) | (uint32_t)b) != 0u ? 0x40u : 0u)) : v;
-    return ((hi >> 16) & 0x8000u) | v;
-}
-
 struct BF16S {
     using E = __nv_bfloat16;
     static constexpr bool kScaled = false;
     // the pair (a, b) of float64 values rounded to bf16, a in the low half
     static __device__ __forceinline__ uint32_t pack64(double a, double b, float) {
-        return f64_bf16_bits(a) | (f64_bf16_bits(b) << 16);
+        return fmp::f64_to_bf16_bits(a) | (fmp::f64_to_bf16_bits(b) << 16);
     }
     static __device__ __forceinline__ uint32_t pack(float a, float b) {
         const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);

@@ -55,6 +55,25 @@ __device__ __forceinline__ double f32_to_f64_scaled(float x, int k) {
     return __longlong_as_double(static_cast<long long>(d));
 }
 
+// x rounded to bf16 (to nearest, ties to even) by integer operations, as
+// the 16-bit pattern: the same value as rounding to fp32 by odd and then to
+// bf16. Results below 2^-126 give a signed zero, above the range infinity;
+// NaN stays NaN.
+__device__ __forceinline__ unsigned f64_to_bf16_bits(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32);
+    const int ex = (int)(hi >> 20) & 0x7FF;
+    const int e = ex - 1023 + 127;
+    const unsigned m7 = (hi >> 13) & 0x7Fu;
+    const unsigned sticky = ((hi & 0xFFFu) | (unsigned)b) != 0u ? 1u : 0u;
+    unsigned v = ((unsigned)e << 7) + m7;
+    v += ((hi >> 12) & 1u) & (sticky | (m7 & 1u));   // a carry moves into the exponent
+    v = (e <= 0 || ex == 0) ? 0u : v;
+    v = (e >= 255) ? 0x7F80u : v;
+    v = ex == 0x7FF ? (0x7F80u | (((hi & 0xFFFFFu) | (unsigned)b) != 0u ? 0x40u : 0u)) : v;
+    return ((hi >> 16) & 0x8000u) | v;
+}
+
 // A positive normal s as 2^k * m, m in [1, 2] rounded to fp32 (relative error
 // at most 2^-24); anything else gives k = 0, m = 0.
 __device__ __forceinline__ void split_pow2(double s, int& k, float& m) {
