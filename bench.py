@@ -105,7 +105,8 @@ def parse():
                         "the K timed with CUDA events; box: the exact solve of the 32^3 PEC box")
     p.add_argument("--workload", default="grid256", choices=["grid128", "grid256", "uneven", "box32"])
     p.add_argument("--fused", type=int, default=None,
-                   help="bf16/fp16: largest extent of the fused cluster kernel (0: none; default 40)")
+                   help="bf16/fp16: largest extent of the fused cluster kernel (0: none; default 40, or 0 when "
+                        "the boxes it could take are too few to fill the GPU beside larger ones)")
     p.add_argument("--streamed", type=int, default=None,
                    help="bf16/fp16 boxes outside the fused list: 1 one persistent streamed launch (default), "
                         "0 the three-pass kernels")

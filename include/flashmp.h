@@ -173,7 +173,10 @@ int fmp_get_tuning(fmp_ctx* ctx, int* slab_group, int* tile_group);
  * thread-block cluster of three CTAs per box, the box resident in shared
  * memory): for bf16 and fp16, boxes whose extents are all <= max_extent take
  * it, the others the streamed solve (below) or the three-pass kernels.
- * max_extent in [0, 40]; 0 turns it off; default 40. tf32 always runs the
+ * max_extent in [0, 40]; 0 turns it off. Default 40, except when some boxes
+ * exceed 40 and the others would fill fewer than two waves of clusters (3
+ * CTAs per box against two per SM): then 0, so that the streamed solve's one
+ * persistent launch takes every box. tf32 always runs the
  * three-pass kernels. Results agree within the reduced-precision error, not
  * bitwise. */
 int fmp_set_fused(fmp_ctx* ctx, int max_extent);

@@ -246,6 +246,23 @@ cudaError_t make_plan(FmpPlan& p, const std::vector<FmpBox>& boxes, cudaStream_t
         if ((e = upload(&p.d_items_ob, OB, s))) return e;
         if ((e = upload(&p.d_items_oc, OC, s))) return e;
     }
+    // Default fused choice. When some boxes exceed the fused kernel's extents
+    // (they go to the streamed launch), the fused kernel keeps the others only
+    // if their clusters fill two waves of the GPU; a smaller fused launch
+    // leaves SMs idle for a whole box solve, which costs more than streaming
+    // those boxes with the rest in the one persistent launch (uneven
+    // 320x256x192, 48 of 294 boxes fusable: 0.806 ms per bf16 apply split,
+    // 0.787 ms all streamed). fmp_set_fused overrides it.
+    {
+        int n_fusable = 0, n_sms = 0;
+        for (const FmpBox& b : boxes) n_fusable += fusable(b, FMP_FUSED_MAX) ? 1 : 0;
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && p.streamed &&
+            n_fusable < (int)boxes.size() && 3 * n_fusable < 2 * 2 * n_sms)
+            p.fused_max = 0;
+        (void)cudaGetLastError();
+    }
     return regroup(p, boxes, p.slab_group, p.tile_group, p.fused_max, s);
 }
 

@@ -39,6 +39,7 @@ namespace {
 
 constexpr int kFL = FMP_FUSED_MAX;     // row stride (x) of the box array, largest extent
 constexpr int kNT = kFL / 8;           // n-tiles of 8 for a full axis
+constexpr int kGP = 8;                 // element pairs in flight per thread in the gather (16 measured no faster)
 
 // NR rows per slab and NR slabs; slab stride NR * kFL + 8 (the extra 16 B
 // keep the 8 rows of a strided ldmatrix off one bank group); NTH threads.
@@ -361,7 +362,9 @@ k_fused_solve(const double* __restrict__ r, double* __restrict__ zout, const Fmp
     }
     // gather: element pairs (x, x+1) of each (z, y) row of the extended box.
     // Thread t takes pairs t, t + kFT, ...; its (z, y, pair) position advances
-    // by carries instead of divisions.
+    // by carries instead of divisions. kGP pairs per thread are loaded before
+    // any is converted, so each thread waits out the memory latency once per
+    // kGP pairs.
     {
         const int npr = (mx + 1) >> 1;
         const double* src0 = r + ((long long)c * nz + B.ext_lo[2]) * (long long)ny * nx +
@@ -380,10 +383,10 @@ k_fused_solve(const double* __restrict__ r, double* __restrict__ zout, const Fmp
             z += step_z + carry;
         };
         while (z < mz) {
-            double v[8][2];
-            int off[8];
+            double v[kGP][2];
+            int off[kGP];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < kGP; ++u) {
                 v[u][0] = v[u][1] = 0.0;
                 off[u] = -1;
                 if (z < mz) {
@@ -396,7 +399,7 @@ k_fused_solve(const double* __restrict__ r, double* __restrict__ zout, const Fmp
                 }
             }
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
+            for (int u = 0; u < kGP; ++u)
                 if (off[u] >= 0)
                     *reinterpret_cast<uint32_t*>(D + off[u]) =
                         Tr::pack(f64_to_f32_odd(v[u][0]) * inv_s, f64_to_f32_odd(v[u][1]) * inv_s);

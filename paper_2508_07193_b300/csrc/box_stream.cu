@@ -53,6 +53,7 @@ constexpr int kLT = kMaxP + 8;             // row stride (elements) of tables an
 constexpr int kQ = 8;                      // x-octet lines per B item
 constexpr int kPS = kQ * 8 + 8;            // z-row stride (elements) of the B tile: 272 B
 constexpr int kSGMax = 8;                  // most z-slabs per A / C item
+constexpr int kGR = 4;                     // rows per warp step of the pass-A gather
 constexpr long long kWaitLimit = 1LL << 23;   // x ~128 ns: about a second
 
 constexpr size_t kTabBytes = 2ull * kMaxP * kLT * 2;
@@ -386,12 +387,12 @@ __device__ void pass_a(const StreamArgs& A, int bi, const FmpBox& B, long long s
     const float inv_s = 1.f / box_scale(A.bmax, bi);
     const double* src0 = A.r + ((long long)c * A.nz + B.ext_lo[2]) * A.ny * (long long)A.nx +
                          (long long)B.ext_lo[1] * A.nx + B.ext_lo[0];
-    // gather: one row (slab sl, y < MYp) per warp step; element pairs
-    // x < MXp, zero beyond the box and on its walls
-    for (int q0 = warp; q0 < zn * MYp; q0 += 2 * kW) {
-        double v[2][2][2];
+    // gather: kGR rows (slab sl, y < MYp) per warp step, all loaded before any
+    // is converted; element pairs x < MXp, zero beyond the box and on its walls
+    for (int q0 = warp; q0 < zn * MYp; q0 += kGR * kW) {
+        double v[kGR][2][2];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < kGR; ++u) {
             const int q = q0 + u * kW;
             const int sl = q / MYp, y = q - sl * MYp, kz = z0 + sl;
             const double* sp = src0 + ((long long)kz * A.ny + y) * A.nx;
@@ -407,7 +408,7 @@ __device__ void pass_a(const StreamArgs& A, int bi, const FmpBox& B, long long s
             }
         }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < kGR; ++u) {
             const int q = q0 + u * kW;
             if (q >= zn * MYp) break;
             const int sl = q / MYp, y = q - sl * MYp;

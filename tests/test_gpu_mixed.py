@@ -113,21 +113,31 @@ def test_grouping_changes_speed_not_results_and_autotune_picks_one(tmp_path):
 
 
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
-def test_fused_and_three_pass_boxes_in_one_apply(prec):
-    """x cuts (20, 60) with overlap 2 give boxes of extent 22 (fused) and 62
-    (three-pass) in the same preconditioner apply."""
+def test_fused_and_other_boxes_in_one_apply(prec):
+    """x cuts (20, 60) with overlap 2 give boxes of extent 22 (fusable) and 62
+    in the same preconditioner apply. By default the two fusable boxes are too
+    few to fill the GPU, so the streamed launch takes all four; with the fused
+    kernel chosen, the two small boxes go through it and the large ones
+    through the streamed launch, or with the streamed solve off through the
+    three-pass kernels."""
     w = wl.small(grid=(80, 24, 16), cuts=((20, 60), (12, 12), (16,)), overlap=2, seed=23, n_eps_boxes=5)
     ctx = context(w, precision=prec)
-    assert ctx.get_fused() == (40, 2)
+    assert ctx.get_fused() == (0, 0) and ctx.get_streamed() == (1, 4)
     ee = yee.edge_eps(w.grid, w.eps_cell)
     boxes = ras.partition(w.grid, w.cuts, w.overlap)
     ref = ras.precond_apply(w.rhs, boxes, ee, w.beta)
-    z = host(ctx.precond_apply(dev(w.rhs)))
+    r = dev(w.rhs)
+    check(host(ctx.precond_apply(r)), ref, prec, boxes)
+    ctx.set_fused(40)
+    assert ctx.get_fused() == (40, 2) and ctx.get_streamed() == (1, 2)
+    z = host(ctx.precond_apply(r))
     check(z, ref, prec, boxes)
     assert np.all(z[wl.edge_wall_mask(w.grid)] == 0.0)
+    ctx.set_streamed(0)
+    assert ctx.get_fused() == (40, 2) and ctx.get_streamed() == (0, 0)
+    check(host(ctx.precond_apply(r)), ref, prec, boxes)
     ctx.set_fused(0)
-    z3 = host(ctx.precond_apply(dev(w.rhs)))
-    check(z3, ref, prec, boxes)
+    check(host(ctx.precond_apply(r)), ref, prec, boxes)
 
 
 def test_fused_box_extents_one_to_forty():
