@@ -761,14 +761,21 @@ def run_ours(args):
         ctx.precond_apply(r, z)
         z64 = z.clone()
         owned = [ctx.box(i) for i in range(ctx.num_boxes())]
-        for p in ("fp64", "fp64_ozaki", "bf16", "fp16", "tf32"):
+        # (form, transform precision, Krylov method): every precision with the
+        # run's method, and the reduced-precision transforms with BiCGSTAB
+        # (two applies and two SpMVs per iteration, no Gram-Schmidt) beside an
+        # FGMRES run
+        runs = [(p, p, args.krylov) for p in ("fp64", "fp64_ozaki", "bf16", "fp16", "tf32")]
+        if args.krylov == "fgmres":
+            runs += [(p + "_bicgstab", p, "bicgstab") for p in ("bf16", "fp16")]
+        for name, p, kr in runs:
             if p == "fp64_ozaki" and max_ext > OZAKI_MAX_EXTENT:
                 continue
-            if p == args.precision:
-                forms[p] = {"ms_per_step": ms, "iters": iters[0] if iters else None, "true_rel_res_max": true_res,
-                            "precond_ms": ms_p}
+            if p == args.precision and kr == args.krylov:
+                forms[name] = {"ms_per_step": ms, "iters": iters[0] if iters else None, "true_rel_res_max": true_res,
+                               "precond_ms": ms_p}
             else:
-                ctx.set_options(precision=p)
+                ctx.set_options(precision=p, krylov=kr)
                 infos.clear()
                 for _ in range(args.warmup):
                     step()
@@ -787,16 +794,18 @@ def run_ours(args):
                     ctx.precond_apply(r, z)
                 e1.record(stream)
                 torch.cuda.synchronize()
-                forms[p] = {"ms_per_step": fm, "iters": infos[0]["iters"],
-                            "true_rel_res_max": max(i["true_rel_res"] for i in infos),
-                            "precond_ms": e0.elapsed_time(e1) / n_p}
+                forms[name] = {"ms_per_step": fm, "iters": infos[0]["iters"],
+                               "true_rel_res_max": max(i["true_rel_res"] for i in infos),
+                               "precond_ms": e0.elapsed_time(e1) / n_p}
+                if kr != args.krylov:
+                    forms[name]["krylov"] = "BiCGSTAB" if kr == "bicgstab" else "FGMRES(30)"
             if p != "fp64":
-                ctx.set_options(precision=p)
+                ctx.set_options(precision=p, krylov=kr)
                 ctx.precond_apply(r, z)
-                forms[p]["precond_err_vs_fp64"] = precond_error(z, z64, owned)
+                forms[name]["precond_err_vs_fp64"] = precond_error(z, z64, owned)
             if p == "fp64_ozaki":
-                forms[p]["mma_tflops"] = ozaki_mma_flops(ctx) / (forms[p]["precond_ms"] * 1e-3) / 1e12
-        ctx.set_options(precision=args.precision)
+                forms[name]["mma_tflops"] = ozaki_mma_flops(ctx) / (forms[name]["precond_ms"] * 1e-3) / 1e12
+        ctx.set_options(precision=args.precision, krylov=args.krylov)
         out["forms"] = forms
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, iters[0] if iters else 1)

@@ -678,7 +678,8 @@ int fmp_set_options(fmp_ctx* c, const fmp_options* o) {
     if (!valid_ctx(c) || !o) return FMP_ERR_ARG;
     int rc = check_options(o);
     if (rc != FMP_OK) return rc;
-    if (o->precision != c->opt.precision || o->restart != c->opt.restart) fmp_invalidate_graphs(c);
+    if (o->precision != c->opt.precision || o->restart != c->opt.restart || o->krylov != c->opt.krylov)
+        fmp_invalidate_graphs(c);
     c->opt = *o;
     return FMP_OK;
 }
