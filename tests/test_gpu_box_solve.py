@@ -25,6 +25,30 @@ def test_box_solve_matches_oracle(grid):
     assert np.all(x[ras.box_wall(grid)] == 0.0)
 
 
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_box_solve_every_extent_2_to_40(axis):
+    """Single boxes whose extent along one axis runs through 2 .. 40, the other
+    two 6 and 5: every folding shape of the float64 transforms (odd extents,
+    even ones whose halves are odd or even, and the third level's inner
+    transforms of 1 .. 20 points), for the DCT-II axis of one component and
+    the DST-I axes of the others."""
+    from paper_2508_07193_b300 import flashmp as F
+    worst = 0.0
+    for m in range(2, 41):
+        grid = [6, 5, 6]
+        grid[axis] = m
+        nx, ny, nz = grid
+        w = wl.make_workload("box", tuple(grid), seed=m + 100 * axis, uniform_eps=True, overlap=0)
+        ctx = F.Context(tuple(grid), np.full((nz, ny, nx), 3.0), 0.25)
+        x = host(ctx.box_solve(0, dev(w.rhs)))
+        ctx.close()
+        ref = box.exact_solve(w.rhs, 3.0, 0.25)
+        worst = max(worst, rel(x, ref))
+        assert rel(x, ref) <= FP64_TOL, (grid, rel(x, ref))
+        assert np.all(x[ras.box_wall(tuple(grid))] == 0.0)
+    print("worst", worst)
+
+
 def test_box32_workload_residual():
     w = wl.box32()
     ctx = context(w)

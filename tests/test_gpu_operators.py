@@ -84,10 +84,32 @@ def test_curlcurl_is_exact_on_integer_fields():
     assert np.array_equal(y, ref)
 
 
+@pytest.mark.parametrize("grid", [(20, 18, 14), (33, 17, 37), (40, 9, 3), (9, 40, 70)])
+def test_curlcurl_exact_with_plane_scales(grid):
+    """Each z-plane of an integer field scaled by its own power of two (up and
+    down along z, so the running exponent maximum of a column grows in steps
+    and older planes shift into it): K x stays exact, bit for bit against the
+    oracle's sparse product. Grids whose nz leaves ragged and single-plane
+    columns."""
+    w = wl.make_workload("planes", grid, seed=sum(grid), n_eps_boxes=2, cuts=tuple((n,) for n in grid),
+                         overlap=0)
+    ctx = context(w)
+    rng = np.random.default_rng(11)
+    x = rng.integers(-100, 101, size=w.rhs.shape).astype(np.float64)
+    s = (np.arange(grid[2]) * 37) % 31           # per-plane exponent, 0 .. 30
+    x *= np.ldexp(1.0, s)[None, :, None, None]
+    x[wl.edge_wall_mask(w.grid)] = 0.0
+    y = host(ctx.curlcurl_apply(dev(x), c_eps=0.0, c_k=1.0))
+    ref = (yee.double_curl(w.grid) @ x.reshape(-1)).reshape(x.shape)
+    ref[wl.edge_wall_mask(w.grid)] = 0.0
+    assert np.array_equal(y, ref)
+
+
 def test_curlcurl_wide_dynamic_range_and_tiny_tiles():
-    """Values 2^-300 .. 2^300 across and inside the 32 x 8 x 2 tiles: the
-    error stays below the float64 bar relative to the field; a field of
-    values near 2^-1000 (tile exponents below the split scale) too."""
+    """Values 2^-300 .. 2^300 across and inside the 32 x 8 tiles and along
+    their columns: the error stays below the float64 bar relative to the
+    field; a field of values near 2^-1000 (exponents below the split scale)
+    too."""
     w = CASES[0]
     ctx = context(w)
     ee = yee.edge_eps(w.grid, w.eps_cell)
