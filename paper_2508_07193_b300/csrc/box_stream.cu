@@ -53,7 +53,7 @@ constexpr int kLT = kMaxP + 8;             // row stride (elements) of tables an
 constexpr int kQ = 8;                      // x-octet lines per B item
 constexpr int kPS = kQ * 8 + 8;            // z-row stride (elements) of the B tile: 272 B
 constexpr int kSGMax = 8;                  // most z-slabs per A / C item
-constexpr int kGR = 4;                     // rows per warp step of the pass-A gather
+constexpr int kGP = 6;                     // element pairs in flight per thread in the pass-A gather
 constexpr long long kWaitLimit = 1LL << 23;   // x ~128 ns: about a second
 
 constexpr size_t kTabBytes = 2ull * kMaxP * kLT * 2;
@@ -387,38 +387,35 @@ __device__ void pass_a(const StreamArgs& A, int bi, const FmpBox& B, long long s
     const float inv_s = 1.f / box_scale(A.bmax, bi);
     const double* src0 = A.r + ((long long)c * A.nz + B.ext_lo[2]) * A.ny * (long long)A.nx +
                          (long long)B.ext_lo[1] * A.nx + B.ext_lo[0];
-    // gather: kGR rows (slab sl, y < MYp) per warp step, all loaded before any
-    // is converted; element pairs x < MXp, zero beyond the box and on its walls
-    for (int q0 = warp; q0 < zn * MYp; q0 += kGR * kW) {
-        double v[kGR][2][2];
+    // gather: element pairs (x, x + 1), x < MXp, of the zn slabs' rows y < MYp,
+    // walked flat over (slab, row, pair) so that every lane has a pair; kGP
+    // pairs per thread are loaded before any is converted. Zero beyond the
+    // box and on its walls: Ex rows y = 0 or z = 0, Ey rows z = 0 and column
+    // x = 0, Ez rows y = 0 and column x = 0.
+    {
+        const int total = zn * MYp * npairs;
+        const int x_first = c != 0 ? 1 : 0;
+        Walk3 it(threadIdx.x, kT, MYp, npairs);   // (slab, row, pair)
+        for (int q0 = threadIdx.x; q0 < total; q0 += kGP * kT) {
+            double v[kGP][2];
+            int off[kGP];
 #pragma unroll
-        for (int u = 0; u < kGR; ++u) {
-            const int q = q0 + u * kW;
-            const int sl = q / MYp, y = q - sl * MYp, kz = z0 + sl;
-            const double* sp = src0 + ((long long)kz * A.ny + y) * A.nx;
-            // box walls: Ex rows y = 0 or z = 0, Ey rows z = 0 and column x = 0,
-            // Ez rows y = 0 and column x = 0
-            const bool row = q < zn * MYp && y < my && !(c != 1 && y == 0) && !(c != 2 && kz == 0);
-            const int x_first = c != 0 ? 1 : 0;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int x = 2 * (lane + 32 * h);
-                v[u][h][0] = row && x < mx && x >= x_first ? __ldg(sp + x) : 0.0;
-                v[u][h][1] = row && x + 1 < mx ? __ldg(sp + x + 1) : 0.0;
+            for (int u = 0; u < kGP; ++u) {
+                v[u][0] = v[u][1] = 0.0;
+                off[u] = -1;
+                if (q0 + u * kT < total) {
+                    const int sl = it.i1, y = it.i2, x = 2 * it.i3, kz = z0 + sl;
+                    const bool row = y < my && !(c != 1 && y == 0) && !(c != 2 && kz == 0);
+                    const double* sp = src0 + ((long long)kz * A.ny + y) * A.nx + x;
+                    if (row && x < mx && x >= x_first) v[u][0] = __ldg(sp);
+                    if (row && x + 1 < mx) v[u][1] = __ldg(sp + 1);
+                    off[u] = sl * kSlab + y * kLT + x;
+                    it.next();
+                }
             }
-        }
 #pragma unroll
-        for (int u = 0; u < kGR; ++u) {
-            const int q = q0 + u * kW;
-            if (q >= zn * MYp) break;
-            const int sl = q / MYp, y = q - sl * MYp;
-            E* row = D + sl * kSlab + y * kLT;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int p = lane + 32 * h;
-                if (p < npairs)
-                    *reinterpret_cast<uint32_t*>(row + 2 * p) = Tr::pack64(v[u][h][0], v[u][h][1], inv_s);
-            }
+            for (int u = 0; u < kGP; ++u)
+                if (off[u] >= 0) *reinterpret_cast<uint32_t*>(D + off[u]) = Tr::pack64(v[u][0], v[u][1], inv_s);
         }
     }
     cp_wait_all();   // the tables
