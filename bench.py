@@ -251,12 +251,12 @@ def _macs(f):
 
 
 def _fold01_adds(f):
-    """Additions that make the class-0 and class-1 inputs of a line (each slot
-    computed on its own)."""
+    """Additions that make the class-0 and class-1 inputs of a line (a class-0
+    and a class-1 slot share their two second-level inputs)."""
     if not f["L"]:
         return f["len"][0] + f["len"][1] - f["mid"]
     L = f["L"]
-    return 6 * (L // 2) + (L % 2)
+    return 4 * (L // 2) + (L % 2)
 
 
 def _items_ops(f, q0, g_of_q):
@@ -270,11 +270,12 @@ def _items_ops(f, q0, g_of_q):
 
 
 def _inner_slot_terms(g):
-    """Terms of the inner slots of g (each slot one chain of FMAs or adds)."""
+    """Operations of the inner slots of g from weighted inputs (a product and
+    an FMA per two-term sum; a class-0 / class-1 pair shares its two sums)."""
     if not g["L"]:
         return 2 * g["npair"] + g["mid"] + 2 * (g["len"][1])
     L = g["L"]
-    return 8 * (L // 2) + 2 * (L % 2) + 2 * g["len"][2]
+    return 6 * (L // 2) + 2 * (L % 2) + 2 * g["len"][2]
 
 
 def _fwd_ops(m, dst):
@@ -287,7 +288,7 @@ def _fwd_ops(m, dst):
     ops = f["n"][0] * f["len"][0] + f["n"][1] * f["len"][1] + _fold01_adds(f)
     if not dst:   # scaled differences, inner fold, inner rows, recurrence
         L2 = g["L"]
-        inner_adds = (6 * (L2 // 2) + (L2 % 2) + g["len"][2]) if L2 else (N - g["mid"])
+        inner_adds = (4 * (L2 // 2) + (L2 % 2) + g["len"][2]) if L2 else (N - g["mid"])
         return ops + 2 * N + inner_adds + _macs(g) + (N - 1)
     # reversed pair sums, then the inner inverse-direction items
     return ops + (N - 1) + _items_ops(g, 0, lambda cnt: cnt * g["n"][2])

@@ -61,6 +61,60 @@ __device__ __forceinline__ void f3_slot(const Fold3& f, int s, int& c, int& q) {
     q = s - pick(f.seg, c);
 }
 
+// Fold items of one line of a forward pass. With the second level, item
+// i < L/2 makes class-0 slot i and class-1 slot i from the two second-level
+// inputs they share, f2(i) and f2(L - 1 - i) (their sum and difference), item
+// L/2 of an odd L the class-0 middle slot, and the rest class 2's slots
+// (pre(q): slot q's value); without it, one item per slot. store(slot, value)
+// takes a slot of the folded line (class segments as in Fold3).
+__device__ __forceinline__ int f3_fold_items(const Fold3& f) {
+    return f.two ? f.L / 2 + (f.L & 1) + f.len[2] : f.len[0] + f.len[1];
+}
+template <class GetV, class Pre, class Store>
+__device__ __forceinline__ void f3_fold_item(const Fold3& f, int i, GetV v, Pre pre, Store store) {
+    if (!f.two) {
+        const int c = i < f.len[0] ? 0 : 1, q = c ? i - f.len[0] : i;
+        store(pick(f.seg, c) + q, f3_input(f, c, q, v));
+        return;
+    }
+    auto fsym = [&](int p) { return p < f.npair ? v(f.off + p) + v(f.m - 1 - p) : v(f.mid); };
+    auto fanti = [&](int p) { return v(f.off + p) - v(f.m - 1 - p); };
+    auto f2 = [&](int p) { return f.s2sym ? fsym(p) : fanti(p); };
+    const int h = f.L / 2;
+    if (i < h) {
+        const double a = f2(i), b = f2(f.L - 1 - i);
+        store(f.seg[0] + i, a + b);
+        store(f.seg[1] + i, a - b);
+    } else if (i == h && (f.L & 1)) {
+        store(f.seg[0] + h, f2(h));
+    } else {
+        const int q = i - h - (f.L & 1);
+        store(f.seg[2] + q, pre(q));
+    }
+}
+
+// Item (line, i) of work index t over `lines` lines, segment by segment (the
+// pairs, the middle, class 2; without the second level class 0, class 1),
+// the item fastest within a segment, so a warp runs one kind of item.
+__device__ __forceinline__ void f3_fold_work(const Fold3& f, int lines, int t, int& line, int& i) {
+    const int n0 = f.two ? f.L / 2 : f.len[0], n1 = f.two ? (f.L & 1) : f.len[1];
+    const int n2 = f.two ? f.len[2] : 0;
+    if (t < lines * n0) {
+        line = t / n0;
+        i = t - line * n0;
+        return;
+    }
+    t -= lines * n0;
+    if (t < lines * n1) {
+        line = t / n1;
+        i = n0 + (t - line * n1);
+        return;
+    }
+    t -= lines * n1;
+    line = t / n2;
+    i = n0 + n1 + (t - line * n2);
+}
+
 // Class, row and mode of output row r (rows ordered class by class).
 __device__ __forceinline__ void f3_row(const Fold3& f, int r, int& c, int& j, int& k) {
     c = r < f.n[0] ? 0 : (r < f.n[0] + f.n[1] ? 1 : 2);
@@ -148,60 +202,13 @@ __device__ __forceinline__ void f3_inverse_item(const Fold3& f, const double* T,
 
 // Forward direction, the value kept for class-2 input p (< N) of a line
 // whose class-2 folded inputs are a(p): DCT-II: d_p a(p), folded again by
-// the inner table's layout (f3_inner_slot) in the next phase; DST-I:
+// the inner table's layout (f3_fold_item on g) in the next phase; DST-I:
 // a(N - 1 - p), the reversed inputs that the inner inverse-direction items
 // read as modes.
 template <class GetA>
 __device__ __forceinline__ double f3_fwd_pre(const Fold3& f, const double* Ti, int p, GetA a) {
     return f.off == 0 ? Ti[f.itab + p] * a(p) : a(f.n[2] - 1 - p);
 }
-// Inverse direction, inner slot s (layout g) straight from the class-2
-// modes y(p) (mode 1 + 2 p) with the weights w(p): d_p (DCT-II) or (-1)^p
-// (DST-I), as one chain of FMAs over the slot's (up to four) terms.
-template <class GetY, class GetW>
-__device__ __forceinline__ double f3_inv_slot(const Fold3& g, int s, GetY y, GetW w) {
-    int c, q;
-    f3_slot(g, s, c, q);
-    const int n = g.m;
-    double acc = 0.0;
-    auto add = [&](int p, bool neg) {
-        const double wp = w(p);
-        acc = fma(neg ? -wp : wp, y(p), acc);
-    };
-    auto sym = [&](int a, bool neg) {
-        if (a < g.npair) {
-            add(a, neg);
-            add(n - 1 - a, neg);
-        } else {
-            add(g.mid, neg);
-        }
-    };
-    if (!g.two) {
-        if (c == 0) {
-            sym(q, false);
-        } else {
-            add(q, false);
-            add(n - 1 - q, true);
-        }
-        return acc;
-    }
-    if (c == 2) {
-        add(q, false);
-        add(n - 1 - q, true);
-        return acc;
-    }
-    sym(q, false);
-    if (c == 1 || q < g.L / 2) sym(g.L - 1 - q, c == 1);
-    return acc;
-}
-// Inner folded slot s from the inner inputs v(p) (layout g = fold2(N, false)).
-template <class GetV>
-__device__ __forceinline__ double f3_inner_slot(const Fold3& g, int s, GetV v) {
-    int c, q;
-    f3_slot(g, s, c, q);
-    return f3_input(g, c, q, v);
-}
-
 // DCT-IV from DCT-II: y_0 = Y_0 (row 0 of the inner table is halved),
 // y_k = Y_k - y_(k-1), in place over N values at stride st.
 __device__ __forceinline__ void f3_recur(double* v, int n, int st) {
@@ -277,25 +284,28 @@ k_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox* _
     }
     __syncthreads();
     const int LX = fx.seg[2] + fx.len[2];
-    // folded inputs class by class ((y, q) of class 0, then 1, then 2): the
-    // classes fold with different numbers of additions
-    for (int t = threadIdx.x; t < my * LX; t += blockDim.x) {
-        int cc = 0, u = t;
-        while (cc < 2 && u >= my * pick(fx.len, cc)) { u -= my * pick(fx.len, cc); ++cc; }
-        const int y = u / pick(fx.len, cc), q = u - y * pick(fx.len, cc);
+    // folded inputs, item by item (the kinds of item fold with different
+    // numbers of additions)
+    for (int t = threadIdx.x; t < my * f3_fold_items(fx); t += blockDim.x) {
+        int y, i;
+        f3_fold_work(fx, my, t, y, i);
         const double* row = X + y * mx;
-        auto v = [&](int i) { return row[i]; };
-        AB[y * LX + pick(fx.seg, cc) + q] =
-            (fx.two && cc == 2) ? f3_fwd_pre(fx, TXi, q, [&](int p) { return f3_input(fx, 2, p, v); })
-                                : f3_input(fx, cc, q, v);
+        double* ab = AB + y * LX;
+        auto v = [&](int k) { return row[k]; };
+        f3_fold_item(
+            fx, i, v, [&](int q) { return f3_fwd_pre(fx, TXi, q, [&](int p) { return f3_input(fx, 2, p, v); }); },
+            [&](int slot, double val) { ab[slot] = val; });
     }
     __syncthreads();
     if (fx.two && !sx) {   // DCT-II third level: the inner slots, in X (free now)
-        const int N = fx.n[2];
-        for (int t = threadIdx.x; t < my * N; t += blockDim.x) {
-            const int y = t / N, s2 = t - y * N;
+        for (int t = threadIdx.x; t < my * f3_fold_items(gx); t += blockDim.x) {
+            int y, i;
+            f3_fold_work(gx, my, t, y, i);
             const double* a = AB + y * LX + fx.seg[2];
-            X[y * LX + fx.seg[2] + s2] = f3_inner_slot(gx, s2, [&](int p) { return a[p]; });
+            double* o = X + y * LX + fx.seg[2];
+            auto v = [&](int p) { return a[p]; };
+            f3_fold_item(gx, i, v, [&](int q) { return f3_input(gx, 2, q, v); },
+                         [&](int sl, double val) { o[sl] = val; });
         }
         __syncthreads();
     }
@@ -347,21 +357,22 @@ k_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox* _
         __syncthreads();
     }
     const int LY = fy.seg[2] + fy.len[2];
-    for (int t = threadIdx.x; t < LY * mx; t += blockDim.x) {
-        const int s = t / mx, kx = t - s * mx;
-        int cc, q;
-        f3_slot(fy, s, cc, q);
+    for (int t = threadIdx.x; t < f3_fold_items(fy) * mx; t += blockDim.x) {
+        const int i = t / mx, kx = t - i * mx;
         auto v = [&](int y) { return P[y * mx + kx]; };
-        X[t] = (fy.two && cc == 2) ? f3_fwd_pre(fy, TYi, q, [&](int p) { return f3_input(fy, 2, p, v); })
-                                   : f3_input(fy, cc, q, v);
+        f3_fold_item(
+            fy, i, v, [&](int q) { return f3_fwd_pre(fy, TYi, q, [&](int p) { return f3_input(fy, 2, p, v); }); },
+            [&](int slot, double val) { X[slot * mx + kx] = val; });
     }
     __syncthreads();
     if (fy.two && !sy) {   // DCT-II third level: the inner slots, in AB (free now)
-        const int N = fy.n[2];
-        for (int t = threadIdx.x; t < N * mx; t += blockDim.x) {
-            const int s2 = t / mx, kx = t - s2 * mx;
+        for (int t = threadIdx.x; t < f3_fold_items(gy) * mx; t += blockDim.x) {
+            const int i = t / mx, kx = t - i * mx;
             const double* a = X + fy.seg[2] * mx + kx;
-            AB[(fy.seg[2] + s2) * mx + kx] = f3_inner_slot(gy, s2, [&](int p) { return a[p * mx]; });
+            double* o = AB + fy.seg[2] * mx + kx;
+            auto v = [&](int p) { return a[p * mx]; };
+            f3_fold_item(gy, i, v, [&](int q) { return f3_input(gy, 2, q, v); },
+                         [&](int sl, double val) { o[sl * mx] = val; });
         }
         __syncthreads();
     }
@@ -447,28 +458,33 @@ k_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int2
         Buf[t] = col < ncol ? base[(long long)cz * nxy + col0 + col] : 0.0;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < 3 * mz * CT; t += blockDim.x) {
-        const int cz = t / CT, col = t - cz * CT;
-        const int c = cz / mz, s = cz - c * mz;
-        const Fold3& f = c == 2 ? fc : fs;
-        const double* in = Buf + c * mz * CT + col;
-        double v = 0.0;
-        if (s < f.seg[2] + f.len[2]) {
-            int cc, q;
-            f3_slot(f, s, cc, q);
+    {   // folded inputs, item by item per component (columns fastest)
+        const int nic = f3_fold_items(fc), nis = f3_fold_items(fs), ni = nic > nis ? nic : nis;
+        for (int t = threadIdx.x; t < 3 * ni * CT; t += blockDim.x) {
+            const int ci = t / CT, col = t - ci * CT;
+            const int c = ci / ni, i = ci - c * ni;
+            if (i >= (c == 2 ? nic : nis)) continue;
+            const Fold3& f = c == 2 ? fc : fs;
+            const double* in = Buf + c * mz * CT + col;
+            double* ab = AB + c * mz * CT + col;
             auto vin = [&](int z) { return in[z * CT]; };
-            v = (three && cc == 2)
-                    ? f3_fwd_pre(f, (c == 2 ? TC : TS) + f.toff[2], q, [&](int p) { return f3_input(f, 2, p, vin); })
-                    : f3_input(f, cc, q, vin);
+            f3_fold_item(
+                f, i, vin,
+                [&](int q) {
+                    const double* Ti = (c == 2 ? TC : TS) + f.toff[2];
+                    return f3_fwd_pre(f, Ti, q, [&](int p) { return f3_input(f, 2, p, vin); });
+                },
+                [&](int slot, double val) { ab[slot * CT] = val; });
         }
-        AB[t] = v;
     }
     __syncthreads();
     if (three) {   // Ez (DCT-II): the inner slots
-        for (int t = threadIdx.x; t < N * CT; t += blockDim.x) {
-            const int s2 = t / CT, col = t - s2 * CT;
+        for (int t = threadIdx.x; t < f3_fold_items(g) * CT; t += blockDim.x) {
+            const int i = t / CT, col = t - i * CT;
             const double* a = AB + (2 * mz + fc.seg[2]) * CT + col;
-            XS[t] = f3_inner_slot(g, s2, [&](int p) { return a[p * CT]; });
+            auto v = [&](int p) { return a[p * CT]; };
+            f3_fold_item(g, i, v, [&](int q) { return f3_input(g, 2, q, v); },
+                         [&](int sl, double val) { XS[sl * CT + col] = val; });
         }
         __syncthreads();
     }
@@ -545,13 +561,17 @@ k_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int2
     double* Gin = AB;
     double* Gq = AB + 3 * N * CT;
     if (three) {
-        for (int t = threadIdx.x; t < 3 * N * CT; t += blockDim.x) {
-            const int cs = t / CT, col = t - cs * CT;
-            const int c = cs / N, s2 = cs - c * N;
+        const int ng = f3_fold_items(g);
+        for (int t = threadIdx.x; t < 3 * ng * CT; t += blockDim.x) {
+            const int ci = t / CT, col = t - ci * CT;
+            const int c = ci / ng, i = ci - c * ng;
             const double* e = Buf + (c * mz + 1) * CT + col;
             const double* d = TC + fc.toff[2] + fc.itab;
-            Gin[t] = f3_inv_slot(g, s2, [&](int p) { return e[2 * p * CT]; },
-                                 [&](int p) { return c == 2 ? d[p] : ((p & 1) ? -1.0 : 1.0); });
+            double* o = Gin + c * N * CT + col;
+            // the inner inputs: d_p y(p) (Ez, DCT-II) or (-1)^p y(p) (Ex, Ey, DST-I)
+            auto v = [&](int p) { return (c == 2 ? d[p] : ((p & 1) ? -1.0 : 1.0)) * e[2 * p * CT]; };
+            f3_fold_item(g, i, v, [&](int q) { return f3_input(g, 2, q, v); },
+                         [&](int sl, double val) { o[sl * CT] = val; });
         }
         __syncthreads();
         for (int t = threadIdx.x; t < 3 * N * CT; t += blockDim.x) {
@@ -633,10 +653,12 @@ k_inv_xy(const double* __restrict__ scr, double* __restrict__ zout, const FmpBox
         const int N = f.n[2];
         double* Gq = Gin + N * lines;
         const double* d = Ti + f.itab;
-        for (int t = threadIdx.x; t < N * lines; t += blockDim.x) {
-            const int s2 = t / lines, l = t - s2 * lines;
-            Gin[t] = f3_inv_slot(g, s2, [&](int p) { return y(l, p); },
-                                 [&](int p) { return f.off == 0 ? d[p] : ((p & 1) ? -1.0 : 1.0); });
+        for (int t = threadIdx.x; t < f3_fold_items(g) * lines; t += blockDim.x) {
+            const int i = t / lines, l = t - i * lines;
+            // the inner inputs: d_p y(p) (DCT-II) or (-1)^p y(p) (DST-I)
+            auto v = [&](int p) { return (f.off == 0 ? d[p] : ((p & 1) ? -1.0 : 1.0)) * y(l, p); };
+            f3_fold_item(g, i, v, [&](int q) { return f3_input(g, 2, q, v); },
+                         [&](int sl, double val) { Gin[sl * lines + l] = val; });
         }
         __syncthreads();
         for (int t = threadIdx.x; t < N * lines; t += blockDim.x) {
