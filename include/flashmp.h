@@ -185,18 +185,27 @@ int fmp_set_fused(fmp_ctx* ctx, int max_extent);
 int fmp_get_fused(fmp_ctx* ctx, int* max_extent, int* n_fused);
 
 /* Gram-Schmidt arithmetic of FGMRES (Table 3's dots and AXPYs per
- * iteration): fixed_point = 0 (default) runs the float64 FMA passes;
- * fixed_point = 1 runs the basis dot and update passes with exact 64-bit
+ * iteration), an fmp_orth_mode:
+ * FMP_ORTH_FLOAT64 runs the float64 FMA passes.
+ * FMP_ORTH_FIXED runs the basis dot and update passes with exact 64-bit
  * integer products on fixed-point copies of the basis vectors (each relative
  * to its own largest element; the float64 basis stays the preconditioner's
  * input; 8 more bytes per basis slot), off the float64 pipe: every product
  * is exact, each dot is rounded to float64 once per thread, each update
  * correction once per element. On this part the integer passes measured
  * slower than the float64 ones (the conversions and 64 x 64-bit multiplies
- * cost more issue slots than the float64 FMAs they replace). Results agree
- * to rounding, not bitwise. */
-int fmp_set_orth(fmp_ctx* ctx, int fixed_point);
-int fmp_get_orth(fmp_ctx* ctx, int* fixed_point);
+ * cost more issue slots than the float64 FMAs they replace).
+ * FMP_ORTH_SPLIT (default) gives the oldest vectors of each pass (about a
+ * third of a dot pass's, a quarter of an update pass's from ten vectors on,
+ * at most six) those exact fixed-point products, converted from the float64
+ * basis as it is read (no copies), and the rest float64 FMAs, so that the
+ * float64 and the integer pipes share the work and HBM bounds the passes.
+ * Results of the three agree to rounding, not bitwise (the same iteration
+ * counts on the benchmark workloads). Returns FMP_ERR_ARG for another
+ * value. */
+enum fmp_orth_mode { FMP_ORTH_FLOAT64 = 0, FMP_ORTH_FIXED = 1, FMP_ORTH_SPLIT = 2 };
+int fmp_set_orth(fmp_ctx* ctx, int mode);
+int fmp_get_orth(fmp_ctx* ctx, int* mode);
 
 /* Streamed reduced-precision box solve (not in the paper; Algorithm 1 over
  * subdomains of uneven size, extents 2 .. 80, in one persistent launch): for

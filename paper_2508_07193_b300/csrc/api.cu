@@ -754,19 +754,19 @@ int fmp_get_fused(fmp_ctx* c, int* max_extent, int* n_fused) {
     return FMP_OK;
 }
 
-int fmp_set_orth(fmp_ctx* c, int fixed_point) {
-    if (!valid_ctx(c) || fixed_point < 0 || fixed_point > 1) return FMP_ERR_ARG;
+int fmp_set_orth(fmp_ctx* c, int mode) {
+    if (!valid_ctx(c) || mode < FMP_ORTH_FLOAT64 || mode > FMP_ORTH_SPLIT) return FMP_ERR_ARG;
     if (int rc = latched(c)) return rc;
-    if (fixed_point == c->gs_fixed) return FMP_OK;
+    if (mode == c->gs_mode) return FMP_OK;
     FMP_CK(cudaStreamSynchronize(c->stream));
-    c->gs_fixed = fixed_point;
+    c->gs_mode = mode;
     fmp_invalidate_graphs(c);
     return FMP_OK;
 }
 
-int fmp_get_orth(fmp_ctx* c, int* fixed_point) {
-    if (!valid_ctx(c) || !fixed_point) return FMP_ERR_ARG;
-    *fixed_point = c->gs_fixed;
+int fmp_get_orth(fmp_ctx* c, int* mode) {
+    if (!valid_ctx(c) || !mode) return FMP_ERR_ARG;
+    *mode = c->gs_mode;
     return FMP_OK;
 }
 

@@ -428,7 +428,7 @@ k_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox* _
 
 // Pass B: z transform, per-mode 3x3 solve, inverse z transform (owned z).
 template <int CT>
-__global__ void __launch_bounds__(kThreads, 5)
+__global__ void __launch_bounds__(kThreads, 6)
 k_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int2* __restrict__ items,
           const double* __restrict__ tabs, const double* __restrict__ modeinv, double beta,
           const double* __restrict__ gate) {

@@ -264,7 +264,7 @@ struct fmp_ctx {
     long long launches = 0;       // kernels launched by this context (graph nodes included)
     size_t ld = 0;                // padded vector length
     double* d_V = nullptr;        // (restart+1) x ld
-    int gs_fixed = 0;             // Gram-Schmidt passes in exact fixed point (1) or float64 (0, default)
+    int gs_mode = FMP_ORTH_SPLIT;     // Gram-Schmidt arithmetic (fmp_set_orth)
     long long* d_X = nullptr;     // (restart+1) x ld fixed-point copies of the FGMRES basis
     unsigned* d_vmax = nullptr;   // restart+2: largest |V_i| as sign-cleared high words
     double* d_Z = nullptr;        // restart x ld
@@ -291,10 +291,12 @@ cudaError_t fmp_launch_transform_solve_fp64(const FmpPlan& p, const double* tabs
                                             const double* r, double* z, double* scratch, int nx, int ny, int nz,
                                             double beta, cudaStream_t s, const double* gate);
 cudaError_t fmp_stencil_init();   // kernel attributes of the operator apply
-// y = s_b * b + c_eps * eps o x + c_k * K x  (b may be null)
+// y = s_b * b + c_eps * eps o x + c_k * K x  (b may be null); with ymax, the
+// largest |y| (sign-cleared high word) is raised into *ymax (atomicMax)
 cudaError_t fmp_launch_curlcurl(const double* x, const double* eps, double* y, double c_eps,
                                 double c_k, int nx, int ny, int nz, cudaStream_t s,
-                                const double* gate, const double* b = nullptr, double s_b = 0.0);
+                                const double* gate, const double* b = nullptr, double s_b = 0.0,
+                                unsigned* ymax = nullptr);
 cudaError_t fmp_launch_cn_rhs(const double* E, const double* H, const double* J,
                               const double* eps, double beta, double dt, double* R, int nx,
                               int ny, int nz, cudaStream_t s);

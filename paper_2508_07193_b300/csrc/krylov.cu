@@ -272,6 +272,30 @@ __device__ void arnoldi_finish(double* st, const St& L, int j, const double* h, 
     }
 }
 
+// The last block of an update pass, given nrm = ||w - V h||: mode 0 finishes
+// the column with h1, or raises the re-orthogonalisation flag when the
+// projection cancelled more than 1 - kReorthRatio of ||w||; mode 1 finishes
+// it with h1 + h2. V[j+1] = w stays unnormalised, with sv[j+1] = 1 / h(j+1, j).
+__device__ void update_finish(double* st, const St& L, int j, int nv, int mode, double nrm) {
+    if (mode == 0) {
+        const double wn = sqrt(st[L.h1 + nv]);   // ||w|| before projection
+        if (nrm >= kReorthRatio * wn || !isfinite(nrm)) {
+            st[L.sc + SC_REORTH] = 0.0;
+            arnoldi_finish(st, L, j, st + L.h1, nrm);
+            st[L.sv + j + 1] = st[L.sc + SC_INV];
+        } else {
+            st[L.sc + SC_REORTH] = 1.0;
+            st[L.sc + SC_NREORTH] += 1.0;
+        }
+    } else {
+        double hsum[kMaxV];
+        for (int i = 0; i <= j; ++i) hsum[i] = st[L.h1 + i] + st[L.h2 + i];
+        st[L.sc + SC_REORTH] = 0.0;
+        arnoldi_finish(st, L, j, hsum, nrm);
+        st[L.sv + j + 1] = st[L.sc + SC_INV];
+    }
+}
+
 // w -= V h. mode 0: h = h1, then the DGKS test decides between finishing the
 // column and raising the re-orthogonalisation flag. mode 1 (flag up only):
 // h = h2, then finish the column with h1 + h2. One thread per element like
@@ -309,25 +333,8 @@ k_update(const double* __restrict__ V, size_t ld, double* __restrict__ w, size_t
         block_totals(partials, 1, &tot);
         __syncthreads();
         if (threadIdx.x == 0) {
-            const double nrm = sqrt(tot);
             *ticket = 0;
-            if (mode == 0) {
-                const double wn = sqrt(st[L.h1 + nv]);   // ||w|| before projection
-                if (nrm >= kReorthRatio * wn || !isfinite(nrm)) {
-                    st[L.sc + SC_REORTH] = 0.0;
-                    arnoldi_finish(st, L, j, st + L.h1, nrm);
-                    st[L.sv + j + 1] = st[L.sc + SC_INV];   // V[j+1] = w, unnormalised
-                } else {
-                    st[L.sc + SC_REORTH] = 1.0;
-                    st[L.sc + SC_NREORTH] += 1.0;
-                }
-            } else {
-                double hsum[kMaxV];
-                for (int i = 0; i <= j; ++i) hsum[i] = st[L.h1 + i] + st[L.h2 + i];
-                st[L.sc + SC_REORTH] = 0.0;
-                arnoldi_finish(st, L, j, hsum, nrm);
-                st[L.sv + j + 1] = st[L.sc + SC_INV];
-            }
+            update_finish(st, L, j, nv, mode, sqrt(tot));
         }
     }
 }
@@ -429,6 +436,16 @@ __device__ __forceinline__ long long fix62(double v, int ex) {
     const long long X = (e == 0 || sh > 63 || sh < 0) ? 0LL : (long long)(m >> sh);
     return (b >> 63) ? -X : X;
 }
+// W = trunc(w 2^(1075 - rw)) for |w| < 2^(rw - 1022): the 53-bit mantissa
+// shifted right by rw - e(w); zero and subnormals 0
+__device__ __forceinline__ long long fix53(double w, int rw) {
+    const unsigned long long wb = (unsigned long long)__double_as_longlong(w);
+    const int ew = (int)(wb >> 52) & 0x7FF;
+    const int sh = rw - ew;
+    const long long W = (ew == 0 || sh > 63 || sh < 0) ? 0LL
+                                                        : (long long)(((wb & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> sh);
+    return (wb >> 63) ? -W : W;
+}
 __device__ __forceinline__ unsigned abs_hi(double v) { return (unsigned)__double2hiint(v) & 0x7FFFFFFFu; }
 
 // one block per SM for large bases (128-bit sums in registers)
@@ -458,13 +475,7 @@ k_dots_fx(const double* __restrict__ V, long long* __restrict__ X, size_t ld, co
     for (size_t e = (size_t)blockIdx.x * kT + threadIdx.x; e < n; e += (size_t)gridDim.x * kT) {
         const double wv = __ldg(w + e);
         ww = fma(wv, wv, ww);
-        // W = w 2^(1075 - rw): the 53-bit mantissa shifted right by rw - e(w)
-        const unsigned long long wb = (unsigned long long)__double_as_longlong(wv);
-        const int ew = (int)(wb >> 52) & 0x7FF;
-        const int sh = rw - ew;
-        long long W = (ew == 0 || sh > 63 || sh < 0) ? 0LL
-                                                      : (long long)(((wb & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> sh);
-        W = (wb >> 63) ? -W : W;
+        const long long W = fix53(wv, rw);
 #pragma unroll
         for (int g = 0; g < NV - 1; ++g) mac128(acc[g], __ldg(X + (size_t)g * ld + e), W);
         long long x;
@@ -556,38 +567,206 @@ k_update_fx(const long long* __restrict__ X, size_t ld, double* __restrict__ w, 
         block_totals(partials, 1, &tot);
         __syncthreads();
         if (threadIdx.x == 0) {
-            const double nrm = sqrt(tot);
             *ticket = 0;
-            if (mode == 0) {
-                const double wn = sqrt(st[L.h1 + nv]);   // ||w|| before projection
-                if (nrm >= kReorthRatio * wn || !isfinite(nrm)) {
-                    st[L.sc + SC_REORTH] = 0.0;
-                    arnoldi_finish(st, L, j, st + L.h1, nrm);
-                    st[L.sv + j + 1] = st[L.sc + SC_INV];   // V[j+1] = w, unnormalised
-                } else {
-                    st[L.sc + SC_REORTH] = 1.0;
-                    st[L.sc + SC_NREORTH] += 1.0;
+            update_finish(st, L, j, nv, mode, sqrt(tot));
+        }
+    }
+}
+
+// ---- split basis passes (fmp_set_orth(ctx, 2)) -----------------------------
+// The float64 passes issue one float64 FMA per 8 bytes, which on this part
+// caps them near 0.7 of HBM; the fixed-point passes move every product to the
+// integer pipes and become issue-bound. These passes give each pipe a share:
+// the oldest vectors of a pass take exact fixed-point products (X_i converted
+// from the float64 vector as it is loaded, so no fixed-point copies are kept;
+// scales as in the fixed-point passes), the others float64 FMAs. The shares
+// (measured per basis size at 128^3): a dot pass moves about a third of its
+// vectors, at most six (more integer accumulators crowd the registers out of
+// the loads in flight); an update pass, whose integer sum is converted to
+// float64 once per element, a quarter, at most six, and none below ten
+// vectors (there the conversion costs about what it saves). The vectors'
+// largest magnitudes (vmax) are tracked as for the fixed-point passes.
+#ifndef FMP_SPLIT_DOTS_DEN
+#define FMP_SPLIT_DOTS_DEN 3
+#endif
+#ifndef FMP_SPLIT_UPDATE_DEN
+#define FMP_SPLIT_UPDATE_DEN 4
+#endif
+constexpr int kSplitCap = 6;   // at most this many fixed-point vectors per pass
+__host__ __device__ constexpr int split_share(int nv, int den) {
+    return (nv + 1) / den < kSplitCap ? (nv + 1) / den : kSplitCap;
+}
+__host__ __device__ constexpr int split_dots(int nv) { return split_share(nv, FMP_SPLIT_DOTS_DEN); }
+__host__ __device__ constexpr int split_update(int nv) { return nv < 10 ? 0 : split_share(nv, FMP_SPLIT_UPDATE_DEN); }
+// (one block of 255 registers per SM for large bases, which would hold more
+// fixed-point vectors, measured 13-28 % slower than two of 128)
+__host__ __device__ constexpr int split_blocks_per_sm(int nv) { return nv <= 8 ? 4 : 2; }
+
+// t 2^k as float64, truncated toward zero, by integer operations (no branch):
+// the update's fixed-point sum reaches float64 without the float64 pipe.
+// Results below 2^-1022 flush to zero; |t| 2^k stays far below the overflow
+// threshold here (it is a correction of the size of w).
+__device__ __forceinline__ double i64_scaled_f64(long long t, int k) {
+    const unsigned long long sgn = (unsigned long long)t & 0x8000000000000000ull;
+    const unsigned long long a = t < 0 ? 0ull - (unsigned long long)t : (unsigned long long)t;
+    const int lz = __clzll((long long)a);                       // 64 when a = 0
+    const unsigned long long nrm = a << (lz & 63);              // leading one at bit 63
+    const int field = 63 - lz + k + 1023;                       // biased exponent of the result
+    const unsigned long long bits =
+        sgn | ((unsigned long long)field << 52) | ((nrm >> 11) & 0xFFFFFFFFFFFFFull);
+    return (a == 0ull || field <= 0) ? 0.0 : __longlong_as_double((long long)bits);
+}
+
+// out[i] = <V_i, w> for i < NV and out[NV] = <w, w>, vectors i < split_dots(NV)
+// in exact fixed point (w as W = fix53(w, Rw)); mode 0 also clears vmax[NV]
+// for the update passes (as k_dots_fx). The launch gives every thread at most
+// kFold elements.
+template <int NV>
+__global__ void __launch_bounds__(kT, split_blocks_per_sm(NV))
+k_dots_sp(const double* __restrict__ V, size_t ld, const double* __restrict__ w, size_t n, double* st, int R,
+          int out_off, int mode, unsigned* vmax, double* partials, unsigned int* ticket) {
+    constexpr int NI = split_dots(NV);
+    constexpr int NIa = NI > 0 ? NI : 1;
+    constexpr int U = basis_unroll(NV);
+    const St L = st_layout(R);
+    if (gated(st, L.sc) || (mode == 1 && st[L.sc + SC_REORTH] == 0.0)) return;
+    const int rw = NI > 0 ? (int)(vmax[mode == 0 ? R + 1 : NV] >> 20) : 0;
+    int ex[NIa];
+    I128 ia[NIa];
+#pragma unroll
+    for (int g = 0; g < NIa; ++g) {
+        ex[g] = NI > 0 ? (int)(vmax[g] >> 20) : 0;
+        ia[g].lo = 0ull;
+        ia[g].hi = 0;
+    }
+    constexpr int G = pow2_at_least(NV);
+    double acc[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) acc[g] = 0.0;
+    double ww = 0.0;
+    for (size_t e0 = (size_t)blockIdx.x * kT * U + threadIdx.x; e0 < n; e0 += (size_t)gridDim.x * kT * U) {
+        double x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) x[u] = e0 + u * kT < n ? __ldg(w + e0 + u * kT) : 0.0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const size_t e = e0 + u * kT;
+            if (e < n) {
+                ww = fma(x[u], x[u], ww);
+#pragma unroll
+                for (int g = NI; g < NV; ++g) acc[g] = fma(__ldg(V + (size_t)g * ld + e), x[u], acc[g]);
+                if (NI > 0) {
+                    const long long W = fix53(x[u], rw);
+#pragma unroll
+                    for (int g = 0; g < NI; ++g) mac128(ia[g], fix62(__ldg(V + (size_t)g * ld + e), ex[g]), W);
                 }
-            } else {
-                double hsum[kMaxV];
-                for (int i = 0; i <= j; ++i) hsum[i] = st[L.h1 + i] + st[L.h2 + i];
-                st[L.sc + SC_REORTH] = 0.0;
-                arnoldi_finish(st, L, j, hsum, nrm);
-                st[L.sv + j + 1] = st[L.sc + SC_INV];
             }
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < NI; ++g) acc[g] = ldexp(i128_fp64(ia[g]), ex[g] + rw - 2159);
+    if (mode == 0 && blockIdx.x == 0 && threadIdx.x == 0) vmax[NV] = 0u;
+    __shared__ double wsum[kT / 32][kMaxV + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int slot;
+    const double v = warp_reduce_scatter<G>(acc, lane, slot);
+    if ((lane & (32 / G - 1)) == 0) wsum[warp][slot] = v;
+    const double wv = warp_sum(ww);
+    if (lane == 0) wsum[warp][kMaxV] = wv;
+    __syncthreads();
+    __shared__ double tot[kMaxV + 2];
+    if (threadIdx.x <= NV) {
+        const int sl = threadIdx.x < NV ? threadIdx.x : kMaxV;
+        double sum = 0.0;
+        for (int q = 0; q < kT / 32; ++q) sum += wsum[q][sl];
+        tot[threadIdx.x] = sum;
+    }
+    __syncthreads();
+    if (block_publish(tot, NV + 1, partials, ticket)) {
+        block_totals(partials, NV + 1, st + out_off);
+        __syncthreads();
+        if (threadIdx.x < NV) st[out_off + threadIdx.x] *= st[L.sv + threadIdx.x];
+        if (threadIdx.x == 0) *ticket = 0;
+    }
+}
+
+// w -= V h: vectors i < split_update(NV) as the exact 128-bit sum
+// S = sum D_i X_i of k_update_fx (|S| < 2^122 for at most eight of them), cut
+// to its top bits T = S >> 59 (|T| < 2^63; what is cut lies below 2^-60 of
+// the largest possible term) and added as T 2^(Gx + 2) to the float64 FMA
+// chain of the others; the rest (norm, DGKS test, vmax[j + 1]) as k_update_fx.
+template <int NV>
+__global__ void __launch_bounds__(kT, split_blocks_per_sm(NV))
+k_update_sp(const double* __restrict__ V, size_t ld, double* __restrict__ w, size_t n, double* st, int R, int j,
+            int mode, unsigned* vmax, double* partials, unsigned int* ticket) {
+    constexpr int nv = NV;
+    constexpr int NI = split_update(NV);
+    constexpr int NIa = NI > 0 ? NI : 1;
+    constexpr int U = basis_unroll(NV);
+    static_assert(NI <= 8, "the 128-bit sum bound above");
+    const St L = st_layout(R);
+    if (gated(st, L.sc) || (mode == 1 && st[L.sc + SC_REORTH] == 0.0)) return;
+    const double* h = st + (mode == 0 ? L.h1 : L.h2);
+    double hr[NV];
+#pragma unroll
+    for (int g = 0; g < NV; ++g) hr[g] = -h[g] * st[L.sv + g];
+    // c_i = hr_i 2^(ex_i - 1084) = D_i 2^(Gx - 57), one exponent Gx for all i < NI
+    int ex[NIa];
+    double c[NIa];
+    int Gx = -4000;
+#pragma unroll
+    for (int g = 0; g < NIa; ++g) {
+        ex[g] = NI > 0 ? (int)(vmax[g] >> 20) : 0;
+        c[g] = NI > 0 ? ldexp(hr[g], ex[g] - 1084) : 0.0;
+        int eg = 0;
+        if (c[g] != 0.0 && isfinite(c[g])) { frexp(c[g], &eg); Gx = max(Gx, eg); }
+    }
+    long long D[NIa];
+#pragma unroll
+    for (int g = 0; g < NIa; ++g) D[g] = (NI > 0 && isfinite(c[g])) ? (long long)ldexp(c[g], 57 - Gx) : 0LL;
+    double acc[1] = {0.0};
+    unsigned mx = 0u;
+    for (size_t e0 = (size_t)blockIdx.x * kT * U + threadIdx.x; e0 < n; e0 += (size_t)gridDim.x * kT * U) {
+        double x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) x[u] = e0 + u * kT < n ? w[e0 + u * kT] : 0.0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const size_t e = e0 + u * kT;
+            if (e < n) {
+#pragma unroll
+                for (int g = NI; g < NV; ++g) x[u] = fma(hr[g], __ldg(V + (size_t)g * ld + e), x[u]);
+                if (NI > 0) {
+                    I128 sm;
+                    sm.lo = 0ull;
+                    sm.hi = 0;
+#pragma unroll
+                    for (int g = 0; g < NI; ++g) mac128(sm, D[g], fix62(__ldg(V + (size_t)g * ld + e), ex[g]));
+                    const long long T = (long long)((sm.lo >> 59) | ((unsigned long long)sm.hi << 5));
+                    x[u] += i64_scaled_f64(T, Gx + 2);
+                }
+                w[e] = x[u];
+                acc[0] = fma(x[u], x[u], acc[0]);
+                mx = max(mx, abs_hi(x[u]));
+            }
+        }
+    }
+    {
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        if ((threadIdx.x & 31) == 0 && mx != 0u) atomicMax(vmax + j + 1, mx);
+    }
+    if (block_partials(acc, 1, partials, ticket)) {
+        __shared__ double tot;
+        block_totals(partials, 1, &tot);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            *ticket = 0;
+            update_finish(st, L, j, nv, mode, sqrt(tot));
         }
     }
 }
 
 // *out = the largest |v| (high words), after a cleared *out.
-__global__ void k_absmax_gated(const double* __restrict__ v, size_t n, unsigned* out, const double* gate) {
-    if (gate && *gate != 0.0) return;
-    unsigned m = 0u;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
-        m = max(m, abs_hi(__ldg(v + e)));
-    m = __reduce_max_sync(0xffffffffu, m);
-    if ((threadIdx.x & 31) == 0 && m != 0u) atomicMax(out, m);
-}
 __global__ void k_absmax(const double* __restrict__ v, size_t n, unsigned* out) {
     unsigned m = 0u;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
@@ -833,6 +1012,16 @@ void launch_update_fx_nv(const FxArgs& a, cudaStream_t s) {
     k_update_fx<NV><<<grid_basis(a.n, fx_blocks_per_sm(NV)), kT, 0, s>>>(a.X, a.ld, a.w, a.n, a.st, a.R, a.j, a.mode,
                                                                          a.vmax, a.partials, a.ticket);
 }
+template <int NV>
+void launch_dots_sp_nv(const FxArgs& a, cudaStream_t s) {
+    k_dots_sp<NV><<<grid_fx(a.n, split_blocks_per_sm(NV)), kT, 0, s>>>(a.V, a.ld, a.w, a.n, a.st, a.R, a.out_off,
+                                                                        a.mode, a.vmax, a.partials, a.ticket);
+}
+template <int NV>
+void launch_update_sp_nv(const FxArgs& a, cudaStream_t s) {
+    k_update_sp<NV><<<grid_basis(a.n, split_blocks_per_sm(NV)), kT, 0, s>>>(a.V, a.ld, a.w, a.n, a.st, a.R, a.j,
+                                                                             a.mode, a.vmax, a.partials, a.ticket);
+}
 using FxLaunch = void (*)(const FxArgs&, cudaStream_t);
 template <int... I>
 constexpr std::array<FxLaunch, sizeof...(I)> dots_fx_table(std::integer_sequence<int, I...>) {
@@ -842,6 +1031,16 @@ template <int... I>
 constexpr std::array<FxLaunch, sizeof...(I)> update_fx_table(std::integer_sequence<int, I...>) {
     return {{&launch_update_fx_nv<I + 1>...}};
 }
+template <int... I>
+constexpr std::array<FxLaunch, sizeof...(I)> dots_sp_table(std::integer_sequence<int, I...>) {
+    return {{&launch_dots_sp_nv<I + 1>...}};
+}
+template <int... I>
+constexpr std::array<FxLaunch, sizeof...(I)> update_sp_table(std::integer_sequence<int, I...>) {
+    return {{&launch_update_sp_nv<I + 1>...}};
+}
+constexpr auto kDotsSp = dots_sp_table(std::make_integer_sequence<int, kMaxV>{});
+constexpr auto kUpdatesSp = update_sp_table(std::make_integer_sequence<int, kMaxV>{});
 constexpr auto kDotsFx = dots_fx_table(std::make_integer_sequence<int, kMaxV>{});
 constexpr auto kUpdatesFx = update_fx_table(std::make_integer_sequence<int, kMaxV>{});
 constexpr auto kDots = dots_table(std::make_integer_sequence<int, kMaxV>{});
@@ -950,19 +1149,22 @@ int arnoldi_step(fmp_ctx* c, int j, fmp_solve_info* inf) {
             FMP_CK(cudaGetLastError());
         }
     }
+    const int nv = j + 1;
+    const bool fixed = c->gs_mode == FMP_ORTH_FIXED && c->d_X;
+    const bool split = c->gs_mode == FMP_ORTH_SPLIT && c->d_vmax;
     {
         Timer tm(c, &inf->ms_spmv, "matvec");
+        // the largest |w| for the dots' common fixed-point scale, from the
+        // SpMV's epilogue, when a fixed-point product needs it
+        unsigned* wmax = (fixed || (split && split_dots(nv) > 0)) ? c->d_vmax + R + 1 : nullptr;
+        if (wmax) FMP_CK(cudaMemsetAsync(wmax, 0, sizeof(unsigned), s));
         ++c->launches;
-        FMP_CK(fmp_launch_curlcurl(zj, c->d_eps_edge, w, 1.0, c->beta, c->nx, c->ny, c->nz, s, gate));
+        FMP_CK(fmp_launch_curlcurl(zj, c->d_eps_edge, w, 1.0, c->beta, c->nx, c->ny, c->nz, s, gate, nullptr, 0.0,
+                                   wmax));
     }
     {
         Timer tm(c, &inf->ms_orth, "orth");
-        const int nv = j + 1;
-        if (c->gs_fixed && c->d_X) {
-            // the largest |w| of the SpMV's output, for the dots' common scale
-            FMP_CK(cudaMemsetAsync(c->d_vmax + R + 1, 0, sizeof(unsigned), s));
-            ++c->launches;
-            k_absmax_gated<<<grid_n(n), kT, 0, s>>>(w, n, c->d_vmax + R + 1, gate);
+        if (fixed) {
             FxArgs a{V, c->d_X, ld, w, n, st, R, j, L.h1, 0, c->d_vmax, c->d_partials, c->d_ticket};
             c->launches += 2;
             kDotsFx[nv - 1](a, s);
@@ -972,6 +1174,17 @@ int arnoldi_step(fmp_ctx* c, int j, fmp_solve_info* inf) {
             c->launches += 2;
             kDotsFx[nv - 1](a, s);
             kUpdatesFx[nv - 1](a, s);
+            FMP_CK(cudaGetLastError());
+        } else if (split) {
+            FxArgs a{V, nullptr, ld, w, n, st, R, j, L.h1, 0, c->d_vmax, c->d_partials, c->d_ticket};
+            c->launches += 2;
+            kDotsSp[nv - 1](a, s);
+            kUpdatesSp[nv - 1](a, s);
+            a.out_off = L.h2;
+            a.mode = 1;
+            c->launches += 2;
+            kDotsSp[nv - 1](a, s);
+            kUpdatesSp[nv - 1](a, s);
             FMP_CK(cudaGetLastError());
         } else {
             ++c->launches;
@@ -1028,8 +1241,11 @@ cudaError_t fmp_ensure_krylov(fmp_ctx* c) {
     const int R = c->opt.restart;
     const int need_v = R + 1 > 9 ? R + 1 : 9;   // BiCGSTAB uses 9: r, rhat, p, v, s, t, phat, shat, x
     const int need_z = c->opt.krylov == FMP_KRYLOV_BICGSTAB ? 0 : R;
-    const bool need_x = c->opt.krylov != FMP_KRYLOV_BICGSTAB && c->gs_fixed;
-    if (c->d_V && c->kry_restart == R && c->kry_nv >= need_v && c->kry_nz >= need_z && (!need_x || c->d_X))
+    const bool fgmres = c->opt.krylov != FMP_KRYLOV_BICGSTAB;
+    const bool need_x = fgmres && c->gs_mode == FMP_ORTH_FIXED;
+    const bool need_vmax = fgmres && c->gs_mode != FMP_ORTH_FLOAT64;
+    if (c->d_V && c->kry_restart == R && c->kry_nv >= need_v && c->kry_nz >= need_z && (!need_x || c->d_X) &&
+        (!need_vmax || c->d_vmax))
         return cudaSuccess;
     cudaFree(c->d_V); cudaFree(c->d_Z); cudaFree(c->d_state); cudaFree(c->d_X); cudaFree(c->d_vmax);
     c->d_V = c->d_Z = c->d_state = nullptr;
@@ -1042,10 +1258,9 @@ cudaError_t fmp_ensure_krylov(fmp_ctx* c) {
     if ((e = cudaMalloc(&c->d_V, sizeof(double) * c->ld * need_v))) return e;
     if (need_z && (e = cudaMalloc(&c->d_Z, sizeof(double) * c->ld * need_z))) return e;
     if ((e = cudaMalloc(&c->d_state, sizeof(double) * st_layout(R).total))) return e;
-    if (need_x) {   // fixed-point copies of the basis and their largest magnitudes
-        if ((e = cudaMalloc(&c->d_X, sizeof(long long) * c->ld * (R + 1)))) return e;
-        if ((e = cudaMalloc(&c->d_vmax, sizeof(unsigned) * (R + 2)))) return e;
-    }
+    // fixed-point copies of the basis; the largest magnitudes of its vectors
+    if (need_x && (e = cudaMalloc(&c->d_X, sizeof(long long) * c->ld * (R + 1)))) return e;
+    if (need_vmax && (e = cudaMalloc(&c->d_vmax, sizeof(unsigned) * (R + 2)))) return e;
     if ((e = cudaMemsetAsync(c->d_state, 0, sizeof(double) * st_layout(R).total, c->stream))) return e;
     c->kry_nv = need_v; c->kry_nz = need_z; c->kry_restart = R;
     return cudaSuccess;
@@ -1100,7 +1315,7 @@ int fmp_fgmres(fmp_ctx* c, const double* b, double* x, fmp_solve_info* info) {
         ++c->launches;
         k_cycle_init<<<1, 1, 0, s>>>(st, R, c->opt.rtol, budget);
         FMP_CK(cudaGetLastError());
-        if (c->gs_fixed && c->d_X) {   // the largest |V_0| for its fixed-point copy
+        if (c->gs_mode != FMP_ORTH_FLOAT64 && c->d_vmax) {   // the largest |V_0|, the scale of its fixed point
             FMP_CK(cudaMemsetAsync(c->d_vmax, 0, sizeof(unsigned), s));
             ++c->launches;
             k_absmax<<<grid_n(n), kT, 0, s>>>(V, n, c->d_vmax);

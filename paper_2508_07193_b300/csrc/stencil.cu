@@ -135,6 +135,8 @@ constexpr int TX = 32, TY = 8;
 constexpr int PX = TX + 2, PY = TY + 2, PLANE = 3 * PX * PY;   // E tile with halo
 constexpr int FX = TX + 1, FY = TY + 1, FPLANE = 3 * FX * FY;  // faces, low halo
 
+__device__ __forceinline__ unsigned abs_hi(double v) { return (unsigned)__double2hiint(v) & 0x7FFFFFFFu; }
+
 // FORM selects the epilogue, so that the solver's forms spend no float64
 // operation on a factor of one: 0 any (c_eps, c_k, s_b, b); 1 the operator
 // itself, c_eps = 1 and no b; 2 the residual, c_eps = -1, s_b = 1 and b.
@@ -204,11 +206,11 @@ __device__ __forceinline__ double from_fixed(long long K, int emax) {
 // blocks of two planes converted with their two halo planes each: about 550
 // thread instructions per cell instead of 650 (ncu), 0.059 -> 0.057 ms at
 // 128^3, 0.417 -> 0.373 ms at 256^3.
-template <int FORM>
+template <int FORM, bool YMAX>
 __global__ void __launch_bounds__(TX * TY, 4)
 k_curlcurl_zm(const double* __restrict__ x, const double* __restrict__ eps, double* __restrict__ y,
               const double* __restrict__ b, double s_b, double c_eps, double c_k, Dims d, int kz,
-              const double* __restrict__ gate) {
+              const double* __restrict__ gate, unsigned* __restrict__ ymax) {
     if (gate && *gate != 0.0) return;
     constexpr int NQ = (PLANE + TX * TY - 1) / (TX * TY);   // E slots per thread and plane (4)
     constexpr int NFQ = (FPLANE / 3 + TX * TY - 1) / (TX * TY);   // face slots per thread, per component (2)
@@ -303,6 +305,7 @@ k_curlcurl_zm(const double* __restrict__ x, const double* __restrict__ eps, doub
     const int gi = i0 + tx, gj = j0 + ty;
     const bool live = gi < d.nx && gj < d.ny;
     const int fo = (ty + 1) * FX + tx + 1;
+    unsigned mx = 0u;
     for (int k = k0; k < k1; ++k) {
         // va holds plane k + 1; its exponent joins the running maximum
         exponent(va, k + 1);
@@ -349,7 +352,12 @@ k_curlcurl_zm(const double* __restrict__ x, const double* __restrict__ eps, doub
             y[o] = vx;
             y[d.comp + o] = vy;
             y[2 * d.comp + o] = vz;
+            if constexpr (YMAX) mx = max(mx, max(abs_hi(vx), max(abs_hi(vy), abs_hi(vz))));
         }
+    }
+    if constexpr (YMAX) {   // the largest |y| (sign-cleared high words) into *ymax
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        if ((threadIdx.x & 31) == 0 && mx != 0u) atomicMax(ymax, mx);
     }
 }
 
@@ -460,16 +468,21 @@ cudaError_t fmp_stencil_init() { return cudaSuccess; }
 int zm_planes(int nz) { return std::max(8, std::min(16, nz / 16)); }
 
 cudaError_t fmp_launch_curlcurl(const double* x, const double* eps, double* y, double c_eps, double c_k, int nx,
-                                int ny, int nz, cudaStream_t s, const double* gate, const double* b, double s_b) {
+                                int ny, int nz, cudaStream_t s, const double* gate, const double* b, double s_b,
+                                unsigned* ymax) {
     const int kz = zm_planes(nz);
     const dim3 g((nx + TX - 1) / TX, (ny + TY - 1) / TY, (nz + kz - 1) / kz);
     const Dims d = dims(nx, ny, nz);
-    if (c_eps == 1.0 && !b)
-        k_curlcurl_zm<1><<<g, TX * TY, 0, s>>>(x, eps, y, b, s_b, c_eps, c_k, d, kz, gate);
-    else if (c_eps == -1.0 && b && s_b == 1.0)
-        k_curlcurl_zm<2><<<g, TX * TY, 0, s>>>(x, eps, y, b, s_b, c_eps, c_k, d, kz, gate);
-    else
-        k_curlcurl_zm<0><<<g, TX * TY, 0, s>>>(x, eps, y, b, s_b, c_eps, c_k, d, kz, gate);
+    if (ymax) {
+        if (c_eps != 1.0 || b) return cudaErrorInvalidValue;   // the Arnoldi step's form only
+        k_curlcurl_zm<1, true><<<g, TX * TY, 0, s>>>(x, eps, y, b, s_b, c_eps, c_k, d, kz, gate, ymax);
+    } else if (c_eps == 1.0 && !b) {
+        k_curlcurl_zm<1, false><<<g, TX * TY, 0, s>>>(x, eps, y, b, s_b, c_eps, c_k, d, kz, gate, nullptr);
+    } else if (c_eps == -1.0 && b && s_b == 1.0) {
+        k_curlcurl_zm<2, false><<<g, TX * TY, 0, s>>>(x, eps, y, b, s_b, c_eps, c_k, d, kz, gate, nullptr);
+    } else {
+        k_curlcurl_zm<0, false><<<g, TX * TY, 0, s>>>(x, eps, y, b, s_b, c_eps, c_k, d, kz, gate, nullptr);
+    }
     return cudaGetLastError();
 }
 

@@ -298,14 +298,25 @@ class Context:
         _check(lib().fmp_get_streamed(self._h, C.byref(m), C.byref(n)), "fmp_get_streamed")
         return m.value, n.value
 
-    def set_orth(self, fixed_point=True):
-        """Gram-Schmidt passes in exact fixed point, or float64 (the default; fmp_set_orth)."""
-        _check(lib().fmp_set_orth(self._h, int(bool(fixed_point))), "fmp_set_orth")
+    ORTH_MODES = {"float64": 0, "fixed": 1, "split": 2}
+
+    def set_orth(self, mode="fixed"):
+        """Gram-Schmidt arithmetic of FGMRES (fmp_set_orth): "float64",
+        "fixed" (exact fixed-point products on kept copies) or "split" (the
+        default: fixed-point products for the oldest vectors of each pass,
+        float64 FMAs for the rest); True / False stand for "fixed" /
+        "float64", and 0, 1, 2 for the three."""
+        if isinstance(mode, bool):
+            mode = int(mode)
+        elif isinstance(mode, str):
+            mode = self.ORTH_MODES[mode]
+        _check(lib().fmp_set_orth(self._h, int(mode)), "fmp_set_orth")
 
     def get_orth(self):
+        """The Gram-Schmidt mode as its number: 0 float64, 1 fixed, 2 split."""
         v = C.c_int()
         _check(lib().fmp_get_orth(self._h, C.byref(v)), "fmp_get_orth")
-        return bool(v.value)
+        return v.value
 
     def stream_check(self):
         """FMP_OK, or FMP_ERR_CUDA when a wait of the streamed solve ran out

@@ -25,8 +25,10 @@ def _oracle_ops(w):
     wl.small(grid=(24, 24, 24), cuts=((8, 8, 8),) * 3, overlap=2, seed=22, n_eps_boxes=6),
     wl.small(grid=(12, 10, 8), cuts=((3, 3, 3, 3), (2, 8), (8,)), overlap=2, seed=23, n_eps_boxes=3, beta=25.0),
 ], ids=["small", "27boxes", "beta25"])
-def test_fgmres_matches_oracle(w):
+@pytest.mark.parametrize("orth", ["float64", "split"])
+def test_fgmres_matches_oracle(w, orth):
     ctx = context(w, rtol=1e-10)
+    ctx.set_orth(orth)
     x, info = ctx.krylov_solve(dev(w.rhs))
     x = host(x)
     ee, A, M = _oracle_ops(w)
@@ -145,19 +147,23 @@ def test_grid256_solve_matches_the_oracle_run():
     ctx.close()
 
 
-def test_fixed_point_orthogonalisation_agrees_with_float64():
-    """The Gram-Schmidt passes in exact fixed point (fmp_set_orth(1)) against
-    the float64 FMA passes (the default) on the 128^3 workload: the same
+@pytest.mark.parametrize("mode", ["fixed", "split"])
+def test_fixed_point_orthogonalisation_agrees_with_float64(mode):
+    """The Gram-Schmidt passes in exact fixed point (fmp_set_orth(1)), and
+    split between fixed-point and float64 products (fmp_set_orth(2), the
+    default), against the float64 FMA passes on the 128^3 workload: the same
     iteration count, the same true residual to 1e-6 relative and solutions
-    within 1e-10 of each other (both are rounded float64 Arnoldi processes of
-    the same Krylov space; the fixed-point one has exact products and sums)."""
+    within 1e-10 of each other (all are rounded float64 Arnoldi processes of
+    the same Krylov space; the fixed-point products and sums are exact)."""
     from tests._gpu import rel2
     w = wl.grid128()
     ctx = context(w)
-    assert not ctx.get_orth()
+    assert ctx.get_orth() == ctx.ORTH_MODES["split"]
+    ctx.set_orth("float64")
+    assert ctx.get_orth() == 0
     x0, i0 = ctx.krylov_solve(dev(w.rhs))
-    ctx.set_orth(True)
-    assert ctx.get_orth()
+    ctx.set_orth(mode)
+    assert ctx.get_orth() == ctx.ORTH_MODES[mode]
     x1, i1 = ctx.krylov_solve(dev(w.rhs))
     assert i1["iters"] == i0["iters"]
     assert i1["true_rel_res"] == pytest.approx(i0["true_rel_res"], rel=1e-6)
