@@ -633,7 +633,10 @@ int fmp_setup(fmp_ctx** out, fmp_grid g, const double* eps_cell, double beta, co
     long long big = 0;
     for (const FmpBox& b : boxes) big = std::max(big, 3LL * b.m[0] * b.m[1] * b.m[2]);
     SETUP_CK(cudaMalloc(&c->d_scratch1, sizeof(double) * (size_t)big));
-    SETUP_CK(cudaMalloc(&c->d_partials, sizeof(double) * 148 * 8 * 40));
+    {   // reduction partials: the vector kernels' blocks, or two per CTA of an operator apply
+        const size_t np = std::max<size_t>((size_t)148 * 8 * 40, 2 * (size_t)fmp_curlcurl_ctas(c->nx, c->ny, c->nz));
+        SETUP_CK(cudaMalloc(&c->d_partials, sizeof(double) * np));
+    }
     SETUP_CK(cudaMalloc(&c->d_ticket, sizeof(unsigned int) * 4));
     SETUP_CK(cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned int) * 4, c->stream));
     SETUP_CK(cudaMalloc(&c->d_tmp, sizeof(double) * c->n_slots));

@@ -291,12 +291,24 @@ cudaError_t fmp_launch_transform_solve_fp64(const FmpPlan& p, const double* tabs
                                             const double* r, double* z, double* scratch, int nx, int ny, int nz,
                                             double beta, cudaStream_t s, const double* gate);
 cudaError_t fmp_stencil_init();   // kernel attributes of the operator apply
-// y = s_b * b + c_eps * eps o x + c_k * K x  (b may be null); with ymax, the
-// largest |y| (sign-cleared high word) is raised into *ymax (atomicMax)
+// Optional epilogues of the operator apply (the form c_eps = 1, no b): ymax
+// raises the largest |y| (sign-cleared high word) into *ymax (atomicMax); out
+// receives <a, y> (and <y, y> in out[1] with with_yy), reduced through
+// partials (2 doubles per CTA, fmp_curlcurl_ctas) and a zeroed ticket.
+struct CcEpilogue {
+    unsigned* ymax = nullptr;
+    const double* a = nullptr;
+    double* out = nullptr;
+    bool with_yy = false;
+    double* partials = nullptr;
+    unsigned* ticket = nullptr;
+};
+// y = s_b * b + c_eps * eps o x + c_k * K x  (b may be null)
 cudaError_t fmp_launch_curlcurl(const double* x, const double* eps, double* y, double c_eps,
                                 double c_k, int nx, int ny, int nz, cudaStream_t s,
                                 const double* gate, const double* b = nullptr, double s_b = 0.0,
-                                unsigned* ymax = nullptr);
+                                const CcEpilogue& ep = CcEpilogue());
+long long fmp_curlcurl_ctas(int nx, int ny, int nz);   // CTAs of one operator apply
 cudaError_t fmp_launch_cn_rhs(const double* E, const double* H, const double* J,
                               const double* eps, double beta, double dt, double* R, int nx,
                               int ny, int nz, cudaStream_t s);

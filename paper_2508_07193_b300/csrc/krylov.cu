@@ -1159,8 +1159,10 @@ int arnoldi_step(fmp_ctx* c, int j, fmp_solve_info* inf) {
         unsigned* wmax = (fixed || (split && split_dots(nv) > 0)) ? c->d_vmax + R + 1 : nullptr;
         if (wmax) FMP_CK(cudaMemsetAsync(wmax, 0, sizeof(unsigned), s));
         ++c->launches;
+        CcEpilogue ep;
+        ep.ymax = wmax;
         FMP_CK(fmp_launch_curlcurl(zj, c->d_eps_edge, w, 1.0, c->beta, c->nx, c->ny, c->nz, s, gate, nullptr, 0.0,
-                                   wmax));
+                                   ep));
     }
     {
         Timer tm(c, &inf->ms_orth, "orth");
@@ -1375,13 +1377,6 @@ int bicg_iteration(fmp_ctx* c, fmp_solve_info* inf) {
     const double* gate = sc + SC_DONE;
     double *r = c->d_V, *rh = r + ld, *p = rh + ld, *v = p + ld, *sv = v + ld, *t = sv + ld, *ph = t + ld,
            *sh = ph + ld, *xi = sh + ld;
-    auto dots = [&](const double* a0, const double* b0, const double* a1 = nullptr, const double* b1 = nullptr) {
-        Pairs pr{};
-        pr.a[0] = a0; pr.b[0] = b0; pr.n = 1;
-        if (a1) { pr.a[1] = a1; pr.b[1] = b1; pr.n = 2; }
-        ++c->launches;
-        launch_pairdots(pr, n, sc + SC_D0, c->d_partials, c->d_ticket, grid_n(n), s, gate);
-    };
     ++c->launches;
     k_bicg_p<<<grid_n(n), kT, 0, s>>>(p, r, v, n, sc);
     {
@@ -1389,12 +1384,17 @@ int bicg_iteration(fmp_ctx* c, fmp_solve_info* inf) {
         int rc = fmp_precond_gated(c, p, ph, gate);
         if (rc != FMP_OK) return rc;
     }
-    {
+    {   // v = A phat with <rhat, v> in its epilogue
         Timer tm(c, &inf->ms_spmv, "matvec");
         ++c->launches;
-        FMP_CK(fmp_launch_curlcurl(ph, c->d_eps_edge, v, 1.0, c->beta, c->nx, c->ny, c->nz, s, gate));
+        CcEpilogue ep;
+        ep.a = rh;
+        ep.out = sc + SC_D0;
+        ep.partials = c->d_partials;
+        ep.ticket = c->d_ticket + 1;
+        FMP_CK(fmp_launch_curlcurl(ph, c->d_eps_edge, v, 1.0, c->beta, c->nx, c->ny, c->nz, s, gate, nullptr, 0.0,
+                                   ep));
     }
-    dots(rh, v);
     ++c->launches;
     k_bicg_s<<<grid_n(n), kT, 0, s>>>(sv, r, v, n, sc);
     {
@@ -1402,12 +1402,18 @@ int bicg_iteration(fmp_ctx* c, fmp_solve_info* inf) {
         int rc = fmp_precond_gated(c, sv, sh, gate);
         if (rc != FMP_OK) return rc;
     }
-    {
+    {   // t = A shat with <s, t> and <t, t> in its epilogue
         Timer tm(c, &inf->ms_spmv, "matvec");
         ++c->launches;
-        FMP_CK(fmp_launch_curlcurl(sh, c->d_eps_edge, t, 1.0, c->beta, c->nx, c->ny, c->nz, s, gate));
+        CcEpilogue ep;
+        ep.a = sv;
+        ep.out = sc + SC_D0;
+        ep.with_yy = true;
+        ep.partials = c->d_partials;
+        ep.ticket = c->d_ticket + 1;
+        FMP_CK(fmp_launch_curlcurl(sh, c->d_eps_edge, t, 1.0, c->beta, c->nx, c->ny, c->nz, s, gate, nullptr, 0.0,
+                                   ep));
     }
-    dots(t, sv, t, t);
     ++c->launches;
     k_bicg_xr<<<grid_n(n), kT, 0, s>>>(xi, r, ph, sh, sv, t, rh, n, sc, c->d_partials, c->d_ticket);
     FMP_CK(cudaGetLastError());

@@ -136,6 +136,10 @@ constexpr int PX = TX + 2, PY = TY + 2, PLANE = 3 * PX * PY;   // E tile with ha
 constexpr int FX = TX + 1, FY = TY + 1, FPLANE = 3 * FX * FY;  // faces, low halo
 
 __device__ __forceinline__ unsigned abs_hi(double v) { return (unsigned)__double2hiint(v) & 0x7FFFFFFFu; }
+__device__ __forceinline__ double warp_sum_d(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 
 // FORM selects the epilogue, so that the solver's forms spend no float64
 // operation on a factor of one: 0 any (c_eps, c_k, s_b, b); 1 the operator
@@ -206,11 +210,15 @@ __device__ __forceinline__ double from_fixed(long long K, int emax) {
 // blocks of two planes converted with their two halo planes each: about 550
 // thread instructions per cell instead of 650 (ncu), 0.059 -> 0.057 ms at
 // 128^3, 0.417 -> 0.373 ms at 256^3.
-template <int FORM, bool YMAX>
+// EPI selects an epilogue over the outputs: 0 none; 1 the largest |y| (high
+// words) into *ep.ymax; 2 <a, y> into ep.out[0]; 3 <a, y> and <y, y> into
+// ep.out[0], ep.out[1] (per-CTA partial sums, added in CTA order by the last
+// CTA to finish: deterministic).
+template <int FORM, int EPI>
 __global__ void __launch_bounds__(TX * TY, 4)
 k_curlcurl_zm(const double* __restrict__ x, const double* __restrict__ eps, double* __restrict__ y,
               const double* __restrict__ b, double s_b, double c_eps, double c_k, Dims d, int kz,
-              const double* __restrict__ gate, unsigned* __restrict__ ymax) {
+              const double* __restrict__ gate, CcEpilogue ep) {
     if (gate && *gate != 0.0) return;
     constexpr int NQ = (PLANE + TX * TY - 1) / (TX * TY);   // E slots per thread and plane (4)
     constexpr int NFQ = (FPLANE / 3 + TX * TY - 1) / (TX * TY);   // face slots per thread, per component (2)
@@ -306,6 +314,7 @@ k_curlcurl_zm(const double* __restrict__ x, const double* __restrict__ eps, doub
     const bool live = gi < d.nx && gj < d.ny;
     const int fo = (ty + 1) * FX + tx + 1;
     unsigned mx = 0u;
+    double da = 0.0, dy = 0.0;
     for (int k = k0; k < k1; ++k) {
         // va holds plane k + 1; its exponent joins the running maximum
         exponent(va, k + 1);
@@ -352,12 +361,48 @@ k_curlcurl_zm(const double* __restrict__ x, const double* __restrict__ eps, doub
             y[o] = vx;
             y[d.comp + o] = vy;
             y[2 * d.comp + o] = vz;
-            if constexpr (YMAX) mx = max(mx, max(abs_hi(vx), max(abs_hi(vy), abs_hi(vz))));
+            if constexpr (EPI == 1) mx = max(mx, max(abs_hi(vx), max(abs_hi(vy), abs_hi(vz))));
+            if constexpr (EPI >= 2) {
+                da = fma(__ldg(ep.a + o), vx, da);
+                da = fma(__ldg(ep.a + d.comp + o), vy, da);
+                da = fma(__ldg(ep.a + 2 * d.comp + o), vz, da);
+            }
+            if constexpr (EPI == 3) dy = fma(vx, vx, fma(vy, vy, fma(vz, vz, dy)));
         }
     }
-    if constexpr (YMAX) {   // the largest |y| (sign-cleared high words) into *ymax
+    if constexpr (EPI == 1) {   // the largest |y| (sign-cleared high words) into *ymax
         mx = __reduce_max_sync(0xffffffffu, mx);
-        if ((threadIdx.x & 31) == 0 && mx != 0u) atomicMax(ymax, mx);
+        if ((threadIdx.x & 31) == 0 && mx != 0u) atomicMax(ep.ymax, mx);
+    }
+    if constexpr (EPI >= 2) {
+        constexpr int ND = EPI == 3 ? 2 : 1;
+        __shared__ double red[2][TX * TY / 32];
+        __shared__ bool last;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const double w0 = warp_sum_d(da), w1 = warp_sum_d(dy);
+        if (lane == 0) { red[0][warp] = w0; red[1][warp] = w1; }
+        __syncthreads();
+        const unsigned cta = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+        const unsigned ncta = gridDim.x * gridDim.y * gridDim.z;
+        if (threadIdx.x < ND) {
+            double sum = 0.0;
+            for (int q = 0; q < TX * TY / 32; ++q) sum += red[threadIdx.x][q];
+            ep.partials[2 * (size_t)cta + threadIdx.x] = sum;
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) last = atomicAdd(ep.ticket, 1u) == ncta - 1;
+        __syncthreads();
+        if (last) {
+            __threadfence();
+            if (warp < ND) {
+                double sum = 0.0;
+                for (unsigned q = lane; q < ncta; q += 32) sum += __ldcg(ep.partials + 2 * (size_t)q + warp);
+                sum = warp_sum_d(sum);
+                if (lane == 0) ep.out[warp] = sum;
+            }
+            if (threadIdx.x == 0) *ep.ticket = 0u;
+        }
     }
 }
 
@@ -467,21 +512,33 @@ cudaError_t fmp_stencil_init() { return cudaSuccess; }
 // 16; 16 best at 256^3, 0.373 ms against 0.384 with 8 and 0.382 with 48).
 int zm_planes(int nz) { return std::max(8, std::min(16, nz / 16)); }
 
+long long fmp_curlcurl_ctas(int nx, int ny, int nz) {
+    const int kz = zm_planes(nz);
+    return (long long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY) * ((nz + kz - 1) / kz);
+}
+
 cudaError_t fmp_launch_curlcurl(const double* x, const double* eps, double* y, double c_eps, double c_k, int nx,
                                 int ny, int nz, cudaStream_t s, const double* gate, const double* b, double s_b,
-                                unsigned* ymax) {
+                                const CcEpilogue& ep) {
     const int kz = zm_planes(nz);
     const dim3 g((nx + TX - 1) / TX, (ny + TY - 1) / TY, (nz + kz - 1) / kz);
     const Dims d = dims(nx, ny, nz);
-    if (ymax) {
-        if (c_eps != 1.0 || b) return cudaErrorInvalidValue;   // the Arnoldi step's form only
-        k_curlcurl_zm<1, true><<<g, TX * TY, 0, s>>>(x, eps, y, b, s_b, c_eps, c_k, d, kz, gate, ymax);
+    const int epi = ep.ymax ? 1 : ep.out ? (ep.with_yy ? 3 : 2) : 0;
+    if (epi) {   // the Krylov solvers' operator form only
+        if (c_eps != 1.0 || b) return cudaErrorInvalidValue;
+        if (epi >= 2 && (!ep.a || !ep.partials || !ep.ticket)) return cudaErrorInvalidValue;
+        if (epi == 1)
+            k_curlcurl_zm<1, 1><<<g, TX * TY, 0, s>>>(x, eps, y, b, s_b, c_eps, c_k, d, kz, gate, ep);
+        else if (epi == 2)
+            k_curlcurl_zm<1, 2><<<g, TX * TY, 0, s>>>(x, eps, y, b, s_b, c_eps, c_k, d, kz, gate, ep);
+        else
+            k_curlcurl_zm<1, 3><<<g, TX * TY, 0, s>>>(x, eps, y, b, s_b, c_eps, c_k, d, kz, gate, ep);
     } else if (c_eps == 1.0 && !b) {
-        k_curlcurl_zm<1, false><<<g, TX * TY, 0, s>>>(x, eps, y, b, s_b, c_eps, c_k, d, kz, gate, nullptr);
+        k_curlcurl_zm<1, 0><<<g, TX * TY, 0, s>>>(x, eps, y, b, s_b, c_eps, c_k, d, kz, gate, ep);
     } else if (c_eps == -1.0 && b && s_b == 1.0) {
-        k_curlcurl_zm<2, false><<<g, TX * TY, 0, s>>>(x, eps, y, b, s_b, c_eps, c_k, d, kz, gate, nullptr);
+        k_curlcurl_zm<2, 0><<<g, TX * TY, 0, s>>>(x, eps, y, b, s_b, c_eps, c_k, d, kz, gate, ep);
     } else {
-        k_curlcurl_zm<0, false><<<g, TX * TY, 0, s>>>(x, eps, y, b, s_b, c_eps, c_k, d, kz, gate, nullptr);
+        k_curlcurl_zm<0, 0><<<g, TX * TY, 0, s>>>(x, eps, y, b, s_b, c_eps, c_k, d, kz, gate, ep);
     }
     return cudaGetLastError();
 }
