@@ -50,6 +50,25 @@ def test_fgmres_restart_and_initial_guess():
     assert info["restarts"] >= 2 and info["true_rel_res"] <= 1e-9
 
 
+@pytest.mark.parametrize("orth", ["split", "float64", "fixed"])
+def test_fgmres_longest_restart(orth):
+    """FGMRES(32), the longest restart (basis passes over up to 32 vectors;
+    the split passes then hold six vectors in fixed point), in each
+    Gram-Schmidt mode, on a workload that needs more than one cycle: the true
+    residual recomputed with the oracle's operator reaches the tolerance."""
+    w = wl.small(grid=(24, 20, 16), cuts=((8, 8, 8), (10, 10), (16,)), overlap=2, seed=31, n_eps_boxes=5,
+                 beta=25.0)
+    ctx = context(w, restart=32, rtol=1e-11)
+    ctx.set_orth(orth)
+    x, info = ctx.krylov_solve(dev(w.rhs))
+    ee, A, M = _oracle_ops(w)
+    b = w.rhs.reshape(-1)
+    true = np.linalg.norm(b - A @ host(x).reshape(-1)) / np.linalg.norm(b)
+    assert info["restarts"] >= 2 and info["iters"] > 32
+    assert true <= 1e-11 and info["true_rel_res"] == pytest.approx(true, rel=1e-6, abs=1e-14)
+    ctx.close()
+
+
 def test_max_iters_reports_not_converged():
     from paper_2508_07193_b300 import flashmp as F
     w = wl.small()
