@@ -221,6 +221,7 @@ cudaError_t make_plan(FmpPlan& p, const std::vector<FmpBox>& boxes, cudaStream_t
     std::vector<int4> A, C;
     std::vector<int2> B;
     build_items(boxes, fmp_column_tile_fp64(p.max_m), A, B, C);
+    fmp_fp64_classes(p, boxes, A, B, C);
     p.n_items_a = (int)A.size(); p.n_items_b = (int)B.size(); p.n_items_c = (int)C.size();
     cudaError_t e;
     if ((e = upload(&p.d_boxes, boxes, s))) return e;

@@ -30,6 +30,9 @@
 // loops with lanes idle in each.
 #include "fmp_internal.h"
 
+#include <algorithm>
+#include <utility>
+
 namespace {
 
 constexpr int kThreads = 256;
@@ -750,7 +753,64 @@ size_t smem_b(const FmpPlan& p) {
     return sizeof(double) * (6 * p.max_m[2] * CT + 2 * p.max_room + (p.max_m[2] / 2) * CT);
 }
 
+// Shared memory one box needs in each pass (the layouts of the kernels above,
+// sized by the box's own extents).
+size_t need_ac(const FmpBox& b) {
+    return sizeof(double) * (3 * (size_t)b.m[0] * b.m[1] + fold3_room(b.m[0]) + fold3_room(b.m[1]));
+}
+template <int CT>
+size_t need_b(const FmpBox& b) {
+    return sizeof(double) * (6 * (size_t)b.m[2] * CT + 2 * fold3_room(b.m[2]) + (b.m[2] / 2) * CT);
+}
+
+// CTAs per SM that a CTA's shared memory allows, at most the launch bounds' 6.
+int ctas_for(size_t smem) {
+    static int per_sm = -1, reserved = 0;
+    if (per_sm < 0) {
+        int dev = 0, v = 0;
+        per_sm = 233472;   // 228 KB unless the device says otherwise
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess && v > 0)
+            per_sm = v;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess) reserved = v;
+        cudaGetLastError();
+    }
+    const long long k = per_sm / (long long)(smem + reserved);
+    return (int)std::max(1LL, std::min(6LL, k));
+}
+
+// Stable order by resident-CTA count (most first); one class per run.
+template <class Item, class Need>
+void classify(std::vector<Item>& v, const std::vector<FmpBox>& boxes, Need need, FmpLaunchClass* cls, int& ncls) {
+    std::vector<std::pair<int, Item>> keyed;
+    keyed.reserve(v.size());
+    for (const Item& it : v) keyed.push_back({ctas_for(need(boxes[it.x])), it});
+    std::stable_sort(keyed.begin(), keyed.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    ncls = 0;
+    for (size_t i = 0; i < keyed.size(); ++i) {
+        v[i] = keyed[i].second;
+        if (i == 0 || keyed[i].first != keyed[i - 1].first) {
+            cls[ncls] = FmpLaunchClass();
+            cls[ncls].first = (int)i;
+            ++ncls;
+        }
+        FmpLaunchClass& c = cls[ncls - 1];
+        ++c.count;
+        c.smem = std::max(c.smem, need(boxes[keyed[i].second.x]));
+    }
+}
+
 }  // namespace
+
+void fmp_fp64_classes(FmpPlan& p, const std::vector<FmpBox>& boxes, std::vector<int4>& A, std::vector<int2>& B,
+                      std::vector<int4>& C) {
+    classify(A, boxes, need_ac, p.cls_a, p.n_cls_a);
+    if (fmp_column_tile_fp64(p.max_m) == 32)
+        classify(B, boxes, need_b<32>, p.cls_b, p.n_cls_b);
+    else
+        classify(B, boxes, need_b<16>, p.cls_b, p.n_cls_b);
+    classify(C, boxes, need_ac, p.cls_c, p.n_cls_c);
+}
 
 // Opt the three kernels into the dynamic shared memory the plan needs (at
 // set-up, outside any stream capture).
@@ -770,15 +830,29 @@ cudaError_t fmp_transform_init_fp64(const FmpPlan& p) {
 cudaError_t fmp_launch_transform_solve_fp64(const FmpPlan& p, const double* tabs, const double* modeinv,
                                             const double* r, double* z, double* scratch, int nx, int ny, int nz,
                                             double beta, cudaStream_t s, const double* gate) {
-    const size_t sa = smem_a(p), sc = smem_c(p);
+    // one launch per class of boxes with the same resident-CTA count: a box of
+    // 68 x 68 cells per slab would otherwise hold every CTA of the pass to one
+    // per SM
     const bool wide = fmp_column_tile_fp64(p.max_m) == 32;
-    const size_t sb = wide ? smem_b<32>(p) : smem_b<16>(p);
-    k_fwd_xy<<<p.n_items_a, kThreads, sa, s>>>(r, scratch, p.d_boxes, p.d_items_a, tabs, nx, ny, nz, gate);
-    if (wide)
-        k_z_solve<32><<<p.n_items_b, kThreads, sb, s>>>(scratch, p.d_boxes, p.d_items_b, tabs, modeinv, beta, gate);
-    else
-        k_z_solve<16><<<p.n_items_b, kThreads, sb, s>>>(scratch, p.d_boxes, p.d_items_b, tabs, modeinv, beta, gate);
-    k_inv_xy<<<p.n_items_c, kThreads, sc, s>>>(scratch, z, p.d_boxes, p.d_items_c, tabs, nx, ny, nz, gate);
+    for (int i = 0; i < p.n_cls_a; ++i) {
+        const FmpLaunchClass& k = p.cls_a[i];
+        k_fwd_xy<<<k.count, kThreads, k.smem, s>>>(r, scratch, p.d_boxes, p.d_items_a + k.first, tabs, nx, ny, nz,
+                                                   gate);
+    }
+    for (int i = 0; i < p.n_cls_b; ++i) {
+        const FmpLaunchClass& k = p.cls_b[i];
+        if (wide)
+            k_z_solve<32><<<k.count, kThreads, k.smem, s>>>(scratch, p.d_boxes, p.d_items_b + k.first, tabs, modeinv,
+                                                            beta, gate);
+        else
+            k_z_solve<16><<<k.count, kThreads, k.smem, s>>>(scratch, p.d_boxes, p.d_items_b + k.first, tabs, modeinv,
+                                                            beta, gate);
+    }
+    for (int i = 0; i < p.n_cls_c; ++i) {
+        const FmpLaunchClass& k = p.cls_c[i];
+        k_inv_xy<<<k.count, kThreads, k.smem, s>>>(scratch, z, p.d_boxes, p.d_items_c + k.first, tabs, nx, ny, nz,
+                                                   gate);
+    }
     return cudaGetLastError();
 }
 

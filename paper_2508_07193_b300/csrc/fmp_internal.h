@@ -158,6 +158,14 @@ struct FmpStreamBox {
     int need_b;
 };
 
+// One launch of a float64 pass: items [first, first + count) of its list,
+// whose boxes need at most smem bytes of shared memory.
+struct FmpLaunchClass {
+    int first = 0, count = 0;
+    size_t smem = 0;
+};
+constexpr int kFp64Classes = 6;   // one per resident-CTA count 1..6
+
 // Launch-shape description of one batched transform solve (the three passes).
 struct FmpPlan {
     FmpBox* d_boxes = nullptr;  // device array of boxes
@@ -168,6 +176,10 @@ struct FmpPlan {
     int n_items_b = 0;
     int4* d_items_c = nullptr;  // (box, comp, owned slab, 0): inverse y/x
     int n_items_c = 0;
+    // the float64 lists ordered by the shared memory their boxes need, one
+    // launch per run of items with the same resident-CTA count
+    FmpLaunchClass cls_a[kFp64Classes], cls_b[kFp64Classes], cls_c[kFp64Classes];
+    int n_cls_a = 0, n_cls_b = 0, n_cls_c = 0;
     // grouped work lists of the reduced-precision passes (tables staged once
     // per CTA): (box, comp, first slab, slabs) for A and C, (box, first
     // column, columns, 0) for B
@@ -287,6 +299,10 @@ cudaError_t fmp_launch_eps_bar(const double* eps_edge, FmpBox* d_boxes, int n_bo
 cudaError_t fmp_transform_init_fp64(const FmpPlan& p);
 int fmp_column_tile(const int* max_m);        // column tile of the reduced-precision pass B
 int fmp_column_tile_fp64(const int* max_m);   // column tile of the float64 pass B
+// Orders the float64 passes' lists A, B, C by their boxes' shared-memory
+// needs and records the launch classes in p.
+void fmp_fp64_classes(FmpPlan& p, const std::vector<FmpBox>& boxes, std::vector<int4>& A, std::vector<int2>& B,
+                      std::vector<int4>& C);
 cudaError_t fmp_launch_transform_solve_fp64(const FmpPlan& p, const double* tabs, const double* modeinv,
                                             const double* r, double* z, double* scratch, int nx, int ny, int nz,
                                             double beta, cudaStream_t s, const double* gate);

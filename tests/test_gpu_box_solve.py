@@ -96,3 +96,26 @@ def test_precond_128_sampled_boxes():
         (x0, y0, z0), (x1, y1, z1) = b.own_lo, b.own_hi
         sl = (slice(None), slice(z0, z1), slice(y0, y1), slice(x0, x1))
         assert rel(z[sl], part[sl]) <= FP64_TOL
+
+
+def test_precond_uneven_sampled_boxes_per_size_class():
+    """The uneven 320 x 256 x 192 workload (extents 28-68) in float64: its
+    boxes run in several launches of each pass, grouped by the shared memory
+    they need. Owned blocks of the smallest, the largest and two more boxes
+    against the oracle one by one."""
+    w = wl.grid_uneven()
+    ctx = context(w)
+    z = host(ctx.precond_apply(dev(w.rhs)))
+    ee = yee.edge_eps(w.grid, w.eps_cell)
+    boxes = ras.partition(w.grid, w.cuts, w.overlap)
+    size = lambda i: np.prod([boxes[i].ext_hi[a] - boxes[i].ext_lo[a] for a in range(3)])
+    picks = {min(range(len(boxes)), key=size), max(range(len(boxes)), key=size), 0, len(boxes) // 2}
+    for i in sorted(picks):
+        b = boxes[i]
+        eb = box.exact_solve(ras.restrict(w.rhs, b), ras.eps_bar(ee, b), w.beta)
+        part = np.zeros_like(w.rhs)
+        ras.prolong_owned(part, eb, b)
+        (x0, y0, z0), (x1, y1, z1) = b.own_lo, b.own_hi
+        sl = (slice(None), slice(z0, z1), slice(y0, y1), slice(x0, x1))
+        assert rel(z[sl], part[sl]) <= FP64_TOL
+    ctx.close()
