@@ -296,7 +296,6 @@ __global__ void k_symmetrize_lower(double* __restrict__ C, int n) {
     }
 }
 
-size_t smem_xy(int mx, int my) { return sizeof(double) * (2 * mx * my + mx * mx + my * my); }
 size_t smem_z(int mz) { return sizeof(double) * (6 * mz * kColTile + 4 * mz * mz); }
 
 // Tables of one extent m: forward V^T, forward U^T, inverse V, inverse U (each
