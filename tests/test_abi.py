@@ -76,3 +76,19 @@ def test_setup_rejects_bad_arguments_before_touching_the_device(so):
     assert L.fmp_set_streamed(None, 1) == F.FMP_ERR_ARG
     assert L.fmp_stream_check(None) == F.FMP_ERR_ARG
     L.fmp_destroy(None)
+
+
+def test_orth_modes_match_the_header(so):
+    """The binding's Gram-Schmidt mode names carry the values of the header's
+    fmp_orth_mode; a null context is refused for every mode."""
+    from paper_2508_07193_b300 import flashmp as F
+    text = open(HEADER).read()
+    m = re.search(r"enum fmp_orth_mode \{([^}]*)\}", text)
+    vals = {k: int(v) for k, v in re.findall(r"FMP_ORTH_(\w+) = (\d+)", m.group(1))}
+    assert vals == {"FLOAT64": 0, "FIXED": 1, "SPLIT": 2}
+    assert F.Context.ORTH_MODES == {k.lower(): v for k, v in vals.items()}
+    L = F.lib()
+    for v in vals.values():
+        assert L.fmp_set_orth(None, v) == F.FMP_ERR_ARG
+    out = C.c_int()
+    assert L.fmp_get_orth(None, C.byref(out)) == F.FMP_ERR_ARG
