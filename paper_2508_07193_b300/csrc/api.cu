@@ -565,6 +565,11 @@ int fmp_setup(fmp_ctx** out, fmp_grid g, const double* eps_cell, double beta, co
         b.inv_off = scr / 3;
         scr += 3LL * b.m[0] * b.m[1] * b.m[2];
     }
+    long long n_modeinv = scr / 3;   // then the scaled singular values of every box
+    for (FmpBox& b : boxes) {
+        b.sigs_off = n_modeinv;
+        n_modeinv += b.m[0] + b.m[1] + b.m[2];
+    }
     cudaError_t e;
 #define SETUP_CK(x) do { if ((e = (x)) != cudaSuccess) { (void)cudaGetLastError(); \
         return fail(e == cudaErrorMemoryAllocation ? FMP_ERR_NOMEM : FMP_ERR_CUDA); } } while (0)
@@ -616,8 +621,9 @@ int fmp_setup(fmp_ctx** out, fmp_grid g, const double* eps_cell, double beta, co
     SETUP_CK(cudaStreamSynchronize(c->stream));
     c->h_boxes = boxes;
     {   // per box and mode: 1 / (eps_bar + beta |sigma|^2), the diagonal factor of the
-        // closed-form 3x3 inverse (Eq. 12), used by the float64 pass B
-        std::vector<double> inv((size_t)(c->ras.scratch_doubles / 3));
+        // closed-form 3x3 inverse (Eq. 12); then per box s sigma_a with s = sqrt(beta /
+        // eps_bar), so that pass B forms e = inv (r + (s sigma . r) s sigma)
+        std::vector<double> inv((size_t)n_modeinv);
         for (const FmpBox& b : boxes) {
             const double* sx = tabs.data() + b.sig_off[0];
             const double* sy = tabs.data() + b.sig_off[1];
@@ -627,6 +633,10 @@ int fmp_setup(fmp_ctx** out, fmp_grid g, const double* eps_cell, double beta, co
                 for (int ky = 0; ky < b.m[1]; ++ky)
                     for (int kx = 0; kx < b.m[0]; ++kx)
                         *o++ = 1.0 / (b.eps_bar + beta * (sx[kx] * sx[kx] + sy[ky] * sy[ky] + sz[kz] * sz[kz]));
+            const double sc = std::sqrt(beta / b.eps_bar);
+            double* q = inv.data() + b.sigs_off;
+            for (int a = 0; a < 3; ++a)
+                for (int k = 0; k < b.m[a]; ++k) *q++ = sc * tabs[b.sig_off[a] + k];
         }
         SETUP_CK(upload(&c->d_modeinv, inv, c->stream));
     }

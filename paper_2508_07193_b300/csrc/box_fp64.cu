@@ -23,7 +23,8 @@
 // extents) from the class products. About 3/8 m^2 FMAs per line of an even
 // extent instead of m^2. The 3x3 block B = eps_bar I + beta(|s|^2 I - s s^T) is
 // inverted by Sherman-Morrison: B^{-1} r = (r + (beta/eps_bar) s (s.r)) /
-// (eps_bar + beta |s|^2), the denominator read from a per-box mode table.
+// (eps_bar + beta |s|^2), the reciprocal of the denominator and the scaled
+// sqrt(beta/eps_bar) s read from per-box tables.
 //
 // These kernels are bound by the float64 pipe (1/64 of the fp32 rate on this
 // part). Work indices run class by class, so a warp never executes two classes'
@@ -450,8 +451,7 @@ k_fwd_xy(const double* __restrict__ r, double* __restrict__ scr, const FmpBox* _
 template <int CT>
 __global__ void __launch_bounds__(kThreads, 6)
 k_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int2* __restrict__ items,
-          const double* __restrict__ tabs, const double* __restrict__ modeinv, double beta,
-          const double* __restrict__ gate) {
+          const double* __restrict__ tabs, const double* __restrict__ modeinv, const double* __restrict__ gate) {
     if (gate && *gate != 0.0) return;
     extern __shared__ double sm[];
     const int2 it = items[blockIdx.x];
@@ -555,12 +555,13 @@ k_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int2
         for (int col = threadIdx.x; col < CT; col += blockDim.x) f3_recur(Buf + (2 * mz + 1) * CT + col, N, 2 * CT);
         __syncthreads();
     }
-    const double* sgx = tabs + B.sig_off[0];
-    const double* sgy = tabs + B.sig_off[1];
-    const double* sgz = tabs + B.sig_off[2];
-    // e_c = inv (r_c + (beta / eps_bar) sigma_c (sigma . r)), inv = 1 / (eps_bar
-    // + beta |sigma|^2) read from the per-box mode table
-    const double beb = beta / B.eps_bar;
+    // e_c = inv (r_c + (beta / eps_bar) sigma_c (sigma . r)) = inv (r_c + a s_c)
+    // with s = sqrt(beta / eps_bar) sigma and a = s . r (nine float64
+    // operations a mode); inv = 1 / (eps_bar + beta |sigma|^2) and s from the
+    // per-box tables
+    const double* sgx = modeinv + B.sigs_off;
+    const double* sgy = sgx + mx;
+    const double* sgz = sgy + my;
     const double* inv_tab = modeinv + B.inv_off + col0;
     for (int t = threadIdx.x; t < mz * CT; t += blockDim.x) {
         const int kz = t / CT, col = t - kz * CT;
@@ -571,11 +572,10 @@ k_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int2
         double* o = Buf + kz * CT + col;
         const double r0 = o[0], r1 = o[mz * CT], r2 = o[2 * mz * CT];
         const double inv = inv_tab[(long long)kz * nxy + col];
-        const double sr = fma(sx, r0, fma(sy, r1, sz * r2));
-        const double f = (beb * inv) * sr;
-        o[0] = fma(f, sx, inv * r0);
-        o[mz * CT] = fma(f, sy, inv * r1);
-        o[2 * mz * CT] = fma(f, sz, inv * r2);
+        const double a = fma(sx, r0, fma(sy, r1, sz * r2));
+        o[0] = inv * fma(a, sx, r0);
+        o[mz * CT] = inv * fma(a, sy, r1);
+        o[2 * mz * CT] = inv * fma(a, sz, r2);
     }
     __syncthreads();
     // the third level's class-2 contributions G[c][q][col], q < N: the inner
@@ -843,10 +843,10 @@ cudaError_t fmp_launch_transform_solve_fp64(const FmpPlan& p, const double* tabs
         const FmpLaunchClass& k = p.cls_b[i];
         if (wide)
             k_z_solve<32><<<k.count, kThreads, k.smem, s>>>(scratch, p.d_boxes, p.d_items_b + k.first, tabs, modeinv,
-                                                            beta, gate);
+                                                            gate);
         else
             k_z_solve<16><<<k.count, kThreads, k.smem, s>>>(scratch, p.d_boxes, p.d_items_b + k.first, tabs, modeinv,
-                                                            beta, gate);
+                                                            gate);
     }
     for (int i = 0; i < p.n_cls_c; ++i) {
         const FmpLaunchClass& k = p.cls_c[i];

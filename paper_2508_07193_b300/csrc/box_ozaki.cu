@@ -380,7 +380,7 @@ template <int M>
 __global__ void __launch_bounds__(kT, Sz<M>::kMinBlocks)
 k_oz_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const int4* __restrict__ items,
              const uint4* __restrict__ otab, const double* __restrict__ tabs, const double* __restrict__ modeinv,
-             double beta, const double* __restrict__ gate) {
+             const double* __restrict__ gate) {
     if (gate && *gate != 0.0) return;
     using SZ = Sz<M>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -399,10 +399,9 @@ k_oz_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const i
     const uint4 *TCf = tb, *TCi = tb + tf, *TSf = tb + 2 * tf, *TSi = tb + 3 * tf;
     const int F = B.oz_F[2];
     const int ps = kLB * LZ;
-    const double* sgx = tabs + B.sig_off[0];
-    const double* sgy = tabs + B.sig_off[1];
-    const double* sgz = tabs + B.sig_off[2];
-    const double beb = beta / B.eps_bar;
+    const double* sgx = modeinv + B.sigs_off;   // sqrt(beta / eps_bar) sigma per axis
+    const double* sgy = sgx + mx;
+    const double* sgz = sgy + my;
     const double* inv_tab = modeinv + B.inv_off;
     double* S = scr + B.scr_off;
     const int oz0 = B.own_lo[2], oz1 = B.own_lo[2] + B.own_n[2];
@@ -437,8 +436,8 @@ k_oz_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const i
                            [&](int l, int kz, double x) { V[l * SZ::kLine + kz] = x; });
         }
         __syncthreads();
-        // e_c = inv (r_c + (beta / eps_bar) sigma_c (sigma . r)), inv = 1 / (eps_bar
-        // + beta |sigma|^2) from the per-box mode table
+        // e_c = inv (r_c + a s_c), s = sqrt(beta / eps_bar) sigma, a = s . r, inv =
+        // 1 / (eps_bar + beta |sigma|^2): both from the per-box tables
         for (int t = threadIdx.x; t < mz * ncol; t += kT) {
             const int kz = t / ncol, col = t - kz * ncol;
             const int q = col0 + col;
@@ -447,9 +446,8 @@ k_oz_z_solve(double* __restrict__ scr, const FmpBox* __restrict__ boxes, const i
             double* o = V + col * SZ::kLine + kz;
             const double r0 = o[0], r1 = o[kCT * SZ::kLine], r2 = o[2 * kCT * SZ::kLine];
             const double inv = inv_tab[(long long)kz * nxy + q];
-            const double sr = fma(sx, r0, fma(sy, r1, sz * r2));
-            const double f = (beb * inv) * sr;
-            const double e0 = fma(f, sx, inv * r0), e1 = fma(f, sy, inv * r1), e2 = fma(f, sz, inv * r2);
+            const double a = fma(sx, r0, fma(sy, r1, sz * r2));
+            const double e0 = inv * fma(a, sx, r0), e1 = inv * fma(a, sy, r1), e2 = inv * fma(a, sz, r2);
             o[0] = e0;
             o[kCT * SZ::kLine] = e1;
             o[2 * kCT * SZ::kLine] = e2;
@@ -621,7 +619,7 @@ void launch_size(const FmpPlan& p, const uint4* otab, const double* tabs, const 
                                                             gate);
     if (p.n_items_ob > 0)
         k_oz_z_solve<M><<<p.n_items_ob, kT, kSmemB<M>, s>>>(scratch, p.d_boxes, p.d_items_ob, otab, tabs, modeinv,
-                                                             beta, gate);
+                                                             gate);
     if (p.n_items_oc > 0)
         k_oz_inv_xy<M><<<p.n_items_oc, kT, kSmemC<M>, s>>>(scratch, z, p.d_boxes, p.d_items_oc, otab, nx, ny, nz,
                                                             gate);

@@ -36,6 +36,7 @@ struct FmpBox {
     int oz_F[3];       // their table exponent: every |T| <= 2^F
     long long scr_off; // offset (doubles) of the box's [3][mz][my][mx] scratch
     long long inv_off; // offset of the box's [mz][my][mx] table 1 / (eps_bar + beta |sigma|^2)
+    long long sigs_off; // offset, in the same array, of sqrt(beta / eps_bar) sigma_a (m_x, m_y, m_z values)
     double eps_bar;    // subdomain-mean edge permittivity
 };
 
@@ -243,7 +244,8 @@ struct fmp_ctx {
     int single_box = -1;          // box index the single plan was built for
     double* d_scratch = nullptr;  // transform scratch for the RAS plan
     double* d_scratch1 = nullptr; // scratch for one box (fmp_box_solve)
-    double* d_modeinv = nullptr;  // per box and mode 1 / (eps_bar + beta |sigma|^2) (float64 pass B)
+    double* d_modeinv = nullptr;  // per box and mode 1 / (eps_bar + beta |sigma|^2), then per box the
+                                  // scaled singular values (float64 and digit-split pass B)
     void* d_tab_mp[3] = {};       // reduced-precision tables: bf16, fp16, tf32 (same layout)
     uint32_t* d_tab_oz = nullptr; // digit-plane tables of the digit-split float64 transforms (fragment order)
     double* d_bscale = nullptr;   // per-box scale factors (fp16 transforms)
