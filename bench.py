@@ -342,7 +342,7 @@ def _box_executed(m, own_lo, ext_lo, own_n):
         tot += mx * my * (_fwd_ops(mz, sz) + _inv_ops(mz, sz, q0(mz, sz, 2)))                 # pass B
         own_z = hi[2] - lo[2]
         tot += own_z * (mx * _inv_ops(my, sy, q0(my, sy, 1)) + (hi[1] - lo[1]) * _inv_ops(mx, sx, q0(mx, sx, 0)))
-    return tot + 11 * mx * my * mz
+    return tot + 9 * mx * my * mz   # the per-mode 3x3 (Eq. 12): nine float64 operations
 
 
 def _rup(v, a):
