@@ -55,7 +55,7 @@ def fp64_issue_peak_tops(sm_mhz=None):
 # (workload, precision); the capture is summarised in the profiles/ file named
 # beside each entry. Absent: not captured for this kernel version.
 TRAFFIC_BYTES = {
-    ("yee256_ras8x8x8_ol2", "fp64"): 2965.7e6,   # transform_fp64_precond_grid256.md
+    ("yee256_ras8x8x8_ol2", "fp64"): 2965.6e6,   # transform_fp64_precond_grid256.md
     ("yee256_ras8x8x8_ol2", "bf16"): 748.3e6,    # fused_bf16_precond_grid256.md
     ("yee128_ras4x4x4_ol2", "fp64_ozaki"): 246.8e6,   # transform_fp64_ozaki_precond_grid128.md
 }
